@@ -1,0 +1,597 @@
+"""Plain FP64 CPU oracle for one Krylov-projected time step of the
+Deslauriers-Dubuc (DD) wavelet-collocation solver for filtered 2-D
+incompressible flow (Walsh & Alam, "Fujiwhara interaction of tropical cyclone
+scale vortices using a weighted residual collocation method").
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this module.  The
+library under ``paper_1604_08159_gb300/`` never imports it, and this module
+shares no code with the CUDA path (the only shared module is the seeded
+parameter generator ``paper_1604_08159_gb300/workloads.py``, which holds none of
+the method's arithmetic).
+
+Storage
+-------
+Every field is a full ``NJ x NJ`` float64 array indexed ``[k, i]`` (row ``k`` is
+the y index, column ``i`` the x index) with ``x_i = -pi + i*h``,
+``y_k = -pi + k*h``, ``h = 2*pi/NJ`` and ``NJ = N0 * 2**J`` on the doubly
+periodic square ``[-pi, pi)^2``.  The adaptive grid is a boolean mask of the
+same shape; a compact vector over the grid is ``field[mask]`` (row-major
+order).  Points of level ``j`` all lie on the sublattice of stride
+``s_j = 2**(J-j)``; most routines below work on such sublattice views
+``F[::s, ::s]``, on which the level-``j`` points are those with an odd row or
+column index.
+
+What each function follows
+--------------------------
+``levels``                 Sec. 2.4: nested dyadic meshes G^0 c ... c G^J.
+``dd4_x/dd4_y``            Sec. 2.4: DD subdivision of order 2p = 4 (the 4-point
+                           Lagrange predictor from the coarser neighbours).
+``predict_level``          Sec. 2.4: tensor-product DD prediction in 2-D.
+``reconstruct``            Eq. 6: u^N evaluated on the finest lattice from the
+                           retained coefficients (details of dropped points 0).
+``details``                Eq. 6: the coefficient that disappears at the coarser
+                           scale, d = u - Pred(u).
+``significant``            Eq. 6: epsilon-thresholding, |u - u^N|_inf < eps.
+``adjacent_zone``          Sec. 2.4 (2^d - 1 children inserted in the
+                           neighbourhood of a node); the rule itself is a
+                           reading (the adaptive wavelet collocation zone).
+``closure``                Perfect-reconstruction closure of the grid (reading).
+``stencil_levels``         Sec. 2.5: the finest spacing at which a point has
+                           neighbours (reading).
+``ghost_set``              Points outside the grid that the Sec. 2.5 stencils
+                           read, with their values from Eq. 6 (reading).
+``d1/d2``                  Sec. 2.5: collocation derivatives; for 2p = 4 the DD
+                           first-derivative weights are those of the 5-point
+                           4th-order central difference; the second-derivative
+                           reading is the 5-point 4th-order stencil.
+``streamfunction``         Poisson solve (the paper is silent): exact inverse of
+                           the 4th-order collocation Laplacian on the periodic
+                           finest lattice.
+``velocity``               U = dpsi/dy, V = -dpsi/dx.
+``strain``, ``smagorinsky_nut``, ``stress_vorticity_forcing``, ``sgs_forcing``
+                           Eq. 5: Smagorinsky model, vorticity form of -div(tau).
+``apply_operator``         Sec. 2.1/2.5: the frozen linear right-hand side A_n q.
+``arnoldi_phi1``           Abstract / Sec. 2.1: projection of the discrete system
+                           onto a Krylov subspace (exponential-Euler reading).
+``step``                   One full time step followed by grid adaptation.
+
+Parity pins live in ``tests/test_oracle_*.py`` (closed forms, invariants,
+brute force on tiny lattices, the paper's Table 1 convergence rate).  Every
+function above is pinned; none is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+__all__ = [
+    "Config", "State", "StepInfo", "levels", "dd4_x", "dd4_y", "predict_level",
+    "level_mask_sub", "reconstruct", "details", "significant", "adjacent_zone",
+    "closure", "stencil_levels", "ghost_set", "at", "d1", "d2",
+    "adaptive_derivatives", "streamfunction", "velocity", "strain",
+    "smagorinsky_nut", "stress_vorticity_forcing", "sgs_forcing", "laplacian_symbol",
+    "vortex_field", "Frozen", "freeze", "apply_operator", "arnoldi_phi1",
+    "phi1_augmented", "adapt", "initial_state", "state_from_field", "step",
+    "diagnostics", "BREAKDOWN_TOL",
+]
+
+# Happy-breakdown test of the Arnoldi process: stop when the new direction is
+# this small relative to |A v_j| (the Krylov space is then invariant).
+BREAKDOWN_TOL = 1e-12
+
+
+@dataclass
+class Config:
+    """Run parameters.  ``sgs`` is ``"off"``, ``"apriori"`` (Eq. 5 with a
+    constant strain-rate magnitude ``s_apriori``, as the paper does) or
+    ``"dynamic"`` (pointwise |S| from the resolved field)."""
+
+    n0: int
+    J: int
+    eps: float
+    re: float
+    dt: float = 1e-2
+    m: int = 20
+    sgs: str = "off"
+    cs: float = 0.0
+    s_apriori: float = 0.0
+    rayleigh_r: float = 0.0
+
+    @property
+    def NJ(self) -> int:
+        return self.n0 << self.J
+
+    @property
+    def h(self) -> float:
+        return 2.0 * np.pi / self.NJ
+
+    @property
+    def nu(self) -> float:
+        return 1.0 / self.re
+
+    @property
+    def nu_eff(self) -> float:
+        """Viscosity inside the linear operator: nu, plus the constant eddy
+        viscosity (C_s h_J)^2 |S| of Eq. 5 in the a-priori mode."""
+        if self.sgs == "apriori":
+            return self.nu + (self.cs * self.h) ** 2 * self.s_apriori
+        return self.nu
+
+
+# --------------------------------------------------------------------------
+# A1: lattice and levels (Sec. 2.4)
+# --------------------------------------------------------------------------
+
+def levels(n0: int, J: int) -> np.ndarray:
+    """Level of every finest-lattice point: 0 on the coarsest mesh (both
+    indices multiples of 2^J), else the level j at which the point is first
+    inserted, i.e. J - min(t(i), t(k)) with t(i) the number of trailing zero
+    bits of i capped at J (t(0) = J)."""
+    NJ = n0 << J
+    idx = np.arange(NJ)
+    t = np.zeros(NJ, dtype=np.int64)
+    for b in range(1, J + 1):
+        t[idx % (1 << b) == 0] = b
+    return (J - np.minimum(t[:, None], t[None, :])).astype(np.int64)
+
+
+def level_mask_sub(n: int) -> np.ndarray:
+    """On a sublattice of stride 2^(J-j), the level-j points are those with an
+    odd row or column index."""
+    odd = np.arange(n) % 2 == 1
+    return odd[None, :] | odd[:, None]
+
+
+def at(F: np.ndarray, di: int = 0, dk: int = 0) -> np.ndarray:
+    """Periodic neighbour access: result[k, i] = F[k + dk, i + di]."""
+    return np.roll(F, shift=(-dk, -di), axis=(0, 1))
+
+
+# --------------------------------------------------------------------------
+# A2: DD4 prediction, reconstruction and details (Sec. 2.4, Eq. 6)
+# --------------------------------------------------------------------------
+
+def dd4_x(F: np.ndarray) -> np.ndarray:
+    """DD order-4 prediction along x on a sublattice: the cubic through the
+    neighbours at -3, -1, +1, +3 evaluated at 0, weights (-1, 9, 9, -1)/16,
+    evaluated as (9*(a+b) - (c+d)) * (1/16)."""
+    return (9.0 * (at(F, -1) + at(F, 1)) - (at(F, -3) + at(F, 3))) * 0.0625
+
+
+def dd4_y(F: np.ndarray) -> np.ndarray:
+    """As ``dd4_x`` along y."""
+    return (9.0 * (at(F, 0, -1) + at(F, 0, 1)) - (at(F, 0, -3) + at(F, 0, 3))) * 0.0625
+
+
+def predict_level(F: np.ndarray, J: int, j: int) -> np.ndarray:
+    """DD prediction of every level-j point from coarser points.  Returns an
+    array on the stride-2^(J-j) sublattice: points odd in x only are predicted
+    along x, points odd in y only along y, points odd in both by the tensor
+    product (x prediction of the four rows, then y prediction).  Entries at
+    even-even sublattice points are not meaningful."""
+    s = 1 << (J - j)
+    sub = F[::s, ::s]
+    n = sub.shape[0]
+    odd = np.arange(n) % 2 == 1
+    oi, ok = odd[None, :], odd[:, None]
+    px = dd4_x(sub)
+    py = dd4_y(sub)
+    pxy = dd4_y(px)
+    return np.where(oi & ~ok, px, np.where(~oi & ok, py, pxy))
+
+
+def reconstruct(values: np.ndarray, active: np.ndarray, J: int) -> np.ndarray:
+    """R(u) of Eq. 6 on the full finest lattice: the values on the active set,
+    and coarse-to-fine DD prediction (detail 0) at every other point."""
+    R = np.where(active, values, 0.0)
+    for j in range(1, J + 1):
+        s = 1 << (J - j)
+        P = predict_level(R, J, j)
+        sub = R[::s, ::s]
+        fill = level_mask_sub(sub.shape[0]) & ~active[::s, ::s]
+        sub[fill] = P[fill]
+    return R
+
+
+def details(R: np.ndarray, active: np.ndarray, J: int) -> np.ndarray:
+    """Wavelet coefficients d = u - Pred(u) at active points of level >= 1
+    (Eq. 6); 0 elsewhere.  ``R`` must hold the values on the active set and on
+    the predictor points of every active point (true for a closed grid)."""
+    d = np.zeros_like(R)
+    for j in range(1, J + 1):
+        s = 1 << (J - j)
+        P = predict_level(R, J, j)
+        sub = R[::s, ::s]
+        sel = level_mask_sub(sub.shape[0]) & active[::s, ::s]
+        dv = d[::s, ::s]
+        dv[sel] = (sub - P)[sel]
+    return d
+
+
+# --------------------------------------------------------------------------
+# A3: significance, adjacent zone, closure, stencil levels, ghosts
+# --------------------------------------------------------------------------
+
+def significant(d: np.ndarray, active: np.ndarray, lev: np.ndarray, eps: float) -> np.ndarray:
+    """S = level 0 plus every active point of level >= 1 with |d| >= eps."""
+    return (lev == 0) | (active & (lev >= 1) & (np.abs(d) >= eps))
+
+
+def adjacent_zone(S: np.ndarray, lev: np.ndarray, J: int) -> np.ndarray:
+    """S plus its adjacent zone: every significant point of level j >= 1 adds
+    the lattice points of level j and j+1 (j+1 <= J) lying within 2^(J-j)
+    finest cells of it in both x and y (periodic).  Level 0 adds nothing."""
+    A = S.copy()
+    for j in range(1, J + 1):
+        Sj = S & (lev == j)
+        if not Sj.any():
+            continue
+        s = 1 << (J - j)
+        step = s // 2 if j < J else s
+        target = (lev == j) | (lev == j + 1)
+        offs = range(-s, s + 1, step)
+        for dk in offs:
+            for di in offs:
+                A |= np.roll(Sj, (dk, di), axis=(0, 1)) & target
+    return A
+
+
+def _predictor_marks(src: np.ndarray) -> np.ndarray:
+    """Given a mask of level-j points on their sublattice, mark the DD4
+    predictor points of each one (offsets +-1, +-3 along x, along y, or the
+    4 x 4 tensor product, according to the point's type)."""
+    n = src.shape[0]
+    odd = np.arange(n) % 2 == 1
+    oi, ok = odd[None, :], odd[:, None]
+    X = src & oi & ~ok
+    Y = src & ~oi & ok
+    XY = src & oi & ok
+    M = np.zeros_like(src)
+    for a in (-3, -1, 1, 3):
+        M |= np.roll(X, a, axis=1)
+        M |= np.roll(Y, a, axis=0)
+        for b in (-3, -1, 1, 3):
+            M |= np.roll(XY, (b, a), axis=(0, 1))
+    return M
+
+
+def closure(A: np.ndarray, J: int) -> np.ndarray:
+    """Close the grid under DD prediction, finest level first: every point of
+    level j in the grid adds its predictor points (all of coarser level), so
+    that the grid's values are a valid multiresolution representation."""
+    A = A.copy()
+    for j in range(J, 0, -1):
+        s = 1 << (J - j)
+        sub = A[::s, ::s]
+        src = sub & level_mask_sub(sub.shape[0])
+        sub |= _predictor_marks(src)
+    return A
+
+
+def stencil_levels(A: np.ndarray, lev: np.ndarray, J: int):
+    """Stencil level j* per axis for each active point P: the largest
+    j in [lev(P), J] such that P + h_j e or P - h_j e is active; lev(P) if
+    there is none.  Returns (jx, jy), -1 outside the grid."""
+    jx = np.where(A, lev, -1)
+    jy = jx.copy()
+    for j in range(0, J + 1):
+        s = 1 << (J - j)
+        sA = A[::s, ::s]
+        nbx = np.roll(sA, 1, axis=1) | np.roll(sA, -1, axis=1)
+        nby = np.roll(sA, 1, axis=0) | np.roll(sA, -1, axis=0)
+        vx = jx[::s, ::s]
+        vy = jy[::s, ::s]
+        vx[sA & nbx] = j
+        vy[sA & nby] = j
+    return jx, jy
+
+
+def ghost_set(A: np.ndarray, jx: np.ndarray, jy: np.ndarray, J: int) -> np.ndarray:
+    """Ghost points: the points P +- h_{j*} e, P +- 2 h_{j*} e read by the
+    derivative stencil of an active point P that are not active, plus, finest
+    level first, the non-active predictor points of every ghost."""
+    G = np.zeros_like(A)
+    for j in range(0, J + 1):
+        s = 1 << (J - j)
+        sx = (A & (jx == j))[::s, ::s]
+        sy = (A & (jy == j))[::s, ::s]
+        M = np.zeros_like(sx)
+        for a in (-2, -1, 1, 2):
+            M |= np.roll(sx, a, axis=1)
+            M |= np.roll(sy, a, axis=0)
+        gv = G[::s, ::s]
+        gv |= M
+    G &= ~A
+    for j in range(J, 0, -1):
+        s = 1 << (J - j)
+        gv = G[::s, ::s]
+        src = gv & level_mask_sub(gv.shape[0])
+        gv |= _predictor_marks(src) & ~A[::s, ::s]
+    return G
+
+
+# --------------------------------------------------------------------------
+# Collocation derivatives (Sec. 2.5)
+# --------------------------------------------------------------------------
+
+def d1(F: np.ndarray, axis: int, h: float) -> np.ndarray:
+    """First derivative with unit (sub)lattice offsets and spacing h:
+    (8 (u_{+1} - u_{-1}) - (u_{+2} - u_{-2})) / (12 h)."""
+    if axis == 1:
+        p1, m1, p2, m2 = at(F, 1), at(F, -1), at(F, 2), at(F, -2)
+    else:
+        p1, m1, p2, m2 = at(F, 0, 1), at(F, 0, -1), at(F, 0, 2), at(F, 0, -2)
+    return (8.0 * (p1 - m1) - (p2 - m2)) / (12.0 * h)
+
+
+def d2(F: np.ndarray, axis: int, h: float) -> np.ndarray:
+    """Second derivative: (-(u_{+2} + u_{-2}) + 16 (u_{+1} + u_{-1}) - 30 u) / (12 h^2)."""
+    if axis == 1:
+        p1, m1, p2, m2 = at(F, 1), at(F, -1), at(F, 2), at(F, -2)
+    else:
+        p1, m1, p2, m2 = at(F, 0, 1), at(F, 0, -1), at(F, 0, 2), at(F, 0, -2)
+    return (-(p2 + m2) + 16.0 * (p1 + m1) - 30.0 * F) / (12.0 * h * h)
+
+
+def adaptive_derivatives(R: np.ndarray, A: np.ndarray, jx: np.ndarray, jy: np.ndarray,
+                         J: int, hJ: float):
+    """Dx, Dy, Dxx, Dyy of the reconstructed field R at active points, each
+    along its axis with spacing h_{j*} = h_J 2^(J-j*) (lattice arrays, 0 off
+    the grid)."""
+    Dx = np.zeros_like(R)
+    Dy = np.zeros_like(R)
+    Dxx = np.zeros_like(R)
+    Dyy = np.zeros_like(R)
+    for j in range(0, J + 1):
+        s = 1 << (J - j)
+        h = hJ * s
+        sub = R[::s, ::s]
+        sx = (A & (jx == j))[::s, ::s]
+        sy = (A & (jy == j))[::s, ::s]
+        if sx.any():
+            Dx[::s, ::s][sx] = d1(sub, 1, h)[sx]
+            Dxx[::s, ::s][sx] = d2(sub, 1, h)[sx]
+        if sy.any():
+            Dy[::s, ::s][sy] = d1(sub, 0, h)[sy]
+            Dyy[::s, ::s][sy] = d2(sub, 0, h)[sy]
+    return Dx, Dy, Dxx, Dyy
+
+
+# --------------------------------------------------------------------------
+# A4/A5: streamfunction, velocity, Smagorinsky (Eq. 5)
+# --------------------------------------------------------------------------
+
+def laplacian_symbol(NJ: int, h: float) -> np.ndarray:
+    """sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta) / (12 h^2): minus the
+    Fourier symbol of the 4th-order second-derivative stencil, theta = 2 pi n / NJ."""
+    theta = 2.0 * np.pi * np.arange(NJ) / NJ
+    return (30.0 - 32.0 * np.cos(theta) + 2.0 * np.cos(2.0 * theta)) / (12.0 * h * h)
+
+
+def streamfunction(R: np.ndarray, h: float) -> np.ndarray:
+    """psi with L_h psi = -(R - mean R), L_h the 4th-order collocation
+    Laplacian on the periodic lattice, mean(psi) = 0."""
+    NJ = R.shape[0]
+    sig = laplacian_symbol(NJ, h)
+    den = sig[:, None] + sig[None, :]
+    den[0, 0] = 1.0
+    F = np.fft.fft2(R) / den
+    F[0, 0] = 0.0
+    return np.real(np.fft.ifft2(F))
+
+
+def velocity(psi: np.ndarray, h: float):
+    """U = dpsi/dy, V = -dpsi/dx (finest-lattice stencils)."""
+    return d1(psi, 0, h), -d1(psi, 1, h)
+
+
+def strain(psi: np.ndarray, U: np.ndarray, h: float):
+    """Resolved strain of the velocity (U, V) = (psi_y, -psi_x):
+    S11 = dU/dx = d2psi/dxdy (= -S22), S12 = (dU/dy + dV/dx)/2 = (psi_yy - psi_xx)/2."""
+    return d1(U, 1, h), 0.5 * (d2(psi, 0, h) - d2(psi, 1, h))
+
+
+def smagorinsky_nut(S11: np.ndarray, S12: np.ndarray, cs: float, h: float) -> np.ndarray:
+    """Eq. 5: nu_t = (C_s Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij) = 2 sqrt(S11^2 + S12^2)
+    in 2-D incompressible flow, Delta = h_J (the smallest DD scale)."""
+    return (cs * h) ** 2 * (2.0 * np.sqrt(S11 * S11 + S12 * S12))
+
+
+def stress_vorticity_forcing(S11: np.ndarray, S12: np.ndarray, nut: np.ndarray, h: float) -> np.ndarray:
+    """Vorticity of the momentum forcing -d tau_ij/dx_j with tau_ij = -2 nu_t S_ij:
+    g = (Dxx - Dyy)(2 nu_t S12) - 4 Dx Dy (nu_t S11)."""
+    a = 2.0 * nut * S12
+    c = nut * S11
+    return d2(a, 1, h) - d2(a, 0, h) - 4.0 * d1(d1(c, 0, h), 1, h)
+
+
+def sgs_forcing(psi: np.ndarray, U: np.ndarray, cs: float, h: float):
+    """Smagorinsky forcing of the vorticity equation with pointwise |S| (Eq. 5).
+    Returns (g, nu_t) on the lattice."""
+    S11, S12 = strain(psi, U, h)
+    nut = smagorinsky_nut(S11, S12, cs, h)
+    return stress_vorticity_forcing(S11, S12, nut, h), nut
+
+
+def vortex_field(NJ: int, xc, yc, gamma, s) -> np.ndarray:
+    """Sum of Gaussian vortices omega = Gamma/(pi s^2) exp(-r^2/s^2) (Sec. 3.1,
+    the Lamb-Oseen core), r the minimum-image distance on [-pi, pi)^2."""
+    h = 2.0 * np.pi / NJ
+    x = -np.pi + h * np.arange(NJ)
+    X = x[None, :]
+    Y = x[:, None]
+    om = np.zeros((NJ, NJ))
+    for xc_, yc_, g_, s_ in zip(np.atleast_1d(xc), np.atleast_1d(yc),
+                                np.atleast_1d(gamma), np.atleast_1d(s)):
+        dx = np.mod(X - xc_ + np.pi, 2.0 * np.pi) - np.pi
+        dy = np.mod(Y - yc_ + np.pi, 2.0 * np.pi) - np.pi
+        om = om + g_ / (np.pi * s_ * s_) * np.exp(-(dx * dx + dy * dy) / (s_ * s_))
+    return om
+
+
+# --------------------------------------------------------------------------
+# A6-A9: frozen operator, Arnoldi, phi_1, update
+# --------------------------------------------------------------------------
+
+@dataclass
+class Frozen:
+    """The linearisation frozen at t^n: grid, stencil levels, velocity and SGS
+    forcing at the lattice, effective viscosity and Rayleigh coefficient."""
+    A: np.ndarray
+    jx: np.ndarray
+    jy: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    g: np.ndarray
+    R: np.ndarray
+    psi: np.ndarray
+    nu_eff: float
+    r: float
+
+
+def freeze(cfg: Config, A: np.ndarray, omega: np.ndarray) -> Frozen:
+    """A4-A5: reconstruct omega, solve for psi, velocities and SGS forcing."""
+    lev = levels(cfg.n0, cfg.J)
+    jx, jy = stencil_levels(A, lev, cfg.J)
+    R = reconstruct(omega, A, cfg.J)
+    psi = streamfunction(R, cfg.h)
+    U, V = velocity(psi, cfg.h)
+    if cfg.sgs == "dynamic":
+        g, _ = sgs_forcing(psi, U, cfg.cs, cfg.h)
+    else:
+        g = np.zeros_like(R)
+    return Frozen(A, jx, jy, U, V, g, R, psi, cfg.nu_eff, cfg.rayleigh_r)
+
+
+def apply_operator(cfg: Config, fz: Frozen, q: np.ndarray) -> np.ndarray:
+    """A_n q = -U Dx q - V Dy q + nu_eff (Dxx + Dyy) q - r q at the active
+    points (compact vector in, compact vector out); derivatives at each point's
+    stencil level with ghost values from the DD reconstruction of q."""
+    Q = np.zeros_like(fz.R)
+    Q[fz.A] = q
+    RQ = reconstruct(Q, fz.A, cfg.J)
+    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h)
+    a = fz.A
+    return -fz.U[a] * Dx[a] - fz.V[a] * Dy[a] + fz.nu_eff * (Dxx[a] + Dyy[a]) - fz.r * q
+
+
+def phi1_augmented(H: np.ndarray, dt: float) -> np.ndarray:
+    """y = phi_1(dt H) e_1 from the exponential of the augmented matrix
+    [[dt H, e_1], [0, 0]] (its last column above the corner)."""
+    k = H.shape[0]
+    M = np.zeros((k + 1, k + 1))
+    M[:k, :k] = dt * H
+    M[0, k] = 1.0
+    E = scipy.linalg.expm(M)
+    return E[:k, k]
+
+
+@dataclass
+class StepInfo:
+    beta: float
+    k: int               # Krylov dimension used (< m after a happy breakdown)
+    h_last: float        # h_{k+1,k}
+    H: np.ndarray
+    y: np.ndarray
+
+
+def arnoldi_phi1(matvec, b: np.ndarray, m: int, dt: float):
+    """Krylov projection of dt * phi_1(dt A) b: Arnoldi with classical
+    Gram-Schmidt applied twice, unweighted l2 inner product over the active
+    points, happy breakdown when h_{j+1,j} <= BREAKDOWN_TOL |A v_j|.
+    Returns (dt * beta * V_k phi_1(dt H_k) e_1, StepInfo)."""
+    n = b.size
+    beta = float(np.linalg.norm(b))
+    if beta == 0.0:
+        return np.zeros(n), StepInfo(0.0, 0, 0.0, np.zeros((0, 0)), np.zeros(0))
+    Vb = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    Vb[:, 0] = b / beta
+    k = m
+    for j in range(m):
+        w = matvec(Vb[:, j])
+        wn = float(np.linalg.norm(w))
+        for _ in range(2):
+            c = Vb[:, : j + 1].T @ w
+            w = w - Vb[:, : j + 1] @ c
+            H[: j + 1, j] += c
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] <= BREAKDOWN_TOL * wn:
+            k = j + 1
+            break
+        Vb[:, j + 1] = w / H[j + 1, j]
+    y = phi1_augmented(H[:k, :k], dt)
+    return dt * beta * (Vb[:, :k] @ y), StepInfo(beta, k, float(H[k, k - 1]), H[: k + 1, :k].copy(), y)
+
+
+# --------------------------------------------------------------------------
+# A10: adaptation, initial state, full step, diagnostics
+# --------------------------------------------------------------------------
+
+@dataclass
+class State:
+    active: np.ndarray
+    omega: np.ndarray    # lattice array, meaningful on ``active``
+    t: float = 0.0
+    nstep: int = 0
+
+
+def adapt(cfg: Config, active: np.ndarray, omega: np.ndarray):
+    """Grid adaptation: details of omega on the current grid, threshold,
+    adjacent zone, closure; values at newly added points from the
+    reconstruction R(omega) on the current grid.  Returns (A', omega', d)."""
+    lev = levels(cfg.n0, cfg.J)
+    R = reconstruct(omega, active, cfg.J)
+    d = details(R, active, cfg.J)
+    S = significant(d, active, lev, cfg.eps)
+    A2 = closure(adjacent_zone(S, lev, cfg.J), cfg.J)
+    return A2, np.where(A2, R, 0.0), d
+
+
+def state_from_field(cfg: Config, omega_lattice: np.ndarray) -> State:
+    """Initial grid from a field sampled on the full lattice: the full-lattice
+    transform, then one thresholding/adaptation pass."""
+    full = np.ones(omega_lattice.shape, dtype=bool)
+    A, om, _ = adapt(cfg, full, np.asarray(omega_lattice, dtype=np.float64))
+    return State(A, om)
+
+
+def initial_state(cfg: Config, xc, yc, gamma, s) -> State:
+    return state_from_field(cfg, vortex_field(cfg.NJ, xc, yc, gamma, s))
+
+
+def step(cfg: Config, st: State):
+    """One Krylov-projected exponential-Euler step,
+    omega^{n+1} = omega^n + dt phi_1(dt A_n)(A_n omega^n + g_n),
+    followed by grid adaptation.  Returns (new state, StepInfo)."""
+    fz = freeze(cfg, st.active, st.omega)
+    om = st.omega[st.active]
+    b = apply_operator(cfg, fz, om) + fz.g[st.active]
+    inc, info = arnoldi_phi1(lambda q: apply_operator(cfg, fz, q), b, cfg.m, cfg.dt)
+    new = np.zeros_like(st.omega)
+    new[st.active] = om + inc
+    A2, om2, _ = adapt(cfg, st.active, new)
+    return State(A2, om2, st.t + cfg.dt, st.nstep + 1), info
+
+
+def diagnostics(cfg: Config, st: State) -> dict:
+    """Energy E = 1/2 int |U|^2, enstrophy Z = 1/2 int omega^2, palinstrophy
+    P = 1/2 int |grad omega|^2 and circulation int omega, by the rectangle rule
+    on the reconstructed lattice fields."""
+    h = cfg.h
+    R = reconstruct(st.omega, st.active, cfg.J)
+    psi = streamfunction(R, h)
+    U, V = velocity(psi, h)
+    gx, gy = d1(R, 1, h), d1(R, 0, h)
+    w = h * h
+    return {
+        "E": 0.5 * w * float(np.sum(U * U + V * V)),
+        "Z": 0.5 * w * float(np.sum(R * R)),
+        "P": 0.5 * w * float(np.sum(gx * gx + gy * gy)),
+        "circulation": w * float(np.sum(R)),
+        "n_active": int(st.active.sum()),
+    }
