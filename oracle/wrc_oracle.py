@@ -367,9 +367,12 @@ def adaptive_derivatives(R: np.ndarray, A: np.ndarray, jx: np.ndarray, jy: np.nd
 
 def laplacian_symbol(NJ: int, h: float) -> np.ndarray:
     """sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta) / (12 h^2): minus the
-    Fourier symbol of the 4th-order second-derivative stencil, theta = 2 pi n / NJ."""
-    theta = 2.0 * np.pi * np.arange(NJ) / NJ
-    return (30.0 - 32.0 * np.cos(theta) + 2.0 * np.cos(2.0 * theta)) / (12.0 * h * h)
+    Fourier symbol of the 4th-order second-derivative stencil at
+    theta = 2 pi n / NJ.  Evaluated through the exact identity
+    30 - 32 cos t + 2 cos 2t = 16 s^2 (3 + s^2), s = sin(t/2), which avoids the
+    cancellation of the direct form at small theta."""
+    s2 = np.sin(np.pi * np.arange(NJ) / NJ) ** 2
+    return 16.0 * s2 * (3.0 + s2) / (12.0 * h * h)
 
 
 def streamfunction(R: np.ndarray, h: float) -> np.ndarray:
