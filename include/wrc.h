@@ -1,0 +1,191 @@
+/*
+ * wrc.h -- C ABI of the GB300 library for the Deslauriers-Dubuc (DD)
+ * wavelet-collocation solver of filtered 2-D incompressible flow with a
+ * Krylov-projected time step (Walsh & Alam, "Fujiwhara interaction of
+ * tropical cyclone scale vortices using a weighted residual collocation
+ * method", arXiv:1604.08159).
+ *
+ * Problem (Sec. 2.2-2.5 in their barotropic, incompressible reading): the
+ * vorticity omega on the doubly periodic square [-pi, pi)^2 obeys
+ *     d omega/dt + U . grad omega = nu_eff lap omega + g_SGS - r omega,
+ *     lap psi = -(omega - mean omega),  U = dpsi/dy,  V = -dpsi/dx,
+ * with nu = 1/Re, the Smagorinsky model of Eq. 5 (constant |S| "a priori",
+ * or pointwise |S| as a vorticity forcing g_SGS), and Rayleigh friction r.
+ * omega is held on an adaptive grid: the finest lattice is NJ x NJ with
+ * NJ = n0 * 2^J, h_J = 2 pi / NJ; the grid is the epsilon-thresholded set of
+ * DD4 wavelet coefficients (Eq. 6) plus its adjacent zone and closure.  One
+ * time step is the exponential-Euler step
+ *     omega^{n+1} = omega^n + dt phi_1(dt A_n) (A_n omega^n + g_n)
+ * with A_n the frozen linear operator (Sec. 2.1: projection of the discrete
+ * system onto a Krylov subspace), followed by grid adaptation.
+ *
+ * Conventions common to every call:
+ *  - Lattice arrays are NJ*NJ, row-major, index p = k*NJ + i with
+ *    x_i = -pi + i h_J, y_k = -pi + k h_J.
+ *  - "Active" vectors are ordered by increasing lattice index p.
+ *  - A pointer argument with device_ptr = 0 is a host pointer; with
+ *    device_ptr = 1 it is CUDA device memory that the run's stream may read
+ *    or write.  The caller owns every buffer it passes; nothing is retained
+ *    after the call returns.
+ *  - Every call returns a wrc_status; nothing is thrown across the ABI.
+ *    wrc_last_error() gives a message for the last failing call on a run.
+ *  - Calls on one run are not thread-safe; distinct runs are independent.
+ *  - wrc_step is asynchronous on the run's stream; every query
+ *    synchronises that stream before it returns.
+ */
+#ifndef WRC_H
+#define WRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wrc_run wrc_run;
+
+typedef enum {
+    WRC_OK = 0,
+    WRC_ERR_ARG = -1,            /* invalid argument or configuration */
+    WRC_ERR_OOM = -2,            /* a device allocation failed */
+    WRC_ERR_CUDA = -3,           /* a CUDA call or kernel launch failed */
+    WRC_ERR_BREAKDOWN_NAN = -4,  /* a non-finite value appeared in the Arnoldi process */
+    WRC_ERR_TIMEOUT = -5,        /* a bounded wait ran out */
+    WRC_ERR_BUSY = -6,           /* the server has no free slot or memory */
+    WRC_ERR_STATE = -7           /* call out of order (e.g. step before init) */
+} wrc_status;
+
+typedef enum { WRC_FP64 = 0, WRC_MIXED = 1 } wrc_precision;
+typedef enum { WRC_SGS_OFF = 0, WRC_SGS_APRIORI = 1, WRC_SGS_DYNAMIC = 2 } wrc_sgs;
+typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
+               WRC_FIELD_V = 3, WRC_FIELD_NUT = 4 } wrc_field;
+
+#define WRC_MAX_M 31       /* largest Krylov dimension */
+#define WRC_MAX_NJ 4096    /* largest finest lattice (NJ*NJ < 2^24) */
+#define WRC_MAX_VORTICES 64
+
+/* Run parameters.
+ *  n0        coarsest points per direction: a power of two, >= 4
+ *  J         refinement levels, >= 1, with n0 * 2^J <= WRC_MAX_NJ
+ *  krylov_m  Krylov dimension m, 1..WRC_MAX_M
+ *  sgs       wrc_sgs; prec: wrc_precision
+ *  eps       threshold on |d| (absolute), >= 0 (Eq. 6)
+ *  re        Reynolds number; nu = 1/re
+ *  cs        Smagorinsky constant C_s (Eq. 5), filter width Delta = h_J
+ *  s_apriori the constant |S| used when sgs == WRC_SGS_APRIORI
+ *  rayleigh_r linear damping coefficient r (Sec. 2.3), >= 0
+ *  dt        time step, > 0                                            */
+typedef struct {
+    int32_t n0, J, krylov_m, sgs, prec, reserved;
+    double eps, re, cs, s_apriori, rayleigh_r, dt;
+} wrc_config;
+
+/* Create a run on the current CUDA device, bound to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Allocates the run's
+ * device state.  Errors: WRC_ERR_ARG for an invalid config or out == NULL,
+ * WRC_ERR_OOM, WRC_ERR_CUDA.  On error *out is NULL. */
+wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out);
+
+/* Initial condition (Sec. 3.1): the sum of n Gaussian vortices
+ * omega = gamma/(pi s^2) exp(-r^2/s^2), r the minimum-image distance to
+ * (xc, yc), sampled on the full lattice; then the full-lattice forward
+ * transform, thresholding and adaptation (Eq. 6).  Host arrays of length n,
+ * 1 <= n <= WRC_MAX_VORTICES, s > 0. */
+wrc_status wrc_init_vortices(wrc_run* run, int32_t n, const double* xc, const double* yc,
+                             const double* gamma, const double* s);
+
+/* Initial condition from a sampled lattice field omega_lattice (NJ*NJ),
+ * then transform, thresholding and adaptation as above. */
+wrc_status wrc_init_field(wrc_run* run, const double* omega_lattice, int32_t device_ptr);
+
+/* Set the adaptive grid directly: `active` (NJ*NJ bytes, 0/1) and the values
+ * omega_lattice (NJ*NJ, read at active points only).  The grid must contain
+ * every level-0 point and be closed under DD prediction (every active point's
+ * predictor points active); otherwise WRC_ERR_ARG.  No thresholding is done;
+ * stencil levels and ghost points are rebuilt. */
+wrc_status wrc_set_grid(wrc_run* run, const uint8_t* active, const double* omega_lattice,
+                        int32_t device_ptr);
+
+/* Rebuild the grid from the current omega with threshold eps (which becomes
+ * the run's eps): details on the grid, significance, adjacent zone, closure,
+ * values at new points from the reconstruction (Eq. 6). */
+wrc_status wrc_threshold(wrc_run* run, double eps);
+
+/* Advance nsteps time steps (each: reconstruction, streamfunction, velocity
+ * and SGS forcing, Krylov projection, phi_1 update, adaptation).  Returns
+ * after the launches are queued; one host synchronisation per step reads the
+ * new grid's sizes. */
+wrc_status wrc_step(wrc_run* run, int32_t nsteps);
+
+/* Wait for the run's stream.  Returns WRC_ERR_BREAKDOWN_NAN if a step met a
+ * non-finite Arnoldi coefficient since the last call. */
+wrc_status wrc_sync(wrc_run* run);
+
+/* Sizes of the current grid: active points, ghost points and active points
+ * per level (per_level has J+1 entries; any pointer may be NULL). */
+wrc_status wrc_query_counts(wrc_run* run, int64_t* n_active, int64_t* n_ghost, int64_t* per_level);
+
+/* The active set: lattice indices (int32) and omega values, ordered by
+ * lattice index; at most `cap` entries are written (WRC_ERR_ARG if cap is
+ * smaller than the active count).  Either output may be NULL. */
+wrc_status wrc_query_active(wrc_run* run, int32_t* idx_out, double* omega_out, int64_t cap,
+                            int32_t device_ptr);
+
+/* Masks of the current grid as NJ*NJ bytes (0/1): active points, ghost
+ * points, and the significant points of the last thresholding.  Any output
+ * may be NULL. */
+wrc_status wrc_query_masks(wrc_run* run, uint8_t* active, uint8_t* ghost, uint8_t* significant,
+                           int32_t device_ptr);
+
+/* Wavelet details d = u - Pred(u) of the last thresholding (Eq. 6), one per
+ * active point of the grid it was computed on (0 at level-0 points), in that
+ * grid's order; cap as in wrc_query_active. */
+wrc_status wrc_query_details(wrc_run* run, double* d_out, int64_t cap, int32_t device_ptr);
+
+/* Per active point the stencil level j* along x and y (Sec. 2.5: the finest
+ * level at which the point has an active neighbour), as bytes. */
+wrc_status wrc_query_stencil_levels(wrc_run* run, uint8_t* jx_out, uint8_t* jy_out, int64_t cap,
+                                    int32_t device_ptr);
+
+/* Lattice field (NJ*NJ) for the current state: WRC_FIELD_OMEGA the
+ * reconstruction R(omega) (Eq. 6), PSI the streamfunction, U and V the
+ * velocity, NUT the Smagorinsky eddy viscosity (C_s h_J)^2 |S| (Eq. 5). */
+wrc_status wrc_query_field(wrc_run* run, int32_t which, double* out, int32_t device_ptr);
+
+/* Freeze the linearisation at the current state (reconstruction,
+ * streamfunction, velocity, SGS forcing), as the first part of a step does. */
+wrc_status wrc_freeze(wrc_run* run);
+
+/* w = A_n q at the active points for the frozen linearisation (Sec. 2.5
+ * derivatives at each point's stencil level, ghost values by DD prediction):
+ * A_n q = -U Dx q - V Dy q + nu_eff (Dxx + Dyy) q - r q.  Optionally also
+ * the SGS forcing g_n at the active points (g_out may be NULL).  q and w
+ * hold n_active values.  Requires wrc_freeze after the last grid change. */
+wrc_status wrc_apply_operator(wrc_run* run, const double* q, double* w, double* g_out,
+                              int32_t device_ptr);
+
+/* Krylov data of the last step: beta = |b|, k = dimension used (< m after
+ * a happy breakdown), h_last = h_{k+1,k}, H ((m+1) x m row-major, may be
+ * NULL) and y = phi_1(dt H_k) e_1 (m entries, may be NULL). */
+wrc_status wrc_query_krylov(wrc_run* run, double* beta, int32_t* k, double* h_last, double* H,
+                            double* y);
+
+/* Diagnostics of the current state, out[0..7] = energy E = 1/2 int |U|^2,
+ * enstrophy Z = 1/2 int omega^2, palinstrophy P = 1/2 int |grad omega|^2,
+ * circulation int omega (rectangle rule on the reconstructed lattice
+ * fields), time t, step count, active count, ghost count. */
+wrc_status wrc_diagnostics(wrc_run* run, double out[8]);
+
+/* Message of the last failing call on `run` ("" if none); for a NULL run,
+ * the last failure of wrc_create on this thread. */
+const char* wrc_last_error(const wrc_run* run);
+
+/* Release the run's device memory (synchronises its stream first). */
+void wrc_destroy(wrc_run* run);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WRC_H */

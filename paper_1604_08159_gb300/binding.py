@@ -1,0 +1,319 @@
+"""ctypes binding of ``libwrc.so`` (include/wrc.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of the method.  Host arrays are numpy arrays; device arrays are
+CUDA tensors (``torch``), passed with ``device_ptr = 1``.  If the library is
+missing, loading fails with an error: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_uint8, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwrc.so")
+
+WRC_OK = 0
+STATUS = {0: "WRC_OK", -1: "WRC_ERR_ARG", -2: "WRC_ERR_OOM", -3: "WRC_ERR_CUDA",
+          -4: "WRC_ERR_BREAKDOWN_NAN", -5: "WRC_ERR_TIMEOUT", -6: "WRC_ERR_BUSY", -7: "WRC_ERR_STATE"}
+FIELD_OMEGA, FIELD_PSI, FIELD_U, FIELD_V, FIELD_NUT = range(5)
+MAX_M = 31
+
+
+class WrcConfig(ctypes.Structure):
+    _fields_ = [("n0", c_int32), ("J", c_int32), ("krylov_m", c_int32), ("sgs", c_int32),
+                ("prec", c_int32), ("reserved", c_int32), ("eps", c_double), ("re", c_double),
+                ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double)]
+
+
+# name -> (restype, argtypes); the list of entry points of include/wrc.h
+SIGNATURES = {
+    "wrc_create": (c_int32, [POINTER(WrcConfig), c_void_p, POINTER(c_void_p)]),
+    "wrc_init_vortices": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wrc_init_field": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "wrc_set_grid": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "wrc_threshold": (c_int32, [c_void_p, c_double]),
+    "wrc_step": (c_int32, [c_void_p, c_int32]),
+    "wrc_sync": (c_int32, [c_void_p]),
+    "wrc_query_counts": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wrc_query_active": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
+    "wrc_query_masks": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
+    "wrc_query_details": (c_int32, [c_void_p, c_void_p, c_int64, c_int32]),
+    "wrc_query_stencil_levels": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
+    "wrc_query_field": (c_int32, [c_void_p, c_int32, c_void_p, c_int32]),
+    "wrc_freeze": (c_int32, [c_void_p]),
+    "wrc_apply_operator": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
+    "wrc_query_krylov": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "wrc_diagnostics": (c_int32, [c_void_p, c_void_p]),
+    "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
+    "wrc_destroy": (None, [c_void_p]),
+}
+
+_lib = None
+
+
+class WrcError(RuntimeError):
+    def __init__(self, fn: str, status: int, message: str):
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libwrc.so (built by ``paper_1604_08159_gb300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run paper_1604_08159_gb300.build.build() (nvcc) first")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """(pointer, device_ptr flag) of a numpy array or a CUDA tensor; (None, 0) for None."""
+    if x is None:
+        return None, 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(fn: str, st: int, run=None):
+    if st != WRC_OK:
+        msg = load().wrc_last_error(run)
+        raise WrcError(fn, st, msg.decode() if msg else "")
+
+
+def _flag(*ptrs):
+    flags = {f for _, f in ptrs if _ is not None}
+    if len(flags) > 1:
+        raise ValueError("mix of host and device buffers in one call")
+    return flags.pop() if flags else 0
+
+
+def make_config(params) -> WrcConfig:
+    """WrcConfig from a ``workloads.RunParams``-like object."""
+    return WrcConfig(params.n0, params.J, params.m, params.sgs, params.prec, 0, params.eps, params.re,
+                     params.cs, params.s_apriori, params.rayleigh_r, params.dt)
+
+
+# ---- entry points -------------------------------------------------------------
+
+def wrc_create(cfg: WrcConfig, stream: int | None = None) -> int:
+    h = c_void_p()
+    _check("wrc_create", load().wrc_create(byref(cfg), c_void_p(stream or 0), byref(h)))
+    return h.value
+
+
+def wrc_init_vortices(run, xc, yc, gamma, s):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xc, yc, gamma, s)]
+    _check("wrc_init_vortices", load().wrc_init_vortices(run, arrs[0].size, *[a.ctypes.data for a in arrs]), run)
+
+
+def wrc_init_field(run, omega):
+    p, f = _ptr(omega)
+    _check("wrc_init_field", load().wrc_init_field(run, p, f), run)
+
+
+def wrc_set_grid(run, active, omega):
+    pa, fa = _ptr(active)
+    po, fo = _ptr(omega)
+    _check("wrc_set_grid", load().wrc_set_grid(run, pa, po, _flag((pa, fa), (po, fo))), run)
+
+
+def wrc_threshold(run, eps: float):
+    _check("wrc_threshold", load().wrc_threshold(run, eps), run)
+
+
+def wrc_step(run, nsteps: int = 1):
+    _check("wrc_step", load().wrc_step(run, nsteps), run)
+
+
+def wrc_sync(run):
+    _check("wrc_sync", load().wrc_sync(run), run)
+
+
+def wrc_query_counts(run, J: int):
+    na, ng = c_int64(), c_int64()
+    per = np.zeros(J + 1, dtype=np.int64)
+    _check("wrc_query_counts", load().wrc_query_counts(run, byref(na), byref(ng), per.ctypes.data), run)
+    return na.value, ng.value, per
+
+
+def wrc_query_active(run, idx_out=None, omega_out=None, cap: int = 0):
+    pi, fi = _ptr(idx_out)
+    po, fo = _ptr(omega_out)
+    _check("wrc_query_active", load().wrc_query_active(run, pi, po, cap, _flag((pi, fi), (po, fo))), run)
+
+
+def wrc_query_masks(run, active=None, ghost=None, significant=None):
+    ps = [_ptr(x) for x in (active, ghost, significant)]
+    _check("wrc_query_masks", load().wrc_query_masks(run, ps[0][0], ps[1][0], ps[2][0], _flag(*ps)), run)
+
+
+def wrc_query_details(run, d_out, cap: int):
+    p, f = _ptr(d_out)
+    _check("wrc_query_details", load().wrc_query_details(run, p, cap, f), run)
+
+
+def wrc_query_stencil_levels(run, jx_out, jy_out, cap: int):
+    px, fx = _ptr(jx_out)
+    py, fy = _ptr(jy_out)
+    _check("wrc_query_stencil_levels",
+           load().wrc_query_stencil_levels(run, px, py, cap, _flag((px, fx), (py, fy))), run)
+
+
+def wrc_query_field(run, which: int, out):
+    p, f = _ptr(out)
+    _check("wrc_query_field", load().wrc_query_field(run, which, p, f), run)
+
+
+def wrc_freeze(run):
+    _check("wrc_freeze", load().wrc_freeze(run), run)
+
+
+def wrc_apply_operator(run, q, w, g_out=None):
+    ps = [_ptr(x) for x in (q, w, g_out)]
+    _check("wrc_apply_operator", load().wrc_apply_operator(run, ps[0][0], ps[1][0], ps[2][0], _flag(*ps)), run)
+
+
+def wrc_query_krylov(run, m: int):
+    beta, hl = c_double(), c_double()
+    k = c_int32()
+    H = np.zeros((m + 1) * m)
+    y = np.zeros(m)
+    _check("wrc_query_krylov",
+           load().wrc_query_krylov(run, byref(beta), byref(k), byref(hl), H.ctypes.data, y.ctypes.data), run)
+    return {"beta": beta.value, "k": k.value, "h_last": hl.value, "H": H.reshape(m + 1, m), "y": y}
+
+
+def wrc_diagnostics(run):
+    out = np.zeros(8)
+    _check("wrc_diagnostics", load().wrc_diagnostics(run, out.ctypes.data), run)
+    keys = ("E", "Z", "P", "circulation", "t", "nstep", "n_active", "n_ghost")
+    return dict(zip(keys, out.tolist()))
+
+
+def wrc_last_error(run) -> str:
+    m = load().wrc_last_error(run)
+    return m.decode() if m else ""
+
+
+def wrc_destroy(run):
+    if run:
+        load().wrc_destroy(run)
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class Run:
+    """One run on the current CUDA device (numpy in and out by default)."""
+
+    def __init__(self, params, stream: int | None = None):
+        self.params = params
+        self.NJ = params.n0 << params.J
+        self.J = params.J
+        self.m = params.m
+        self.h = wrc_create(make_config(params), stream)
+
+    def close(self):
+        if self.h:
+            wrc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_vortices(self, v):
+        wrc_init_vortices(self.h, v.xc, v.yc, v.gamma, v.s)
+
+    def init_field(self, omega):
+        wrc_init_field(self.h, np.ascontiguousarray(omega, dtype=np.float64) if isinstance(omega, np.ndarray) else omega)
+
+    def set_grid(self, active, omega):
+        wrc_set_grid(self.h, np.ascontiguousarray(active, dtype=np.uint8), np.ascontiguousarray(omega, dtype=np.float64))
+
+    def threshold(self, eps):
+        wrc_threshold(self.h, eps)
+
+    def step(self, n=1):
+        wrc_step(self.h, n)
+
+    def sync(self):
+        wrc_sync(self.h)
+
+    def counts(self):
+        return wrc_query_counts(self.h, self.J)
+
+    def active(self):
+        na = self.counts()[0]
+        idx = np.zeros(na, dtype=np.int32)
+        om = np.zeros(na)
+        wrc_query_active(self.h, idx, om, na)
+        return idx, om
+
+    def masks(self):
+        n2 = self.NJ * self.NJ
+        a, g, s = (np.zeros(n2, dtype=np.uint8) for _ in range(3))
+        wrc_query_masks(self.h, a, g, s)
+        return [x.reshape(self.NJ, self.NJ).astype(bool) for x in (a, g, s)]
+
+    def details(self, count):
+        d = np.zeros(count)
+        wrc_query_details(self.h, d, count)
+        return d
+
+    def stencil_levels(self):
+        na = self.counts()[0]
+        jx = np.zeros(na, dtype=np.uint8)
+        jy = np.zeros(na, dtype=np.uint8)
+        wrc_query_stencil_levels(self.h, jx, jy, na)
+        return jx, jy
+
+    def field(self, which):
+        out = np.zeros(self.NJ * self.NJ)
+        wrc_query_field(self.h, which, out)
+        return out.reshape(self.NJ, self.NJ)
+
+    def freeze(self):
+        wrc_freeze(self.h)
+
+    def apply_operator(self, q):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        w = np.zeros_like(q)
+        g = np.zeros_like(q)
+        wrc_apply_operator(self.h, q, w, g)
+        return w, g
+
+    def krylov(self):
+        return wrc_query_krylov(self.h, self.m)
+
+    def diagnostics(self):
+        return wrc_diagnostics(self.h)

@@ -1,0 +1,666 @@
+// C ABI (include/wrc.h): run state on the device and the orchestration of one
+// time step -- reconstruction, streamfunction, velocity and Smagorinsky
+// forcing, Krylov projection with the phi_1 update, grid adaptation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+
+#include "../../include/wrc.h"
+#include "kernels.h"
+
+using namespace wrc;
+
+namespace {
+
+// Happy breakdown of the Arnoldi process: h_{j+1,j} <= tol |A v_j|.
+constexpr double kBreakdownTol = 1e-12;
+
+thread_local std::string g_create_error;
+
+// Growable device buffer on the stream-ordered allocator.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t grow(size_t need, size_t keep, cudaStream_t s) {
+        if (need <= bytes) return cudaSuccess;
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, need, s);
+        if (e != cudaSuccess) return e;
+        if (p && keep) {
+            e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (p) cudaFreeAsync(p, s);
+        p = q;
+        bytes = need;
+        return cudaSuccess;
+    }
+    void release(cudaStream_t s) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T* as() const { return (T*)p; }
+};
+
+}  // namespace
+
+struct wrc_run {
+    wrc_config cfg{};
+    Geom g{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    std::string err;
+    long long N = 0;   // NJ * NJ
+
+    // lattice arrays
+    double* L = nullptr;     // omega on the grid / its reconstruction
+    double* Lq = nullptr;    // Krylov vector on the grid + ghost values
+    double* psi = nullptr;
+    double2* C1 = nullptr;   // FFT / Smagorinsky work arrays
+    double2* C2 = nullptr;
+    uint8_t *act = nullptr, *nxt = nullptr, *gho = nullptr, *sig = nullptr, *JJ = nullptr;
+    int* list = nullptr;     // active points, then ghosts by level
+    int *blk_counts = nullptr, *blk_off = nullptr, *counts_dev = nullptr;
+    int* counts_host = nullptr;   // pinned
+    int* flag_dev = nullptr;
+    unsigned long long* lvl_dev = nullptr;
+    double* vort_dev = nullptr;
+    double* diag_dev = nullptr;
+    PoissonPlan plan;
+
+    // compact arrays (one entry per active point)
+    DevBuf meta[2], omega[2], Ua, Va, ga, det, w, basis, tmp;
+    int cur = 0;
+    long long cap = 0;
+
+    // Krylov small arrays
+    KrylovDev K{};
+
+    // state
+    long long n_active = 0, n_ghost = 0, det_count = 0;
+    long long gcount[16] = {0}, goff[16] = {0};
+    double t = 0.0;
+    long long nstep = 0;
+    bool init = false, frozen = false;
+};
+
+namespace {
+
+wrc_status fail(wrc_run* R, wrc_status s, const std::string& msg) {
+    if (R) R->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(R, e_ == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+    } while (0)
+
+#define CKL(what)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = cudaGetLastError();                                                    \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(R, WRC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+#define TRY(expr)                                                                               \
+    do {                                                                                        \
+        wrc_status s_ = (expr);                                                                 \
+        if (s_ != WRC_OK) return s_;                                                            \
+    } while (0)
+
+double nu_eff(const wrc_run* R) {
+    double nu = 1.0 / R->cfg.re;
+    if (R->cfg.sgs == WRC_SGS_APRIORI) nu += (R->cfg.cs * R->g.h) * (R->cfg.cs * R->g.h) * R->cfg.s_apriori;
+    return nu;
+}
+
+wrc_status ensure_capacity(wrc_run* R, long long n) {
+    if (n <= R->cap) return WRC_OK;
+    long long c = n + n / 4 + 1024;
+    c = (c + 255) / 256 * 256;
+    const int m = R->cfg.krylov_m;
+    const cudaStream_t s = R->st;
+    const size_t b8 = sizeof(double) * (size_t)c;
+    // meta/omega of the current grid and the details keep their contents
+    CK(R->meta[R->cur].grow(sizeof(uint32_t) * c, sizeof(uint32_t) * R->n_active, s));
+    CK(R->meta[1 - R->cur].grow(sizeof(uint32_t) * c, 0, s));
+    CK(R->omega[R->cur].grow(b8, sizeof(double) * R->n_active, s));
+    CK(R->omega[1 - R->cur].grow(b8, 0, s));
+    CK(R->det.grow(b8, sizeof(double) * R->det_count, s));
+    CK(R->Ua.grow(b8, 0, s));
+    CK(R->Va.grow(b8, 0, s));
+    CK(R->ga.grow(b8, 0, s));
+    CK(R->w.grow(b8, 0, s));
+    CK(R->tmp.grow(b8, 0, s));
+    // the basis is rebuilt every step; its leading dimension changes with c
+    R->basis.release(s);
+    CK(R->basis.grow(b8 * (size_t)(m + 1), 0, s));
+    R->cap = c;
+    R->K.basis = R->basis.p;
+    R->K.w = R->w.p;
+    R->K.ld = c;
+    return WRC_OK;
+}
+
+// The new grid is in `nxt` and its values are in L: stencil levels, ghosts,
+// compaction into the index list, then the compact arrays of the new grid.
+wrc_status rebuild_from_mask(wrc_run* R) {
+    const Geom& g = R->g;
+    const cudaStream_t s = R->st;
+    CK(cudaMemsetAsync(R->gho, 0, R->N, s));
+    launch_stencil_ghost(R->nxt, R->gho, R->JJ, g, s);
+    for (int j = g.J; j >= 1; --j) launch_closure_level(R->gho, R->nxt, j, g, s);
+    const int nkeys = g.J + 1;
+    launch_compact(R->nxt, R->gho, g, nkeys, R->blk_counts, R->blk_off, R->counts_dev, R->list, s);
+    CKL("compaction");
+    CK(cudaMemcpyAsync(R->counts_host, R->counts_dev, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const long long na = R->counts_host[0];
+    long long off = na, ng = 0;
+    for (int j = 1; j <= g.J; ++j) {
+        R->gcount[j] = R->counts_host[j];
+        R->goff[j] = off;
+        off += R->gcount[j];
+        ng += R->gcount[j];
+    }
+    TRY(ensure_capacity(R, na));
+    const int nc = 1 - R->cur;
+    launch_finalize<double>(R->list, na, R->JJ, R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<double>(), s);
+    CKL("finalize");
+    std::swap(R->act, R->nxt);
+    R->cur = nc;
+    R->n_active = na;
+    R->n_ghost = ng;
+    R->frozen = false;
+    return WRC_OK;
+}
+
+// Thresholding with eps: details of the values in L on the current grid (or
+// on every lattice point for a freshly sampled field), significance and
+// adjacent zone into nxt, closure, then the rebuild.
+wrc_status threshold_current(wrc_run* R, double eps, bool whole_lattice) {
+    const Geom& g = R->g;
+    const cudaStream_t s = R->st;
+    CK(cudaMemsetAsync(R->sig, 0, R->N, s));
+    CK(cudaMemsetAsync(R->nxt, 0, R->N, s));
+    if (whole_lattice) {
+        launch_details_adj<double>(nullptr, R->N, R->L, eps, nullptr, R->sig, R->nxt, g, s);
+        R->det_count = 0;
+    } else {
+        launch_details_adj<double>(R->meta[R->cur].as<uint32_t>(), R->n_active, R->L, eps, R->det.as<double>(),
+                                   R->sig, R->nxt, g, s);
+        R->det_count = R->n_active;
+    }
+    for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
+    CKL("threshold");
+    return rebuild_from_mask(R);
+}
+
+// L <- R(omega): the grid values, then coarse-to-fine prediction elsewhere.
+wrc_status reconstruct(wrc_run* R) {
+    launch_scatter<double>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<double>(), R->n_active, R->L, R->st);
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<double>(R->L, R->act, j, R->g, R->st);
+    CKL("reconstruct");
+    return WRC_OK;
+}
+
+// Linearisation at the current state: R(omega), psi, U, V and the SGS forcing.
+wrc_status freeze(wrc_run* R) {
+    TRY(reconstruct(R));
+    const cudaStream_t s = R->st;
+    launch_poisson(R->plan, R->L, R->psi, R->C1, R->C2, R->g, s);
+    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
+    launch_velocity_active<double>(R->psi, meta, R->n_active, R->Ua.as<double>(), R->Va.as<double>(), R->g, s);
+    if (R->cfg.sgs == WRC_SGS_DYNAMIC) {
+        double* t0 = (double*)R->C1;
+        double* t1 = t0 + R->N;
+        double* t2 = (double*)R->C2;
+        double* t3 = t2 + R->N;
+        launch_sgs<double>(R->psi, meta, R->n_active, R->cfg.cs, R->ga.as<double>(), t0, t1, t2, t3, R->g, s);
+    }
+    CKL("freeze");
+    R->frozen = true;
+    return WRC_OK;
+}
+
+void ghost_fill(wrc_run* R, double* F, const int* kstop, int jstep) {
+    for (int j = 1; j <= R->g.J; ++j)
+        launch_ghost_fill<double>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
+}
+
+// Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)).
+wrc_status krylov(wrc_run* R) {
+    const cudaStream_t s = R->st;
+    const long long n = R->n_active;
+    const int m = R->cfg.krylov_m;
+    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
+    const double* ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<double>() : nullptr;
+    KrylovDev& K = R->K;
+    CK(cudaMemsetAsync(K.H, 0, sizeof(double) * (m + 1) * m, s));
+    // b = A omega + g
+    launch_matvec<double>(R->L, meta, n, R->Ua.as<double>(), R->Va.as<double>(), ga, nu_eff(R), R->cfg.rayleigh_r,
+                          R->w.as<double>(), R->g, nullptr, 0, s);
+    launch_gs_pass<double>(K, n, 0, 0, nullptr, K.o1, nullptr, 0, s);
+    launch_krylov_start(K, m, s);
+    launch_normalize_scatter<double>(K, meta, n, 0, m, R->Lq, s);
+    for (int j = 0; j < m; ++j) {
+        ghost_fill(R, R->Lq, K.kstop, j);
+        launch_matvec<double>(R->Lq, meta, n, R->Ua.as<double>(), R->Va.as<double>(), nullptr, nu_eff(R),
+                              R->cfg.rayleigh_r, R->w.as<double>(), R->g, K.kstop, j, s);
+        launch_gs_pass<double>(K, n, j + 1, j + 1, nullptr, K.o1, K.kstop, j, s);
+        launch_gs_pass<double>(K, n, j + 1, j + 1, K.o1, K.o2, K.kstop, j, s);
+        launch_gs_pass<double>(K, n, j + 1, 0, K.o2, K.o3, K.kstop, j, s);
+        launch_arnoldi_col(K, j, m, kBreakdownTol, s);
+        if (j + 1 < m) launch_normalize_scatter<double>(K, meta, n, j + 1, m, R->Lq, s);
+    }
+    launch_phi1(K, m, R->cfg.dt, s);
+    launch_update<double>(K, meta, n, R->cfg.dt, R->omega[R->cur].as<double>(), R->L, s);
+    CKL("krylov");
+    return WRC_OK;
+}
+
+wrc_status step_once(wrc_run* R) {
+    TRY(freeze(R));
+    TRY(krylov(R));
+    // adaptation: L holds omega^{n+1} at the grid points; reconstruct the rest
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<double>(R->L, R->act, j, R->g, R->st);
+    TRY(threshold_current(R, R->cfg.eps, false));
+    R->t += R->cfg.dt;
+    R->nstep += 1;
+    return WRC_OK;
+}
+
+wrc_status check_ready(wrc_run* R) {
+    if (!R) return WRC_ERR_ARG;
+    if (!R->init) return fail(R, WRC_ERR_STATE, "run has no initial condition");
+    return WRC_OK;
+}
+
+wrc_status copy_out(wrc_run* R, void* dst, const void* src, size_t bytes, int device_ptr) {
+    if (!bytes) return WRC_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, R->st));
+    return WRC_OK;
+}
+
+wrc_status copy_in(wrc_run* R, void* dst, const void* src, size_t bytes, int device_ptr) {
+    if (!bytes) return WRC_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, R->st));
+    return WRC_OK;
+}
+
+void free_run(wrc_run* R) {
+    if (!R) return;
+    cudaStream_t s = R->st;
+    cudaStreamSynchronize(s);
+    for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
+                    &R->basis, &R->tmp})
+        b->release(s);
+    cudaStreamSynchronize(s);
+    void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list,
+                    R->blk_counts, R->blk_off, R->counts_dev, R->flag_dev, R->lvl_dev, R->vort_dev, R->diag_dev,
+                    R->K.H, R->K.o1, R->K.partials, R->K.kstop};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (R->counts_host) cudaFreeHost(R->counts_host);
+    poisson_plan_free(R->plan);
+    delete R;
+}
+
+bool valid_config(const wrc_config* c, std::string& why) {
+    if (!c) { why = "cfg is NULL"; return false; }
+    if (c->n0 < 4 || (c->n0 & (c->n0 - 1))) { why = "n0 must be a power of two >= 4"; return false; }
+    if (c->J < 1 || c->J > 10) { why = "J must be in 1..10"; return false; }
+    if ((long long)c->n0 << c->J > WRC_MAX_NJ) { why = "n0 * 2^J exceeds WRC_MAX_NJ"; return false; }
+    if (c->krylov_m < 1 || c->krylov_m > WRC_MAX_M) { why = "krylov_m must be in 1..WRC_MAX_M"; return false; }
+    if (c->sgs < 0 || c->sgs > 2) { why = "unknown sgs mode"; return false; }
+    if (c->prec != WRC_FP64) { why = "only WRC_FP64 is available in this build"; return false; }
+    if (!(c->eps >= 0) || !(c->re > 0) || !(c->dt > 0) || !(c->rayleigh_r >= 0) || !(c->cs >= 0) ||
+        !(c->s_apriori >= 0)) {
+        why = "eps, re, dt, rayleigh_r, cs, s_apriori out of range";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
+    if (!out) return WRC_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!valid_config(cfg, why)) {
+        g_create_error = why;
+        return WRC_ERR_ARG;
+    }
+    wrc_run* R = new wrc_run();
+    R->cfg = *cfg;
+    R->st = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&R->device);
+    const int NJ = cfg->n0 << cfg->J;
+    int Lg = 0;
+    while ((1 << Lg) < NJ) ++Lg;
+    R->g.NJ = NJ;
+    R->g.L = Lg;
+    R->g.J = cfg->J;
+    R->g.mask = NJ - 1;
+    R->g.h = 2.0 * 3.141592653589793238462643383279502884 / NJ;
+    R->N = (long long)NJ * NJ;
+    const long long N = R->N;
+    const int m = cfg->krylov_m;
+    const int nblk = (int)((N + kTile - 1) / kTile);
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    cudaError_t e = cudaSuccess;
+    void** lp[] = {(void**)&R->L, (void**)&R->Lq, (void**)&R->psi};
+    for (auto p : lp)
+        if (e == cudaSuccess) e = alloc(p, sizeof(double) * N);
+    if (e == cudaSuccess) e = alloc((void**)&R->C1, sizeof(double2) * N);
+    if (e == cudaSuccess) e = alloc((void**)&R->C2, sizeof(double2) * N);
+    uint8_t** mp[] = {&R->act, &R->nxt, &R->gho, &R->sig, &R->JJ};
+    for (auto p : mp)
+        if (e == cudaSuccess) e = alloc((void**)p, N);
+    if (e == cudaSuccess) e = alloc((void**)&R->list, sizeof(int) * N);
+    if (e == cudaSuccess) e = alloc((void**)&R->blk_counts, sizeof(int) * nblk * kMaxKeys);
+    if (e == cudaSuccess) e = alloc((void**)&R->blk_off, sizeof(int) * nblk * kMaxKeys);
+    if (e == cudaSuccess) e = alloc((void**)&R->counts_dev, sizeof(int) * kMaxKeys);
+    if (e == cudaSuccess) e = alloc((void**)&R->flag_dev, sizeof(int) * 4);
+    if (e == cudaSuccess) e = alloc((void**)&R->lvl_dev, sizeof(unsigned long long) * 16);
+    if (e == cudaSuccess) e = alloc((void**)&R->vort_dev, sizeof(double) * 4 * WRC_MAX_VORTICES);
+    if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
+    // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
+    if (e == cudaSuccess) e = alloc((void**)&R->K.H, sizeof(double) * (m + 1) * m);
+    if (e == cudaSuccess) e = alloc((void**)&R->K.o1, sizeof(double) * (3 * 33 + 1 + 32));
+    if (e == cudaSuccess) e = alloc((void**)&R->K.partials, sizeof(double) * kMaxBlocks * 33);
+    if (e == cudaSuccess) e = alloc((void**)&R->K.kstop, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&R->counts_host, sizeof(int) * kMaxKeys);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
+        free_run(R);
+        return e == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA;
+    }
+    R->K.o2 = R->K.o1 + 33;
+    R->K.o3 = R->K.o2 + 33;
+    R->K.beta = R->K.o3 + 33;
+    R->K.y = R->K.beta + 1;
+    R->K.flags = R->K.kstop + 1;
+    R->K.counter = (unsigned*)(R->K.kstop + 2);
+    cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 4, R->st);
+    cudaMemsetAsync(R->flag_dev, 0, sizeof(int) * 4, R->st);
+    if (poisson_plan_init(R->plan, R->g, R->st) != 0 || phi1_init() != 0) {
+        g_create_error = "FFT/expm kernel set-up failed";
+        free_run(R);
+        return WRC_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(R->st) != cudaSuccess) {
+        g_create_error = std::string("set-up: ") + cudaGetErrorString(cudaGetLastError());
+        free_run(R);
+        return WRC_ERR_CUDA;
+    }
+    *out = R;
+    return WRC_OK;
+}
+
+wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const double* yc, const double* gamma,
+                             const double* s) {
+    if (!R) return WRC_ERR_ARG;
+    if (n < 1 || n > WRC_MAX_VORTICES || !xc || !yc || !gamma || !s)
+        return fail(R, WRC_ERR_ARG, "need 1..WRC_MAX_VORTICES vortices and four host arrays");
+    double prm[4 * WRC_MAX_VORTICES];
+    for (int v = 0; v < n; ++v) {
+        if (!(s[v] > 0) || !std::isfinite(xc[v]) || !std::isfinite(yc[v]) || !std::isfinite(gamma[v]))
+            return fail(R, WRC_ERR_ARG, "vortex parameters must be finite with s > 0");
+        prm[v] = xc[v];
+        prm[n + v] = yc[v];
+        prm[2 * n + v] = gamma[v];
+        prm[3 * n + v] = s[v];
+    }
+    CK(cudaMemcpyAsync(R->vort_dev, prm, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, R->st));
+    launch_init_vortices<double>(R->L, R->vort_dev, n, R->g, R->st);
+    CKL("init_vortices");
+    CK(cudaStreamSynchronize(R->st));   // prm is a stack array
+    CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
+    R->n_active = 0;
+    TRY(threshold_current(R, R->cfg.eps, true));
+    R->init = true;
+    R->t = 0.0;
+    R->nstep = 0;
+    return WRC_OK;
+}
+
+wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t device_ptr) {
+    if (!R) return WRC_ERR_ARG;
+    if (!omega_lattice) return fail(R, WRC_ERR_ARG, "omega_lattice is NULL");
+    TRY(copy_in(R, R->L, omega_lattice, sizeof(double) * R->N, device_ptr));
+    CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
+    R->n_active = 0;
+    TRY(threshold_current(R, R->cfg.eps, true));
+    R->init = true;
+    R->t = 0.0;
+    R->nstep = 0;
+    return WRC_OK;
+}
+
+wrc_status wrc_set_grid(wrc_run* R, const uint8_t* active, const double* omega_lattice, int32_t device_ptr) {
+    if (!R) return WRC_ERR_ARG;
+    if (!active || !omega_lattice) return fail(R, WRC_ERR_ARG, "NULL input");
+    TRY(copy_in(R, R->nxt, active, R->N, device_ptr));
+    TRY(copy_in(R, R->L, omega_lattice, sizeof(double) * R->N, device_ptr));
+    CK(cudaMemsetAsync(R->flag_dev, 0, sizeof(int), R->st));
+    launch_validate_grid(R->nxt, R->flag_dev, R->g, R->st);
+    CKL("validate");
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, R->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, R->st));
+    CK(cudaStreamSynchronize(R->st));
+    if (flag & 1) return fail(R, WRC_ERR_ARG, "grid misses a level-0 point");
+    if (flag & 2) return fail(R, WRC_ERR_ARG, "grid is not closed under DD prediction");
+    CK(cudaMemsetAsync(R->sig, 0, R->N, R->st));
+    R->det_count = 0;
+    TRY(rebuild_from_mask(R));
+    R->init = true;
+    return WRC_OK;
+}
+
+wrc_status wrc_threshold(wrc_run* R, double eps) {
+    TRY(check_ready(R));
+    if (!(eps >= 0)) return fail(R, WRC_ERR_ARG, "eps must be >= 0");
+    R->cfg.eps = eps;
+    TRY(reconstruct(R));
+    return threshold_current(R, eps, false);
+}
+
+wrc_status wrc_step(wrc_run* R, int32_t nsteps) {
+    TRY(check_ready(R));
+    if (nsteps < 0) return fail(R, WRC_ERR_ARG, "nsteps < 0");
+    for (int q = 0; q < nsteps; ++q) TRY(step_once(R));
+    return WRC_OK;
+}
+
+wrc_status wrc_sync(wrc_run* R) {
+    if (!R) return WRC_ERR_ARG;
+    CK(cudaStreamSynchronize(R->st));
+    int flags = 0;
+    CK(cudaMemcpy(&flags, R->K.flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags & 1) {
+        CK(cudaMemset(R->K.flags, 0, sizeof(int)));
+        return fail(R, WRC_ERR_BREAKDOWN_NAN, "non-finite value in the Arnoldi process");
+    }
+    return WRC_OK;
+}
+
+wrc_status wrc_query_counts(wrc_run* R, int64_t* n_active, int64_t* n_ghost, int64_t* per_level) {
+    TRY(check_ready(R));
+    if (n_active) *n_active = R->n_active;
+    if (n_ghost) *n_ghost = R->n_ghost;
+    if (per_level) {
+        CK(cudaMemsetAsync(R->lvl_dev, 0, sizeof(unsigned long long) * 16, R->st));
+        launch_level_counts(R->meta[R->cur].as<uint32_t>(), R->n_active, R->lvl_dev, R->g, R->st);
+        CKL("level counts");
+        unsigned long long h[16];
+        CK(cudaMemcpyAsync(h, R->lvl_dev, sizeof(h), cudaMemcpyDeviceToHost, R->st));
+        CK(cudaStreamSynchronize(R->st));
+        for (int j = 0; j <= R->g.J; ++j) per_level[j] = (int64_t)h[j];
+    }
+    return WRC_OK;
+}
+
+wrc_status wrc_query_active(wrc_run* R, int32_t* idx_out, double* omega_out, int64_t cap, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
+    const long long n = R->n_active;
+    if (idx_out) {
+        int* tmpi = R->tmp.as<int>();   // tmp holds >= n doubles, i.e. >= 2n ints
+        launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, tmpi, nullptr, nullptr, R->st);
+        CKL("unpack");
+        TRY(copy_out(R, idx_out, tmpi, sizeof(int) * n, device_ptr));
+    }
+    if (omega_out) TRY(copy_out(R, omega_out, R->omega[R->cur].p, sizeof(double) * n, device_ptr));
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_query_masks(wrc_run* R, uint8_t* active, uint8_t* ghost, uint8_t* significant, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (active) TRY(copy_out(R, active, R->act, R->N, device_ptr));
+    if (ghost) TRY(copy_out(R, ghost, R->gho, R->N, device_ptr));
+    if (significant) TRY(copy_out(R, significant, R->sig, R->N, device_ptr));
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_query_details(wrc_run* R, double* d_out, int64_t cap, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!d_out) return fail(R, WRC_ERR_ARG, "NULL output");
+    if (cap < R->det_count) return fail(R, WRC_ERR_ARG, "cap smaller than the detail count");
+    TRY(copy_out(R, d_out, R->det.p, sizeof(double) * R->det_count, device_ptr));
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_query_stencil_levels(wrc_run* R, uint8_t* jx_out, uint8_t* jy_out, int64_t cap, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
+    const long long n = R->n_active;
+    uint8_t* jx = R->tmp.as<uint8_t>();
+    uint8_t* jy = jx + n;
+    launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, nullptr, jx, jy, R->st);
+    CKL("unpack");
+    if (jx_out) TRY(copy_out(R, jx_out, jx, n, device_ptr));
+    if (jy_out) TRY(copy_out(R, jy_out, jy, n, device_ptr));
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_query_field(wrc_run* R, int32_t which, double* out, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!out || which < 0 || which > 4) return fail(R, WRC_ERR_ARG, "bad field or NULL output");
+    const size_t bytes = sizeof(double) * R->N;
+    if (which == WRC_FIELD_OMEGA) {
+        TRY(reconstruct(R));
+        TRY(copy_out(R, out, R->L, bytes, device_ptr));
+    } else {
+        TRY(freeze(R));
+        if (which == WRC_FIELD_PSI) {
+            TRY(copy_out(R, out, R->psi, bytes, device_ptr));
+        } else {
+            double* t0 = (double*)R->C1;   // U
+            double* t1 = t0 + R->N;        // V
+            double* t2 = (double*)R->C2;   // nu_t
+            launch_lattice_uv_nut<double>(R->psi, t0, t1, which == WRC_FIELD_NUT ? t2 : nullptr, R->cfg.cs, t0,
+                                          R->g, R->st);
+            CKL("lattice fields");
+            const double* src = which == WRC_FIELD_U ? t0 : which == WRC_FIELD_V ? t1 : t2;
+            TRY(copy_out(R, out, src, bytes, device_ptr));
+        }
+    }
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_freeze(wrc_run* R) {
+    TRY(check_ready(R));
+    TRY(freeze(R));
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_apply_operator(wrc_run* R, const double* q, double* w, double* g_out, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!R->frozen) return fail(R, WRC_ERR_STATE, "call wrc_freeze after the last grid change");
+    if (!q || !w) return fail(R, WRC_ERR_ARG, "NULL input or output");
+    const long long n = R->n_active;
+    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
+    TRY(copy_in(R, R->tmp.p, q, sizeof(double) * n, device_ptr));
+    launch_scatter<double>(meta, R->tmp.as<double>(), n, R->Lq, R->st);
+    ghost_fill(R, R->Lq, nullptr, 0);
+    launch_matvec<double>(R->Lq, meta, n, R->Ua.as<double>(), R->Va.as<double>(), nullptr, nu_eff(R),
+                          R->cfg.rayleigh_r, R->tmp.as<double>(), R->g, nullptr, 0, R->st);
+    CKL("apply_operator");
+    TRY(copy_out(R, w, R->tmp.p, sizeof(double) * n, device_ptr));
+    if (g_out) {
+        if (R->cfg.sgs == WRC_SGS_DYNAMIC) {
+            TRY(copy_out(R, g_out, R->ga.p, sizeof(double) * n, device_ptr));
+        } else if (device_ptr) {
+            CK(cudaMemsetAsync(g_out, 0, sizeof(double) * n, R->st));
+        } else {
+            std::memset(g_out, 0, sizeof(double) * n);
+        }
+    }
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_query_krylov(wrc_run* R, double* beta, int32_t* k, double* h_last, double* H, double* y) {
+    TRY(check_ready(R));
+    const int m = R->cfg.krylov_m;
+    double hb[(WRC_MAX_M + 1) * WRC_MAX_M];
+    double bb = 0, yb[WRC_MAX_M + 1];
+    int kk = 0;
+    CK(cudaMemcpyAsync(hb, R->K.H, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToHost, R->st));
+    CK(cudaMemcpyAsync(&bb, R->K.beta, sizeof(double), cudaMemcpyDeviceToHost, R->st));
+    CK(cudaMemcpyAsync(yb, R->K.y, sizeof(double) * m, cudaMemcpyDeviceToHost, R->st));
+    CK(cudaMemcpyAsync(&kk, R->K.kstop, sizeof(int), cudaMemcpyDeviceToHost, R->st));
+    CK(cudaStreamSynchronize(R->st));
+    if (beta) *beta = bb;
+    if (k) *k = kk;
+    if (h_last) *h_last = kk > 0 ? hb[(size_t)kk * m + (kk - 1)] : 0.0;
+    if (H) std::memcpy(H, hb, sizeof(double) * (m + 1) * m);
+    if (y) std::memcpy(y, yb, sizeof(double) * m);
+    return WRC_OK;
+}
+
+wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
+    TRY(check_ready(R));
+    if (!out) return fail(R, WRC_ERR_ARG, "NULL output");
+    TRY(reconstruct(R));
+    launch_poisson(R->plan, R->L, R->psi, R->C1, R->C2, R->g, R->st);
+    launch_diag(R->L, R->psi, R->K.partials, R->K.counter, R->diag_dev, R->g, R->st);
+    CKL("diagnostics");
+    double s[4];
+    CK(cudaMemcpyAsync(s, R->diag_dev, sizeof(s), cudaMemcpyDeviceToHost, R->st));
+    CK(cudaStreamSynchronize(R->st));
+    const double w = R->g.h * R->g.h;
+    out[0] = 0.5 * w * s[2];
+    out[1] = 0.5 * w * s[1];
+    out[2] = 0.5 * w * s[3];
+    out[3] = w * s[0];
+    out[4] = R->t;
+    out[5] = (double)R->nstep;
+    out[6] = (double)R->n_active;
+    out[7] = (double)R->n_ghost;
+    return WRC_OK;
+}
+
+const char* wrc_last_error(const wrc_run* R) { return R ? R->err.c_str() : g_create_error.c_str(); }
+
+void wrc_destroy(wrc_run* R) { free_run(R); }
+
+}  // extern "C"

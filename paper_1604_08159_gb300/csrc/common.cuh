@@ -1,0 +1,127 @@
+// Device-side helpers shared by the library's kernels: lattice geometry,
+// levels, the DD4 predictor (Sec. 2.4) and the collocation stencils (Sec. 2.5).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace wrc {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 8;   // grid-stride cap: 8 resident blocks per SM
+constexpr int kMaxKeys = 16;          // compaction buckets (active + ghosts per level)
+constexpr int kTileRounds = 16;       // compaction tile = kThreads * kTileRounds points
+constexpr int kTile = kThreads * kTileRounds;
+
+// Finest-lattice geometry.  NJ is a power of two; p = k*NJ + i.
+struct Geom {
+    int NJ;      // points per direction
+    int L;       // log2(NJ)
+    int J;       // number of refinement levels
+    int mask;    // NJ - 1
+    double h;    // h_J = 2 pi / NJ
+};
+
+// Level of lattice point (i, k): 0 when both are multiples of 2^J, else the
+// level at which the point is first inserted, J - min(tz(i), tz(k), J).
+__host__ __device__ __forceinline__ int level_of(int i, int k, int J) {
+#ifdef __CUDA_ARCH__
+    return J - (__ffs((unsigned)(i | k) | (1u << J)) - 1);
+#else
+    unsigned v = (unsigned)(i | k) | (1u << J);
+    int t = 0;
+    while (!(v & 1u)) { v >>= 1; ++t; }
+    return J - t;
+#endif
+}
+
+// Arithmetic with explicit IEEE rounding (no FMA contraction), so that the
+// predictor and the details are bit-identical to a plain evaluation of
+// (9*(a+b) - (c+d)) * 0.0625.
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+
+// DD order-4 predictor from the neighbours at -1, +1 (a, b) and -3, +3 (c, d):
+// the cubic through them evaluated at 0, weights (-1, 9, 9, -1)/16.
+template <typename T>
+__device__ __forceinline__ T dd4(T a, T b, T c, T d) {
+    return rmul(rsub(rmul(T(9), radd(a, b)), radd(c, d)), T(0.0625));
+}
+
+// DD prediction at lattice point (i, k) of level j >= 1 from the coarser
+// points of field F: along x for points odd in x only, along y for points odd
+// in y only, tensor product (x prediction of four rows, then y) otherwise.
+template <typename T>
+__device__ __forceinline__ T predict(const T* __restrict__ F, int i, int k, int j, const Geom& g) {
+    const int sh = g.J - j;
+    const int s = 1 << sh;
+    const int m = g.mask;
+    const bool oi = (i >> sh) & 1;
+    const bool ok = (k >> sh) & 1;
+    if (oi && !ok) {
+        const T* row = F + ((size_t)k << g.L);
+        return dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+    }
+    if (!oi && ok) {
+        return dd4<T>(F[((size_t)((k - s) & m) << g.L) + i], F[((size_t)((k + s) & m) << g.L) + i],
+                      F[((size_t)((k - 3 * s) & m) << g.L) + i], F[((size_t)((k + 3 * s) & m) << g.L) + i]);
+    }
+    T r[4];
+    const int ks[4] = {k - s, k + s, k - 3 * s, k + 3 * s};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const T* row = F + ((size_t)(ks[q] & m) << g.L);
+        r[q] = dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+    }
+    return dd4<T>(r[0], r[1], r[2], r[3]);
+}
+
+// Number of level-j points (j >= 1): the stride-2^(J-j) sublattice minus the
+// stride-2^(J-j+1) one.
+__host__ __device__ __forceinline__ long long level_count(int j, const Geom& g) {
+    const long long n = g.NJ >> (g.J - j);
+    return n * n - (n / 2) * (n / 2);
+}
+
+// t-th level-j point: first the odd sublattice rows (all columns), then the
+// even rows (odd columns), each in row-major order.
+__device__ __forceinline__ void level_point(long long t, int j, const Geom& g, int& i, int& k) {
+    const int sh = g.J - j;
+    const int n = g.NJ >> sh;
+    const long long half = (long long)n * (n >> 1);
+    int ic, kr;
+    if (t < half) {
+        kr = 2 * (int)(t / n) + 1;
+        ic = (int)(t % n);
+    } else {
+        const long long u = t - half;
+        const int nh = n >> 1;
+        kr = 2 * (int)(u / nh);
+        ic = 2 * (int)(u % nh) + 1;
+    }
+    i = ic << sh;
+    k = kr << sh;
+}
+
+// Packed per-active-point word: lattice index (24 bits) and the stencil
+// levels j*_x, j*_y (4 bits each).
+__host__ __device__ __forceinline__ uint32_t pack_meta(int p, int jx, int jy) {
+    return (uint32_t)p | ((uint32_t)jx << 24) | ((uint32_t)jy << 28);
+}
+__host__ __device__ __forceinline__ int meta_pos(uint32_t m) { return (int)(m & 0xFFFFFFu); }
+__host__ __device__ __forceinline__ int meta_jx(uint32_t m) { return (int)((m >> 24) & 15u); }
+__host__ __device__ __forceinline__ int meta_jy(uint32_t m) { return (int)(m >> 28); }
+
+inline int blocks_for(long long n, int threads = kThreads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > kMaxBlocks) b = kMaxBlocks;
+    return (int)b;
+}
+
+}  // namespace wrc

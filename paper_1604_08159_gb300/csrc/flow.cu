@@ -1,0 +1,268 @@
+// Velocity from the streamfunction, the Smagorinsky forcing of Eq. 5, the
+// frozen linear operator A_n of the Krylov step (Sec. 2.5 collocation
+// derivatives at each point's stencil level), and lattice diagnostics.
+#include "kernels.h"
+
+namespace wrc {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T at(const T* __restrict__ F, int i, int k, const Geom& g) {
+    return F[((size_t)(k & g.mask) << g.L) + (i & g.mask)];
+}
+
+// 4th-order first and second derivatives on the finest lattice, scaled by
+// c1 = 1/(12 h), c2 = 1/(12 h^2).
+template <typename T>
+__device__ __forceinline__ T dx1(const T* F, int i, int k, const Geom& g, T c1) {
+    return (T(8) * (at(F, i + 1, k, g) - at(F, i - 1, k, g)) - (at(F, i + 2, k, g) - at(F, i - 2, k, g))) * c1;
+}
+template <typename T>
+__device__ __forceinline__ T dy1(const T* F, int i, int k, const Geom& g, T c1) {
+    return (T(8) * (at(F, i, k + 1, g) - at(F, i, k - 1, g)) - (at(F, i, k + 2, g) - at(F, i, k - 2, g))) * c1;
+}
+template <typename T>
+__device__ __forceinline__ T dx2(const T* F, int i, int k, const Geom& g, T c2) {
+    return (-(at(F, i + 2, k, g) + at(F, i - 2, k, g)) + T(16) * (at(F, i + 1, k, g) + at(F, i - 1, k, g)) -
+            T(30) * at(F, i, k, g)) * c2;
+}
+template <typename T>
+__device__ __forceinline__ T dy2(const T* F, int i, int k, const Geom& g, T c2) {
+    return (-(at(F, i, k + 2, g) + at(F, i, k - 2, g)) + T(16) * (at(F, i, k + 1, g) + at(F, i, k - 1, g)) -
+            T(30) * at(F, i, k, g)) * c2;
+}
+
+template <typename T>
+__global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __restrict__ meta, long long n,
+                                  T* __restrict__ Ua, T* __restrict__ Va, Geom g, T c1) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        const int i = p & g.mask, k = p >> g.L;
+        Ua[a] = dy1(psi, i, k, g, c1);
+        Va[a] = -dx1(psi, i, k, g, c1);
+    }
+}
+
+// Smagorinsky pass 1: t0 = U = dpsi/dy, t1 = S12 = (psi_yy - psi_xx)/2.
+template <typename T>
+__global__ void k_sgs1(const T* __restrict__ psi, T* __restrict__ t0, T* __restrict__ t1, Geom g, T c1, T c2) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        t0[p] = dy1(psi, i, k, g, c1);
+        t1[p] = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
+    }
+}
+
+// Pass 2: S11 = dU/dx, nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5);
+// t2 = 2 nu_t S12, t3 = nu_t S11, t1 <- nu_t.
+template <typename T>
+__global__ void k_sgs2(const T* __restrict__ t0, T* __restrict__ t1, T* __restrict__ t2, T* __restrict__ t3,
+                       Geom g, T c1, T csh2) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const T s11 = dx1(t0, i, k, g, c1);
+        const T s12 = t1[p];
+        const T nut = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
+        t2[p] = T(2) * nut * s12;
+        t3[p] = nut * s11;
+        t1[p] = nut;
+    }
+}
+
+// Pass 3: t0 = d(t3)/dy.
+template <typename T>
+__global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c1) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        t0[p] = dy1(t3, i, k, g, c1);
+    }
+}
+
+// Pass 4 at the active points: g = Dxx(t2) - Dyy(t2) - 4 Dx(t0).
+template <typename T>
+__global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const uint32_t* __restrict__ meta,
+                       long long n, T* __restrict__ ga, Geom g, T c1, T c2) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        const int i = p & g.mask, k = p >> g.L;
+        ga[a] = dx2(t2, i, k, g, c2) - dy2(t2, i, k, g, c2) - T(4) * dx1(t0, i, k, g, c1);
+    }
+}
+
+template <typename T>
+__global__ void k_lattice_uv(const T* __restrict__ psi, T* __restrict__ U, T* __restrict__ V, Geom g, T c1) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        U[p] = dy1(psi, i, k, g, c1);
+        V[p] = -dx1(psi, i, k, g, c1);
+    }
+}
+
+template <typename T>
+__global__ void k_lattice_nut(const T* __restrict__ psi, const T* __restrict__ U, T* __restrict__ nut, Geom g,
+                              T c1, T c2, T csh2) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const T s11 = dx1(U, i, k, g, c1);
+        const T s12 = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
+        nut[p] = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
+    }
+}
+
+// w = A_n q at the active points: -U Dx q - V Dy q + nu (Dxx + Dyy) q - r q (+ g),
+// each derivative along its axis at the point's stencil level j*, i.e. with
+// lattice offsets +-s, +-2s, s = 2^(J-j*), and spacing h_{j*} = s h_J.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_matvec(const T* __restrict__ F, const uint32_t* __restrict__ meta,
+                                                     long long n, const T* __restrict__ Ua,
+                                                     const T* __restrict__ Va, const T* __restrict__ ga, T nu,
+                                                     T r, T* __restrict__ w, Geom g, T c1J, T c2J,
+                                                     const int* __restrict__ kstop, int jstep) {
+    if (kstop && jstep >= *kstop) return;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const uint32_t mw = meta[a];
+        const int p = meta_pos(mw);
+        const int i = p & g.mask, k = p >> g.L;
+        const int shx = g.J - meta_jx(mw), shy = g.J - meta_jy(mw);
+        const int sx = 1 << shx, sy = 1 << shy;
+        const T* row = F + ((size_t)k << g.L);
+        const T q0 = row[i];
+        const T xp1 = row[(i + sx) & g.mask], xm1 = row[(i - sx) & g.mask];
+        const T xp2 = row[(i + 2 * sx) & g.mask], xm2 = row[(i - 2 * sx) & g.mask];
+        const T yp1 = F[((size_t)((k + sy) & g.mask) << g.L) + i], ym1 = F[((size_t)((k - sy) & g.mask) << g.L) + i];
+        const T yp2 = F[((size_t)((k + 2 * sy) & g.mask) << g.L) + i];
+        const T ym2 = F[((size_t)((k - 2 * sy) & g.mask) << g.L) + i];
+        // 1/(12 h_j) = c1J 2^-sh and 1/(12 h_j^2) = c2J 4^-sh (exact power-of-two scalings)
+        const T c1x = ldexp(c1J, -shx), c1y = ldexp(c1J, -shy);
+        const T c2x = ldexp(c2J, -2 * shx), c2y = ldexp(c2J, -2 * shy);
+        const T Dx = (T(8) * (xp1 - xm1) - (xp2 - xm2)) * c1x;
+        const T Dy = (T(8) * (yp1 - ym1) - (yp2 - ym2)) * c1y;
+        const T Dxx = (-(xp2 + xm2) + T(16) * (xp1 + xm1) - T(30) * q0) * c2x;
+        const T Dyy = (-(yp2 + ym2) + T(16) * (yp1 + ym1) - T(30) * q0) * c2y;
+        T v = -Ua[a] * Dx - Va[a] * Dy + nu * (Dxx + Dyy) - r * q0;
+        if (ga) v += ga[a];
+        w[a] = v;
+    }
+}
+
+// Lattice sums of R, R^2, U^2 + V^2 and |grad R|^2 (deterministic two-stage
+// reduction: per-block partials, then the last block sums them in order).
+__global__ void __launch_bounds__(kThreads) k_diag(const double* __restrict__ R, const double* __restrict__ psi,
+                                                   double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                   double* __restrict__ out, Geom g, double c1) {
+    __shared__ double s_red[kThreads / 32][4];
+    __shared__ bool s_last;
+    const long long N = (long long)g.NJ * g.NJ;
+    double acc[4] = {0, 0, 0, 0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const double r = R[p];
+        const double U = dy1(psi, i, k, g, c1), V = -dx1(psi, i, k, g, c1);
+        const double gx = dx1(R, i, k, g, c1), gy = dy1(R, i, k, g, c1);
+        acc[0] += r;
+        acc[1] += r * r;
+        acc[2] += U * U + V * V;
+        acc[3] += gx * gx + gy * gy;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0;
+        for (int w = 0; w < kThreads / 32; ++w) v += s_red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x < 4) {
+            double v = 0;
+            for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partials[(size_t)b * 4 + threadIdx.x]);
+            out[threadIdx.x] = v;
+        }
+        if (threadIdx.x == 0) *counter = 0;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va, const Geom& g,
+                            cudaStream_t s) {
+    if (n > 0) k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h)));
+}
+
+template <typename T>
+void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1, T* t2, T* t3,
+                const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.NJ * g.NJ;
+    const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
+    const T csh2 = T((cs * g.h) * (cs * g.h));
+    k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, t0, t1, g, c1, c2);
+    k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(t0, t1, t2, t3, g, c1, csh2);
+    k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1);
+    if (n > 0) k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2);
+}
+
+template <typename T>
+void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.NJ * g.NJ;
+    const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
+    T* Uw = U ? U : tmp;
+    k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1);
+    if (nut)
+        k_lattice_nut<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h)));
+}
+
+template <typename T>
+void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va, const T* ga, double nu,
+                   double r, T* w, const Geom& g, const int* kstop, int jstep, cudaStream_t s) {
+    if (n > 0)
+        k_matvec<T><<<blocks_for(n), kThreads, 0, s>>>(F, meta, n, Ua, Va, ga, T(nu), T(r), w, g,
+                                                       T(1.0 / (12.0 * g.h)), T(1.0 / (12.0 * g.h * g.h)), kstop,
+                                                       jstep);
+}
+
+void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
+                 const Geom& g, cudaStream_t s) {
+    k_diag<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
+                                                                    1.0 / (12.0 * g.h));
+}
+
+#define WRC_INST(T)                                                                                          \
+    template void launch_velocity_active<T>(const T*, const uint32_t*, long long, T*, T*, const Geom&,      \
+                                            cudaStream_t);                                                  \
+    template void launch_sgs<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, T*, T*,           \
+                                const Geom&, cudaStream_t);                                                 \
+    template void launch_lattice_uv_nut<T>(const T*, T*, T*, T*, double, T*, const Geom&, cudaStream_t);     \
+    template void launch_matvec<T>(const T*, const uint32_t*, long long, const T*, const T*, const T*,      \
+                                   double, double, T*, const Geom&, const int*, int, cudaStream_t);
+WRC_INST(double)
+WRC_INST(float)
+#undef WRC_INST
+
+}  // namespace wrc

@@ -1,0 +1,437 @@
+// Lattice kernels: initial condition, DD reconstruction and details (Sec. 2.4,
+// Eq. 6), thresholding with the adjacent zone, closure under prediction,
+// stencil levels and ghost points (Sec. 2.5), and the stable multi-bucket
+// compaction that turns the masks into index lists.
+#include "kernels.h"
+
+namespace wrc {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+template <typename T>
+__global__ void k_init_vortices(T* __restrict__ L, const double* __restrict__ prm, int n, Geom g) {
+    const long long N = (long long)g.NJ * g.NJ;
+    const double twopi = 2.0 * kPi;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const double x = -kPi + g.h * i, y = -kPi + g.h * k;
+        double om = 0.0;
+        for (int v = 0; v < n; ++v) {
+            double dx = x - prm[v], dy = y - prm[n + v];
+            dx -= twopi * floor((dx + kPi) / twopi);   // minimum image in [-pi, pi)
+            dy -= twopi * floor((dy + kPi) / twopi);
+            const double s2 = prm[3 * n + v] * prm[3 * n + v];
+            om += prm[2 * n + v] / (kPi * s2) * exp(-(dx * dx + dy * dy) / s2);
+        }
+        L[p] = (T)om;
+    }
+}
+
+template <typename T>
+__global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict__ vals, long long n,
+                          T* __restrict__ L) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        L[meta_pos(meta[a])] = vals[a];
+}
+
+// Coarse-to-fine inverse transform for one level: every non-active level-j
+// point gets its DD prediction (its detail is zero, Eq. 6).
+template <typename T>
+__global__ void k_recon_level(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
+    const long long cnt = level_count(j, g);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, k;
+        level_point(t, j, g, i, k);
+        const long long p = ((long long)k << g.L) + i;
+        if (!act[p]) L[p] = predict<T>(L, i, k, j, g);
+    }
+}
+
+// Details d = u - Pred(u) at the active points (meta == nullptr: every lattice
+// point), significance |d| >= eps (level 0 always significant), and the
+// adjacent zone of every significant point of level j >= 1: the points of
+// level j and j+1 within 2^(J-j) fine cells in x and y.  All writes to the
+// masks store the value 1, so concurrent writers agree.
+template <typename T>
+__global__ void k_details_adj(const uint32_t* __restrict__ meta, long long n, const T* __restrict__ L,
+                              double eps, T* __restrict__ det, uint8_t* __restrict__ sig,
+                              uint8_t* __restrict__ nxt, Geom g) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const long long p = meta ? (long long)meta_pos(meta[a]) : a;
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const int lev = level_of(i, k, g.J);
+        T d = T(0);
+        bool s = true;
+        if (lev > 0) {
+            d = rsub(L[p], predict<T>(L, i, k, lev, g));
+            s = fabs((double)d) >= eps;
+        }
+        if (det) det[a] = d;
+        if (!s) continue;
+        sig[p] = 1;
+        nxt[p] = 1;
+        if (lev == 0) continue;
+        const int r = 1 << (g.J - lev);
+        const int step = lev < g.J ? (r >> 1) : r;
+        for (int dk = -r; dk <= r; dk += step) {
+            const int qk = (k + dk) & g.mask;
+            for (int di = -r; di <= r; di += step) {
+                const int qi = (i + di) & g.mask;
+                const int lq = level_of(qi, qk, g.J);
+                if (lq == lev || lq == lev + 1) nxt[((long long)qk << g.L) + qi] = 1;
+            }
+        }
+    }
+}
+
+// Visit the DD4 predictor points of level-j point (i, k).
+template <typename F>
+__device__ __forceinline__ void for_predictor_points(int i, int k, int j, const Geom& g, F&& f) {
+    const int sh = g.J - j;
+    const int s = 1 << sh;
+    const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
+    const int off[4] = {-3 * s, -s, s, 3 * s};
+    if (oi && !ok) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f((i + off[q]) & g.mask, k);
+    } else if (!oi && ok) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f(i, (k + off[q]) & g.mask);
+    } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f((i + off[q]) & g.mask, (k + off[b]) & g.mask);
+    }
+}
+
+// Closure under prediction for one level (finest first): every marked level-j
+// point marks its predictor points, except where `excl` is set.
+__global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __restrict__ excl, int j, Geom g) {
+    const long long cnt = level_count(j, g);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, k;
+        level_point(t, j, g, i, k);
+        if (!mask[((long long)k << g.L) + i]) continue;
+        for_predictor_points(i, k, j, g, [&](int qi, int qk) {
+            const long long q = ((long long)qk << g.L) + qi;
+            if (!excl || !excl[q]) mask[q] = 1;
+        });
+    }
+}
+
+// Stencil levels and ghost marks.  For an active point P of level l the
+// stencil level along x is the largest j in [l, J] with an active point at
+// P +- h_j e_x (l if none); the stencil reads P +- h_{j*}, P +- 2 h_{j*}, and
+// the non-active ones among them are ghosts.  Same along y.
+__global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __restrict__ gho,
+                                uint8_t* __restrict__ JJ, Geom g) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        if (!act[p]) continue;
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const int lev = level_of(i, k, g.J);
+        const uint8_t* row = act + ((long long)k << g.L);
+        int jx = lev, jy = lev;
+        for (int j = g.J; j > lev; --j) {
+            const int s = 1 << (g.J - j);
+            if (row[(i + s) & g.mask] || row[(i - s) & g.mask]) { jx = j; break; }
+        }
+        for (int j = g.J; j > lev; --j) {
+            const int s = 1 << (g.J - j);
+            if (act[((long long)((k + s) & g.mask) << g.L) + i] || act[((long long)((k - s) & g.mask) << g.L) + i]) {
+                jy = j;
+                break;
+            }
+        }
+        JJ[p] = (uint8_t)(jx | (jy << 4));
+        const int sx = 1 << (g.J - jx), sy = 1 << (g.J - jy);
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+            if (o == 0) continue;
+            const long long qx = ((long long)k << g.L) + ((i + o * sx) & g.mask);
+            if (!act[qx]) gho[qx] = 1;
+            const long long qy = ((long long)((k + o * sy) & g.mask) << g.L) + i;
+            if (!act[qy]) gho[qy] = 1;
+        }
+    }
+}
+
+__global__ void k_validate_grid(const uint8_t* __restrict__ act, int* __restrict__ flag, Geom g) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const int lev = level_of(i, k, g.J);
+        if (lev == 0) {
+            if (!act[p]) atomicOr(flag, 1);
+            continue;
+        }
+        if (!act[p]) continue;
+        bool ok = true;
+        for_predictor_points(i, k, lev, g, [&](int qi, int qk) {
+            if (!act[((long long)qk << g.L) + qi]) ok = false;
+        });
+        if (!ok) atomicOr(flag, 2);
+    }
+}
+
+// ---- stable multi-bucket compaction -----------------------------------------
+// key(p) = 0 for an active point, j for a ghost of level j, -1 otherwise; the
+// output list holds bucket 0, then bucket 1, ..., each in lattice order.
+
+__device__ __forceinline__ int compact_key(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho,
+                                           long long p, const Geom& g) {
+    if (act[p]) return 0;
+    if (gho[p]) return level_of((int)(p & g.mask), (int)(p >> g.L), g.J);
+    return -1;
+}
+
+__global__ void k_compact_count(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho, Geom g,
+                                int nkeys, int* __restrict__ blk_counts) {
+    __shared__ int sc[kMaxKeys];
+    if (threadIdx.x < kMaxKeys) sc[threadIdx.x] = 0;
+    __syncthreads();
+    const long long N = (long long)g.NJ * g.NJ;
+    const long long base = (long long)blockIdx.x * kTile;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kTileRounds; ++r) {
+        const long long p = base + (long long)r * kThreads + threadIdx.x;
+        const int key = p < N ? compact_key(act, gho, p, g) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && __popc(peers & ((1u << lane) - 1u)) == 0) atomicAdd(&sc[key], __popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < nkeys) blk_counts[(long long)blockIdx.x * nkeys + threadIdx.x] = sc[threadIdx.x];
+}
+
+// Exclusive scan of v over a block of 1024 threads; *total receives the sum.
+__device__ int block_excl_scan_1024(int v, int& total) {
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const int excl = x - v + (wid > 0 ? ws[wid - 1] : 0);
+    total = ws[31];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ blk_counts, int nblk, int nkeys,
+                                                       int* __restrict__ blk_off, int* __restrict__ counts) {
+    __shared__ int s_tot[kMaxKeys];
+    const int chunk = (nblk + 1023) / 1024;
+    const int b0 = threadIdx.x * chunk;
+    const int b1 = min(b0 + chunk, nblk);
+    for (int kk = 0; kk < nkeys; ++kk) {
+        int sum = 0;
+        for (int b = b0; b < b1; ++b) sum += blk_counts[(long long)b * nkeys + kk];
+        int total;
+        const int excl = block_excl_scan_1024(sum, total);
+        int run = excl;
+        for (int b = b0; b < b1; ++b) {
+            blk_off[(long long)b * nkeys + kk] = run;
+            run += blk_counts[(long long)b * nkeys + kk];
+        }
+        if (threadIdx.x == 0) s_tot[kk] = total;
+    }
+    __syncthreads();
+    // bucket bases
+    for (int kk = 0; kk < nkeys; ++kk) {
+        int base = 0;
+        for (int q = 0; q < kk; ++q) base += s_tot[q];
+        for (int b = b0; b < b1; ++b) blk_off[(long long)b * nkeys + kk] += base;
+    }
+    if (threadIdx.x < nkeys) counts[threadIdx.x] = s_tot[threadIdx.x];
+}
+
+__global__ void k_compact_scatter(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho, Geom g,
+                                  int nkeys, const int* __restrict__ blk_off, int* __restrict__ list) {
+    __shared__ int s_base[kMaxKeys];
+    __shared__ int s_wc[kThreads / 32][kMaxKeys];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < nkeys) s_base[threadIdx.x] = blk_off[(long long)blockIdx.x * nkeys + threadIdx.x];
+    const long long N = (long long)g.NJ * g.NJ;
+    const long long base = (long long)blockIdx.x * kTile;
+    for (int r = 0; r < kTileRounds; ++r) {
+        for (int t = threadIdx.x; t < (kThreads / 32) * kMaxKeys; t += kThreads) (&s_wc[0][0])[t] = 0;
+        __syncthreads();
+        const long long p = base + (long long)r * kThreads + threadIdx.x;
+        const int key = p < N ? compact_key(act, gho, p, g) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (key >= 0 && rank == 0) s_wc[wid][key] = __popc(peers);
+        __syncthreads();
+        if (key >= 0) {
+            int off = s_base[key];
+            for (int w = 0; w < wid; ++w) off += s_wc[w][key];
+            list[off + rank] = (int)p;
+        }
+        __syncthreads();
+        if (threadIdx.x < nkeys) {
+            int tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += s_wc[w][threadIdx.x];
+            s_base[threadIdx.x] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_finalize(const int* __restrict__ list, long long n, const uint8_t* __restrict__ JJ,
+                           const T* __restrict__ L, uint32_t* __restrict__ meta, T* __restrict__ omega) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = list[a];
+        const int jj = JJ[p];
+        meta[a] = pack_meta(p, jj & 15, jj >> 4);
+        omega[a] = L[p];
+    }
+}
+
+// Ghost values of one level from coarser active/ghost values (coarse to fine).
+template <typename T>
+__global__ void k_ghost_fill(T* __restrict__ F, const int* __restrict__ glist, long long n, int j, Geom g,
+                             const int* __restrict__ kstop, int jstep) {
+    if (kstop && jstep >= *kstop) return;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = glist[a];
+        F[p] = predict<T>(F, p & g.mask, p >> g.L, j, g);
+    }
+}
+
+__global__ void k_level_counts(const uint32_t* __restrict__ meta, long long n, unsigned long long* counts, Geom g) {
+    __shared__ unsigned int sc[16];
+    if (threadIdx.x < 16) sc[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        atomicAdd(&sc[level_of(p & g.mask, p >> g.L, g.J)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x <= g.J && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)sc[threadIdx.x]);
+}
+
+__global__ void k_meta_to_mask(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ mask) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        mask[meta_pos(meta[a])] = 1;
+}
+
+__global__ void k_list_to_mask(const int* __restrict__ list, long long n, uint8_t* __restrict__ mask) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        mask[list[a]] = 1;
+}
+
+__global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, int* idx, uint8_t* jx, uint8_t* jy) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = meta[a];
+        if (idx) idx[a] = meta_pos(m);
+        if (jx) jx[a] = (uint8_t)meta_jx(m);
+        if (jy) jy[a] = (uint8_t)meta_jy(m);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s) {
+    k_init_vortices<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(L, params, n, g);
+}
+template <typename T>
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s) {
+    if (n > 0) k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L);
+}
+template <typename T>
+void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
+    k_recon_level<T><<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(L, act, j, g);
+}
+template <typename T>
+void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
+                        uint8_t* nxt, const Geom& g, cudaStream_t s) {
+    if (n > 0) k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g);
+}
+void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s) {
+    k_closure_level<<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(mask, excl, j, g);
+}
+void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s) {
+    k_stencil_ghost<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, gho, JJ, g);
+}
+void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s) {
+    k_validate_grid<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, flag, g);
+}
+void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int nkeys, int* blk_counts,
+                    int* blk_off, int* counts, int* list, cudaStream_t s) {
+    const long long N = (long long)g.NJ * g.NJ;
+    const int nblk = (int)((N + kTile - 1) / kTile);
+    k_compact_count<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_counts);
+    k_compact_scan<<<1, 1024, 0, s>>>(blk_counts, nblk, nkeys, blk_off, counts);
+    k_compact_scatter<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_off, list);
+}
+template <typename T>
+void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
+                     cudaStream_t s) {
+    if (n > 0) k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega);
+}
+template <typename T>
+void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop, int jstep,
+                       cudaStream_t s) {
+    if (n > 0) k_ghost_fill<T><<<blocks_for(n), kThreads, 0, s>>>(F, glist, n, j, g, kstop, jstep);
+}
+void launch_level_counts(const uint32_t* meta, long long n, unsigned long long* counts, const Geom& g,
+                         cudaStream_t s) {
+    if (n > 0) k_level_counts<<<blocks_for(n), kThreads, 0, s>>>(meta, n, counts, g);
+}
+void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaStream_t s) {
+    if (n > 0) k_meta_to_mask<<<blocks_for(n), kThreads, 0, s>>>(meta, n, mask);
+}
+void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s) {
+    if (n > 0) k_list_to_mask<<<blocks_for(n), kThreads, 0, s>>>(list, n, mask);
+}
+void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy, cudaStream_t s) {
+    if (n > 0) k_meta_unpack<<<blocks_for(n), kThreads, 0, s>>>(meta, n, idx, jx, jy);
+}
+
+#define WRC_INST(T)                                                                                       \
+    template void launch_init_vortices<T>(T*, const double*, int, const Geom&, cudaStream_t);             \
+    template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t);              \
+    template void launch_recon_level<T>(T*, const uint8_t*, int, const Geom&, cudaStream_t);              \
+    template void launch_details_adj<T>(const uint32_t*, long long, const T*, double, T*, uint8_t*,       \
+                                        uint8_t*, const Geom&, cudaStream_t);                             \
+    template void launch_finalize<T>(const int*, long long, const uint8_t*, const T*, uint32_t*, T*,      \
+                                     cudaStream_t);                                                       \
+    template void launch_ghost_fill<T>(T*, const int*, long long, int, const Geom&, const int*, int,      \
+                                       cudaStream_t);
+WRC_INST(double)
+WRC_INST(float)
+#undef WRC_INST
+
+}  // namespace wrc

@@ -1,0 +1,96 @@
+// Host-side launchers of the library's CUDA kernels (internal interface).
+#pragma once
+
+#include "common.cuh"
+
+namespace wrc {
+
+// ---- grid.cu: lattice, transform, thresholding, index sets -----------------
+template <typename T>
+void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s);
+template <typename T>
+void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det,
+                        uint8_t* sig, uint8_t* nxt, const Geom& g, cudaStream_t s);
+void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s);
+void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s);
+void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s);
+void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int nkeys, int* blk_counts,
+                    int* blk_off, int* counts, int* list, cudaStream_t s);
+template <typename T>
+void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
+                     cudaStream_t s);
+template <typename T>
+void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop,
+                       int jstep, cudaStream_t s);
+void launch_level_counts(const uint32_t* meta, long long n, unsigned long long* counts, const Geom& g,
+                         cudaStream_t s);
+void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaStream_t s);
+void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s);
+void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy,
+                        cudaStream_t s);
+
+// ---- fft.cu: streamfunction -------------------------------------------------
+struct PoissonPlan {
+    int n = 0, logn = 0;
+    double2* tw = nullptr;     // exp(-2 pi i t/n), t < n/2
+    double* sigma = nullptr;   // symbol of the 4th-order second-derivative stencil
+};
+int poisson_plan_init(PoissonPlan& p, const Geom& g, cudaStream_t s);
+void poisson_plan_free(PoissonPlan& p);
+// psi = L_h^{-1}(-(R - mean R)), mean(psi) = 0; C1, C2 are NJ*NJ complex work arrays.
+void launch_poisson(const PoissonPlan& p, const double* R, double* psi, double2* C1, double2* C2,
+                    const Geom& g, cudaStream_t s);
+
+// ---- flow.cu: velocity, Smagorinsky forcing, operator, diagnostics ----------
+template <typename T>
+void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va,
+                            const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1,
+                T* t2, T* t3, const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g,
+                           cudaStream_t s);
+template <typename T>
+void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va,
+                   const T* ga, double nu, double r, T* w, const Geom& g, const int* kstop, int jstep,
+                   cudaStream_t s);
+// sums over the lattice of R, R^2, U^2 + V^2, |grad R|^2 -> out[0..3]
+void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
+                 const Geom& g, cudaStream_t s);
+
+// ---- krylov.cu: Arnoldi, phi_1, update --------------------------------------
+struct KrylovDev {
+    void* basis;       // (m+1) x ld, element type of the run's bulk precision
+    long long ld;
+    void* w;           // ld
+    double* H;         // (m+1) x m row-major
+    double* o1;        // 33 each: reduction outputs
+    double* o2;
+    double* o3;
+    double* beta;      // [1]
+    double* y;         // [m]
+    int* kstop;        // [1] Krylov dimension in use
+    int* flags;        // [1] bit 0: non-finite value met
+    double* partials;  // kMaxBlocks * 33
+    unsigned* counter; // [1]
+};
+template <typename T>
+void launch_gs_pass(const KrylovDev& K, long long n, int nv, int ndots, const double* coef, double* out,
+                    const int* kstop, int jstep, cudaStream_t s);
+void launch_krylov_start(const KrylovDev& K, int m, cudaStream_t s);
+void launch_arnoldi_col(const KrylovDev& K, int j, int m, double tol, cudaStream_t s);
+template <typename T>
+void launch_normalize_scatter(const KrylovDev& K, const uint32_t* meta, long long n, int j, int m, T* Fq,
+                              cudaStream_t s);
+int phi1_init();
+void launch_phi1(const KrylovDev& K, int m, double dt, cudaStream_t s);
+template <typename T>
+void launch_update(const KrylovDev& K, const uint32_t* meta, long long n, double dt, T* omega, T* L,
+                   cudaStream_t s);
+
+}  // namespace wrc
