@@ -1,0 +1,325 @@
+"""Benchmark: active-point updates/s of the Krylov-projected DD
+wavelet-collocation step on GB300.
+
+One step = one pass of the whole hot path (reconstruction, streamfunction,
+velocity and Smagorinsky forcing, Krylov projection with the phi_1 update,
+grid adaptation) over the active grid of the 1024^2 Fujiwhara pair workload
+(coarsest 32^2, J = 5, eps = 1e-4, m = 30, dynamic Smagorinsky C_s = 0.17,
+Re = 5000, dt = 1e-2, FP64).  One active-point update = one active point
+advanced one full step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances an independent replica (seed
+offset by rank; no collective on the data path) and rank 0 prints the
+whole-job line.  ``--impl reference`` times the FP64 CPU oracle on the host
+cores instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1604_08159_gb300 import workloads as W  # noqa: E402
+
+METRIC = "active-point updates/s"
+UNIT = "updates/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_for(rank: int):
+    return W.fujiwhara_1024(seed=2 + rank)
+
+
+def oracle_config(p):
+    from oracle import wrc_oracle as O
+    return O.Config(n0=p.n0, J=p.J, eps=p.eps, re=p.re, dt=p.dt, m=p.m, sgs=p.sgs_name(), cs=p.cs,
+                    s_apriori=p.s_apriori, rayleigh_r=p.rayleigh_r)
+
+
+def time_oracle(wl, nsteps: int, warmup: int = 0):
+    """Time the oracle (as it stands) for nsteps steps of the workload from
+    its initial state; returns (updates/s, wall s, cores used, per-step N_a)."""
+    from oracle import wrc_oracle as O
+    cfg = oracle_config(wl.params)
+    v = wl.vortices
+    st = O.initial_state(cfg, v.xc, v.yc, v.gamma, v.s)
+    for _ in range(warmup):
+        st, _ = O.step(cfg, st)
+    upd = 0
+    t0 = time.perf_counter()
+    c0 = os.times()
+    for _ in range(nsteps):
+        upd += int(st.active.sum())
+        st, _ = O.step(cfg, st)
+    wall = time.perf_counter() - t0
+    c1 = os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    cores = max(1, int(round(cpu / wall))) if wall > 0 else 1
+    return upd / wall, wall, cores, upd
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except (ValueError, KeyError, TypeError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload_for(0)
+    warm = min(args.warmup, 1)
+    val, wall, cores, upd = time_oracle(wl, args.steps, warmup=warm)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "NJ": wl.params.NJ, "n0": wl.params.n0,
+                                        "J": wl.params.J, "eps": wl.params.eps, "m": wl.params.m,
+                                        "sgs": wl.params.sgs_name()},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps of {wl.name} after {warm} warm-up step(s)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1604_08159_gb300 import binding as B
+    from paper_1604_08159_gb300 import build as BLD
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        backend = "nccl" if dist.is_nccl_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if rank == 0:
+        BLD.build()
+    if ws > 1:
+        dist.barrier()
+    B.load()
+
+    wl = workload_for(rank)
+    p = wl.params
+    stream = torch.cuda.Stream()
+    run = B.Run(p, stream=stream.cuda_stream)
+    run.init_vortices(wl.vortices)
+    run.step(args.warmup)
+    run.sync()
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    upd = 0
+    l0 = run.stats()["launches"]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    with sampler:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for q in range(args.steps):
+                flush.zero_()                      # L2 flush between timed steps (outside the events)
+                starts[q].record(stream)
+                upd += run.stats()["n_active"]
+                run.step(1)
+                ends[q].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = run.stats()["launches"] - l0      # library kernels only (the flush is torch's)
+    run.sync()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    # dominant kernel: the Gram-Schmidt passes, timed with events on the run's stream
+    run.profile(True)
+    prof_steps = min(args.steps, 5)
+    run.step(prof_steps)
+    rec = run.profile_record()
+    run.profile(False)
+    peak, peak_src = hbm_peak()
+    achieved = rec["bytes"] / (rec["ms"] * 1e-3) / 1e9 if rec["ms"] > 0 else 0.0
+
+    # end to end through the C-ABI with host buffers (pinned), a fresh run
+    e2e = None
+    if not args.no_e2e:
+        v = wl.vortices
+        prm = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+               for a in (v.xc, v.yc, v.gamma, v.s)]
+        run2 = B.Run(p, stream=stream.cuda_stream)
+        idx_h = torch.empty(p.NJ * p.NJ, dtype=torch.int32).pin_memory()
+        om_h = torch.empty(p.NJ * p.NJ, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        B.wrc_init_vortices(run2.h, *[a.numpy() for a in prm])
+        e2e_upd, d2h = 0, 0
+        for _ in range(args.steps):
+            na = run2.stats()["n_active"]
+            e2e_upd += na
+            run2.step(1)
+            na2 = run2.stats()["n_active"]
+            B.wrc_query_active(run2.h, idx_h, om_h, p.NJ * p.NJ)
+            d2h += 12 * na2
+        torch.cuda.synchronize()
+        e2e_wall = time.perf_counter() - t1
+        run2.close()
+        e2e = {"value": e2e_upd / e2e_wall, "unit": UNIT,
+               "h2d_bytes_per_step": int(32 * v.n / args.steps),
+               "d2h_bytes_per_step": int(d2h / args.steps)}
+
+    # max over ranks
+    t_dev = dev_ms
+    if ws > 1:
+        tt = torch.tensor([dev_ms, float(upd)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_dev = float(mx[0])
+        upd = int(tt[1])
+    value = upd / (t_dev * 1e-3)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cval, cwall, cores, cupd = time_oracle(wl, args.cpu_steps)
+            cpu = {"value": cval, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{args.cpu_steps} oracle steps of {wl.name} from t=0 ({cupd} updates, {cwall:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "NJ": p.NJ, "n0": p.n0, "J": p.J, "eps": p.eps, "m": p.m,
+                       "sgs": p.sgs_name(), "cs": p.cs, "re": p.re, "dt": p.dt,
+                       "mean_active_points": upd / max(1, args.steps * ws),
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "wall_s": wall},
+            "roofline": {"bound": "hbm", "kernel": "k_gs_pass (Arnoldi Gram-Schmidt pass)",
+                         "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "launches": rec["passes"], "avg_launch_us": 1e3 * rec["ms"] / max(1, rec["passes"]),
+                         "bytes_per_launch": rec["bytes"] / max(1, rec["passes"])},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": sampler.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    run.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

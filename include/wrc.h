@@ -177,6 +177,21 @@ wrc_status wrc_query_krylov(wrc_run* run, double* beta, int32_t* k, double* h_la
  * fields), time t, step count, active count, ghost count. */
 wrc_status wrc_diagnostics(wrc_run* run, double out[8]);
 
+/* Counters: out[0] kernel launches made by the library in this process,
+ * out[1] steps taken by this run, out[2] host synchronisations made by its
+ * steps and grid rebuilds, out[3] current active count. */
+wrc_status wrc_query_stats(wrc_run* run, int64_t out[4]);
+
+/* Event timing of the Arnoldi Gram-Schmidt passes (the step's main stream
+ * of basis-vector traffic): when enabled, every pass is bracketed by CUDA
+ * events on the run's stream; enabling or disabling clears the record. */
+wrc_status wrc_profile(wrc_run* run, int32_t enable);
+
+/* Profile record since wrc_profile(run, 1): out[0] passes, out[1] their
+ * total device time in ms, out[2] their algorithmic bytes (basis vectors and
+ * w read, w written back when updated), out[3] = 0.  Synchronises. */
+wrc_status wrc_query_profile(wrc_run* run, double out[4]);
+
 /* Message of the last failing call on `run` ("" if none); for a NULL run,
  * the last failure of wrc_create on this thread. */
 const char* wrc_last_error(const wrc_run* run);

@@ -49,6 +49,9 @@ SIGNATURES = {
     "wrc_apply_operator": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
     "wrc_query_krylov": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "wrc_diagnostics": (c_int32, [c_void_p, c_void_p]),
+    "wrc_query_stats": (c_int32, [c_void_p, c_void_p]),
+    "wrc_profile": (c_int32, [c_void_p, c_int32]),
+    "wrc_query_profile": (c_int32, [c_void_p, c_void_p]),
     "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_destroy": (None, [c_void_p]),
 }
@@ -212,6 +215,22 @@ def wrc_diagnostics(run):
     return dict(zip(keys, out.tolist()))
 
 
+def wrc_query_stats(run):
+    out = np.zeros(4, dtype=np.int64)
+    _check("wrc_query_stats", load().wrc_query_stats(run, out.ctypes.data), run)
+    return {"launches": int(out[0]), "steps": int(out[1]), "host_syncs": int(out[2]), "n_active": int(out[3])}
+
+
+def wrc_profile(run, enable: bool):
+    _check("wrc_profile", load().wrc_profile(run, 1 if enable else 0), run)
+
+
+def wrc_query_profile(run):
+    out = np.zeros(4)
+    _check("wrc_query_profile", load().wrc_query_profile(run, out.ctypes.data), run)
+    return {"passes": int(out[0]), "ms": float(out[1]), "bytes": float(out[2])}
+
+
 def wrc_last_error(run) -> str:
     m = load().wrc_last_error(run)
     return m.decode() if m else ""
@@ -317,3 +336,12 @@ class Run:
 
     def diagnostics(self):
         return wrc_diagnostics(self.h)
+
+    def stats(self):
+        return wrc_query_stats(self.h)
+
+    def profile(self, enable=True):
+        wrc_profile(self.h, enable)
+
+    def profile_record(self):
+        return wrc_query_profile(self.h)

@@ -1,8 +1,10 @@
 // C ABI (include/wrc.h): run state on the device and the orchestration of one
 // time step -- reconstruction, streamfunction, velocity and Smagorinsky
 // forcing, Krylov projection with the phi_1 update, grid adaptation.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <vector>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -11,6 +13,13 @@
 #include "kernels.h"
 
 using namespace wrc;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void wrc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long wrc::launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -79,6 +88,12 @@ struct wrc_run {
 
     // Krylov small arrays
     KrylovDev K{};
+
+    // event timing of the Gram-Schmidt passes (wrc_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, double>> ev_used;   // (index of start event, algorithmic bytes)
+    long long host_syncs = 0;
 
     // state
     long long n_active = 0, n_ghost = 0, det_count = 0;
@@ -163,6 +178,7 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     CKL("compaction");
     CK(cudaMemcpyAsync(R->counts_host, R->counts_dev, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    R->host_syncs += 1;
     const long long na = R->counts_host[0];
     long long off = na, ng = 0;
     for (int j = 1; j <= g.J; ++j) {
@@ -231,6 +247,30 @@ wrc_status freeze(wrc_run* R) {
     return WRC_OK;
 }
 
+// One Gram-Schmidt pass; with profiling on, bracketed by events on the run's
+// stream and booked with its algorithmic bytes: the nv basis vectors and w
+// read, w written back when coef is given.
+wrc_status gs_pass(wrc_run* R, long long n, int nv, int ndots, const double* coef, double* out, const int* kstop,
+                   int jstep) {
+    int e0 = -1;
+    if (R->profiling) {
+        while (R->ev_pool.size() < R->ev_used.size() * 2 + 2) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            R->ev_pool.push_back(e);
+        }
+        e0 = (int)R->ev_used.size() * 2;
+        CK(cudaEventRecord(R->ev_pool[e0], R->st));
+    }
+    launch_gs_pass<double>(R->K, n, nv, ndots, coef, out, kstop, jstep, R->st);
+    if (R->profiling) {
+        CK(cudaEventRecord(R->ev_pool[e0 + 1], R->st));
+        const double bytes = (double)n * sizeof(double) * (nv + 1 + (coef ? 1 : 0));
+        R->ev_used.push_back({e0, bytes});
+    }
+    return WRC_OK;
+}
+
 void ghost_fill(wrc_run* R, double* F, const int* kstop, int jstep) {
     for (int j = 1; j <= R->g.J; ++j)
         launch_ghost_fill<double>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
@@ -248,16 +288,16 @@ wrc_status krylov(wrc_run* R) {
     // b = A omega + g
     launch_matvec<double>(R->L, meta, n, R->Ua.as<double>(), R->Va.as<double>(), ga, nu_eff(R), R->cfg.rayleigh_r,
                           R->w.as<double>(), R->g, nullptr, 0, s);
-    launch_gs_pass<double>(K, n, 0, 0, nullptr, K.o1, nullptr, 0, s);
+    TRY(gs_pass(R, n, 0, 0, nullptr, K.o1, nullptr, 0));
     launch_krylov_start(K, m, s);
     launch_normalize_scatter<double>(K, meta, n, 0, m, R->Lq, s);
     for (int j = 0; j < m; ++j) {
         ghost_fill(R, R->Lq, K.kstop, j);
         launch_matvec<double>(R->Lq, meta, n, R->Ua.as<double>(), R->Va.as<double>(), nullptr, nu_eff(R),
                               R->cfg.rayleigh_r, R->w.as<double>(), R->g, K.kstop, j, s);
-        launch_gs_pass<double>(K, n, j + 1, j + 1, nullptr, K.o1, K.kstop, j, s);
-        launch_gs_pass<double>(K, n, j + 1, j + 1, K.o1, K.o2, K.kstop, j, s);
-        launch_gs_pass<double>(K, n, j + 1, 0, K.o2, K.o3, K.kstop, j, s);
+        TRY(gs_pass(R, n, j + 1, j + 1, nullptr, K.o1, K.kstop, j));
+        TRY(gs_pass(R, n, j + 1, j + 1, K.o1, K.o2, K.kstop, j));
+        TRY(gs_pass(R, n, j + 1, 0, K.o2, K.o3, K.kstop, j));
         launch_arnoldi_col(K, j, m, kBreakdownTol, s);
         if (j + 1 < m) launch_normalize_scatter<double>(K, meta, n, j + 1, m, R->Lq, s);
     }
@@ -310,6 +350,7 @@ void free_run(wrc_run* R) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
+    for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
     poisson_plan_free(R->plan);
     delete R;
 }
@@ -656,6 +697,40 @@ wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
     out[5] = (double)R->nstep;
     out[6] = (double)R->n_active;
     out[7] = (double)R->n_ghost;
+    return WRC_OK;
+}
+
+wrc_status wrc_query_stats(wrc_run* R, int64_t out[4]) {
+    if (!R || !out) return WRC_ERR_ARG;
+    out[0] = launches_total();
+    out[1] = R->nstep;
+    out[2] = R->host_syncs;
+    out[3] = R->n_active;
+    return WRC_OK;
+}
+
+wrc_status wrc_profile(wrc_run* R, int32_t enable) {
+    if (!R) return WRC_ERR_ARG;
+    CK(cudaStreamSynchronize(R->st));
+    R->profiling = enable != 0;
+    R->ev_used.clear();
+    return WRC_OK;
+}
+
+wrc_status wrc_query_profile(wrc_run* R, double out[4]) {
+    if (!R || !out) return WRC_ERR_ARG;
+    CK(cudaStreamSynchronize(R->st));
+    double ms = 0.0, bytes = 0.0;
+    for (const auto& u : R->ev_used) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, R->ev_pool[u.first], R->ev_pool[u.first + 1]));
+        ms += t;
+        bytes += u.second;
+    }
+    out[0] = (double)R->ev_used.size();
+    out[1] = ms;
+    out[2] = bytes;
+    out[3] = 0.0;
     return WRC_OK;
 }
 

@@ -117,6 +117,10 @@ __host__ __device__ __forceinline__ int meta_pos(uint32_t m) { return (int)(m & 
 __host__ __device__ __forceinline__ int meta_jx(uint32_t m) { return (int)((m >> 24) & 15u); }
 __host__ __device__ __forceinline__ int meta_jy(uint32_t m) { return (int)(m >> 28); }
 
+// Process-wide count of kernel launches made by the library (host side).
+void note_launch();
+long long launches_total();
+
 inline int blocks_for(long long n, int threads = kThreads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

@@ -132,7 +132,7 @@ int poisson_plan_init(PoissonPlan& p, const Geom& g, cudaStream_t s) {
         cudaFuncSetAttribute(k_fft_y_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_fft_x_inv_real, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -2;
-    k_fft_init<<<(p.n + 255) / 256, 256, 0, s>>>(p.tw, p.sigma, p.n, 1.0 / (3.0 * g.h * g.h));
+    { k_fft_init<<<(p.n + 255) / 256, 256, 0, s>>>(p.tw, p.sigma, p.n, 1.0 / (3.0 * g.h * g.h)); note_launch(); }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -149,11 +149,11 @@ void launch_poisson(const PoissonPlan& p, const double* R, double* psi, double2*
     const size_t smem = sizeof(double2) * n;
     const int thr = n >= 512 ? 256 : (n / 2 >= 32 ? n / 2 : 32);
     const dim3 tgrid((n + 31) / 32, (n + 31) / 32), tblk(32, 8);
-    k_fft_x_fwd_real<<<n, thr, smem, s>>>(R, C1, n, p.logn, p.tw);
-    k_transpose<<<tgrid, tblk, 0, s>>>(C1, C2, n);
-    k_fft_y_solve<<<n, thr, smem, s>>>(C2, n, p.logn, p.tw, p.sigma, 1.0 / ((double)n * (double)n));
-    k_transpose<<<tgrid, tblk, 0, s>>>(C2, C1, n);
-    k_fft_x_inv_real<<<n, thr, smem, s>>>(C1, psi, n, p.logn, p.tw);
+    { k_fft_x_fwd_real<<<n, thr, smem, s>>>(R, C1, n, p.logn, p.tw); note_launch(); }
+    { k_transpose<<<tgrid, tblk, 0, s>>>(C1, C2, n); note_launch(); }
+    { k_fft_y_solve<<<n, thr, smem, s>>>(C2, n, p.logn, p.tw, p.sigma, 1.0 / ((double)n * (double)n)); note_launch(); }
+    { k_transpose<<<tgrid, tblk, 0, s>>>(C2, C1, n); note_launch(); }
+    { k_fft_x_inv_real<<<n, thr, smem, s>>>(C1, psi, n, p.logn, p.tw); note_launch(); }
     (void)g;
 }
 

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const double* __restrict__ R,
 template <typename T>
 void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va, const Geom& g,
                             cudaStream_t s) {
-    if (n > 0) k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h)));
+    if (n > 0) { k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h))); note_launch(); }
 }
 
 template <typename T>
@@ -222,10 +222,10 @@ void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* g
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
-    k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, t0, t1, g, c1, c2);
-    k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(t0, t1, t2, t3, g, c1, csh2);
-    k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1);
-    if (n > 0) k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2);
+    { k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, t0, t1, g, c1, c2); note_launch(); }
+    { k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(t0, t1, t2, t3, g, c1, csh2); note_launch(); }
+    { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1); note_launch(); }
+    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2); note_launch(); }
 }
 
 template <typename T>
@@ -233,24 +233,24 @@ void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, 
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     T* Uw = U ? U : tmp;
-    k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1);
+    { k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1); note_launch(); }
     if (nut)
-        k_lattice_nut<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h)));
+        { k_lattice_nut<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h))); note_launch(); }
 }
 
 template <typename T>
 void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va, const T* ga, double nu,
                    double r, T* w, const Geom& g, const int* kstop, int jstep, cudaStream_t s) {
     if (n > 0)
-        k_matvec<T><<<blocks_for(n), kThreads, 0, s>>>(F, meta, n, Ua, Va, ga, T(nu), T(r), w, g,
+        { k_matvec<T><<<blocks_for(n), kThreads, 0, s>>>(F, meta, n, Ua, Va, ga, T(nu), T(r), w, g,
                                                        T(1.0 / (12.0 * g.h)), T(1.0 / (12.0 * g.h * g.h)), kstop,
-                                                       jstep);
+                                                       jstep); note_launch(); }
 }
 
 void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
                  const Geom& g, cudaStream_t s) {
-    k_diag<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
-                                                                    1.0 / (12.0 * g.h));
+    { k_diag<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
+                                                                    1.0 / (12.0 * g.h)); note_launch(); }
 }
 
 #define WRC_INST(T)                                                                                          \

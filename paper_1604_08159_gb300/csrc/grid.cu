@@ -364,60 +364,60 @@ __global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, in
 
 template <typename T>
 void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s) {
-    k_init_vortices<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(L, params, n, g);
+    { k_init_vortices<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(L, params, n, g); note_launch(); }
 }
 template <typename T>
 void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s) {
-    if (n > 0) k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L);
+    if (n > 0) { k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L); note_launch(); }
 }
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
-    k_recon_level<T><<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(L, act, j, g);
+    { k_recon_level<T><<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
                         uint8_t* nxt, const Geom& g, cudaStream_t s) {
-    if (n > 0) k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g);
+    if (n > 0) { k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g); note_launch(); }
 }
 void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s) {
-    k_closure_level<<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(mask, excl, j, g);
+    { k_closure_level<<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(mask, excl, j, g); note_launch(); }
 }
 void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s) {
-    k_stencil_ghost<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, gho, JJ, g);
+    { k_stencil_ghost<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, gho, JJ, g); note_launch(); }
 }
 void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s) {
-    k_validate_grid<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, flag, g);
+    { k_validate_grid<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, flag, g); note_launch(); }
 }
 void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int nkeys, int* blk_counts,
                     int* blk_off, int* counts, int* list, cudaStream_t s) {
     const long long N = (long long)g.NJ * g.NJ;
     const int nblk = (int)((N + kTile - 1) / kTile);
-    k_compact_count<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_counts);
-    k_compact_scan<<<1, 1024, 0, s>>>(blk_counts, nblk, nkeys, blk_off, counts);
-    k_compact_scatter<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_off, list);
+    { k_compact_count<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_counts); note_launch(); }
+    { k_compact_scan<<<1, 1024, 0, s>>>(blk_counts, nblk, nkeys, blk_off, counts); note_launch(); }
+    { k_compact_scatter<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_off, list); note_launch(); }
 }
 template <typename T>
 void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
                      cudaStream_t s) {
-    if (n > 0) k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega);
+    if (n > 0) { k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega); note_launch(); }
 }
 template <typename T>
 void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop, int jstep,
                        cudaStream_t s) {
-    if (n > 0) k_ghost_fill<T><<<blocks_for(n), kThreads, 0, s>>>(F, glist, n, j, g, kstop, jstep);
+    if (n > 0) { k_ghost_fill<T><<<blocks_for(n), kThreads, 0, s>>>(F, glist, n, j, g, kstop, jstep); note_launch(); }
 }
 void launch_level_counts(const uint32_t* meta, long long n, unsigned long long* counts, const Geom& g,
                          cudaStream_t s) {
-    if (n > 0) k_level_counts<<<blocks_for(n), kThreads, 0, s>>>(meta, n, counts, g);
+    if (n > 0) { k_level_counts<<<blocks_for(n), kThreads, 0, s>>>(meta, n, counts, g); note_launch(); }
 }
 void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaStream_t s) {
-    if (n > 0) k_meta_to_mask<<<blocks_for(n), kThreads, 0, s>>>(meta, n, mask);
+    if (n > 0) { k_meta_to_mask<<<blocks_for(n), kThreads, 0, s>>>(meta, n, mask); note_launch(); }
 }
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s) {
-    if (n > 0) k_list_to_mask<<<blocks_for(n), kThreads, 0, s>>>(list, n, mask);
+    if (n > 0) { k_list_to_mask<<<blocks_for(n), kThreads, 0, s>>>(list, n, mask); note_launch(); }
 }
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy, cudaStream_t s) {
-    if (n > 0) k_meta_unpack<<<blocks_for(n), kThreads, 0, s>>>(meta, n, idx, jx, jy);
+    if (n > 0) { k_meta_unpack<<<blocks_for(n), kThreads, 0, s>>>(meta, n, idx, jx, jy); note_launch(); }
 }
 
 #define WRC_INST(T)                                                                                       \

@@ -310,23 +310,23 @@ void launch_gs_pass(const KrylovDev& K, long long n, int nv, int ndots, const do
     T* w = (T*)K.w;
     const int need = nv > ndots ? nv : ndots;
     if (need <= 8)
-        k_gs_pass<T, 8><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep);
+        { k_gs_pass<T, 8><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep); note_launch(); }
     else if (need <= 16)
-        k_gs_pass<T, 16><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep);
+        { k_gs_pass<T, 16><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep); note_launch(); }
     else
-        k_gs_pass<T, 32><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep);
+        { k_gs_pass<T, 32><<<nb, kThreads, 0, s>>>(basis, K.ld, n, nv, ndots, w, coef, out, K.partials, K.counter, kstop, jstep); note_launch(); }
 }
 
-void launch_krylov_start(const KrylovDev& K, int m, cudaStream_t s) { k_krylov_start<<<1, 1, 0, s>>>(K, m); }
+void launch_krylov_start(const KrylovDev& K, int m, cudaStream_t s) { { k_krylov_start<<<1, 1, 0, s>>>(K, m); note_launch(); } }
 
 void launch_arnoldi_col(const KrylovDev& K, int j, int m, double tol, cudaStream_t s) {
-    k_arnoldi_col<<<1, 1, 0, s>>>(K, j, m, tol);
+    { k_arnoldi_col<<<1, 1, 0, s>>>(K, j, m, tol); note_launch(); }
 }
 
 template <typename T>
 void launch_normalize_scatter(const KrylovDev& K, const uint32_t* meta, long long n, int j, int m, T* Fq,
                               cudaStream_t s) {
-    if (n > 0) k_normalize_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(K, meta, n, j, m, Fq);
+    if (n > 0) { k_normalize_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(K, meta, n, j, m, Fq); note_launch(); }
 }
 
 int phi1_init() {
@@ -335,12 +335,12 @@ int phi1_init() {
 }
 
 void launch_phi1(const KrylovDev& K, int m, double dt, cudaStream_t s) {
-    k_phi1<<<1, 256, 7 * kES * sizeof(double), s>>>(K, m, dt);
+    { k_phi1<<<1, 256, 7 * kES * sizeof(double), s>>>(K, m, dt); note_launch(); }
 }
 
 template <typename T>
 void launch_update(const KrylovDev& K, const uint32_t* meta, long long n, double dt, T* omega, T* L, cudaStream_t s) {
-    if (n > 0) k_update<T><<<blocks_for(n), kThreads, 0, s>>>(K, meta, n, dt, omega, L);
+    if (n > 0) { k_update<T><<<blocks_for(n), kThreads, 0, s>>>(K, meta, n, dt, omega, L); note_launch(); }
 }
 
 #define WRC_INST(T)                                                                                          \
