@@ -86,8 +86,19 @@ struct wrc_run {
     int cur = 0;
     long long cap = 0;
 
-    // Krylov small arrays
-    KrylovDev K{};
+    // Krylov small arrays and cooperative-kernel scratch
+    struct {
+        double* H = nullptr;      // (m+1) x m
+        double* beta = nullptr;   // [1]
+        double* y = nullptr;      // [32]
+        int* kstop = nullptr;     // ints: kstop, flags, err, pad, bar[2], counter, pad
+        int* flags = nullptr;
+        int* err = nullptr;
+        unsigned* bar = nullptr;
+        unsigned* counter = nullptr;
+        double* part = nullptr;   // partial sums of the cooperative kernel / diagnostics
+    } K;
+    int max_blocks = 1;
 
     // event timing of the Gram-Schmidt passes (wrc_profile)
     bool profiling = false;
@@ -159,9 +170,6 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     R->basis.release(s);
     CK(R->basis.grow(b8 * (size_t)(m + 1), 0, s));
     R->cap = c;
-    R->K.basis = R->basis.p;
-    R->K.w = R->w.p;
-    R->K.ld = c;
     return WRC_OK;
 }
 
@@ -177,8 +185,13 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     launch_compact(R->nxt, R->gho, g, nkeys, R->blk_counts, R->blk_off, R->counts_dev, R->list, s);
     CKL("compaction");
     CK(cudaMemcpyAsync(R->counts_host, R->counts_dev, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(R->counts_host + kMaxKeys, R->K.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     R->host_syncs += 1;
+    if (R->counts_host[kMaxKeys] != 0) {
+        CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
+        return fail(R, WRC_ERR_TIMEOUT, "a grid barrier wait of the Krylov kernel ran out");
+    }
     const long long na = R->counts_host[0];
     long long off = na, ng = 0;
     for (int j = 1; j <= g.J; ++j) {
@@ -247,11 +260,64 @@ wrc_status freeze(wrc_run* R) {
     return WRC_OK;
 }
 
-// One Gram-Schmidt pass; with profiling on, bracketed by events on the run's
-// stream and booked with its algorithmic bytes: the nv basis vectors and w
-// read, w written back when coef is given.
-wrc_status gs_pass(wrc_run* R, long long n, int nv, int ndots, const double* coef, double* out, const int* kstop,
-                   int jstep) {
+void ghost_fill(wrc_run* R, double* F, const int* kstop, int jstep) {
+    for (int j = 1; j <= R->g.J; ++j)
+        launch_ghost_fill<double>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
+}
+
+// Algorithmic bytes of one Krylov step over n active points with Krylov
+// dimension k (FP64 words): k + 1 operator applications reading q, U, V and
+// writing w; at Arnoldi step j a fused single Gram-Schmidt pass reading j + 1
+// basis vectors and w twice and writing w; the combination reading k vectors
+// and omega and writing omega.
+double krylov_algorithmic_bytes(long long n, int k) {
+    double words = 4.0 * (k + 1) + (double)k + 2.0;
+    for (int j = 0; j < k; ++j) words += 2.0 * (j + 1) + 3.0;
+    return 8.0 * words * (double)n;
+}
+
+// Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
+// one cooperative launch.
+wrc_status krylov(wrc_run* R) {
+    const cudaStream_t s = R->st;
+    const long long n = R->n_active;
+    const int m = R->cfg.krylov_m;
+    KrylovStepArgs A{};
+    A.g = R->g;
+    A.meta = R->meta[R->cur].as<uint32_t>();
+    A.n = (int)n;
+    A.glist = R->list;
+    for (int j = 0; j < 16; ++j) {
+        A.gbeg[j] = j <= R->g.J ? (int)R->goff[j] : 0;
+        A.gcnt[j] = (j >= 1 && j <= R->g.J) ? (int)R->gcount[j] : 0;
+    }
+    A.Ua = R->Ua.as<double>();
+    A.Va = R->Va.as<double>();
+    A.ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<double>() : nullptr;
+    A.nu = nu_eff(R);
+    A.r = R->cfg.rayleigh_r;
+    A.c1J = 1.0 / (12.0 * R->g.h);
+    A.c2J = 1.0 / (12.0 * R->g.h * R->g.h);
+    A.L = R->L;
+    A.Lq = R->Lq;
+    A.omega = R->omega[R->cur].as<double>();
+    A.basis = R->basis.as<double>();
+    A.ld = R->cap;
+    A.w = R->w.as<double>();
+    A.H = R->K.H;
+    A.y = R->K.y;
+    A.beta = R->K.beta;
+    A.kstop = R->K.kstop;
+    A.flags = R->K.flags;
+    A.part = R->K.part;
+    A.bar = R->K.bar;
+    A.err = R->K.err;
+    A.m = m;
+    A.dt = R->cfg.dt;
+    A.tol = kBreakdownTol;
+    A.limit_ns = 2000000000ull;
+    const int blocks = krylov_step_blocks(n, R->max_blocks);
+    CK(cudaMemsetAsync(R->K.H, 0, sizeof(double) * (m + 1) * m, s));
     int e0 = -1;
     if (R->profiling) {
         while (R->ev_pool.size() < R->ev_used.size() * 2 + 2) {
@@ -260,50 +326,13 @@ wrc_status gs_pass(wrc_run* R, long long n, int nv, int ndots, const double* coe
             R->ev_pool.push_back(e);
         }
         e0 = (int)R->ev_used.size() * 2;
-        CK(cudaEventRecord(R->ev_pool[e0], R->st));
+        CK(cudaEventRecord(R->ev_pool[e0], s));
     }
-    launch_gs_pass<double>(R->K, n, nv, ndots, coef, out, kstop, jstep, R->st);
+    CK(launch_krylov_step(A, blocks, s));
     if (R->profiling) {
-        CK(cudaEventRecord(R->ev_pool[e0 + 1], R->st));
-        const double bytes = (double)n * sizeof(double) * (nv + 1 + (coef ? 1 : 0));
-        R->ev_used.push_back({e0, bytes});
+        CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
+        R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m)});
     }
-    return WRC_OK;
-}
-
-void ghost_fill(wrc_run* R, double* F, const int* kstop, int jstep) {
-    for (int j = 1; j <= R->g.J; ++j)
-        launch_ghost_fill<double>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
-}
-
-// Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)).
-wrc_status krylov(wrc_run* R) {
-    const cudaStream_t s = R->st;
-    const long long n = R->n_active;
-    const int m = R->cfg.krylov_m;
-    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
-    const double* ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<double>() : nullptr;
-    KrylovDev& K = R->K;
-    CK(cudaMemsetAsync(K.H, 0, sizeof(double) * (m + 1) * m, s));
-    // b = A omega + g
-    launch_matvec<double>(R->L, meta, n, R->Ua.as<double>(), R->Va.as<double>(), ga, nu_eff(R), R->cfg.rayleigh_r,
-                          R->w.as<double>(), R->g, nullptr, 0, s);
-    TRY(gs_pass(R, n, 0, 0, nullptr, K.o1, nullptr, 0));
-    launch_krylov_start(K, m, s);
-    launch_normalize_scatter<double>(K, meta, n, 0, m, R->Lq, s);
-    for (int j = 0; j < m; ++j) {
-        ghost_fill(R, R->Lq, K.kstop, j);
-        launch_matvec<double>(R->Lq, meta, n, R->Ua.as<double>(), R->Va.as<double>(), nullptr, nu_eff(R),
-                              R->cfg.rayleigh_r, R->w.as<double>(), R->g, K.kstop, j, s);
-        TRY(gs_pass(R, n, j + 1, j + 1, nullptr, K.o1, K.kstop, j));
-        TRY(gs_pass(R, n, j + 1, j + 1, K.o1, K.o2, K.kstop, j));
-        TRY(gs_pass(R, n, j + 1, 0, K.o2, K.o3, K.kstop, j));
-        launch_arnoldi_col(K, j, m, kBreakdownTol, s);
-        if (j + 1 < m) launch_normalize_scatter<double>(K, meta, n, j + 1, m, R->Lq, s);
-    }
-    launch_phi1(K, m, R->cfg.dt, s);
-    launch_update<double>(K, meta, n, R->cfg.dt, R->omega[R->cur].as<double>(), R->L, s);
-    CKL("krylov");
     return WRC_OK;
 }
 
@@ -346,7 +375,7 @@ void free_run(wrc_run* R) {
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list,
                     R->blk_counts, R->blk_off, R->counts_dev, R->flag_dev, R->lvl_dev, R->vort_dev, R->diag_dev,
-                    R->K.H, R->K.o1, R->K.partials, R->K.kstop};
+                    R->K.H, R->K.kstop, R->K.part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
@@ -418,25 +447,31 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     if (e == cudaSuccess) e = alloc((void**)&R->vort_dev, sizeof(double) * 4 * WRC_MAX_VORTICES);
     if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
     // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
-    if (e == cudaSuccess) e = alloc((void**)&R->K.H, sizeof(double) * (m + 1) * m);
-    if (e == cudaSuccess) e = alloc((void**)&R->K.o1, sizeof(double) * (3 * 33 + 1 + 32));
-    if (e == cudaSuccess) e = alloc((void**)&R->K.partials, sizeof(double) * kMaxBlocks * 33);
-    if (e == cudaSuccess) e = alloc((void**)&R->K.kstop, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&R->counts_host, sizeof(int) * kMaxKeys);
+    if (krylov_step_init(&R->max_blocks) != 0) {
+        g_create_error = "cooperative Krylov kernel set-up failed";
+        free_run(R);
+        return WRC_ERR_CUDA;
+    }
+    if (e == cudaSuccess) e = alloc((void**)&R->K.H, sizeof(double) * ((m + 1) * m + 1 + 32));
+    if (e == cudaSuccess) e = alloc((void**)&R->K.kstop, sizeof(int) * 8);
+    const size_t npart = krylov_partials_doubles(R->max_blocks) > (size_t)kMaxBlocks * 4
+                             ? krylov_partials_doubles(R->max_blocks) : (size_t)kMaxBlocks * 4;
+    if (e == cudaSuccess) e = alloc((void**)&R->K.part, sizeof(double) * npart);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&R->counts_host, sizeof(int) * (kMaxKeys + 4));
     if (e != cudaSuccess) {
         g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
         free_run(R);
         return e == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA;
     }
-    R->K.o2 = R->K.o1 + 33;
-    R->K.o3 = R->K.o2 + 33;
-    R->K.beta = R->K.o3 + 33;
+    R->K.beta = R->K.H + (m + 1) * m;
     R->K.y = R->K.beta + 1;
     R->K.flags = R->K.kstop + 1;
-    R->K.counter = (unsigned*)(R->K.kstop + 2);
-    cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 4, R->st);
+    R->K.err = R->K.kstop + 2;
+    R->K.bar = (unsigned*)(R->K.kstop + 4);
+    R->K.counter = (unsigned*)(R->K.kstop + 6);
+    cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 8, R->st);
     cudaMemsetAsync(R->flag_dev, 0, sizeof(int) * 4, R->st);
-    if (poisson_plan_init(R->plan, R->g, R->st) != 0 || phi1_init() != 0) {
+    if (poisson_plan_init(R->plan, R->g, R->st) != 0) {
         g_create_error = "FFT/expm kernel set-up failed";
         free_run(R);
         return WRC_ERR_CUDA;
@@ -683,7 +718,7 @@ wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
     if (!out) return fail(R, WRC_ERR_ARG, "NULL output");
     TRY(reconstruct(R));
     launch_poisson(R->plan, R->L, R->psi, R->C1, R->C2, R->g, R->st);
-    launch_diag(R->L, R->psi, R->K.partials, R->K.counter, R->diag_dev, R->g, R->st);
+    launch_diag(R->L, R->psi, R->K.part, R->K.counter, R->diag_dev, R->g, R->st);
     CKL("diagnostics");
     double s[4];
     CK(cudaMemcpyAsync(s, R->diag_dev, sizeof(s), cudaMemcpyDeviceToHost, R->st));

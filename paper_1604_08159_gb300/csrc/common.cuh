@@ -46,6 +46,14 @@ __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 
+// Loads of data that other blocks of the same kernel may have written go
+// through L2 only (L1 is not coherent across SMs).
+template <typename T, bool CG>
+__device__ __forceinline__ T ldv(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // DD order-4 predictor from the neighbours at -1, +1 (a, b) and -3, +3 (c, d):
 // the cubic through them evaluated at 0, weights (-1, 9, 9, -1)/16.
 template <typename T>
@@ -56,7 +64,7 @@ __device__ __forceinline__ T dd4(T a, T b, T c, T d) {
 // DD prediction at lattice point (i, k) of level j >= 1 from the coarser
 // points of field F: along x for points odd in x only, along y for points odd
 // in y only, tensor product (x prediction of four rows, then y) otherwise.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ T predict(const T* __restrict__ F, int i, int k, int j, const Geom& g) {
     const int sh = g.J - j;
     const int s = 1 << sh;
@@ -65,18 +73,21 @@ __device__ __forceinline__ T predict(const T* __restrict__ F, int i, int k, int 
     const bool ok = (k >> sh) & 1;
     if (oi && !ok) {
         const T* row = F + ((size_t)k << g.L);
-        return dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+        return dd4<T>(ldv<T, CG>(row + ((i - s) & m)), ldv<T, CG>(row + ((i + s) & m)),
+                      ldv<T, CG>(row + ((i - 3 * s) & m)), ldv<T, CG>(row + ((i + 3 * s) & m)));
     }
     if (!oi && ok) {
-        return dd4<T>(F[((size_t)((k - s) & m) << g.L) + i], F[((size_t)((k + s) & m) << g.L) + i],
-                      F[((size_t)((k - 3 * s) & m) << g.L) + i], F[((size_t)((k + 3 * s) & m) << g.L) + i]);
+        return dd4<T>(ldv<T, CG>(F + ((size_t)((k - s) & m) << g.L) + i), ldv<T, CG>(F + ((size_t)((k + s) & m) << g.L) + i),
+                      ldv<T, CG>(F + ((size_t)((k - 3 * s) & m) << g.L) + i),
+                      ldv<T, CG>(F + ((size_t)((k + 3 * s) & m) << g.L) + i));
     }
     T r[4];
     const int ks[4] = {k - s, k + s, k - 3 * s, k + 3 * s};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const T* row = F + ((size_t)(ks[q] & m) << g.L);
-        r[q] = dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+        r[q] = dd4<T>(ldv<T, CG>(row + ((i - s) & m)), ldv<T, CG>(row + ((i + s) & m)),
+                      ldv<T, CG>(row + ((i - 3 * s) & m)), ldv<T, CG>(row + ((i + 3 * s) & m)));
     }
     return dd4<T>(r[0], r[1], r[2], r[3]);
 }

@@ -2,6 +2,7 @@
 // frozen linear operator A_n of the Krylov step (Sec. 2.5 collocation
 // derivatives at each point's stencil level), and lattice diagnostics.
 #include "kernels.h"
+#include "operator.cuh"
 
 namespace wrc {
 
@@ -134,26 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const T* __restrict__ F, co
     if (kstop && jstep >= *kstop) return;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
-        const uint32_t mw = meta[a];
-        const int p = meta_pos(mw);
-        const int i = p & g.mask, k = p >> g.L;
-        const int shx = g.J - meta_jx(mw), shy = g.J - meta_jy(mw);
-        const int sx = 1 << shx, sy = 1 << shy;
-        const T* row = F + ((size_t)k << g.L);
-        const T q0 = row[i];
-        const T xp1 = row[(i + sx) & g.mask], xm1 = row[(i - sx) & g.mask];
-        const T xp2 = row[(i + 2 * sx) & g.mask], xm2 = row[(i - 2 * sx) & g.mask];
-        const T yp1 = F[((size_t)((k + sy) & g.mask) << g.L) + i], ym1 = F[((size_t)((k - sy) & g.mask) << g.L) + i];
-        const T yp2 = F[((size_t)((k + 2 * sy) & g.mask) << g.L) + i];
-        const T ym2 = F[((size_t)((k - 2 * sy) & g.mask) << g.L) + i];
-        // 1/(12 h_j) = c1J 2^-sh and 1/(12 h_j^2) = c2J 4^-sh (exact power-of-two scalings)
-        const T c1x = ldexp(c1J, -shx), c1y = ldexp(c1J, -shy);
-        const T c2x = ldexp(c2J, -2 * shx), c2y = ldexp(c2J, -2 * shy);
-        const T Dx = (T(8) * (xp1 - xm1) - (xp2 - xm2)) * c1x;
-        const T Dy = (T(8) * (yp1 - ym1) - (yp2 - ym2)) * c1y;
-        const T Dxx = (-(xp2 + xm2) + T(16) * (xp1 + xm1) - T(30) * q0) * c2x;
-        const T Dyy = (-(yp2 + ym2) + T(16) * (yp1 + ym1) - T(30) * q0) * c2y;
-        T v = -Ua[a] * Dx - Va[a] * Dy + nu * (Dxx + Dyy) - r * q0;
+        T v = apply_point<T, false>(F, meta[a], Ua[a], Va[a], nu, r, g, c1J, c2J);
         if (ga) v += ga[a];
         w[a] = v;
     }

@@ -63,34 +63,38 @@ void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, c
 void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
                  const Geom& g, cudaStream_t s);
 
-// ---- krylov.cu: Arnoldi, phi_1, update --------------------------------------
-struct KrylovDev {
-    void* basis;       // (m+1) x ld, element type of the run's bulk precision
+// ---- krylov.cu: the Krylov-projected step as one cooperative kernel ---------
+struct KrylovStepArgs {
+    Geom g;
+    const uint32_t* meta;   // active points (packed lattice index + stencil levels)
+    int n;                  // active count
+    const int* glist;       // ghost lattice indices, level by level
+    int gbeg[16], gcnt[16]; // ghosts of level l: glist[gbeg[l] .. gbeg[l] + gcnt[l])
+    const double* Ua;
+    const double* Va;
+    const double* ga;       // SGS forcing at the active points or nullptr
+    double nu, r, c1J, c2J; // nu_eff, Rayleigh r, 1/(12 h_J), 1/(12 h_J^2)
+    double* L;              // R(omega) on the lattice (in), omega^{n+1} at the active points (out)
+    double* Lq;             // lattice array of the current Krylov vector and its ghost values
+    double* omega;          // compact omega, updated in place
+    double* basis;          // (m+1) x ld
     long long ld;
-    void* w;           // ld
-    double* H;         // (m+1) x m row-major
-    double* o1;        // 33 each: reduction outputs
-    double* o2;
-    double* o3;
-    double* beta;      // [1]
-    double* y;         // [m]
-    int* kstop;        // [1] Krylov dimension in use
-    int* flags;        // [1] bit 0: non-finite value met
-    double* partials;  // kMaxBlocks * 33
-    unsigned* counter; // [1]
+    double* w;
+    double* H;              // (m+1) x m row-major
+    double* y;              // m
+    double* beta;           // [1]
+    int* kstop;             // [1] Krylov dimension used
+    int* flags;             // [1] bit 0: non-finite value met
+    double* part;           // 3 x blocks x 33 partial sums
+    unsigned* bar;          // grid barrier: {count, generation}
+    int* err;               // bit 1: a barrier wait ran out
+    int m;
+    double dt, tol;
+    unsigned long long limit_ns;
 };
-template <typename T>
-void launch_gs_pass(const KrylovDev& K, long long n, int nv, int ndots, const double* coef, double* out,
-                    const int* kstop, int jstep, cudaStream_t s);
-void launch_krylov_start(const KrylovDev& K, int m, cudaStream_t s);
-void launch_arnoldi_col(const KrylovDev& K, int j, int m, double tol, cudaStream_t s);
-template <typename T>
-void launch_normalize_scatter(const KrylovDev& K, const uint32_t* meta, long long n, int j, int m, T* Fq,
-                              cudaStream_t s);
-int phi1_init();
-void launch_phi1(const KrylovDev& K, int m, double dt, cudaStream_t s);
-template <typename T>
-void launch_update(const KrylovDev& K, const uint32_t* meta, long long n, double dt, T* omega, T* L,
-                   cudaStream_t s);
+int krylov_step_init(int* max_blocks);
+int krylov_step_blocks(long long n, int max_blocks);
+cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s);
+size_t krylov_partials_doubles(int max_blocks);
 
 }  // namespace wrc
