@@ -182,14 +182,18 @@ wrc_status wrc_diagnostics(wrc_run* run, double out[8]);
  * steps and grid rebuilds, out[3] current active count. */
 wrc_status wrc_query_stats(wrc_run* run, int64_t out[4]);
 
-/* Event timing of the Arnoldi Gram-Schmidt passes (the step's main stream
- * of basis-vector traffic): when enabled, every pass is bracketed by CUDA
- * events on the run's stream; enabling or disabling clears the record. */
+/* Event timing of the Krylov part of each step (the cooperative Arnoldi
+ * kernel, phi_1 and the update): when enabled, each step's Krylov launches
+ * are bracketed by CUDA events on the run's stream; enabling or disabling
+ * clears the record. */
 wrc_status wrc_profile(wrc_run* run, int32_t enable);
 
-/* Profile record since wrc_profile(run, 1): out[0] passes, out[1] their
- * total device time in ms, out[2] their algorithmic bytes (basis vectors and
- * w read, w written back when updated), out[3] = 0.  Synchronises. */
+/* Profile record since wrc_profile(run, 1): out[0] Krylov launches timed,
+ * out[1] their total device time in ms, out[2] their algorithmic bytes (per
+ * active point: 4 words per operator application, 2(j+1)+3 words at Arnoldi
+ * step j, k+2 words for the combination), out[3] their algorithmic FP64
+ * operations (30 per operator application, 8(j+1)+4 at step j, 3k more).
+ * Synchronises. */
 wrc_status wrc_query_profile(wrc_run* run, double out[4]);
 
 /* Message of the last failing call on `run` ("" if none); for a NULL run,

@@ -228,7 +228,7 @@ def wrc_profile(run, enable: bool):
 def wrc_query_profile(run):
     out = np.zeros(4)
     _check("wrc_query_profile", load().wrc_query_profile(run, out.ctypes.data), run)
-    return {"passes": int(out[0]), "ms": float(out[1]), "bytes": float(out[2])}
+    return {"launches": int(out[0]), "ms": float(out[1]), "bytes": float(out[2]), "flops": float(out[3])}
 
 
 def wrc_last_error(run) -> str:

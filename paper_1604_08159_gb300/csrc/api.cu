@@ -73,6 +73,7 @@ struct wrc_run {
     double2* C2 = nullptr;
     uint8_t *act = nullptr, *nxt = nullptr, *gho = nullptr, *sig = nullptr, *JJ = nullptr;
     int* list = nullptr;     // active points, then ghosts by level
+    int* lat2idx = nullptr;  // lattice -> combined active/ghost number
     int *blk_counts = nullptr, *blk_off = nullptr, *counts_dev = nullptr;
     int* counts_host = nullptr;   // pinned
     int* flag_dev = nullptr;
@@ -85,6 +86,9 @@ struct wrc_run {
     DevBuf meta[2], omega[2], Ua, Va, ga, det, w, basis, tmp;
     int cur = 0;
     long long cap = 0;
+    // ghost interpolation rows and the ghost values of the basis vectors
+    DevBuf row_len, row_idx, row_w, Gb;
+    long long cap_g = 0;
 
     // Krylov small arrays and cooperative-kernel scratch
     struct {
@@ -94,6 +98,7 @@ struct wrc_run {
         int* kstop = nullptr;     // ints: kstop, flags, err, pad, bar[2], counter, pad
         int* flags = nullptr;
         int* err = nullptr;
+        int* overflow = nullptr;
         unsigned* bar = nullptr;
         unsigned* counter = nullptr;
         double* part = nullptr;   // partial sums of the cooperative kernel / diagnostics
@@ -103,7 +108,8 @@ struct wrc_run {
     // event timing of the Gram-Schmidt passes (wrc_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, double>> ev_used;   // (index of start event, algorithmic bytes)
+    struct ProfRec { int ev; double bytes, flops; };
+    std::vector<ProfRec> ev_used;   // start-event index, algorithmic bytes and flops per launch
     long long host_syncs = 0;
 
     // state
@@ -173,6 +179,21 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     return WRC_OK;
 }
 
+wrc_status ensure_ghost_capacity(wrc_run* R, long long ng) {
+    if (ng <= R->cap_g) return WRC_OK;
+    long long c = ng + ng / 4 + 1024;
+    c = (c + 255) / 256 * 256;
+    const cudaStream_t s = R->st;
+    const int m = R->cfg.krylov_m;
+    CK(R->row_len.grow(sizeof(int) * c, 0, s));
+    CK(R->row_idx.grow(sizeof(int) * c * kGhostRowMax, 0, s));
+    CK(R->row_w.grow(sizeof(double) * c * kGhostRowMax, 0, s));
+    R->Gb.release(s);
+    CK(R->Gb.grow(sizeof(double) * c * (m + 1), 0, s));
+    R->cap_g = c;
+    return WRC_OK;
+}
+
 // The new grid is in `nxt` and its values are in L: stencil levels, ghosts,
 // compaction into the index list, then the compact arrays of the new grid.
 wrc_status rebuild_from_mask(wrc_run* R) {
@@ -190,6 +211,8 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     R->host_syncs += 1;
     if (R->counts_host[kMaxKeys] != 0) {
         CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
+        const int ev = R->counts_host[kMaxKeys];
+        if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded kGhostRowMax terms");
         return fail(R, WRC_ERR_TIMEOUT, "a grid barrier wait of the Krylov kernel ran out");
     }
     const long long na = R->counts_host[0];
@@ -201,8 +224,12 @@ wrc_status rebuild_from_mask(wrc_run* R) {
         ng += R->gcount[j];
     }
     TRY(ensure_capacity(R, na));
+    TRY(ensure_ghost_capacity(R, ng));
     const int nc = 1 - R->cur;
     launch_finalize<double>(R->list, na, R->JJ, R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<double>(), s);
+    CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
+    launch_ghost_rows(R->list, na, R->goff, R->gcount, g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
+                      R->row_w.as<double>(), kGhostRowMax, g, R->K.overflow, s);
     CKL("finalize");
     std::swap(R->act, R->nxt);
     R->cur = nc;
@@ -276,6 +303,16 @@ double krylov_algorithmic_bytes(long long n, int k) {
     return 8.0 * words * (double)n;
 }
 
+// Algorithmic FP64 operations of the same step per active point: 30 per
+// operator application (k + 1 of them), at Arnoldi step j two Gram-Schmidt
+// passes of dots and updates, 8 (j + 1), plus 4 for the norms, one division
+// per normalised entry, and 2 k for the combination.
+double krylov_algorithmic_flops(long long n, int k) {
+    double f = 30.0 * (k + 1) + 3.0 * k;
+    for (int j = 0; j < k; ++j) f += 8.0 * (j + 1) + 4.0;
+    return f * (double)n;
+}
+
 // Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
 // one cooperative launch.
 wrc_status krylov(wrc_run* R) {
@@ -286,11 +323,15 @@ wrc_status krylov(wrc_run* R) {
     A.g = R->g;
     A.meta = R->meta[R->cur].as<uint32_t>();
     A.n = (int)n;
-    A.glist = R->list;
-    for (int j = 0; j < 16; ++j) {
-        A.gbeg[j] = j <= R->g.J ? (int)R->goff[j] : 0;
-        A.gcnt[j] = (j >= 1 && j <= R->g.J) ? (int)R->gcount[j] : 0;
-    }
+    A.glist = R->list + n;
+    A.ng = (int)R->n_ghost;
+    A.row_len = R->row_len.as<int>();
+    A.row_idx = R->row_idx.as<int>();
+    A.row_w = R->row_w.as<double>();
+    A.rmax = kGhostRowMax;
+    A.row_overflow = R->K.overflow;
+    A.Gb = R->Gb.as<double>();
+    A.ldg = R->cap_g;
     A.Ua = R->Ua.as<double>();
     A.Va = R->Va.as<double>();
     A.ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<double>() : nullptr;
@@ -331,7 +372,7 @@ wrc_status krylov(wrc_run* R) {
     CK(launch_krylov_step(A, blocks, s));
     if (R->profiling) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
-        R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m)});
+        R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
     }
     return WRC_OK;
 }
@@ -370,10 +411,10 @@ void free_run(wrc_run* R) {
     cudaStream_t s = R->st;
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
-                    &R->basis, &R->tmp})
+                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb})
         b->release(s);
     cudaStreamSynchronize(s);
-    void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list,
+    void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list, R->lat2idx,
                     R->blk_counts, R->blk_off, R->counts_dev, R->flag_dev, R->lvl_dev, R->vort_dev, R->diag_dev,
                     R->K.H, R->K.kstop, R->K.part};
     for (void* p : ptrs)
@@ -439,6 +480,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     for (auto p : mp)
         if (e == cudaSuccess) e = alloc((void**)p, N);
     if (e == cudaSuccess) e = alloc((void**)&R->list, sizeof(int) * N);
+    if (e == cudaSuccess) e = alloc((void**)&R->lat2idx, sizeof(int) * N);
     if (e == cudaSuccess) e = alloc((void**)&R->blk_counts, sizeof(int) * nblk * kMaxKeys);
     if (e == cudaSuccess) e = alloc((void**)&R->blk_off, sizeof(int) * nblk * kMaxKeys);
     if (e == cudaSuccess) e = alloc((void**)&R->counts_dev, sizeof(int) * kMaxKeys);
@@ -467,6 +509,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     R->K.y = R->K.beta + 1;
     R->K.flags = R->K.kstop + 1;
     R->K.err = R->K.kstop + 2;
+    R->K.overflow = R->K.kstop + 3;
     R->K.bar = (unsigned*)(R->K.kstop + 4);
     R->K.counter = (unsigned*)(R->K.kstop + 6);
     cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 8, R->st);
@@ -755,17 +798,18 @@ wrc_status wrc_profile(wrc_run* R, int32_t enable) {
 wrc_status wrc_query_profile(wrc_run* R, double out[4]) {
     if (!R || !out) return WRC_ERR_ARG;
     CK(cudaStreamSynchronize(R->st));
-    double ms = 0.0, bytes = 0.0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
     for (const auto& u : R->ev_used) {
         float t = 0.f;
-        CK(cudaEventElapsedTime(&t, R->ev_pool[u.first], R->ev_pool[u.first + 1]));
+        CK(cudaEventElapsedTime(&t, R->ev_pool[u.ev], R->ev_pool[u.ev + 1]));
         ms += t;
-        bytes += u.second;
+        bytes += u.bytes;
+        flops += u.flops;
     }
     out[0] = (double)R->ev_used.size();
     out[1] = ms;
     out[2] = bytes;
-    out[3] = 0.0;
+    out[3] = flops;
     return WRC_OK;
 }
 

@@ -360,6 +360,81 @@ __global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, in
     }
 }
 
+// Index of every grid point in the combined numbering: active points
+// 0..n_a-1, then the ghosts n_a.. in list order.
+__global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __restrict__ lat2idx) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        lat2idx[list[t]] = (int)t;
+}
+
+// Interpolation rows of the ghosts of one level: the value of a ghost is the
+// DD prediction from its predictor points, which are active points or ghosts
+// of coarser levels (whose rows exist already); substituting gives the ghost
+// as a weighted sum of active values.  The weights are products of the DD4
+// weights (-1, 9, 9, -1)/16, exact binary fractions, and repeated points are
+// merged, so the rows are exact.  A row longer than rmax sets *overflow.
+__global__ void k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act,
+                                   long long n_tot, const int* __restrict__ lat2idx, int* __restrict__ row_len,
+                                   int* __restrict__ row_idx, double* __restrict__ row_w, int rmax, int j, Geom g,
+                                   int* __restrict__ overflow) {
+    constexpr int kCap = 64;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long gi = gbeg - n_act + t;          // ghost number
+        const int p = list[gbeg + t];
+        const int i = p & g.mask, k = p >> g.L;
+        int idx[kCap];
+        double wt[kCap];
+        int len = 0;
+        bool over = false;
+        auto add = [&](int id, double w) {
+            for (int e = 0; e < len; ++e)
+                if (idx[e] == id) { wt[e] += w; return; }
+            if (len < rmax && len < kCap) { idx[len] = id; wt[len] = w; ++len; }
+            else over = true;
+        };
+        const int sh = g.J - j;
+        const int s = 1 << sh;
+        const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
+        const int off[4] = {-3 * s, -s, s, 3 * s};
+        const double w4[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
+        for (int b = 0; b < 4; ++b) {
+            for (int a = 0; a < 4; ++a) {
+                int qi, qk;
+                double w;
+                if (oi && !ok) {
+                    if (b) break;
+                    qi = (i + off[a]) & g.mask; qk = k; w = w4[a];
+                } else if (!oi && ok) {
+                    if (b) break;
+                    qi = i; qk = (k + off[a]) & g.mask; w = w4[a];
+                } else {
+                    qi = (i + off[a]) & g.mask; qk = (k + off[b]) & g.mask; w = w4[a] * w4[b];
+                }
+                const int id = lat2idx[((long long)qk << g.L) + qi];
+                if (id < 0 || id >= n_tot) {          // not a grid point: record, do not read
+                    over = true;
+                    continue;
+                }
+                if (id < n_act) {
+                    add(id, w);
+                } else {
+                    const long long r = id - n_act;
+                    const int rl = row_len[r];
+                    for (int e = 0; e < rl; ++e) add(row_idx[r * rmax + e], w * row_w[r * rmax + e]);
+                }
+            }
+        }
+        row_len[gi] = len;
+        for (int e = 0; e < len; ++e) {
+            row_idx[gi * rmax + e] = idx[e];
+            row_w[gi * rmax + e] = wt[e];
+        }
+        if (over) atomicOr(overflow, 4);
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -415,6 +490,19 @@ void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaS
 }
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s) {
     if (n > 0) { k_list_to_mask<<<blocks_for(n), kThreads, 0, s>>>(list, n, mask); note_launch(); }
+}
+void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
+                       int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
+                       int* overflow, cudaStream_t s) {
+    long long tot = n_act;
+    for (int j = 1; j <= J; ++j) tot += gcnt[j];
+    if (tot > 0) { k_lat2idx<<<blocks_for(tot), kThreads, 0, s>>>(list, tot, lat2idx); note_launch(); }
+    for (int j = 1; j <= J; ++j)
+        if (gcnt[j] > 0) {
+            k_ghost_rows_level<<<blocks_for(gcnt[j], 128), 128, 0, s>>>(list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len,
+                                                                      row_idx, row_w, rmax, j, g, overflow);
+            note_launch();
+        }
 }
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy, cudaStream_t s) {
     if (n > 0) { k_meta_unpack<<<blocks_for(n), kThreads, 0, s>>>(meta, n, idx, jx, jy); note_launch(); }

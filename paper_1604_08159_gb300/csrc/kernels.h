@@ -32,6 +32,12 @@ void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaS
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s);
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy,
                         cudaStream_t s);
+// Interpolation rows of all ghosts (levels 1..J; ghosts of level j at
+// list[goff[j] ..]) over the active points, and the combined index map.
+constexpr int kGhostRowMax = 64;
+void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
+                       int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
+                       int* overflow, cudaStream_t s);
 
 // ---- fft.cu: streamfunction -------------------------------------------------
 struct PoissonPlan {
@@ -68,8 +74,15 @@ struct KrylovStepArgs {
     Geom g;
     const uint32_t* meta;   // active points (packed lattice index + stencil levels)
     int n;                  // active count
-    const int* glist;       // ghost lattice indices, level by level
-    int gbeg[16], gcnt[16]; // ghosts of level l: glist[gbeg[l] .. gbeg[l] + gcnt[l])
+    const int* glist;       // ghost lattice indices (all levels), ng of them
+    int ng;
+    const int* row_len;     // ghost interpolation rows over the active points
+    const int* row_idx;
+    const double* row_w;
+    int rmax;
+    const int* row_overflow; // non-zero: some row exceeded rmax (the kernel refuses to run)
+    double* Gb;             // ghost values of the basis vectors, (m+1) x ldg
+    long long ldg;
     const double* Ua;
     const double* Va;
     const double* ga;       // SGS forcing at the active points or nullptr
