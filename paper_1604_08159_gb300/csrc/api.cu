@@ -7,6 +7,7 @@
 #include <vector>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <utility>
 
 #include "../../include/wrc.h"
@@ -65,12 +66,18 @@ struct wrc_run {
     std::string err;
     long long N = 0;   // NJ * NJ
 
-    // lattice arrays
-    double* L = nullptr;     // omega on the grid / its reconstruction
-    double* Lq = nullptr;    // Krylov vector on the grid + ghost values
-    double* psi = nullptr;
-    double2* C1 = nullptr;   // FFT / Smagorinsky work arrays
-    double2* C2 = nullptr;
+    // bulk precision: double, or float for the mixed mode (FP64 stays in the
+    // Krylov inner products, the Hessenberg matrix and phi_1)
+    bool fp32 = false;
+    size_t es = sizeof(double);
+
+    // lattice arrays (bulk type)
+    void* L = nullptr;       // omega on the grid / its reconstruction
+    void* Lq = nullptr;      // Krylov vector on the grid + ghost values
+    void* psi = nullptr;
+    void* C1 = nullptr;      // FFT work arrays (complex) / Smagorinsky temporaries
+    void* C2 = nullptr;
+    DevBuf lat64;            // NJ*NJ doubles for conversions of lattice fields (mixed mode)
     uint8_t *act = nullptr, *nxt = nullptr, *gho = nullptr, *sig = nullptr, *JJ = nullptr;
     int* list = nullptr;     // active points, then ghosts by level
     int* lat2idx = nullptr;  // lattice -> combined active/ghost number
@@ -148,10 +155,20 @@ wrc_status fail(wrc_run* R, wrc_status s, const std::string& msg) {
         if (s_ != WRC_OK) return s_;                                                            \
     } while (0)
 
+// Run the internal function template fn for the run's bulk type.
+#define DISPATCH(R, fn, ...) ((R)->fp32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
+
 double nu_eff(const wrc_run* R) {
     double nu = 1.0 / R->cfg.re;
     if (R->cfg.sgs == WRC_SGS_APRIORI) nu += (R->cfg.cs * R->g.h) * (R->cfg.cs * R->g.h) * R->cfg.s_apriori;
     return nu;
+}
+
+// 2 NJ*NJ doubles of device scratch: lattice conversions, and in the mixed mode the
+// third and fourth FFT work arrays.
+double* lattice_scratch(wrc_run* R) {
+    if (R->lat64.grow(2 * sizeof(double) * R->N, 0, R->st) != cudaSuccess) return nullptr;
+    return R->lat64.as<double>();
 }
 
 wrc_status ensure_capacity(wrc_run* R, long long n) {
@@ -160,21 +177,21 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     c = (c + 255) / 256 * 256;
     const int m = R->cfg.krylov_m;
     const cudaStream_t s = R->st;
-    const size_t b8 = sizeof(double) * (size_t)c;
+    const size_t be = R->es * (size_t)c;
     // meta/omega of the current grid and the details keep their contents
     CK(R->meta[R->cur].grow(sizeof(uint32_t) * c, sizeof(uint32_t) * R->n_active, s));
     CK(R->meta[1 - R->cur].grow(sizeof(uint32_t) * c, 0, s));
-    CK(R->omega[R->cur].grow(b8, sizeof(double) * R->n_active, s));
-    CK(R->omega[1 - R->cur].grow(b8, 0, s));
-    CK(R->det.grow(b8, sizeof(double) * R->det_count, s));
-    CK(R->Ua.grow(b8, 0, s));
-    CK(R->Va.grow(b8, 0, s));
-    CK(R->ga.grow(b8, 0, s));
-    CK(R->w.grow(b8, 0, s));
-    CK(R->tmp.grow(b8, 0, s));
+    CK(R->omega[R->cur].grow(be, R->es * R->n_active, s));
+    CK(R->omega[1 - R->cur].grow(be, 0, s));
+    CK(R->det.grow(be, R->es * R->det_count, s));
+    CK(R->Ua.grow(be, 0, s));
+    CK(R->Va.grow(be, 0, s));
+    CK(R->ga.grow(be, 0, s));
+    CK(R->w.grow(be, 0, s));
+    CK(R->tmp.grow(sizeof(double) * (size_t)c, 0, s));   // doubles: conversions and queries
     // the basis is rebuilt every step; its leading dimension changes with c
     R->basis.release(s);
-    CK(R->basis.grow(b8 * (size_t)(m + 1), 0, s));
+    CK(R->basis.grow(be * (size_t)(m + 1), 0, s));
     R->cap = c;
     return WRC_OK;
 }
@@ -189,13 +206,14 @@ wrc_status ensure_ghost_capacity(wrc_run* R, long long ng) {
     CK(R->row_idx.grow(sizeof(int) * c * kGhostRowMax, 0, s));
     CK(R->row_w.grow(sizeof(double) * c * kGhostRowMax, 0, s));
     R->Gb.release(s);
-    CK(R->Gb.grow(sizeof(double) * c * (m + 1), 0, s));
+    CK(R->Gb.grow(R->es * c * (m + 1), 0, s));
     R->cap_g = c;
     return WRC_OK;
 }
 
 // The new grid is in `nxt` and its values are in L: stencil levels, ghosts,
 // compaction into the index list, then the compact arrays of the new grid.
+template <typename T>
 wrc_status rebuild_from_mask(wrc_run* R) {
     const Geom& g = R->g;
     const cudaStream_t s = R->st;
@@ -226,7 +244,7 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     TRY(ensure_capacity(R, na));
     TRY(ensure_ghost_capacity(R, ng));
     const int nc = 1 - R->cur;
-    launch_finalize<double>(R->list, na, R->JJ, R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<double>(), s);
+    launch_finalize<T>(R->list, na, R->JJ, (const T*)R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<T>(), s);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
     launch_ghost_rows(R->list, na, R->goff, R->gcount, g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
                       R->row_w.as<double>(), kGhostRowMax, g, R->K.overflow, s);
@@ -242,54 +260,77 @@ wrc_status rebuild_from_mask(wrc_run* R) {
 // Thresholding with eps: details of the values in L on the current grid (or
 // on every lattice point for a freshly sampled field), significance and
 // adjacent zone into nxt, closure, then the rebuild.
+template <typename T>
 wrc_status threshold_current(wrc_run* R, double eps, bool whole_lattice) {
     const Geom& g = R->g;
     const cudaStream_t s = R->st;
     CK(cudaMemsetAsync(R->sig, 0, R->N, s));
     CK(cudaMemsetAsync(R->nxt, 0, R->N, s));
     if (whole_lattice) {
-        launch_details_adj<double>(nullptr, R->N, R->L, eps, nullptr, R->sig, R->nxt, g, s);
+        launch_details_adj<T>(nullptr, R->N, (const T*)R->L, eps, nullptr, R->sig, R->nxt, g, s);
         R->det_count = 0;
     } else {
-        launch_details_adj<double>(R->meta[R->cur].as<uint32_t>(), R->n_active, R->L, eps, R->det.as<double>(),
-                                   R->sig, R->nxt, g, s);
+        launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->n_active, (const T*)R->L, eps, R->det.as<T>(),
+                              R->sig, R->nxt, g, s);
         R->det_count = R->n_active;
     }
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
     CKL("threshold");
-    return rebuild_from_mask(R);
+    return rebuild_from_mask<T>(R);
 }
 
 // L <- R(omega): the grid values, then coarse-to-fine prediction elsewhere.
+template <typename T>
 wrc_status reconstruct(wrc_run* R) {
-    launch_scatter<double>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<double>(), R->n_active, R->L, R->st);
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<double>(R->L, R->act, j, R->g, R->st);
+    launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->n_active, (T*)R->L, R->st);
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
     CKL("reconstruct");
     return WRC_OK;
 }
 
 // Linearisation at the current state: R(omega), psi, U, V and the SGS forcing.
+template <typename T>
 wrc_status freeze(wrc_run* R) {
-    TRY(reconstruct(R));
+    TRY(reconstruct<T>(R));
     const cudaStream_t s = R->st;
-    launch_poisson(R->plan, R->L, R->psi, R->C1, R->C2, R->g, s);
     const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
-    launch_velocity_active<double>(R->psi, meta, R->n_active, R->Ua.as<double>(), R->Va.as<double>(), R->g, s);
-    if (R->cfg.sgs == WRC_SGS_DYNAMIC) {
-        double* t0 = (double*)R->C1;
-        double* t1 = t0 + R->N;
-        double* t2 = (double*)R->C2;
-        double* t3 = t2 + R->N;
-        launch_sgs<double>(R->psi, meta, R->n_active, R->cfg.cs, R->ga.as<double>(), t0, t1, t2, t3, R->g, s);
+    T* t0 = (T*)R->C1;
+    T* t1 = t0 + R->N;
+    T* t2 = (T*)R->C2;
+    T* t3 = t2 + R->N;
+    const T* Ulat = nullptr;
+    if (R->fp32) {
+        // FP32 bulk: U = D_y psi, V = -D_x psi and the strain S11, S12 come
+        // from the spectrum, because finest-lattice stencils on an FP32 psi
+        // cancel 2 (first derivatives) to 5 (second derivatives) digits away.
+        double* scr = lattice_scratch(R);
+        if (!scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+        const bool dyn = R->cfg.sgs == WRC_SGS_DYNAMIC;
+        T* S11 = t2;
+        T* S12 = t3;
+        launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, (T*)R->Lq, t0, scr,
+                          dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr);
+        launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->n_active, R->Ua.as<T>(), R->Va.as<T>(), s);
+        if (dyn)
+            launch_sgs_from_strain<T>(S11, S12, meta, R->n_active, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s);
+        CKL("freeze");
+        R->frozen = true;
+        return WRC_OK;
+    } else {
+        launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s);
+        launch_velocity_active<T>((const T*)R->psi, meta, R->n_active, R->Ua.as<T>(), R->Va.as<T>(), R->g, s);
     }
+    if (R->cfg.sgs == WRC_SGS_DYNAMIC)
+        launch_sgs<T>((const T*)R->psi, meta, R->n_active, R->cfg.cs, R->ga.as<T>(), t0, t1, t2, t3, R->g, s, Ulat);
     CKL("freeze");
     R->frozen = true;
     return WRC_OK;
 }
 
-void ghost_fill(wrc_run* R, double* F, const int* kstop, int jstep) {
+template <typename T>
+void ghost_fill(wrc_run* R, T* F, const int* kstop, int jstep) {
     for (int j = 1; j <= R->g.J; ++j)
-        launch_ghost_fill<double>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
+        launch_ghost_fill<T>(F, R->list + R->goff[j], R->gcount[j], j, R->g, kstop, jstep, R->st);
 }
 
 // Algorithmic bytes of one Krylov step over n active points with Krylov
@@ -315,6 +356,7 @@ double krylov_algorithmic_flops(long long n, int k) {
 
 // Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
 // one cooperative launch.
+template <typename T>
 wrc_status krylov(wrc_run* R) {
     const cudaStream_t s = R->st;
     const long long n = R->n_active;
@@ -330,21 +372,21 @@ wrc_status krylov(wrc_run* R) {
     A.row_w = R->row_w.as<double>();
     A.rmax = kGhostRowMax;
     A.row_overflow = R->K.overflow;
-    A.Gb = R->Gb.as<double>();
+    A.Gb = R->Gb.p;
     A.ldg = R->cap_g;
-    A.Ua = R->Ua.as<double>();
-    A.Va = R->Va.as<double>();
-    A.ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<double>() : nullptr;
+    A.Ua = R->Ua.p;
+    A.Va = R->Va.p;
+    A.ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.p : nullptr;
     A.nu = nu_eff(R);
     A.r = R->cfg.rayleigh_r;
     A.c1J = 1.0 / (12.0 * R->g.h);
     A.c2J = 1.0 / (12.0 * R->g.h * R->g.h);
     A.L = R->L;
     A.Lq = R->Lq;
-    A.omega = R->omega[R->cur].as<double>();
-    A.basis = R->basis.as<double>();
+    A.omega = R->omega[R->cur].p;
+    A.basis = R->basis.p;
     A.ld = R->cap;
-    A.w = R->w.as<double>();
+    A.w = R->w.p;
     A.H = R->K.H;
     A.y = R->K.y;
     A.beta = R->K.beta;
@@ -369,7 +411,7 @@ wrc_status krylov(wrc_run* R) {
         e0 = (int)R->ev_used.size() * 2;
         CK(cudaEventRecord(R->ev_pool[e0], s));
     }
-    CK(launch_krylov_step(A, blocks, s));
+    CK(launch_krylov_step<T>(A, blocks, s));
     if (R->profiling) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
         R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
@@ -377,12 +419,13 @@ wrc_status krylov(wrc_run* R) {
     return WRC_OK;
 }
 
+template <typename T>
 wrc_status step_once(wrc_run* R) {
-    TRY(freeze(R));
-    TRY(krylov(R));
+    TRY(freeze<T>(R));
+    TRY(krylov<T>(R));
     // adaptation: L holds omega^{n+1} at the grid points; reconstruct the rest
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<double>(R->L, R->act, j, R->g, R->st);
-    TRY(threshold_current(R, R->cfg.eps, false));
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
+    TRY(threshold_current<T>(R, R->cfg.eps, false));
     R->t += R->cfg.dt;
     R->nstep += 1;
     return WRC_OK;
@@ -406,12 +449,143 @@ wrc_status copy_in(wrc_run* R, void* dst, const void* src, size_t bytes, int dev
     return WRC_OK;
 }
 
+// n values of the bulk type (device) out to doubles (host or device); FP32
+// values are widened in `scratch` (device, >= n doubles) first.
+template <typename T>
+wrc_status out_as_double(wrc_run* R, double* dst, const T* src, long long n, int device_ptr, double* scratch) {
+    if constexpr (std::is_same<T, double>::value) {
+        (void)scratch;
+        return copy_out(R, dst, src, sizeof(double) * n, device_ptr);
+    } else {
+        launch_convert<float, double>(src, scratch, n, R->st);
+        CKL("convert");
+        return copy_out(R, dst, scratch, sizeof(double) * n, device_ptr);
+    }
+}
+
+// n doubles (host or device) into the bulk type on the device.
+template <typename T>
+wrc_status in_from_double(wrc_run* R, T* dst, const double* src, long long n, int device_ptr, double* scratch) {
+    if constexpr (std::is_same<T, double>::value) {
+        (void)scratch;
+        return copy_in(R, dst, src, sizeof(double) * n, device_ptr);
+    } else {
+        TRY(copy_in(R, scratch, src, sizeof(double) * n, device_ptr));
+        launch_convert<double, float>(scratch, dst, n, R->st);
+        CKL("convert");
+        return WRC_OK;
+    }
+}
+
+template <typename T>
+wrc_status init_field_t(wrc_run* R, const double* omega_lattice, int device_ptr) {
+    double* scr = R->fp32 ? lattice_scratch(R) : nullptr;
+    if (R->fp32 && !scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+    TRY(in_from_double<T>(R, (T*)R->L, omega_lattice, R->N, device_ptr, scr));
+    CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
+    R->n_active = 0;
+    return threshold_current<T>(R, R->cfg.eps, true);
+}
+
+template <typename T>
+wrc_status set_grid_t(wrc_run* R, const uint8_t* active, const double* omega_lattice, int device_ptr) {
+    double* scr = R->fp32 ? lattice_scratch(R) : nullptr;
+    if (R->fp32 && !scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+    TRY(copy_in(R, R->nxt, active, R->N, device_ptr));
+    TRY(in_from_double<T>(R, (T*)R->L, omega_lattice, R->N, device_ptr, scr));
+    CK(cudaMemsetAsync(R->flag_dev, 0, sizeof(int), R->st));
+    launch_validate_grid(R->nxt, R->flag_dev, R->g, R->st);
+    CKL("validate");
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, R->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, R->st));
+    CK(cudaStreamSynchronize(R->st));
+    if (flag & 1) return fail(R, WRC_ERR_ARG, "grid misses a level-0 point");
+    if (flag & 2) return fail(R, WRC_ERR_ARG, "grid is not closed under DD prediction");
+    CK(cudaMemsetAsync(R->sig, 0, R->N, R->st));
+    R->det_count = 0;
+    return rebuild_from_mask<T>(R);
+}
+
+template <typename T>
+wrc_status threshold_t(wrc_run* R, double eps) {
+    TRY(reconstruct<T>(R));
+    return threshold_current<T>(R, eps, false);
+}
+
+template <typename T>
+wrc_status query_field_t(wrc_run* R, int which, double* out, int device_ptr) {
+    double* scr = R->fp32 ? lattice_scratch(R) : nullptr;
+    if (R->fp32 && !scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+    if (which == WRC_FIELD_OMEGA) {
+        TRY(reconstruct<T>(R));
+        return out_as_double<T>(R, out, (const T*)R->L, R->N, device_ptr, scr);
+    }
+    TRY(freeze<T>(R));
+    if (which == WRC_FIELD_PSI) return out_as_double<T>(R, out, (const T*)R->psi, R->N, device_ptr, scr);
+    T* t0 = (T*)R->C1;   // U
+    T* t1 = t0 + R->N;   // V
+    T* t2 = (T*)R->C2;   // nu_t
+    if (R->fp32) {
+        // spectral U, V (into Lq and C1) and strain (into C2), as in freeze
+        T* S11 = (T*)R->C2;
+        T* S12 = S11 + R->N;
+        launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, R->st, (T*)R->Lq, (T*)R->C1,
+                          scr, S11, S12, (void*)(scr + R->N));
+        T* nut = (T*)R->C1 + R->N;
+        if (which == WRC_FIELD_NUT) launch_nut_from_strain<T>(S11, S12, nut, R->cfg.cs, R->g, R->st);
+        CKL("lattice fields");
+        const T* src = which == WRC_FIELD_U ? (const T*)R->Lq : which == WRC_FIELD_V ? (const T*)R->C1 : nut;
+        // convert through the second half of the scratch (its first half was an FFT work array)
+        return out_as_double<T>(R, out, src, R->N, device_ptr, scr + R->N);
+    }
+    launch_lattice_uv_nut<T>((const T*)R->psi, t0, t1, which == WRC_FIELD_NUT ? t2 : nullptr, R->cfg.cs, t0, R->g,
+                             R->st);
+    CKL("lattice fields");
+    const T* src = which == WRC_FIELD_U ? t0 : which == WRC_FIELD_V ? t1 : t2;
+    return out_as_double<T>(R, out, src, R->N, device_ptr, scr);
+}
+
+template <typename T>
+wrc_status apply_operator_t(wrc_run* R, const double* q, double* w, double* g_out, int device_ptr) {
+    const long long n = R->n_active;
+    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
+    double* scr = R->tmp.as<double>();
+    T* qb = R->w.as<T>();
+    TRY(in_from_double<T>(R, qb, q, n, device_ptr, scr));
+    launch_scatter<T>(meta, qb, n, (T*)R->Lq, R->st);
+    ghost_fill<T>(R, (T*)R->Lq, nullptr, 0);
+    launch_matvec<T>((const T*)R->Lq, meta, n, R->Ua.as<T>(), R->Va.as<T>(), nullptr, nu_eff(R), R->cfg.rayleigh_r,
+                     qb, R->g, nullptr, 0, R->st);
+    CKL("apply_operator");
+    TRY(out_as_double<T>(R, w, qb, n, device_ptr, scr));
+    if (g_out) {
+        if (R->cfg.sgs == WRC_SGS_DYNAMIC) {
+            TRY(out_as_double<T>(R, g_out, R->ga.as<T>(), n, device_ptr, scr));
+        } else if (device_ptr) {
+            CK(cudaMemsetAsync(g_out, 0, sizeof(double) * n, R->st));
+        } else {
+            CK(cudaStreamSynchronize(R->st));
+            std::memset(g_out, 0, sizeof(double) * n);
+        }
+    }
+    return WRC_OK;
+}
+
+template <typename T>
+wrc_status diagnostics_t(wrc_run* R) {
+    TRY(reconstruct<T>(R));
+    launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, R->st);
+    launch_diag<T>((const T*)R->L, (const T*)R->psi, R->K.part, R->K.counter, R->diag_dev, R->g, R->st);
+    CKL("diagnostics");
+    return WRC_OK;
+}
+
 void free_run(wrc_run* R) {
     if (!R) return;
     cudaStream_t s = R->st;
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
-                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb})
+                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list, R->lat2idx,
@@ -432,7 +606,7 @@ bool valid_config(const wrc_config* c, std::string& why) {
     if ((long long)c->n0 << c->J > WRC_MAX_NJ) { why = "n0 * 2^J exceeds WRC_MAX_NJ"; return false; }
     if (c->krylov_m < 1 || c->krylov_m > WRC_MAX_M) { why = "krylov_m must be in 1..WRC_MAX_M"; return false; }
     if (c->sgs < 0 || c->sgs > 2) { why = "unknown sgs mode"; return false; }
-    if (c->prec != WRC_FP64) { why = "only WRC_FP64 is available in this build"; return false; }
+    if (c->prec != WRC_FP64 && c->prec != WRC_MIXED) { why = "unknown precision"; return false; }
     if (!(c->eps >= 0) || !(c->re > 0) || !(c->dt > 0) || !(c->rayleigh_r >= 0) || !(c->cs >= 0) ||
         !(c->s_apriori >= 0)) {
         why = "eps, re, dt, rayleigh_r, cs, s_apriori out of range";
@@ -455,6 +629,8 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     }
     wrc_run* R = new wrc_run();
     R->cfg = *cfg;
+    R->fp32 = cfg->prec == WRC_MIXED;
+    R->es = R->fp32 ? sizeof(float) : sizeof(double);
     R->st = (cudaStream_t)cuda_stream;
     cudaGetDevice(&R->device);
     const int NJ = cfg->n0 << cfg->J;
@@ -473,9 +649,9 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     cudaError_t e = cudaSuccess;
     void** lp[] = {(void**)&R->L, (void**)&R->Lq, (void**)&R->psi};
     for (auto p : lp)
-        if (e == cudaSuccess) e = alloc(p, sizeof(double) * N);
-    if (e == cudaSuccess) e = alloc((void**)&R->C1, sizeof(double2) * N);
-    if (e == cudaSuccess) e = alloc((void**)&R->C2, sizeof(double2) * N);
+        if (e == cudaSuccess) e = alloc(p, R->es * N);
+    if (e == cudaSuccess) e = alloc(&R->C1, 2 * R->es * N);
+    if (e == cudaSuccess) e = alloc(&R->C2, 2 * R->es * N);
     uint8_t** mp[] = {&R->act, &R->nxt, &R->gho, &R->sig, &R->JJ};
     for (auto p : mp)
         if (e == cudaSuccess) e = alloc((void**)p, N);
@@ -489,7 +665,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     if (e == cudaSuccess) e = alloc((void**)&R->vort_dev, sizeof(double) * 4 * WRC_MAX_VORTICES);
     if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
     // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
-    if (krylov_step_init(&R->max_blocks) != 0) {
+    if (krylov_step_init(R->fp32, &R->max_blocks) != 0) {
         g_create_error = "cooperative Krylov kernel set-up failed";
         free_run(R);
         return WRC_ERR_CUDA;
@@ -514,7 +690,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     R->K.counter = (unsigned*)(R->K.kstop + 6);
     cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 8, R->st);
     cudaMemsetAsync(R->flag_dev, 0, sizeof(int) * 4, R->st);
-    if (poisson_plan_init(R->plan, R->g, R->st) != 0) {
+    if (poisson_plan_init(R->plan, R->g, R->fp32, R->st) != 0) {
         g_create_error = "FFT/expm kernel set-up failed";
         free_run(R);
         return WRC_ERR_CUDA;
@@ -543,12 +719,13 @@ wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const doub
         prm[3 * n + v] = s[v];
     }
     CK(cudaMemcpyAsync(R->vort_dev, prm, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, R->st));
-    launch_init_vortices<double>(R->L, R->vort_dev, n, R->g, R->st);
+    if (R->fp32) launch_init_vortices<float>((float*)R->L, R->vort_dev, n, R->g, R->st);
+    else launch_init_vortices<double>((double*)R->L, R->vort_dev, n, R->g, R->st);
     CKL("init_vortices");
     CK(cudaStreamSynchronize(R->st));   // prm is a stack array
     CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
     R->n_active = 0;
-    TRY(threshold_current(R, R->cfg.eps, true));
+    TRY(DISPATCH(R, threshold_current, R, R->cfg.eps, true));
     R->init = true;
     R->t = 0.0;
     R->nstep = 0;
@@ -558,10 +735,7 @@ wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const doub
 wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
     if (!omega_lattice) return fail(R, WRC_ERR_ARG, "omega_lattice is NULL");
-    TRY(copy_in(R, R->L, omega_lattice, sizeof(double) * R->N, device_ptr));
-    CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
-    R->n_active = 0;
-    TRY(threshold_current(R, R->cfg.eps, true));
+    TRY(DISPATCH(R, init_field_t, R, omega_lattice, device_ptr));
     R->init = true;
     R->t = 0.0;
     R->nstep = 0;
@@ -571,19 +745,7 @@ wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t devic
 wrc_status wrc_set_grid(wrc_run* R, const uint8_t* active, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
     if (!active || !omega_lattice) return fail(R, WRC_ERR_ARG, "NULL input");
-    TRY(copy_in(R, R->nxt, active, R->N, device_ptr));
-    TRY(copy_in(R, R->L, omega_lattice, sizeof(double) * R->N, device_ptr));
-    CK(cudaMemsetAsync(R->flag_dev, 0, sizeof(int), R->st));
-    launch_validate_grid(R->nxt, R->flag_dev, R->g, R->st);
-    CKL("validate");
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, R->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, R->st));
-    CK(cudaStreamSynchronize(R->st));
-    if (flag & 1) return fail(R, WRC_ERR_ARG, "grid misses a level-0 point");
-    if (flag & 2) return fail(R, WRC_ERR_ARG, "grid is not closed under DD prediction");
-    CK(cudaMemsetAsync(R->sig, 0, R->N, R->st));
-    R->det_count = 0;
-    TRY(rebuild_from_mask(R));
+    TRY(DISPATCH(R, set_grid_t, R, active, omega_lattice, device_ptr));
     R->init = true;
     return WRC_OK;
 }
@@ -592,14 +754,13 @@ wrc_status wrc_threshold(wrc_run* R, double eps) {
     TRY(check_ready(R));
     if (!(eps >= 0)) return fail(R, WRC_ERR_ARG, "eps must be >= 0");
     R->cfg.eps = eps;
-    TRY(reconstruct(R));
-    return threshold_current(R, eps, false);
+    return DISPATCH(R, threshold_t, R, eps);
 }
 
 wrc_status wrc_step(wrc_run* R, int32_t nsteps) {
     TRY(check_ready(R));
     if (nsteps < 0) return fail(R, WRC_ERR_ARG, "nsteps < 0");
-    for (int q = 0; q < nsteps; ++q) TRY(step_once(R));
+    for (int q = 0; q < nsteps; ++q) TRY(DISPATCH(R, step_once, R));
     return WRC_OK;
 }
 
@@ -635,13 +796,17 @@ wrc_status wrc_query_active(wrc_run* R, int32_t* idx_out, double* omega_out, int
     TRY(check_ready(R));
     if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
     const long long n = R->n_active;
+    if (omega_out) {
+        if (R->fp32) TRY(out_as_double<float>(R, omega_out, R->omega[R->cur].as<float>(), n, device_ptr, R->tmp.as<double>()));
+        else TRY(copy_out(R, omega_out, R->omega[R->cur].p, sizeof(double) * n, device_ptr));
+        CK(cudaStreamSynchronize(R->st));
+    }
     if (idx_out) {
         int* tmpi = R->tmp.as<int>();   // tmp holds >= n doubles, i.e. >= 2n ints
         launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, tmpi, nullptr, nullptr, R->st);
         CKL("unpack");
         TRY(copy_out(R, idx_out, tmpi, sizeof(int) * n, device_ptr));
     }
-    if (omega_out) TRY(copy_out(R, omega_out, R->omega[R->cur].p, sizeof(double) * n, device_ptr));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
 }
@@ -659,7 +824,8 @@ wrc_status wrc_query_details(wrc_run* R, double* d_out, int64_t cap, int32_t dev
     TRY(check_ready(R));
     if (!d_out) return fail(R, WRC_ERR_ARG, "NULL output");
     if (cap < R->det_count) return fail(R, WRC_ERR_ARG, "cap smaller than the detail count");
-    TRY(copy_out(R, d_out, R->det.p, sizeof(double) * R->det_count, device_ptr));
+    if (R->fp32) TRY(out_as_double<float>(R, d_out, R->det.as<float>(), R->det_count, device_ptr, R->tmp.as<double>()));
+    else TRY(copy_out(R, d_out, R->det.p, sizeof(double) * R->det_count, device_ptr));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
 }
@@ -681,32 +847,14 @@ wrc_status wrc_query_stencil_levels(wrc_run* R, uint8_t* jx_out, uint8_t* jy_out
 wrc_status wrc_query_field(wrc_run* R, int32_t which, double* out, int32_t device_ptr) {
     TRY(check_ready(R));
     if (!out || which < 0 || which > 4) return fail(R, WRC_ERR_ARG, "bad field or NULL output");
-    const size_t bytes = sizeof(double) * R->N;
-    if (which == WRC_FIELD_OMEGA) {
-        TRY(reconstruct(R));
-        TRY(copy_out(R, out, R->L, bytes, device_ptr));
-    } else {
-        TRY(freeze(R));
-        if (which == WRC_FIELD_PSI) {
-            TRY(copy_out(R, out, R->psi, bytes, device_ptr));
-        } else {
-            double* t0 = (double*)R->C1;   // U
-            double* t1 = t0 + R->N;        // V
-            double* t2 = (double*)R->C2;   // nu_t
-            launch_lattice_uv_nut<double>(R->psi, t0, t1, which == WRC_FIELD_NUT ? t2 : nullptr, R->cfg.cs, t0,
-                                          R->g, R->st);
-            CKL("lattice fields");
-            const double* src = which == WRC_FIELD_U ? t0 : which == WRC_FIELD_V ? t1 : t2;
-            TRY(copy_out(R, out, src, bytes, device_ptr));
-        }
-    }
+    TRY(DISPATCH(R, query_field_t, R, which, out, device_ptr));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
 }
 
 wrc_status wrc_freeze(wrc_run* R) {
     TRY(check_ready(R));
-    TRY(freeze(R));
+    TRY(DISPATCH(R, freeze, R));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
 }
@@ -715,24 +863,7 @@ wrc_status wrc_apply_operator(wrc_run* R, const double* q, double* w, double* g_
     TRY(check_ready(R));
     if (!R->frozen) return fail(R, WRC_ERR_STATE, "call wrc_freeze after the last grid change");
     if (!q || !w) return fail(R, WRC_ERR_ARG, "NULL input or output");
-    const long long n = R->n_active;
-    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
-    TRY(copy_in(R, R->tmp.p, q, sizeof(double) * n, device_ptr));
-    launch_scatter<double>(meta, R->tmp.as<double>(), n, R->Lq, R->st);
-    ghost_fill(R, R->Lq, nullptr, 0);
-    launch_matvec<double>(R->Lq, meta, n, R->Ua.as<double>(), R->Va.as<double>(), nullptr, nu_eff(R),
-                          R->cfg.rayleigh_r, R->tmp.as<double>(), R->g, nullptr, 0, R->st);
-    CKL("apply_operator");
-    TRY(copy_out(R, w, R->tmp.p, sizeof(double) * n, device_ptr));
-    if (g_out) {
-        if (R->cfg.sgs == WRC_SGS_DYNAMIC) {
-            TRY(copy_out(R, g_out, R->ga.p, sizeof(double) * n, device_ptr));
-        } else if (device_ptr) {
-            CK(cudaMemsetAsync(g_out, 0, sizeof(double) * n, R->st));
-        } else {
-            std::memset(g_out, 0, sizeof(double) * n);
-        }
-    }
+    TRY(DISPATCH(R, apply_operator_t, R, q, w, g_out, device_ptr));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
 }
@@ -759,10 +890,7 @@ wrc_status wrc_query_krylov(wrc_run* R, double* beta, int32_t* k, double* h_last
 wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
     TRY(check_ready(R));
     if (!out) return fail(R, WRC_ERR_ARG, "NULL output");
-    TRY(reconstruct(R));
-    launch_poisson(R->plan, R->L, R->psi, R->C1, R->C2, R->g, R->st);
-    launch_diag(R->L, R->psi, R->K.part, R->K.counter, R->diag_dev, R->g, R->st);
-    CKL("diagnostics");
+    TRY(DISPATCH(R, diagnostics_t, R));
     double s[4];
     CK(cudaMemcpyAsync(s, R->diag_dev, sizeof(s), cudaMemcpyDeviceToHost, R->st));
     CK(cudaStreamSynchronize(R->st));

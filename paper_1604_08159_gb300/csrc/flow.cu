@@ -46,15 +46,42 @@ __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __r
     }
 }
 
-// Smagorinsky pass 1: t0 = U = dpsi/dy, t1 = S12 = (psi_yy - psi_xx)/2.
+// Smagorinsky pass 1: t0 = U = dpsi/dy (unless given), t1 = S12 = (psi_yy - psi_xx)/2.
 template <typename T>
 __global__ void k_sgs1(const T* __restrict__ psi, T* __restrict__ t0, T* __restrict__ t1, Geom g, T c1, T c2) {
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p & g.mask), k = (int)(p >> g.L);
-        t0[p] = dy1(psi, i, k, g, c1);
+        if (t0) t0[p] = dy1(psi, i, k, g, c1);
         t1[p] = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
+    }
+}
+
+// nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5); a = 2 nu_t S12, c = nu_t S11
+// (nut and c may be null).
+template <typename T>
+__global__ void k_strain_nut(const T* __restrict__ S11, const T* __restrict__ S12, T* __restrict__ nut,
+                             T* __restrict__ a, T* __restrict__ c, long long N, T csh2) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const T s11 = S11[p], s12 = S12[p];
+        const T nt = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
+        if (nut) nut[p] = nt;
+        if (a) a[p] = T(2) * nt * s12;
+        if (c) c[p] = nt * s11;
+    }
+}
+
+template <typename T>
+__global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restrict__ Vlat,
+                                  const uint32_t* __restrict__ meta, long long n, T* __restrict__ Ua,
+                                  T* __restrict__ Va) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        Ua[a] = Ulat[p];
+        Va[a] = Vlat[p];
     }
 }
 
@@ -143,9 +170,10 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const T* __restrict__ F, co
 
 // Lattice sums of R, R^2, U^2 + V^2 and |grad R|^2 (deterministic two-stage
 // reduction: per-block partials, then the last block sums them in order).
-__global__ void __launch_bounds__(kThreads) k_diag(const double* __restrict__ R, const double* __restrict__ psi,
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_diag(const T* __restrict__ R, const T* __restrict__ psi,
                                                    double* __restrict__ partials, unsigned* __restrict__ counter,
-                                                   double* __restrict__ out, Geom g, double c1) {
+                                                   double* __restrict__ out, Geom g, T c1) {
     __shared__ double s_red[kThreads / 32][4];
     __shared__ bool s_last;
     const long long N = (long long)g.NJ * g.NJ;
@@ -153,9 +181,9 @@ __global__ void __launch_bounds__(kThreads) k_diag(const double* __restrict__ R,
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p & g.mask), k = (int)(p >> g.L);
-        const double r = R[p];
-        const double U = dy1(psi, i, k, g, c1), V = -dx1(psi, i, k, g, c1);
-        const double gx = dx1(R, i, k, g, c1), gy = dy1(R, i, k, g, c1);
+        const double r = (double)R[p];
+        const double U = (double)dy1(psi, i, k, g, c1), V = -(double)dx1(psi, i, k, g, c1);
+        const double gx = (double)dx1(R, i, k, g, c1), gy = (double)dy1(R, i, k, g, c1);
         acc[0] += r;
         acc[1] += r * r;
         acc[2] += U * U + V * V;
@@ -200,22 +228,47 @@ void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* 
 
 template <typename T>
 void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1, T* t2, T* t3,
-                const Geom& g, cudaStream_t s) {
+                const Geom& g, cudaStream_t s, const T* Ulat) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
-    { k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, t0, t1, g, c1, c2); note_launch(); }
-    { k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(t0, t1, t2, t3, g, c1, csh2); note_launch(); }
+    { k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Ulat ? nullptr : t0, t1, g, c1, c2); note_launch(); }
+    { k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(Ulat ? Ulat : t0, t1, t2, t3, g, c1, csh2); note_launch(); }
     { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1); note_launch(); }
     if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2); note_launch(); }
 }
 
 template <typename T>
-void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g, cudaStream_t s) {
+void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.NJ * g.NJ;
+    const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
+    const T csh2 = T((cs * g.h) * (cs * g.h));
+    { k_strain_nut<T><<<blocks_for(N), kThreads, 0, s>>>(S11, S12, nullptr, ta, tc, N, csh2); note_launch(); }
+    { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(tc, tdyc, g, c1); note_launch(); }
+    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(ta, tdyc, meta, n, ga, g, c1, c2); note_launch(); }
+}
+
+template <typename T>
+void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.NJ * g.NJ;
+    { k_strain_nut<T><<<blocks_for(N), kThreads, 0, s>>>(S11, S12, nut, nullptr, nullptr, N,
+                                                          T((cs * g.h) * (cs * g.h))); note_launch(); }
+}
+
+template <typename T>
+void launch_velocity_gather(const T* Ulat, const T* Vlat, const uint32_t* meta, long long n, T* Ua, T* Va,
+                            cudaStream_t s) {
+    if (n > 0) { k_velocity_gather<T><<<blocks_for(n), kThreads, 0, s>>>(Ulat, Vlat, meta, n, Ua, Va); note_launch(); }
+}
+
+template <typename T>
+void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g, cudaStream_t s,
+                           bool uv_given) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     T* Uw = U ? U : tmp;
-    { k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1); note_launch(); }
+    if (!uv_given) { k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1); note_launch(); }
     if (nut)
         { k_lattice_nut<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h))); note_launch(); }
 }
@@ -229,20 +282,41 @@ void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, c
                                                        jstep); note_launch(); }
 }
 
-void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
-                 const Geom& g, cudaStream_t s) {
-    { k_diag<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
-                                                                    1.0 / (12.0 * g.h)); note_launch(); }
+template <typename T>
+void launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
+                 cudaStream_t s) {
+    { k_diag<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
+                                                                       T(1.0 / (12.0 * g.h))); note_launch(); }
 }
+
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        out[t] = (B)in[t];
+}
+
+template <typename A, typename B>
+void launch_convert(const A* in, B* out, long long n, cudaStream_t s) {
+    if (n > 0) { k_convert<A, B><<<blocks_for(n), kThreads, 0, s>>>(in, out, n); note_launch(); }
+}
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 
 #define WRC_INST(T)                                                                                          \
     template void launch_velocity_active<T>(const T*, const uint32_t*, long long, T*, T*, const Geom&,      \
                                             cudaStream_t);                                                  \
     template void launch_sgs<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, T*, T*,           \
-                                const Geom&, cudaStream_t);                                                 \
-    template void launch_lattice_uv_nut<T>(const T*, T*, T*, T*, double, T*, const Geom&, cudaStream_t);     \
+                                const Geom&, cudaStream_t, const T*);                                       \
+    template void launch_velocity_gather<T>(const T*, const T*, const uint32_t*, long long, T*, T*,         \
+                                            cudaStream_t);                                                  \
+    template void launch_sgs_from_strain<T>(const T*, const T*, const uint32_t*, long long, double, T*, T*, \
+                                            T*, T*, const Geom&, cudaStream_t);                             \
+    template void launch_nut_from_strain<T>(const T*, const T*, T*, double, const Geom&, cudaStream_t);     \
+    template void launch_lattice_uv_nut<T>(const T*, T*, T*, T*, double, T*, const Geom&, cudaStream_t,     \
+                                           bool);                                                           \
     template void launch_matvec<T>(const T*, const uint32_t*, long long, const T*, const T*, const T*,      \
-                                   double, double, T*, const Geom&, const int*, int, cudaStream_t);
+                                   double, double, T*, const Geom&, const int*, int, cudaStream_t);        \
+    template void launch_diag<T>(const T*, const T*, double*, unsigned*, double*, const Geom&, cudaStream_t);
 WRC_INST(double)
 WRC_INST(float)
 #undef WRC_INST

@@ -42,32 +42,55 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
 // ---- fft.cu: streamfunction -------------------------------------------------
 struct PoissonPlan {
     int n = 0, logn = 0;
-    double2* tw = nullptr;     // exp(-2 pi i t/n), t < n/2
-    double* sigma = nullptr;   // symbol of the 4th-order second-derivative stencil
+    bool fp32 = false;
+    void* tw = nullptr;      // exp(-2 pi i t/n), t < n/2 (complex of the run's bulk type)
+    void* sigma = nullptr;   // symbol of the 4th-order second-derivative stencil
+    void* dsym = nullptr;    // symbol of the 4th-order first-derivative stencil (imaginary part)
 };
-int poisson_plan_init(PoissonPlan& p, const Geom& g, cudaStream_t s);
+int poisson_plan_init(PoissonPlan& p, const Geom& g, bool fp32, cudaStream_t s);
 void poisson_plan_free(PoissonPlan& p);
-// psi = L_h^{-1}(-(R - mean R)), mean(psi) = 0; C1, C2 are NJ*NJ complex work arrays.
-void launch_poisson(const PoissonPlan& p, const double* R, double* psi, double2* C1, double2* C2,
-                    const Geom& g, cudaStream_t s);
+// psi = L_h^{-1}(-(R - mean R)), mean(psi) = 0; C1, C2 are NJ*NJ complex work
+// arrays.  With U, V and a third work array C3, also U = D_y psi and
+// V = -D_x psi on the lattice, evaluated in the Fourier domain (no cancellation);
+// with S11, S12 and a fourth work array C4, also the strain S11 = D_x D_y psi and
+// S12 = (D_yy - D_xx) psi / 2.  S11 and S12 may not alias C1, C2 or C3.
+template <typename T>
+void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1, void* C2, const Geom& g, cudaStream_t s,
+                    T* U = nullptr, T* V = nullptr, void* C3 = nullptr, T* S11 = nullptr, T* S12 = nullptr,
+                    void* C4 = nullptr);
 
 // ---- flow.cu: velocity, Smagorinsky forcing, operator, diagnostics ----------
 template <typename T>
 void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va,
                             const Geom& g, cudaStream_t s);
+// Smagorinsky forcing at the active points; Ulat (optional) is U = dpsi/dy on
+// the lattice, otherwise computed from psi by the stencil.
 template <typename T>
 void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1,
-                T* t2, T* t3, const Geom& g, cudaStream_t s);
+                T* t2, T* t3, const Geom& g, cudaStream_t s, const T* Ulat = nullptr);
+// Smagorinsky forcing from the lattice strain (S11, S12): nu_t, then
+// a = 2 nu_t S12 and c = nu_t S11 into ta, tc, D_y c into tdyc, g at the active points.
+template <typename T>
+void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s);
+template <typename T>
+void launch_velocity_gather(const T* Ulat, const T* Vlat, const uint32_t* meta, long long n, T* Ua, T* Va,
+                            cudaStream_t s);
 template <typename T>
 void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g,
-                           cudaStream_t s);
+                           cudaStream_t s, bool uv_given = false);
 template <typename T>
 void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va,
                    const T* ga, double nu, double r, T* w, const Geom& g, const int* kstop, int jstep,
                    cudaStream_t s);
-// sums over the lattice of R, R^2, U^2 + V^2, |grad R|^2 -> out[0..3]
-void launch_diag(const double* R, const double* psi, double* partials, unsigned* counter, double* out,
-                 const Geom& g, cudaStream_t s);
+// sums over the lattice of R, R^2, U^2 + V^2, |grad R|^2 -> out[0..3] (FP64 sums)
+template <typename T>
+void launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
+                 cudaStream_t s);
+template <typename A, typename B>
+void launch_convert(const A* in, B* out, long long n, cudaStream_t s);
 
 // ---- krylov.cu: the Krylov-projected step as one cooperative kernel ---------
 struct KrylovStepArgs {
@@ -81,18 +104,19 @@ struct KrylovStepArgs {
     const double* row_w;
     int rmax;
     const int* row_overflow; // non-zero: some row exceeded rmax (the kernel refuses to run)
-    double* Gb;             // ghost values of the basis vectors, (m+1) x ldg
+    void* Gb;               // ghost values of the basis vectors, (m+1) x ldg
     long long ldg;
-    const double* Ua;
-    const double* Va;
-    const double* ga;       // SGS forcing at the active points or nullptr
+    // arrays of the run's bulk type (double, or float for the mixed mode)
+    const void* Ua;
+    const void* Va;
+    const void* ga;         // SGS forcing at the active points or nullptr
     double nu, r, c1J, c2J; // nu_eff, Rayleigh r, 1/(12 h_J), 1/(12 h_J^2)
-    double* L;              // R(omega) on the lattice (in), omega^{n+1} at the active points (out)
-    double* Lq;             // lattice array of the current Krylov vector and its ghost values
-    double* omega;          // compact omega, updated in place
-    double* basis;          // (m+1) x ld
+    void* L;                // R(omega) on the lattice (in), omega^{n+1} at the active points (out)
+    void* Lq;               // lattice array of the current Krylov vector and its ghost values
+    void* omega;            // compact omega, updated in place
+    void* basis;            // (m+1) x ld
     long long ld;
-    double* w;
+    void* w;
     double* H;              // (m+1) x m row-major
     double* y;              // m
     double* beta;           // [1]
@@ -105,8 +129,9 @@ struct KrylovStepArgs {
     double dt, tol;
     unsigned long long limit_ns;
 };
-int krylov_step_init(int* max_blocks);
+int krylov_step_init(bool fp32, int* max_blocks);
 int krylov_step_blocks(long long n, int max_blocks);
+template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s);
 size_t krylov_partials_doubles(int max_blocks);
 

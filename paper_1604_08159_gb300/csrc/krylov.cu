@@ -167,24 +167,40 @@ __global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const
     if (lane < m) y[lane] = lane < k ? x : 0.0;
 }
 
-// omega <- omega + dt beta V_k y, also written into the lattice array L.
-__global__ void k_update(const double* __restrict__ basis, long long ld, const double* __restrict__ y,
+// omega <- omega + dt beta V_k y (accumulated in FP64), also written into the
+// lattice array L.
+template <typename T>
+__global__ void k_update(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
                          const double* __restrict__ beta, const int* __restrict__ kstop, double dt,
-                         const uint32_t* __restrict__ meta, int n, double* __restrict__ omega, double* __restrict__ L) {
+                         const uint32_t* __restrict__ meta, int n, T* __restrict__ omega, T* __restrict__ L) {
     __shared__ double s_c[kNV];
     const int k = *kstop;
     for (int t = threadIdx.x; t < k; t += blockDim.x) s_c[t] = dt * beta[0] * y[t];
     __syncthreads();
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
         double inc = 0.0;
-        for (int t = 0; t < k; ++t) inc += s_c[t] * basis[(size_t)t * ld + a];
-        const double x = omega[a] + inc;
+        for (int t = 0; t < k; ++t) inc += s_c[t] * (double)basis[(size_t)t * ld + a];
+        const T x = (T)((double)omega[a] + inc);
         omega[a] = x;
         L[meta_pos(meta[a])] = x;
     }
 }
 
+// x - c v in the bulk type: FP64 for the plain mode, FP32 (coefficient
+// rounded) for the mixed mode.
+__device__ __forceinline__ double axmy(double x, double v, double c) { return x - v * c; }
+__device__ __forceinline__ float axmy(float x, float v, double c) { return x - v * (float)c; }
+
+template <typename T>
 __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
+    const T* __restrict__ Ua = (const T*)A.Ua;
+    const T* __restrict__ Va = (const T*)A.Va;
+    const T* __restrict__ ga = (const T*)A.ga;
+    const T* __restrict__ Lb = (const T*)A.L;
+    T* __restrict__ Lq = (T*)A.Lq;
+    T* __restrict__ basis = (T*)A.basis;
+    T* __restrict__ w = (T*)A.w;
+    T* __restrict__ Gb = (T*)A.Gb;
     __shared__ double s_red[kPT / 32][kNV + 1];
     __shared__ double s_h[kOutP];
     __shared__ double s_c[kNV];
@@ -195,8 +211,9 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
     double* P0 = A.part;
     double* P1 = P0 + (size_t)gridDim.x * kOutP;
     double* P2 = P1 + (size_t)gridDim.x * kOutP;
-    const double nu = A.nu, r = A.r;
+    const T nu = (T)A.nu, r = (T)A.r, c1J = (T)A.c1J, c2J = (T)A.c2J;
     const int m = A.m;
+    const long long ld = A.ld, ldg = A.ldg;
     double acc[kNV + 1];
     if (*(volatile const int*)A.row_overflow) {
         if (lead) atomicOr(A.err, 4);
@@ -207,10 +224,10 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
 #pragma unroll
     for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
     for (int a = a0; a < n; a += stride) {
-        double v = apply_point<double, false>(A.L, A.meta[a], A.Ua[a], A.Va[a], nu, r, A.g, A.c1J, A.c2J);
-        if (A.ga) v += A.ga[a];
-        A.w[a] = v;
-        acc[kNV] += v * v;
+        T v = apply_point<T, false>(Lb, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+        if (ga) v += ga[a];
+        w[a] = v;
+        acc[kNV] += (double)v * (double)v;
     }
     block_partials(acc, 0, P0 + (size_t)blockIdx.x * kOutP, s_red);
     if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
@@ -228,17 +245,18 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
         // rows, at the ghosts
         const double inv = 1.0 / beta;
         for (int a = a0; a < n; a += stride) {
-            const double v = A.w[a] * inv;
-            A.basis[a] = v;
-            A.Lq[meta_pos(A.meta[a])] = v;
+            const T v = (T)((double)w[a] * inv);
+            basis[a] = v;
+            Lq[meta_pos(A.meta[a])] = v;
         }
         for (int t = a0; t < A.ng; t += stride) {
             const int rl = A.row_len[t];
             double gv = 0.0;
-            for (int e = 0; e < rl; ++e) gv += A.row_w[(size_t)t * A.rmax + e] * __ldcg(A.w + A.row_idx[(size_t)t * A.rmax + e]);
-            gv *= inv;
-            A.Gb[t] = gv;
-            A.Lq[A.glist[t]] = gv;
+            for (int e = 0; e < rl; ++e)
+                gv += A.row_w[(size_t)t * A.rmax + e] * (double)__ldcg(w + A.row_idx[(size_t)t * A.rmax + e]);
+            const T g = (T)(gv * inv);
+            Gb[t] = g;
+            Lq[A.glist[t]] = g;
         }
         if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
         for (int j = 0; j < m; ++j) {
@@ -247,12 +265,13 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
 #pragma unroll
             for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
             for (int a = a0; a < n; a += stride) {
-                const double v = apply_point<double, true>(A.Lq, A.meta[a], A.Ua[a], A.Va[a], nu, r, A.g, A.c1J, A.c2J);
-                A.w[a] = v;
+                const T v = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+                w[a] = v;
+                const double vd = (double)v;
 #pragma unroll
                 for (int t = 0; t < kNV; ++t)
-                    if (t < nv) acc[t] += A.basis[(size_t)t * A.ld + a] * v;
-                acc[kNV] += v * v;
+                    if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * vd;
+                acc[kNV] += vd * vd;
             }
             block_partials(acc, nv, P0 + (size_t)blockIdx.x * kOutP, s_red);
             if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
@@ -264,15 +283,16 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
 #pragma unroll
             for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
             for (int a = a0; a < n; a += stride) {
-                double x = A.w[a];
+                T x = w[a];
 #pragma unroll
                 for (int t = 0; t < kNV; ++t)
-                    if (t < nv) x -= A.basis[(size_t)t * A.ld + a] * s_c[t];
-                A.w[a] = x;
+                    if (t < nv) x = axmy(x, basis[(size_t)t * ld + a], s_c[t]);
+                w[a] = x;
+                const double xd = (double)x;
 #pragma unroll
                 for (int t = 0; t < kNV; ++t)
-                    if (t < nv) acc[t] += A.basis[(size_t)t * A.ld + a] * x;
-                acc[kNV] += x * x;
+                    if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * xd;
+                acc[kNV] += xd * xd;
             }
             block_partials(acc, nv, P1 + (size_t)blockIdx.x * kOutP, s_red);
             if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
@@ -306,23 +326,23 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
             // ghosts by linearity from w' and the ghost values of v_0..v_j
             const double inv2 = 1.0 / hn;
             for (int a = a0; a < n; a += stride) {
-                double x = A.w[a];
+                T x = w[a];
 #pragma unroll
                 for (int t = 0; t < kNV; ++t)
-                    if (t < nv) x -= A.basis[(size_t)t * A.ld + a] * s_c[t];
-                const double v = x * inv2;
-                A.basis[(size_t)(j + 1) * A.ld + a] = v;
-                A.Lq[meta_pos(A.meta[a])] = v;
+                    if (t < nv) x = axmy(x, basis[(size_t)t * ld + a], s_c[t]);
+                const T v = (T)((double)x * inv2);
+                basis[(size_t)(j + 1) * ld + a] = v;
+                Lq[meta_pos(A.meta[a])] = v;
             }
             for (int t = a0; t < A.ng; t += stride) {
                 const int rl = A.row_len[t];
                 double gv = 0.0;
                 for (int e = 0; e < rl; ++e)
-                    gv += A.row_w[(size_t)t * A.rmax + e] * __ldcg(A.w + A.row_idx[(size_t)t * A.rmax + e]);
-                for (int q = 0; q < nv; ++q) gv -= s_c[q] * A.Gb[(size_t)q * A.ldg + t];
-                gv *= inv2;
-                A.Gb[(size_t)(j + 1) * A.ldg + t] = gv;
-                A.Lq[A.glist[t]] = gv;
+                    gv += A.row_w[(size_t)t * A.rmax + e] * (double)__ldcg(w + A.row_idx[(size_t)t * A.rmax + e]);
+                for (int q = 0; q < nv; ++q) gv -= s_c[q] * (double)Gb[(size_t)q * ldg + t];
+                const T g = (T)(gv * inv2);
+                Gb[(size_t)(j + 1) * ldg + t] = g;
+                Lq[A.glist[t]] = g;
             }
             if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
         }
@@ -332,12 +352,13 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
 
 }  // namespace
 
-int krylov_step_init(int* max_blocks) {
+int krylov_step_init(bool fp32, int* max_blocks) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step, kPT, 0) != cudaSuccess || per < 1)
-        return -2;
+    const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float>, kPT, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double>, kPT, 0);
+    if (e != cudaSuccess || per < 1) return -2;
     *max_blocks = sms * per;
     return 0;
 }
@@ -349,19 +370,23 @@ int krylov_step_blocks(long long n, int max_blocks) {
     return (int)b;
 }
 
+template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
     KrylovStepArgs a = args;
     void* params[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step, dim3(blocks), dim3(kPT), params, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T>, dim3(blocks), dim3(kPT), params, 0, s);
     if (e != cudaSuccess) return e;
     note_launch();
     k_phi1<<<1, 32, 0, s>>>(args.H, args.kstop, args.m, args.dt, args.y);
     note_launch();
-    k_update<<<blocks_for(args.n), kThreads, 0, s>>>(args.basis, args.ld, args.y, args.beta, args.kstop, args.dt,
-                                                     args.meta, args.n, args.omega, args.L);
+    k_update<T><<<blocks_for(args.n), kThreads, 0, s>>>((const T*)args.basis, args.ld, args.y, args.beta, args.kstop,
+                                                        args.dt, args.meta, args.n, (T*)args.omega, (T*)args.L);
     note_launch();
     return cudaGetLastError();
 }
+
+template cudaError_t launch_krylov_step<double>(const KrylovStepArgs&, int, cudaStream_t);
+template cudaError_t launch_krylov_step<float>(const KrylovStepArgs&, int, cudaStream_t);
 
 size_t krylov_partials_doubles(int max_blocks) { return (size_t)3 * max_blocks * kOutP; }
 
