@@ -17,9 +17,16 @@ using namespace wrc;
 
 namespace {
 std::atomic<long long> g_launches{0};
+// While a CUDA graph is being captured on this thread, launches are only
+// counted into the graph (and booked each time the graph is launched).
+thread_local bool g_capturing = false;
+thread_local long long g_captured = 0;
 }
 
-void wrc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void wrc::note_launch() {
+    if (g_capturing) ++g_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 long long wrc::launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
@@ -115,12 +122,22 @@ struct wrc_run {
     // event timing of the Gram-Schmidt passes (wrc_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
+    // CUDA graphs of the step phases, per phase and ping-pong parity; rebuilt
+    // when a buffer they use is reallocated (layout) or eps changes
+    struct Phase {
+        cudaGraphExec_t exec = nullptr;
+        long long layout = -1;
+        long long kernels = 0;
+    } graphs[3][2];
+    long long layout = 0;
+    bool use_graphs = false;
     struct ProfRec { int ev; double bytes, flops; };
     std::vector<ProfRec> ev_used;   // start-event index, algorithmic bytes and flops per launch
     long long host_syncs = 0;
 
     // state
     long long n_active = 0, n_ghost = 0, det_count = 0;
+    long long pend_na = 0, pend_ng = 0;   // counts of the grid being rebuilt
     long long gcount[16] = {0}, goff[16] = {0};
     double t = 0.0;
     long long nstep = 0;
@@ -193,6 +210,7 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     R->basis.release(s);
     CK(R->basis.grow(be * (size_t)(m + 1), 0, s));
     R->cap = c;
+    R->layout += 1;
     return WRC_OK;
 }
 
@@ -208,13 +226,14 @@ wrc_status ensure_ghost_capacity(wrc_run* R, long long ng) {
     R->Gb.release(s);
     CK(R->Gb.grow(R->es * c * (m + 1), 0, s));
     R->cap_g = c;
+    R->layout += 1;
     return WRC_OK;
 }
 
-// The new grid is in `nxt` and its values are in L: stencil levels, ghosts,
-// compaction into the index list, then the compact arrays of the new grid.
-template <typename T>
-wrc_status rebuild_from_mask(wrc_run* R) {
+// A grid rebuild in three parts.  Part 1 (device, capturable): the new grid
+// is in `nxt` and its values in L; stencil levels, ghosts, compaction into
+// the index list; the per-key counts and the error word go to pinned memory.
+wrc_status rebuild_part1(wrc_run* R) {
     const Geom& g = R->g;
     const cudaStream_t s = R->st;
     CK(cudaMemsetAsync(R->gho, 0, R->N, s));
@@ -222,9 +241,16 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->gho, R->nxt, j, g, s);
     const int nkeys = g.J + 1;
     launch_compact(R->nxt, R->gho, g, nkeys, R->blk_counts, R->blk_off, R->counts_dev, R->list, s);
-    CKL("compaction");
     CK(cudaMemcpyAsync(R->counts_host, R->counts_dev, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(R->counts_host + kMaxKeys, R->K.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKL("compaction");
+    return WRC_OK;
+}
+
+// Host part: wait for the counts, report a Krylov-kernel error, grow buffers.
+wrc_status rebuild_host(wrc_run* R) {
+    const Geom& g = R->g;
+    const cudaStream_t s = R->st;
     CK(cudaStreamSynchronize(s));
     R->host_syncs += 1;
     if (R->counts_host[kMaxKeys] != 0) {
@@ -243,46 +269,112 @@ wrc_status rebuild_from_mask(wrc_run* R) {
     }
     TRY(ensure_capacity(R, na));
     TRY(ensure_ghost_capacity(R, ng));
+    R->pend_na = na;
+    R->pend_ng = ng;
+    return WRC_OK;
+}
+
+// Part 2 (device, capturable): compact arrays of the new grid and the ghost
+// interpolation rows, all sizes read from the counts on the device.
+template <typename T>
+wrc_status rebuild_part2(wrc_run* R) {
+    const cudaStream_t s = R->st;
     const int nc = 1 - R->cur;
-    launch_finalize<T>(R->list, na, R->JJ, (const T*)R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<T>(), s);
+    launch_finalize<T>(R->list, R->cap, R->JJ, (const T*)R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<T>(), s,
+                       R->counts_dev);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
-    launch_ghost_rows(R->list, na, R->goff, R->gcount, g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
-                      R->row_w.as<double>(), kGhostRowMax, g, R->K.overflow, s);
+    launch_ghost_rows(R->list, 0, nullptr, nullptr, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
+                      R->row_w.as<double>(), kGhostRowMax, R->g, R->K.overflow, s, R->counts_dev, R->cap, R->cap_g);
     CKL("finalize");
+    return WRC_OK;
+}
+
+void rebuild_commit(wrc_run* R) {
     std::swap(R->act, R->nxt);
-    R->cur = nc;
-    R->n_active = na;
-    R->n_ghost = ng;
+    R->cur = 1 - R->cur;
+    R->n_active = R->pend_na;
+    R->n_ghost = R->pend_ng;
     R->frozen = false;
+}
+
+// Run a phase: replay its CUDA graph for the current parity, capturing it
+// first when missing or stale; without graphs (legacy default stream) issue
+// the launches directly.
+template <typename F>
+wrc_status run_phase(wrc_run* R, int phase, F&& body) {
+    if (!R->use_graphs) return body();
+    auto& G = R->graphs[phase][R->cur];
+    if (!G.exec || G.layout != R->layout) {
+        if (G.exec) {
+            cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
+        CK(cudaStreamBeginCapture(R->st, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
+        g_captured = 0;
+        const wrc_status st = body();
+        g_capturing = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(R->st, &graph);
+        if (st != WRC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CK(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+        G.layout = R->layout;
+        G.kernels = g_captured;
+    }
+    CK(cudaGraphLaunch(G.exec, R->st));
+    g_launches.fetch_add(G.kernels, std::memory_order_relaxed);
     return WRC_OK;
 }
 
 // Thresholding with eps: details of the values in L on the current grid (or
 // on every lattice point for a freshly sampled field), significance and
-// adjacent zone into nxt, closure, then the rebuild.
+// adjacent zone into nxt, closure; then the rebuild.
 template <typename T>
-wrc_status threshold_current(wrc_run* R, double eps, bool whole_lattice) {
+wrc_status threshold_body(wrc_run* R, double eps, bool whole_lattice) {
     const Geom& g = R->g;
     const cudaStream_t s = R->st;
     CK(cudaMemsetAsync(R->sig, 0, R->N, s));
     CK(cudaMemsetAsync(R->nxt, 0, R->N, s));
-    if (whole_lattice) {
+    if (whole_lattice)
         launch_details_adj<T>(nullptr, R->N, (const T*)R->L, eps, nullptr, R->sig, R->nxt, g, s);
-        R->det_count = 0;
-    } else {
-        launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->n_active, (const T*)R->L, eps, R->det.as<T>(),
-                              R->sig, R->nxt, g, s);
-        R->det_count = R->n_active;
-    }
+    else
+        launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, (const T*)R->L, eps, R->det.as<T>(), R->sig,
+                              R->nxt, g, s, R->counts_dev);
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
     CKL("threshold");
-    return rebuild_from_mask<T>(R);
+    return rebuild_part1(R);
+}
+
+template <typename T>
+wrc_status rebuild_from_mask(wrc_run* R) {
+    TRY(rebuild_part1(R));
+    TRY(rebuild_host(R));
+    TRY(rebuild_part2<T>(R));
+    rebuild_commit(R);
+    return WRC_OK;
+}
+
+template <typename T>
+wrc_status threshold_current(wrc_run* R, double eps, bool whole_lattice) {
+    TRY(threshold_body<T>(R, eps, whole_lattice));
+    R->det_count = whole_lattice ? 0 : R->n_active;
+    TRY(rebuild_host(R));
+    TRY(rebuild_part2<T>(R));
+    rebuild_commit(R);
+    return WRC_OK;
 }
 
 // L <- R(omega): the grid values, then coarse-to-fine prediction elsewhere.
 template <typename T>
 wrc_status reconstruct(wrc_run* R) {
-    launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->n_active, (T*)R->L, R->st);
+    launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->cap, (T*)R->L, R->st,
+                      R->counts_dev);
     for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
     CKL("reconstruct");
     return WRC_OK;
@@ -310,18 +402,21 @@ wrc_status freeze(wrc_run* R) {
         T* S12 = t3;
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, (T*)R->Lq, t0, scr,
                           dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr);
-        launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->n_active, R->Ua.as<T>(), R->Va.as<T>(), s);
+        launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), s, R->counts_dev);
         if (dyn)
-            launch_sgs_from_strain<T>(S11, S12, meta, R->n_active, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s);
+            launch_sgs_from_strain<T>(S11, S12, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s,
+                                      R->counts_dev);
         CKL("freeze");
         R->frozen = true;
         return WRC_OK;
     } else {
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s);
-        launch_velocity_active<T>((const T*)R->psi, meta, R->n_active, R->Ua.as<T>(), R->Va.as<T>(), R->g, s);
+        launch_velocity_active<T>((const T*)R->psi, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), R->g, s,
+                                  R->counts_dev);
     }
     if (R->cfg.sgs == WRC_SGS_DYNAMIC)
-        launch_sgs<T>((const T*)R->psi, meta, R->n_active, R->cfg.cs, R->ga.as<T>(), t0, t1, t2, t3, R->g, s, Ulat);
+        launch_sgs<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t0, t1, t2, t3, R->g, s, Ulat,
+                      R->counts_dev);
     CKL("freeze");
     R->frozen = true;
     return WRC_OK;
@@ -419,13 +514,24 @@ wrc_status krylov(wrc_run* R) {
     return WRC_OK;
 }
 
+enum { kPhaseFreeze = 0, kPhaseAdapt1 = 1, kPhaseAdapt2 = 2 };
+
+// One time step: [freeze] -> Krylov launch -> [adapt part 1] -> host sync for
+// the new grid's sizes -> [adapt part 2]; bracketed phases run as CUDA graphs.
 template <typename T>
 wrc_status step_once(wrc_run* R) {
-    TRY(freeze<T>(R));
+    TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
+    R->frozen = true;
     TRY(krylov<T>(R));
-    // adaptation: L holds omega^{n+1} at the grid points; reconstruct the rest
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
-    TRY(threshold_current<T>(R, R->cfg.eps, false));
+    TRY(run_phase(R, kPhaseAdapt1, [&] {
+        // L holds omega^{n+1} at the grid points; reconstruct the rest, threshold
+        for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
+        return threshold_body<T>(R, R->cfg.eps, false);
+    }));
+    R->det_count = R->n_active;
+    TRY(rebuild_host(R));
+    TRY(run_phase(R, kPhaseAdapt2, [&] { return rebuild_part2<T>(R); }));
+    rebuild_commit(R);
     R->t += R->cfg.dt;
     R->nstep += 1;
     return WRC_OK;
@@ -595,6 +701,9 @@ void free_run(wrc_run* R) {
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
     for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
+    for (auto& ph : R->graphs)
+        for (auto& G : ph)
+            if (G.exec) cudaGraphExecDestroy(G.exec);
     poisson_plan_free(R->plan);
     delete R;
 }
@@ -690,6 +799,12 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     R->K.counter = (unsigned*)(R->K.kstop + 6);
     cudaMemsetAsync(R->K.kstop, 0, sizeof(int) * 8, R->st);
     cudaMemsetAsync(R->flag_dev, 0, sizeof(int) * 4, R->st);
+    R->use_graphs = R->st != nullptr;   // stream capture needs a non-legacy stream
+    if (R->fp32 && !lattice_scratch(R)) {
+        g_create_error = "lattice scratch allocation failed";
+        free_run(R);
+        return WRC_ERR_OOM;
+    }
     if (poisson_plan_init(R->plan, R->g, R->fp32, R->st) != 0) {
         g_create_error = "FFT/expm kernel set-up failed";
         free_run(R);
@@ -754,6 +869,7 @@ wrc_status wrc_threshold(wrc_run* R, double eps) {
     TRY(check_ready(R));
     if (!(eps >= 0)) return fail(R, WRC_ERR_ARG, "eps must be >= 0");
     R->cfg.eps = eps;
+    R->layout += 1;   // eps is baked into the captured thresholding phase
     return DISPATCH(R, threshold_t, R, eps);
 }
 

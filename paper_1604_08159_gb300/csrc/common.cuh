@@ -128,6 +128,11 @@ __host__ __device__ __forceinline__ int meta_pos(uint32_t m) { return (int)(m & 
 __host__ __device__ __forceinline__ int meta_jx(uint32_t m) { return (int)((m >> 24) & 15u); }
 __host__ __device__ __forceinline__ int meta_jy(uint32_t m) { return (int)(m >> 28); }
 
+// Effective item count of a launch: from device memory when dn is given (the
+// launch then covers a capacity n >= *dn with a grid-stride loop, so it can
+// be captured in a CUDA graph), else n.
+__device__ __forceinline__ long long eff_n(const int* dn, long long n) { return dn ? (long long)*dn : n; }
+
 // Process-wide count of kernel launches made by the library (host side).
 void note_launch();
 long long launches_total();

@@ -36,7 +36,8 @@ __device__ __forceinline__ T dy2(const T* F, int i, int k, const Geom& g, T c2) 
 
 template <typename T>
 __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __restrict__ meta, long long n,
-                                  T* __restrict__ Ua, T* __restrict__ Va, Geom g, T c1) {
+                                  T* __restrict__ Ua, T* __restrict__ Va, Geom g, T c1, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const int p = meta_pos(meta[a]);
@@ -76,7 +77,8 @@ __global__ void k_strain_nut(const T* __restrict__ S11, const T* __restrict__ S1
 template <typename T>
 __global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restrict__ Vlat,
                                   const uint32_t* __restrict__ meta, long long n, T* __restrict__ Ua,
-                                  T* __restrict__ Va) {
+                                  T* __restrict__ Va, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const int p = meta_pos(meta[a]);
@@ -117,7 +119,8 @@ __global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c
 // Pass 4 at the active points: g = Dxx(t2) - Dyy(t2) - 4 Dx(t0).
 template <typename T>
 __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const uint32_t* __restrict__ meta,
-                       long long n, T* __restrict__ ga, Geom g, T c1, T c2) {
+                       long long n, T* __restrict__ ga, Geom g, T c1, T c2, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const int p = meta_pos(meta[a]);
@@ -222,31 +225,31 @@ __global__ void __launch_bounds__(kThreads) k_diag(const T* __restrict__ R, cons
 
 template <typename T>
 void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va, const Geom& g,
-                            cudaStream_t s) {
-    if (n > 0) { k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h))); note_launch(); }
+                            cudaStream_t s, const int* dn) {
+    if (n > 0) { k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h)), dn); note_launch(); }
 }
 
 template <typename T>
 void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1, T* t2, T* t3,
-                const Geom& g, cudaStream_t s, const T* Ulat) {
+                const Geom& g, cudaStream_t s, const T* Ulat, const int* dn) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
     { k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Ulat ? nullptr : t0, t1, g, c1, c2); note_launch(); }
     { k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(Ulat ? Ulat : t0, t1, t2, t3, g, c1, csh2); note_launch(); }
     { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1); note_launch(); }
-    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2); note_launch(); }
+    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
 template <typename T>
 void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
-                            T* tc, T* tdyc, const Geom& g, cudaStream_t s) {
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
     { k_strain_nut<T><<<blocks_for(N), kThreads, 0, s>>>(S11, S12, nullptr, ta, tc, N, csh2); note_launch(); }
     { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(tc, tdyc, g, c1); note_launch(); }
-    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(ta, tdyc, meta, n, ga, g, c1, c2); note_launch(); }
+    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(ta, tdyc, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
 template <typename T>
@@ -258,8 +261,8 @@ void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const
 
 template <typename T>
 void launch_velocity_gather(const T* Ulat, const T* Vlat, const uint32_t* meta, long long n, T* Ua, T* Va,
-                            cudaStream_t s) {
-    if (n > 0) { k_velocity_gather<T><<<blocks_for(n), kThreads, 0, s>>>(Ulat, Vlat, meta, n, Ua, Va); note_launch(); }
+                            cudaStream_t s, const int* dn) {
+    if (n > 0) { k_velocity_gather<T><<<blocks_for(n), kThreads, 0, s>>>(Ulat, Vlat, meta, n, Ua, Va, dn); note_launch(); }
 }
 
 template <typename T>
@@ -304,13 +307,13 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
 
 #define WRC_INST(T)                                                                                          \
     template void launch_velocity_active<T>(const T*, const uint32_t*, long long, T*, T*, const Geom&,      \
-                                            cudaStream_t);                                                  \
+                                            cudaStream_t, const int*);                                      \
     template void launch_sgs<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, T*, T*,           \
-                                const Geom&, cudaStream_t, const T*);                                       \
+                                const Geom&, cudaStream_t, const T*, const int*);                           \
     template void launch_velocity_gather<T>(const T*, const T*, const uint32_t*, long long, T*, T*,         \
-                                            cudaStream_t);                                                  \
+                                            cudaStream_t, const int*);                                      \
     template void launch_sgs_from_strain<T>(const T*, const T*, const uint32_t*, long long, double, T*, T*, \
-                                            T*, T*, const Geom&, cudaStream_t);                             \
+                                            T*, T*, const Geom&, cudaStream_t, const int*);                 \
     template void launch_nut_from_strain<T>(const T*, const T*, T*, double, const Geom&, cudaStream_t);     \
     template void launch_lattice_uv_nut<T>(const T*, T*, T*, T*, double, T*, const Geom&, cudaStream_t,     \
                                            bool);                                                           \

@@ -32,7 +32,8 @@ __global__ void k_init_vortices(T* __restrict__ L, const double* __restrict__ pr
 
 template <typename T>
 __global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict__ vals, long long n,
-                          T* __restrict__ L) {
+                          T* __restrict__ L, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x)
         L[meta_pos(meta[a])] = vals[a];
@@ -60,7 +61,8 @@ __global__ void k_recon_level(T* __restrict__ L, const uint8_t* __restrict__ act
 template <typename T>
 __global__ void k_details_adj(const uint32_t* __restrict__ meta, long long n, const T* __restrict__ L,
                               double eps, T* __restrict__ det, uint8_t* __restrict__ sig,
-                              uint8_t* __restrict__ nxt, Geom g) {
+                              uint8_t* __restrict__ nxt, Geom g, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const long long p = meta ? (long long)meta_pos(meta[a]) : a;
@@ -303,7 +305,9 @@ __global__ void k_compact_scatter(const uint8_t* __restrict__ act, const uint8_t
 
 template <typename T>
 __global__ void k_finalize(const int* __restrict__ list, long long n, const uint8_t* __restrict__ JJ,
-                           const T* __restrict__ L, uint32_t* __restrict__ meta, T* __restrict__ omega) {
+                           const T* __restrict__ L, uint32_t* __restrict__ meta, T* __restrict__ omega,
+                           const int* __restrict__ dn) {
+    n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const int p = list[a];
@@ -362,7 +366,12 @@ __global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, in
 
 // Index of every grid point in the combined numbering: active points
 // 0..n_a-1, then the ghosts n_a.. in list order.
-__global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __restrict__ lat2idx) {
+__global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __restrict__ lat2idx,
+                          const int* __restrict__ dcounts, int nkeys) {
+    if (dcounts) {
+        n = 0;
+        for (int q = 0; q < nkeys; ++q) n += dcounts[q];
+    }
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
         lat2idx[list[t]] = (int)t;
@@ -377,8 +386,18 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
 __global__ void k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act,
                                    long long n_tot, const int* __restrict__ lat2idx, int* __restrict__ row_len,
                                    int* __restrict__ row_idx, double* __restrict__ row_w, int rmax, int j, Geom g,
-                                   int* __restrict__ overflow) {
+                                   int* __restrict__ overflow, const int* __restrict__ dcounts, int nkeys) {
     constexpr int kCap = 64;
+    if (dcounts) {   // key 0: active points, key l: ghosts of level l
+        n_act = dcounts[0];
+        gbeg = 0;
+        n_tot = 0;
+        for (int q = 0; q < nkeys; ++q) {
+            if (q < j) gbeg += dcounts[q];
+            n_tot += dcounts[q];
+        }
+        cnt = dcounts[j];
+    }
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
          t += (long long)gridDim.x * blockDim.x) {
         const long long gi = gbeg - n_act + t;          // ghost number
@@ -442,8 +461,8 @@ void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cuda
     { k_init_vortices<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(L, params, n, g); note_launch(); }
 }
 template <typename T>
-void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s) {
-    if (n > 0) { k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L); note_launch(); }
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn) {
+    if (n > 0) { k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L, dn); note_launch(); }
 }
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
@@ -451,8 +470,8 @@ void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStre
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
-                        uint8_t* nxt, const Geom& g, cudaStream_t s) {
-    if (n > 0) { k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g); note_launch(); }
+                        uint8_t* nxt, const Geom& g, cudaStream_t s, const int* dn) {
+    if (n > 0) { k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g, dn); note_launch(); }
 }
 void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s) {
     { k_closure_level<<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(mask, excl, j, g); note_launch(); }
@@ -473,8 +492,8 @@ void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int n
 }
 template <typename T>
 void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
-                     cudaStream_t s) {
-    if (n > 0) { k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega); note_launch(); }
+                     cudaStream_t s, const int* dn) {
+    if (n > 0) { k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega, dn); note_launch(); }
 }
 template <typename T>
 void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop, int jstep,
@@ -493,14 +512,25 @@ void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream
 }
 void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
                        int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
-                       int* overflow, cudaStream_t s) {
+                       int* overflow, cudaStream_t s, const int* dcounts, long long cap_a, long long cap_g) {
+    if (dcounts) {
+        // sizes on the device, grids over the capacities (capturable)
+        { k_lat2idx<<<blocks_for(cap_a + cap_g), kThreads, 0, s>>>(list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
+        for (int j = 1; j <= J; ++j) {
+            k_ghost_rows_level<<<blocks_for(cap_g, 128), 128, 0, s>>>(list, 0, 0, 0, 0, lat2idx, row_len, row_idx,
+                                                                     row_w, rmax, j, g, overflow, dcounts, J + 1);
+            note_launch();
+        }
+        return;
+    }
     long long tot = n_act;
     for (int j = 1; j <= J; ++j) tot += gcnt[j];
-    if (tot > 0) { k_lat2idx<<<blocks_for(tot), kThreads, 0, s>>>(list, tot, lat2idx); note_launch(); }
+    if (tot > 0) { k_lat2idx<<<blocks_for(tot), kThreads, 0, s>>>(list, tot, lat2idx, nullptr, 0); note_launch(); }
     for (int j = 1; j <= J; ++j)
         if (gcnt[j] > 0) {
-            k_ghost_rows_level<<<blocks_for(gcnt[j], 128), 128, 0, s>>>(list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len,
-                                                                      row_idx, row_w, rmax, j, g, overflow);
+            k_ghost_rows_level<<<blocks_for(gcnt[j], 128), 128, 0, s>>>(list, goff[j], gcnt[j], n_act, tot, lat2idx,
+                                                                      row_len, row_idx, row_w, rmax, j, g, overflow,
+                                                                      nullptr, 0);
             note_launch();
         }
 }
@@ -510,12 +540,12 @@ void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx
 
 #define WRC_INST(T)                                                                                       \
     template void launch_init_vortices<T>(T*, const double*, int, const Geom&, cudaStream_t);             \
-    template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t);              \
+    template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t, const int*);  \
     template void launch_recon_level<T>(T*, const uint8_t*, int, const Geom&, cudaStream_t);              \
     template void launch_details_adj<T>(const uint32_t*, long long, const T*, double, T*, uint8_t*,       \
-                                        uint8_t*, const Geom&, cudaStream_t);                             \
+                                        uint8_t*, const Geom&, cudaStream_t, const int*);                 \
     template void launch_finalize<T>(const int*, long long, const uint8_t*, const T*, uint32_t*, T*,      \
-                                     cudaStream_t);                                                       \
+                                     cudaStream_t, const int*);                                           \
     template void launch_ghost_fill<T>(T*, const int*, long long, int, const Geom&, const int*, int,      \
                                        cudaStream_t);
 WRC_INST(double)

@@ -8,13 +8,15 @@ namespace wrc {
 // ---- grid.cu: lattice, transform, thresholding, index sets -----------------
 template <typename T>
 void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s);
+// Launchers taking `dn` read the item count from device memory when it is
+// given (n is then the capacity the grid covers; capturable in a CUDA graph).
 template <typename T>
-void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s);
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn = nullptr);
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s);
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det,
-                        uint8_t* sig, uint8_t* nxt, const Geom& g, cudaStream_t s);
+                        uint8_t* sig, uint8_t* nxt, const Geom& g, cudaStream_t s, const int* dn = nullptr);
 void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s);
 void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s);
 void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s);
@@ -22,7 +24,7 @@ void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int n
                     int* blk_off, int* counts, int* list, cudaStream_t s);
 template <typename T>
 void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* dn = nullptr);
 template <typename T>
 void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop,
                        int jstep, cudaStream_t s);
@@ -35,9 +37,12 @@ void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx
 // Interpolation rows of all ghosts (levels 1..J; ghosts of level j at
 // list[goff[j] ..]) over the active points, and the combined index map.
 constexpr int kGhostRowMax = 64;
+// With dcounts (the compaction's per-key counts on the device), all sizes are
+// read on the device and the grids cover cap_a + cap_g items.
 void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
                        int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
-                       int* overflow, cudaStream_t s);
+                       int* overflow, cudaStream_t s, const int* dcounts = nullptr, long long cap_a = 0,
+                       long long cap_g = 0);
 
 // ---- fft.cu: streamfunction -------------------------------------------------
 struct PoissonPlan {
@@ -62,22 +67,22 @@ void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1, void* C2
 // ---- flow.cu: velocity, Smagorinsky forcing, operator, diagnostics ----------
 template <typename T>
 void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va,
-                            const Geom& g, cudaStream_t s);
+                            const Geom& g, cudaStream_t s, const int* dn = nullptr);
 // Smagorinsky forcing at the active points; Ulat (optional) is U = dpsi/dy on
 // the lattice, otherwise computed from psi by the stencil.
 template <typename T>
 void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1,
-                T* t2, T* t3, const Geom& g, cudaStream_t s, const T* Ulat = nullptr);
+                T* t2, T* t3, const Geom& g, cudaStream_t s, const T* Ulat = nullptr, const int* dn = nullptr);
 // Smagorinsky forcing from the lattice strain (S11, S12): nu_t, then
 // a = 2 nu_t S12 and c = nu_t S11 into ta, tc, D_y c into tdyc, g at the active points.
 template <typename T>
 void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
-                            T* tc, T* tdyc, const Geom& g, cudaStream_t s);
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn = nullptr);
 template <typename T>
 void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s);
 template <typename T>
 void launch_velocity_gather(const T* Ulat, const T* Vlat, const uint32_t* meta, long long n, T* Ua, T* Va,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* dn = nullptr);
 template <typename T>
 void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, const Geom& g,
                            cudaStream_t s, bool uv_given = false);

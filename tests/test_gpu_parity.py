@@ -252,3 +252,25 @@ def test_4096_lattice_grid_and_streamfunction():
         R = O.reconstruct(st.omega, st.active, cfg.J)
         ref = O.streamfunction(R, cfg.h)
         assert np.abs(psi - ref).max() <= OP_TOL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_MIXED])
+def test_graph_replayed_steps_bit_identical_to_direct_launches(prec):
+    """On a non-default stream the step phases run as captured CUDA graphs
+    (re-captured when buffers grow); the results must be bit-identical to
+    the directly launched run, since the kernels and their order are the same
+    and every reduction is deterministic."""
+    import torch
+    p = W.RunParams(**{**W.fujiwhara_small().params.as_dict(), "prec": prec,
+                       "sgs": W.SGS_DYNAMIC, "cs": 0.17})
+    v = W.fujiwhara_small().vortices
+    outs = []
+    for use_stream in (False, True):
+        stream = torch.cuda.Stream() if use_stream else None
+        with B.Run(p, stream=stream.cuda_stream if stream else None) as run:
+            run.init_vortices(v)
+            run.step(6)
+            run.sync()
+            outs.append(run.active())
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
