@@ -203,6 +203,58 @@ const char* wrc_last_error(const wrc_run* run);
 /* Release the run's device memory (synchronises its stream first). */
 void wrc_destroy(wrc_run* run);
 
+/* ---- Batched ensemble ------------------------------------------------------
+ * Uneven members (different lattices, parameters and initial conditions;
+ * one precision for all) advanced together.  Each step runs the members'
+ * reconstruction, streamfunction and adaptation phases as captured CUDA
+ * graphs spread over eight member streams, and the Krylov part of all members
+ * in ONE cooperative launch whose blocks are shared out in proportion to the
+ * members' active counts (a member's partial sums, barrier and breakdown
+ * decisions are its own).  The path of a member is the single-run path
+ * (Sec. 2.1-2.5 as in wrc_step); only the block decomposition of its
+ * reductions differs, so a member's result equals its solo run to rounding.
+ * There is one host synchronisation per ensemble step. */
+typedef struct wrc_ensemble wrc_ensemble;
+
+/* Create n members from cfgs[0..n) (all with the same prec) on the current
+ * device; the batched launch runs on cuda_stream (NULL = legacy default
+ * stream; member phases always run on the ensemble's own streams).  Errors
+ * as wrc_create; wrc_ensemble_last_error(NULL) explains a failed create. */
+wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_stream, wrc_ensemble** out);
+
+/* The run handle of a member, for initial conditions (wrc_init_vortices,
+ * wrc_init_field, wrc_set_grid) and every query.  Owned by the ensemble: do
+ * not destroy it and do not call wrc_step on it while the ensemble is used. */
+wrc_status wrc_ensemble_member(wrc_ensemble* e, int32_t member, wrc_run** run);
+
+/* Advance every member nsteps steps (all members need an initial condition). */
+wrc_status wrc_ensemble_step(wrc_ensemble* e, int32_t nsteps);
+
+/* Block shape of the batched Krylov kernel: threads per block (64, 128 or
+ * 256) and target active points per thread (1..64). */
+wrc_status wrc_ensemble_set_shape(wrc_ensemble* e, int32_t threads_per_block, int32_t points_per_thread);
+
+/* Autotuner: time the batched Krylov launch over steps_per_candidate real
+ * steps for each of the 9 shapes {64,128,256} x {1,2,4}, keep the fastest and
+ * cache it for this process per (precision, member-count bucket,
+ * active-count bucket); a cached choice is applied without stepping.  The
+ * chosen shape is written to out_shape[0..1] (may be NULL). */
+wrc_status wrc_ensemble_tune(wrc_ensemble* e, int32_t steps_per_candidate, int32_t out_shape[2]);
+
+/* out[0] members, out[1] total active points, out[2] ensemble steps taken,
+ * out[3] blocks of the last batched launch, out[4..5] the block shape. */
+wrc_status wrc_ensemble_stats(wrc_ensemble* e, int64_t out[6]);
+
+/* Event timing of the batched Krylov launches: returns in *ms (may be NULL)
+ * the device time recorded since the last call and clears it; enable != 0
+ * keeps recording. */
+wrc_status wrc_ensemble_profile(wrc_ensemble* e, int32_t enable, double* ms);
+
+const char* wrc_ensemble_last_error(const wrc_ensemble* e);
+
+/* Destroy the members and the ensemble (synchronises). */
+void wrc_ensemble_destroy(wrc_ensemble* e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,15 @@ SIGNATURES = {
     "wrc_query_profile": (c_int32, [c_void_p, c_void_p]),
     "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_destroy": (None, [c_void_p]),
+    "wrc_ensemble_create": (c_int32, [c_int32, c_void_p, c_void_p, POINTER(c_void_p)]),
+    "wrc_ensemble_member": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
+    "wrc_ensemble_step": (c_int32, [c_void_p, c_int32]),
+    "wrc_ensemble_set_shape": (c_int32, [c_void_p, c_int32, c_int32]),
+    "wrc_ensemble_tune": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "wrc_ensemble_stats": (c_int32, [c_void_p, c_void_p]),
+    "wrc_ensemble_profile": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "wrc_ensemble_last_error": (ctypes.c_char_p, [c_void_p]),
+    "wrc_ensemble_destroy": (None, [c_void_p]),
 }
 
 _lib = None
@@ -345,3 +354,122 @@ class Run:
 
     def profile_record(self):
         return wrc_query_profile(self.h)
+
+
+# ---- batched ensemble ------------------------------------------------------------
+
+def _echeck(fn: str, st: int, ens=None):
+    if st != WRC_OK:
+        msg = load().wrc_ensemble_last_error(ens)
+        raise WrcError(fn, st, msg.decode() if msg else "")
+
+
+def wrc_ensemble_create(cfgs, stream: int | None = None) -> int:
+    arr = (WrcConfig * len(cfgs))(*cfgs)
+    h = c_void_p()
+    _echeck("wrc_ensemble_create", load().wrc_ensemble_create(len(cfgs), arr, c_void_p(stream or 0), byref(h)))
+    return h.value
+
+
+def wrc_ensemble_member(ens, member: int) -> int:
+    h = c_void_p()
+    _echeck("wrc_ensemble_member", load().wrc_ensemble_member(ens, member, byref(h)), ens)
+    return h.value
+
+
+def wrc_ensemble_step(ens, nsteps: int = 1):
+    _echeck("wrc_ensemble_step", load().wrc_ensemble_step(ens, nsteps), ens)
+
+
+def wrc_ensemble_set_shape(ens, threads_per_block: int, points_per_thread: int):
+    _echeck("wrc_ensemble_set_shape", load().wrc_ensemble_set_shape(ens, threads_per_block, points_per_thread), ens)
+
+
+def wrc_ensemble_tune(ens, steps_per_candidate: int = 1):
+    out = np.zeros(2, dtype=np.int32)
+    _echeck("wrc_ensemble_tune", load().wrc_ensemble_tune(ens, steps_per_candidate, out.ctypes.data), ens)
+    return int(out[0]), int(out[1])
+
+
+def wrc_ensemble_stats(ens):
+    out = np.zeros(6, dtype=np.int64)
+    _echeck("wrc_ensemble_stats", load().wrc_ensemble_stats(ens, out.ctypes.data), ens)
+    keys = ("members", "n_active", "steps", "blocks", "threads_per_block", "points_per_thread")
+    return dict(zip(keys, (int(x) for x in out)))
+
+
+def wrc_ensemble_profile(ens, enable: bool):
+    ms = c_double()
+    _echeck("wrc_ensemble_profile", load().wrc_ensemble_profile(ens, 1 if enable else 0, byref(ms)), ens)
+    return ms.value
+
+
+def wrc_ensemble_last_error(ens) -> str:
+    m = load().wrc_ensemble_last_error(ens)
+    return m.decode() if m else ""
+
+
+def wrc_ensemble_destroy(ens):
+    if ens:
+        load().wrc_ensemble_destroy(ens)
+
+
+class Member(Run):
+    """A member of an Ensemble: the Run interface on a borrowed handle."""
+
+    def __init__(self, params, handle):
+        self.params = params
+        self.NJ = params.n0 << params.J
+        self.J = params.J
+        self.m = params.m
+        self.h = handle
+
+    def close(self):
+        self.h = None          # owned by the ensemble
+
+
+class Ensemble:
+    """Members advanced together (one batched Krylov launch per step)."""
+
+    def __init__(self, params_list, stream: int | None = None):
+        self.params = list(params_list)
+        self.h = wrc_ensemble_create([make_config(p) for p in self.params], stream)
+        self.members = [Member(p, wrc_ensemble_member(self.h, i)) for i, p in enumerate(self.params)]
+
+    def step(self, n=1):
+        wrc_ensemble_step(self.h, n)
+
+    def tune(self, steps_per_candidate=1):
+        return wrc_ensemble_tune(self.h, steps_per_candidate)
+
+    def set_shape(self, threads_per_block, points_per_thread):
+        wrc_ensemble_set_shape(self.h, threads_per_block, points_per_thread)
+
+    def stats(self):
+        return wrc_ensemble_stats(self.h)
+
+    def profile(self, enable=True):
+        return wrc_ensemble_profile(self.h, enable)
+
+    def sync(self):
+        for m in self.members:
+            m.sync()
+
+    def close(self):
+        if self.h:
+            for m in self.members:
+                m.close()
+            wrc_ensemble_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

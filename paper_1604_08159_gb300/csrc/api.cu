@@ -1,8 +1,12 @@
 // C ABI (include/wrc.h): run state on the device and the orchestration of one
 // time step -- reconstruction, streamfunction, velocity and Smagorinsky
 // forcing, Krylov projection with the phi_1 update, grid adaptation.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <vector>
 #include <cstring>
@@ -36,26 +40,36 @@ constexpr double kBreakdownTol = 1e-12;
 
 thread_local std::string g_create_error;
 
-// Growable device buffer on the stream-ordered allocator.
+// Growable device buffer.  Plain cudaMalloc/cudaFree (not the stream-ordered
+// allocator, whose reuse of memory freed on another run's stream can put a
+// hidden inter-stream dependency in front of a graph capture); growth is
+// rare, and the free waits for the buffer's stream first.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
     cudaError_t grow(size_t need, size_t keep, cudaStream_t s) {
         if (need <= bytes) return cudaSuccess;
         void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, need, s);
+        cudaError_t e = cudaMalloc(&q, need);
         if (e != cudaSuccess) return e;
         if (p && keep) {
             e = cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
         }
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            cudaFree(p);
+        }
         p = q;
         bytes = need;
         return cudaSuccess;
     }
     void release(cudaStream_t s) {
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            cudaStreamSynchronize(s);
+            cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -306,10 +320,15 @@ wrc_status run_phase(wrc_run* R, int phase, F&& body) {
     auto& G = R->graphs[phase][R->cur];
     if (!G.exec || G.layout != R->layout) {
         if (G.exec) {
+            CK(cudaStreamSynchronize(R->st));   // the stale graph may still be running
             cudaGraphExecDestroy(G.exec);
             G.exec = nullptr;
         }
-        CK(cudaStreamBeginCapture(R->st, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess)
+            return fail(R, WRC_ERR_CUDA, std::string("error pending before capture of phase ") +
+                                             std::to_string(phase) + ": " + cudaGetErrorString(pending));
+        CK(cudaStreamBeginCapture(R->st, cudaStreamCaptureModeRelaxed));
         g_capturing = true;
         g_captured = 0;
         const wrc_status st = body();
@@ -318,6 +337,8 @@ wrc_status run_phase(wrc_run* R, int phase, F&& body) {
         const cudaError_t ec = cudaStreamEndCapture(R->st, &graph);
         if (st != WRC_OK) {
             if (graph) cudaGraphDestroy(graph);
+            R->err = "capture of phase " + std::to_string(phase) + " (parity " + std::to_string(R->cur) +
+                     "): " + R->err + " / end capture: " + cudaGetErrorString(ec);
             return st;
         }
         CK(ec);
@@ -375,6 +396,7 @@ template <typename T>
 wrc_status reconstruct(wrc_run* R) {
     launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->cap, (T*)R->L, R->st,
                       R->counts_dev);
+    CKL("reconstruct/scatter");
     for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
     CKL("reconstruct");
     return WRC_OK;
@@ -384,6 +406,7 @@ wrc_status reconstruct(wrc_run* R) {
 template <typename T>
 wrc_status freeze(wrc_run* R) {
     TRY(reconstruct<T>(R));
+    CKL("freeze/reconstruct");
     const cudaStream_t s = R->st;
     const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
     T* t0 = (T*)R->C1;
@@ -402,7 +425,9 @@ wrc_status freeze(wrc_run* R) {
         T* S12 = t3;
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, (T*)R->Lq, t0, scr,
                           dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr);
+        CKL("freeze/poisson");
         launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), s, R->counts_dev);
+        CKL("freeze/velocity");
         if (dyn)
             launch_sgs_from_strain<T>(S11, S12, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s,
                                       R->counts_dev);
@@ -449,11 +474,8 @@ double krylov_algorithmic_flops(long long n, int k) {
     return f * (double)n;
 }
 
-// Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
-// one cooperative launch.
-template <typename T>
-wrc_status krylov(wrc_run* R) {
-    const cudaStream_t s = R->st;
+// Arguments of the Krylov step of run R (its current grid and buffers).
+KrylovStepArgs krylov_args(wrc_run* R) {
     const long long n = R->n_active;
     const int m = R->cfg.krylov_m;
     KrylovStepArgs A{};
@@ -494,8 +516,18 @@ wrc_status krylov(wrc_run* R) {
     A.dt = R->cfg.dt;
     A.tol = kBreakdownTol;
     A.limit_ns = 2000000000ull;
+    return A;
+}
+
+// Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
+// one cooperative launch.
+template <typename T>
+wrc_status krylov(wrc_run* R) {
+    const cudaStream_t s = R->st;
+    const long long n = R->n_active;
+    const int m = R->cfg.krylov_m;
+    const KrylovStepArgs A = krylov_args(R);
     const int blocks = krylov_step_blocks(n, R->max_blocks);
-    CK(cudaMemsetAsync(R->K.H, 0, sizeof(double) * (m + 1) * m, s));
     int e0 = -1;
     if (R->profiling) {
         while (R->ev_pool.size() < R->ev_used.size() * 2 + 2) {
@@ -1060,5 +1092,391 @@ wrc_status wrc_query_profile(wrc_run* R, double out[4]) {
 const char* wrc_last_error(const wrc_run* R) { return R ? R->err.c_str() : g_create_error.c_str(); }
 
 void wrc_destroy(wrc_run* R) { free_run(R); }
+
+}  // extern "C"
+
+// ============================================================================
+// Batched ensemble (uneven members in one cooperative Krylov launch per step)
+// ============================================================================
+
+struct wrc_ensemble {
+    std::vector<wrc_run*> members;
+    cudaStream_t main = nullptr;             // the caller's stream (the batched launch)
+    bool own_main = false;                   // created here when the caller passed NULL
+    std::vector<cudaStream_t> streams;       // member streams (owned)
+    std::vector<cudaEvent_t> ev_streams;     // one per member stream
+    cudaEvent_t ev_main = nullptr;
+    bool fp32 = false;
+    int pt = 128;                            // threads per block of the batched kernel
+    int ept = 1;                             // target active points per thread
+    KrylovStepArgs* h_args = nullptr;        // pinned
+    int* h_blk = nullptr;                    // pinned: block -> member, then member block offsets
+    KrylovStepArgs* d_args = nullptr;
+    int* d_blk = nullptr;
+    int blk_cap = 0;
+    int last_blocks = 0;
+    long long nstep = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_ens_create_error;
+constexpr int kEnsStreams = 8;
+
+wrc_status efail(wrc_ensemble* E, wrc_status s, const std::string& msg) {
+    if (E) E->err = msg;
+    return s;
+}
+
+#define ECK(call)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return efail(E, e_ == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA,       \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+// Member failures are reported with the member's index and message.
+wrc_status member_fail(wrc_ensemble* E, size_t i, wrc_status st) {
+    return efail(E, st, "member " + std::to_string(i) + ": " + E->members[i]->err);
+}
+
+// Block plan: member i gets ceil(n_i / (pt * ept)) blocks, clamped to
+// [1, its partial-sum capacity]; if the total exceeds what can be co-resident,
+// every member's share is scaled down (keeping at least one block each).
+wrc_status plan_batch(wrc_ensemble* E, int max_coresident, int& total) {
+    const size_t M = E->members.size();
+    std::vector<int> nb(M);
+    long long sum = 0;
+    for (size_t i = 0; i < M; ++i) {
+        const wrc_run* R = E->members[i];
+        long long b = (R->n_active + (long long)E->pt * E->ept - 1) / ((long long)E->pt * E->ept);
+        b = b < 1 ? 1 : b;
+        b = b > R->max_blocks ? R->max_blocks : b;
+        nb[i] = (int)b;
+        sum += b;
+    }
+    if ((long long)M > max_coresident)
+        return efail(E, WRC_ERR_ARG, "more members than co-resident blocks of the batched kernel");
+    if (sum > max_coresident) {
+        const double f = (double)(max_coresident - (long long)M) / (double)(sum - (long long)M);
+        sum = 0;
+        for (size_t i = 0; i < M; ++i) {
+            nb[i] = 1 + (int)std::floor((nb[i] - 1) * f);
+            sum += nb[i];
+        }
+    }
+    total = (int)sum;
+    if (total + (int)M + 1 > E->blk_cap) {
+        if (E->h_blk) cudaFreeHost(E->h_blk);
+        if (E->d_blk) cudaFree(E->d_blk);
+        E->blk_cap = total + (int)M + 1 + 1024;
+        ECK(cudaMallocHost((void**)&E->h_blk, sizeof(int) * E->blk_cap));
+        ECK(cudaMalloc((void**)&E->d_blk, sizeof(int) * E->blk_cap));
+    }
+    int* blk2mem = E->h_blk;
+    int* b0 = E->h_blk + total;
+    int off = 0;
+    for (size_t i = 0; i < M; ++i) {
+        b0[i] = off;
+        for (int b = 0; b < nb[i]; ++b) blk2mem[off + b] = (int)i;
+        off += nb[i];
+    }
+    b0[M] = off;
+    return WRC_OK;
+}
+
+template <typename T>
+wrc_status ensemble_step_once(wrc_ensemble* E) {
+    const size_t M = E->members.size();
+    const int S = (int)E->streams.size();
+    // phase 1: freeze every member on its stream
+    for (size_t i = 0; i < M; ++i) {
+        wrc_run* R = E->members[i];
+        const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); });
+        if (st != WRC_OK) return member_fail(E, i, st);
+        R->frozen = true;
+    }
+    for (int q = 0; q < S; ++q) {
+        ECK(cudaEventRecord(E->ev_streams[q], E->streams[q]));
+        ECK(cudaStreamWaitEvent(E->main, E->ev_streams[q], 0));
+    }
+    // phase 2: the Krylov step of all members in one cooperative launch
+    const int maxb = krylov_batch_max_blocks(E->fp32, E->pt);
+    if (maxb <= 0) return efail(E, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
+    int total = 0;
+    TRY(plan_batch(E, maxb, total));
+    int max_n = 1;
+    for (size_t i = 0; i < M; ++i) {
+        E->h_args[i] = krylov_args(E->members[i]);
+        max_n = std::max(max_n, (int)E->members[i]->n_active);
+    }
+    ECK(cudaMemcpyAsync(E->d_args, E->h_args, sizeof(KrylovStepArgs) * M, cudaMemcpyHostToDevice, E->main));
+    ECK(cudaMemcpyAsync(E->d_blk, E->h_blk, sizeof(int) * (total + M + 1), cudaMemcpyHostToDevice, E->main));
+    cudaEvent_t pa = nullptr, pb = nullptr;
+    if (E->profiling) {
+        ECK(cudaEventCreate(&pa));
+        ECK(cudaEventCreate(&pb));
+        ECK(cudaEventRecord(pa, E->main));
+    }
+    ECK(launch_krylov_batch<T>(E->d_args, E->d_blk, E->d_blk + total, (int)M, total, E->pt, max_n, E->main));
+    if (E->profiling) {
+        ECK(cudaEventRecord(pb, E->main));
+        E->prof.push_back({pa, pb});
+    }
+    E->last_blocks = total;
+    ECK(cudaEventRecord(E->ev_main, E->main));
+    // phase 3: adaptation part 1 on the member streams
+    for (int q = 0; q < S; ++q) ECK(cudaStreamWaitEvent(E->streams[q], E->ev_main, 0));
+    for (size_t i = 0; i < M; ++i) {
+        wrc_run* R = E->members[i];
+        const wrc_status st = run_phase(R, kPhaseAdapt1, [&] {
+            for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
+            return threshold_body<T>(R, R->cfg.eps, false);
+        });
+        if (st != WRC_OK) return member_fail(E, i, st);
+        R->det_count = R->n_active;
+    }
+    // one wait for all members, then the host part and adaptation part 2
+    for (int q = 0; q < S; ++q) ECK(cudaStreamSynchronize(E->streams[q]));
+    for (size_t i = 0; i < M; ++i) {
+        wrc_run* R = E->members[i];
+        wrc_status st = rebuild_host(R);
+        if (st == WRC_OK) st = run_phase(R, kPhaseAdapt2, [&] { return rebuild_part2<T>(R); });
+        if (st != WRC_OK) return member_fail(E, i, st);
+        rebuild_commit(R);
+        R->t += R->cfg.dt;
+        R->nstep += 1;
+    }
+    // the member streams must not run ahead of the next batched launch's reads
+    for (int q = 0; q < S; ++q) {
+        ECK(cudaEventRecord(E->ev_streams[q], E->streams[q]));
+        ECK(cudaStreamWaitEvent(E->main, E->ev_streams[q], 0));
+    }
+    E->nstep += 1;
+    return WRC_OK;
+}
+
+// Autotuner cache: best (threads per block, points per thread) per precision,
+// member-count bucket and total-active-points bucket, for this process.
+struct TuneKey {
+    bool fp32;
+    int mb, nb;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(fp32, mb, nb) < std::tie(o.fp32, o.mb, o.nb);
+    }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mutex;
+
+int log2_bucket(long long v) {
+    int b = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+TuneKey tune_key(const wrc_ensemble* E) {
+    long long tot = 0;
+    for (const wrc_run* R : E->members) tot += R->n_active;
+    return {E->fp32, log2_bucket((long long)E->members.size()), log2_bucket(tot)};
+}
+
+}  // namespace
+
+extern "C" {
+
+wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_stream, wrc_ensemble** out) {
+    if (!out) return WRC_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !cfgs) {
+        g_ens_create_error = "need at least one member configuration";
+        return WRC_ERR_ARG;
+    }
+    for (int i = 1; i < n; ++i)
+        if (cfgs[i].prec != cfgs[0].prec) {
+            g_ens_create_error = "all members of an ensemble share one precision";
+            return WRC_ERR_ARG;
+        }
+    wrc_ensemble* E = new wrc_ensemble();
+    E->main = (cudaStream_t)cuda_stream;
+    if (!E->main) {   // keep the batched launches off the legacy default stream
+        if (cudaStreamCreateWithFlags(&E->main, cudaStreamNonBlocking) != cudaSuccess) {
+            g_ens_create_error = "stream creation failed";
+            delete E;
+            return WRC_ERR_CUDA;
+        }
+        E->own_main = true;
+    }
+    E->fp32 = cfgs[0].prec == WRC_MIXED;
+    auto cleanup = [&](wrc_status st, const std::string& msg) {
+        g_ens_create_error = msg;
+        wrc_ensemble_destroy(E);
+        return st;
+    };
+    const int S = std::min(kEnsStreams, (int)n);
+    for (int q = 0; q < S; ++q) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(WRC_ERR_CUDA, "stream creation failed");
+        E->streams.push_back(st);
+        E->ev_streams.push_back(ev);
+    }
+    if (cudaEventCreateWithFlags(&E->ev_main, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(WRC_ERR_CUDA, "event creation failed");
+    for (int i = 0; i < n; ++i) {
+        wrc_run* R = nullptr;
+        const wrc_status st = wrc_create(&cfgs[i], E->streams[i % S], &R);
+        if (st != WRC_OK) return cleanup(st, "member " + std::to_string(i) + ": " + g_create_error);
+        E->members.push_back(R);
+    }
+    if (cudaMallocHost((void**)&E->h_args, sizeof(KrylovStepArgs) * n) != cudaSuccess ||
+        cudaMalloc((void**)&E->d_args, sizeof(KrylovStepArgs) * n) != cudaSuccess)
+        return cleanup(WRC_ERR_OOM, "argument table allocation failed");
+    *out = E;
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_member(wrc_ensemble* E, int32_t member, wrc_run** run) {
+    if (!E || !run) return WRC_ERR_ARG;
+    if (member < 0 || member >= (int)E->members.size()) return efail(E, WRC_ERR_ARG, "member index out of range");
+    *run = E->members[member];
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_step(wrc_ensemble* E, int32_t nsteps) {
+    if (!E) return WRC_ERR_ARG;
+    if (nsteps < 0) return efail(E, WRC_ERR_ARG, "nsteps < 0");
+    for (size_t i = 0; i < E->members.size(); ++i)
+        if (!E->members[i]->init) return efail(E, WRC_ERR_STATE, "member " + std::to_string(i) + " has no initial condition");
+    for (int q = 0; q < nsteps; ++q) TRY(E->fp32 ? ensemble_step_once<float>(E) : ensemble_step_once<double>(E));
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_set_shape(wrc_ensemble* E, int32_t threads_per_block, int32_t points_per_thread) {
+    if (!E) return WRC_ERR_ARG;
+    if ((threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256) || points_per_thread < 1 ||
+        points_per_thread > 64)
+        return efail(E, WRC_ERR_ARG, "threads_per_block must be 64, 128 or 256; points_per_thread 1..64");
+    E->pt = threads_per_block;
+    E->ept = points_per_thread;
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_tune(wrc_ensemble* E, int32_t steps_per_candidate, int32_t out_shape[2]) {
+    if (!E) return WRC_ERR_ARG;
+    if (steps_per_candidate < 1) return efail(E, WRC_ERR_ARG, "steps_per_candidate < 1");
+    const TuneKey key = tune_key(E);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            E->pt = it->second.first;
+            E->ept = it->second.second;
+            if (out_shape) {
+                out_shape[0] = E->pt;
+                out_shape[1] = E->ept;
+            }
+            return WRC_OK;
+        }
+    }
+    const int pts[3] = {64, 128, 256};
+    const int epts[3] = {1, 2, 4};
+    double best = 1e300;
+    int bpt = E->pt, bept = E->ept;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            E->pt = pts[a];
+            E->ept = epts[b];
+            E->profiling = true;
+            TRY(wrc_ensemble_step(E, steps_per_candidate));
+            ECK(cudaStreamSynchronize(E->main));
+            double ms = 0.0;
+            for (auto& pe : E->prof) {
+                float t = 0.f;
+                ECK(cudaEventElapsedTime(&t, pe.first, pe.second));
+                ms += t;
+                cudaEventDestroy(pe.first);
+                cudaEventDestroy(pe.second);
+            }
+            E->prof.clear();
+            E->profiling = false;
+            if (ms < best) {
+                best = ms;
+                bpt = pts[a];
+                bept = epts[b];
+            }
+        }
+    E->pt = bpt;
+    E->ept = bept;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = {bpt, bept};
+    }
+    if (out_shape) {
+        out_shape[0] = bpt;
+        out_shape[1] = bept;
+    }
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_stats(wrc_ensemble* E, int64_t out[6]) {
+    if (!E || !out) return WRC_ERR_ARG;
+    long long tot = 0;
+    for (const wrc_run* R : E->members) tot += R->n_active;
+    out[0] = (int64_t)E->members.size();
+    out[1] = tot;
+    out[2] = E->nstep;
+    out[3] = E->last_blocks;
+    out[4] = E->pt;
+    out[5] = E->ept;
+    return WRC_OK;
+}
+
+wrc_status wrc_ensemble_profile(wrc_ensemble* E, int32_t enable, double* ms_out) {
+    if (!E) return WRC_ERR_ARG;
+    ECK(cudaStreamSynchronize(E->main));
+    double ms = 0.0;
+    for (auto& pe : E->prof) {
+        float t = 0.f;
+        ECK(cudaEventElapsedTime(&t, pe.first, pe.second));
+        ms += t;
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    E->prof.clear();
+    if (ms_out) *ms_out = ms;
+    E->profiling = enable != 0;
+    return WRC_OK;
+}
+
+const char* wrc_ensemble_last_error(const wrc_ensemble* E) { return E ? E->err.c_str() : g_ens_create_error.c_str(); }
+
+void wrc_ensemble_destroy(wrc_ensemble* E) {
+    if (!E) return;
+    if (E->main) cudaStreamSynchronize(E->main);
+    for (cudaStream_t st : E->streams) cudaStreamSynchronize(st);
+    for (wrc_run* R : E->members) wrc_destroy(R);
+    for (auto& pe : E->prof) {
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    for (cudaEvent_t ev : E->ev_streams) cudaEventDestroy(ev);
+    if (E->ev_main) cudaEventDestroy(E->ev_main);
+    for (cudaStream_t st : E->streams) cudaStreamDestroy(st);
+    if (E->own_main && E->main) cudaStreamDestroy(E->main);
+    if (E->h_args) cudaFreeHost(E->h_args);
+    if (E->d_args) cudaFree(E->d_args);
+    if (E->h_blk) cudaFreeHost(E->h_blk);
+    if (E->d_blk) cudaFree(E->d_blk);
+    delete E;
+}
 
 }  // extern "C"

@@ -187,12 +187,16 @@ __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int n
     }
 }
 
+constexpr int kMaxLattice = 4096;   // WRC_MAX_NJ
+
 template <typename T>
 int plan_init_t(PoissonPlan& p, const Geom& g, cudaStream_t s) {
     if (cudaMalloc(&p.tw, sizeof(cx_t<T>) * (p.n / 2 > 0 ? p.n / 2 : 1)) != cudaSuccess) return -1;
     if (cudaMalloc(&p.sigma, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.dsym, sizeof(T) * p.n) != cudaSuccess) return -1;
-    const int smem = (int)(sizeof(cx_t<T>) * p.n);
+    // The dynamic shared-memory limit is a per-kernel, process-wide attribute:
+    // set it for the largest lattice, so runs of different sizes coexist.
+    const int smem = (int)(sizeof(cx_t<T>) * kMaxLattice);
     if (cudaFuncSetAttribute(k_fft_x_fwd_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_fft_y_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * smem) != cudaSuccess ||
         cudaFuncSetAttribute(k_fft_x_inv_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||

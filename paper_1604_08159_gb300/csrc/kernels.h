@@ -139,5 +139,12 @@ int krylov_step_blocks(long long n, int max_blocks);
 template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s);
 size_t krylov_partials_doubles(int max_blocks);
+// Batched Krylov step: `members` problems (device array of arguments) in one
+// cooperative launch of `blocks` blocks of pt (64, 128 or 256) threads; block
+// b works on problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q+1]-1.
+int krylov_batch_max_blocks(bool fp32, int pt);
+template <typename T>
+cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2mem, const int* d_mem_b0,
+                                int members, int blocks, int pt, int max_n, cudaStream_t s);
 
 }  // namespace wrc

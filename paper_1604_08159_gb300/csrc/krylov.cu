@@ -19,7 +19,7 @@ namespace wrc {
 
 namespace {
 
-constexpr int kPT = 128;      // threads per block (FP64 issue, not occupancy, bounds the phases)
+constexpr int kPT = 128;      // threads per block of the single-run kernel
 constexpr int kNV = 32;       // accumulator slots: basis vectors per pass (<= m + 1 <= 32)
 constexpr int kOutP = 33;     // partial sums per block: kNV dots + a squared norm
 constexpr int kTaylor = 20;   // Taylor terms per scaling sub-step of exp(M) e_k
@@ -36,10 +36,11 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // of each block is bounded by limit_ns; a block that runs out sets bit 1 of
 // *err, and every waiter leaves as soon as *err is non-zero, so the kernel
 // always returns.
-__device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns) {
+// The barrier spans the nb blocks of one problem (bid = block index within it).
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, int bid, int nb) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        const unsigned inc = bid == 0 ? 0x80000000u - (unsigned)(nb - 1) : 1u;
         __threadfence();
         const unsigned old = atomicAdd(bar, inc);
         volatile unsigned* vbar = bar;
@@ -63,6 +64,7 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns) 
 // (NS = ndots rounded up to a power of two) are reduced across the warp by a
 // reduce-scatter (NS - 1 exchanges; afterwards lane l holds the warp sum of
 // accumulator l mod NS), the norm by a shuffle tree.
+template <int PT>
 __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots, double* dst,
                                                double (*s_red)[kNV + 1]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -91,7 +93,7 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
     for (int t = threadIdx.x; t <= ndots; t += blockDim.x) {
         const int src = t < ndots ? t : kNV;
         double sum = 0.0;
-        for (int q = 0; q < kPT / 32; ++q) sum += s_red[q][src];
+        for (int q = 0; q < PT / 32; ++q) sum += s_red[q][src];
         dst[t] = sum;
     }
 }
@@ -99,15 +101,16 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
 // Sum over all blocks of part[b * kOutP + t], t < nout, into s_out: lane t
 // of warp w adds blocks w, w + nwarps, ... in order (one output per lane), the
 // warps' sums are then added in warp order.  Same order in every block.
+template <int PT>
 __device__ __forceinline__ void reduce_all(const double* part, int nout, double* s_out,
-                                           double (*s_red)[kNV + 1]) {
+                                           double (*s_red)[kNV + 1], int nb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kW = kPT / 32;
+    constexpr int kW = PT / 32;
     for (int t0 = 0; t0 < nout; t0 += 32) {
         const int t = t0 + lane;
         double v = 0.0;
         if (t < nout)
-            for (unsigned b = wid; b < gridDim.x; b += kW) v += __ldcg(part + (size_t)b * kOutP + t);
+            for (int b = wid; b < nb; b += kW) v += __ldcg(part + (size_t)b * kOutP + t);
         if (t < nout) s_red[wid][t] = v;
     }
     __syncthreads();
@@ -126,8 +129,8 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
 // Taylor series: with s = max(1, ceil(|M|_1)), B = M / s has |B|_1 <= 1,
 // x <- sum_{i<=20} B^i x / i!  applied s times; the dropped tail is at most
 // sum_{i>20} 1/i! < 2e-20 of |x| per sub-step.  One warp, lane r holds row r.
-__global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const int* __restrict__ kstop, int m,
-                                             double dt, double* __restrict__ y) {
+__device__ __forceinline__ void phi1_warp(const double* __restrict__ H, const int* __restrict__ kstop, int m,
+                                          double dt, double* __restrict__ y) {
     const int lane = threadIdx.x;
     const int k = *kstop;
     if (k <= 0) {
@@ -167,17 +170,23 @@ __global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const
     if (lane < m) y[lane] = lane < k ? x : 0.0;
 }
 
+__global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const int* __restrict__ kstop, int m,
+                                             double dt, double* __restrict__ y) {
+    phi1_warp(H, kstop, m, dt, y);
+}
+
 // omega <- omega + dt beta V_k y (accumulated in FP64), also written into the
 // lattice array L.
 template <typename T>
-__global__ void k_update(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
-                         const double* __restrict__ beta, const int* __restrict__ kstop, double dt,
-                         const uint32_t* __restrict__ meta, int n, T* __restrict__ omega, T* __restrict__ L) {
+__device__ __forceinline__ void update_body(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
+                                            const double* __restrict__ beta, const int* __restrict__ kstop,
+                                            double dt, const uint32_t* __restrict__ meta, int n,
+                                            T* __restrict__ omega, T* __restrict__ L, int bx, int gx) {
     __shared__ double s_c[kNV];
     const int k = *kstop;
     for (int t = threadIdx.x; t < k; t += blockDim.x) s_c[t] = dt * beta[0] * y[t];
     __syncthreads();
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+    for (int a = bx * blockDim.x + threadIdx.x; a < n; a += gx * blockDim.x) {
         double inc = 0.0;
         for (int t = 0; t < k; ++t) inc += s_c[t] * (double)basis[(size_t)t * ld + a];
         const T x = (T)((double)omega[a] + inc);
@@ -186,13 +195,22 @@ __global__ void k_update(const T* __restrict__ basis, long long ld, const double
     }
 }
 
+template <typename T>
+__global__ void k_update(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
+                         const double* __restrict__ beta, const int* __restrict__ kstop, double dt,
+                         const uint32_t* __restrict__ meta, int n, T* __restrict__ omega, T* __restrict__ L) {
+    update_body<T>(basis, ld, y, beta, kstop, dt, meta, n, omega, L, blockIdx.x, gridDim.x);
+}
+
 // x - c v in the bulk type: FP64 for the plain mode, FP32 (coefficient
 // rounded) for the mixed mode.
 __device__ __forceinline__ double axmy(double x, double v, double c) { return x - v * c; }
 __device__ __forceinline__ float axmy(float x, float v, double c) { return x - v * (float)c; }
 
-template <typename T>
-__global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
+// The Krylov step of one problem, run by its nb blocks (bid = this block's
+// index among them).
+template <typename T, int PT>
+__device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int bid, const int nb) {
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
     const T* __restrict__ ga = (const T*)A.ga;
@@ -201,16 +219,16 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
     T* __restrict__ basis = (T*)A.basis;
     T* __restrict__ w = (T*)A.w;
     T* __restrict__ Gb = (T*)A.Gb;
-    __shared__ double s_red[kPT / 32][kNV + 1];
+    __shared__ double s_red[PT / 32][kNV + 1];
     __shared__ double s_h[kOutP];
     __shared__ double s_c[kNV];
     const int n = A.n;
-    const int stride = gridDim.x * blockDim.x;
-    const int a0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const int stride = nb * PT;
+    const int a0 = bid * PT + threadIdx.x;
+    const bool lead = bid == 0 && threadIdx.x == 0;
     double* P0 = A.part;
-    double* P1 = P0 + (size_t)gridDim.x * kOutP;
-    double* P2 = P1 + (size_t)gridDim.x * kOutP;
+    double* P1 = P0 + (size_t)nb * kOutP;
+    double* P2 = P1 + (size_t)nb * kOutP;
     const T nu = (T)A.nu, r = (T)A.r, c1J = (T)A.c1J, c2J = (T)A.c2J;
     const int m = A.m;
     const long long ld = A.ld, ldg = A.ldg;
@@ -219,6 +237,8 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
         if (lead) atomicOr(A.err, 4);
         return;
     }
+    if (bid == 0)   // H is written by this block only
+        for (int t = threadIdx.x; t < (m + 1) * m; t += blockDim.x) A.H[t] = 0.0;
 
     // b = A_n omega + g  (L holds R(omega), ghosts included)
 #pragma unroll
@@ -229,9 +249,9 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
         w[a] = v;
         acc[kNV] += (double)v * (double)v;
     }
-    block_partials(acc, 0, P0 + (size_t)blockIdx.x * kOutP, s_red);
-    if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
-    reduce_all(P0, 1, s_h, s_red);
+    block_partials<PT>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
+    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+    reduce_all<PT>(P0, 1, s_h, s_red, nb);
     const double beta = sqrt(s_h[0]);
     int k = m;
     if (!(beta > 0.0) || !isfinite(beta)) {
@@ -258,7 +278,7 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
             Gb[t] = g;
             Lq[A.glist[t]] = g;
         }
-        if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
         for (int j = 0; j < m; ++j) {
             const int nv = j + 1;
             // phase 1: w = A v_j and the first Gram-Schmidt dots
@@ -273,9 +293,9 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
                     if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * vd;
                 acc[kNV] += vd * vd;
             }
-            block_partials(acc, nv, P0 + (size_t)blockIdx.x * kOutP, s_red);
-            if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
-            reduce_all(P0, nv + 1, s_h, s_red);
+            block_partials<PT>(acc, nv, P0 + (size_t)bid * kOutP, s_red);
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+            reduce_all<PT>(P0, nv + 1, s_h, s_red, nb);
             const double wn2 = s_h[nv];
             for (int t = threadIdx.x; t < nv; t += blockDim.x) s_c[t] = s_h[t];
             __syncthreads();
@@ -294,9 +314,9 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
                     if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * xd;
                 acc[kNV] += xd * xd;
             }
-            block_partials(acc, nv, P1 + (size_t)blockIdx.x * kOutP, s_red);
-            if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
-            reduce_all(P1, nv + 1, s_h, s_red);
+            block_partials<PT>(acc, nv, P1 + (size_t)bid * kOutP, s_red);
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+            reduce_all<PT>(P1, nv + 1, s_h, s_red, nb);
             // h_{:,j} = h1 + h2; |w''|^2 = |w'|^2 - |h2|^2 (V orthonormal, h2 = V^T w')
             bool bad = false;
             double h2n = 0.0;
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
                 h2n += s_h[t] * s_h[t];
             }
             const double hn = sqrt(fmax(s_h[nv] - h2n, 0.0));
-            if (blockIdx.x == 0) {
+            if (bid == 0) {
                 for (int t = threadIdx.x; t < nv; t += blockDim.x) A.H[(size_t)t * m + j] = s_c[t] + s_h[t];
                 if (threadIdx.x == 0) A.H[(size_t)(j + 1) * m + j] = hn;
             }
@@ -344,10 +364,40 @@ __global__ void __launch_bounds__(kPT, 1) k_krylov_step(KrylovStepArgs A) {
                 Gb[(size_t)(j + 1) * ldg + t] = g;
                 Lq[A.glist[t]] = g;
             }
-            if (!grid_sync(A.bar, A.err, A.limit_ns)) return;
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
         }
     }
     if (lead) *A.kstop = k;
+}
+
+template <typename T, int PT>
+__global__ void __launch_bounds__(PT, 1) k_krylov_step(KrylovStepArgs A) {
+    krylov_body<T, PT>(A, blockIdx.x, gridDim.x);
+}
+
+// Batched form: several problems in one cooperative launch; block b works on
+// problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q + 1] - 1.
+template <typename T, int PT>
+__global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __restrict__ args,
+                                                        const int* __restrict__ blk2mem,
+                                                        const int* __restrict__ mem_b0) {
+    const int q = blk2mem[blockIdx.x];
+    const int b0 = mem_b0[q];
+    krylov_body<T, PT>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
+}
+
+// phi_1 for problem blockIdx.x of a batch (one warp each).
+__global__ void __launch_bounds__(32) k_phi1_batch(const KrylovStepArgs* __restrict__ args) {
+    const KrylovStepArgs& A = args[blockIdx.x];
+    phi1_warp(A.H, A.kstop, A.m, A.dt, A.y);
+}
+
+// Update of problem blockIdx.y of a batch.
+template <typename T>
+__global__ void k_update_batch(const KrylovStepArgs* __restrict__ args) {
+    const KrylovStepArgs& A = args[blockIdx.y];
+    update_body<T>((const T*)A.basis, A.ld, A.y, A.beta, A.kstop, A.dt, A.meta, A.n, (T*)A.omega, (T*)A.L,
+                   blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -356,8 +406,8 @@ int krylov_step_init(bool fp32, int* max_blocks) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float>, kPT, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double>, kPT, 0);
+    const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float, kPT>, kPT, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double, kPT>, kPT, 0);
     if (e != cudaSuccess || per < 1) return -2;
     *max_blocks = sms * per;
     return 0;
@@ -374,7 +424,7 @@ template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
     KrylovStepArgs a = args;
     void* params[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T>, dim3(blocks), dim3(kPT), params, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT>, dim3(blocks), dim3(kPT), params, 0, s);
     if (e != cudaSuccess) return e;
     note_launch();
     k_phi1<<<1, 32, 0, s>>>(args.H, args.kstop, args.m, args.dt, args.y);
@@ -389,5 +439,45 @@ template cudaError_t launch_krylov_step<double>(const KrylovStepArgs&, int, cuda
 template cudaError_t launch_krylov_step<float>(const KrylovStepArgs&, int, cudaStream_t);
 
 size_t krylov_partials_doubles(int max_blocks) { return (size_t)3 * max_blocks * kOutP; }
+
+namespace {
+template <typename T, int PT>
+const void* batch_kernel() { return (const void*)k_krylov_batch<T, PT>; }
+}  // namespace
+
+int krylov_batch_max_blocks(bool fp32, int pt) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* k = nullptr;
+    switch (pt) {
+        case 64: k = fp32 ? batch_kernel<float, 64>() : batch_kernel<double, 64>(); break;
+        case 128: k = fp32 ? batch_kernel<float, 128>() : batch_kernel<double, 128>(); break;
+        case 256: k = fp32 ? batch_kernel<float, 256>() : batch_kernel<double, 256>(); break;
+        default: return -1;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, pt, 0) != cudaSuccess || per < 1) return -2;
+    return sms * per;
+}
+
+template <typename T>
+cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2mem, const int* d_mem_b0,
+                                int members, int blocks, int pt, int max_n, cudaStream_t s) {
+    void* params[] = {(void*)&d_args, (void*)&d_blk2mem, (void*)&d_mem_b0};
+    const void* k = pt == 64 ? batch_kernel<T, 64>() : pt == 256 ? batch_kernel<T, 256>() : batch_kernel<T, 128>();
+    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(pt), params, 0, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_phi1_batch<<<members, 32, 0, s>>>(d_args);
+    note_launch();
+    k_update_batch<T><<<dim3(blocks_for(max_n) < 64 ? blocks_for(max_n) : 64, members), kThreads, 0, s>>>(d_args);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_krylov_batch<double>(const KrylovStepArgs*, const int*, const int*, int, int, int, int,
+                                                 cudaStream_t);
+template cudaError_t launch_krylov_batch<float>(const KrylovStepArgs*, const int*, const int*, int, int, int, int,
+                                                cudaStream_t);
 
 }  // namespace wrc

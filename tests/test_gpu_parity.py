@@ -274,3 +274,22 @@ def test_graph_replayed_steps_bit_identical_to_direct_launches(prec):
             outs.append(run.active())
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_MIXED])
+def test_runs_of_different_sizes_coexist(prec):
+    """Per-kernel launch limits are process-wide: creating a small run after a
+    large one must not break the large one's steps (graph-captured too)."""
+    import torch
+    big = W.RunParams(n0=32, J=3, eps=1e-3, re=2000.0, sgs=W.SGS_DYNAMIC, cs=0.17, prec=prec)
+    small = W.RunParams(n0=16, J=1, eps=1e-3, re=2000.0, prec=prec)
+    v = W.random_field_params(seed=3, n=2)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with B.Run(big, stream=s1.cuda_stream) as a, B.Run(small, stream=s2.cuda_stream) as b:
+        a.init_vortices(v)
+        b.init_vortices(v)
+        a.step(2)
+        b.step(2)
+        a.sync()
+        b.sync()
+        assert a.counts()[0] > 0 and b.counts()[0] > 0

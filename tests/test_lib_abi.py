@@ -64,3 +64,15 @@ def test_null_run_handles(lib):
     assert lib.wrc_step(None, 1) == -1
     assert lib.wrc_sync(None) == -1
     lib.wrc_destroy(None)
+
+
+def test_ensemble_create_rejects_bad_arguments_without_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.wrc_ensemble_create(0, None, None, ctypes.byref(h)) == -1
+    a = B.WrcConfig(16, 3, 20, 0, 0, 0, 1e-3, 5000.0, 0.0, 0.0, 0.0, 1e-2)
+    b = B.WrcConfig(16, 3, 20, 0, 1, 0, 1e-3, 5000.0, 0.0, 0.0, 0.0, 1e-2)
+    arr = (B.WrcConfig * 2)(a, b)
+    assert lib.wrc_ensemble_create(2, arr, None, ctypes.byref(h)) == -1
+    assert b"precision" in lib.wrc_ensemble_last_error(None)
+    assert lib.wrc_ensemble_step(None, 1) == -1
+    lib.wrc_ensemble_destroy(None)
