@@ -203,6 +203,27 @@ const char* wrc_last_error(const wrc_run* run);
 /* Release the run's device memory (synchronises its stream first). */
 void wrc_destroy(wrc_run* run);
 
+/* ---- Diagnostics without allocation ------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code running while a stream is captured
+ * into a CUDA graph, host frameworks that own all device memory through their
+ * own pool, real-time loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
+ * Same quantities as wrc_diagnostics out[0..3] (E, Z, P, circulation) for a
+ * reconstructed vorticity lattice omega_lattice and its streamfunction
+ * psi_lattice (device arrays, NJ*NJ doubles, e.g. from wrc_query_field with
+ * device_ptr = 1), written to the device array out[0..3]; asynchronous on
+ * cuda_stream.  It allocates nothing: its scratch (one row of 4 partial sums
+ * per reduction block, 1216 blocks at most, and a counter: 39 KB) is a fixed
+ * array in the library that every GPU using the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address, so make it before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or devices' views of one
+ * call) race and give wrong sums; serialise them.  NJ must be a power of two,
+ * 8 <= NJ <= WRC_MAX_NJ; otherwise WRC_ERR_ARG. */
+wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattice, const double* psi_lattice, int32_t NJ,
+                                           double* out, void* cuda_stream);
+
 /* ---- Batched ensemble ------------------------------------------------------
  * Uneven members (different lattices, parameters and initial conditions;
  * one precision for all) advanced together.  Each step runs the members'

@@ -54,6 +54,7 @@ SIGNATURES = {
     "wrc_query_profile": (c_int32, [c_void_p, c_void_p]),
     "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_destroy": (None, [c_void_p]),
+    "wrc_lattice_diagnostics_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "wrc_ensemble_create": (c_int32, [c_int32, c_void_p, c_void_p, POINTER(c_void_p)]),
     "wrc_ensemble_member": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "wrc_ensemble_step": (c_int32, [c_void_p, c_int32]),
@@ -354,6 +355,18 @@ class Run:
 
     def profile_record(self):
         return wrc_query_profile(self.h)
+
+
+def wrc_lattice_diagnostics_noalloc(omega_lattice, psi_lattice, NJ: int, out, stream: int | None = None):
+    """Device tensors in and out; allocates nothing on the device."""
+    po, fo = _ptr(omega_lattice)
+    pp, fp = _ptr(psi_lattice)
+    pq, fq = _ptr(out)
+    if not (fo and fp and fq):
+        raise ValueError("wrc_lattice_diagnostics_noalloc takes device arrays")
+    st = load().wrc_lattice_diagnostics_noalloc(po, pp, NJ, pq, c_void_p(stream or 0))
+    if st != WRC_OK:
+        raise WrcError("wrc_lattice_diagnostics_noalloc", st, "invalid argument or CUDA error")
 
 
 # ---- batched ensemble ------------------------------------------------------------
