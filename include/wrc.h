@@ -276,6 +276,117 @@ const char* wrc_ensemble_last_error(const wrc_ensemble* e);
 /* Destroy the members and the ensemble (synchronises). */
 void wrc_ensemble_destroy(wrc_ensemble* e);
 
+/* ---- Request server (continuous batching) ----------------------------------
+ * The paper has no counterpart: a host-side scheduler for many independent
+ * runs (Sec. 3 initial conditions of 1..WRC_MAX_VORTICES Gaussian vortices,
+ * any lattice and parameters) that arrive over time.  A worker thread owns
+ * all GPU work.  Each admitted run keeps its whole adaptive-grid state on the
+ * device until its last step; only its final result (diagnostics and active
+ * set) is copied to the host, after which its device memory is freed.
+ *
+ * Admission, in arrival order (a request that does not fit blocks the ones
+ * behind it): a request is admitted once it has arrived, fewer than max_slots
+ * runs are resident, and the HBM charged to the resident runs plus the
+ * request's estimate (wrc_server_estimate) stays within hbm_budget_bytes.  A
+ * resident run is charged the larger of its estimate and the bytes it holds.
+ * If creating a run still finds the device out of memory, the request goes
+ * back to the head of the queue and nothing more is admitted until a resident
+ * run finishes.
+ *
+ * WRC_SERVE_BATCHED (continuous batching): every worker iteration advances
+ * every resident run by one step -- the runs of each precision in one batched
+ * step as wrc_ensemble_step does (one cooperative Krylov launch for all of
+ * them) -- then retires the runs that reached their step count and admits
+ * new arrivals, so runs join and leave the batch between steps.  A run's
+ * result equals its solo wrc_step result to rounding (only the block
+ * decomposition of its reductions differs).  A run whose step fails is
+ * retired as failed; the others carry on.
+ * WRC_SERVE_FIFO: the plain per-run form for comparison -- one run at a
+ * time, in arrival order, stepped with wrc_step.
+ *
+ * Times are seconds on a monotonic clock since wrc_server_create. */
+typedef struct wrc_server wrc_server;
+
+typedef enum { WRC_SERVE_BATCHED = 0, WRC_SERVE_FIFO = 1 } wrc_serve_policy;
+typedef enum { WRC_REQ_QUEUED = 0, WRC_REQ_RUNNING = 1, WRC_REQ_DONE = 2, WRC_REQ_FAILED = 3 } wrc_request_state;
+
+typedef struct {
+    int32_t policy;               /* wrc_serve_policy */
+    int32_t max_slots;            /* resident runs at most, 1..1024 (FIFO: 1) */
+    int32_t threads_per_block;    /* batched kernel shape: 64/128/256, or 0 for the */
+    int32_t points_per_thread;    /* autotuned shape if one is cached, else 128 x 1 */
+    double hbm_budget_bytes;      /* admission budget, > 0 (e.g. 150e9) */
+} wrc_server_config;
+
+typedef struct {
+    int32_t state;                /* wrc_request_state */
+    int32_t status;               /* wrc_status of a failed request, else WRC_OK */
+    int64_t steps;                /* steps taken so far */
+    int64_t n_active, n_ghost;    /* grid sizes at the end (DONE) */
+    double t_arrival;             /* when the request counts as arrived */
+    double t_admit;               /* when its run was created (-1 before) */
+    double t_done;                /* when its result was ready (-1 before) */
+    double diag[4];               /* E, Z, P, circulation at the end (as wrc_diagnostics) */
+    double time;                  /* simulated time at the end */
+    double updates;               /* active-point updates: sum of the active count over its steps */
+    double charged_bytes;         /* HBM charged while resident */
+} wrc_request_info;
+
+/* Device bytes charged on admission for a run of configuration cfg: the
+ * allocations wrc_create makes for its lattice (exact) plus the compact
+ * arrays for an active-count bound N_a,max = min(NJ^2, 8192 + NJ^2/16) and
+ * N_a,max/2 ghost points, at the capacity the run grows them to.  Host
+ * arithmetic only.  WRC_ERR_ARG for an invalid cfg. */
+wrc_status wrc_server_estimate(const wrc_config* cfg, double* bytes);
+
+/* Start a server (and its worker thread) on the current CUDA device.
+ * WRC_ERR_ARG for an invalid config; wrc_server_last_error(NULL) explains. */
+wrc_status wrc_server_create(const wrc_server_config* cfg, wrc_server** out);
+
+/* Queue a run: configuration, nv vortices (host arrays, as
+ * wrc_init_vortices), nsteps >= 0 steps, and its arrival time arrival_s in
+ * server seconds (a time in the past, e.g. 0, means now; a later time holds
+ * the request until then, which replays a trace without host timing jitter).
+ * Writes the request id.  WRC_ERR_ARG for invalid arguments, WRC_ERR_BUSY if
+ * the estimate exceeds the whole budget, WRC_ERR_STATE after a fatal server
+ * error. */
+wrc_status wrc_server_submit(wrc_server* srv, const wrc_config* cfg, int32_t nv, const double* xc, const double* yc,
+                             const double* gamma, const double* s, int64_t nsteps, double arrival_s, int64_t* id);
+
+/* State, timing and (once DONE) result of a request.  WRC_ERR_ARG for an
+ * unknown or released id. */
+wrc_status wrc_server_query(wrc_server* srv, int64_t id, wrc_request_info* out);
+
+/* The final active set of a DONE request (as wrc_query_active, host arrays,
+ * either may be NULL; WRC_ERR_ARG if cap < n_active, WRC_ERR_STATE if the
+ * request is not DONE). */
+wrc_status wrc_server_result_active(wrc_server* srv, int64_t id, int32_t* idx_out, double* omega_out, int64_t cap);
+
+/* Message of a FAILED request, copied into buf (cap bytes, NUL-terminated). */
+wrc_status wrc_server_request_error(wrc_server* srv, int64_t id, char* buf, int64_t cap);
+
+/* Wait until request id (or, for id = -1, every request submitted so far) is
+ * DONE or FAILED; WRC_ERR_TIMEOUT after timeout_s seconds. */
+wrc_status wrc_server_wait(wrc_server* srv, int64_t id, double timeout_s);
+
+/* Forget a finished request and its host result. */
+wrc_status wrc_server_release(wrc_server* srv, int64_t id);
+
+/* out[0] submitted, out[1] done, out[2] failed, out[3] queued, out[4]
+ * resident now, out[5] most resident at once, out[6] HBM charged now, out[7]
+ * most HBM charged at once, out[8] worker iterations that stepped runs,
+ * out[9] active-point updates of all steps, out[10] server clock now,
+ * out[11] 1 after a fatal server error. */
+wrc_status wrc_server_stats(wrc_server* srv, double out[12]);
+
+/* Message of the last server-level failure ("" if none); for NULL, the last
+ * failure of wrc_server_create on this thread. */
+const char* wrc_server_last_error(const wrc_server* srv);
+
+/* Stop the worker after its current iteration, fail the requests still
+ * queued or resident, free every run and the server. */
+void wrc_server_destroy(wrc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

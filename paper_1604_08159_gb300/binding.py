@@ -30,6 +30,20 @@ class WrcConfig(ctypes.Structure):
                 ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double)]
 
 
+class WrcServerConfig(ctypes.Structure):
+    _fields_ = [("policy", c_int32), ("max_slots", c_int32), ("threads_per_block", c_int32),
+                ("points_per_thread", c_int32), ("hbm_budget_bytes", c_double)]
+
+
+class WrcRequestInfo(ctypes.Structure):
+    _fields_ = [("state", c_int32), ("status", c_int32), ("steps", c_int64), ("n_active", c_int64),
+                ("n_ghost", c_int64), ("t_arrival", c_double), ("t_admit", c_double), ("t_done", c_double),
+                ("diag", c_double * 4), ("time", c_double), ("updates", c_double), ("charged_bytes", c_double)]
+
+
+SERVE_BATCHED, SERVE_FIFO = 0, 1
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 # name -> (restype, argtypes); the list of entry points of include/wrc.h
 SIGNATURES = {
     "wrc_create": (c_int32, [POINTER(WrcConfig), c_void_p, POINTER(c_void_p)]),
@@ -64,6 +78,18 @@ SIGNATURES = {
     "wrc_ensemble_profile": (c_int32, [c_void_p, c_int32, c_void_p]),
     "wrc_ensemble_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_ensemble_destroy": (None, [c_void_p]),
+    "wrc_server_estimate": (c_int32, [POINTER(WrcConfig), POINTER(c_double)]),
+    "wrc_server_create": (c_int32, [POINTER(WrcServerConfig), POINTER(c_void_p)]),
+    "wrc_server_submit": (c_int32, [c_void_p, POINTER(WrcConfig), c_int32, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_int64, c_double, POINTER(c_int64)]),
+    "wrc_server_query": (c_int32, [c_void_p, c_int64, POINTER(WrcRequestInfo)]),
+    "wrc_server_result_active": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_int64]),
+    "wrc_server_request_error": (c_int32, [c_void_p, c_int64, c_void_p, c_int64]),
+    "wrc_server_wait": (c_int32, [c_void_p, c_int64, c_double]),
+    "wrc_server_release": (c_int32, [c_void_p, c_int64]),
+    "wrc_server_stats": (c_int32, [c_void_p, c_void_p]),
+    "wrc_server_last_error": (ctypes.c_char_p, [c_void_p]),
+    "wrc_server_destroy": (None, [c_void_p]),
 }
 
 _lib = None
@@ -473,6 +499,136 @@ class Ensemble:
             for m in self.members:
                 m.close()
             wrc_ensemble_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- request server -------------------------------------------------------------
+
+def _scheck(fn: str, st: int, srv=None):
+    if st != WRC_OK:
+        msg = load().wrc_server_last_error(srv)
+        raise WrcError(fn, st, msg.decode() if msg else "")
+
+
+def wrc_server_estimate(cfg: WrcConfig) -> float:
+    b = c_double()
+    st = load().wrc_server_estimate(byref(cfg), byref(b))
+    if st != WRC_OK:
+        raise WrcError("wrc_server_estimate", st, "invalid configuration")
+    return b.value
+
+
+def wrc_server_create(policy: int = SERVE_BATCHED, max_slots: int = 256, hbm_budget_bytes: float = 150e9,
+                      threads_per_block: int = 0, points_per_thread: int = 0) -> int:
+    cfg = WrcServerConfig(policy, max_slots, threads_per_block, points_per_thread, hbm_budget_bytes)
+    h = c_void_p()
+    _scheck("wrc_server_create", load().wrc_server_create(byref(cfg), byref(h)))
+    return h.value
+
+
+def wrc_server_submit(srv, cfg: WrcConfig, xc, yc, gamma, s, nsteps: int, arrival_s: float = 0.0) -> int:
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xc, yc, gamma, s)]
+    rid = c_int64()
+    _scheck("wrc_server_submit", load().wrc_server_submit(
+        srv, byref(cfg), arrs[0].size, *[a.ctypes.data for a in arrs], nsteps, arrival_s, byref(rid)), srv)
+    return rid.value
+
+
+def wrc_server_query(srv, rid: int) -> WrcRequestInfo:
+    info = WrcRequestInfo()
+    _scheck("wrc_server_query", load().wrc_server_query(srv, rid, byref(info)), srv)
+    return info
+
+
+def wrc_server_result_active(srv, rid: int, cap: int):
+    idx = np.empty(cap, dtype=np.int32)
+    om = np.empty(cap, dtype=np.float64)
+    _scheck("wrc_server_result_active",
+            load().wrc_server_result_active(srv, rid, idx.ctypes.data, om.ctypes.data, cap), srv)
+    return idx, om
+
+
+def wrc_server_request_error(srv, rid: int) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _scheck("wrc_server_request_error", load().wrc_server_request_error(srv, rid, buf, 1024), srv)
+    return buf.value.decode()
+
+
+def wrc_server_wait(srv, rid: int = -1, timeout_s: float = 600.0):
+    _scheck("wrc_server_wait", load().wrc_server_wait(srv, rid, timeout_s), srv)
+
+
+def wrc_server_release(srv, rid: int):
+    _scheck("wrc_server_release", load().wrc_server_release(srv, rid), srv)
+
+
+def wrc_server_stats(srv) -> dict:
+    out = np.zeros(12, dtype=np.float64)
+    _scheck("wrc_server_stats", load().wrc_server_stats(srv, out.ctypes.data), srv)
+    keys = ("submitted", "done", "failed", "queued", "resident", "peak_resident", "charged_bytes",
+            "peak_charged_bytes", "iterations", "updates", "clock_s", "fatal")
+    return dict(zip(keys, out.tolist()))
+
+
+def wrc_server_last_error(srv) -> str:
+    msg = load().wrc_server_last_error(srv)
+    return msg.decode() if msg else ""
+
+
+def wrc_server_destroy(srv):
+    load().wrc_server_destroy(srv)
+
+
+class Server:
+    """Request server: runs submitted with arrival times are admitted by slot
+    and HBM budget and advanced together (continuous batching), or one at a
+    time (FIFO)."""
+
+    def __init__(self, policy: int = SERVE_BATCHED, max_slots: int = 256, hbm_budget_bytes: float = 150e9,
+                 threads_per_block: int = 0, points_per_thread: int = 0):
+        self.h = wrc_server_create(policy, max_slots, hbm_budget_bytes, threads_per_block, points_per_thread)
+
+    def submit(self, params, vortices, nsteps: int, arrival_s: float = 0.0) -> int:
+        return wrc_server_submit(self.h, make_config(params), vortices.xc, vortices.yc, vortices.gamma,
+                                 vortices.s, nsteps, arrival_s)
+
+    def query(self, rid: int) -> WrcRequestInfo:
+        return wrc_server_query(self.h, rid)
+
+    def result(self, rid: int):
+        """(lattice indices, omega) of a finished request's final active set."""
+        info = self.query(rid)
+        if info.state != REQ_DONE:
+            raise WrcError("result", -7, wrc_server_request_error(self.h, rid) or "request not done")
+        return wrc_server_result_active(self.h, rid, int(info.n_active))
+
+    def error(self, rid: int) -> str:
+        return wrc_server_request_error(self.h, rid)
+
+    def wait(self, rid: int = -1, timeout_s: float = 600.0):
+        wrc_server_wait(self.h, rid, timeout_s)
+
+    def release(self, rid: int):
+        wrc_server_release(self.h, rid)
+
+    def stats(self) -> dict:
+        return wrc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            wrc_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -15,6 +15,7 @@
 #include <utility>
 
 #include "../../include/wrc.h"
+#include "batch.h"
 #include "kernels.h"
 
 using namespace wrc;
@@ -155,6 +156,8 @@ struct wrc_run {
     long long gcount[16] = {0}, goff[16] = {0};
     double t = 0.0;
     long long nstep = 0;
+    double updates = 0.0;   // sum of the active count over the steps taken
+    bool nonfinite = false; // a step met a non-finite Arnoldi coefficient (seen at its grid rebuild)
     bool init = false, frozen = false;
 };
 
@@ -257,6 +260,7 @@ wrc_status rebuild_part1(wrc_run* R) {
     launch_compact(R->nxt, R->gho, g, nkeys, R->blk_counts, R->blk_off, R->counts_dev, R->list, s);
     CK(cudaMemcpyAsync(R->counts_host, R->counts_dev, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(R->counts_host + kMaxKeys, R->K.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(R->counts_host + kMaxKeys + 1, R->K.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     CKL("compaction");
     return WRC_OK;
 }
@@ -267,6 +271,7 @@ wrc_status rebuild_host(wrc_run* R) {
     const cudaStream_t s = R->st;
     CK(cudaStreamSynchronize(s));
     R->host_syncs += 1;
+    if (R->counts_host[kMaxKeys + 1] & 1) R->nonfinite = true;
     if (R->counts_host[kMaxKeys] != 0) {
         CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
         const int ev = R->counts_host[kMaxKeys];
@@ -552,6 +557,7 @@ enum { kPhaseFreeze = 0, kPhaseAdapt1 = 1, kPhaseAdapt2 = 2 };
 // the new grid's sizes -> [adapt part 2]; bracketed phases run as CUDA graphs.
 template <typename T>
 wrc_status step_once(wrc_run* R) {
+    const long long na0 = R->n_active;
     TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
     R->frozen = true;
     TRY(krylov<T>(R));
@@ -566,6 +572,7 @@ wrc_status step_once(wrc_run* R) {
     rebuild_commit(R);
     R->t += R->cfg.dt;
     R->nstep += 1;
+    R->updates += (double)na0;
     return WRC_OK;
 }
 
@@ -757,6 +764,8 @@ bool valid_config(const wrc_config* c, std::string& why) {
 }
 
 }  // namespace
+
+bool wrc::valid_run_config(const wrc_config* c, std::string& why) { return valid_config(c, why); }
 
 extern "C" {
 
@@ -1096,71 +1105,43 @@ void wrc_destroy(wrc_run* R) { free_run(R); }
 }  // extern "C"
 
 // ============================================================================
-// Batched ensemble (uneven members in one cooperative Krylov launch per step)
+// Batched stepping of several runs (ensemble and server)
 // ============================================================================
-
-struct wrc_ensemble {
-    std::vector<wrc_run*> members;
-    cudaStream_t main = nullptr;             // the caller's stream (the batched launch)
-    bool own_main = false;                   // created here when the caller passed NULL
-    std::vector<cudaStream_t> streams;       // member streams (owned)
-    std::vector<cudaEvent_t> ev_streams;     // one per member stream
-    cudaEvent_t ev_main = nullptr;
-    bool fp32 = false;
-    int pt = 128;                            // threads per block of the batched kernel
-    int ept = 1;                             // target active points per thread
-    KrylovStepArgs* h_args = nullptr;        // pinned
-    int* h_blk = nullptr;                    // pinned: block -> member, then member block offsets
-    KrylovStepArgs* d_args = nullptr;
-    int* d_blk = nullptr;
-    int blk_cap = 0;
-    int last_blocks = 0;
-    long long nstep = 0;
-    bool profiling = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
-    std::string err;
-};
 
 namespace {
 
-thread_local std::string g_ens_create_error;
-constexpr int kEnsStreams = 8;
+constexpr int kBatchStreams = 8;
 
-wrc_status efail(wrc_ensemble* E, wrc_status s, const std::string& msg) {
-    if (E) E->err = msg;
+wrc_status cfail(BatchCtx& C, wrc_status s, const std::string& msg) {
+    C.err = msg;
     return s;
 }
 
-#define ECK(call)                                                                               \
+#define BCK(call)                                                                               \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \
         if (e_ != cudaSuccess)                                                                  \
-            return efail(E, e_ == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA,       \
+            return cfail(C, e_ == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA,       \
                          std::string(#call) + ": " + cudaGetErrorString(e_));                   \
     } while (0)
 
-// Member failures are reported with the member's index and message.
-wrc_status member_fail(wrc_ensemble* E, size_t i, wrc_status st) {
-    return efail(E, st, "member " + std::to_string(i) + ": " + E->members[i]->err);
-}
-
-// Block plan: member i gets ceil(n_i / (pt * ept)) blocks, clamped to
+// Block plan: run i gets ceil(n_i / (pt * ept)) blocks, clamped to
 // [1, its partial-sum capacity]; if the total exceeds what can be co-resident,
-// every member's share is scaled down (keeping at least one block each).
-wrc_status plan_batch(wrc_ensemble* E, int max_coresident, int& total) {
-    const size_t M = E->members.size();
+// every run's share is scaled down (keeping at least one block each).
+wrc_status plan_batch(BatchCtx& C, const std::vector<wrc_run*>& runs, int max_coresident, int& total) {
+    const size_t M = runs.size();
     std::vector<int> nb(M);
     long long sum = 0;
     for (size_t i = 0; i < M; ++i) {
-        const wrc_run* R = E->members[i];
-        long long b = (R->n_active + (long long)E->pt * E->ept - 1) / ((long long)E->pt * E->ept);
+        const wrc_run* R = runs[i];
+        long long b = (R->n_active + (long long)C.pt * C.ept - 1) / ((long long)C.pt * C.ept);
         b = b < 1 ? 1 : b;
         b = b > R->max_blocks ? R->max_blocks : b;
         nb[i] = (int)b;
         sum += b;
     }
     if ((long long)M > max_coresident)
-        return efail(E, WRC_ERR_ARG, "more members than co-resident blocks of the batched kernel");
+        return cfail(C, WRC_ERR_ARG, "more runs than co-resident blocks of the batched kernel");
     if (sum > max_coresident) {
         const double f = (double)(max_coresident - (long long)M) / (double)(sum - (long long)M);
         sum = 0;
@@ -1170,15 +1151,28 @@ wrc_status plan_batch(wrc_ensemble* E, int max_coresident, int& total) {
         }
     }
     total = (int)sum;
-    if (total + (int)M + 1 > E->blk_cap) {
-        if (E->h_blk) cudaFreeHost(E->h_blk);
-        if (E->d_blk) cudaFree(E->d_blk);
-        E->blk_cap = total + (int)M + 1 + 1024;
-        ECK(cudaMallocHost((void**)&E->h_blk, sizeof(int) * E->blk_cap));
-        ECK(cudaMalloc((void**)&E->d_blk, sizeof(int) * E->blk_cap));
+    if (total + (int)M + 1 > C.blk_cap) {
+        BCK(cudaStreamSynchronize(C.main));   // the old tables may still be read
+        if (C.h_blk) cudaFreeHost(C.h_blk);
+        if (C.d_blk) cudaFree(C.d_blk);
+        C.h_blk = nullptr;
+        C.d_blk = nullptr;
+        C.blk_cap = total + (int)M + 1 + 1024;
+        BCK(cudaMallocHost((void**)&C.h_blk, sizeof(int) * C.blk_cap));
+        BCK(cudaMalloc((void**)&C.d_blk, sizeof(int) * C.blk_cap));
     }
-    int* blk2mem = E->h_blk;
-    int* b0 = E->h_blk + total;
+    if ((int)M > C.args_cap) {
+        BCK(cudaStreamSynchronize(C.main));
+        if (C.h_args) cudaFreeHost(C.h_args);
+        if (C.d_args) cudaFree(C.d_args);
+        C.h_args = nullptr;
+        C.d_args = nullptr;
+        C.args_cap = (int)M + 64;
+        BCK(cudaMallocHost((void**)&C.h_args, sizeof(KrylovStepArgs) * C.args_cap));
+        BCK(cudaMalloc((void**)&C.d_args, sizeof(KrylovStepArgs) * C.args_cap));
+    }
+    int* blk2mem = C.h_blk;
+    int* b0 = C.h_blk + total;
     int off = 0;
     for (size_t i = 0; i < M; ++i) {
         b0[i] = off;
@@ -1189,85 +1183,130 @@ wrc_status plan_batch(wrc_ensemble* E, int max_coresident, int& total) {
     return WRC_OK;
 }
 
+// The batched launch and the stream joins around it, for the runs `live`.
 template <typename T>
-wrc_status ensemble_step_once(wrc_ensemble* E) {
-    const size_t M = E->members.size();
-    const int S = (int)E->streams.size();
-    // phase 1: freeze every member on its stream
-    for (size_t i = 0; i < M; ++i) {
-        wrc_run* R = E->members[i];
-        const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); });
-        if (st != WRC_OK) return member_fail(E, i, st);
-        R->frozen = true;
+wrc_status batch_krylov(BatchCtx& C, const std::vector<wrc_run*>& live) {
+    for (size_t q = 0; q < C.streams.size(); ++q) {
+        BCK(cudaEventRecord(C.ev_streams[q], C.streams[q]));
+        BCK(cudaStreamWaitEvent(C.main, C.ev_streams[q], 0));
     }
-    for (int q = 0; q < S; ++q) {
-        ECK(cudaEventRecord(E->ev_streams[q], E->streams[q]));
-        ECK(cudaStreamWaitEvent(E->main, E->ev_streams[q], 0));
-    }
-    // phase 2: the Krylov step of all members in one cooperative launch
-    const int maxb = krylov_batch_max_blocks(E->fp32, E->pt);
-    if (maxb <= 0) return efail(E, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
+    const int maxb = krylov_batch_max_blocks(C.fp32, C.pt);
+    if (maxb <= 0) return cfail(C, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
     int total = 0;
-    TRY(plan_batch(E, maxb, total));
+    TRY(plan_batch(C, live, maxb, total));
+    const size_t M = live.size();
     int max_n = 1;
     for (size_t i = 0; i < M; ++i) {
-        E->h_args[i] = krylov_args(E->members[i]);
-        max_n = std::max(max_n, (int)E->members[i]->n_active);
+        C.h_args[i] = krylov_args(live[i]);
+        max_n = std::max(max_n, (int)live[i]->n_active);
     }
-    ECK(cudaMemcpyAsync(E->d_args, E->h_args, sizeof(KrylovStepArgs) * M, cudaMemcpyHostToDevice, E->main));
-    ECK(cudaMemcpyAsync(E->d_blk, E->h_blk, sizeof(int) * (total + M + 1), cudaMemcpyHostToDevice, E->main));
+    BCK(cudaMemcpyAsync(C.d_args, C.h_args, sizeof(KrylovStepArgs) * M, cudaMemcpyHostToDevice, C.main));
+    BCK(cudaMemcpyAsync(C.d_blk, C.h_blk, sizeof(int) * (total + M + 1), cudaMemcpyHostToDevice, C.main));
     cudaEvent_t pa = nullptr, pb = nullptr;
-    if (E->profiling) {
-        ECK(cudaEventCreate(&pa));
-        ECK(cudaEventCreate(&pb));
-        ECK(cudaEventRecord(pa, E->main));
+    if (C.profiling) {
+        BCK(cudaEventCreate(&pa));
+        BCK(cudaEventCreate(&pb));
+        BCK(cudaEventRecord(pa, C.main));
     }
-    ECK(launch_krylov_batch<T>(E->d_args, E->d_blk, E->d_blk + total, (int)M, total, E->pt, max_n, E->main));
-    if (E->profiling) {
-        ECK(cudaEventRecord(pb, E->main));
-        E->prof.push_back({pa, pb});
+    BCK(launch_krylov_batch<T>(C.d_args, C.d_blk, C.d_blk + total, (int)M, total, C.pt, max_n, C.main));
+    if (C.profiling) {
+        BCK(cudaEventRecord(pb, C.main));
+        C.prof.push_back({pa, pb});
     }
-    E->last_blocks = total;
-    ECK(cudaEventRecord(E->ev_main, E->main));
-    // phase 3: adaptation part 1 on the member streams
-    for (int q = 0; q < S; ++q) ECK(cudaStreamWaitEvent(E->streams[q], E->ev_main, 0));
+    C.last_blocks = total;
+    BCK(cudaEventRecord(C.ev_main, C.main));
+    for (size_t q = 0; q < C.streams.size(); ++q) BCK(cudaStreamWaitEvent(C.streams[q], C.ev_main, 0));
+    return WRC_OK;
+}
+
+// One step of every run: freeze phases on the runs' streams, one batched
+// Krylov launch, adaptation part 1, one wait for all streams, then the host
+// part and adaptation part 2 of each run.
+template <typename T>
+wrc_status batch_step_t(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vector<wrc_status>& rs) {
+    const size_t M = runs.size();
+    rs.assign(M, WRC_OK);
+    if (!M) return WRC_OK;
+    wrc_status first = WRC_OK;
+    std::string first_msg;
+    auto mark = [&](size_t i, wrc_status st) {
+        rs[i] = st;
+        if (first == WRC_OK) {
+            first = st;
+            first_msg = "run " + std::to_string(i) + ": " + runs[i]->err;
+        }
+    };
+    // a failure that is not one run's fails every run still going
+    auto fail_all = [&](wrc_status st) {
+        for (size_t i = 0; i < M; ++i)
+            if (rs[i] == WRC_OK) {
+                rs[i] = st;
+                runs[i]->err = "batched step: " + C.err;
+            }
+        return st;
+    };
+    std::vector<long long> na0(M);
     for (size_t i = 0; i < M; ++i) {
-        wrc_run* R = E->members[i];
+        wrc_run* R = runs[i];
+        na0[i] = R->n_active;
+        const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); });
+        if (st != WRC_OK) mark(i, st);
+        else R->frozen = true;
+    }
+    std::vector<wrc_run*> live;
+    std::vector<size_t> live_i;
+    for (size_t i = 0; i < M; ++i)
+        if (rs[i] == WRC_OK) {
+            live.push_back(runs[i]);
+            live_i.push_back(i);
+        }
+    if (!live.empty()) {
+        const wrc_status st = batch_krylov<T>(C, live);
+        if (st != WRC_OK) return fail_all(st);
+    }
+    for (size_t i : live_i) {
+        wrc_run* R = runs[i];
         const wrc_status st = run_phase(R, kPhaseAdapt1, [&] {
             for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
             return threshold_body<T>(R, R->cfg.eps, false);
         });
-        if (st != WRC_OK) return member_fail(E, i, st);
-        R->det_count = R->n_active;
+        if (st != WRC_OK) mark(i, st);
+        else R->det_count = R->n_active;
     }
-    // one wait for all members, then the host part and adaptation part 2
-    for (int q = 0; q < S; ++q) ECK(cudaStreamSynchronize(E->streams[q]));
-    for (size_t i = 0; i < M; ++i) {
-        wrc_run* R = E->members[i];
+    for (cudaStream_t st : C.streams) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail_all(cfail(C, WRC_ERR_CUDA, std::string("stream wait: ") + cudaGetErrorString(e)));
+    }
+    for (size_t i : live_i) {
+        if (rs[i] != WRC_OK) continue;
+        wrc_run* R = runs[i];
         wrc_status st = rebuild_host(R);
         if (st == WRC_OK) st = run_phase(R, kPhaseAdapt2, [&] { return rebuild_part2<T>(R); });
-        if (st != WRC_OK) return member_fail(E, i, st);
+        if (st != WRC_OK) {
+            mark(i, st);
+            continue;
+        }
         rebuild_commit(R);
         R->t += R->cfg.dt;
         R->nstep += 1;
+        R->updates += (double)na0[i];
     }
-    // the member streams must not run ahead of the next batched launch's reads
-    for (int q = 0; q < S; ++q) {
-        ECK(cudaEventRecord(E->ev_streams[q], E->streams[q]));
-        ECK(cudaStreamWaitEvent(E->main, E->ev_streams[q], 0));
+    // the run streams must not run ahead of the next batched launch's reads
+    for (size_t q = 0; q < C.streams.size(); ++q) {
+        const cudaError_t e1 = cudaEventRecord(C.ev_streams[q], C.streams[q]);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(C.main, C.ev_streams[q], 0) : e1;
+        if (e2 != cudaSuccess) return fail_all(cfail(C, WRC_ERR_CUDA, std::string("stream join: ") + cudaGetErrorString(e2)));
     }
-    E->nstep += 1;
-    return WRC_OK;
+    if (first != WRC_OK) C.err = first_msg;
+    return first;
 }
 
 // Autotuner cache: best (threads per block, points per thread) per precision,
-// member-count bucket and total-active-points bucket, for this process.
+// run-count bucket and total-active-points bucket, for this process.
 struct TuneKey {
     bool fp32;
     int mb, nb;
-    bool operator<(const TuneKey& o) const {
-        return std::tie(fp32, mb, nb) < std::tie(o.fp32, o.mb, o.nb);
-    }
+    bool operator<(const TuneKey& o) const { return std::tie(fp32, mb, nb) < std::tie(o.fp32, o.mb, o.nb); }
 };
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 std::mutex g_tune_mutex;
@@ -1281,10 +1320,151 @@ int log2_bucket(long long v) {
     return b;
 }
 
-TuneKey tune_key(const wrc_ensemble* E) {
+// Capacity a compact array is grown to for n entries (as ensure_capacity).
+long long grown_capacity(long long n) {
+    long long c = n + n / 4 + 1024;
+    return (c + 255) / 256 * 256;
+}
+
+}  // namespace
+
+wrc_status wrc::batch_init(BatchCtx& C, cudaStream_t main, int nstreams, bool fp32) {
+    C.fp32 = fp32;
+    C.main = main;
+    if (!C.main) {   // keep the batched launches off the legacy default stream
+        BCK(cudaStreamCreateWithFlags(&C.main, cudaStreamNonBlocking));
+        C.own_main = true;
+    }
+    for (int q = 0; q < nstreams; ++q) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        C.streams.push_back(st);
+        BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        C.ev_streams.push_back(ev);
+    }
+    BCK(cudaEventCreateWithFlags(&C.ev_main, cudaEventDisableTiming));
+    return WRC_OK;
+}
+
+void wrc::batch_free(BatchCtx& C) {
+    if (C.main) cudaStreamSynchronize(C.main);
+    for (cudaStream_t st : C.streams) cudaStreamSynchronize(st);
+    for (auto& pe : C.prof) {
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    C.prof.clear();
+    for (cudaEvent_t ev : C.ev_streams) cudaEventDestroy(ev);
+    if (C.ev_main) cudaEventDestroy(C.ev_main);
+    for (cudaStream_t st : C.streams) cudaStreamDestroy(st);
+    if (C.own_main && C.main) cudaStreamDestroy(C.main);
+    if (C.h_args) cudaFreeHost(C.h_args);
+    if (C.d_args) cudaFree(C.d_args);
+    if (C.h_blk) cudaFreeHost(C.h_blk);
+    if (C.d_blk) cudaFree(C.d_blk);
+    C = BatchCtx();
+}
+
+wrc_status wrc::batch_step(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vector<wrc_status>* per_run) {
+    std::vector<wrc_status> local;
+    std::vector<wrc_status>& rs = per_run ? *per_run : local;
+    return C.fp32 ? batch_step_t<float>(C, runs, rs) : batch_step_t<double>(C, runs, rs);
+}
+
+double wrc::batch_take_profile(BatchCtx& C) {
+    if (C.main) cudaStreamSynchronize(C.main);
+    double ms = 0.0;
+    for (auto& pe : C.prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pe.first, pe.second) == cudaSuccess) ms += t;
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    C.prof.clear();
+    return ms;
+}
+
+bool wrc::tuned_shape(bool fp32, long long runs, long long active, int& pt, int& ept) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune_cache.find({fp32, log2_bucket(runs), log2_bucket(active)});
+    if (it == g_tune_cache.end()) return false;
+    pt = it->second.first;
+    ept = it->second.second;
+    return true;
+}
+
+void wrc::store_tuned_shape(bool fp32, long long runs, long long active, int pt, int ept) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tune_cache[{fp32, log2_bucket(runs), log2_bucket(active)}] = {pt, ept};
+}
+
+double wrc::run_bytes_for(const wrc_config& cfg, long long na, long long ng) {
+    const double N = (double)((long long)cfg.n0 << cfg.J) * (double)((long long)cfg.n0 << cfg.J);
+    const double es = cfg.prec == WRC_MIXED ? 4.0 : 8.0;
+    const double m1 = cfg.krylov_m + 1;
+    const double nblk = std::ceil(N / kTile);
+    // L, Lq, psi; complex C1, C2; five byte masks; list and lat2idx; block
+    // counts and offsets; the 2N-double scratch (mixed mode always, FP64 on
+    // the first query that converts a lattice field)
+    double b = 7.0 * es * N + 5.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + 16.0 * N;
+    // FFT tables: twiddles, symbols
+    b += 4.0 * es * std::sqrt(N) + 16.0 * std::sqrt(N);
+    // Krylov small arrays and partial sums (at most kMaxBlocks blocks)
+    b += 8.0 * (m1 * cfg.krylov_m + 33) +
+         8.0 * (double)std::max(krylov_partials_doubles(kMaxBlocks), (size_t)kMaxBlocks * 4);
+    const double c = (double)grown_capacity(na), cg = (double)grown_capacity(ng);
+    // meta x2, omega x2, details, U, V, g, w, basis (m+1), doubles scratch
+    b += c * (8.0 + 2.0 * es + 5.0 * es + es * m1 + 8.0);
+    // ghost rows: length, kGhostRowMax indices and weights; ghost basis values
+    b += cg * (4.0 + (4.0 + 8.0) * kGhostRowMax + es * m1);
+    return b;
+}
+
+double wrc::run_device_bytes(const wrc_run* R) {
+    const wrc_config& cfg = R->cfg;
+    const double N = (double)R->N;
+    const double es = (double)R->es;
+    const double m1 = cfg.krylov_m + 1;
+    const double nblk = std::ceil(N / kTile);
+    double b = 7.0 * es * N + 5.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + (double)R->lat64.bytes;
+    b += 4.0 * es * R->g.NJ + 16.0 * R->g.NJ;
+    b += 8.0 * (m1 * cfg.krylov_m + 33) +
+         8.0 * (double)std::max(krylov_partials_doubles(R->max_blocks), (size_t)kMaxBlocks * 4);
+    const DevBuf* bufs[] = {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga,
+                            &R->det, &R->w, &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb};
+    for (const DevBuf* d : bufs) b += (double)d->bytes;
+    return b;
+}
+
+double wrc::run_updates(const wrc_run* R) { return R->updates; }
+
+bool wrc::run_nonfinite(const wrc_run* R) { return R->nonfinite; }
+
+// ============================================================================
+// Batched ensemble
+// ============================================================================
+
+struct wrc_ensemble {
+    BatchCtx C;
+    std::vector<wrc_run*> members;
+    long long nstep = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_ens_create_error;
+
+wrc_status efail(wrc_ensemble* E, wrc_status s, const std::string& msg) {
+    if (E) E->err = msg;
+    return s;
+}
+
+long long ensemble_active(const wrc_ensemble* E) {
     long long tot = 0;
     for (const wrc_run* R : E->members) tot += R->n_active;
-    return {E->fp32, log2_bucket((long long)E->members.size()), log2_bucket(tot)};
+    return tot;
 }
 
 }  // namespace
@@ -1304,42 +1484,21 @@ wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_str
             return WRC_ERR_ARG;
         }
     wrc_ensemble* E = new wrc_ensemble();
-    E->main = (cudaStream_t)cuda_stream;
-    if (!E->main) {   // keep the batched launches off the legacy default stream
-        if (cudaStreamCreateWithFlags(&E->main, cudaStreamNonBlocking) != cudaSuccess) {
-            g_ens_create_error = "stream creation failed";
-            delete E;
-            return WRC_ERR_CUDA;
-        }
-        E->own_main = true;
-    }
-    E->fp32 = cfgs[0].prec == WRC_MIXED;
     auto cleanup = [&](wrc_status st, const std::string& msg) {
         g_ens_create_error = msg;
         wrc_ensemble_destroy(E);
         return st;
     };
-    const int S = std::min(kEnsStreams, (int)n);
-    for (int q = 0; q < S; ++q) {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-            return cleanup(WRC_ERR_CUDA, "stream creation failed");
-        E->streams.push_back(st);
-        E->ev_streams.push_back(ev);
-    }
-    if (cudaEventCreateWithFlags(&E->ev_main, cudaEventDisableTiming) != cudaSuccess)
-        return cleanup(WRC_ERR_CUDA, "event creation failed");
+    if (batch_init(E->C, (cudaStream_t)cuda_stream, std::min(kBatchStreams, (int)n), cfgs[0].prec == WRC_MIXED) !=
+        WRC_OK)
+        return cleanup(WRC_ERR_CUDA, E->C.err);
+    const int S = (int)E->C.streams.size();
     for (int i = 0; i < n; ++i) {
         wrc_run* R = nullptr;
-        const wrc_status st = wrc_create(&cfgs[i], E->streams[i % S], &R);
+        const wrc_status st = wrc_create(&cfgs[i], E->C.streams[i % S], &R);
         if (st != WRC_OK) return cleanup(st, "member " + std::to_string(i) + ": " + g_create_error);
         E->members.push_back(R);
     }
-    if (cudaMallocHost((void**)&E->h_args, sizeof(KrylovStepArgs) * n) != cudaSuccess ||
-        cudaMalloc((void**)&E->d_args, sizeof(KrylovStepArgs) * n) != cudaSuccess)
-        return cleanup(WRC_ERR_OOM, "argument table allocation failed");
     *out = E;
     return WRC_OK;
 }
@@ -1355,8 +1514,13 @@ wrc_status wrc_ensemble_step(wrc_ensemble* E, int32_t nsteps) {
     if (!E) return WRC_ERR_ARG;
     if (nsteps < 0) return efail(E, WRC_ERR_ARG, "nsteps < 0");
     for (size_t i = 0; i < E->members.size(); ++i)
-        if (!E->members[i]->init) return efail(E, WRC_ERR_STATE, "member " + std::to_string(i) + " has no initial condition");
-    for (int q = 0; q < nsteps; ++q) TRY(E->fp32 ? ensemble_step_once<float>(E) : ensemble_step_once<double>(E));
+        if (!E->members[i]->init)
+            return efail(E, WRC_ERR_STATE, "member " + std::to_string(i) + " has no initial condition");
+    for (int q = 0; q < nsteps; ++q) {
+        const wrc_status st = batch_step(E->C, E->members, nullptr);
+        if (st != WRC_OK) return efail(E, st, E->C.err);
+        E->nstep += 1;
+    }
     return WRC_OK;
 }
 
@@ -1365,61 +1529,47 @@ wrc_status wrc_ensemble_set_shape(wrc_ensemble* E, int32_t threads_per_block, in
     if ((threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256) || points_per_thread < 1 ||
         points_per_thread > 64)
         return efail(E, WRC_ERR_ARG, "threads_per_block must be 64, 128 or 256; points_per_thread 1..64");
-    E->pt = threads_per_block;
-    E->ept = points_per_thread;
+    E->C.pt = threads_per_block;
+    E->C.ept = points_per_thread;
     return WRC_OK;
 }
 
 wrc_status wrc_ensemble_tune(wrc_ensemble* E, int32_t steps_per_candidate, int32_t out_shape[2]) {
     if (!E) return WRC_ERR_ARG;
     if (steps_per_candidate < 1) return efail(E, WRC_ERR_ARG, "steps_per_candidate < 1");
-    const TuneKey key = tune_key(E);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mutex);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            E->pt = it->second.first;
-            E->ept = it->second.second;
-            if (out_shape) {
-                out_shape[0] = E->pt;
-                out_shape[1] = E->ept;
-            }
-            return WRC_OK;
+    const long long nmem = (long long)E->members.size(), nact = ensemble_active(E);
+    int cpt = 0, cept = 0;
+    if (tuned_shape(E->C.fp32, nmem, nact, cpt, cept)) {
+        E->C.pt = cpt;
+        E->C.ept = cept;
+        if (out_shape) {
+            out_shape[0] = cpt;
+            out_shape[1] = cept;
         }
+        return WRC_OK;
     }
     const int pts[3] = {64, 128, 256};
     const int epts[3] = {1, 2, 4};
     double best = 1e300;
-    int bpt = E->pt, bept = E->ept;
+    int bpt = E->C.pt, bept = E->C.ept;
+    batch_take_profile(E->C);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            E->pt = pts[a];
-            E->ept = epts[b];
-            E->profiling = true;
+            E->C.pt = pts[a];
+            E->C.ept = epts[b];
+            E->C.profiling = true;
             TRY(wrc_ensemble_step(E, steps_per_candidate));
-            ECK(cudaStreamSynchronize(E->main));
-            double ms = 0.0;
-            for (auto& pe : E->prof) {
-                float t = 0.f;
-                ECK(cudaEventElapsedTime(&t, pe.first, pe.second));
-                ms += t;
-                cudaEventDestroy(pe.first);
-                cudaEventDestroy(pe.second);
-            }
-            E->prof.clear();
-            E->profiling = false;
+            const double ms = batch_take_profile(E->C);
+            E->C.profiling = false;
             if (ms < best) {
                 best = ms;
                 bpt = pts[a];
                 bept = epts[b];
             }
         }
-    E->pt = bpt;
-    E->ept = bept;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[key] = {bpt, bept};
-    }
+    E->C.pt = bpt;
+    E->C.ept = bept;
+    store_tuned_shape(E->C.fp32, nmem, nact, bpt, bept);
     if (out_shape) {
         out_shape[0] = bpt;
         out_shape[1] = bept;
@@ -1429,31 +1579,20 @@ wrc_status wrc_ensemble_tune(wrc_ensemble* E, int32_t steps_per_candidate, int32
 
 wrc_status wrc_ensemble_stats(wrc_ensemble* E, int64_t out[6]) {
     if (!E || !out) return WRC_ERR_ARG;
-    long long tot = 0;
-    for (const wrc_run* R : E->members) tot += R->n_active;
     out[0] = (int64_t)E->members.size();
-    out[1] = tot;
+    out[1] = ensemble_active(E);
     out[2] = E->nstep;
-    out[3] = E->last_blocks;
-    out[4] = E->pt;
-    out[5] = E->ept;
+    out[3] = E->C.last_blocks;
+    out[4] = E->C.pt;
+    out[5] = E->C.ept;
     return WRC_OK;
 }
 
 wrc_status wrc_ensemble_profile(wrc_ensemble* E, int32_t enable, double* ms_out) {
     if (!E) return WRC_ERR_ARG;
-    ECK(cudaStreamSynchronize(E->main));
-    double ms = 0.0;
-    for (auto& pe : E->prof) {
-        float t = 0.f;
-        ECK(cudaEventElapsedTime(&t, pe.first, pe.second));
-        ms += t;
-        cudaEventDestroy(pe.first);
-        cudaEventDestroy(pe.second);
-    }
-    E->prof.clear();
+    const double ms = batch_take_profile(E->C);
     if (ms_out) *ms_out = ms;
-    E->profiling = enable != 0;
+    E->C.profiling = enable != 0;
     return WRC_OK;
 }
 
@@ -1461,21 +1600,10 @@ const char* wrc_ensemble_last_error(const wrc_ensemble* E) { return E ? E->err.c
 
 void wrc_ensemble_destroy(wrc_ensemble* E) {
     if (!E) return;
-    if (E->main) cudaStreamSynchronize(E->main);
-    for (cudaStream_t st : E->streams) cudaStreamSynchronize(st);
+    if (E->C.main) cudaStreamSynchronize(E->C.main);
+    for (cudaStream_t st : E->C.streams) cudaStreamSynchronize(st);
     for (wrc_run* R : E->members) wrc_destroy(R);
-    for (auto& pe : E->prof) {
-        cudaEventDestroy(pe.first);
-        cudaEventDestroy(pe.second);
-    }
-    for (cudaEvent_t ev : E->ev_streams) cudaEventDestroy(ev);
-    if (E->ev_main) cudaEventDestroy(E->ev_main);
-    for (cudaStream_t st : E->streams) cudaStreamDestroy(st);
-    if (E->own_main && E->main) cudaStreamDestroy(E->main);
-    if (E->h_args) cudaFreeHost(E->h_args);
-    if (E->d_args) cudaFree(E->d_args);
-    if (E->h_blk) cudaFreeHost(E->h_blk);
-    if (E->d_blk) cudaFree(E->d_blk);
+    batch_free(E->C);
     delete E;
 }
 

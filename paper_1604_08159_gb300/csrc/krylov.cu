@@ -129,8 +129,14 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
 // Taylor series: with s = max(1, ceil(|M|_1)), B = M / s has |B|_1 <= 1,
 // x <- sum_{i<=20} B^i x / i!  applied s times; the dropped tail is at most
 // sum_{i>20} 1/i! < 2e-20 of |x| per sub-step.  One warp, lane r holds row r.
+// Largest scaling count of the Taylor evaluation: a step with |dt H|_1 above
+// it (or not finite) has blown up; phi_1 is then not evaluated, y is set to
+// NaN and the non-finite flag is raised, so that the step fails cleanly
+// instead of looping ceil(|dt H|_1) times.
+constexpr double kMaxPhiScale = 4096.0;
+
 __device__ __forceinline__ void phi1_warp(const double* __restrict__ H, const int* __restrict__ kstop, int m,
-                                          double dt, double* __restrict__ y) {
+                                          double dt, double* __restrict__ y, int* __restrict__ flags) {
     const int lane = threadIdx.x;
     const int k = *kstop;
     if (k <= 0) {
@@ -153,6 +159,11 @@ __device__ __forceinline__ void phi1_warp(const double* __restrict__ H, const in
         for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
         nrm = fmax(nrm, cs);
     }
+    if (!(nrm <= kMaxPhiScale)) {
+        if (lane == 0) atomicOr(flags, 1);
+        if (lane < m) y[lane] = lane < k ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+        return;
+    }
     const int s = nrm > 1.0 ? (int)ceil(nrm) : 1;
     const double inv_s = 1.0 / s;
     double x = lane == k ? 1.0 : 0.0;
@@ -171,8 +182,8 @@ __device__ __forceinline__ void phi1_warp(const double* __restrict__ H, const in
 }
 
 __global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const int* __restrict__ kstop, int m,
-                                             double dt, double* __restrict__ y) {
-    phi1_warp(H, kstop, m, dt, y);
+                                             double dt, double* __restrict__ y, int* __restrict__ flags) {
+    phi1_warp(H, kstop, m, dt, y, flags);
 }
 
 // omega <- omega + dt beta V_k y (accumulated in FP64), also written into the
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __
 // phi_1 for problem blockIdx.x of a batch (one warp each).
 __global__ void __launch_bounds__(32) k_phi1_batch(const KrylovStepArgs* __restrict__ args) {
     const KrylovStepArgs& A = args[blockIdx.x];
-    phi1_warp(A.H, A.kstop, A.m, A.dt, A.y);
+    phi1_warp(A.H, A.kstop, A.m, A.dt, A.y, A.flags);
 }
 
 // Update of problem blockIdx.y of a batch.
@@ -427,7 +438,7 @@ cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStrea
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT>, dim3(blocks), dim3(kPT), params, 0, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_phi1<<<1, 32, 0, s>>>(args.H, args.kstop, args.m, args.dt, args.y);
+    k_phi1<<<1, 32, 0, s>>>(args.H, args.kstop, args.m, args.dt, args.y, args.flags);
     note_launch();
     k_update<T><<<blocks_for(args.n), kThreads, 0, s>>>((const T*)args.basis, args.ld, args.y, args.beta, args.kstop,
                                                         args.dt, args.meta, args.n, (T*)args.omega, (T*)args.L);

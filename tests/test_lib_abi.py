@@ -76,3 +76,54 @@ def test_ensemble_create_rejects_bad_arguments_without_gpu(lib):
     assert b"precision" in lib.wrc_ensemble_last_error(None)
     assert lib.wrc_ensemble_step(None, 1) == -1
     lib.wrc_ensemble_destroy(None)
+
+
+def _cfg(n0=32, J=2, prec=0, m=30):
+    return B.WrcConfig(n0, J, m, 2, prec, 0, 1e-4, 5000.0, 0.17, 0.0, 0.0, 1e-2)
+
+
+def test_server_estimate_is_host_arithmetic_and_ordered(lib):
+    est = {}
+    for J in range(2, 8):
+        for prec in (0, 1):
+            est[J, prec] = B.wrc_server_estimate(_cfg(J=J, prec=prec))
+    for J in range(2, 8):
+        # FP32 bulk arrays halve most of the footprint
+        assert est[J, 1] < est[J, 0]
+        if J > 2:
+            assert est[J, 0] > est[J - 1, 0]
+    # large lattices: the lattice arrays dominate, so doubling NJ takes ~4x
+    assert 3.5 < est[7, 0] / est[6, 0] < 4.5
+    # a run holds at least its seven bulk lattice arrays and five byte masks
+    N = 4096 ** 2
+    assert est[7, 0] > (7 * 8 + 5) * N and est[7, 1] > (7 * 4 + 5) * N
+    # and 150 GB admits dozens of the largest runs, not thousands
+    assert 20 < 150e9 / est[7, 1] < 200
+    with pytest.raises(B.WrcError):
+        B.wrc_server_estimate(_cfg(n0=6))
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("policy", 5, "policy"),
+    ("max_slots", 0, "max_slots"),
+    ("max_slots", 5000, "max_slots"),
+    ("threads_per_block", 96, "threads_per_block"),
+    ("points_per_thread", 3, "threads_per_block"),   # shape given by half
+    ("hbm_budget_bytes", 0.0, "budget"),
+])
+def test_server_create_rejects_bad_config_without_gpu(lib, field, value, msg):
+    cfg = B.WrcServerConfig(0, 16, 0, 0, 150e9)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.wrc_server_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert h.value is None
+    assert msg in lib.wrc_server_last_error(None).decode()
+
+
+def test_server_null_handles(lib):
+    rid = ctypes.c_int64()
+    assert lib.wrc_server_submit(None, None, 1, None, None, None, None, 1, 0.0, ctypes.byref(rid)) == -1
+    assert lib.wrc_server_wait(None, -1, 1.0) == -1
+    assert lib.wrc_server_query(None, 0, None) == -1
+    assert lib.wrc_server_stats(None, None) == -1
+    lib.wrc_server_destroy(None)
