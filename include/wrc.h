@@ -185,8 +185,21 @@ wrc_status wrc_query_stats(wrc_run* run, int64_t out[4]);
 /* Event timing of the Krylov part of each step (the cooperative Arnoldi
  * kernel, phi_1 and the update): when enabled, each step's Krylov launches
  * are bracketed by CUDA events on the run's stream; enabling or disabling
- * clears the record. */
+ * clears the record.  enable = 2 also traces the phases of the cooperative
+ * kernel (wrc_query_phase_trace); 0 disables, 1 times only.  WRC_ERR_ARG for
+ * other values. */
 wrc_status wrc_profile(wrc_run* run, int32_t enable);
+
+/* Phase trace of the last cooperative Krylov launch of the run (profiling
+ * mode 2): for each grid barrier p it passed, out[4p..4p+3] = the first and
+ * the last arrival of its blocks, the index of the last block to arrive, and
+ * the release of block 0, in microseconds from the start of block 0 (device
+ * global timer).  Barrier 0 follows b = A_n omega + g, barrier 1 the ghost
+ * values of v_0; then each Arnoldi step has three: after the first dots,
+ * after the second dots, after the new basis vector.  *nphases receives the
+ * count.  WRC_ERR_ARG if cap < 4 * count; WRC_ERR_STATE without a traced
+ * launch.  Synchronises. */
+wrc_status wrc_query_phase_trace(wrc_run* run, double* out, int32_t cap, int32_t* nphases);
 
 /* Profile record since wrc_profile(run, 1): out[0] Krylov launches timed,
  * out[1] their total device time in ms, out[2] their algorithmic bytes (per

@@ -66,6 +66,7 @@ SIGNATURES = {
     "wrc_query_stats": (c_int32, [c_void_p, c_void_p]),
     "wrc_profile": (c_int32, [c_void_p, c_int32]),
     "wrc_query_profile": (c_int32, [c_void_p, c_void_p]),
+    "wrc_query_phase_trace": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_destroy": (None, [c_void_p]),
     "wrc_lattice_diagnostics_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
@@ -257,14 +258,25 @@ def wrc_query_stats(run):
     return {"launches": int(out[0]), "steps": int(out[1]), "host_syncs": int(out[2]), "n_active": int(out[3])}
 
 
-def wrc_profile(run, enable: bool):
-    _check("wrc_profile", load().wrc_profile(run, 1 if enable else 0), run)
+def wrc_profile(run, enable):
+    """enable: False/0 off, True/1 event timing, 2 timing and phase trace."""
+    _check("wrc_profile", load().wrc_profile(run, int(enable)), run)
 
 
 def wrc_query_profile(run):
     out = np.zeros(4)
     _check("wrc_query_profile", load().wrc_query_profile(run, out.ctypes.data), run)
     return {"launches": int(out[0]), "ms": float(out[1]), "bytes": float(out[2]), "flops": float(out[3])}
+
+
+def wrc_query_phase_trace(run):
+    """Per grid barrier of the last traced Krylov launch: (first arrival,
+    last arrival, last block, release of block 0) in microseconds."""
+    cap = 4 * 128
+    out = np.zeros(cap)
+    n = c_int32()
+    _check("wrc_query_phase_trace", load().wrc_query_phase_trace(run, out.ctypes.data, cap, byref(n)), run)
+    return out[:4 * n.value].reshape(n.value, 4)
 
 
 def wrc_last_error(run) -> str:
@@ -381,6 +393,9 @@ class Run:
 
     def profile_record(self):
         return wrc_query_profile(self.h)
+
+    def phase_trace(self):
+        return wrc_query_phase_trace(self.h)
 
 
 def wrc_lattice_diagnostics_noalloc(omega_lattice, psi_lattice, NJ: int, out, stream: int | None = None):

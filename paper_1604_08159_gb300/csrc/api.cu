@@ -136,6 +136,9 @@ struct wrc_run {
 
     // event timing of the Gram-Schmidt passes (wrc_profile)
     bool profiling = false;
+    bool tracing = false;    // phase trace of the Krylov kernel (wrc_profile mode 2)
+    DevBuf trace;
+    int trace_nb = 0;        // blocks of the traced launch
     std::vector<cudaEvent_t> ev_pool;
     // CUDA graphs of the step phases, per phase and ping-pong parity; rebuilt
     // when a buffer they use is reallocated (layout) or eps changes
@@ -521,7 +524,16 @@ KrylovStepArgs krylov_args(wrc_run* R) {
     A.dt = R->cfg.dt;
     A.tol = kBreakdownTol;
     A.limit_ns = 2000000000ull;
+    A.trace = R->tracing ? R->trace.as<unsigned long long>() : nullptr;
     return A;
+}
+
+// Clear the phase trace before a traced launch (on the run's stream).
+wrc_status trace_reset(wrc_run* R, int nb) {
+    if (!R->tracing) return WRC_OK;
+    R->trace_nb = nb;
+    CK(cudaMemsetAsync(R->trace.p, 0, R->trace.bytes, R->st));
+    return WRC_OK;
 }
 
 // Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
@@ -533,6 +545,7 @@ wrc_status krylov(wrc_run* R) {
     const int m = R->cfg.krylov_m;
     const KrylovStepArgs A = krylov_args(R);
     const int blocks = krylov_step_blocks(n, R->max_blocks);
+    TRY(trace_reset(R, blocks));
     int e0 = -1;
     if (R->profiling) {
         while (R->ev_pool.size() < R->ev_used.size() * 2 + 2) {
@@ -730,7 +743,7 @@ void free_run(wrc_run* R) {
     cudaStream_t s = R->st;
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
-                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64})
+                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list, R->lat2idx,
@@ -1074,9 +1087,47 @@ wrc_status wrc_query_stats(wrc_run* R, int64_t out[4]) {
 
 wrc_status wrc_profile(wrc_run* R, int32_t enable) {
     if (!R) return WRC_ERR_ARG;
+    if (enable < 0 || enable > 2) return fail(R, WRC_ERR_ARG, "enable must be 0, 1 or 2");
     CK(cudaStreamSynchronize(R->st));
     R->profiling = enable != 0;
+    R->tracing = enable == 2;
+    if (R->tracing) {
+        const size_t words = 1 + (size_t)kTracePhases * (kMaxBlocks + 1);
+        CK(R->trace.grow(sizeof(unsigned long long) * words, 0, R->st));
+    }
     R->ev_used.clear();
+    return WRC_OK;
+}
+
+wrc_status wrc_query_phase_trace(wrc_run* R, double* out, int32_t cap, int32_t* nphases) {
+    if (!R || !out || !nphases) return WRC_ERR_ARG;
+    if (!R->tracing || !R->trace_nb) return fail(R, WRC_ERR_STATE, "no traced Krylov launch (wrc_profile(run, 2))");
+    CK(cudaStreamSynchronize(R->st));
+    const int nb = R->trace_nb;
+    std::vector<unsigned long long> h(1 + (size_t)kTracePhases * (nb + 1));
+    CK(cudaMemcpy(h.data(), R->trace.p, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost));
+    const unsigned long long t0 = h[0];
+    int np = 0;
+    for (int p = 0; p < kTracePhases; ++p) {
+        const unsigned long long* row = h.data() + 1 + (size_t)p * (nb + 1);
+        if (row[nb] == 0) break;   // block 0 never left barrier p
+        if (4 * (p + 1) > cap) return fail(R, WRC_ERR_ARG, "cap too small for the traced phases");
+        unsigned long long lo = ~0ull, hi = 0;
+        int who = 0;
+        for (int b = 0; b < nb; ++b) {
+            lo = std::min(lo, row[b]);
+            if (row[b] > hi) {
+                hi = row[b];
+                who = b;
+            }
+        }
+        out[4 * p + 0] = 1e-3 * (double)(lo - t0);
+        out[4 * p + 1] = 1e-3 * (double)(hi - t0);
+        out[4 * p + 2] = (double)who;
+        out[4 * p + 3] = 1e-3 * (double)(row[nb] - t0);
+        np = p + 1;
+    }
+    *nphases = np;
     return WRC_OK;
 }
 
@@ -1199,6 +1250,12 @@ wrc_status batch_krylov(BatchCtx& C, const std::vector<wrc_run*>& live) {
     for (size_t i = 0; i < M; ++i) {
         C.h_args[i] = krylov_args(live[i]);
         max_n = std::max(max_n, (int)live[i]->n_active);
+        if (live[i]->tracing) {
+            const int nbi = C.h_blk[total + i + 1] - C.h_blk[total + i];
+            wrc_run* R = live[i];
+            R->trace_nb = nbi;
+            BCK(cudaMemsetAsync(R->trace.p, 0, R->trace.bytes, C.main));
+        }
     }
     BCK(cudaMemcpyAsync(C.d_args, C.h_args, sizeof(KrylovStepArgs) * M, cudaMemcpyHostToDevice, C.main));
     BCK(cudaMemcpyAsync(C.d_blk, C.h_blk, sizeof(int) * (total + M + 1), cudaMemcpyHostToDevice, C.main));

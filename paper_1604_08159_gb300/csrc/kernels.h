@@ -133,7 +133,13 @@ struct KrylovStepArgs {
     int m;
     double dt, tol;
     unsigned long long limit_ns;
+    // phase trace (profiling; nullptr when off): trace[0] the start of block
+    // 0, then per grid barrier p the arrival time of each block b at
+    // trace[1 + p (nb + 1) + b] and block 0's release at trace[1 + p (nb + 1) + nb]
+    // (globaltimer ns), for at most kTracePhases barriers
+    unsigned long long* trace;
 };
+constexpr int kTracePhases = 2 + 3 * 31;
 int krylov_step_init(bool fp32, int* max_blocks);
 int krylov_step_blocks(long long n, int max_blocks);
 template <typename T>

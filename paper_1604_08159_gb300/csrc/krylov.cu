@@ -37,9 +37,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // *err, and every waiter leaves as soon as *err is non-zero, so the kernel
 // always returns.
 // The barrier spans the nb blocks of one problem (bid = block index within it).
-__device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, int bid, int nb) {
+// With a trace buffer, the arrival of each block and the release of block 0
+// are stamped (phase index `ph`, counted by the caller).
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, int bid, int nb,
+                          unsigned long long* trace = nullptr, int ph = 0) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (trace && ph < kTracePhases) trace[1 + (size_t)ph * (nb + 1) + bid] = gtimer();
         const unsigned inc = bid == 0 ? 0x80000000u - (unsigned)(nb - 1) : 1u;
         __threadfence();
         const unsigned old = atomicAdd(bar, inc);
@@ -54,6 +58,7 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, 
             }
         }
         __threadfence();
+        if (trace && ph < kTracePhases && bid == 0) trace[1 + (size_t)ph * (nb + 1) + nb] = gtimer();
     }
     __syncthreads();
     return *(volatile int*)err == 0;
@@ -100,7 +105,11 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
 
 // Sum over all blocks of part[b * kOutP + t], t < nout, into s_out: lane t
 // of warp w adds blocks w, w + nwarps, ... in order (one output per lane), the
-// warps' sums are then added in warp order.  Same order in every block.
+// warps' sums are then added in warp order.  Same order in every block.  The
+// loads go out kReduceBatch at a time ahead of their (ordered) additions, so
+// a block pays one L2 round trip per batch rather than one per partial.
+constexpr int kReduceBatch = 16;
+
 template <int PT>
 __device__ __forceinline__ void reduce_all(const double* part, int nout, double* s_out,
                                            double (*s_red)[kNV + 1], int nb) {
@@ -109,8 +118,25 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
     for (int t0 = 0; t0 < nout; t0 += 32) {
         const int t = t0 + lane;
         double v = 0.0;
-        if (t < nout)
-            for (int b = wid; b < nb; b += kW) v += __ldcg(part + (size_t)b * kOutP + t);
+        if (t < nout) {
+            const double* p = part + t;
+            int b = wid;
+            for (; b + (kReduceBatch - 1) * kW < nb; b += kReduceBatch * kW) {
+                double x[kReduceBatch];
+#pragma unroll
+                for (int u = 0; u < kReduceBatch; ++u) x[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
+#pragma unroll
+                for (int u = 0; u < kReduceBatch; ++u) v += x[u];
+            }
+            const int rest = b < nb ? (nb - 1 - b) / kW + 1 : 0;   // < kReduceBatch
+            double x[kReduceBatch];
+#pragma unroll
+            for (int u = 0; u < kReduceBatch; ++u)
+                if (u < rest) x[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
+#pragma unroll
+            for (int u = 0; u < kReduceBatch; ++u)
+                if (u < rest) v += x[u];
+        }
         if (t < nout) s_red[wid][t] = v;
     }
     __syncthreads();
@@ -213,10 +239,72 @@ __global__ void k_update(const T* __restrict__ basis, long long ld, const double
     update_body<T>(basis, ld, y, beta, kstop, dt, meta, n, omega, L, blockIdx.x, gridDim.x);
 }
 
-// x - c v in the bulk type: FP64 for the plain mode, FP32 (coefficient
-// rounded) for the mixed mode.
-__device__ __forceinline__ double axmy(double x, double v, double c) { return x - v * c; }
-__device__ __forceinline__ float axmy(float x, float v, double c) { return x - v * (float)c; }
+
+// x - sum_{t < nv} c_t v_t for the basis values v_t = basis[t ld] of one
+// point, in the bulk type: four interleaved partial sums of the projections
+// (short dependency chains; FP64 issues one warp instruction per 16 cycles
+// per SM on this part), then subtracted at once.
+template <typename T>
+__device__ __forceinline__ T project_out(T x, const T* __restrict__ col, long long ld, const double* c, int nv) {
+    T p[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int t = 0; t < kNV; ++t)
+        if (t < nv) p[t & 3] += col[(size_t)t * ld] * (T)c[t];
+    return x - ((p[0] + p[1]) + (p[2] + p[3]));
+}
+
+// Ghost values of one Krylov vector.  The ghosts of a problem are dealt out
+// round-robin over its blocks (ghost t to block t mod nb); inside a block
+// each ghost goes to a group of kGhostLanes consecutive lanes, which split
+// its interpolation row (row_idx/row_w over the active values x) and the
+// correction sum_{q<nc} c_q Gb[q][t], fetch their terms kGatherLane at a time
+// ahead of the additions, and combine the lane sums by shuffles.  Returns,
+// for lane 0 of each group with a ghost, the value in *out and its index in
+// *tg (-1 otherwise).  Called by every thread of the block (warp-uniform loop).
+constexpr int kGhostLanes = 4;
+constexpr int kGatherLane = 8;
+
+template <typename T, int PT, typename F>
+__device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* __restrict__ x,
+                                             const T* __restrict__ Gb, long long ldg, const double* c, int nc,
+                                             int bid, int nb, F&& emit) {
+    constexpr int kGroups = PT / kGhostLanes;                 // ghosts per block per pass
+    constexpr int kPerWarp = 32 / kGhostLanes;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gl = lane % kGhostLanes;
+    for (int q0 = wid * kPerWarp; bid + (long long)nb * q0 < A.ng; q0 += kGroups) {
+        const long long tl = bid + (long long)nb * (q0 + lane / kGhostLanes);
+        const bool valid = tl < A.ng;
+        const int t = valid ? (int)tl : 0;
+        const int rl = valid ? A.row_len[t] : 0;
+        const size_t base = (size_t)t * A.rmax;
+        double part = 0.0;
+        for (int e0 = 0; e0 < A.rmax; e0 += kGhostLanes * kGatherLane) {
+            if (!__any_sync(0xffffffffu, e0 < rl)) break;
+            int id[kGatherLane];
+            double wt[kGatherLane], xv[kGatherLane];
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u) {
+                const int e = e0 + gl + kGhostLanes * u;
+                if (e < rl) {
+                    id[u] = A.row_idx[base + e];
+                    wt[u] = A.row_w[base + e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u)
+                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)__ldcg(x + id[u]);
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u)
+                if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
+        }
+        if (valid)
+            for (int q = gl; q < nc; q += kGhostLanes) part -= c[q] * (double)Gb[(size_t)q * ldg + t];
+#pragma unroll
+        for (int o = 1; o < kGhostLanes; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (valid && gl == 0) emit(t, part);
+    }
+}
 
 // The Krylov step of one problem, run by its nb blocks (bid = this block's
 // index among them).
@@ -233,17 +321,20 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_red[PT / 32][kNV + 1];
     __shared__ double s_h[kOutP];
     __shared__ double s_c[kNV];
+    __shared__ double s_sc[4];   // beta, 1/beta, h_{j+1,j}, 1/h_{j+1,j}
+    __shared__ int s_stop;       // 0 go on, 1 happy breakdown, 2 non-finite
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
     const bool lead = bid == 0 && threadIdx.x == 0;
     double* P0 = A.part;
     double* P1 = P0 + (size_t)nb * kOutP;
-    double* P2 = P1 + (size_t)nb * kOutP;
     const T nu = (T)A.nu, r = (T)A.r, c1J = (T)A.c1J, c2J = (T)A.c2J;
     const int m = A.m;
     const long long ld = A.ld, ldg = A.ldg;
     double acc[kNV + 1];
+    int ph = 0;   // grid barriers passed (phase trace)
+    if (lead && A.trace) A.trace[0] = gtimer();
     if (*(volatile const int*)A.row_overflow) {
         if (lead) atomicOr(A.err, 4);
         return;
@@ -261,9 +352,17 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         acc[kNV] += (double)v * (double)v;
     }
     block_partials<PT>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
-    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
     reduce_all<PT>(P0, 1, s_h, s_red, nb);
-    const double beta = sqrt(s_h[0]);
+    // scalars of the step, once per block (FP64 division and square root
+    // are long instruction sequences on this part)
+    if (threadIdx.x == 0) {
+        const double bt = sqrt(s_h[0]);
+        s_sc[0] = bt;
+        s_sc[1] = 1.0 / bt;
+    }
+    __syncthreads();
+    const double beta = s_sc[0];
     int k = m;
     if (!(beta > 0.0) || !isfinite(beta)) {
         k = 0;
@@ -274,22 +373,18 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     if (k > 0) {
         // v_0 = b / beta at the active points and, through the interpolation
         // rows, at the ghosts
-        const double inv = 1.0 / beta;
+        const double inv = s_sc[1];
         for (int a = a0; a < n; a += stride) {
             const T v = (T)((double)w[a] * inv);
             basis[a] = v;
             Lq[meta_pos(A.meta[a])] = v;
         }
-        for (int t = a0; t < A.ng; t += stride) {
-            const int rl = A.row_len[t];
-            double gv = 0.0;
-            for (int e = 0; e < rl; ++e)
-                gv += A.row_w[(size_t)t * A.rmax + e] * (double)__ldcg(w + A.row_idx[(size_t)t * A.rmax + e]);
+        ghost_values<T, PT>(A, w, Gb, ldg, s_c, 0, bid, nb, [&](int t, double gv) {
             const T g = (T)(gv * inv);
             Gb[t] = g;
             Lq[A.glist[t]] = g;
-        }
-        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+        });
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
         for (int j = 0; j < m; ++j) {
             const int nv = j + 1;
             // phase 1: w = A v_j and the first Gram-Schmidt dots
@@ -305,7 +400,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                 acc[kNV] += vd * vd;
             }
             block_partials<PT>(acc, nv, P0 + (size_t)bid * kOutP, s_red);
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
             reduce_all<PT>(P0, nv + 1, s_h, s_red, nb);
             const double wn2 = s_h[nv];
             for (int t = threadIdx.x; t < nv; t += blockDim.x) s_c[t] = s_h[t];
@@ -314,10 +409,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
 #pragma unroll
             for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
             for (int a = a0; a < n; a += stride) {
-                T x = w[a];
-#pragma unroll
-                for (int t = 0; t < kNV; ++t)
-                    if (t < nv) x = axmy(x, basis[(size_t)t * ld + a], s_c[t]);
+                const T x = project_out<T>(w[a], basis + a, ld, s_c, nv);
                 w[a] = x;
                 const double xd = (double)x;
 #pragma unroll
@@ -326,56 +418,59 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                 acc[kNV] += xd * xd;
             }
             block_partials<PT>(acc, nv, P1 + (size_t)bid * kOutP, s_red);
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
             reduce_all<PT>(P1, nv + 1, s_h, s_red, nb);
-            // h_{:,j} = h1 + h2; |w''|^2 = |w'|^2 - |h2|^2 (V orthonormal, h2 = V^T w')
-            bool bad = false;
-            double h2n = 0.0;
-            for (int t = 0; t < nv; ++t) {
-                bad |= !isfinite(s_c[t] + s_h[t]);
-                h2n += s_h[t] * s_h[t];
-            }
-            const double hn = sqrt(fmax(s_h[nv] - h2n, 0.0));
-            if (bid == 0) {
-                for (int t = threadIdx.x; t < nv; t += blockDim.x) A.H[(size_t)t * m + j] = s_c[t] + s_h[t];
-                if (threadIdx.x == 0) A.H[(size_t)(j + 1) * m + j] = hn;
+            // h_{:,j} = h1 + h2; |w''|^2 = |w'|^2 - |h2|^2 (V orthonormal,
+            // h2 = V^T w'), the breakdown tests and 1/h_{j+1,j}: warp 0, once
+            if (threadIdx.x < 32) {
+                const int t = threadIdx.x;
+                double h2 = 0.0;
+                bool bad = false;
+                if (t < nv) {
+                    h2 = s_h[t] * s_h[t];
+                    bad = !isfinite(s_c[t] + s_h[t]);
+                    if (bid == 0) A.H[(size_t)t * m + j] = s_c[t] + s_h[t];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+                bad = __any_sync(0xffffffffu, bad);
+                if (t == 0) {
+                    const double hn = sqrt(fmax(s_h[nv] - h2, 0.0));
+                    s_sc[2] = hn;
+                    s_sc[3] = 1.0 / hn;
+                    s_stop = (bad || !isfinite(hn)) ? 2 : (hn <= A.tol * sqrt(wn2) ? 1 : 0);
+                    if (bid == 0) A.H[(size_t)(j + 1) * m + j] = hn;
+                }
             }
             __syncthreads();
             for (int t = threadIdx.x; t < nv; t += blockDim.x) s_c[t] = s_h[t];
+            const int stop = s_stop;
             __syncthreads();
-            if (bad || !isfinite(hn)) {
+            if (stop == 2) {
                 if (lead) atomicOr(A.flags, 1);
                 k = j + 1;
                 break;
             }
-            if (hn <= A.tol * sqrt(wn2)) {
+            if (stop == 1) {
                 k = j + 1;
                 break;
             }
             if (j + 1 == m) break;
             // phase 3: v_{j+1} = (w' - V h2) / hn at the active points; at the
             // ghosts by linearity from w' and the ghost values of v_0..v_j
-            const double inv2 = 1.0 / hn;
+            const double inv2 = s_sc[3];
             for (int a = a0; a < n; a += stride) {
-                T x = w[a];
-#pragma unroll
-                for (int t = 0; t < kNV; ++t)
-                    if (t < nv) x = axmy(x, basis[(size_t)t * ld + a], s_c[t]);
+                const T x = project_out<T>(w[a], basis + a, ld, s_c, nv);
                 const T v = (T)((double)x * inv2);
                 basis[(size_t)(j + 1) * ld + a] = v;
                 Lq[meta_pos(A.meta[a])] = v;
             }
-            for (int t = a0; t < A.ng; t += stride) {
-                const int rl = A.row_len[t];
-                double gv = 0.0;
-                for (int e = 0; e < rl; ++e)
-                    gv += A.row_w[(size_t)t * A.rmax + e] * (double)__ldcg(w + A.row_idx[(size_t)t * A.rmax + e]);
-                for (int q = 0; q < nv; ++q) gv -= s_c[q] * (double)Gb[(size_t)q * ldg + t];
+            ghost_values<T, PT>(A, w, Gb, ldg, s_c, nv, bid, nb, [&](int t, double gv) {
                 const T g = (T)(gv * inv2);
                 Gb[(size_t)(j + 1) * ldg + t] = g;
                 Lq[A.glist[t]] = g;
-            }
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb)) return;
+            });
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
         }
     }
     if (lead) *A.kstop = k;
