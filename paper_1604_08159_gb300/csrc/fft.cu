@@ -1,9 +1,22 @@
 // Streamfunction solve on the periodic finest lattice: psi = L_h^{-1}(-(R - mean R))
-// with L_h the 4th-order collocation Laplacian, diagonalised by the 2-D DFT.
-// Five passes: real rows -> FFT along x, transpose, FFT along y / divide by the
-// symbol / inverse FFT along y (one CTA per row, all in shared memory),
-// transpose back, inverse FFT along x -> real part.  Radix-2 FFTs run in
-// shared memory, one CTA per row of up to 4096 complex values.
+// with L_h the 4th-order collocation Laplacian (the Sec. 2.5 stencil at h_J),
+// diagonalised by the 2-D DFT.
+//
+// The lattice field is real, so two rows share one complex FFT along x and
+// only the kx = 0 .. n/2 half of each row's spectrum is kept, kx = n/2 packed
+// into the imaginary part of the kx = 0 bin (both bins are real):
+//   1. rows (2q, 2q+1) -> half spectra            (n/2 transforms along x)
+//   2. transpose n x n/2 -> n/2 x n
+//   3. per column kx: FFT along y, divide by the symbol, inverse FFT along y
+//      (n/2 transforms; optionally also the full spectra of U + i V and of
+//      S11 + i S12, two columns kx and n - kx from each half column)
+//   4. transpose back, 5. inverse FFT along x of two real rows at a time.
+// Each FFT runs radix-16 Stockham passes (a radix-2/4/8 pass first when log2 n
+// is not a multiple of 4) on 16 values per thread held in registers, and
+// exchanges them through padded shared memory between passes (two exchanges
+// for n = 4096); no bit reversal.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace wrc {
@@ -17,191 +30,532 @@ template <typename T> using cx_t = typename Cx<T>::type;
 
 template <typename C>
 __device__ __forceinline__ C mk(decltype(C{}.x) a, decltype(C{}.x) b) { C c; c.x = a; c.y = b; return c; }
-
 template <typename C>
-__device__ __forceinline__ C cmul(C a, C b) {
-    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+__device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C>
+__device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C>
+__device__ __forceinline__ C cscale(C a, decltype(C{}.x) s) { return mk<C>(a.x * s, a.y * s); }
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <bool INV, typename C>
+__device__ __forceinline__ C mul_mi(C a) { return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x); }
+// a * w (forward) or a * conj(w) (inverse), w = exp(-2 pi i m / N) given by (c, s) = (cos, sin)
+template <bool INV, typename C>
+__device__ __forceinline__ C rot(C a, double c, double s) {
+    using R = decltype(C{}.x);
+    const R cr = (R)c, sr = INV ? (R)s : (R)(-s);   // w = c + i sr
+    return mk<C>(a.x * cr - a.y * sr, a.x * sr + a.y * cr);
 }
 
-__device__ __forceinline__ int bitrev(int t, int logn) { return (int)(__brev((unsigned)t) >> (32 - logn)); }
+// cos and sin of pi/8 and pi/4
+constexpr double kC8 = 0.92387953251128675613;
+constexpr double kS8 = 0.38268343236508977173;
+constexpr double kR2 = 0.70710678118654752440;
 
-// In-place radix-2 decimation-in-time FFT in shared memory: input in
-// bit-reversed order, output in natural order.  tw[t] = exp(-2 pi i t/n).
-template <typename C>
-__device__ void fft_smem(C* sm, int n, int logn, const C* __restrict__ tw, bool inverse) {
-    for (int st = 1; st <= logn; ++st) {
-        const int half = 1 << (st - 1);
-        const int tstride = n >> st;
-        for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
-            const int pos = b & (half - 1);
-            const int i0 = ((b >> (st - 1)) << st) + pos;
-            const int i1 = i0 + half;
-            C w = tw[pos * tstride];
-            if (inverse) w.y = -w.y;
-            const C u = sm[i0];
-            const C v = cmul(sm[i1], w);
-            sm[i0] = mk<C>(u.x + v.x, u.y + v.y);
-            sm[i1] = mk<C>(u.x - v.x, u.y - v.y);
+// ---- DFTs of 2, 4, 8 and 16 points in registers (natural order in and out) --
+template <bool INV, typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+    const C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    const C s0 = cadd(a0, a2), d0 = csub(a0, a2);
+    const C s1 = cadd(a1, a3), d1 = mul_mi<INV>(csub(a1, a3));
+    a0 = cadd(s0, s1);
+    a2 = csub(s0, s1);
+    a1 = cadd(d0, d1);
+    a3 = csub(d0, d1);
+}
+
+// 8 points: two 4-point DFTs of the even and odd samples, then the radix-2
+// combination with w8^k.
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8(C (&a)[8]) {
+    C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = rot<INV>(o1, kR2, kR2);
+    o2 = mul_mi<INV>(o2);
+    o3 = rot<INV>(o3, -kR2, kR2);
+    a[0] = cadd(e0, o0);
+    a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1);
+    a[5] = csub(e1, o1);
+    a[2] = cadd(e2, o2);
+    a[6] = csub(e2, o2);
+    a[3] = cadd(e3, o3);
+    a[7] = csub(e3, o3);
+}
+
+// 16 points as 4 x 4: index n = 4 n1 + n2, k = k1 + 4 k2.  DFT over n1 for
+// each n2, twiddle w16^(n2 k1), DFT over n2 for each k1; slot 4 k1 + k2 then
+// holds X[k1 + 4 k2].
+template <bool INV, typename C>
+__device__ __forceinline__ void dft16(C (&a)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+    // slot 4 k1 + n2 holds b[n2][k1]; w16^m = (cos, sin)(2 pi m / 16)
+    a[5] = rot<INV>(a[5], kC8, kS8);        // k1 = 1, n2 = 1: m = 1
+    a[6] = rot<INV>(a[6], kR2, kR2);        // k1 = 1, n2 = 2: m = 2
+    a[7] = rot<INV>(a[7], kS8, kC8);        // k1 = 1, n2 = 3: m = 3
+    a[9] = rot<INV>(a[9], kR2, kR2);        // k1 = 2, n2 = 1: m = 2
+    a[10] = mul_mi<INV>(a[10]);             // k1 = 2, n2 = 2: m = 4
+    a[11] = rot<INV>(a[11], -kR2, kR2);     // k1 = 2, n2 = 3: m = 6
+    a[13] = rot<INV>(a[13], kS8, kC8);      // k1 = 3, n2 = 1: m = 3
+    a[14] = rot<INV>(a[14], -kR2, kR2);     // k1 = 3, n2 = 2: m = 6
+    a[15] = rot<INV>(a[15], -kC8, -kS8);    // k1 = 3, n2 = 3: m = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    C t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = a[4 * k1 + k2];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = t[q];
+}
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dft(C (&u)[R]) {
+    if constexpr (R == 2) dft2<INV>(u[0], u[1]);
+    else if constexpr (R == 4) dft4<INV>(u[0], u[1], u[2], u[3]);
+    else if constexpr (R == 8) dft8<INV>(u);
+    else dft16<INV>(u);
+}
+
+// Shared-memory index with one pad slot per 16 (spreads the strided writes
+// of the early passes over the banks).
+__device__ __forceinline__ int pad(int x) { return x + (x >> 4); }
+
+template <int N> struct Log2;
+template <> struct Log2<2> { static constexpr int v = 1; };
+template <> struct Log2<4> { static constexpr int v = 2; };
+template <> struct Log2<8> { static constexpr int v = 3; };
+template <> struct Log2<16> { static constexpr int v = 4; };
+
+// One Stockham pass of radix R over a length-n sequence whose current values
+// sit in the registers of the nt = n/E threads of this transform, v[e] being
+// element i + e nt.  Butterfly b (thread i takes b = i + nt g, g < E/R) reads
+// elements b + r n/R, multiplies them by w_{R p}^{r k} (k = b mod p, p the
+// length of the sub-transforms done so far), takes their R-point DFT and
+// writes element r to (b - k) R + k + r p.  After the last pass (p = n/R)
+// that position is b + r n/R, so the outputs stay in the same registers;
+// otherwise they go through shared memory and come back strided.
+template <int E, int R, bool INV, typename C>
+__device__ __forceinline__ void radix_pass(C (&v)[E], C* sm, int i, int nt, int p, int logn, int logp,
+                                           const C* __restrict__ tw, bool last) {
+    constexpr int G = E / R;
+    const int sh = logn - logp - Log2<R>::v;   // w_{R p}^m = tw[m << sh]
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int b = i + nt * g;
+        const int k = b & (p - 1);
+        C u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = v[g + r * G];
+        if (p > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = __ldg(tw + ((r * k) << sh));
+                if (INV) w.y = -w.y;
+                u[r] = cmul(u[r], w);
+            }
         }
+        dft<R, INV>(u);
+        if (last) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[g + r * G] = u[r];
+        } else {
+            const int base = (b - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[pad(base + r * p)] = u[r];
+        }
+    }
+    if (!last) {
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = sm[pad(i + e * nt)];
         __syncthreads();
     }
 }
 
-// Twiddles exp(-2 pi i t/n) and the symbol
+// Length-n FFT (n = 2^logn) of the strided register vector v (v[e] = element
+// i + e n/E on entry and on exit): a radix-R0 pass first when R0 > 1, then
+// radix-E passes.  Unnormalised; INV uses exp(+2 pi i ...).  Every thread of
+// the block must call it (it synchronises the block).
+template <int E, int R0, bool INV, typename C>
+__device__ __forceinline__ void fft_reg(C (&v)[E], C* sm, int i, int n, int logn, const C* __restrict__ tw) {
+    const int nt = n / E;
+    int p = 1, logp = 0;
+    if constexpr (R0 > 1) {
+        radix_pass<E, R0, INV>(v, sm, i, nt, p, logn, logp, tw, false);
+        p *= R0;
+        logp += Log2<R0>::v;
+    }
+    const int npass = (logn - logp) / Log2<E>::v;
+    for (int q = 0; q < npass; ++q) {
+        radix_pass<E, E, INV>(v, sm, i, nt, p, logn, logp, tw, q == npass - 1);
+        p *= E;
+        logp += Log2<E>::v;
+    }
+}
+
+// ---- kernels ------------------------------------------------------------------
+// Launch shape: transforms of nt = n/E threads each, F = max(1, 128/nt) of
+// them per block, each with its own padded shared buffer of smlen values.
+__host__ __device__ constexpr int smlen_of(int n) { return n + n / 16 + 1; }
+
+// Step 1: rows 2q and 2q+1 of the real field R as z = R[2q] + i R[2q+1];
+// their spectra from Z = FFT(z): X_a[k] = (Z[k] + conj Z[n-k]) / 2,
+// X_b[k] = -i (Z[k] - conj Z[n-k]) / 2, kept for k < n/2 in S (n x n/2), with
+// S[y][0] = X_y[0] + i X_y[n/2].
+template <typename T, int E, int R0>
+__global__ void __launch_bounds__(256) k_px_fwd(const T* __restrict__ Rf, cx_t<T>* __restrict__ S, int n, int logn,
+                                                const cx_t<T>* __restrict__ tw) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nt = n / E, F = blockDim.x / nt;
+    const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
+    const int h = n / 2;
+    const int q = blockIdx.x * F + f;
+    const bool on = q < h;
+    C* sm = (C*)smraw + (size_t)f * smlen_of(n);
+    C v[E];
+    const T* r0 = Rf + (size_t)(2 * q) * n;
+    const T* r1 = r0 + n;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = i + e * nt;
+        v[e] = on ? mk<C>(r0[x], r1[x]) : mk<C>(T(0), T(0));
+    }
+    fft_reg<E, R0, false>(v, sm, i, n, logn, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) sm[pad(i + e * nt)] = v[e];
+    __syncthreads();
+    C* sa = S + (size_t)(2 * q) * h;
+    C* sb = sa + h;
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+        const int x = i + e * nt;   // < n/2
+        if (!on) continue;
+        const C z = v[e];
+        if (x == 0) {
+            const C zh = sm[pad(h)];
+            sa[0] = mk<C>(z.x, zh.x);
+            sb[0] = mk<C>(z.y, zh.y);
+        } else {
+            const C zm = cconj(sm[pad(n - x)]);
+            const C s = cadd(z, zm), d = csub(z, zm);
+            sa[x] = cscale(s, T(0.5));
+            sb[x] = mk<C>(T(0.5) * d.y, T(-0.5) * d.x);
+        }
+    }
+}
+
+// Step 3: column kx of the transposed half spectrum (row kx of ST, length n):
+// FFT along y, then per ky the two values X1, X2 --
+//   kx > 0: X1 = F(ky) f(kx, ky), X2 = conj F(n-ky) f(kx, ky)  (= conj psi_hat(kx, n-ky)),
+//   kx = 0: the packed column holds kx = 0 and kx = n/2:
+//           C0 = (F + conj Fm)/2, CN = -i (F - conj Fm)/2 (Fm = F(n-ky)),
+//           X1 = C0 f(0, ky) (0 at ky = 0), X2 = CN f(n/2, ky),
+// with f = scale / (sigma(kx) + sigma(ky)).  psi: inverse FFT of X1 (kx > 0)
+// or X1 + i X2 (kx = 0), written back into ST.  With QT, columns c1 = kx and
+// c2 = n - kx (kx = 0: c2 = n/2) of the full spectrum of U + i V,
+// (d(kx) + i d(ky)) X1 and (-d(kx) + i d(ky)) X2 (d the first-derivative
+// symbol, odd, 0 at 0 and n/2); with WT those of S11 + i S12,
+// (-d(kx) d(ky) + i (sigma(kx) - sigma(ky))/2) X1 and
+// (d(kx) d(ky) + i (sigma(c2) - sigma(ky))/2) X2.  Each is inverse-transformed
+// along y into row c of QT / WT (n x n).
+template <typename T, int E, int R0, bool QW>
+__global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t<T>* __restrict__ QT,
+                                                  cx_t<T>* __restrict__ WT, int n, int logn,
+                                                  const cx_t<T>* __restrict__ tw, const T* __restrict__ sigma,
+                                                  const T* __restrict__ dsym, T scale) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nt = n / E, F = blockDim.x / nt;
+    const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
+    const int h = n / 2;
+    const int kx = blockIdx.x * F + f;
+    const bool on = kx < h;
+    const int kxs = on ? kx : 0;
+    C* sm = (C*)smraw + (size_t)f * smlen_of(n);
+    C* row = ST + (size_t)kxs * n;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = on ? row[i + e * nt] : mk<C>(T(0), T(0));
+    fft_reg<E, R0, false>(v, sm, i, n, logn, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) sm[pad(i + e * nt)] = v[e];
+    __syncthreads();
+    const T sx = sigma[kxs], sh = sigma[h];
+    C x1[QW ? E : 1], x2[QW ? E : 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int ky = i + e * nt;
+        const C fm = cconj(sm[pad((n - ky) & (n - 1))]);
+        const T sy = sigma[ky];
+        C a, b;
+        if (kxs == 0) {
+            const C s = cadd(v[e], fm), d = csub(v[e], fm);
+            const T f0 = ky == 0 ? T(0) : scale / (sx + sy);
+            const T fn = scale / (sh + sy);
+            a = cscale(s, T(0.5) * f0);
+            b = mk<C>(T(0.5) * fn * d.y, T(-0.5) * fn * d.x);
+        } else {
+            const T fk = scale / (sx + sy);
+            a = cscale(v[e], fk);
+            b = cscale(fm, fk);
+        }
+        if constexpr (QW) {
+            x1[e] = a;
+            x2[e] = b;
+        }
+        // psi: X1 (kx > 0) or X1 + i X2 (packed kx = 0, n/2)
+        v[e] = kxs == 0 ? mk<C>(a.x - b.y, a.y + b.x) : a;
+    }
+    __syncthreads();
+    fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+    if (on)
+#pragma unroll
+        for (int e = 0; e < E; ++e) row[i + e * nt] = v[e];
+    if constexpr (QW) {
+        const int c2 = kxs == 0 ? h : n - kxs;
+        const T dx = dsym[kxs], sc2 = sigma[c2];
+        // U + i V
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cmul(x1[e], mk<C>(dx, dsym[i + e * nt]));
+        fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+        if (on)
+#pragma unroll
+            for (int e = 0; e < E; ++e) QT[(size_t)kxs * n + i + e * nt] = v[e];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cmul(x2[e], mk<C>(-dx, dsym[i + e * nt]));
+        fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+        if (on)
+#pragma unroll
+            for (int e = 0; e < E; ++e) QT[(size_t)c2 * n + i + e * nt] = v[e];
+        if (WT) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ky = i + e * nt;
+                v[e] = cmul(x1[e], mk<C>(-dx * dsym[ky], T(0.5) * (sx - sigma[ky])));
+            }
+            fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+            if (on)
+#pragma unroll
+                for (int e = 0; e < E; ++e) WT[(size_t)kxs * n + i + e * nt] = v[e];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ky = i + e * nt;
+                v[e] = cmul(x2[e], mk<C>(dx * dsym[ky], T(0.5) * (sc2 - sigma[ky])));
+            }
+            fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+            if (on)
+#pragma unroll
+                for (int e = 0; e < E; ++e) WT[(size_t)c2 * n + i + e * nt] = v[e];
+        }
+    }
+}
+
+// Step 5 for psi: rows 2q, 2q+1 from their half spectra (Hermitian extension
+// X[n-k] = conj X[k]; X[0], X[n/2] from the packed bin): Z = X_a + i X_b,
+// inverse FFT, real part to row 2q, imaginary part to row 2q+1.
+template <typename T, int E, int R0>
+__global__ void __launch_bounds__(256) k_px_inv_real(const cx_t<T>* __restrict__ S, T* __restrict__ out, int n,
+                                                     int logn, const cx_t<T>* __restrict__ tw) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nt = n / E, F = blockDim.x / nt;
+    const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
+    const int h = n / 2;
+    const int q = blockIdx.x * F + f;
+    const bool on = q < h;
+    C* sm = (C*)smraw + (size_t)f * smlen_of(n);
+    const C* sa = S + (size_t)(2 * (on ? q : 0)) * h;
+    const C* sb = sa + h;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = i + e * nt;
+        C a, b;
+        if (x == 0) {
+            a = mk<C>(sa[0].x, T(0));
+            b = mk<C>(sb[0].x, T(0));
+        } else if (x == h) {
+            a = mk<C>(sa[0].y, T(0));
+            b = mk<C>(sb[0].y, T(0));
+        } else if (x < h) {
+            a = sa[x];
+            b = sb[x];
+        } else {
+            a = cconj(sa[n - x]);
+            b = cconj(sb[n - x]);
+        }
+        v[e] = mk<C>(a.x - b.y, a.y + b.x);
+    }
+    fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+    if (!on) return;
+    T* o0 = out + (size_t)(2 * q) * n;
+    T* o1 = o0 + n;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        o0[i + e * nt] = v[e].x;
+        o1[i + e * nt] = v[e].y;
+    }
+}
+
+// Step 5 for a full complex spectrum (U + i V, S11 + i S12): row y, inverse
+// FFT, real part to A, imaginary part to B.
+template <typename T, int E, int R0>
+__global__ void __launch_bounds__(256) k_px_inv_pair(const cx_t<T>* __restrict__ Q, T* __restrict__ A,
+                                                     T* __restrict__ B, int n, int logn,
+                                                     const cx_t<T>* __restrict__ tw) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nt = n / E, F = blockDim.x / nt;
+    const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
+    const int y = blockIdx.x * F + f;
+    const bool on = y < n;
+    C* sm = (C*)smraw + (size_t)f * smlen_of(n);
+    const C* row = Q + (size_t)(on ? y : 0) * n;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = row[i + e * nt];
+    fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+    if (!on) return;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        A[(size_t)y * n + i + e * nt] = v[e].x;
+        B[(size_t)y * n + i + e * nt] = v[e].y;
+    }
+}
+
+// out[c][r] = in[r][c] for a rows x cols complex matrix, 32 x 32 tiles.
+template <typename C>
+__global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int rows, int cols) {
+    __shared__ C tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int gr = r0 + r, gc = c0 + threadIdx.x;
+        if (gr < rows && gc < cols) tile[r][threadIdx.x] = in[(size_t)gr * cols + gc];
+    }
+    __syncthreads();
+    for (int c = threadIdx.y; c < 32; c += blockDim.y) {
+        const int gc = c0 + c, gr = r0 + threadIdx.x;
+        if (gr < rows && gc < cols) out[(size_t)gc * rows + gr] = tile[threadIdx.x][c];
+    }
+}
+
+// Twiddles exp(-2 pi i t/n) (t < n) and the symbols
 // sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta)/(12 h^2) = 4 s^2 (3 + s^2)/(3 h^2),
-// s = sin(theta/2), theta = 2 pi t/n, both evaluated in FP64 and stored as T.
+// s = sin(theta/2), theta = 2 pi t/n, of the 4th-order second difference, and
+// d(theta) = (8 sin theta - sin 2 theta)/(6 h) of the first difference (its
+// symbol is i d), all evaluated in FP64 and stored as T.
 template <typename T>
 __global__ void k_fft_init(cx_t<T>* tw, T* sigma, T* dsym, int n, double inv3h2, double inv6h) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         double sn, cs;
-        if (t < n / 2) {
-            sincospi(2.0 * t / n, &sn, &cs);
-            tw[t] = mk<cx_t<T>>((T)cs, (T)(-sn));
-        }
+        sincospi(2.0 * t / n, &sn, &cs);
+        tw[t] = mk<cx_t<T>>((T)cs, (T)(-sn));
         const double s = sinpi((double)t / n);
         const double s2 = s * s;
         sigma[t] = (T)(4.0 * s2 * (3.0 + s2) * inv3h2);
-        // symbol of the 4th-order first derivative: i (8 sin theta - sin 2 theta) / (6 h)
         dsym[t] = (T)((8.0 * sinpi(2.0 * t / n) - sinpi(4.0 * t / n)) * inv6h);
     }
 }
 
-// Pass 1: each CTA transforms one real row along x.
-template <typename T>
-__global__ void k_fft_x_fwd_real(const T* __restrict__ R, cx_t<T>* __restrict__ C, int n, int logn,
-                                 const cx_t<T>* __restrict__ tw) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx_t<T>* sm = (cx_t<T>*)smraw;
-    const T* row = R + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[bitrev(t, logn)] = mk<cx_t<T>>(row[t], T(0));
-    __syncthreads();
-    fft_smem(sm, n, logn, tw, false);
-    cx_t<T>* out = C + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) out[t] = sm[t];
-}
+constexpr int kMaxLattice = 4096;   // WRC_MAX_NJ
+constexpr int kMaxSmem = (int)sizeof(double2) * smlen_of(kMaxLattice);
 
-// Pass 3: row kx of the transposed spectrum: FFT along y, divide by the
-// symbol (mode (0,0) set to 0, 1/n^2 normalisation folded in), inverse FFT.
-// With Q given, also the spectrum of U + i V, U = D_y psi, V = -D_x psi
-// (D the 4th-order first-derivative stencil, symbol i d(theta)):
-// (d(theta_x) + i d(theta_y)) psi_hat, inverse-transformed along y into Q.
-// With W given, also the spectrum of S11 + i S12, S11 = D_x D_y psi and
-// S12 = (D_yy - D_xx) psi / 2: (-d_x d_y + i (sigma_x - sigma_y) / 2) psi_hat.
-template <typename T>
-__global__ void k_fft_y_solve(cx_t<T>* __restrict__ C, cx_t<T>* __restrict__ Q, cx_t<T>* __restrict__ W, int n,
-                              int logn, const cx_t<T>* __restrict__ tw, const T* __restrict__ sigma,
-                              const T* __restrict__ dsym, T scale) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx_t<T>* sm = (cx_t<T>*)smraw;
-    cx_t<T>* sq = sm + n;
-    cx_t<T>* sw = sq + n;
-    cx_t<T>* row = C + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[bitrev(t, logn)] = row[t];
-    __syncthreads();
-    fft_smem(sm, n, logn, tw, false);
-    const T sx = sigma[blockIdx.x];
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const T den = sx + sigma[t];
-        const T f = (blockIdx.x == 0 && t == 0) ? T(0) : scale / den;
-        sm[t] = mk<cx_t<T>>(sm[t].x * f, sm[t].y * f);
-        if (Q) sq[t] = cmul(sm[t], mk<cx_t<T>>(dsym[blockIdx.x], dsym[t]));
-        if (W) sw[t] = cmul(sm[t], mk<cx_t<T>>(-dsym[blockIdx.x] * dsym[t], T(0.5) * (sx - sigma[t])));
+// The kernels of one (E, R0) shape; dynamic shared memory limits are
+// process-wide per kernel, so they are set once for the largest lattice.
+template <typename T, int E, int R0>
+struct Shape {
+    static int setup() {
+        int bad = 0;
+        bad |= cudaFuncSetAttribute(k_px_fwd<T, E, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        bad |= cudaFuncSetAttribute(k_py_solve<T, E, R0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kMaxSmem);
+        bad |= cudaFuncSetAttribute(k_px_inv_real<T, E, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if constexpr (std::is_same<T, float>::value) {
+            bad |= cudaFuncSetAttribute(k_py_solve<T, E, R0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kMaxSmem);
+            bad |= cudaFuncSetAttribute(k_px_inv_pair<T, E, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kMaxSmem);
+        }
+        return bad;
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int r = bitrev(t, logn);
-        if (t < r) {
-            const cx_t<T> a = sm[t];
-            sm[t] = sm[r];
-            sm[r] = a;
-            if (Q) {
-                const cx_t<T> b = sq[t];
-                sq[t] = sq[r];
-                sq[r] = b;
-            }
-            if (W) {
-                const cx_t<T> c = sw[t];
-                sw[t] = sw[r];
-                sw[r] = c;
+
+    static void run(const PoissonPlan& p, const T* Rf, T* psi, cx_t<T>* C1, cx_t<T>* C2, cudaStream_t s, T* U, T* V,
+                    cx_t<T>* C3, T* S11, T* S12, cx_t<T>* C4) {
+        using C = cx_t<T>;
+        const int n = p.n, logn = p.logn, h = n / 2;
+        const int nt = n / E, F = nt >= 128 ? 1 : 128 / nt;
+        const int thr = F * nt;
+        const size_t smem = sizeof(C) * (size_t)F * smlen_of(n);
+        const C* tw = (const C*)p.tw;
+        const dim3 tb(32, 8);
+        const dim3 g_nh((h + 31) / 32, (n + 31) / 32);   // n x h  -> h x n
+        const dim3 g_hn((n + 31) / 32, (h + 31) / 32);   // h x n  -> n x h
+        const dim3 g_nn((n + 31) / 32, (n + 31) / 32);
+        const int b_half = (h + F - 1) / F, b_full = (n + F - 1) / F;
+        C* S = C1;         // n x h half spectra
+        C* ST = C1 + (size_t)n * h;   // h x n, transposed
+        const bool uv = U && V && C3;
+        const bool st = uv && S11 && S12 && C4;
+        { k_px_fwd<T, E, R0><<<b_half, thr, smem, s>>>(Rf, S, n, logn, tw); note_launch(); }
+        { k_transpose<C><<<g_nh, tb, 0, s>>>(S, ST, n, h); note_launch(); }
+        const T scale = T(1.0 / ((double)n * (double)n));
+        if constexpr (std::is_same<T, float>::value) {
+            if (uv) {
+                C* QT = C2;                    // n x n
+                C* WT = st ? C3 : nullptr;     // n x n
+                { k_py_solve<T, E, R0, true><<<b_half, thr, smem, s>>>(ST, QT, WT, n, logn, tw,
+                                                                        (const T*)p.sigma, (const T*)p.dsym,
+                                                                        scale); note_launch(); }
+                { k_transpose<C><<<g_hn, tb, 0, s>>>(ST, S, h, n); note_launch(); }
+                { k_px_inv_real<T, E, R0><<<b_half, thr, smem, s>>>(S, psi, n, logn, tw); note_launch(); }
+                // U + i V: QT (C2) -> a buffer that V (the caller's, possibly in C1) does not overlap
+                C* Q = st ? C4 : C3;
+                { k_transpose<C><<<g_nn, tb, 0, s>>>(QT, Q, n, n); note_launch(); }
+                { k_px_inv_pair<T, E, R0><<<b_full, thr, smem, s>>>(Q, U, V, n, logn, tw); note_launch(); }
+                if (st) {
+                    { k_transpose<C><<<g_nn, tb, 0, s>>>(WT, C4, n, n); note_launch(); }
+                    { k_px_inv_pair<T, E, R0><<<b_full, thr, smem, s>>>(C4, S11, S12, n, logn, tw); note_launch(); }
+                }
+                return;
             }
         }
+        { k_py_solve<T, E, R0, false><<<b_half, thr, smem, s>>>(ST, nullptr, nullptr, n, logn, tw,
+                                                                 (const T*)p.sigma, (const T*)p.dsym,
+                                                                 scale); note_launch(); }
+        { k_transpose<C><<<g_hn, tb, 0, s>>>(ST, S, h, n); note_launch(); }
+        { k_px_inv_real<T, E, R0><<<b_half, thr, smem, s>>>(S, psi, n, logn, tw); note_launch(); }
+        (void)C2;
     }
-    __syncthreads();
-    fft_smem(sm, n, logn, tw, true);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) row[t] = sm[t];
-    if (Q) {
-        fft_smem(sq, n, logn, tw, true);
-        cx_t<T>* qrow = Q + (size_t)blockIdx.x * n;
-        for (int t = threadIdx.x; t < n; t += blockDim.x) qrow[t] = sq[t];
-    }
-    if (W) {
-        fft_smem(sw, n, logn, tw, true);
-        cx_t<T>* wrow = W + (size_t)blockIdx.x * n;
-        for (int t = threadIdx.x; t < n; t += blockDim.x) wrow[t] = sw[t];
-    }
-}
+};
 
-// Pass 5: inverse FFT along x, real part.
 template <typename T>
-__global__ void k_fft_x_inv_real(const cx_t<T>* __restrict__ C, T* __restrict__ psi, int n, int logn,
-                                 const cx_t<T>* __restrict__ tw) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx_t<T>* sm = (cx_t<T>*)smraw;
-    const cx_t<T>* row = C + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[bitrev(t, logn)] = row[t];
-    __syncthreads();
-    fft_smem(sm, n, logn, tw, true);
-    T* out = psi + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) out[t] = sm[t].x;
+int setup_all() {
+    return Shape<T, 8, 1>::setup() | Shape<T, 16, 1>::setup() | Shape<T, 16, 2>::setup() |
+           Shape<T, 16, 4>::setup() | Shape<T, 16, 8>::setup();
 }
-
-// Pass 5 for U + i V: inverse FFT along x, real part to U, imaginary to V.
-template <typename T>
-__global__ void k_fft_x_inv_pair(const cx_t<T>* __restrict__ C, T* __restrict__ U, T* __restrict__ V, int n,
-                                 int logn, const cx_t<T>* __restrict__ tw) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx_t<T>* sm = (cx_t<T>*)smraw;
-    const cx_t<T>* row = C + (size_t)blockIdx.x * n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) sm[bitrev(t, logn)] = row[t];
-    __syncthreads();
-    fft_smem(sm, n, logn, tw, true);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        U[(size_t)blockIdx.x * n + t] = sm[t].x;
-        V[(size_t)blockIdx.x * n + t] = sm[t].y;
-    }
-}
-
-// out[c][r] = in[r][c] for an n x n complex matrix, 32 x 32 tiles.
-template <typename C>
-__global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int n) {
-    __shared__ C tile[32][33];
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int gy = by + r, gx = bx + threadIdx.x;
-        if (gy < n && gx < n) tile[r][threadIdx.x] = in[(size_t)gy * n + gx];
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int gy = bx + r, gx = by + threadIdx.x;
-        if (gy < n && gx < n) out[(size_t)gy * n + gx] = tile[threadIdx.x][r];
-    }
-}
-
-constexpr int kMaxLattice = 4096;   // WRC_MAX_NJ
 
 template <typename T>
 int plan_init_t(PoissonPlan& p, const Geom& g, cudaStream_t s) {
-    if (cudaMalloc(&p.tw, sizeof(cx_t<T>) * (p.n / 2 > 0 ? p.n / 2 : 1)) != cudaSuccess) return -1;
+    if (cudaMalloc(&p.tw, sizeof(cx_t<T>) * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.sigma, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.dsym, sizeof(T) * p.n) != cudaSuccess) return -1;
-    // The dynamic shared-memory limit is a per-kernel, process-wide attribute:
-    // set it for the largest lattice, so runs of different sizes coexist.
-    const int smem = (int)(sizeof(cx_t<T>) * kMaxLattice);
-    if (cudaFuncSetAttribute(k_fft_x_fwd_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_y_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_x_inv_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fft_x_inv_pair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -2;
+    if (setup_all<T>() != 0) return -2;
     { k_fft_init<T><<<(p.n + 255) / 256, 256, 0, s>>>((cx_t<T>*)p.tw, (T*)p.sigma, (T*)p.dsym, p.n,
                                                        1.0 / (3.0 * g.h * g.h), 1.0 / (6.0 * g.h)); note_launch(); }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
@@ -213,6 +567,7 @@ int poisson_plan_init(PoissonPlan& p, const Geom& g, bool fp32, cudaStream_t s) 
     p.n = g.NJ;
     p.logn = g.L;
     p.fp32 = fp32;
+    if (p.n < 8 || p.n > kMaxLattice || (p.n & (p.n - 1))) return -4;
     return fp32 ? plan_init_t<float>(p, g, s) : plan_init_t<double>(p, g, s);
 }
 
@@ -233,31 +588,12 @@ void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1v, void* C
     C* C2 = (C*)C2v;
     C* C3 = (C*)C3v;
     C* C4 = (C*)C4v;
-    const bool uv = U && V && C3;
-    const bool st = uv && S11 && S12 && C4;
-    const int n = p.n;
-    const size_t smem = sizeof(C) * n;
-    const int thr = n >= 512 ? 256 : (n / 2 >= 32 ? n / 2 : 32);
-    const dim3 tgrid((n + 31) / 32, (n + 31) / 32), tblk(32, 8);
-    const C* tw = (const C*)p.tw;
-    { k_fft_x_fwd_real<T><<<n, thr, smem, s>>>(R, C1, n, p.logn, tw); note_launch(); }
-    { k_transpose<C><<<tgrid, tblk, 0, s>>>(C1, C2, n); note_launch(); }
-    { k_fft_y_solve<T><<<n, thr, (1 + (uv ? 1 : 0) + (st ? 1 : 0)) * smem, s>>>(
-          C2, uv ? C1 : nullptr, st ? C4 : nullptr, n, p.logn, tw, (const T*)p.sigma, (const T*)p.dsym,
-          T(1.0 / ((double)n * (double)n))); note_launch(); }
-    if (uv) {
-        { k_transpose<C><<<tgrid, tblk, 0, s>>>(C2, C3, n); note_launch(); }
-        { k_fft_x_inv_real<T><<<n, thr, smem, s>>>(C3, psi, n, p.logn, tw); note_launch(); }
-        { k_transpose<C><<<tgrid, tblk, 0, s>>>(C1, C2, n); note_launch(); }
-        { k_fft_x_inv_pair<T><<<n, thr, smem, s>>>(C2, U, V, n, p.logn, tw); note_launch(); }
-        if (st) {
-            { k_transpose<C><<<tgrid, tblk, 0, s>>>(C4, C3, n); note_launch(); }
-            { k_fft_x_inv_pair<T><<<n, thr, smem, s>>>(C3, S11, S12, n, p.logn, tw); note_launch(); }
-        }
-    } else {
-        { k_transpose<C><<<tgrid, tblk, 0, s>>>(C2, C1, n); note_launch(); }
-        { k_fft_x_inv_real<T><<<n, thr, smem, s>>>(C1, psi, n, p.logn, tw); note_launch(); }
-    }
+    const int logn = p.logn;
+    if (logn < 4) Shape<T, 8, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
+    else if (logn % 4 == 0) Shape<T, 16, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
+    else if (logn % 4 == 1) Shape<T, 16, 2>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
+    else if (logn % 4 == 2) Shape<T, 16, 4>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
+    else Shape<T, 16, 8>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
     (void)g;
 }
 
