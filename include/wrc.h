@@ -196,8 +196,9 @@ wrc_status wrc_profile(wrc_run* run, int32_t enable);
  * the release of block 0, in microseconds from the start of block 0 (device
  * global timer).  Barrier 0 follows b = A_n omega + g, barrier 1 the ghost
  * values of v_0; then each Arnoldi step has three: after the first dots,
- * after the second dots, after the new basis vector.  *nphases receives the
- * count.  WRC_ERR_ARG if cap < 4 * count; WRC_ERR_STATE without a traced
+ * after the second dots, after the new basis vector (the last step stops
+ * after its second); the final barrier follows phi_1, before the update.
+ * *nphases receives the count.  WRC_ERR_ARG if cap < 4 * count; WRC_ERR_STATE without a traced
  * launch.  Synchronises. */
 wrc_status wrc_query_phase_trace(wrc_run* run, double* out, int32_t cap, int32_t* nphases);
 

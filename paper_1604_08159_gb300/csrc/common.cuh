@@ -101,19 +101,21 @@ __host__ __device__ __forceinline__ long long level_count(int j, const Geom& g) 
 
 // t-th level-j point: first the odd sublattice rows (all columns), then the
 // even rows (odd columns), each in row-major order.
+// (n = NJ / 2^(J-j) is a power of two, so the divisions are shifts; t < NJ^2 < 2^24.)
 __device__ __forceinline__ void level_point(long long t, int j, const Geom& g, int& i, int& k) {
     const int sh = g.J - j;
-    const int n = g.NJ >> sh;
-    const long long half = (long long)n * (n >> 1);
+    const int ln = g.L - sh;                 // log2 n
+    const int n = 1 << ln;
+    const int tt = (int)t;
+    const int half = n << (ln - 1);          // n * n/2
     int ic, kr;
-    if (t < half) {
-        kr = 2 * (int)(t / n) + 1;
-        ic = (int)(t % n);
+    if (tt < half) {
+        kr = 2 * (tt >> ln) + 1;
+        ic = tt & (n - 1);
     } else {
-        const long long u = t - half;
-        const int nh = n >> 1;
-        kr = 2 * (int)(u / nh);
-        ic = 2 * (int)(u % nh) + 1;
+        const int u = tt - half;
+        kr = 2 * (u >> (ln - 1));
+        ic = 2 * (u & ((n >> 1) - 1)) + 1;
     }
     i = ic << sh;
     k = kr << sh;

@@ -383,11 +383,25 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
 // as a weighted sum of active values.  The weights are products of the DD4
 // weights (-1, 9, 9, -1)/16, exact binary fractions, and repeated points are
 // merged, so the rows are exact.  A row longer than rmax sets *overflow.
-__global__ void k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act,
-                                   long long n_tot, const int* __restrict__ lat2idx, int* __restrict__ row_len,
-                                   int* __restrict__ row_idx, double* __restrict__ row_w, int rmax, int j, Geom g,
-                                   int* __restrict__ overflow, const int* __restrict__ dcounts, int nkeys) {
+// One warp per ghost: the predictor points are visited in a fixed order and
+// each one's row (a single entry for an active point) is merged into the
+// ghost's row by all lanes at once -- a row's entries are distinct, so every
+// entry either adds to one existing entry or is appended, new entries in
+// row order.  The entries, their order and their sums are those of merging
+// the terms one by one.
+constexpr int kRowWarps = 4;   // warps (ghosts in flight) per block
+
+__global__ void __launch_bounds__(32 * kRowWarps)
+k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
+                   const int* __restrict__ lat2idx, int* __restrict__ row_len, int* __restrict__ row_idx,
+                   double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
+                   const int* __restrict__ dcounts, int nkeys) {
     constexpr int kCap = 64;
+    __shared__ int s_idx[kRowWarps][kCap];
+    __shared__ double s_wt[kRowWarps][kCap];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* idx = s_idx[wid];
+    double* wt = s_wt[wid];
     if (dcounts) {   // key 0: active points, key l: ghosts of level l
         n_act = dcounts[0];
         gbeg = 0;
@@ -398,59 +412,87 @@ __global__ void k_ghost_rows_level(const int* __restrict__ list, long long gbeg,
         }
         cnt = dcounts[j];
     }
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
-         t += (long long)gridDim.x * blockDim.x) {
+    const int cap = rmax < kCap ? rmax : kCap;
+    const int sh = g.J - j;
+    const int s = 1 << sh;
+    const int off[4] = {-3 * s, -s, s, 3 * s};
+    const double w4[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
+    for (long long t = (long long)blockIdx.x * kRowWarps + wid; t < cnt; t += (long long)gridDim.x * kRowWarps) {
         const long long gi = gbeg - n_act + t;          // ghost number
         const int p = list[gbeg + t];
         const int i = p & g.mask, k = p >> g.L;
-        int idx[kCap];
-        double wt[kCap];
+        const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
+        const bool two_d = oi == ok;                    // odd-odd: tensor product of two 1-D predictions
         int len = 0;
         bool over = false;
-        auto add = [&](int id, double w) {
-            for (int e = 0; e < len; ++e)
-                if (idx[e] == id) { wt[e] += w; return; }
-            if (len < rmax && len < kCap) { idx[len] = id; wt[len] = w; ++len; }
-            else over = true;
-        };
-        const int sh = g.J - j;
-        const int s = 1 << sh;
-        const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
-        const int off[4] = {-3 * s, -s, s, 3 * s};
-        const double w4[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < (two_d ? 4 : 1); ++b) {
             for (int a = 0; a < 4; ++a) {
-                int qi, qk;
-                double w;
-                if (oi && !ok) {
-                    if (b) break;
-                    qi = (i + off[a]) & g.mask; qk = k; w = w4[a];
-                } else if (!oi && ok) {
-                    if (b) break;
-                    qi = i; qk = (k + off[a]) & g.mask; w = w4[a];
+                int qi = i, qk = k;
+                double w = w4[a];
+                if (two_d) {
+                    qi = (i + off[a]) & g.mask;
+                    qk = (k + off[b]) & g.mask;
+                    w = w4[a] * w4[b];
+                } else if (oi) {
+                    qi = (i + off[a]) & g.mask;
                 } else {
-                    qi = (i + off[a]) & g.mask; qk = (k + off[b]) & g.mask; w = w4[a] * w4[b];
+                    qk = (k + off[a]) & g.mask;
                 }
                 const int id = lat2idx[((long long)qk << g.L) + qi];
-                if (id < 0 || id >= n_tot) {          // not a grid point: record, do not read
+                if (id < 0 || id >= n_tot) {            // not a grid point: record, do not read
                     over = true;
                     continue;
                 }
-                if (id < n_act) {
-                    add(id, w);
-                } else {
+                const int* ri = nullptr;
+                const double* rw = nullptr;
+                int rl = 1;
+                if (id >= n_act) {
                     const long long r = id - n_act;
-                    const int rl = row_len[r];
-                    for (int e = 0; e < rl; ++e) add(row_idx[r * rmax + e], w * row_w[r * rmax + e]);
+                    rl = row_len[r];
+                    ri = row_idx + r * rmax;
+                    rw = row_w + r * rmax;
+                }
+                for (int e0 = 0; e0 < rl; e0 += 32) {
+                    const int e = e0 + lane;
+                    const bool has = e < rl;
+                    int my = 0;
+                    double mw = 0.0;
+                    if (has) {
+                        my = ri ? ri[e] : id;
+                        mw = ri ? w * rw[e] : w;
+                    }
+                    int pos = -1;
+                    if (has)
+                        for (int q = 0; q < len; ++q)
+                            if (idx[q] == my) {
+                                pos = q;
+                                break;
+                            }
+                    if (pos >= 0) wt[pos] += mw;
+                    const unsigned fresh = __ballot_sync(0xffffffffu, has && pos < 0);
+                    if (has && pos < 0) {
+                        const int slot = len + __popc(fresh & ((1u << lane) - 1u));
+                        if (slot < cap) {
+                            idx[slot] = my;
+                            wt[slot] = mw;
+                        }
+                    }
+                    const int nf = __popc(fresh);
+                    if (len + nf > cap) over = true;
+                    len = len + nf < cap ? len + nf : cap;
+                    __syncwarp();
                 }
             }
         }
-        row_len[gi] = len;
-        for (int e = 0; e < len; ++e) {
+        for (int e = lane; e < len; e += 32) {
             row_idx[gi * rmax + e] = idx[e];
             row_w[gi * rmax + e] = wt[e];
         }
-        if (over) atomicOr(overflow, 4);
+        if (lane == 0) {
+            row_len[gi] = len;
+            if (over) atomicOr(overflow, 4);
+        }
+        __syncwarp();
     }
 }
 
@@ -517,8 +559,8 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
         // sizes on the device, grids over the capacities (capturable)
         { k_lat2idx<<<blocks_for(cap_a + cap_g), kThreads, 0, s>>>(list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
         for (int j = 1; j <= J; ++j) {
-            k_ghost_rows_level<<<blocks_for(cap_g, 128), 128, 0, s>>>(list, 0, 0, 0, 0, lat2idx, row_len, row_idx,
-                                                                     row_w, rmax, j, g, overflow, dcounts, J + 1);
+            k_ghost_rows_level<<<blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s>>>(
+                list, 0, 0, 0, 0, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, dcounts, J + 1);
             note_launch();
         }
         return;
@@ -528,9 +570,9 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
     if (tot > 0) { k_lat2idx<<<blocks_for(tot), kThreads, 0, s>>>(list, tot, lat2idx, nullptr, 0); note_launch(); }
     for (int j = 1; j <= J; ++j)
         if (gcnt[j] > 0) {
-            k_ghost_rows_level<<<blocks_for(gcnt[j], 128), 128, 0, s>>>(list, goff[j], gcnt[j], n_act, tot, lat2idx,
-                                                                      row_len, row_idx, row_w, rmax, j, g, overflow,
-                                                                      nullptr, 0);
+            k_ghost_rows_level<<<blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s>>>(
+                list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, nullptr,
+                0);
             note_launch();
         }
 }

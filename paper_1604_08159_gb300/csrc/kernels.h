@@ -139,7 +139,7 @@ struct KrylovStepArgs {
     // (globaltimer ns), for at most kTracePhases barriers
     unsigned long long* trace;
 };
-constexpr int kTracePhases = 2 + 3 * 31;
+constexpr int kTracePhases = 3 + 3 * 31;
 int krylov_step_init(bool fp32, int* max_blocks);
 int krylov_step_blocks(long long n, int max_blocks);
 template <typename T>

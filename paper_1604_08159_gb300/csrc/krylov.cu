@@ -4,8 +4,9 @@
 //   Arnoldi with classical Gram-Schmidt applied twice (FP64 inner products,
 //   deterministic reductions; the norm after the second pass from
 //   |w''|^2 = |w'|^2 - |h2|^2), happy breakdown when h_{j+1,j} <= tol |A v_j|,
-//   then (two small kernels) y = phi_1(dt H_k) e_1 from the exponential of the
-//   augmented Hessenberg matrix and omega <- omega + dt beta V_k y.
+//   then, in the same launch, y = phi_1(dt H_k) e_1 from the exponential of
+//   the augmented Hessenberg matrix (block 0), one more grid barrier, and
+//   omega <- omega + dt beta V_k y (every block, its own points).
 // Ghost values of each new basis vector come from exact interpolation rows
 // over the active points, so one Arnoldi step takes three phases: operator and
 // first dots | first update and second dots | second update, normalisation
@@ -22,7 +23,6 @@ namespace {
 constexpr int kPT = 128;      // threads per block of the single-run kernel
 constexpr int kNV = 32;       // accumulator slots: basis vectors per pass (<= m + 1 <= 32)
 constexpr int kOutP = 33;     // partial sums per block: kNV dots + a squared norm
-constexpr int kTaylor = 20;   // Taylor terms per scaling sub-step of exp(M) e_k
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -152,93 +152,120 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
 // y = phi_1(dt H_k) e_1 is the upper part of the last column of exp(M),
 // M = [[dt H_k, e_1], [0, 0]] ((k+1) x (k+1)).  That column, exp(M) e_k, is
 // computed as the action of the exponential by scaling and the truncated
-// Taylor series: with s = max(1, ceil(|M|_1)), B = M / s has |B|_1 <= 1,
-// x <- sum_{i<=20} B^i x / i!  applied s times; the dropped tail is at most
-// sum_{i>20} 1/i! < 2e-20 of |x| per sub-step.  One warp, lane r holds row r.
-// Largest scaling count of the Taylor evaluation: a step with |dt H|_1 above
-// it (or not finite) has blown up; phi_1 is then not evaluated, y is set to
-// NaN and the non-finite flag is raised, so that the step fails cleanly
-// instead of looping ceil(|dt H|_1) times.
+// Taylor series: B = M / s, x <- sum_{i<=m} B^i x / i!  applied s times.
+// With theta = |M|_inf / s (max row sum; the bound only needs a
+// sub-multiplicative norm) the dropped tail is at most
+// sum_{i>m} theta^i / i! of |x|, and (theta, m) is taken from
+//   (1/4, 12), (1/2, 15), (1, 18), (2, 24), (4, 32),
+// each pair keeping that tail below 1e-17, as the one with the fewest
+// matrix-vector products s m (s = max(1, ceil(|M|_inf / theta))).  exp(B)
+// shrinks no vector by more than e^-theta, so the relative truncation error
+// is below 6e-16 per sub-step.  Each product is 32 x 32 in FP64 on one SM,
+// so their count matters.  One warp, lane r holds row r.
+constexpr int kPhiChoices = 5;
+__constant__ double c_phi_theta[kPhiChoices] = {0.25, 0.5, 1.0, 2.0, 4.0};
+__constant__ int c_phi_terms[kPhiChoices] = {12, 15, 18, 24, 32};
+constexpr int kTaylorMax = 32;
+__constant__ double c_inv[kTaylorMax + 1] = {
+    0.0,       1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,
+    1.0 / 9,   1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17,
+    1.0 / 18,  1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26,
+    1.0 / 27,  1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32};
+
+// Largest norm of the Taylor evaluation: a step with |dt H| above it (or not
+// finite) has blown up; phi_1 is then not evaluated, y is set to NaN and the
+// non-finite flag is raised, so that the step fails cleanly instead of
+// looping over an unbounded number of sub-steps.
 constexpr double kMaxPhiScale = 4096.0;
 
-__device__ __forceinline__ void phi1_warp(const double* __restrict__ H, const int* __restrict__ kstop, int m,
-                                          double dt, double* __restrict__ y, int* __restrict__ flags) {
-    const int lane = threadIdx.x;
-    const int k = *kstop;
-    if (k <= 0) {
-        for (int t = lane; t < m; t += 32) y[t] = 0.0;
-        return;
-    }
-    double row[32];
+// phi_1 by one block of PT threads: lane r of warp w holds row r of M over
+// the column group w (32 / (PT/32) columns); each product B x is summed per
+// group, then over the groups by warp 0, which keeps x and the partial sum of
+// the series (the four FP64 sub-pipes of the SM share the products).
+// s_part: [PT/32][>= 32], s_x: [>= 32], s_int: [3]; y (m entries) in global memory.
+template <int PT>
+__device__ __forceinline__ void phi1_block(const double* __restrict__ H, int k, int m, double dt,
+                                           double* __restrict__ y, int* __restrict__ flags,
+                                           double (*s_part)[kNV + 1], double* s_x, int* s_int) {
+    constexpr int G = PT / 32;
+    constexpr int CPG = 32 / G;
+    const int r = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c0 = w * CPG;
+    double row[CPG];
+    double rs = 0.0;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
+    for (int cc = 0; cc < CPG; ++cc) {
+        const int c = c0 + cc;
         double v = 0.0;
-        if (lane < k && c < k) v = dt * H[(size_t)lane * m + c];
-        if (lane == 0 && c == k) v = 1.0;
-        row[c] = v;
+        if (r < k && c < k) v = dt * H[(size_t)r * m + c];
+        if (r == 0 && c == k) v = 1.0;
+        row[cc] = v;
+        rs += fabs(v);
     }
-    double nrm = 0.0;   // |M|_1 = max column sum
+    s_part[w][r] = rs;
+    __syncthreads();
+    if (w == 0) {
+        double t = 0.0;   // |row r|_1
+        for (int q = 0; q < G; ++q) t += s_part[q][r];
+        double nrm = t;   // |M|_inf
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        double cs = fabs(row[c]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        nrm = fmax(nrm, cs);
+        for (int o = 16; o > 0; o >>= 1) nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+        const bool blown = __any_sync(0xffffffffu, !(t == t)) || !(nrm <= kMaxPhiScale);
+        if (r == 0) {
+            int sb = 1, mb = kTaylorMax;
+            if (!blown) {
+                long best = 1L << 40;
+                for (int q = 0; q < kPhiChoices; ++q) {
+                    const int sq = nrm > c_phi_theta[q] ? (int)ceil(nrm / c_phi_theta[q]) : 1;
+                    const long cost = (long)sq * c_phi_terms[q];
+                    if (cost < best) {
+                        best = cost;
+                        sb = sq;
+                        mb = c_phi_terms[q];
+                    }
+                }
+            }
+            s_int[0] = blown ? 1 : 0;
+            s_int[1] = sb;
+            s_int[2] = mb;
+        }
     }
-    if (!(nrm <= kMaxPhiScale)) {
-        if (lane == 0) atomicOr(flags, 1);
-        if (lane < m) y[lane] = lane < k ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+    __syncthreads();
+    const int blown = s_int[0], s = s_int[1], mt = s_int[2];
+    if (blown) {
+        if (threadIdx.x == 0) atomicOr(flags, 1);
+        for (int t = threadIdx.x; t < m; t += PT) y[t] = t < k ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
         return;
     }
-    const int s = nrm > 1.0 ? (int)ceil(nrm) : 1;
-    const double inv_s = 1.0 / s;
-    double x = lane == k ? 1.0 : 0.0;
-    for (int q = 0; q < s; ++q) {
-        double acc = x, term = x;
-        for (int i = 1; i <= kTaylor; ++i) {
-            double nt[4] = {0.0, 0.0, 0.0, 0.0};
+    if (s > 1) {
+        const double inv_s = 1.0 / s;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) nt[c & 3] += row[c] * __shfl_sync(0xffffffffu, term, c);
-            term = ((nt[0] + nt[1]) + (nt[2] + nt[3])) * (inv_s / i);
-            acc += term;
+        for (int cc = 0; cc < CPG; ++cc) row[cc] *= inv_s;
+    }
+    double x = (w == 0 && r == k) ? 1.0 : 0.0;   // meaningful in warp 0
+    for (int q = 0; q < s; ++q) {
+        double acc = x;
+        if (w == 0) s_x[r] = x;
+        __syncthreads();
+        for (int i = 1; i <= mt; ++i) {
+            double pr = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < CPG; ++cc) pr += row[cc] * s_x[c0 + cc];
+            s_part[w][r] = pr;
+            __syncthreads();
+            if (w == 0) {
+                double t = s_part[0][r];
+                for (int g = 1; g < G; ++g) t += s_part[g][r];
+                t *= c_inv[i];
+                acc += t;
+                s_x[r] = t;
+            }
+            __syncthreads();
         }
         x = acc;
     }
-    if (lane < m) y[lane] = lane < k ? x : 0.0;
+    if (w == 0 && r < m) y[r] = r < k ? x : 0.0;
 }
-
-__global__ void __launch_bounds__(32) k_phi1(const double* __restrict__ H, const int* __restrict__ kstop, int m,
-                                             double dt, double* __restrict__ y, int* __restrict__ flags) {
-    phi1_warp(H, kstop, m, dt, y, flags);
-}
-
-// omega <- omega + dt beta V_k y (accumulated in FP64), also written into the
-// lattice array L.
-template <typename T>
-__device__ __forceinline__ void update_body(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
-                                            const double* __restrict__ beta, const int* __restrict__ kstop,
-                                            double dt, const uint32_t* __restrict__ meta, int n,
-                                            T* __restrict__ omega, T* __restrict__ L, int bx, int gx) {
-    __shared__ double s_c[kNV];
-    const int k = *kstop;
-    for (int t = threadIdx.x; t < k; t += blockDim.x) s_c[t] = dt * beta[0] * y[t];
-    __syncthreads();
-    for (int a = bx * blockDim.x + threadIdx.x; a < n; a += gx * blockDim.x) {
-        double inc = 0.0;
-        for (int t = 0; t < k; ++t) inc += s_c[t] * (double)basis[(size_t)t * ld + a];
-        const T x = (T)((double)omega[a] + inc);
-        omega[a] = x;
-        L[meta_pos(meta[a])] = x;
-    }
-}
-
-template <typename T>
-__global__ void k_update(const T* __restrict__ basis, long long ld, const double* __restrict__ y,
-                         const double* __restrict__ beta, const int* __restrict__ kstop, double dt,
-                         const uint32_t* __restrict__ meta, int n, T* __restrict__ omega, T* __restrict__ L) {
-    update_body<T>(basis, ld, y, beta, kstop, dt, meta, n, omega, L, blockIdx.x, gridDim.x);
-}
-
 
 // x - sum_{t < nv} c_t v_t for the basis values v_t = basis[t ld] of one
 // point, in the bulk type: four interleaved partial sums of the projections
@@ -323,6 +350,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_c[kNV];
     __shared__ double s_sc[4];   // beta, 1/beta, h_{j+1,j}, 1/h_{j+1,j}
     __shared__ int s_stop;       // 0 go on, 1 happy breakdown, 2 non-finite
+    __shared__ int s_int[3];     // phi_1: blown up, sub-steps, Taylor terms
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
@@ -473,6 +501,28 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
         }
     }
+    // y = phi_1(dt H_k) e_1 by block 0 (which wrote H), then every block:
+    // omega <- omega + dt beta V_k y at its points (accumulated in FP64), also
+    // written into the lattice array L
+    if (k == 0) {
+        if (bid == 0)
+            for (int t = threadIdx.x; t < m; t += PT) A.y[t] = 0.0;
+        if (lead) *A.kstop = 0;
+        return;
+    }
+    if (bid == 0) phi1_block<PT>(A.H, k, m, A.dt, A.y, A.flags, s_red, s_h, s_int);
+    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+    for (int t = threadIdx.x; t < k; t += PT) s_c[t] = A.dt * beta * __ldcg(A.y + t);
+    __syncthreads();
+    T* __restrict__ om = (T*)A.omega;
+    T* __restrict__ Lo = (T*)A.L;
+    for (int a = a0; a < n; a += stride) {
+        double inc = 0.0;
+        for (int t = 0; t < k; ++t) inc += s_c[t] * (double)basis[(size_t)t * ld + a];
+        const T x = (T)((double)om[a] + inc);
+        om[a] = x;
+        Lo[meta_pos(A.meta[a])] = x;
+    }
     if (lead) *A.kstop = k;
 }
 
@@ -490,20 +540,6 @@ __global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __
     const int q = blk2mem[blockIdx.x];
     const int b0 = mem_b0[q];
     krylov_body<T, PT>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
-}
-
-// phi_1 for problem blockIdx.x of a batch (one warp each).
-__global__ void __launch_bounds__(32) k_phi1_batch(const KrylovStepArgs* __restrict__ args) {
-    const KrylovStepArgs& A = args[blockIdx.x];
-    phi1_warp(A.H, A.kstop, A.m, A.dt, A.y, A.flags);
-}
-
-// Update of problem blockIdx.y of a batch.
-template <typename T>
-__global__ void k_update_batch(const KrylovStepArgs* __restrict__ args) {
-    const KrylovStepArgs& A = args[blockIdx.y];
-    update_body<T>((const T*)A.basis, A.ld, A.y, A.beta, A.kstop, A.dt, A.meta, A.n, (T*)A.omega, (T*)A.L,
-                   blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -532,11 +568,6 @@ cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStrea
     void* params[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT>, dim3(blocks), dim3(kPT), params, 0, s);
     if (e != cudaSuccess) return e;
-    note_launch();
-    k_phi1<<<1, 32, 0, s>>>(args.H, args.kstop, args.m, args.dt, args.y, args.flags);
-    note_launch();
-    k_update<T><<<blocks_for(args.n), kThreads, 0, s>>>((const T*)args.basis, args.ld, args.y, args.beta, args.kstop,
-                                                        args.dt, args.meta, args.n, (T*)args.omega, (T*)args.L);
     note_launch();
     return cudaGetLastError();
 }
@@ -574,10 +605,8 @@ cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2m
     cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(pt), params, 0, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_phi1_batch<<<members, 32, 0, s>>>(d_args);
-    note_launch();
-    k_update_batch<T><<<dim3(blocks_for(max_n) < 64 ? blocks_for(max_n) : 64, members), kThreads, 0, s>>>(d_args);
-    note_launch();
+    (void)members;
+    (void)max_n;
     return cudaGetLastError();
 }
 
