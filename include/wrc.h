@@ -270,7 +270,8 @@ wrc_status wrc_ensemble_step(wrc_ensemble* e, int32_t nsteps);
 wrc_status wrc_ensemble_set_shape(wrc_ensemble* e, int32_t threads_per_block, int32_t points_per_thread);
 
 /* Autotuner: time the batched Krylov launch over steps_per_candidate real
- * steps for each of the 9 shapes {64,128,256} x {1,2,4}, keep the fastest and
+ * steps for each of the 9 shapes {64,128,256} x {1,2,4} (those with at least
+ * one co-resident block per member), keep the fastest and
  * cache it for this process per (precision, member-count bucket,
  * active-count bucket); a cached choice is applied without stepping.  The
  * chosen shape is written to out_shape[0..1] (may be NULL). */

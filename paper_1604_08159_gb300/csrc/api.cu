@@ -1612,6 +1612,8 @@ wrc_status wrc_ensemble_tune(wrc_ensemble* E, int32_t steps_per_candidate, int32
     batch_take_profile(E->C);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
+            // a shape needs one co-resident block per member at least
+            if (krylov_batch_max_blocks(E->C.fp32, pts[a]) < (int)E->members.size()) continue;
             E->C.pt = pts[a];
             E->C.ept = epts[b];
             E->C.profiling = true;
