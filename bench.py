@@ -64,6 +64,21 @@ def workload_for(rank: int):
     return W.fujiwhara_1024(seed=2 + rank)
 
 
+def combine_ranks(dev_ms: float, upd: int, device):
+    """Whole-job numbers over the ranks of an initialised process group: the
+    slowest rank's device time (MAX) and the updates of all ranks (SUM).  A
+    single process returns its own numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dev_ms, upd
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(upd)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), int(u[0])
+
+
 def oracle_config(p):
     from oracle import wrc_oracle as O
     return O.Config(n0=p.n0, J=p.J, eps=p.eps, re=p.re, dt=p.dt, m=p.m, sgs=p.sgs_name(), cs=p.cs,
@@ -373,14 +388,7 @@ def run_ours(args):
         ensemble = measure_ensemble(args)
 
     # max over ranks
-    t_dev = dev_ms
-    if ws > 1:
-        tt = torch.tensor([dev_ms, float(upd)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_dev = float(mx[0])
-        upd = int(tt[1])
+    t_dev, upd = combine_ranks(dev_ms, upd, "cuda")
     value = upd / (t_dev * 1e-3)
 
     line = None
