@@ -60,8 +60,16 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_for(rank: int):
-    return W.fujiwhara_1024(seed=2 + rank)
+WORKLOADS = {
+    # the headline configuration: 1024^2 pair, dynamic Smagorinsky, FP64
+    "fujiwhara_1024": lambda rank: W.fujiwhara_1024(seed=2 + rank),
+    # 4096^2 three-vortex configuration, mixed precision (for profiling)
+    "three_vortex_4096": lambda rank: W.three_vortex_4096(seed=3 + rank),
+}
+
+
+def workload_for(rank: int, name: str = "fujiwhara_1024"):
+    return WORKLOADS[name](rank)
 
 
 def combine_ranks(dev_ms: float, upd: int, device):
@@ -266,11 +274,34 @@ def measure_ensemble(args):
             "throughput_ratio": batched / solo if solo > 0 else None}
 
 
+KRYLOV_SOURCES = ("csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh", "csrc/kernels.h")
+
+
+def krylov_traffic(workload: str):
+    """DRAM bytes per launch of the Krylov kernel from the committed ncu
+    summary of this workload, or None if there is none or the kernel's
+    sources changed since the counters were taken."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_krylov_step_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_b = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    m_h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
+    if not (m_b and m_h):
+        return None
+    h = hashlib.sha256()
+    for f in KRYLOV_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1604_08159_gb300", f), "rb").read())
+    return int(m_b.group(1)) if h.hexdigest() == m_h.group(1) else None
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    wl = workload_for(0)
+    wl = workload_for(0, args.workload)
     warm = min(args.warmup, 1)
     val, wall, cores, upd = time_oracle(wl, args.steps, warmup=warm)
     line = {
@@ -308,7 +339,7 @@ def run_ours(args):
         dist.barrier()
     B.load()
 
-    wl = workload_for(rank)
+    wl = workload_for(rank, args.workload)
     p = wl.params
     stream = torch.cuda.Stream()
     run = B.Run(p, stream=stream.cuda_stream)
@@ -401,7 +432,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if p.prec == W.PREC_MIXED else "f64",
+            "data": "synthetic",
             "config": {"workload": wl.name, "NJ": p.NJ, "n0": p.n0, "J": p.J, "eps": p.eps, "m": p.m,
                        "sgs": p.sgs_name(), "cs": p.cs, "re": p.re, "dt": p.dt,
                        "mean_active_points": upd / max(1, args.steps * ws),
@@ -410,7 +442,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "k_krylov_step (Arnoldi, phi_1 and the update: the Krylov part of a step)",
                          "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                         "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+                         "frac": achieved_gflops / FP64_PEAK_GFLOPS,
+                         "traffic": krylov_traffic("fujiwhara_1024" if args.workload == "fujiwhara_1024" else "-"),
+                         "traffic_unit": "DRAM bytes per launch (ncu; null once the kernel changed)",
                          "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(1, rec["launches"]),
                          "flops_per_launch": rec["flops"] / max(1, rec["launches"]),
                          "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
@@ -440,6 +474,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fujiwhara_1024")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
