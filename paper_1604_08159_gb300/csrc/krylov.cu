@@ -103,11 +103,14 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
     }
 }
 
-// Sum over all blocks of part[b * kOutP + t], t < nout, into s_out: lane t
-// of warp w adds blocks w, w + nwarps, ... in order (one output per lane), the
-// warps' sums are then added in warp order.  Same order in every block.  The
-// loads go out kReduceBatch at a time ahead of their (ordered) additions, so
-// a block pays one L2 round trip per batch rather than one per partial.
+// Sum over all blocks of part[b * kOutP + t], t < nout, into s_out.  The
+// lanes of a warp are split into L = 32 / ns groups (ns = nout rounded up to
+// a power of two, at most 32, so L > 1 only when nout <= 16): lane g ns + t of
+// warp w adds output t of blocks w + 4 (g + L u), u = 0, 1, ... (for 4 warps),
+// in order; the groups are then combined by shuffles and the warps' sums
+// added in warp order.  Same order in every block.  A lane's loads go out
+// kReduceBatch at a time ahead of their ordered additions, so one L2 round
+// trip covers up to kReduceBatch partials per lane.
 constexpr int kReduceBatch = 16;
 
 template <int PT>
@@ -115,35 +118,39 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
                                            double (*s_red)[kNV + 1], int nb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kW = PT / 32;
-    for (int t0 = 0; t0 < nout; t0 += 32) {
-        const int t = t0 + lane;
-        double v = 0.0;
-        if (t < nout) {
-            const double* p = part + t;
-            int b = wid;
-            for (; b + (kReduceBatch - 1) * kW < nb; b += kReduceBatch * kW) {
-                double x[kReduceBatch];
-#pragma unroll
-                for (int u = 0; u < kReduceBatch; ++u) x[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
-#pragma unroll
-                for (int u = 0; u < kReduceBatch; ++u) v += x[u];
-            }
-            const int rest = b < nb ? (nb - 1 - b) / kW + 1 : 0;   // < kReduceBatch
+    if (nout > 32) nout = 32;   // (never: nout <= m + 1 <= 32)
+    int ns = 1;
+    while (ns < nout) ns <<= 1;
+    const int L = 32 / ns;
+    const int t = lane & (ns - 1), g = lane / ns;
+    const int bstep = kW * L;
+    double v = 0.0;
+    if (t < nout) {
+        const double* p = part + t;
+        int b = wid + kW * g;
+        for (; b + (kReduceBatch - 1) * bstep < nb; b += kReduceBatch * bstep) {
             double x[kReduceBatch];
 #pragma unroll
-            for (int u = 0; u < kReduceBatch; ++u)
-                if (u < rest) x[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
+            for (int u = 0; u < kReduceBatch; ++u) x[u] = __ldcg(p + (size_t)(b + u * bstep) * kOutP);
 #pragma unroll
-            for (int u = 0; u < kReduceBatch; ++u)
-                if (u < rest) v += x[u];
+            for (int u = 0; u < kReduceBatch; ++u) v += x[u];
         }
-        if (t < nout) s_red[wid][t] = v;
+        const int rest = b < nb ? (nb - 1 - b) / bstep + 1 : 0;   // < kReduceBatch
+        double x[kReduceBatch];
+#pragma unroll
+        for (int u = 0; u < kReduceBatch; ++u)
+            if (u < rest) x[u] = __ldcg(p + (size_t)(b + u * bstep) * kOutP);
+#pragma unroll
+        for (int u = 0; u < kReduceBatch; ++u)
+            if (u < rest) v += x[u];
     }
+    for (int o = ns; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // the L groups
+    if (g == 0 && t < nout) s_red[wid][t] = v;
     __syncthreads();
-    for (int t = threadIdx.x; t < nout; t += blockDim.x) {
-        double v = 0.0;
-        for (int q = 0; q < kW; ++q) v += s_red[q][t];
-        s_out[t] = v;
+    for (int q = threadIdx.x; q < nout; q += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kW; ++w) s += s_red[w][q];
+        s_out[q] = s;
     }
     __syncthreads();
 }
@@ -267,6 +274,25 @@ __device__ __forceinline__ void phi1_block(const double* __restrict__ H, int k, 
     if (w == 0 && r < m) y[r] = r < k ? x : 0.0;
 }
 
+// sqrt(q) and 1/sqrt(q) in FP64 for the normalisation of a new basis vector:
+// an FP32 reciprocal square root as the seed, then two Newton-Raphson steps
+// y <- y (3 - q y^2) / 2 in FP64 (each doubles the correct bits: ~22 -> ~44
+// -> full precision), sqrt(q) = q y.  FP64 division and square root are long
+// instruction sequences on this part; this is a handful of FMAs.  Values
+// outside the FP32 range take the library's sqrt and division.
+__device__ __forceinline__ void sqrt_and_rsqrt(double q, double& s, double& r) {
+    if (q > 1e-30 && q < 1e30) {
+        double y = (double)rsqrtf((float)q);
+        y = y * (1.5 - 0.5 * q * y * y);
+        y = y * (1.5 - 0.5 * q * y * y);
+        r = y;
+        s = q * y;
+    } else {
+        s = sqrt(q);
+        r = 1.0 / s;
+    }
+}
+
 // x - sum_{t < nv} c_t v_t for the basis values v_t = basis[t ld] of one
 // point, in the bulk type: four interleaved partial sums of the projections
 // (short dependency chains; FP64 issues one warp instruction per 16 cycles
@@ -385,9 +411,10 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     // scalars of the step, once per block (FP64 division and square root
     // are long instruction sequences on this part)
     if (threadIdx.x == 0) {
-        const double bt = sqrt(s_h[0]);
+        double bt, ib;
+        sqrt_and_rsqrt(s_h[0], bt, ib);
         s_sc[0] = bt;
-        s_sc[1] = 1.0 / bt;
+        s_sc[1] = ib;
     }
     __syncthreads();
     const double beta = s_sc[0];
@@ -463,10 +490,13 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                 for (int o = 16; o > 0; o >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, o);
                 bad = __any_sync(0xffffffffu, bad);
                 if (t == 0) {
-                    const double hn = sqrt(fmax(s_h[nv] - h2, 0.0));
+                    const double q = fmax(s_h[nv] - h2, 0.0);   // h_{j+1,j}^2
+                    double hn, inv;
+                    sqrt_and_rsqrt(q, hn, inv);
                     s_sc[2] = hn;
-                    s_sc[3] = 1.0 / hn;
-                    s_stop = (bad || !isfinite(hn)) ? 2 : (hn <= A.tol * sqrt(wn2) ? 1 : 0);
+                    s_sc[3] = inv;
+                    // breakdown: h <= tol |A v_j|, compared squared
+                    s_stop = (bad || !isfinite(q)) ? 2 : (q <= A.tol * A.tol * wn2 ? 1 : 0);
                     if (bid == 0) A.H[(size_t)(j + 1) * m + j] = hn;
                 }
             }
