@@ -101,6 +101,7 @@ struct wrc_run {
     void* C2 = nullptr;
     DevBuf lat64;            // NJ*NJ doubles for conversions of lattice fields (mixed mode)
     uint8_t *act = nullptr, *nxt = nullptr, *gho = nullptr, *sig = nullptr, *JJ = nullptr;
+    uint8_t* halo = nullptr;   // Smagorinsky halo mask (FP64 dynamic mode)
     int* list = nullptr;     // active points, then ghosts by level
     int* lat2idx = nullptr;  // lattice -> combined active/ghost number
     int *blk_counts = nullptr, *blk_off = nullptr, *counts_dev = nullptr;
@@ -421,7 +422,6 @@ wrc_status freeze(wrc_run* R) {
     T* t1 = t0 + R->N;
     T* t2 = (T*)R->C2;
     T* t3 = t2 + R->N;
-    const T* Ulat = nullptr;
     if (R->fp32) {
         // FP32 bulk: U = D_y psi, V = -D_x psi and the strain S11, S12 come
         // from the spectrum, because finest-lattice stencils on an FP32 psi
@@ -448,8 +448,8 @@ wrc_status freeze(wrc_run* R) {
                                   R->counts_dev);
     }
     if (R->cfg.sgs == WRC_SGS_DYNAMIC)
-        launch_sgs<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t0, t1, t2, t3, R->g, s, Ulat,
-                      R->counts_dev);
+        launch_sgs_halo<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t2, t3, R->halo, R->g, s,
+                           R->counts_dev);
     CKL("freeze");
     R->frozen = true;
     return WRC_OK;
@@ -746,7 +746,7 @@ void free_run(wrc_run* R) {
                     &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace})
         b->release(s);
     cudaStreamSynchronize(s);
-    void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->list, R->lat2idx,
+    void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->halo, R->list, R->lat2idx,
                     R->blk_counts, R->blk_off, R->counts_dev, R->flag_dev, R->lvl_dev, R->vort_dev, R->diag_dev,
                     R->K.H, R->K.kstop, R->K.part};
     for (void* p : ptrs)
@@ -815,7 +815,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
         if (e == cudaSuccess) e = alloc(p, R->es * N);
     if (e == cudaSuccess) e = alloc(&R->C1, 2 * R->es * N);
     if (e == cudaSuccess) e = alloc(&R->C2, 2 * R->es * N);
-    uint8_t** mp[] = {&R->act, &R->nxt, &R->gho, &R->sig, &R->JJ};
+    uint8_t** mp[] = {&R->act, &R->nxt, &R->gho, &R->sig, &R->JJ, &R->halo};
     for (auto p : mp)
         if (e == cudaSuccess) e = alloc((void**)p, N);
     if (e == cudaSuccess) e = alloc((void**)&R->list, sizeof(int) * N);
@@ -1461,10 +1461,10 @@ double wrc::run_bytes_for(const wrc_config& cfg, long long na, long long ng) {
     const double es = cfg.prec == WRC_MIXED ? 4.0 : 8.0;
     const double m1 = cfg.krylov_m + 1;
     const double nblk = std::ceil(N / kTile);
-    // L, Lq, psi; complex C1, C2; five byte masks; list and lat2idx; block
+    // L, Lq, psi; complex C1, C2; six byte masks; list and lat2idx; block
     // counts and offsets; the 2N-double scratch (mixed mode always, FP64 on
     // the first query that converts a lattice field)
-    double b = 7.0 * es * N + 5.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + 16.0 * N;
+    double b = 7.0 * es * N + 6.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + 16.0 * N;
     // FFT tables: twiddles, symbols
     b += 4.0 * es * std::sqrt(N) + 16.0 * std::sqrt(N);
     // Krylov small arrays and partial sums (at most kMaxBlocks blocks)
@@ -1484,7 +1484,7 @@ double wrc::run_device_bytes(const wrc_run* R) {
     const double es = (double)R->es;
     const double m1 = cfg.krylov_m + 1;
     const double nblk = std::ceil(N / kTile);
-    double b = 7.0 * es * N + 5.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + (double)R->lat64.bytes;
+    double b = 7.0 * es * N + 6.0 * N + 8.0 * N + 8.0 * nblk * kMaxKeys + (double)R->lat64.bytes;
     b += 4.0 * es * R->g.NJ + 16.0 * R->g.NJ;
     b += 8.0 * (m1 * cfg.krylov_m + 33) +
          8.0 * (double)std::max(krylov_partials_doubles(R->max_blocks), (size_t)kMaxBlocks * 4);

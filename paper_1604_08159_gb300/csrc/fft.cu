@@ -287,42 +287,45 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
     const int kx = blockIdx.x * F + f;
     const bool on = kx < h;
     const int kxs = on ? kx : 0;
-    C* sm = (C*)smraw + (size_t)f * smlen_of(n);
+    // exchange buffer of the FFT passes; with QW the forward spectrum keeps a
+    // buffer of its own (F(ky) in natural order), from which every output
+    // recomputes its values instead of holding them in registers
+    C* sm = (C*)smraw + (size_t)f * (QW ? 2 : 1) * smlen_of(n);
+    C* fb = QW ? sm + smlen_of(n) : sm;
     C* row = ST + (size_t)kxs * n;
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = on ? row[i + e * nt] : mk<C>(T(0), T(0));
     fft_reg<E, R0, false>(v, sm, i, n, logn, tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) sm[pad(i + e * nt)] = v[e];
+    for (int e = 0; e < E; ++e) fb[pad(i + e * nt)] = v[e];
     __syncthreads();
     const T sx = sigma[kxs], sh = sigma[h];
-    C x1[QW ? E : 1], x2[QW ? E : 1];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int ky = i + e * nt;
-        const C fm = cconj(sm[pad((n - ky) & (n - 1))]);
+    // X1, X2 at ky from the forward spectrum (see above)
+    auto x12 = [&](int ky, C& a, C& b) {
+        const C fk = fb[pad(ky)];
+        const C fm = cconj(fb[pad((n - ky) & (n - 1))]);
         const T sy = sigma[ky];
-        C a, b;
         if (kxs == 0) {
-            const C s = cadd(v[e], fm), d = csub(v[e], fm);
+            const C s = cadd(fk, fm), d = csub(fk, fm);
             const T f0 = ky == 0 ? T(0) : scale / (sx + sy);
             const T fn = scale / (sh + sy);
             a = cscale(s, T(0.5) * f0);
             b = mk<C>(T(0.5) * fn * d.y, T(-0.5) * fn * d.x);
         } else {
-            const T fk = scale / (sx + sy);
-            a = cscale(v[e], fk);
-            b = cscale(fm, fk);
+            const T fc = scale / (sx + sy);
+            a = cscale(fk, fc);
+            b = cscale(fm, fc);
         }
-        if constexpr (QW) {
-            x1[e] = a;
-            x2[e] = b;
-        }
-        // psi: X1 (kx > 0) or X1 + i X2 (packed kx = 0, n/2)
+    };
+    // psi: X1 (kx > 0) or X1 + i X2 (packed kx = 0, n/2)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        C a, b;
+        x12(i + e * nt, a, b);
         v[e] = kxs == 0 ? mk<C>(a.x - b.y, a.y + b.x) : a;
     }
-    __syncthreads();
+    if constexpr (!QW) __syncthreads();   // fb is the exchange buffer
     fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
     if (on)
 #pragma unroll
@@ -330,24 +333,35 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
     if constexpr (QW) {
         const int c2 = kxs == 0 ? h : n - kxs;
         const T dx = dsym[kxs], sc2 = sigma[c2];
-        // U + i V
+        // U + i V, columns c1 = kx and c2
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cmul(x1[e], mk<C>(dx, dsym[i + e * nt]));
+        for (int e = 0; e < E; ++e) {
+            C a, b;
+            x12(i + e * nt, a, b);
+            v[e] = cmul(a, mk<C>(dx, dsym[i + e * nt]));
+        }
         fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
         if (on)
 #pragma unroll
             for (int e = 0; e < E; ++e) QT[(size_t)kxs * n + i + e * nt] = v[e];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cmul(x2[e], mk<C>(-dx, dsym[i + e * nt]));
+        for (int e = 0; e < E; ++e) {
+            C a, b;
+            x12(i + e * nt, a, b);
+            v[e] = cmul(b, mk<C>(-dx, dsym[i + e * nt]));
+        }
         fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
         if (on)
 #pragma unroll
             for (int e = 0; e < E; ++e) QT[(size_t)c2 * n + i + e * nt] = v[e];
         if (WT) {
+            // S11 + i S12
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ky = i + e * nt;
-                v[e] = cmul(x1[e], mk<C>(-dx * dsym[ky], T(0.5) * (sx - sigma[ky])));
+                C a, b;
+                x12(ky, a, b);
+                v[e] = cmul(a, mk<C>(-dx * dsym[ky], T(0.5) * (sx - sigma[ky])));
             }
             fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
             if (on)
@@ -356,7 +370,9 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ky = i + e * nt;
-                v[e] = cmul(x2[e], mk<C>(dx * dsym[ky], T(0.5) * (sc2 - sigma[ky])));
+                C a, b;
+                x12(ky, a, b);
+                v[e] = cmul(b, mk<C>(dx * dsym[ky], T(0.5) * (sc2 - sigma[ky])));
             }
             fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
             if (on)
@@ -519,7 +535,7 @@ struct Shape {
             if (uv) {
                 C* QT = C2;                    // n x n
                 C* WT = st ? C3 : nullptr;     // n x n
-                { k_py_solve<T, E, R0, true><<<b_half, thr, smem, s>>>(ST, QT, WT, n, logn, tw,
+                { k_py_solve<T, E, R0, true><<<b_half, thr, 2 * smem, s>>>(ST, QT, WT, n, logn, tw,
                                                                         (const T*)p.sigma, (const T*)p.dsym,
                                                                         scale); note_launch(); }
                 { k_transpose<C><<<g_hn, tb, 0, s>>>(ST, S, h, n); note_launch(); }

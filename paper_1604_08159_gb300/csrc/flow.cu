@@ -47,18 +47,6 @@ __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __r
     }
 }
 
-// Smagorinsky pass 1: t0 = U = dpsi/dy (unless given), t1 = S12 = (psi_yy - psi_xx)/2.
-template <typename T>
-__global__ void k_sgs1(const T* __restrict__ psi, T* __restrict__ t0, T* __restrict__ t1, Geom g, T c1, T c2) {
-    const long long N = (long long)g.NJ * g.NJ;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
-        if (t0) t0[p] = dy1(psi, i, k, g, c1);
-        t1[p] = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
-    }
-}
-
 // nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5); a = 2 nu_t S12, c = nu_t S11
 // (nut and c may be null).
 template <typename T>
@@ -87,24 +75,6 @@ __global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restric
     }
 }
 
-// Pass 2: S11 = dU/dx, nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5);
-// t2 = 2 nu_t S12, t3 = nu_t S11, t1 <- nu_t.
-template <typename T>
-__global__ void k_sgs2(const T* __restrict__ t0, T* __restrict__ t1, T* __restrict__ t2, T* __restrict__ t3,
-                       Geom g, T c1, T csh2) {
-    const long long N = (long long)g.NJ * g.NJ;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
-        const T s11 = dx1(t0, i, k, g, c1);
-        const T s12 = t1[p];
-        const T nut = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
-        t2[p] = T(2) * nut * s12;
-        t3[p] = nut * s11;
-        t1[p] = nut;
-    }
-}
-
 // Pass 3: t0 = d(t3)/dy.
 template <typename T>
 __global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c1) {
@@ -126,6 +96,64 @@ __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const
         const int p = meta_pos(meta[a]);
         const int i = p & g.mask, k = p >> g.L;
         ga[a] = dx2(t2, i, k, g, c2) - dy2(t2, i, k, g, c2) - T(4) * dx1(t0, i, k, g, c1);
+    }
+}
+
+// Smagorinsky forcing restricted to where it is read (FP64 path).  g at an
+// active point reads 2 nu_t S12 on its cross of radius 2 and D_y(nu_t S11) on
+// its x-neighbours at distance <= 2, i.e. nu_t S12 and nu_t S11 inside the
+// 5 x 5 box around it; those products are formed only at the lattice points
+// of the union of these boxes (the halo), from psi with the same stencils in
+// the same order as a full lattice pass would use.
+__global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ halo, Geom g,
+                                const int* __restrict__ dn) {
+    n = eff_n(dn, n);
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        const int i = p & g.mask, k = p >> g.L;
+#pragma unroll
+        for (int dk = -2; dk <= 2; ++dk)
+#pragma unroll
+            for (int di = -2; di <= 2; ++di)
+                halo[((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask)] = 1;
+    }
+}
+
+// At halo points: S11 = D_x(D_y psi), S12 = (psi_yy - psi_xx)/2,
+// nu_t = (C_s h)^2 2 sqrt(S11^2 + S12^2) (Eq. 5); t2 = 2 nu_t S12, t3 = nu_t S11.
+template <typename T>
+__global__ void k_sgs_halo_products(const T* __restrict__ psi, const uint8_t* __restrict__ halo,
+                                    T* __restrict__ t2, T* __restrict__ t3, Geom g, T c1, T c2, T csh2) {
+    const long long N = (long long)g.NJ * g.NJ;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        if (!halo[p]) continue;
+        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+        const T up1 = dy1(psi, i + 1, k, g, c1), um1 = dy1(psi, i - 1, k, g, c1);
+        const T up2 = dy1(psi, i + 2, k, g, c1), um2 = dy1(psi, i - 2, k, g, c1);
+        const T s11 = (T(8) * (up1 - um1) - (up2 - um2)) * c1;
+        const T s12 = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
+        const T nut = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
+        t2[p] = T(2) * nut * s12;
+        t3[p] = nut * s11;
+    }
+}
+
+// At the active points: g = Dxx(t2) - Dyy(t2) - 4 D_x(D_y t3).
+template <typename T>
+__global__ void k_sgs_halo_forcing(const T* __restrict__ t2, const T* __restrict__ t3,
+                                   const uint32_t* __restrict__ meta, long long n, T* __restrict__ ga, Geom g, T c1,
+                                   T c2, const int* __restrict__ dn) {
+    n = eff_n(dn, n);
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int p = meta_pos(meta[a]);
+        const int i = p & g.mask, k = p >> g.L;
+        const T vp1 = dy1(t3, i + 1, k, g, c1), vm1 = dy1(t3, i - 1, k, g, c1);
+        const T vp2 = dy1(t3, i + 2, k, g, c1), vm2 = dy1(t3, i - 2, k, g, c1);
+        const T dxdy = (T(8) * (vp1 - vm1) - (vp2 - vm2)) * c1;
+        ga[a] = dx2(t2, i, k, g, c2) - dy2(t2, i, k, g, c2) - T(4) * dxdy;
     }
 }
 
@@ -230,15 +258,15 @@ void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* 
 }
 
 template <typename T>
-void launch_sgs(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t0, T* t1, T* t2, T* t3,
-                const Geom& g, cudaStream_t s, const T* Ulat, const int* dn) {
+void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t2, T* t3, uint8_t* halo,
+                     const Geom& g, cudaStream_t s, const int* dn) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
-    { k_sgs1<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Ulat ? nullptr : t0, t1, g, c1, c2); note_launch(); }
-    { k_sgs2<T><<<blocks_for(N), kThreads, 0, s>>>(Ulat ? Ulat : t0, t1, t2, t3, g, c1, csh2); note_launch(); }
-    { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(t3, t0, g, c1); note_launch(); }
-    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t0, meta, n, ga, g, c1, c2, dn); note_launch(); }
+    cudaMemsetAsync(halo, 0, (size_t)N, s);
+    if (n > 0) { k_sgs_halo_mark<<<blocks_for(n), kThreads, 0, s>>>(meta, n, halo, g, dn); note_launch(); }
+    { k_sgs_halo_products<T><<<blocks_for(N), kThreads, 0, s>>>(psi, halo, t2, t3, g, c1, c2, csh2); note_launch(); }
+    if (n > 0) { k_sgs_halo_forcing<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t3, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
 template <typename T>
@@ -308,8 +336,8 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
 #define WRC_INST(T)                                                                                          \
     template void launch_velocity_active<T>(const T*, const uint32_t*, long long, T*, T*, const Geom&,      \
                                             cudaStream_t, const int*);                                      \
-    template void launch_sgs<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, T*, T*,           \
-                                const Geom&, cudaStream_t, const T*, const int*);                           \
+    template void launch_sgs_halo<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, uint8_t*,    \
+                                     const Geom&, cudaStream_t, const int*);                                \
     template void launch_velocity_gather<T>(const T*, const T*, const uint32_t*, long long, T*, T*,         \
                                             cudaStream_t, const int*);                                      \
     template void launch_sgs_from_strain<T>(const T*, const T*, const uint32_t*, long long, double, T*, T*, \

@@ -212,7 +212,8 @@ __global__ void k_compact_count(const uint8_t* __restrict__ act, const uint8_t* 
         if (key >= 0 && __popc(peers & ((1u << lane) - 1u)) == 0) atomicAdd(&sc[key], __popc(peers));
     }
     __syncthreads();
-    if (threadIdx.x < nkeys) blk_counts[(long long)blockIdx.x * nkeys + threadIdx.x] = sc[threadIdx.x];
+    // key-major: the scan reads each key's counts contiguously
+    if (threadIdx.x < nkeys) blk_counts[(long long)threadIdx.x * gridDim.x + blockIdx.x] = sc[threadIdx.x];
 }
 
 // Exclusive scan of v over a block of 1024 threads; *total receives the sum.
@@ -243,31 +244,50 @@ __device__ int block_excl_scan_1024(int v, int& total) {
     return excl;
 }
 
+// Offsets of each block's bucket entries (key-major arrays, [key][block]):
+// one block of 1024 threads, thread t taking a contiguous chunk of blocks;
+// the chunk's counts are read once into registers (up to kScanChunk blocks,
+// more in further rounds), the bucket bases are added when written.
+constexpr int kScanChunk = 4;
+
 __global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ blk_counts, int nblk, int nkeys,
                                                        int* __restrict__ blk_off, int* __restrict__ counts) {
     __shared__ int s_tot[kMaxKeys];
     const int chunk = (nblk + 1023) / 1024;
     const int b0 = threadIdx.x * chunk;
     const int b1 = min(b0 + chunk, nblk);
+    int base = 0;   // bucket base: the totals of the keys before kk
     for (int kk = 0; kk < nkeys; ++kk) {
+        const int* cnt = blk_counts + (long long)kk * nblk;
+        int* off = blk_off + (long long)kk * nblk;
+        int c[kScanChunk];
         int sum = 0;
-        for (int b = b0; b < b1; ++b) sum += blk_counts[(long long)b * nkeys + kk];
+        for (int b = b0; b < b1; b += kScanChunk) {
+#pragma unroll
+            for (int u = 0; u < kScanChunk; ++u) c[u] = b + u < b1 ? cnt[b + u] : 0;
+#pragma unroll
+            for (int u = 0; u < kScanChunk; ++u) sum += c[u];
+        }
         int total;
         const int excl = block_excl_scan_1024(sum, total);
-        int run = excl;
-        for (int b = b0; b < b1; ++b) {
-            blk_off[(long long)b * nkeys + kk] = run;
-            run += blk_counts[(long long)b * nkeys + kk];
+        int run = base + excl;
+        if (b1 - b0 <= kScanChunk) {   // the counts are still in c
+#pragma unroll
+            for (int u = 0; u < kScanChunk; ++u)
+                if (b0 + u < b1) {
+                    off[b0 + u] = run;
+                    run += c[u];
+                }
+        } else {
+            for (int b = b0; b < b1; ++b) {
+                off[b] = run;
+                run += cnt[b];
+            }
         }
         if (threadIdx.x == 0) s_tot[kk] = total;
+        base += total;
     }
     __syncthreads();
-    // bucket bases
-    for (int kk = 0; kk < nkeys; ++kk) {
-        int base = 0;
-        for (int q = 0; q < kk; ++q) base += s_tot[q];
-        for (int b = b0; b < b1; ++b) blk_off[(long long)b * nkeys + kk] += base;
-    }
     if (threadIdx.x < nkeys) counts[threadIdx.x] = s_tot[threadIdx.x];
 }
 
@@ -276,7 +296,7 @@ __global__ void k_compact_scatter(const uint8_t* __restrict__ act, const uint8_t
     __shared__ int s_base[kMaxKeys];
     __shared__ int s_wc[kThreads / 32][kMaxKeys];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x < nkeys) s_base[threadIdx.x] = blk_off[(long long)blockIdx.x * nkeys + threadIdx.x];
+    if (threadIdx.x < nkeys) s_base[threadIdx.x] = blk_off[(long long)threadIdx.x * gridDim.x + blockIdx.x];
     const long long N = (long long)g.NJ * g.NJ;
     const long long base = (long long)blockIdx.x * kTile;
     for (int r = 0; r < kTileRounds; ++r) {
