@@ -149,11 +149,13 @@ template <> struct Log2<16> { static constexpr int v = 4; };
 // writes element r to (b - k) R + k + r p.  After the last pass (p = n/R)
 // that position is b + r n/R, so the outputs stay in the same registers;
 // otherwise they go through shared memory and come back strided.
+// The twiddles of a pass come from its own table ptw[r p + k] = w_{R p}^{r k}
+// (r < R, k < p): the lanes of a warp hold consecutive k, so each load of a
+// warp reads consecutive entries.
 template <int E, int R, bool INV, typename C>
-__device__ __forceinline__ void radix_pass(C (&v)[E], C* sm, int i, int nt, int p, int logn, int logp,
-                                           const C* __restrict__ tw, bool last) {
+__device__ __forceinline__ void radix_pass(C (&v)[E], C* sm, int i, int nt, int p, const C* __restrict__ ptw,
+                                           bool last) {
     constexpr int G = E / R;
-    const int sh = logn - logp - Log2<R>::v;   // w_{R p}^m = tw[m << sh]
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const int b = i + nt * g;
@@ -164,7 +166,7 @@ __device__ __forceinline__ void radix_pass(C (&v)[E], C* sm, int i, int nt, int 
         if (p > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = __ldg(tw + ((r * k) << sh));
+                C w = __ldg(ptw + r * p + k);
                 if (INV) w.y = -w.y;
                 u[r] = cmul(u[r], w);
             }
@@ -191,21 +193,51 @@ __device__ __forceinline__ void radix_pass(C (&v)[E], C* sm, int i, int nt, int 
 // i + e n/E on entry and on exit): a radix-R0 pass first when R0 > 1, then
 // radix-E passes.  Unnormalised; INV uses exp(+2 pi i ...).  Every thread of
 // the block must call it (it synchronises the block).
+// tw: the per-pass twiddle tables, one after the other for the passes with
+// p > 1 (R p entries each), as built by k_fft_pass_tables.
 template <int E, int R0, bool INV, typename C>
 __device__ __forceinline__ void fft_reg(C (&v)[E], C* sm, int i, int n, int logn, const C* __restrict__ tw) {
     const int nt = n / E;
     int p = 1, logp = 0;
+    const C* ptw = tw;
     if constexpr (R0 > 1) {
-        radix_pass<E, R0, INV>(v, sm, i, nt, p, logn, logp, tw, false);
+        radix_pass<E, R0, INV>(v, sm, i, nt, p, ptw, false);   // p = 1: no twiddles
         p *= R0;
         logp += Log2<R0>::v;
     }
     const int npass = (logn - logp) / Log2<E>::v;
     for (int q = 0; q < npass; ++q) {
-        radix_pass<E, E, INV>(v, sm, i, nt, p, logn, logp, tw, q == npass - 1);
+        radix_pass<E, E, INV>(v, sm, i, nt, p, ptw, q == npass - 1);
+        if (p > 1) ptw += E * p;
         p *= E;
         logp += Log2<E>::v;
     }
+}
+
+// The per-pass tables of fft_reg from tw[t] = exp(-2 pi i t / n): for each
+// pass with sub-length p > 1 and radix R, entries w_{R p}^{r k} = tw[(r k) n / (R p)]
+// at [r p + k] (copies, so the transforms are those of the single table).
+template <typename C>
+__global__ void k_fft_pass_tables(const C* __restrict__ tw, C* __restrict__ ptw, int n, int logn, int E, int R0) {
+    int p = 1, logp = 0, off = 0;
+    auto table = [&](int R, int logR) {
+        if (p > 1)
+            for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < R * p; idx += gridDim.x * blockDim.x) {
+                const int r = idx / p, k = idx - r * p;
+                ptw[off + idx] = tw[(r * k) << (logn - logp - logR)];
+            }
+        if (p > 1) off += R * p;
+        p *= R;
+        logp += logR;
+    };
+    int logE = 0;
+    while ((1 << logE) < E) ++logE;
+    if (R0 > 1) {
+        int logR0 = 0;
+        while ((1 << logR0) < R0) ++logR0;
+        table(R0, logR0);
+    }
+    while (logp < logn) table(E, logE);
 }
 
 // ---- kernels ------------------------------------------------------------------
@@ -518,7 +550,7 @@ struct Shape {
         const int nt = n / E, F = nt >= 128 ? 1 : 128 / nt;
         const int thr = F * nt;
         const size_t smem = sizeof(C) * (size_t)F * smlen_of(n);
-        const C* tw = (const C*)p.tw;
+        const C* tw = (const C*)p.ptw;   // per-pass tables
         const dim3 tb(32, 8);
         const dim3 g_nh((h + 31) / 32, (n + 31) / 32);   // n x h  -> h x n
         const dim3 g_hn((n + 31) / 32, (h + 31) / 32);   // h x n  -> n x h
@@ -569,11 +601,16 @@ int setup_all() {
 template <typename T>
 int plan_init_t(PoissonPlan& p, const Geom& g, cudaStream_t s) {
     if (cudaMalloc(&p.tw, sizeof(cx_t<T>) * p.n) != cudaSuccess) return -1;
+    if (cudaMalloc(&p.ptw, sizeof(cx_t<T>) * 2 * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.sigma, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.dsym, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (setup_all<T>() != 0) return -2;
     { k_fft_init<T><<<(p.n + 255) / 256, 256, 0, s>>>((cx_t<T>*)p.tw, (T*)p.sigma, (T*)p.dsym, p.n,
                                                        1.0 / (3.0 * g.h * g.h), 1.0 / (6.0 * g.h)); note_launch(); }
+    const int E = p.logn < 4 ? 8 : 16;
+    const int R0 = p.logn < 4 ? 1 : 1 << (p.logn % 4);
+    { k_fft_pass_tables<cx_t<T>><<<(p.n + 255) / 256, 256, 0, s>>>((const cx_t<T>*)p.tw, (cx_t<T>*)p.ptw, p.n,
+                                                                    p.logn, E, R0); note_launch(); }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -589,6 +626,8 @@ int poisson_plan_init(PoissonPlan& p, const Geom& g, bool fp32, cudaStream_t s) 
 
 void poisson_plan_free(PoissonPlan& p) {
     if (p.tw) cudaFree(p.tw);
+    if (p.ptw) cudaFree(p.ptw);
+    p.ptw = nullptr;
     if (p.sigma) cudaFree(p.sigma);
     if (p.dsym) cudaFree(p.dsym);
     p.tw = nullptr;

@@ -48,7 +48,8 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
 struct PoissonPlan {
     int n = 0, logn = 0;
     bool fp32 = false;
-    void* tw = nullptr;      // exp(-2 pi i t/n), t < n/2 (complex of the run's bulk type)
+    void* tw = nullptr;      // exp(-2 pi i t/n), t < n (complex of the run's bulk type)
+    void* ptw = nullptr;     // the same twiddles as per-pass tables (see fft.cu)
     void* sigma = nullptr;   // symbol of the 4th-order second-derivative stencil
     void* dsym = nullptr;    // symbol of the 4th-order first-derivative stencil (imaginary part)
 };
