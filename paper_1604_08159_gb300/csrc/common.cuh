@@ -11,7 +11,7 @@ namespace wrc {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 152 * 8;   // grid-stride cap: 8 resident blocks per SM
 constexpr int kMaxKeys = 16;          // compaction buckets (active + ghosts per level)
-constexpr int kTileRounds = 16;       // compaction tile = kThreads * kTileRounds points
+constexpr int kTileRounds = 16;       // compaction: points per thread (16, one 16-byte load per mask)
 constexpr int kTile = kThreads * kTileRounds;
 
 // Finest-lattice geometry.  NJ is a power of two; p = k*NJ + i.

@@ -190,30 +190,55 @@ __global__ void k_validate_grid(const uint8_t* __restrict__ act, int* __restrict
 // key(p) = 0 for an active point, j for a ghost of level j, -1 otherwise; the
 // output list holds bucket 0, then bucket 1, ..., each in lattice order.
 
-__device__ __forceinline__ int compact_key(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho,
-                                           long long p, const Geom& g) {
-    if (act[p]) return 0;
-    if (gho[p]) return level_of((int)(p & g.mask), (int)(p >> g.L), g.J);
-    return -1;
+// Keys of the 16 consecutive lattice points p0 .. p0 + 15 of one thread
+// (p0 a multiple of 16; NJ^2 is a multiple of 64): the active and ghost masks
+// read as one 16-byte vector each.
+__device__ __forceinline__ void keys16(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho, long long p0,
+                                       long long N, const Geom& g, int (&key)[16]) {
+    if (p0 >= N) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) key[u] = -1;
+        return;
+    }
+    const uint4 va = *reinterpret_cast<const uint4*>(act + p0);
+    const uint4 vh = *reinterpret_cast<const uint4*>(gho + p0);
+    const uint32_t wa[4] = {va.x, va.y, va.z, va.w}, wh[4] = {vh.x, vh.y, vh.z, vh.w};
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const uint32_t ab = (wa[u >> 2] >> (8 * (u & 3))) & 0xffu;
+        const uint32_t hb = (wh[u >> 2] >> (8 * (u & 3))) & 0xffu;
+        const long long p = p0 + u;
+        key[u] = ab ? 0 : (hb ? level_of((int)(p & g.mask), (int)(p >> g.L), g.J) : -1);
+    }
 }
 
-__global__ void k_compact_count(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho, Geom g,
-                                int nkeys, int* __restrict__ blk_counts) {
-    __shared__ int sc[kMaxKeys];
-    if (threadIdx.x < kMaxKeys) sc[threadIdx.x] = 0;
-    __syncthreads();
+// Counts per key of one tile of kTile = 16 kThreads points (thread t: points
+// 16 t .. 16 t + 15 of the tile), key-major into blk_counts[key][block].
+__global__ void __launch_bounds__(kThreads) k_compact_count(const uint8_t* __restrict__ act,
+                                                            const uint8_t* __restrict__ gho, Geom g, int nkeys,
+                                                            int* __restrict__ blk_counts) {
+    __shared__ int s_w[kThreads / 32][kMaxKeys];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long N = (long long)g.NJ * g.NJ;
-    const long long base = (long long)blockIdx.x * kTile;
-    const int lane = threadIdx.x & 31;
-    for (int r = 0; r < kTileRounds; ++r) {
-        const long long p = base + (long long)r * kThreads + threadIdx.x;
-        const int key = p < N ? compact_key(act, gho, p, g) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && __popc(peers & ((1u << lane) - 1u)) == 0) atomicAdd(&sc[key], __popc(peers));
+    int key[16];
+    keys16(act, gho, (long long)blockIdx.x * kTile + 16LL * threadIdx.x, N, g, key);
+#pragma unroll
+    for (int kk = 0; kk < kMaxKeys; ++kk) {
+        if (kk >= nkeys) break;
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) c += key[u] == kk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) s_w[wid][kk] = c;
     }
     __syncthreads();
-    // key-major: the scan reads each key's counts contiguously
-    if (threadIdx.x < nkeys) blk_counts[(long long)threadIdx.x * gridDim.x + blockIdx.x] = sc[threadIdx.x];
+    if (threadIdx.x < nkeys) {
+        int c = 0;
+        for (int w = 0; w < kThreads / 32; ++w) c += s_w[w][threadIdx.x];
+        // key-major: the scan reads each key's counts contiguously
+        blk_counts[(long long)threadIdx.x * gridDim.x + blockIdx.x] = c;
+    }
 }
 
 // Exclusive scan of v over a block of 1024 threads; *total receives the sum.
@@ -291,35 +316,46 @@ __global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ b
     if (threadIdx.x < nkeys) counts[threadIdx.x] = s_tot[threadIdx.x];
 }
 
-__global__ void k_compact_scatter(const uint8_t* __restrict__ act, const uint8_t* __restrict__ gho, Geom g,
-                                  int nkeys, const int* __restrict__ blk_off, int* __restrict__ list) {
+// Stable scatter of one tile: thread t's entries of key k go after those of
+// the threads before it (an exclusive scan over the block per key) and the
+// block's base offset, in lattice order.
+__global__ void __launch_bounds__(kThreads) k_compact_scatter(const uint8_t* __restrict__ act,
+                                                              const uint8_t* __restrict__ gho, Geom g, int nkeys,
+                                                              const int* __restrict__ blk_off,
+                                                              int* __restrict__ list) {
     __shared__ int s_base[kMaxKeys];
-    __shared__ int s_wc[kThreads / 32][kMaxKeys];
+    __shared__ int s_w[kThreads / 32][kMaxKeys];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x < nkeys) s_base[threadIdx.x] = blk_off[(long long)threadIdx.x * gridDim.x + blockIdx.x];
     const long long N = (long long)g.NJ * g.NJ;
-    const long long base = (long long)blockIdx.x * kTile;
-    for (int r = 0; r < kTileRounds; ++r) {
-        for (int t = threadIdx.x; t < (kThreads / 32) * kMaxKeys; t += kThreads) (&s_wc[0][0])[t] = 0;
-        __syncthreads();
-        const long long p = base + (long long)r * kThreads + threadIdx.x;
-        const int key = p < N ? compact_key(act, gho, p, g) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (key >= 0 && rank == 0) s_wc[wid][key] = __popc(peers);
-        __syncthreads();
-        if (key >= 0) {
-            int off = s_base[key];
-            for (int w = 0; w < wid; ++w) off += s_wc[w][key];
-            list[off + rank] = (int)p;
+    const long long p0 = (long long)blockIdx.x * kTile + 16LL * threadIdx.x;
+    int key[16];
+    keys16(act, gho, p0, N, g, key);
+    int cnt[kMaxKeys], incl[kMaxKeys];
+#pragma unroll
+    for (int kk = 0; kk < kMaxKeys; ++kk) {
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) c += key[u] == kk;
+        cnt[kk] = c;
+        int x = c;   // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        __syncthreads();
-        if (threadIdx.x < nkeys) {
-            int tot = 0;
-            for (int w = 0; w < kThreads / 32; ++w) tot += s_wc[w][threadIdx.x];
-            s_base[threadIdx.x] += tot;
-        }
-        __syncthreads();
+        incl[kk] = x;
+        if (lane == 31 && kk < nkeys) s_w[wid][kk] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kMaxKeys; ++kk) {
+        if (kk >= nkeys || cnt[kk] == 0) continue;
+        int off = s_base[kk] + incl[kk] - cnt[kk];
+        for (int w = 0; w < wid; ++w) off += s_w[w][kk];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if (key[u] == kk) list[off++] = (int)(p0 + u);
     }
 }
 
@@ -403,13 +439,16 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
 // as a weighted sum of active values.  The weights are products of the DD4
 // weights (-1, 9, 9, -1)/16, exact binary fractions, and repeated points are
 // merged, so the rows are exact.  A row longer than rmax sets *overflow.
-// One warp per ghost: the predictor points are visited in a fixed order and
-// each one's row (a single entry for an active point) is merged into the
-// ghost's row by all lanes at once -- a row's entries are distinct, so every
-// entry either adds to one existing entry or is appended, new entries in
-// row order.  The entries, their order and their sums are those of merging
-// the terms one by one.
+// One warp per ghost.  Lane q < 16 takes predictor q (order: a fastest, then
+// b; 4 predictors for a 1-D prediction, 16 for the tensor product), looks up
+// its grid index and, for a ghost, its row length; the rows (up to
+// kRowStage entries each) are then staged in shared memory with all loads in
+// flight, and merged in predictor order by all lanes at once -- a row's
+// entries are distinct, so each entry either adds to one existing entry or
+// is appended, new entries in row order.  The entries, their order and their
+// sums are those of merging the terms one by one.
 constexpr int kRowWarps = 4;   // warps (ghosts in flight) per block
+constexpr int kRowStage = 32;  // staged entries per predictor row (longer rows read the rest directly)
 
 __global__ void __launch_bounds__(32 * kRowWarps)
 k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
@@ -419,6 +458,8 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
     constexpr int kCap = 64;
     __shared__ int s_idx[kRowWarps][kCap];
     __shared__ double s_wt[kRowWarps][kCap];
+    __shared__ int s_pi[kRowWarps][16][kRowStage];
+    __shared__ double s_pw[kRowWarps][16][kRowStage];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* idx = s_idx[wid];
     double* wt = s_wt[wid];
@@ -435,73 +476,98 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
     const int cap = rmax < kCap ? rmax : kCap;
     const int sh = g.J - j;
     const int s = 1 << sh;
-    const int off[4] = {-3 * s, -s, s, 3 * s};
-    const double w4[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
     for (long long t = (long long)blockIdx.x * kRowWarps + wid; t < cnt; t += (long long)gridDim.x * kRowWarps) {
         const long long gi = gbeg - n_act + t;          // ghost number
         const int p = list[gbeg + t];
         const int i = p & g.mask, k = p >> g.L;
         const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
         const bool two_d = oi == ok;                    // odd-odd: tensor product of two 1-D predictions
+        const int np = two_d ? 16 : 4;
+        // lane q < np: predictor q = (a, b) = (q % 4, q / 4)
+        int my_id = -1, my_rl = 0;
+        double my_w = 0.0;
+        if (lane < np) {
+            const int a = lane & 3, b = lane >> 2;
+            const int off_a = (2 * a - 3) * s, off_b = (2 * b - 3) * s;   // -3s, -s, s, 3s
+            const double wa = (a == 1 || a == 2) ? 0.5625 : -0.0625;
+            const double wb = (b == 1 || b == 2) ? 0.5625 : -0.0625;
+            int qi = i, qk = k;
+            if (two_d) {
+                qi = (i + off_a) & g.mask;
+                qk = (k + off_b) & g.mask;
+                my_w = wa * wb;
+            } else if (oi) {
+                qi = (i + off_a) & g.mask;
+                my_w = wa;
+            } else {
+                qk = (k + off_a) & g.mask;
+                my_w = wa;
+            }
+            my_id = lat2idx[((long long)qk << g.L) + qi];
+            if (my_id >= n_act && my_id < n_tot) my_rl = row_len[my_id - n_act];
+            else my_rl = 1;
+        }
+        // stage the predictor rows (their loads all in flight)
+        for (int q = 0; q < np; ++q) {
+            const int id = __shfl_sync(0xffffffffu, my_id, q);
+            const int rl = __shfl_sync(0xffffffffu, my_rl, q);
+            if (id >= n_act && id < n_tot && lane < rl && lane < kRowStage) {
+                const long long r = id - n_act;
+                s_pi[wid][q][lane] = row_idx[r * rmax + lane];
+                s_pw[wid][q][lane] = row_w[r * rmax + lane];
+            }
+        }
+        __syncwarp();
         int len = 0;
         bool over = false;
-        for (int b = 0; b < (two_d ? 4 : 1); ++b) {
-            for (int a = 0; a < 4; ++a) {
-                int qi = i, qk = k;
-                double w = w4[a];
-                if (two_d) {
-                    qi = (i + off[a]) & g.mask;
-                    qk = (k + off[b]) & g.mask;
-                    w = w4[a] * w4[b];
-                } else if (oi) {
-                    qi = (i + off[a]) & g.mask;
-                } else {
-                    qk = (k + off[a]) & g.mask;
-                }
-                const int id = lat2idx[((long long)qk << g.L) + qi];
-                if (id < 0 || id >= n_tot) {            // not a grid point: record, do not read
-                    over = true;
-                    continue;
-                }
-                const int* ri = nullptr;
-                const double* rw = nullptr;
-                int rl = 1;
-                if (id >= n_act) {
-                    const long long r = id - n_act;
-                    rl = row_len[r];
-                    ri = row_idx + r * rmax;
-                    rw = row_w + r * rmax;
-                }
-                for (int e0 = 0; e0 < rl; e0 += 32) {
-                    const int e = e0 + lane;
-                    const bool has = e < rl;
-                    int my = 0;
-                    double mw = 0.0;
-                    if (has) {
-                        my = ri ? ri[e] : id;
-                        mw = ri ? w * rw[e] : w;
+        for (int q = 0; q < np; ++q) {
+            const int id = __shfl_sync(0xffffffffu, my_id, q);
+            const int rl0 = __shfl_sync(0xffffffffu, my_rl, q);
+            const double w = __shfl_sync(0xffffffffu, my_w, q);
+            if (id < 0 || id >= n_tot) {                 // not a grid point: record, do not read
+                over = true;
+                continue;
+            }
+            const bool ghost = id >= n_act;
+            const int rl = ghost ? rl0 : 1;
+            const long long r = id - n_act;
+            for (int e0 = 0; e0 < rl; e0 += 32) {
+                const int e = e0 + lane;
+                const bool has = e < rl;
+                int my = 0;
+                double mw = 0.0;
+                if (has) {
+                    if (!ghost) {
+                        my = id;
+                        mw = w;
+                    } else if (e < kRowStage) {
+                        my = s_pi[wid][q][e];
+                        mw = w * s_pw[wid][q][e];
+                    } else {
+                        my = row_idx[r * rmax + e];
+                        mw = w * row_w[r * rmax + e];
                     }
-                    int pos = -1;
-                    if (has)
-                        for (int q = 0; q < len; ++q)
-                            if (idx[q] == my) {
-                                pos = q;
-                                break;
-                            }
-                    if (pos >= 0) wt[pos] += mw;
-                    const unsigned fresh = __ballot_sync(0xffffffffu, has && pos < 0);
-                    if (has && pos < 0) {
-                        const int slot = len + __popc(fresh & ((1u << lane) - 1u));
-                        if (slot < cap) {
-                            idx[slot] = my;
-                            wt[slot] = mw;
+                }
+                int pos = -1;
+                if (has)
+                    for (int qq = 0; qq < len; ++qq)
+                        if (idx[qq] == my) {
+                            pos = qq;
+                            break;
                         }
+                if (pos >= 0) wt[pos] += mw;
+                const unsigned fresh = __ballot_sync(0xffffffffu, has && pos < 0);
+                if (has && pos < 0) {
+                    const int slot = len + __popc(fresh & ((1u << lane) - 1u));
+                    if (slot < cap) {
+                        idx[slot] = my;
+                        wt[slot] = mw;
                     }
-                    const int nf = __popc(fresh);
-                    if (len + nf > cap) over = true;
-                    len = len + nf < cap ? len + nf : cap;
-                    __syncwarp();
                 }
+                const int nf = __popc(fresh);
+                if (len + nf > cap) over = true;
+                len = len + nf < cap ? len + nf : cap;
+                __syncwarp();
             }
         }
         for (int e = lane; e < len; e += 32) {
