@@ -195,9 +195,11 @@ wrc_status wrc_profile(wrc_run* run, int32_t enable);
  * the last arrival of its blocks, the index of the last block to arrive, and
  * the release of block 0, in microseconds from the start of block 0 (device
  * global timer).  Barrier 0 follows b = A_n omega + g, barrier 1 the ghost
- * values of v_0; then each Arnoldi step has three: after the first dots,
- * after the second dots, after the new basis vector (the last step stops
- * after its second); the final barrier follows phi_1, before the update.
+ * values of v_0, barriers 2 and 3 the first projection of A v_0; then each
+ * further Arnoldi step has two: after its one reduction (the second pass of
+ * the previous vector and the first of the new one) and after the new
+ * vectors (the last step stops after its reduction); the final barrier
+ * follows phi_1, before the update.
  * *nphases receives the count.  WRC_ERR_ARG if cap < 4 * count; WRC_ERR_STATE without a traced
  * launch.  Synchronises. */
 wrc_status wrc_query_phase_trace(wrc_run* run, double* out, int32_t cap, int32_t* nphases);

@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kPT = 128;      // threads per block of the single-run kernel
 constexpr int kNV = 32;       // accumulator slots: basis vectors per pass (<= m + 1 <= 32)
-constexpr int kOutP = 33;     // partial sums per block: kNV dots + a squared norm
+constexpr int kOutP = 66;     // partial sums per block: two sets of (kNV dots + one product)
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -103,22 +103,76 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
     }
 }
 
-// Sum over all blocks of part[b * kOutP + t], t < nout, into s_out.  The
-// lanes of a warp are split into L = 32 / ns groups (ns = nout rounded up to
-// a power of two, at most 32, so L > 1 only when nout <= 16): lane g ns + t of
+// Sum over all blocks of part[b * kOutP + t], t < nout (<= 64), into s_out.
+// Up to 32 outputs, the lanes of a warp are split into L = 32 / ns groups
+// (ns = nout rounded up to a power of two, so L > 1 only for 16 outputs or
+// fewer): lane g ns + t of
 // warp w adds output t of blocks w + 4 (g + L u), u = 0, 1, ... (for 4 warps),
 // in order; the groups are then combined by shuffles and the warps' sums
 // added in warp order.  Same order in every block.  A lane's loads go out
 // kReduceBatch at a time ahead of their ordered additions, so one L2 round
 // trip covers up to kReduceBatch partials per lane.
-constexpr int kReduceBatch = 16;
+constexpr int kReduceBatch = 24;
 
 template <int PT>
 __device__ __forceinline__ void reduce_all(const double* part, int nout, double* s_out,
                                            double (*s_red)[kNV + 1], int nb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kW = PT / 32;
-    if (nout > 32) nout = 32;   // (never: nout <= m + 1 <= 32)
+    if (nout > 32) {
+        // two chunks: lane t adds outputs t and 32 + t (if any) of blocks
+        // w, w + 4, ..., the loads of both going out together
+        constexpr int kB = kReduceBatch / 2;
+        const int t2 = 32 + lane;
+        const bool has2 = t2 < nout;
+        double v1 = 0.0, v2 = 0.0;
+        const double* p = part + lane;
+        int b = wid;
+        for (; b + (kB - 1) * kW < nb; b += kB * kW) {
+            double x1[kB], x2[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                x1[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
+                x2[u] = has2 ? __ldcg(p + 32 + (size_t)(b + u * kW) * kOutP) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                v1 += x1[u];
+                v2 += x2[u];
+            }
+        }
+        const int rest = b < nb ? (nb - 1 - b) / kW + 1 : 0;   // < kB
+        double x1[kB], x2[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (u < rest) {
+                x1[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
+                x2[u] = has2 ? __ldcg(p + 32 + (size_t)(b + u * kW) * kOutP) : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (u < rest) {
+                v1 += x1[u];
+                v2 += x2[u];
+            }
+        s_red[wid][lane] = v1;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 32; q += blockDim.x) {
+            double sum = 0.0;
+            for (int w = 0; w < kW; ++w) sum += s_red[w][q];
+            s_out[q] = sum;
+        }
+        __syncthreads();
+        s_red[wid][lane] = v2;
+        __syncthreads();
+        for (int q = threadIdx.x; q < nout - 32; q += blockDim.x) {
+            double sum = 0.0;
+            for (int w = 0; w < kW; ++w) sum += s_red[w][q];
+            s_out[32 + q] = sum;
+        }
+        __syncthreads();
+        return;
+    }
     int ns = 1;
     while (ns < nout) ns <<= 1;
     const int L = 32 / ns;
@@ -148,9 +202,9 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
     if (g == 0 && t < nout) s_red[wid][t] = v;
     __syncthreads();
     for (int q = threadIdx.x; q < nout; q += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < kW; ++w) s += s_red[w][q];
-        s_out[q] = s;
+        double sum = 0.0;
+        for (int w = 0; w < kW; ++w) sum += s_red[w][q];
+        s_out[q] = sum;
     }
     __syncthreads();
 }
@@ -359,6 +413,67 @@ __device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* _
     }
 }
 
+// Ghost values of step j of the delayed scheme (groups of kGhostLanes lanes
+// per ghost, as ghost_values): q_j at ghost t, Gb_j = (Gu - sum_{q<j} s_q Gb_q) / h,
+// then the next u there, Gu <- (rows . z) / h - sum_{q<=j} c_q Gb_q (with the
+// new Gb_j), also written into the lattice vector Lq.
+template <typename T, int PT>
+__device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __restrict__ z, T* __restrict__ Gb,
+                                           long long ldg, T* __restrict__ Gu, const double* s, const double* c,
+                                           int j, double hinv, T* __restrict__ Lq, int bid, int nb) {
+    constexpr int kGroups = PT / kGhostLanes;
+    constexpr int kPerWarp = 32 / kGhostLanes;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gl = lane % kGhostLanes;
+    for (int q0 = wid * kPerWarp; bid + (long long)nb * q0 < A.ng; q0 += kGroups) {
+        const long long tl = bid + (long long)nb * (q0 + lane / kGhostLanes);
+        const bool valid = tl < A.ng;
+        const int t = valid ? (int)tl : 0;
+        const int rl = valid ? A.row_len[t] : 0;
+        const size_t base = (size_t)t * A.rmax;
+        double part = 0.0;   // rows . z, this lane's share
+        for (int e0 = 0; e0 < A.rmax; e0 += kGhostLanes * kGatherLane) {
+            if (!__any_sync(0xffffffffu, e0 < rl)) break;
+            int id[kGatherLane];
+            double wt[kGatherLane], xv[kGatherLane];
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u) {
+                const int e = e0 + gl + kGhostLanes * u;
+                if (e < rl) {
+                    id[u] = A.row_idx[base + e];
+                    wt[u] = A.row_w[base + e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u)
+                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)__ldcg(z + id[u]);
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u)
+                if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
+        }
+        double ss = 0.0, cs = 0.0;
+        if (valid)
+            for (int q = gl; q < j; q += kGhostLanes) {
+                const double gq = (double)Gb[(size_t)q * ldg + t];
+                ss += s[q] * gq;
+                cs += c[q] * gq;
+            }
+#pragma unroll
+        for (int o = 1; o < kGhostLanes; o <<= 1) {
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        }
+        if (valid && gl == 0) {
+            const T gbj = (T)(((double)Gu[t] - ss) * hinv);
+            const T gu = (T)(part * hinv - (cs + c[j] * (double)gbj));
+            Gb[(size_t)j * ldg + t] = gbj;
+            Gu[t] = gu;
+            Lq[A.glist[t]] = gu;
+        }
+    }
+}
+
 // The Krylov step of one problem, run by its nb blocks (bid = this block's
 // index among them).
 template <typename T, int PT>
@@ -377,12 +492,13 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_sc[4];   // beta, 1/beta, h_{j+1,j}, 1/h_{j+1,j}
     __shared__ int s_stop;       // 0 go on, 1 happy breakdown, 2 non-finite
     __shared__ int s_int[3];     // phi_1: blown up, sub-steps, Taylor terms
+    __shared__ double sH[kNV][kNV + 1];   // H, held by every block
+    __shared__ double s_cc[kNV + 1];      // coefficients of the next u
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
     const bool lead = bid == 0 && threadIdx.x == 0;
     double* P0 = A.part;
-    double* P1 = P0 + (size_t)nb * kOutP;
     const T nu = (T)A.nu, r = (T)A.r, c1J = (T)A.c1J, c2J = (T)A.c2J;
     const int m = A.m;
     const long long ld = A.ld, ldg = A.ldg;
@@ -395,6 +511,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     }
     if (bid == 0)   // H is written by this block only
         for (int t = threadIdx.x; t < (m + 1) * m; t += blockDim.x) A.H[t] = 0.0;
+    for (int t = threadIdx.x; t < kNV * (kNV + 1); t += blockDim.x) (&sH[0][0])[t] = 0.0;
 
     // b = A_n omega + g  (L holds R(omega), ghosts included)
 #pragma unroll
@@ -440,95 +557,193 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             Lq[A.glist[t]] = g;
         });
         if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-        for (int j = 0; j < m; ++j) {
-            const int nv = j + 1;
-            // phase 1: w = A v_j and the first Gram-Schmidt dots
+
+        // Arnoldi with CGS2 whose second pass is delayed by one step: step j
+        // applies A to u, the vector of step j-1 after its first projection,
+        // and one reduction gives s = Q^T u, |u|^2, t = Q^T z and u.z
+        // (z = A u).  Then q_j = (u - Q s) / h with h^2 = |u|^2 - |s|^2 (the
+        // second pass; column j-1 of H gets + s, H[j][j-1] = h), and, by the
+        // Arnoldi relation A Q_{j-1} = Q_j H, A q_j = (z - Q_j g) / h with
+        // g = H s: its first projection h1 = ([t; (u.z - s.t)/h] - g) / h
+        // and the next u = z / h - Q_j (g / h + h1), without a second operator
+        // application.  One reduction and one barrier per step.
+        T* __restrict__ zb = basis + (size_t)m * ld;   // z, in the spare basis row
+        T* __restrict__ Gu = Gb + (size_t)m * ldg;     // ghost values of u
+        // step 0: z = A q_0 and its first projection
+#pragma unroll
+        for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
+        for (int a = a0; a < n; a += stride) {
+            const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+            zb[a] = z;
+            const double zd = (double)z;
+            acc[0] += (double)basis[a] * zd;
+            acc[kNV] += zd * zd;
+        }
+        block_partials<PT>(acc, 1, P0 + (size_t)bid * kOutP, s_red);
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+        reduce_all<PT>(P0, 2, s_h, s_red, nb);
+        if (threadIdx.x == 0) {
+            sH[0][0] = s_h[0];
+            s_c[0] = s_h[0];
+        }
+        __syncthreads();
+        for (int a = a0; a < n; a += stride) {
+            const T u = project_out<T>(zb[a], basis + a, ld, s_c, 1);
+            w[a] = u;
+            Lq[meta_pos(A.meta[a])] = u;
+        }
+        ghost_values<T, PT>(A, zb, Gb, ldg, s_c, 1, bid, nb, [&](int t, double gv) {
+            const T g = (T)gv;
+            Gu[t] = g;
+            Lq[A.glist[t]] = g;
+        });
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+
+        for (int j = 1; j <= m; ++j) {
+            const bool last = j == m;   // only the second pass of u is left
+            // z = A u; dots of u and of z with q_0 .. q_{j-1}.  While both sets
+            // fit the accumulators (j <= 15), one pass and one block reduction,
+            // interleaved: acc[2t] = q_t.u, acc[2t+1] = q_t.z, acc[30] = |u|^2,
+            // acc[31] = u.z; otherwise two passes, acc[t] = q_t.u then q_t.z
+            // (layout in the partials: s, |u|^2, t, u.z)
+            const bool inter = !last && 2 * j <= kNV - 2;
+            if (inter) {
+#pragma unroll
+                for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
+                for (int a = a0; a < n; a += stride) {
+                    const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+                    zb[a] = z;
+                    const double zd = (double)z, ud = (double)w[a];
+#pragma unroll
+                    for (int t = 0; t < kNV / 2 - 1; ++t)
+                        if (t < j) {
+                            const double q = (double)basis[(size_t)t * ld + a];
+                            acc[2 * t] += q * ud;
+                            acc[2 * t + 1] += q * zd;
+                        }
+                    acc[kNV - 2] += ud * ud;
+                    acc[kNV - 1] += ud * zd;
+                }
+                block_partials<PT>(acc, kNV, P0 + (size_t)bid * kOutP, s_red);
+            } else {
 #pragma unroll
             for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
             for (int a = a0; a < n; a += stride) {
-                const T v = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
-                w[a] = v;
-                const double vd = (double)v;
+                const double ud = (double)w[a];
 #pragma unroll
                 for (int t = 0; t < kNV; ++t)
-                    if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * vd;
-                acc[kNV] += vd * vd;
+                    if (t < j) acc[t] += (double)basis[(size_t)t * ld + a] * ud;
+                acc[kNV] += ud * ud;
             }
-            block_partials<PT>(acc, nv, P0 + (size_t)bid * kOutP, s_red);
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-            reduce_all<PT>(P0, nv + 1, s_h, s_red, nb);
-            const double wn2 = s_h[nv];
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) s_c[t] = s_h[t];
-            __syncthreads();
-            // phase 2: w' = w - V h1 (stored), second dots and |w'|^2
+            block_partials<PT>(acc, j, P0 + (size_t)bid * kOutP, s_red);
+            if (!last) {
+                __syncthreads();   // s_red is reused
 #pragma unroll
-            for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
-            for (int a = a0; a < n; a += stride) {
-                const T x = project_out<T>(w[a], basis + a, ld, s_c, nv);
-                w[a] = x;
-                const double xd = (double)x;
+                for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
+                for (int a = a0; a < n; a += stride) {
+                    const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+                    zb[a] = z;
+                    const double zd = (double)z;
 #pragma unroll
-                for (int t = 0; t < kNV; ++t)
-                    if (t < nv) acc[t] += (double)basis[(size_t)t * ld + a] * xd;
-                acc[kNV] += xd * xd;
+                    for (int t = 0; t < kNV; ++t)
+                        if (t < j) acc[t] += (double)basis[(size_t)t * ld + a] * zd;
+                    acc[kNV] += (double)w[a] * zd;
+                }
+                block_partials<PT>(acc, j, P0 + (size_t)bid * kOutP + (j + 1), s_red);
             }
-            block_partials<PT>(acc, nv, P1 + (size_t)bid * kOutP, s_red);
+            }
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-            reduce_all<PT>(P1, nv + 1, s_h, s_red, nb);
-            // h_{:,j} = h1 + h2; |w''|^2 = |w'|^2 - |h2|^2 (V orthonormal,
-            // h2 = V^T w'), the breakdown tests and 1/h_{j+1,j}: warp 0, once
+            reduce_all<PT>(P0, inter ? kNV : (last ? j + 1 : 2 * j + 2), s_h, s_red, nb);
+            // scalars (warp 0, every block the same): the second pass of u,
+            // the breakdown tests, and the coefficients of q_j and the next u
             if (threadIdx.x < 32) {
-                const int t = threadIdx.x;
-                double h2 = 0.0;
-                bool bad = false;
-                if (t < nv) {
-                    h2 = s_h[t] * s_h[t];
-                    bad = !isfinite(s_c[t] + s_h[t]);
-                    if (bid == 0) A.H[(size_t)t * m + j] = s_c[t] + s_h[t];
-                }
+                const int i = threadIdx.x;
+                const double si = i < j ? s_h[inter ? 2 * i : i] : 0.0;
+                const double hp = i < j ? sH[i][j - 1] : 0.0;   // first pass of column j-1
+                const double ti = (!last && i < j) ? s_h[inter ? 2 * i + 1 : j + 1 + i] : 0.0;
+                const double uu = s_h[inter ? kNV - 2 : j];
+                const double uz = last ? 0.0 : s_h[inter ? kNV - 1 : 2 * j + 1];
+                double s2 = si * si, hp2 = hp * hp, st = si * ti;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, o);
-                bad = __any_sync(0xffffffffu, bad);
-                if (t == 0) {
-                    const double q = fmax(s_h[nv] - h2, 0.0);   // h_{j+1,j}^2
-                    double hn, inv;
-                    sqrt_and_rsqrt(q, hn, inv);
-                    s_sc[2] = hn;
-                    s_sc[3] = inv;
-                    // breakdown: h <= tol |A v_j|, compared squared
-                    s_stop = (bad || !isfinite(q)) ? 2 : (q <= A.tol * A.tol * wn2 ? 1 : 0);
-                    if (bid == 0) A.H[(size_t)(j + 1) * m + j] = hn;
+                for (int o = 16; o > 0; o >>= 1) {
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    hp2 += __shfl_xor_sync(0xffffffffu, hp2, o);
+                    st += __shfl_xor_sync(0xffffffffu, st, o);
+                }
+                const bool bad = __any_sync(0xffffffffu, !isfinite(hp + si) || !isfinite(ti)) || !isfinite(uu) ||
+                                 !isfinite(uz);
+                const double q2 = fmax(uu - s2, 0.0);   // h_{j,j-1}^2
+                double h = 0.0, hinv = 0.0;
+                if (i == 0) sqrt_and_rsqrt(q2, h, hinv);
+                h = __shfl_sync(0xffffffffu, h, 0);
+                hinv = __shfl_sync(0xffffffffu, hinv, 0);
+                if (i < j) {
+                    sH[i][j - 1] = hp + si;
+                    s_c[i] = si;
+                }
+                if (i == 0) sH[j][j - 1] = h;
+                // breakdown: h <= tol |A q_{j-1}|, |A q_{j-1}|^2 = |h1|^2 + |u|^2
+                const int stop = (bad || !isfinite(q2)) ? 2 : (q2 <= A.tol * A.tol * (hp2 + uu) ? 1 : 0);
+                __syncwarp();
+                if (stop == 0 && !last) {
+                    double gp[4] = {0.0, 0.0, 0.0, 0.0};   // g = H s, rows 0 .. j
+                    if (i <= j)
+#pragma unroll
+                        for (int c = 0; c < kNV; ++c)
+                            if (c < j) gp[c & 3] += sH[i][c] * s_c[c];
+                    const double gi = (gp[0] + gp[1]) + (gp[2] + gp[3]);
+                    const double qz = (uz - st) * hinv;
+                    const double h1 = i < j ? (ti - gi) * hinv : (i == j ? (qz - gi) * hinv : 0.0);
+                    if (i <= j) {
+                        s_cc[i] = gi * hinv + h1;
+                        sH[i][j] = h1;
+                    }
+                }
+                if (i == 0) {
+                    s_sc[2] = h;
+                    s_sc[3] = hinv;
+                    s_stop = stop;
                 }
             }
             __syncthreads();
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) s_c[t] = s_h[t];
             const int stop = s_stop;
-            __syncthreads();
             if (stop == 2) {
                 if (lead) atomicOr(A.flags, 1);
-                k = j + 1;
+                k = j;
                 break;
             }
-            if (stop == 1) {
-                k = j + 1;
+            if (stop == 1 || last) {
+                k = j;
                 break;
             }
-            if (j + 1 == m) break;
-            // phase 3: v_{j+1} = (w' - V h2) / hn at the active points; at the
-            // ghosts by linearity from w' and the ghost values of v_0..v_j
-            const double inv2 = s_sc[3];
+            // q_j = (u - Q s) / h and the next u = z / h - Q_j c at the own
+            // points; at the ghosts by linearity
+            const double hinv = s_sc[3];
             for (int a = a0; a < n; a += stride) {
-                const T x = project_out<T>(w[a], basis + a, ld, s_c, nv);
-                const T v = (T)((double)x * inv2);
-                basis[(size_t)(j + 1) * ld + a] = v;
-                Lq[meta_pos(A.meta[a])] = v;
+                T ps[4] = {T(0), T(0), T(0), T(0)}, pc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+                for (int t = 0; t < kNV; ++t)
+                    if (t < j) {
+                        const T q = basis[(size_t)t * ld + a];
+                        ps[t & 3] += q * (T)s_c[t];
+                        pc[t & 3] += q * (T)s_cc[t];
+                    }
+                const T qj = (T)((double)(w[a] - ((ps[0] + ps[1]) + (ps[2] + ps[3]))) * hinv);
+                basis[(size_t)j * ld + a] = qj;
+                const T un = (T)((double)zb[a] * hinv) - (((pc[0] + pc[1]) + (pc[2] + pc[3])) + qj * (T)s_cc[j]);
+                w[a] = un;
+                Lq[meta_pos(A.meta[a])] = un;
             }
-            ghost_values<T, PT>(A, w, Gb, ldg, s_c, nv, bid, nb, [&](int t, double gv) {
-                const T g = (T)(gv * inv2);
-                Gb[(size_t)(j + 1) * ldg + t] = g;
-                Lq[A.glist[t]] = g;
-            });
+            ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_c, s_cc, j, hinv, Lq, bid, nb);
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+        }
+        // H (every block holds it) to global memory, by block 0
+        if (bid == 0) {
+            for (int e = threadIdx.x; e < (k + 1) * k; e += PT) {
+                const int i = e / k, c = e - i * k;
+                if (i <= c + 1) A.H[(size_t)i * m + c] = sH[i][c];
+            }
+            __syncthreads();
         }
     }
     // y = phi_1(dt H_k) e_1 by block 0 (which wrote H), then every block:
