@@ -494,6 +494,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ int s_int[3];     // phi_1: blown up, sub-steps, Taylor terms
     __shared__ double sH[kNV][kNV + 1];   // H, held by every block
     __shared__ double s_cc[kNV + 1];      // coefficients of the next u
+    __shared__ double s_tmp[4];           // |s|^2, |h1|^2, s.t of a step
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
@@ -654,55 +655,67 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             }
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
             reduce_all<PT>(P0, inter ? kNV : (last ? j + 1 : 2 * j + 2), s_h, s_red, nb);
-            // scalars (warp 0, every block the same): the second pass of u,
-            // the breakdown tests, and the coefficients of q_j and the next u
-            if (threadIdx.x < 32) {
-                const int i = threadIdx.x;
+            // scalars (every block the same): the second pass of u, the
+            // breakdown tests, and the coefficients of q_j and the next u.  The
+            // FP64 work is spread over the warps: one warp's FP64 instruction
+            // occupies its SM sub-partition for about 64 cycles on this part.
+            {
+                constexpr int kW = PT / 32;
+                const int i = threadIdx.x & 31, wid = threadIdx.x >> 5;
                 const double si = i < j ? s_h[inter ? 2 * i : i] : 0.0;
                 const double hp = i < j ? sH[i][j - 1] : 0.0;   // first pass of column j-1
                 const double ti = (!last && i < j) ? s_h[inter ? 2 * i + 1 : j + 1 + i] : 0.0;
                 const double uu = s_h[inter ? kNV - 2 : j];
                 const double uz = last ? 0.0 : s_h[inter ? kNV - 1 : 2 * j + 1];
-                double s2 = si * si, hp2 = hp * hp, st = si * ti;
+                // |s|^2, |h1|^2 and s.t, each summed by one warp
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                    hp2 += __shfl_xor_sync(0xffffffffu, hp2, o);
-                    st += __shfl_xor_sync(0xffffffffu, st, o);
+                for (int q = 0; q < 3; ++q)
+                    if (q % kW == wid) {
+                        double v = q == 0 ? si * si : (q == 1 ? hp * hp : si * ti);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (i == 0) s_tmp[q] = v;
+                    }
+                __syncthreads();
+                if (wid == 0) {
+                    const bool bad = __any_sync(0xffffffffu, !isfinite(hp + si) || !isfinite(ti)) || !isfinite(uu) ||
+                                     !isfinite(uz);
+                    if (i < j) {
+                        sH[i][j - 1] = hp + si;
+                        s_c[i] = si;
+                    }
+                    if (i == 0) {
+                        const double q2 = fmax(uu - s_tmp[0], 0.0);   // h_{j,j-1}^2
+                        double h, hinv;
+                        sqrt_and_rsqrt(q2, h, hinv);
+                        sH[j][j - 1] = h;
+                        s_sc[2] = h;
+                        s_sc[3] = hinv;
+                        // breakdown: h <= tol |A q_{j-1}|, |A q_{j-1}|^2 = |h1|^2 + |u|^2
+                        s_stop = (bad || !isfinite(q2)) ? 2 : (q2 <= A.tol * A.tol * (s_tmp[1] + uu) ? 1 : 0);
+                    }
                 }
-                const bool bad = __any_sync(0xffffffffu, !isfinite(hp + si) || !isfinite(ti)) || !isfinite(uu) ||
-                                 !isfinite(uz);
-                const double q2 = fmax(uu - s2, 0.0);   // h_{j,j-1}^2
-                double h = 0.0, hinv = 0.0;
-                if (i == 0) sqrt_and_rsqrt(q2, h, hinv);
-                h = __shfl_sync(0xffffffffu, h, 0);
-                hinv = __shfl_sync(0xffffffffu, hinv, 0);
-                if (i < j) {
-                    sH[i][j - 1] = hp + si;
-                    s_c[i] = si;
-                }
-                if (i == 0) sH[j][j - 1] = h;
-                // breakdown: h <= tol |A q_{j-1}|, |A q_{j-1}|^2 = |h1|^2 + |u|^2
-                const int stop = (bad || !isfinite(q2)) ? 2 : (q2 <= A.tol * A.tol * (hp2 + uu) ? 1 : 0);
-                __syncwarp();
-                if (stop == 0 && !last) {
-                    double gp[4] = {0.0, 0.0, 0.0, 0.0};   // g = H s, rows 0 .. j
+                __syncthreads();
+                if (s_stop == 0 && !last) {
+                    // g = H s (rows 0 .. j): column groups c = w (mod kW) per warp
+                    double gp = 0.0;
                     if (i <= j)
 #pragma unroll
-                        for (int c = 0; c < kNV; ++c)
-                            if (c < j) gp[c & 3] += sH[i][c] * s_c[c];
-                    const double gi = (gp[0] + gp[1]) + (gp[2] + gp[3]);
-                    const double qz = (uz - st) * hinv;
-                    const double h1 = i < j ? (ti - gi) * hinv : (i == j ? (qz - gi) * hinv : 0.0);
-                    if (i <= j) {
+                        for (int cc = 0; cc < kNV / kW; ++cc) {
+                            const int c = cc * kW + wid;
+                            if (c < j) gp += sH[i][c] * s_c[c];
+                        }
+                    s_red[wid][i] = gp;
+                    __syncthreads();
+                    if (wid == 0 && i <= j) {
+                        double gi = s_red[0][i];
+                        for (int w = 1; w < kW; ++w) gi += s_red[w][i];
+                        const double hinv = s_sc[3];
+                        const double qz = (uz - s_tmp[2]) * hinv;
+                        const double h1 = i < j ? (ti - gi) * hinv : (qz - gi) * hinv;
                         s_cc[i] = gi * hinv + h1;
                         sH[i][j] = h1;
                     }
-                }
-                if (i == 0) {
-                    s_sc[2] = h;
-                    s_sc[3] = hinv;
-                    s_stop = stop;
                 }
             }
             __syncthreads();
