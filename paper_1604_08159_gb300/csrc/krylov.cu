@@ -368,7 +368,7 @@ __device__ __forceinline__ T project_out(T x, const T* __restrict__ col, long lo
 // ahead of the additions, and combine the lane sums by shuffles.  Returns,
 // for lane 0 of each group with a ghost, the value in *out and its index in
 // *tg (-1 otherwise).  Called by every thread of the block (warp-uniform loop).
-constexpr int kGhostLanes = 4;
+constexpr int kGhostLanes = 8;
 constexpr int kGatherLane = 8;
 
 template <typename T, int PT, typename F>
