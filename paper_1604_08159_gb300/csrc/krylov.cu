@@ -1,18 +1,25 @@
 // Krylov projection of the time step (Sec. 2.1: the discrete system projected
 // onto a Krylov subspace): one persistent cooperative kernel per step,
 //   b = A_n omega + g,  beta = |b|,  v_0 = b / beta,
-//   Arnoldi with classical Gram-Schmidt applied twice (FP64 inner products,
-//   deterministic reductions; the norm after the second pass from
-//   |w''|^2 = |w'|^2 - |h2|^2), happy breakdown when h_{j+1,j} <= tol |A v_j|,
-//   then, in the same launch, y = phi_1(dt H_k) e_1 from the exponential of
-//   the augmented Hessenberg matrix (block 0), one more grid barrier, and
-//   omega <- omega + dt beta V_k y (every block, its own points).
+//   Arnoldi with classical Gram-Schmidt applied twice, the second pass
+//   delayed by one step (FP64 inner products, deterministic reductions; the
+//   norm after the second pass from |u|^2 - |s|^2), happy breakdown when
+//   h_{j+1,j} <= tol |A v_j|, then, in the same launch, y = phi_1(dt H_k) e_1
+//   from the exponential of the augmented Hessenberg matrix (block 0), one
+//   more grid barrier, and omega <- omega + dt beta V_k y (every block, its
+//   own points).
 // Ghost values of each new basis vector come from exact interpolation rows
-// over the active points, so one Arnoldi step takes three phases: operator and
-// first dots | first update and second dots | second update, normalisation
-// and ghosts.  Phases are separated by a grid barrier with a bounded wait; every block
-// reduces the per-block partial sums itself, in the same order, so all blocks
-// hold identical coefficients and take identical breakdown decisions.
+// over the active points.  One Arnoldi step takes two phases: the operator
+// and all dots of the step | the scalars, the new vectors and their ghost
+// values.  Phases are separated by a grid barrier with a bounded wait; every
+// block reduces the per-block partial sums itself, in the same order, so all
+// blocks hold identical coefficients and take identical breakdown decisions.
+// On this part one warp issues at most one FP64 instruction per ~64 cycles
+// (about one per 19 cycles per SM), so the kernel is organised around the
+// count of FP64 instructions each warp issues and the latency of dependent
+// steps, not around bytes.
+#include <type_traits>
+
 #include "kernels.h"
 #include "operator.cuh"
 
@@ -23,6 +30,8 @@ namespace {
 constexpr int kPT = 128;      // threads per block of the single-run kernel
 constexpr int kNV = 32;       // accumulator slots: basis vectors per pass (<= m + 1 <= 32)
 constexpr int kOutP = 66;     // partial sums per block: two sets of (kNV dots + one product)
+constexpr int kGhostLanes = 8;   // lanes per ghost value (ghost_values, ghost_step)
+constexpr int kGatherLane = 8;   // row terms per lane fetched ahead of their additions
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -30,12 +39,84 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
+// Calls f(std::integral_constant<int, t>) for t = n-1, n-2, ..., 0 (0 <= n <= N
+// <= 32): one jump into an unrolled sequence, so that the calls with t >= n
+// issue no instructions at all.  (A loop "if (t < n)" over all N unrolled
+// iterations becomes predicated instructions, and a predicated-off FP64
+// instruction still takes its ~64 issue cycles on this part; a "break" in the
+// loop keeps it from being unrolled, sending indexed accumulators to local
+// memory.)
+template <int N, typename F>
+__device__ __forceinline__ void down_from(int n, F&& f) {
+    static_assert(N >= 1 && N <= 32, "down_from covers at most 32 calls");
+    switch (n) {
+#define WRC_DOWN(t)                                            \
+    case (t) + 1:                                              \
+        if constexpr ((t) < N) f(std::integral_constant<int, (t)>{}); \
+        [[fallthrough]];
+        WRC_DOWN(31) WRC_DOWN(30) WRC_DOWN(29) WRC_DOWN(28) WRC_DOWN(27) WRC_DOWN(26) WRC_DOWN(25) WRC_DOWN(24)
+        WRC_DOWN(23) WRC_DOWN(22) WRC_DOWN(21) WRC_DOWN(20) WRC_DOWN(19) WRC_DOWN(18) WRC_DOWN(17) WRC_DOWN(16)
+        WRC_DOWN(15) WRC_DOWN(14) WRC_DOWN(13) WRC_DOWN(12) WRC_DOWN(11) WRC_DOWN(10) WRC_DOWN(9) WRC_DOWN(8)
+        WRC_DOWN(7) WRC_DOWN(6) WRC_DOWN(5) WRC_DOWN(4) WRC_DOWN(3) WRC_DOWN(2) WRC_DOWN(1) WRC_DOWN(0)
+#undef WRC_DOWN
+        default:
+            break;
+    }
+}
+
+// Sum of x over the 32 lanes of a warp, returned to every lane, through 40
+// doubles of shared memory ws in a fixed order: lane l < 8 adds lanes
+// 4l..4l+3 pairwise, then every lane adds the eight sums pairwise.  Inside
+// this kernel a shuffle tree on FP64 values was measured at ~600 cycles per
+// level on this part; this takes 4 dependent FP64 additions and shared
+// memory round trips.
+__device__ __forceinline__ double warp_sum(double x, double* ws) {
+    const int l = threadIdx.x & 31;
+    ws[l] = x;
+    __syncwarp();
+    if (l < 8) ws[32 + l] = (ws[4 * l] + ws[4 * l + 1]) + (ws[4 * l + 2] + ws[4 * l + 3]);
+    __syncwarp();
+    const double* p = ws + 32;
+    const double r = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    __syncwarp();
+    return r;
+}
+
+// Sums over each group of kGhostLanes (= 8) consecutive lanes of the NV
+// values v[] of every lane, through NV * 32 doubles of shared memory ws: lane
+// gl < NV of a group adds quantity gl of its group pairwise (7 FP64 additions
+// for all quantities at once), and lane 0 of the group receives the sums in
+// v[].  Same order in every block.
+template <int NV>
+__device__ __forceinline__ void group_sums(double (&v)[NV], double* ws) {
+    static_assert(kGhostLanes == 8 && NV <= 8, "groups of eight lanes");
+    const int lane = threadIdx.x & 31, gl = lane & 7, g8 = lane - gl;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) ws[q * 32 + lane] = v[q];
+    __syncwarp();
+    double sum = 0.0;
+    if (gl < NV) {
+        const double* p = ws + gl * 32 + g8;
+        sum = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    }
+    __syncwarp();
+    if (gl < NV) ws[gl * 32 + g8] = sum;
+    __syncwarp();
+    if (gl == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = ws[q * 32 + lane];
+    __syncwarp();
+}
+
 // Grid-wide barrier for a cooperative launch: one atomic per block on a
 // counter whose top bit flips when the last block arrives (block 0 adds
-// 2^31 - (G - 1), the others 1, so each barrier adds exactly 2^31).  The wait
-// of each block is bounded by limit_ns; a block that runs out sets bit 1 of
-// *err, and every waiter leaves as soon as *err is non-zero, so the kernel
-// always returns.
+// 2^31 - (G - 1), the others 1, so each barrier adds exactly 2^31).  The
+// arrival follows a release fence and the wait ends with an acquire fence
+// (fence.acq_rel at GPU scope, lighter than the sequentially consistent
+// __threadfence), so the plain loads of the next phase see every block's
+// writes.  The wait of each block is bounded by limit_ns; a block that runs
+// out sets bit 1 of *err, and every waiter leaves as soon as *err is
+// non-zero, so the kernel always returns.
 // The barrier spans the nb blocks of one problem (bid = block index within it).
 // With a trace buffer, the arrival of each block and the release of block 0
 // are stamped (phase index `ph`, counted by the caller).
@@ -45,7 +126,7 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, 
     if (threadIdx.x == 0) {
         if (trace && ph < kTracePhases) trace[1 + (size_t)ph * (nb + 1) + bid] = gtimer();
         const unsigned inc = bid == 0 ? 0x80000000u - (unsigned)(nb - 1) : 1u;
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         const unsigned old = atomicAdd(bar, inc);
         volatile unsigned* vbar = bar;
         volatile int* verr = err;
@@ -57,19 +138,21 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, 
                 break;
             }
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (trace && ph < kTracePhases && bid == 0) trace[1 + (size_t)ph * (nb + 1) + nb] = gtimer();
     }
     __syncthreads();
     return *(volatile int*)err == 0;
 }
 
-// Per-block sums of acc[0..ndots) and of acc[kNV] (a squared norm) into
-// dst[0..ndots] (the norm at index ndots).  The first NS dot accumulators
+// Per-block sums of acc[0..ndots) into dst[0..ndots) and, with NORM, of
+// acc[kNV] (a squared norm) into dst[ndots].  The first NS dot accumulators
 // (NS = ndots rounded up to a power of two) are reduced across the warp by a
 // reduce-scatter (NS - 1 exchanges; afterwards lane l holds the warp sum of
-// accumulator l mod NS), the norm by a shuffle tree.
-template <int PT>
+// accumulator l mod NS), the norm by a shuffle tree.  Every FP64 addition
+// costs a warp ~64 cycles of issue on this part, so only the NS accumulators
+// in use take part.
+template <int PT, bool NORM>
 __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots, double* dst,
                                                double (*s_red)[kNV + 1]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -90,12 +173,14 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
         for (int s = ns; s < 32; s <<= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], s);
         if (lane < ns) s_red[wid][lane] = acc[0];
     }
-    double v = acc[kNV];
+    if (NORM) {
+        double v = acc[kNV];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[wid][kNV] = v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[wid][kNV] = v;
+    }
     __syncthreads();
-    for (int t = threadIdx.x; t <= ndots; t += blockDim.x) {
+    for (int t = threadIdx.x; t < ndots + (NORM ? 1 : 0); t += blockDim.x) {
         const int src = t < ndots ? t : kNV;
         double sum = 0.0;
         for (int q = 0; q < PT / 32; ++q) sum += s_red[q][src];
@@ -111,7 +196,10 @@ __device__ __forceinline__ void block_partials(double (&acc)[kNV + 1], int ndots
 // in order; the groups are then combined by shuffles and the warps' sums
 // added in warp order.  Same order in every block.  A lane's loads go out
 // kReduceBatch at a time ahead of their ordered additions, so one L2 round
-// trip covers up to kReduceBatch partials per lane.
+// trip covers up to kReduceBatch partials per lane; the additions of a
+// partial batch are entered by one jump (down_from: last partial first).  The partials were written by
+// other blocks before the grid barrier, whose fences make plain loads see
+// them (L1 is invalidated there).
 constexpr int kReduceBatch = 24;
 
 template <int PT>
@@ -132,8 +220,8 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
             double x1[kB], x2[kB];
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
-                x1[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
-                x2[u] = has2 ? __ldcg(p + 32 + (size_t)(b + u * kW) * kOutP) : 0.0;
+                x1[u] = p[(size_t)(b + u * kW) * kOutP];
+                x2[u] = has2 ? p[32 + (size_t)(b + u * kW) * kOutP] : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
@@ -146,15 +234,14 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
 #pragma unroll
         for (int u = 0; u < kB; ++u)
             if (u < rest) {
-                x1[u] = __ldcg(p + (size_t)(b + u * kW) * kOutP);
-                x2[u] = has2 ? __ldcg(p + 32 + (size_t)(b + u * kW) * kOutP) : 0.0;
+                x1[u] = p[(size_t)(b + u * kW) * kOutP];
+                x2[u] = has2 ? p[32 + (size_t)(b + u * kW) * kOutP] : 0.0;
             }
-#pragma unroll
-        for (int u = 0; u < kB; ++u)
-            if (u < rest) {
-                v1 += x1[u];
-                v2 += x2[u];
-            }
+        down_from<kB>(rest, [&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            v1 += x1[u];
+            v2 += x2[u];
+        });
         s_red[wid][lane] = v1;
         __syncthreads();
         for (int q = threadIdx.x; q < 32; q += blockDim.x) {
@@ -185,7 +272,7 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
         for (; b + (kReduceBatch - 1) * bstep < nb; b += kReduceBatch * bstep) {
             double x[kReduceBatch];
 #pragma unroll
-            for (int u = 0; u < kReduceBatch; ++u) x[u] = __ldcg(p + (size_t)(b + u * bstep) * kOutP);
+            for (int u = 0; u < kReduceBatch; ++u) x[u] = p[(size_t)(b + u * bstep) * kOutP];
 #pragma unroll
             for (int u = 0; u < kReduceBatch; ++u) v += x[u];
         }
@@ -193,13 +280,20 @@ __device__ __forceinline__ void reduce_all(const double* part, int nout, double*
         double x[kReduceBatch];
 #pragma unroll
         for (int u = 0; u < kReduceBatch; ++u)
-            if (u < rest) x[u] = __ldcg(p + (size_t)(b + u * bstep) * kOutP);
-#pragma unroll
-        for (int u = 0; u < kReduceBatch; ++u)
-            if (u < rest) v += x[u];
+            if (u < rest) x[u] = p[(size_t)(b + u * bstep) * kOutP];
+        down_from<kReduceBatch>(rest, [&](auto uc) { v += x[decltype(uc)::value]; });
     }
-    for (int o = ns; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // the L groups
-    if (g == 0 && t < nout) s_red[wid][t] = v;
+    // the L groups, added in group order by the lanes of group 0 (shared
+    // memory rather than a shuffle tree: see warp_sum)
+    s_red[wid][lane] = v;
+    __syncwarp();
+    if (L > 1) {
+        double c = v;
+        if (g == 0 && t < nout)
+            for (int q = 1; q < L; ++q) c += s_red[wid][q * ns + t];
+        __syncwarp();
+        if (g == 0 && t < nout) s_red[wid][t] = c;
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < nout; q += blockDim.x) {
         double sum = 0.0;
@@ -328,17 +422,27 @@ __device__ __forceinline__ void phi1_block(const double* __restrict__ H, int k, 
     if (w == 0 && r < m) y[r] = r < k ? x : 0.0;
 }
 
+// True for a finite double (exponent field not all ones), by integer
+// operations on its high word (an FP64 comparison would take a warp's FP64
+// issue slot for ~64 cycles).
+__device__ __forceinline__ bool finite_bits(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+
 // sqrt(q) and 1/sqrt(q) in FP64 for the normalisation of a new basis vector:
 // an FP32 reciprocal square root as the seed, then two Newton-Raphson steps
-// y <- y (3 - q y^2) / 2 in FP64 (each doubles the correct bits: ~22 -> ~44
-// -> full precision), sqrt(q) = q y.  FP64 division and square root are long
-// instruction sequences on this part; this is a handful of FMAs.  Values
-// outside the FP32 range take the library's sqrt and division.
+// y <- y (3/2 - (q/2) y^2) in FP64 (each doubles the correct bits: ~22 -> ~44
+// -> full precision), sqrt(q) = q y; three dependent FP64 operations per
+// step.  FP64 division and square root are long instruction sequences on
+// this part.  q outside [2^-99, 2^99] (or negative, or not finite) takes the
+// library's sqrt and division; the range test is integer work on the
+// exponent.
 __device__ __forceinline__ void sqrt_and_rsqrt(double q, double& s, double& r) {
-    if (q > 1e-30 && q < 1e30) {
+    const int hi = __double2hiint(q);
+    const int e = (hi >> 20) & 0x7ff;
+    if (hi >= 0 && e > 1023 - 99 && e < 1023 + 99) {
+        const double hq = 0.5 * q;
         double y = (double)rsqrtf((float)q);
-        y = y * (1.5 - 0.5 * q * y * y);
-        y = y * (1.5 - 0.5 * q * y * y);
+        y = y * fma(-hq, y * y, 1.5);
+        y = y * fma(-hq, y * y, 1.5);
         r = y;
         s = q * y;
     } else {
@@ -368,13 +472,11 @@ __device__ __forceinline__ T project_out(T x, const T* __restrict__ col, long lo
 // ahead of the additions, and combine the lane sums by shuffles.  Returns,
 // for lane 0 of each group with a ghost, the value in *out and its index in
 // *tg (-1 otherwise).  Called by every thread of the block (warp-uniform loop).
-constexpr int kGhostLanes = 8;
-constexpr int kGatherLane = 8;
 
 template <typename T, int PT, typename F>
 __device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* __restrict__ x,
                                              const T* __restrict__ Gb, long long ldg, const double* c, int nc,
-                                             int bid, int nb, F&& emit) {
+                                             int bid, int nb, double* ws, F&& emit) {
     constexpr int kGroups = PT / kGhostLanes;                 // ghosts per block per pass
     constexpr int kPerWarp = 32 / kGhostLanes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -400,27 +502,28 @@ __device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* _
             }
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
-                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)__ldcg(x + id[u]);
+                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)x[id[u]];
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
                 if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
         }
         if (valid)
             for (int q = gl; q < nc; q += kGhostLanes) part -= c[q] * (double)Gb[(size_t)q * ldg + t];
-#pragma unroll
-        for (int o = 1; o < kGhostLanes; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (valid && gl == 0) emit(t, part);
+        double pv[1] = {part};
+        group_sums<1>(pv, ws);
+        if (valid && gl == 0) emit(t, pv[0]);
     }
 }
 
 // Ghost values of step j of the delayed scheme (groups of kGhostLanes lanes
-// per ghost, as ghost_values): q_j at ghost t, Gb_j = (Gu - sum_{q<j} s_q Gb_q) / h,
-// then the next u there, Gu <- (rows . z) / h - sum_{q<=j} c_q Gb_q (with the
-// new Gb_j), also written into the lattice vector Lq.
+// per ghost, as ghost_values): q_j at ghost g, Gb_j = (Gu - sum_{q<j} s_q Gb_q) / h,
+// then the next u there, Gu <- (rows . z - sum_{q<j} t_q Gb_q - qz Gb_j) / h
+// (with the new Gb_j), also written into the lattice vector Lq.
 template <typename T, int PT>
 __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __restrict__ z, T* __restrict__ Gb,
-                                           long long ldg, T* __restrict__ Gu, const double* s, const double* c,
-                                           int j, double hinv, T* __restrict__ Lq, int bid, int nb) {
+                                           long long ldg, T* __restrict__ Gu, const double* s, const double* tv,
+                                           double qz, int j, double hinv, T* __restrict__ Lq, int bid, int nb,
+                                           double* ws) {
     constexpr int kGroups = PT / kGhostLanes;
     constexpr int kPerWarp = 32 / kGhostLanes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -446,7 +549,7 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
             }
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
-                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)__ldcg(z + id[u]);
+                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)z[id[u]];
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
                 if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
@@ -456,21 +559,102 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
             for (int q = gl; q < j; q += kGhostLanes) {
                 const double gq = (double)Gb[(size_t)q * ldg + t];
                 ss += s[q] * gq;
-                cs += c[q] * gq;
+                cs += tv[q] * gq;
             }
-#pragma unroll
-        for (int o = 1; o < kGhostLanes; o <<= 1) {
-            part += __shfl_xor_sync(0xffffffffu, part, o);
-            ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        }
+        double pv[3] = {part, ss, cs};
+        group_sums<3>(pv, ws);
         if (valid && gl == 0) {
-            const T gbj = (T)(((double)Gu[t] - ss) * hinv);
-            const T gu = (T)(part * hinv - (cs + c[j] * (double)gbj));
+            const T gbj = (T)(((double)Gu[t] - pv[1]) * hinv);
+            const T gu = (T)((pv[0] - pv[2] - qz * (double)gbj) * hinv);
             Gb[(size_t)j * ldg + t] = gbj;
             Gu[t] = gu;
             Lq[A.glist[t]] = gu;
         }
+    }
+}
+
+// The dots of Arnoldi step j >= 1 over the block's own points, with z = A u
+// applied at each point first (with_z; z goes to zb), as block partial sums
+// in dst: [q_0.u .. q_{j-1}.u, |u|^2] at 0..j and [q_0.z .. q_{j-1}.z, u.z]
+// at j+1..2j+1 (the first j+1 only without z).  Transposed: the threads stage
+// u and z of their points in shared memory, and each lane forms whole dot
+// products over its warp's 32 points (x row r = q_r for r < j, u for r = j,
+// loaded 16 bytes at a time), so the sum over the warp's points is part of
+// the product loop and no reduction across lanes is needed: 32 (j < 16, u
+// and z on separate half-warps) or 64 FP64 operations per lane and point
+// batch, against j or 2j products plus ~31 additions per reduce-scatter
+// with one product per point and lane.  The warps' sums are added in warp
+// order.
+template <typename T, int PT>
+__device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool with_z, int bid, int nb, double* dst,
+                                          double (*s_dot)[2 * kNV], double (*s_uz)[2][33]) {
+    const T* __restrict__ Ua = (const T*)A.Ua;
+    const T* __restrict__ Va = (const T*)A.Va;
+    const T* __restrict__ Lq = (const T*)A.Lq;
+    const T* __restrict__ basis = (const T*)A.basis;
+    const T* __restrict__ w = (const T*)A.w;
+    T* __restrict__ zb = (T*)A.basis + (size_t)A.m * A.ld;
+    const T nu = (T)A.nu, r = (T)A.r, c1J = (T)A.c1J, c2J = (T)A.c2J;
+    const int n = A.n, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool split = j < 16;                         // rows 0..j fit a half-warp
+    const int row = split ? (lane & 15) : lane;
+    const bool zlane = split && lane >= 16;
+    const bool act = row <= j && (with_z || !zlane);
+    const T* __restrict__ xbase = row < j ? basis + (size_t)row * A.ld : w;
+    constexpr int kV = 16 / sizeof(T);                 // values per 16-byte load
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    double accA = 0.0, accB = 0.0;
+    for (int wb = bid * PT + wid * 32; wb < n; wb += nb * PT) {
+        const int a = wb + lane;
+        T u = T(0), z = T(0);
+        if (a < n) {
+            u = w[a];
+            if (with_z) {
+                z = apply_point<T, false>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+                zb[a] = z;
+            }
+        }
+        s_uz[wid][0][lane] = (double)u;
+        s_uz[wid][1][lane] = (double)z;
+        __syncwarp();
+        if (act) {
+            const int nv = n - wb;   // valid points of the batch (>= 1; all 32 when >= 32)
+            const V* xr = reinterpret_cast<const V*>(xbase + wb);   // 16-byte aligned: ld and wb are multiples of 32
+            const double* yA = s_uz[wid][zlane ? 1 : 0];
+            const double* yB = s_uz[wid][1];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                V xv[16 / kV];
+#pragma unroll
+                for (int q = 0; q < 16 / kV; ++q) xv[q] = xr[hh * (16 / kV) + q];
+#pragma unroll
+                for (int q = 0; q < 16 / kV; ++q) {
+                    const T* xs = reinterpret_cast<const T*>(&xv[q]);
+#pragma unroll
+                    for (int e = 0; e < kV; ++e) {
+                        const int p = hh * 16 + q * kV + e;
+                        const double x = p < nv ? (double)xs[e] : 0.0;
+                        accA += x * yA[p];
+                        if (!split && with_z) accB += x * yB[p];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (act) {
+        if (split) s_dot[wid][zlane ? j + 1 + row : row] = accA;
+        else {
+            s_dot[wid][row] = accA;
+            if (with_z) s_dot[wid][j + 1 + row] = accB;
+        }
+    }
+    __syncthreads();
+    const int nout = with_z ? 2 * j + 2 : j + 1;
+    for (int t = threadIdx.x; t < nout; t += PT) {
+        double sum = 0.0;
+        for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
+        dst[t] = sum;
     }
 }
 
@@ -487,14 +671,15 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     T* __restrict__ w = (T*)A.w;
     T* __restrict__ Gb = (T*)A.Gb;
     __shared__ double s_red[PT / 32][kNV + 1];
+    __shared__ double s_ws[PT / 32][96];   // warp_sum and group_sums scratch
     __shared__ double s_h[kOutP];
     __shared__ double s_c[kNV];
     __shared__ double s_sc[4];   // beta, 1/beta, h_{j+1,j}, 1/h_{j+1,j}
-    __shared__ int s_stop;       // 0 go on, 1 happy breakdown, 2 non-finite
-    __shared__ int s_int[3];     // phi_1: blown up, sub-steps, Taylor terms
+    __shared__ int s_int[3];     // phi_1: blown up, sub-steps, Taylor terms; Arnoldi: sums finite
     __shared__ double sH[kNV][kNV + 1];   // H, held by every block
-    __shared__ double s_cc[kNV + 1];      // coefficients of the next u
-    __shared__ double s_tmp[4];           // |s|^2, |h1|^2, s.t of a step
+    __shared__ double s_tmp[4];           // h^2, breakdown threshold on h^2, h qz of a step
+    __shared__ double s_dot[PT / 32][2 * kNV];   // the warps' dot sums of a step
+    __shared__ double s_uz[PT / 32][2][33];      // u and z of a warp's points
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
@@ -523,7 +708,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         w[a] = v;
         acc[kNV] += (double)v * (double)v;
     }
-    block_partials<PT>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
+    block_partials<PT, true>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
     if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
     reduce_all<PT>(P0, 1, s_h, s_red, nb);
     // scalars of the step, once per block (FP64 division and square root
@@ -552,7 +737,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             basis[a] = v;
             Lq[meta_pos(A.meta[a])] = v;
         }
-        ghost_values<T, PT>(A, w, Gb, ldg, s_c, 0, bid, nb, [&](int t, double gv) {
+        ghost_values<T, PT>(A, w, Gb, ldg, s_c, 0, bid, nb, s_ws[threadIdx.x >> 5], [&](int t, double gv) {
             const T g = (T)(gv * inv);
             Gb[t] = g;
             Lq[A.glist[t]] = g;
@@ -565,24 +750,24 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         // (z = A u).  Then q_j = (u - Q s) / h with h^2 = |u|^2 - |s|^2 (the
         // second pass; column j-1 of H gets + s, H[j][j-1] = h), and, by the
         // Arnoldi relation A Q_{j-1} = Q_j H, A q_j = (z - Q_j g) / h with
-        // g = H s: its first projection h1 = ([t; (u.z - s.t)/h] - g) / h
-        // and the next u = z / h - Q_j (g / h + h1), without a second operator
-        // application.  One reduction and one barrier per step.
+        // g = H s: its first projection is h1 = ([t; qz] - g) / h, where
+        // qz = q_j.z = (u.z - s.t) / h, and the next u = A q_j - Q_j h1
+        // = (z - Q_j [t; qz]) / h (g cancels), without a second operator
+        // application.  One reduction and one barrier per step; g only
+        // enters column j of H, off the path to the next vectors.
         T* __restrict__ zb = basis + (size_t)m * ld;   // z, in the spare basis row
         T* __restrict__ Gu = Gb + (size_t)m * ldg;     // ghost values of u
         // step 0: z = A q_0 and its first projection
 #pragma unroll
         for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
         for (int a = a0; a < n; a += stride) {
-            const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
+            const T z = apply_point<T, false>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
             zb[a] = z;
-            const double zd = (double)z;
-            acc[0] += (double)basis[a] * zd;
-            acc[kNV] += zd * zd;
+            acc[0] += (double)basis[a] * (double)z;
         }
-        block_partials<PT>(acc, 1, P0 + (size_t)bid * kOutP, s_red);
+        block_partials<PT, false>(acc, 1, P0 + (size_t)bid * kOutP, s_red);
         if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-        reduce_all<PT>(P0, 2, s_h, s_red, nb);
+        reduce_all<PT>(P0, 1, s_h, s_red, nb);
         if (threadIdx.x == 0) {
             sH[0][0] = s_h[0];
             s_c[0] = s_h[0];
@@ -593,7 +778,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             w[a] = u;
             Lq[meta_pos(A.meta[a])] = u;
         }
-        ghost_values<T, PT>(A, zb, Gb, ldg, s_c, 1, bid, nb, [&](int t, double gv) {
+        ghost_values<T, PT>(A, zb, Gb, ldg, s_c, 1, bid, nb, s_ws[threadIdx.x >> 5], [&](int t, double gv) {
             const T g = (T)gv;
             Gu[t] = g;
             Lq[A.glist[t]] = g;
@@ -602,124 +787,78 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
 
         for (int j = 1; j <= m; ++j) {
             const bool last = j == m;   // only the second pass of u is left
-            // z = A u; dots of u and of z with q_0 .. q_{j-1}.  While both sets
-            // fit the accumulators (j <= 15), one pass and one block reduction,
-            // interleaved: acc[2t] = q_t.u, acc[2t+1] = q_t.z, acc[30] = |u|^2,
-            // acc[31] = u.z; otherwise two passes, acc[t] = q_t.u then q_t.z
-            // (layout in the partials: s, |u|^2, t, u.z)
-            const bool inter = !last && 2 * j <= kNV - 2;
-            if (inter) {
-#pragma unroll
-                for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
-                for (int a = a0; a < n; a += stride) {
-                    const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
-                    zb[a] = z;
-                    const double zd = (double)z, ud = (double)w[a];
-#pragma unroll
-                    for (int t = 0; t < kNV / 2 - 1; ++t)
-                        if (t < j) {
-                            const double q = (double)basis[(size_t)t * ld + a];
-                            acc[2 * t] += q * ud;
-                            acc[2 * t + 1] += q * zd;
-                        }
-                    acc[kNV - 2] += ud * ud;
-                    acc[kNV - 1] += ud * zd;
-                }
-                block_partials<PT>(acc, kNV, P0 + (size_t)bid * kOutP, s_red);
-            } else {
-#pragma unroll
-            for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
-            for (int a = a0; a < n; a += stride) {
-                const double ud = (double)w[a];
-#pragma unroll
-                for (int t = 0; t < kNV; ++t)
-                    if (t < j) acc[t] += (double)basis[(size_t)t * ld + a] * ud;
-                acc[kNV] += ud * ud;
-            }
-            block_partials<PT>(acc, j, P0 + (size_t)bid * kOutP, s_red);
-            if (!last) {
-                __syncthreads();   // s_red is reused
-#pragma unroll
-                for (int t = 0; t <= kNV; ++t) acc[t] = 0.0;
-                for (int a = a0; a < n; a += stride) {
-                    const T z = apply_point<T, true>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
-                    zb[a] = z;
-                    const double zd = (double)z;
-#pragma unroll
-                    for (int t = 0; t < kNV; ++t)
-                        if (t < j) acc[t] += (double)basis[(size_t)t * ld + a] * zd;
-                    acc[kNV] += (double)w[a] * zd;
-                }
-                block_partials<PT>(acc, j, P0 + (size_t)bid * kOutP + (j + 1), s_red);
-            }
-            }
+            // z = A u and the dots of u and z with q_0 .. q_{j-1}: the values
+            // [s, |u|^2, t, u.z] (the last step: [s, |u|^2])
+            step_dots<T, PT>(A, j, !last, bid, nb, P0 + (size_t)bid * kOutP, s_dot, s_uz);
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-            reduce_all<PT>(P0, inter ? kNV : (last ? j + 1 : 2 * j + 2), s_h, s_red, nb);
-            // scalars (every block the same): the second pass of u, the
-            // breakdown tests, and the coefficients of q_j and the next u.  The
-            // FP64 work is spread over the warps: one warp's FP64 instruction
-            // occupies its SM sub-partition for about 64 cycles on this part.
-            {
-                constexpr int kW = PT / 32;
-                const int i = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                const double si = i < j ? s_h[inter ? 2 * i : i] : 0.0;
-                const double hp = i < j ? sH[i][j - 1] : 0.0;   // first pass of column j-1
-                const double ti = (!last && i < j) ? s_h[inter ? 2 * i + 1 : j + 1 + i] : 0.0;
-                const double uu = s_h[inter ? kNV - 2 : j];
-                const double uz = last ? 0.0 : s_h[inter ? kNV - 1 : 2 * j + 1];
-                // |s|^2, |h1|^2 and s.t, each summed by one warp
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (q % kW == wid) {
-                        double v = q == 0 ? si * si : (q == 1 ? hp * hp : si * ti);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (i == 0) s_tmp[q] = v;
-                    }
-                __syncthreads();
-                if (wid == 0) {
-                    const bool bad = __any_sync(0xffffffffu, !isfinite(hp + si) || !isfinite(ti)) || !isfinite(uu) ||
-                                     !isfinite(uz);
-                    if (i < j) {
-                        sH[i][j - 1] = hp + si;
-                        s_c[i] = si;
-                    }
-                    if (i == 0) {
-                        const double q2 = fmax(uu - s_tmp[0], 0.0);   // h_{j,j-1}^2
-                        double h, hinv;
-                        sqrt_and_rsqrt(q2, h, hinv);
-                        sH[j][j - 1] = h;
-                        s_sc[2] = h;
-                        s_sc[3] = hinv;
-                        // breakdown: h <= tol |A q_{j-1}|, |A q_{j-1}|^2 = |h1|^2 + |u|^2
-                        s_stop = (bad || !isfinite(q2)) ? 2 : (q2 <= A.tol * A.tol * (s_tmp[1] + uu) ? 1 : 0);
+            reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb);
+            // scalars (every block the same; s_h holds s at 0..j-1, |u|^2 at j,
+            // t at j+1..2j and u.z at 2j+1).  One warp's FP64 instruction
+            // occupies its SM sub-partition for about 64 cycles on this part,
+            // so only |s|^2 -> h^2 -> 1/h runs on the path to the next vectors
+            // (warp 0); warp 1 forms s.t, warp g0 the first-pass norm
+            // |H[:, j-1]|^2 (the breakdown threshold), and warps g0.. the
+            // partial sums of g = H s, which only enter column j of H, written
+            // after the new vectors.
+            constexpr int kW = PT / 32;
+            static_assert(kW >= 2, "the scalar phase splits the work over at least two warps");
+            constexpr int g0 = kW == 2 ? 1 : 2;          // first warp of the g partial sums
+            const int li = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            const double si = li < j ? s_h[li] : 0.0;
+            double hp = 0.0;
+            if (wid == 0) {
+                const double v = warp_sum(si * si, s_ws[wid]);
+                const double q2 = fmax(s_h[j] - v, 0.0);   // h_{j,j-1}^2
+                double h, hinv;
+                sqrt_and_rsqrt(q2, h, hinv);
+                if (li == 0) {
+                    s_sc[2] = h;
+                    s_sc[3] = hinv;
+                    s_tmp[0] = q2;
+                }
+            } else {
+                hp = li < j ? sH[li][j - 1] : 0.0;   // first pass of column j-1
+                if (wid == 1) {
+                    const double ti = (!last && li < j) ? s_h[j + 1 + li] : 0.0;
+                    const double st = warp_sum(si * ti, s_ws[wid]);
+                    if (li == 0) {
+                        const double uu = s_h[j], uz = last ? 0.0 : s_h[2 * j + 1];
+                        s_tmp[2] = uz - st;   // h qz, qz = q_j.z
+                        // a non-finite s or t shows in s.t
+                        s_int[0] = finite_bits(st) && finite_bits(uu) && finite_bits(uz);
                     }
                 }
-                __syncthreads();
-                if (s_stop == 0 && !last) {
-                    // g = H s (rows 0 .. j): column groups c = w (mod kW) per warp
-                    double gp = 0.0;
-                    if (i <= j)
-#pragma unroll
-                        for (int cc = 0; cc < kNV / kW; ++cc) {
-                            const int c = cc * kW + wid;
-                            if (c < j) gp += sH[i][c] * s_c[c];
-                        }
-                    s_red[wid][i] = gp;
-                    __syncthreads();
-                    if (wid == 0 && i <= j) {
-                        double gi = s_red[0][i];
-                        for (int w = 1; w < kW; ++w) gi += s_red[w][i];
-                        const double hinv = s_sc[3];
-                        const double qz = (uz - s_tmp[2]) * hinv;
-                        const double h1 = i < j ? (ti - gi) * hinv : (qz - gi) * hinv;
-                        s_cc[i] = gi * hinv + h1;
-                        sH[i][j] = h1;
+                if (wid == g0) {
+                    const double hh = warp_sum(hp * hp, s_ws[wid]);
+                    if (li == 0) {
+                        // breakdown: h <= tol |A q_{j-1}|, |A q_{j-1}|^2 = |H[:, j-1]|^2 + |u|^2
+                        s_tmp[1] = A.tol * A.tol * (hh + s_h[j]);
+                        s_int[1] = finite_bits(hh);
                     }
+                }
+                if (!last && wid >= g0) {
+                    // rows i < j of g: columns c < j-1 of H, and column j-1
+                    // with its second pass (hp + s), dealt over warps g0..kW-1
+                    constexpr int ng = kW - g0;
+                    const int c0 = wid - g0;
+                    const double hs = hp + si;
+                    double gp[2] = {0.0, 0.0};
+                    if (li < j)
+                        down_from<(kNV + ng - 1) / ng>((j - c0 + ng - 1) / ng, [&](auto cc) {
+                            constexpr int q = decltype(cc)::value;
+                            const int c = q * ng + c0;
+                            gp[q & 1] += (c == j - 1 ? hs : sH[li][c]) * s_h[c];
+                        });
+                    s_red[wid][li] = gp[0] + gp[1];
                 }
             }
             __syncthreads();
-            const int stop = s_stop;
+            const double q2 = s_tmp[0];
+            const int stop = !(s_int[0] && s_int[1] && finite_bits(q2)) ? 2 : (q2 <= s_tmp[1] ? 1 : 0);
+            if (wid == 1) {   // column j-1 of H after its second pass; h_{j,j-1}
+                if (li < j) sH[li][j - 1] = hp + si;
+                if (li == 0) sH[j][j - 1] = s_sc[2];
+            }
             if (stop == 2) {
                 if (lead) atomicOr(A.flags, 1);
                 k = j;
@@ -729,28 +868,47 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                 k = j;
                 break;
             }
-            // q_j = (u - Q s) / h and the next u = z / h - Q_j c at the own
-            // points; at the ghosts by linearity
+            // q_j = (u - Q s) / h and the next u = (z - Q t - q_j qz) / h at
+            // the own points; at the ghosts by linearity
             const double hinv = s_sc[3];
+            const double qz = s_tmp[2] * hinv;
             for (int a = a0; a < n; a += stride) {
+                const T wa = w[a], za = zb[a];
                 T ps[4] = {T(0), T(0), T(0), T(0)}, pc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-                for (int t = 0; t < kNV; ++t)
-                    if (t < j) {
-                        const T q = basis[(size_t)t * ld + a];
-                        ps[t & 3] += q * (T)s_c[t];
-                        pc[t & 3] += q * (T)s_cc[t];
-                    }
-                const T qj = (T)((double)(w[a] - ((ps[0] + ps[1]) + (ps[2] + ps[3]))) * hinv);
+                for (int hh = 0; hh < 2; ++hh) {
+                    T qv[kNV / 2];
+#pragma unroll
+                    for (int t = 0; t < kNV / 2; ++t)
+                        if (hh * (kNV / 2) + t < j) qv[t] = basis[(size_t)(hh * (kNV / 2) + t) * ld + a];
+                    down_from<kNV / 2>(min(j - hh * (kNV / 2), kNV / 2), [&](auto tc) {
+                        constexpr int t = decltype(tc)::value;
+                        ps[t & 3] += qv[t] * (T)s_h[hh * (kNV / 2) + t];
+                        pc[t & 3] += qv[t] * (T)s_h[j + 1 + hh * (kNV / 2) + t];
+                    });
+                }
+                const T qj = (T)((double)(wa - ((ps[0] + ps[1]) + (ps[2] + ps[3]))) * hinv);
                 basis[(size_t)j * ld + a] = qj;
-                const T un = (T)((double)zb[a] * hinv) - (((pc[0] + pc[1]) + (pc[2] + pc[3])) + qj * (T)s_cc[j]);
+                const T un = (T)(((double)za - (double)((pc[0] + pc[1]) + (pc[2] + pc[3])) - (double)qj * qz) * hinv);
                 w[a] = un;
                 Lq[meta_pos(A.meta[a])] = un;
             }
-            ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_c, s_cc, j, hinv, Lq, bid, nb);
+            if (wid == 0) {
+                // column j of H: h1 = ([t; qz] - g) / h, g from the warps' partial
+                // sums (g_j = h s_{j-1})
+                if (li < j) {
+                    double gi = 0.0;
+                    for (int q = g0; q < kW; ++q) gi += s_red[q][li];
+                    sH[li][j] = (s_h[j + 1 + li] - gi) * hinv;
+                } else if (li == j) {
+                    sH[j][j] = (qz - s_sc[2] * s_h[j - 1]) * hinv;
+                }
+            }
+            ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_h, s_h + j + 1, qz, j, hinv, Lq, bid, nb, s_ws[wid]);
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
         }
         // H (every block holds it) to global memory, by block 0
+        __syncthreads();
         if (bid == 0) {
             for (int e = threadIdx.x; e < (k + 1) * k; e += PT) {
                 const int i = e / k, c = e - i * k;
@@ -770,7 +928,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     }
     if (bid == 0) phi1_block<PT>(A.H, k, m, A.dt, A.y, A.flags, s_red, s_h, s_int);
     if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-    for (int t = threadIdx.x; t < k; t += PT) s_c[t] = A.dt * beta * __ldcg(A.y + t);
+    for (int t = threadIdx.x; t < k; t += PT) s_c[t] = A.dt * beta * A.y[t];
     __syncthreads();
     T* __restrict__ om = (T*)A.omega;
     T* __restrict__ Lo = (T*)A.L;
