@@ -32,6 +32,16 @@ constexpr int kNV = 32;       // accumulator slots: basis vectors per pass (<= m
 constexpr int kOutP = 66;     // partial sums per block: two sets of (kNV dots + one product)
 constexpr int kGhostLanes = 8;   // lanes per ghost value (ghost_values, ghost_step)
 constexpr int kGatherLane = 8;   // row terms per lane fetched ahead of their additions
+static_assert(kGhostLanes * kGatherLane == kGhostRowMax, "one gather pass covers a whole interpolation row");
+constexpr int kCacheGroups = 16; // ghosts per block whose interpolation rows are kept in shared memory
+
+// Shared-memory copy of the interpolation rows of a block's first
+// kCacheGroups ghosts (ghost bid + nb q in slot q).
+struct RowCache {
+    int* len;
+    int* idx;      // kCacheGroups x kGhostRowMax
+    double* w;
+};
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -518,49 +528,86 @@ __device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* _
 // Ghost values of step j of the delayed scheme (groups of kGhostLanes lanes
 // per ghost, as ghost_values): q_j at ghost g, Gb_j = (Gu - sum_{q<j} s_q Gb_q) / h,
 // then the next u there, Gu <- (rows . z - sum_{q<j} t_q Gb_q - qz Gb_j) / h
-// (with the new Gb_j), also written into the lattice vector Lq.
+// (with the new Gb_j), also written into the lattice vector Lq.  The
+// interpolation rows of the block's first kCacheGroups ghosts come from the
+// shared-memory copy rc (made at the start of the launch: the rows do not
+// change during it), the others from global memory.  The ghost's earlier
+// values Gb_q are loaded first, and the FP64 products of both sums run for
+// the warp's longest row and for q < j only (down_from), not as predicated
+// instructions.
 template <typename T, int PT>
 __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __restrict__ z, T* __restrict__ Gb,
                                            long long ldg, T* __restrict__ Gu, const double* s, const double* tv,
                                            double qz, int j, double hinv, T* __restrict__ Lq, int bid, int nb,
-                                           double* ws) {
+                                           double* ws, const RowCache& rc) {
     constexpr int kGroups = PT / kGhostLanes;
     constexpr int kPerWarp = 32 / kGhostLanes;
+    constexpr int kHist = kNV / kGhostLanes;          // earlier values per lane
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gl = lane % kGhostLanes;
+    const int nh = (j + kGhostLanes - 1) / kGhostLanes;
     for (int q0 = wid * kPerWarp; bid + (long long)nb * q0 < A.ng; q0 += kGroups) {
-        const long long tl = bid + (long long)nb * (q0 + lane / kGhostLanes);
+        const int qg = q0 + lane / kGhostLanes;       // the ghost's slot in the block
+        const long long tl = bid + (long long)nb * qg;
         const bool valid = tl < A.ng;
         const int t = valid ? (int)tl : 0;
-        const int rl = valid ? A.row_len[t] : 0;
-        const size_t base = (size_t)t * A.rmax;
+        double gq[kHist];
+#pragma unroll
+        for (int u = 0; u < kHist; ++u) {
+            const int q = gl + kGhostLanes * u;
+            gq[u] = (valid && q < j) ? (double)Gb[(size_t)q * ldg + t] : 0.0;
+        }
         double part = 0.0;   // rows . z, this lane's share
-        for (int e0 = 0; e0 < A.rmax; e0 += kGhostLanes * kGatherLane) {
-            if (!__any_sync(0xffffffffu, e0 < rl)) break;
+        if (q0 < kCacheGroups) {   // warp-uniform
+            const int rl = valid ? rc.len[qg] : 0;
+            const int* ri = rc.idx + qg * kGhostRowMax;
+            const double* rw = rc.w + qg * kGhostRowMax;
             int id[kGatherLane];
             double wt[kGatherLane], xv[kGatherLane];
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u) {
-                const int e = e0 + gl + kGhostLanes * u;
-                if (e < rl) {
-                    id[u] = A.row_idx[base + e];
-                    wt[u] = A.row_w[base + e];
-                }
+                const int e = gl + kGhostLanes * u;
+                id[u] = e < rl ? ri[e] : -1;
+                wt[u] = e < rl ? rw[e] : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < kGatherLane; ++u)
-                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)z[id[u]];
+            for (int u = 0; u < kGatherLane; ++u) xv[u] = id[u] >= 0 ? (double)z[id[u]] : 0.0;
+            const int nu = __reduce_max_sync(0xffffffffu, (unsigned)((rl + kGhostLanes - 1) / kGhostLanes));
+            down_from<kGatherLane>(nu, [&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                part += wt[u] * xv[u];
+            });
+        } else {
+            const int rl = valid ? A.row_len[t] : 0;
+            const size_t base = (size_t)t * A.rmax;
+            for (int e0 = 0; e0 < A.rmax; e0 += kGhostLanes * kGatherLane) {
+                if (!__any_sync(0xffffffffu, e0 < rl)) break;
+                int id[kGatherLane];
+                double wt[kGatherLane], xv[kGatherLane];
 #pragma unroll
-            for (int u = 0; u < kGatherLane; ++u)
-                if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
+                for (int u = 0; u < kGatherLane; ++u) {
+                    const int e = e0 + gl + kGhostLanes * u;
+                    if (e < rl) {
+                        id[u] = A.row_idx[base + e];
+                        wt[u] = A.row_w[base + e];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u)
+                    if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)z[id[u]];
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u)
+                    if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
+            }
         }
         double ss = 0.0, cs = 0.0;
-        if (valid)
-            for (int q = gl; q < j; q += kGhostLanes) {
-                const double gq = (double)Gb[(size_t)q * ldg + t];
-                ss += s[q] * gq;
-                cs += tv[q] * gq;
-            }
+        down_from<kHist>(nh, [&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            const int q = gl + kGhostLanes * u;
+            const double sq = q < j ? s[q] : 0.0, tq = q < j ? tv[q] : 0.0;
+            ss += sq * gq[u];
+            cs += tq * gq[u];
+        });
         double pv[3] = {part, ss, cs};
         group_sums<3>(pv, ws);
         if (valid && gl == 0) {
@@ -680,6 +727,10 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_tmp[4];           // h^2, breakdown threshold on h^2, h qz of a step
     __shared__ double s_dot[PT / 32][2 * kNV];   // the warps' dot sums of a step
     __shared__ double s_uz[PT / 32][2][33];      // u and z of a warp's points
+    __shared__ int s_glen[kCacheGroups];
+    __shared__ int s_gidx[kCacheGroups * kGhostRowMax];
+    __shared__ double s_gwt[kCacheGroups * kGhostRowMax];
+    const RowCache rc{s_glen, s_gidx, s_gwt};
     const int n = A.n;
     const int stride = nb * PT;
     const int a0 = bid * PT + threadIdx.x;
@@ -697,6 +748,18 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     }
     if (bid == 0)   // H is written by this block only
         for (int t = threadIdx.x; t < (m + 1) * m; t += blockDim.x) A.H[t] = 0.0;
+    // the interpolation rows of the block's first kCacheGroups ghosts (A.rmax
+    // is kGhostRowMax; read at the first use after the barrier below)
+    for (int e = threadIdx.x; e < kCacheGroups * kGhostRowMax; e += PT) {
+        const int q = e / kGhostRowMax, i = e - q * kGhostRowMax;
+        const long long t = bid + (long long)nb * q;
+        const int rl = t < A.ng ? A.row_len[t] : 0;
+        if (i == 0) s_glen[q] = rl;
+        if (i < rl) {
+            s_gidx[e] = A.row_idx[(size_t)t * A.rmax + i];
+            s_gwt[e] = A.row_w[(size_t)t * A.rmax + i];
+        }
+    }
     for (int t = threadIdx.x; t < kNV * (kNV + 1); t += blockDim.x) (&sH[0][0])[t] = 0.0;
 
     // b = A_n omega + g  (L holds R(omega), ghosts included)
@@ -904,7 +967,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                     sH[j][j] = (qz - s_sc[2] * s_h[j - 1]) * hinv;
                 }
             }
-            ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_h, s_h + j + 1, qz, j, hinv, Lq, bid, nb, s_ws[wid]);
+            ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_h, s_h + j + 1, qz, j, hinv, Lq, bid, nb, s_ws[wid], rc);
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
         }
         // H (every block holds it) to global memory, by block 0
