@@ -544,7 +544,7 @@ wrc_status krylov(wrc_run* R) {
     const long long n = R->n_active;
     const int m = R->cfg.krylov_m;
     const KrylovStepArgs A = krylov_args(R);
-    const int blocks = krylov_step_blocks(n, R->max_blocks);
+    const int blocks = krylov_step_blocks(n, R->max_blocks, R->fp32);
     TRY(trace_reset(R, blocks));
     int e0 = -1;
     if (R->profiling) {

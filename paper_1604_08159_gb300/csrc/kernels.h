@@ -142,8 +142,15 @@ struct KrylovStepArgs {
     unsigned long long* trace;
 };
 constexpr int kTracePhases = 3 + 3 * 31;
+// Co-resident capacity of the single-run Krylov kernel (also for clusters of
+// 2 and 4 blocks, kept for krylov_step_blocks and the launch).
 int krylov_step_init(bool fp32, int* max_blocks);
-int krylov_step_blocks(long long n, int max_blocks);
+// Blocks for n active points: one thread per point, capped at max_blocks,
+// padded to a whole number of 4- or 2-block clusters where that fits.
+int krylov_step_blocks(long long n, int max_blocks, bool fp32);
+// Cooperative launch; clusters of 4 or 2 blocks when `blocks` is a multiple
+// within their capacity (their blocks pre-add the dot sums in distributed
+// shared memory).
 template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s);
 size_t krylov_partials_doubles(int max_blocks);

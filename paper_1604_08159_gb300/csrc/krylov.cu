@@ -18,6 +18,8 @@
 // (about one per 19 cycles per SM), so the kernel is organised around the
 // count of FP64 instructions each warp issues and the latency of dependent
 // steps, not around bytes.
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "kernels.h"
@@ -632,10 +634,14 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
 // and z on separate half-warps) or 64 FP64 operations per lane and point
 // batch, against j or 2j products plus ~31 additions per reduce-scatter
 // with one product per point and lane.  The warps' sums are added in warp
-// order.
-template <typename T, int PT>
+// order.  With thread-block clusters of CL > 1 blocks, the blocks of a
+// cluster leave their sums in shared memory (s_bp) and the cluster's block
+// 0 adds them in rank order through distributed shared memory and writes
+// the cluster's sums to dst: the grid-wide reduction then reads nb / CL
+// partial sums instead of nb.
+template <typename T, int PT, int CL>
 __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool with_z, int bid, int nb, double* dst,
-                                          double (*s_dot)[2 * kNV], double (*s_uz)[2][33]) {
+                                          double (*s_dot)[2 * kNV], double (*s_uz)[2][33], double* s_bp) {
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
     const T* __restrict__ Lq = (const T*)A.Lq;
@@ -699,16 +705,36 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
     }
     __syncthreads();
     const int nout = with_z ? 2 * j + 2 : j + 1;
-    for (int t = threadIdx.x; t < nout; t += PT) {
-        double sum = 0.0;
-        for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
-        dst[t] = sum;
+    if constexpr (CL == 1) {
+        for (int t = threadIdx.x; t < nout; t += PT) {
+            double sum = 0.0;
+            for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
+            dst[t] = sum;
+        }
+    } else {
+        for (int t = threadIdx.x; t < nout; t += PT) {
+            double sum = 0.0;
+            for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
+            s_bp[t] = sum;
+        }
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        cl.sync();
+        if (cl.block_rank() == 0)
+            for (int t = threadIdx.x; t < nout; t += PT) {
+                double sum = s_bp[t];
+#pragma unroll
+                for (int r = 1; r < CL; ++r) sum += cl.map_shared_rank(s_bp, r)[t];
+                dst[t] = sum;
+            }
+        // a peer's s_bp is next written after the grid barrier that follows,
+        // which block 0 reaches only after these reads
     }
 }
 
 // The Krylov step of one problem, run by its nb blocks (bid = this block's
-// index among them).
-template <typename T, int PT>
+// index among them; with clusters of CL blocks, nb is a multiple of CL and
+// the cluster of block bid is bid / CL).
+template <typename T, int PT, int CL>
 __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int bid, const int nb) {
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
@@ -728,6 +754,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_tmp[4];           // h^2, breakdown threshold on h^2, h qz of a step
     __shared__ double s_dot[PT / 32][2 * kNV];   // the warps' dot sums of a step
     __shared__ double s_uz[PT / 32][2][33];      // u and z of a warp's points
+    __shared__ double s_bp[CL > 1 ? kOutP : 1];  // the block's dot sums (clusters)
     __shared__ int s_glen[kCacheGroups];
     __shared__ int s_gidx[kCacheGroups * kGhostRowMax];
     __shared__ double s_gwt[kCacheGroups * kGhostRowMax];
@@ -853,9 +880,9 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             const bool last = j == m;   // only the second pass of u is left
             // z = A u and the dots of u and z with q_0 .. q_{j-1}: the values
             // [s, |u|^2, t, u.z] (the last step: [s, |u|^2])
-            step_dots<T, PT>(A, j, !last, bid, nb, P0 + (size_t)bid * kOutP, s_dot, s_uz);
+            step_dots<T, PT, CL>(A, j, !last, bid, nb, P0 + (size_t)(bid / CL) * kOutP, s_dot, s_uz, s_bp);
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
-            reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb);
+            reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb / CL);
             // scalars (every block the same; s_h holds s at 0..j-1, |u|^2 at j,
             // t at j+1..2j and u.z at 2j+1).  One warp's FP64 instruction
             // occupies its SM sub-partition for about 64 cycles on this part,
@@ -872,7 +899,11 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             double hp = 0.0;
             if (wid == 0) {
                 const double v = warp_sum(si * si, s_ws[wid]);
-                const double q2 = fmax(s_h[j] - v, 0.0);   // h_{j,j-1}^2
+                // h_{j,j-1}^2, clamped at +0 by its sign bit (an FP64 max or
+                // compare takes two to three FP64 issue slots); a NaN here
+                // comes from |u|^2 or s, which the flags below catch
+                double q2 = s_h[j] - v;
+                if (__double_as_longlong(q2) < 0) q2 = 0.0;
                 double h, hinv;
                 sqrt_and_rsqrt(q2, h, hinv);
                 if (li == 0) {
@@ -918,7 +949,10 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             }
             __syncthreads();
             const double q2 = s_tmp[0];
-            const int stop = !(s_int[0] && s_int[1] && finite_bits(q2)) ? 2 : (q2 <= s_tmp[1] ? 1 : 0);
+            // q2 and the threshold are non-negative: compared as integers
+            const int stop = !(s_int[0] && s_int[1] && finite_bits(q2))
+                                 ? 2
+                                 : (__double_as_longlong(q2) <= __double_as_longlong(s_tmp[1]) ? 1 : 0);
             if (wid == 1) {   // column j-1 of H after its second pass; h_{j,j-1}
                 if (li < j) sH[li][j - 1] = hp + si;
                 if (li == 0) sH[j][j - 1] = s_sc[2];
@@ -1006,9 +1040,9 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     if (lead) *A.kstop = k;
 }
 
-template <typename T, int PT>
+template <typename T, int PT, int CL>
 __global__ void __launch_bounds__(PT, 1) k_krylov_step(KrylovStepArgs A) {
-    krylov_body<T, PT>(A, blockIdx.x, gridDim.x);
+    krylov_body<T, PT, CL>(A, blockIdx.x, gridDim.x);
 }
 
 // Batched form: several problems in one cooperative launch; block b works on
@@ -1019,34 +1053,100 @@ __global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __
                                                         const int* __restrict__ mem_b0) {
     const int q = blk2mem[blockIdx.x];
     const int b0 = mem_b0[q];
-    krylov_body<T, PT>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
+    krylov_body<T, PT, 1>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
 }
 
+}  // namespace
+
+namespace {
+// Co-resident blocks of the single-run kernel on this device for clusters of
+// 1, 2 and 4 blocks ([fp32][log2 CL]); 0 where a cluster size cannot be
+// launched cooperatively.
+int g_cap[2][3] = {{0, 0, 0}, {0, 0, 0}};
+
+template <typename T, int CL>
+int cluster_capacity() {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kPT);
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_krylov_step<T, kPT, CL>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc * CL;
+}
+
+// Cluster size for a launch of `blocks` blocks: the largest of 4 and 2 that
+// divides it within the co-resident capacity, else 1.
+int cluster_for(bool fp32, int blocks) {
+    if (blocks % 4 == 0 && blocks <= g_cap[fp32][2]) return 4;
+    if (blocks % 2 == 0 && blocks <= g_cap[fp32][1]) return 2;
+    return 1;
+}
 }  // namespace
 
 int krylov_step_init(bool fp32, int* max_blocks) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float, kPT>, kPT, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double, kPT>, kPT, 0);
+    const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float, kPT, 1>, kPT, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double, kPT, 1>, kPT, 0);
     if (e != cudaSuccess || per < 1) return -2;
     *max_blocks = sms * per;
+    g_cap[fp32][0] = sms * per;
+    g_cap[fp32][1] = fp32 ? cluster_capacity<float, 2>() : cluster_capacity<double, 2>();
+    g_cap[fp32][2] = fp32 ? cluster_capacity<float, 4>() : cluster_capacity<double, 4>();
     return 0;
 }
 
-int krylov_step_blocks(long long n, int max_blocks) {
+int krylov_step_blocks(long long n, int max_blocks, bool fp32) {
     long long b = (n + kPT - 1) / kPT;
     if (b < 1) b = 1;
     if (b > max_blocks) b = max_blocks;
+    // padded to a whole number of clusters where that fits (the extra blocks
+    // have no points and contribute zero partial sums)
+    const long long b4 = (b + 3) / 4 * 4, b2 = (b + 1) / 2 * 2;
+    if (b4 <= g_cap[fp32][2] && b4 <= max_blocks) return (int)b4;
+    if (b2 <= g_cap[fp32][1] && b2 <= max_blocks) return (int)b2;
     return (int)b;
 }
 
+namespace {
+template <typename T, int CL>
+cudaError_t launch_clustered(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = CL;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kPT);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = CL > 1 ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, k_krylov_step<T, kPT, CL>, args);
+}
+}  // namespace
+
 template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
-    KrylovStepArgs a = args;
-    void* params[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT>, dim3(blocks), dim3(kPT), params, 0, s);
+    const int cl = cluster_for(sizeof(T) == 4, blocks);
+    const cudaError_t e = cl == 4   ? launch_clustered<T, 4>(args, blocks, s)
+                          : cl == 2 ? launch_clustered<T, 2>(args, blocks, s)
+                                    : launch_clustered<T, 1>(args, blocks, s);
     if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
