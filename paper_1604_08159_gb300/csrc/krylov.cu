@@ -440,6 +440,23 @@ __device__ __forceinline__ void phi1_block(const double* __restrict__ H, int k, 
 // issue slot for ~64 cycles).
 __device__ __forceinline__ bool finite_bits(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
 
+// Exact float -> double by integer operations on the bits (sign, exponent
+// rebiased by 1023 - 127, mantissa shifted by 29; infinities and NaNs keep
+// the all-ones exponent): the conversion instruction runs on the FP64 pipe,
+// the scarce one on this part, at two to three FP64 operations' cost.  A
+// float subnormal (never met in practice) takes the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned f = __float_as_uint(x);
+    const unsigned e8 = (f >> 23) & 0xffu;
+    const unsigned m = f & 0x7fffffu;
+    if (e8 == 0u && m != 0u) return (double)x;
+    const unsigned e11 = e8 == 0xffu ? 0x7ffu : (e8 == 0u ? 0u : e8 + (1023u - 127u));
+    const unsigned hi = (f & 0x80000000u) | (e11 << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ double dbl(double x) { return x; }
+__device__ __forceinline__ double dbl(float x) { return f2d_exact(x); }
+
 // sqrt(q) and 1/sqrt(q) in FP64 for the normalisation of a new basis vector:
 // an FP32 reciprocal square root as the seed, then two Newton-Raphson steps
 // y <- y (3/2 - (q/2) y^2) in FP64 (each doubles the correct bits: ~22 -> ~44
@@ -515,13 +532,13 @@ __device__ __forceinline__ void ghost_values(const KrylovStepArgs& A, const T* _
             }
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
-                if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)x[id[u]];
+                if (e0 + gl + kGhostLanes * u < rl) xv[u] = dbl(x[id[u]]);
 #pragma unroll
             for (int u = 0; u < kGatherLane; ++u)
                 if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
         }
         if (valid)
-            for (int q = gl; q < nc; q += kGhostLanes) part -= c[q] * (double)Gb[(size_t)q * ldg + t];
+            for (int q = gl; q < nc; q += kGhostLanes) part -= c[q] * dbl(Gb[(size_t)q * ldg + t]);
         double pv[1] = {part};
         group_sums<1>(pv, ws);
         if (valid && gl == 0) emit(t, pv[0]);
@@ -558,7 +575,7 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
 #pragma unroll
         for (int u = 0; u < kHist; ++u) {
             const int q = gl + kGhostLanes * u;
-            gq[u] = (valid && q < j) ? (double)Gb[(size_t)q * ldg + t] : 0.0;
+            gq[u] = (valid && q < j) ? dbl(Gb[(size_t)q * ldg + t]) : 0.0;
         }
         double part = 0.0;   // rows . z, this lane's share
         if (q0 < kCacheGroups) {   // warp-uniform
@@ -574,7 +591,7 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
                 wt[u] = e < rl ? rw[e] : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < kGatherLane; ++u) xv[u] = id[u] >= 0 ? (double)z[id[u]] : 0.0;
+            for (int u = 0; u < kGatherLane; ++u) xv[u] = id[u] >= 0 ? dbl(z[id[u]]) : 0.0;
             const int nu = __reduce_max_sync(0xffffffffu, (unsigned)((rl + kGhostLanes - 1) / kGhostLanes));
             down_from<kGatherLane>(nu, [&](auto uc) {
                 constexpr int u = decltype(uc)::value;
@@ -597,7 +614,7 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
                 }
 #pragma unroll
                 for (int u = 0; u < kGatherLane; ++u)
-                    if (e0 + gl + kGhostLanes * u < rl) xv[u] = (double)z[id[u]];
+                    if (e0 + gl + kGhostLanes * u < rl) xv[u] = dbl(z[id[u]]);
 #pragma unroll
                 for (int u = 0; u < kGatherLane; ++u)
                     if (e0 + gl + kGhostLanes * u < rl) part += wt[u] * xv[u];
@@ -614,8 +631,8 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
         double pv[3] = {part, ss, cs};
         group_sums<3>(pv, ws);
         if (valid && gl == 0) {
-            const T gbj = (T)(((double)Gu[t] - pv[1]) * hinv);
-            const T gu = (T)((pv[0] - pv[2] - qz * (double)gbj) * hinv);
+            const T gbj = (T)((dbl(Gu[t]) - pv[1]) * hinv);
+            const T gu = (T)((pv[0] - pv[2] - qz * dbl(gbj)) * hinv);
             Gb[(size_t)j * ldg + t] = gbj;
             Gu[t] = gu;
             Lq[A.glist[t]] = gu;
@@ -668,8 +685,8 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
                 zb[a] = z;
             }
         }
-        s_uz[wid][0][lane] = (double)u;
-        s_uz[wid][1][lane] = (double)z;
+        s_uz[wid][0][lane] = dbl(u);
+        s_uz[wid][1][lane] = dbl(z);
         __syncwarp();
         if (act) {
             const int nv = n - wb;   // valid points of the batch (>= 1; all 32 when >= 32)
@@ -687,7 +704,7 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
 #pragma unroll
                     for (int e = 0; e < kV; ++e) {
                         const int p = hh * 16 + q * kV + e;
-                        const double x = p < nv ? (double)xs[e] : 0.0;
+                        const double x = p < nv ? dbl(xs[e]) : 0.0;
                         accA += x * yA[p];
                         if (!split && with_z) accB += x * yB[p];
                     }
@@ -755,6 +772,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     __shared__ double s_dot[PT / 32][2 * kNV];   // the warps' dot sums of a step
     __shared__ double s_uz[PT / 32][2][33];      // u and z of a warp's points
     __shared__ double s_bp[CL > 1 ? kOutP : 1];  // the block's dot sums (clusters)
+    __shared__ T s_hT[kOutP];                    // s and t of a step in the bulk type
     __shared__ int s_glen[kCacheGroups];
     __shared__ int s_gidx[kCacheGroups * kGhostRowMax];
     __shared__ double s_gwt[kCacheGroups * kGhostRowMax];
@@ -797,7 +815,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         T v = apply_point<T, false>(Lb, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
         if (ga) v += ga[a];
         w[a] = v;
-        acc[kNV] += (double)v * (double)v;
+        acc[kNV] += dbl(v) * dbl(v);
     }
     block_partials<PT, true>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
     if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
@@ -824,7 +842,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         // rows, at the ghosts
         const double inv = s_sc[1];
         for (int a = a0; a < n; a += stride) {
-            const T v = (T)((double)w[a] * inv);
+            const T v = (T)(dbl(w[a]) * inv);
             basis[a] = v;
             Lq[meta_pos(A.meta[a])] = v;
         }
@@ -854,7 +872,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         for (int a = a0; a < n; a += stride) {
             const T z = apply_point<T, false>(Lq, A.meta[a], Ua[a], Va[a], nu, r, A.g, c1J, c2J);
             zb[a] = z;
-            acc[0] += (double)basis[a] * (double)z;
+            acc[0] += dbl(basis[a]) * dbl(z);
         }
         block_partials<PT, false>(acc, 1, P0 + (size_t)bid * kOutP, s_red);
         if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
@@ -897,6 +915,9 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             const int li = threadIdx.x & 31, wid = threadIdx.x >> 5;
             const double si = li < j ? s_h[li] : 0.0;
             double hp = 0.0;
+            // s and t in the bulk type for the new vectors (one conversion per
+            // value, not per product)
+            for (int t = threadIdx.x; t < 2 * j + 2; t += PT) s_hT[t] = (T)s_h[t];
             if (wid == 0) {
                 const double v = warp_sum(si * si, s_ws[wid]);
                 // h_{j,j-1}^2, clamped at +0 by its sign bit (an FP64 max or
@@ -981,13 +1002,13 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                         if (hh * (kNV / 2) + t < j) qv[t] = basis[(size_t)(hh * (kNV / 2) + t) * ld + a];
                     down_from<kNV / 2>(min(j - hh * (kNV / 2), kNV / 2), [&](auto tc) {
                         constexpr int t = decltype(tc)::value;
-                        ps[t & 3] += qv[t] * (T)s_h[hh * (kNV / 2) + t];
-                        pc[t & 3] += qv[t] * (T)s_h[j + 1 + hh * (kNV / 2) + t];
+                        ps[t & 3] += qv[t] * s_hT[hh * (kNV / 2) + t];
+                        pc[t & 3] += qv[t] * s_hT[j + 1 + hh * (kNV / 2) + t];
                     });
                 }
-                const T qj = (T)((double)(wa - ((ps[0] + ps[1]) + (ps[2] + ps[3]))) * hinv);
+                const T qj = (T)(dbl(wa - ((ps[0] + ps[1]) + (ps[2] + ps[3]))) * hinv);
                 basis[(size_t)j * ld + a] = qj;
-                const T un = (T)(((double)za - (double)((pc[0] + pc[1]) + (pc[2] + pc[3])) - (double)qj * qz) * hinv);
+                const T un = (T)((dbl(za) - dbl((pc[0] + pc[1]) + (pc[2] + pc[3])) - dbl(qj) * qz) * hinv);
                 w[a] = un;
                 Lq[meta_pos(A.meta[a])] = un;
             }
@@ -1032,8 +1053,8 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     T* __restrict__ Lo = (T*)A.L;
     for (int a = a0; a < n; a += stride) {
         double inc = 0.0;
-        for (int t = 0; t < k; ++t) inc += s_c[t] * (double)basis[(size_t)t * ld + a];
-        const T x = (T)((double)om[a] + inc);
+        for (int t = 0; t < k; ++t) inc += s_c[t] * dbl(basis[(size_t)t * ld + a]);
+        const T x = (T)(dbl(om[a]) + inc);
         om[a] = x;
         Lo[meta_pos(A.meta[a])] = x;
     }
