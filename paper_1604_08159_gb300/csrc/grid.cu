@@ -40,16 +40,56 @@ __global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict
 }
 
 // Coarse-to-fine inverse transform for one level: every non-active level-j
-// point gets its DD prediction (its detail is zero, Eq. 6).
+// point gets its DD prediction (its detail is zero, Eq. 6), in two passes.
+// Pass 1: the points odd in one direction only (one 1-D prediction each),
+// the first n^2/4 indices odd rows and even columns, the next n^2/4 even rows
+// and odd columns (n = NJ / 2^(J-j) points per row at this level).
 template <typename T>
-__global__ void k_recon_level(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
-    const long long cnt = level_count(j, g);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, k;
-        level_point(t, j, g, i, k);
+__global__ void k_recon_level_1d(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
+    const int sh = g.J - j;
+    const int lh = g.L - sh - 1;             // log2(n / 2)
+    const int q = 1 << (2 * lh);             // n^2 / 4
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * q; t += gridDim.x * blockDim.x) {
+        const int u = t < q ? t : t - q;
+        const int r = u >> lh, c = u & ((1 << lh) - 1);
+        const int k = (t < q ? 2 * r + 1 : 2 * r) << sh;
+        const int i = (t < q ? 2 * c : 2 * c + 1) << sh;
         const long long p = ((long long)k << g.L) + i;
         if (!act[p]) L[p] = predict<T>(L, i, k, j, g);
+    }
+}
+
+// Pass 2: the points odd in both directions.  Their prediction is the y
+// prediction over the x predictions of rows k -+ s, k -+ 3s at column i, and
+// those x predictions are exactly the values pass 1 stored at the points
+// (i, k -+ s), (i, k -+ 3s) unless these are active (same operands, same
+// rounded operations): only the rows of active neighbours are predicted
+// again.  Bit-identical to the tensor-product predictor, with one 1-D
+// prediction per point instead of five for most points.
+template <typename T>
+__global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
+    const int sh = g.J - j;
+    const int s = 1 << sh, m = g.mask;
+    const int lh = g.L - sh - 1;
+    const int q = 1 << (2 * lh);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < q; t += gridDim.x * blockDim.x) {
+        const int r = t >> lh, c = t & ((1 << lh) - 1);
+        const int k = (2 * r + 1) << sh, i = (2 * c + 1) << sh;
+        const long long p = ((long long)k << g.L) + i;
+        if (act[p]) continue;
+        const int ks[4] = {(k - s) & m, (k + s) & m, (k - 3 * s) & m, (k + 3 * s) & m};
+        T rv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const long long pe = ((long long)ks[e] << g.L) + i;
+            if (!act[pe]) {
+                rv[e] = L[pe];
+            } else {
+                const T* row = L + ((size_t)ks[e] << g.L);
+                rv[e] = dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+            }
+        }
+        L[p] = dd4<T>(rv[0], rv[1], rv[2], rv[3]);
     }
 }
 
@@ -594,7 +634,9 @@ void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cuda
 }
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
-    { k_recon_level<T><<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
+    const long long q = level_count(j, g) / 3;   // n^2 / 4
+    { k_recon_level_1d<T><<<blocks_for(2 * q), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
+    { k_recon_level_2d<T><<<blocks_for(q), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
