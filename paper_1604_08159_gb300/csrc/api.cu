@@ -280,6 +280,10 @@ wrc_status rebuild_host(wrc_run* R) {
         CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
         const int ev = R->counts_host[kMaxKeys];
         if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded kGhostRowMax terms");
+        if (ev & 8)
+            return fail(R, WRC_ERR_CUDA,
+                        "the Krylov kernel was launched without its thread-block clusters (set WRC_KRYLOV_CLUSTER=1 "
+                        "to use the unclustered kernel)");
         return fail(R, WRC_ERR_TIMEOUT, "a grid barrier wait of the Krylov kernel ran out");
     }
     const long long na = R->counts_host[0];

@@ -486,9 +486,17 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
 // flight, and merged in predictor order by all lanes at once -- a row's
 // entries are distinct, so each entry either adds to one existing entry or
 // is appended, new entries in row order.  The entries, their order and their
-// sums are those of merging the terms one by one.
+// sums are those of merging the terms one by one.  An entry finds its place
+// through a per-warp hash table in shared memory (key: the active point,
+// value: its slot in the row; open addressing, linear probing), instead of
+// a scan of the row built so far.  The predictor weights are products of
+// (-1, 9, 9, -1)/16, from a constant table.
 constexpr int kRowWarps = 4;   // warps (ghosts in flight) per block
 constexpr int kRowStage = 32;  // staged entries per predictor row (longer rows read the rest directly)
+constexpr int kRowHash = 128;  // hash slots per warp (at least twice the row capacity)
+__constant__ double c_dd4w[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
+
+__device__ __forceinline__ int row_hash(int key) { return (int)(((unsigned)key * 2654435761u) >> 25); }
 
 __global__ void __launch_bounds__(32 * kRowWarps)
 k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
@@ -496,13 +504,22 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
                    double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
                    const int* __restrict__ dcounts, int nkeys) {
     constexpr int kCap = 64;
+    static_assert(kRowHash >= 2 * kCap && (kRowHash & (kRowHash - 1)) == 0 && kRowHash == 128, "row_hash gives 7 bits");
     __shared__ int s_idx[kRowWarps][kCap];
     __shared__ double s_wt[kRowWarps][kCap];
     __shared__ int s_pi[kRowWarps][16][kRowStage];
     __shared__ double s_pw[kRowWarps][16][kRowStage];
+    __shared__ int s_hkey[kRowWarps][kRowHash];   // -1: empty
+    __shared__ int s_hval[kRowWarps][kRowHash];   // slot of the key in the row
+    __shared__ int s_hpos[kRowWarps][kCap];       // hash slot of row entry e (for clearing)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* idx = s_idx[wid];
     double* wt = s_wt[wid];
+    int* hkey = s_hkey[wid];
+    int* hval = s_hval[wid];
+    int* hpos = s_hpos[wid];
+    for (int h = lane; h < kRowHash; h += 32) hkey[h] = -1;
+    __syncwarp();
     if (dcounts) {   // key 0: active points, key l: ghosts of level l
         n_act = dcounts[0];
         gbeg = 0;
@@ -525,23 +542,17 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
         const int np = two_d ? 16 : 4;
         // lane q < np: predictor q = (a, b) = (q % 4, q / 4)
         int my_id = -1, my_rl = 0;
-        double my_w = 0.0;
         if (lane < np) {
             const int a = lane & 3, b = lane >> 2;
             const int off_a = (2 * a - 3) * s, off_b = (2 * b - 3) * s;   // -3s, -s, s, 3s
-            const double wa = (a == 1 || a == 2) ? 0.5625 : -0.0625;
-            const double wb = (b == 1 || b == 2) ? 0.5625 : -0.0625;
             int qi = i, qk = k;
             if (two_d) {
                 qi = (i + off_a) & g.mask;
                 qk = (k + off_b) & g.mask;
-                my_w = wa * wb;
             } else if (oi) {
                 qi = (i + off_a) & g.mask;
-                my_w = wa;
             } else {
                 qk = (k + off_a) & g.mask;
-                my_w = wa;
             }
             my_id = lat2idx[((long long)qk << g.L) + qi];
             if (my_id >= n_act && my_id < n_tot) my_rl = row_len[my_id - n_act];
@@ -563,7 +574,8 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
         for (int q = 0; q < np; ++q) {
             const int id = __shfl_sync(0xffffffffu, my_id, q);
             const int rl0 = __shfl_sync(0xffffffffu, my_rl, q);
-            const double w = __shfl_sync(0xffffffffu, my_w, q);
+            // weight of predictor q: a product of two DD4 weights (exact), or one
+            const double w = two_d ? c_dd4w[q & 3] * c_dd4w[q >> 2] : c_dd4w[q];
             if (id < 0 || id >= n_tot) {                 // not a grid point: record, do not read
                 over = true;
                 continue;
@@ -590,11 +602,14 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
                 }
                 int pos = -1;
                 if (has)
-                    for (int qq = 0; qq < len; ++qq)
-                        if (idx[qq] == my) {
-                            pos = qq;
+                    for (int h = row_hash(my);; h = (h + 1) & (kRowHash - 1)) {
+                        const int key = hkey[h];
+                        if (key == my) {
+                            pos = hval[h];
                             break;
                         }
+                        if (key < 0) break;
+                    }
                 if (pos >= 0) wt[pos] += mw;
                 const unsigned fresh = __ballot_sync(0xffffffffu, has && pos < 0);
                 if (has && pos < 0) {
@@ -602,6 +617,13 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
                     if (slot < cap) {
                         idx[slot] = my;
                         wt[slot] = mw;
+                        // distinct keys in one round: a claimed slot is another key's
+                        for (int h = row_hash(my);; h = (h + 1) & (kRowHash - 1))
+                            if (atomicCAS(&hkey[h], -1, my) == -1) {
+                                hval[h] = slot;
+                                hpos[slot] = h;
+                                break;
+                            }
                     }
                 }
                 const int nf = __popc(fresh);
@@ -613,6 +635,7 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
         for (int e = lane; e < len; e += 32) {
             row_idx[gi * rmax + e] = idx[e];
             row_w[gi * rmax + e] = wt[e];
+            hkey[hpos[e]] = -1;   // empty the table for the next ghost
         }
         if (lane == 0) {
             row_len[gi] = len;

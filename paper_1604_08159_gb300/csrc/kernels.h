@@ -131,7 +131,7 @@ struct KrylovStepArgs {
     int* flags;             // [1] bit 0: non-finite value met
     double* part;           // 3 x blocks x 33 partial sums
     unsigned* bar;          // grid barrier: {count, generation}
-    int* err;               // bit 1: a barrier wait ran out
+    int* err;               // bit 1: a barrier wait ran out; bit 2 (4): row overflow; bit 3 (8): clusters not formed
     int m;
     double dt, tol;
     unsigned long long limit_ns;

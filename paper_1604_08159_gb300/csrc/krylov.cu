@@ -20,6 +20,8 @@
 // steps, not around bytes.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include <type_traits>
 
 #include "kernels.h"
@@ -792,6 +794,14 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         if (lead) atomicOr(A.err, 4);
         return;
     }
+    if constexpr (CL > 1) {
+        // the cluster pre-sums read peers' shared memory: refuse to run (every
+        // block, before any barrier) unless the launch formed the clusters
+        if (cooperative_groups::this_cluster().num_blocks() != (unsigned)CL) {
+            if (lead) atomicOr(A.err, 8);
+            return;
+        }
+    }
     if (bid == 0)   // H is written by this block only
         for (int t = threadIdx.x; t < (m + 1) * m; t += blockDim.x) A.H[t] = 0.0;
     // the interpolation rows of the block's first kCacheGroups ghosts (A.rmax
@@ -1117,6 +1127,10 @@ int cluster_for(bool fp32, int blocks) {
 }  // namespace
 
 int krylov_step_init(bool fp32, int* max_blocks) {
+    // WRC_KRYLOV_CLUSTER = 1 or 2 caps the cluster size (default 4), e.g. for
+    // profilers that do not form the clusters of a cooperative launch
+    int cmax = 4;
+    if (const char* ev = getenv("WRC_KRYLOV_CLUSTER")) cmax = atoi(ev) >= 4 ? 4 : (atoi(ev) >= 2 ? 2 : 1);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1125,8 +1139,8 @@ int krylov_step_init(bool fp32, int* max_blocks) {
     if (e != cudaSuccess || per < 1) return -2;
     *max_blocks = sms * per;
     g_cap[fp32][0] = sms * per;
-    g_cap[fp32][1] = fp32 ? cluster_capacity<float, 2>() : cluster_capacity<double, 2>();
-    g_cap[fp32][2] = fp32 ? cluster_capacity<float, 4>() : cluster_capacity<double, 4>();
+    g_cap[fp32][1] = cmax < 2 ? 0 : (fp32 ? cluster_capacity<float, 2>() : cluster_capacity<double, 2>());
+    g_cap[fp32][2] = cmax < 4 ? 0 : (fp32 ? cluster_capacity<float, 4>() : cluster_capacity<double, 4>());
     return 0;
 }
 
@@ -1157,7 +1171,7 @@ cudaError_t launch_clustered(const KrylovStepArgs& args, int blocks, cudaStream_
     cfg.blockDim = dim3(kPT);
     cfg.stream = s;
     cfg.attrs = at;
-    cfg.numAttrs = CL > 1 ? 2 : 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k_krylov_step<T, kPT, CL>, args);
 }
 }  // namespace
@@ -1165,9 +1179,14 @@ cudaError_t launch_clustered(const KrylovStepArgs& args, int blocks, cudaStream_
 template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
     const int cl = cluster_for(sizeof(T) == 4, blocks);
-    const cudaError_t e = cl == 4   ? launch_clustered<T, 4>(args, blocks, s)
-                          : cl == 2 ? launch_clustered<T, 2>(args, blocks, s)
-                                    : launch_clustered<T, 1>(args, blocks, s);
+    cudaError_t e;
+    if (cl == 4) e = launch_clustered<T, 4>(args, blocks, s);
+    else if (cl == 2) e = launch_clustered<T, 2>(args, blocks, s);
+    else {
+        KrylovStepArgs a = args;
+        void* params[] = {&a};
+        e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT, 1>, dim3(blocks), dim3(kPT), params, 0, s);
+    }
     if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
