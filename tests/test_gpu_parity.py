@@ -293,3 +293,14 @@ def test_runs_of_different_sizes_coexist(prec):
         a.sync()
         b.sync()
         assert a.counts()[0] > 0 and b.counts()[0] > 0
+
+
+@pytest.mark.parametrize("cluster", ["1", "2"])
+def test_unclustered_krylov_kernel_matches_oracle(cluster, monkeypatch):
+    """The Krylov launch without thread-block clusters (WRC_KRYLOV_CLUSTER=1,
+    the form profilers run) and with clusters of two: the same steps against
+    the oracle.  The cluster size only changes the order of the cross-block
+    additions."""
+    monkeypatch.setenv("WRC_KRYLOV_CLUSTER", cluster)
+    wl = W.fujiwhara_small()
+    _run_steps_compare(wl.params, wl.vortices, nsteps=3)
