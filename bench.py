@@ -445,6 +445,8 @@ def run_ours(args):
                          "frac": achieved_gflops / FP64_PEAK_GFLOPS,
                          "traffic": krylov_traffic("fujiwhara_1024" if args.workload == "fujiwhara_1024" else "-"),
                          "traffic_unit": "DRAM bytes per launch (ncu; null once the kernel changed)",
+                         "traffic_source": "profiles/k_krylov_step_fujiwhara_1024.md: ncu capture of the "
+                                           "unclustered form (WRC_KRYLOV_CLUSTER=1), same sources and DRAM reads",
                          "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(1, rec["launches"]),
                          "flops_per_launch": rec["flops"] / max(1, rec["launches"]),
                          "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
