@@ -139,6 +139,31 @@ __device__ __forceinline__ long long eff_n(const int* dn, long long n) { return 
 void note_launch();
 long long launches_total();
 
+// Programmatic dependent launch.  The grid, flow and Poisson kernels are
+// launched with launch_pdl, so that a kernel's blocks can be scheduled while
+// its predecessor in the stream drains; each such kernel calls pdl_wait()
+// before touching global memory (it returns once the predecessor has
+// completed and its writes are visible; without the launch attribute it
+// returns at once) and pdl_trigger() after its work, which lets the
+// successor's launch begin.  Measured ~1 us saved per kernel boundary.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, (KArgs)args...);
+}
+
 inline int blocks_for(long long n, int threads = kThreads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;

@@ -219,6 +219,7 @@ __device__ __forceinline__ void fft_reg(C (&v)[E], C* sm, int i, int n, int logn
 // at [r p + k] (copies, so the transforms are those of the single table).
 template <typename C>
 __global__ void k_fft_pass_tables(const C* __restrict__ tw, C* __restrict__ ptw, int n, int logn, int E, int R0) {
+    pdl_wait();
     int p = 1, logp = 0, off = 0;
     auto table = [&](int R, int logR) {
         if (p > 1)
@@ -238,6 +239,7 @@ __global__ void k_fft_pass_tables(const C* __restrict__ tw, C* __restrict__ ptw,
         table(R0, logR0);
     }
     while (logp < logn) table(E, logE);
+    pdl_trigger();
 }
 
 // ---- kernels ------------------------------------------------------------------
@@ -252,6 +254,7 @@ __host__ __device__ constexpr int smlen_of(int n) { return n + n / 16 + 1; }
 template <typename T, int E, int R0>
 __global__ void __launch_bounds__(256) k_px_fwd(const T* __restrict__ Rf, cx_t<T>* __restrict__ S, int n, int logn,
                                                 const cx_t<T>* __restrict__ tw) {
+    pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(256) k_px_fwd(const T* __restrict__ Rf, cx_t<T
             sb[x] = mk<C>(T(0.5) * d.y, T(-0.5) * d.x);
         }
     }
+    pdl_trigger();
 }
 
 // Step 3: column kx of the transposed half spectrum (row kx of ST, length n):
@@ -311,6 +315,7 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
                                                   cx_t<T>* __restrict__ WT, int n, int logn,
                                                   const cx_t<T>* __restrict__ tw, const T* __restrict__ sigma,
                                                   const T* __restrict__ dsym, T scale) {
+    pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
@@ -412,6 +417,7 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
                 for (int e = 0; e < E; ++e) WT[(size_t)c2 * n + i + e * nt] = v[e];
         }
     }
+    pdl_trigger();
 }
 
 // Step 5 for psi: rows 2q, 2q+1 from their half spectra (Hermitian extension
@@ -420,6 +426,7 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
 template <typename T, int E, int R0>
 __global__ void __launch_bounds__(256) k_px_inv_real(const cx_t<T>* __restrict__ S, T* __restrict__ out, int n,
                                                      int logn, const cx_t<T>* __restrict__ tw) {
+    pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
@@ -459,6 +466,7 @@ __global__ void __launch_bounds__(256) k_px_inv_real(const cx_t<T>* __restrict__
         o0[i + e * nt] = v[e].x;
         o1[i + e * nt] = v[e].y;
     }
+    pdl_trigger();
 }
 
 // Step 5 for a full complex spectrum (U + i V, S11 + i S12): row y, inverse
@@ -467,6 +475,7 @@ template <typename T, int E, int R0>
 __global__ void __launch_bounds__(256) k_px_inv_pair(const cx_t<T>* __restrict__ Q, T* __restrict__ A,
                                                      T* __restrict__ B, int n, int logn,
                                                      const cx_t<T>* __restrict__ tw) {
+    pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
@@ -485,11 +494,13 @@ __global__ void __launch_bounds__(256) k_px_inv_pair(const cx_t<T>* __restrict__
         A[(size_t)y * n + i + e * nt] = v[e].x;
         B[(size_t)y * n + i + e * nt] = v[e].y;
     }
+    pdl_trigger();
 }
 
 // out[c][r] = in[r][c] for a rows x cols complex matrix, 32 x 32 tiles.
 template <typename C>
 __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int rows, int cols) {
+    pdl_wait();
     __shared__ C tile[32][33];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -501,6 +512,7 @@ __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int r
         const int gc = c0 + c, gr = r0 + threadIdx.x;
         if (gr < rows && gc < cols) out[(size_t)gc * rows + gr] = tile[threadIdx.x][c];
     }
+    pdl_trigger();
 }
 
 // Twiddles exp(-2 pi i t/n) (t < n) and the symbols
@@ -510,6 +522,7 @@ __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int r
 // symbol is i d), all evaluated in FP64 and stored as T.
 template <typename T>
 __global__ void k_fft_init(cx_t<T>* tw, T* sigma, T* dsym, int n, double inv3h2, double inv6h) {
+    pdl_wait();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         double sn, cs;
         sincospi(2.0 * t / n, &sn, &cs);
@@ -519,6 +532,7 @@ __global__ void k_fft_init(cx_t<T>* tw, T* sigma, T* dsym, int n, double inv3h2,
         sigma[t] = (T)(4.0 * s2 * (3.0 + s2) * inv3h2);
         dsym[t] = (T)((8.0 * sinpi(2.0 * t / n) - sinpi(4.0 * t / n)) * inv6h);
     }
+    pdl_trigger();
 }
 
 constexpr int kMaxLattice = 4096;   // WRC_MAX_NJ
@@ -560,34 +574,34 @@ struct Shape {
         C* ST = C1 + (size_t)n * h;   // h x n, transposed
         const bool uv = U && V && C3;
         const bool st = uv && S11 && S12 && C4;
-        { k_px_fwd<T, E, R0><<<b_half, thr, smem, s>>>(Rf, S, n, logn, tw); note_launch(); }
-        { k_transpose<C><<<g_nh, tb, 0, s>>>(S, ST, n, h); note_launch(); }
+        { launch_pdl(k_px_fwd<T, E, R0>, b_half, thr, smem, s, Rf, S, n, logn, tw); note_launch(); }
+        { launch_pdl(k_transpose<C>, g_nh, tb, 0, s, S, ST, n, h); note_launch(); }
         const T scale = T(1.0 / ((double)n * (double)n));
         if constexpr (std::is_same<T, float>::value) {
             if (uv) {
                 C* QT = C2;                    // n x n
                 C* WT = st ? C3 : nullptr;     // n x n
-                { k_py_solve<T, E, R0, true><<<b_half, thr, 2 * smem, s>>>(ST, QT, WT, n, logn, tw,
+                { launch_pdl(k_py_solve<T, E, R0, true>, b_half, thr, 2 * smem, s, ST, QT, WT, n, logn, tw,
                                                                         (const T*)p.sigma, (const T*)p.dsym,
                                                                         scale); note_launch(); }
-                { k_transpose<C><<<g_hn, tb, 0, s>>>(ST, S, h, n); note_launch(); }
-                { k_px_inv_real<T, E, R0><<<b_half, thr, smem, s>>>(S, psi, n, logn, tw); note_launch(); }
+                { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
+                { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw); note_launch(); }
                 // U + i V: QT (C2) -> a buffer that V (the caller's, possibly in C1) does not overlap
                 C* Q = st ? C4 : C3;
-                { k_transpose<C><<<g_nn, tb, 0, s>>>(QT, Q, n, n); note_launch(); }
-                { k_px_inv_pair<T, E, R0><<<b_full, thr, smem, s>>>(Q, U, V, n, logn, tw); note_launch(); }
+                { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, QT, Q, n, n); note_launch(); }
+                { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, Q, U, V, n, logn, tw); note_launch(); }
                 if (st) {
-                    { k_transpose<C><<<g_nn, tb, 0, s>>>(WT, C4, n, n); note_launch(); }
-                    { k_px_inv_pair<T, E, R0><<<b_full, thr, smem, s>>>(C4, S11, S12, n, logn, tw); note_launch(); }
+                    { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, WT, C4, n, n); note_launch(); }
+                    { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, C4, S11, S12, n, logn, tw); note_launch(); }
                 }
                 return;
             }
         }
-        { k_py_solve<T, E, R0, false><<<b_half, thr, smem, s>>>(ST, nullptr, nullptr, n, logn, tw,
+        { launch_pdl(k_py_solve<T, E, R0, false>, b_half, thr, smem, s, ST, nullptr, nullptr, n, logn, tw,
                                                                  (const T*)p.sigma, (const T*)p.dsym,
                                                                  scale); note_launch(); }
-        { k_transpose<C><<<g_hn, tb, 0, s>>>(ST, S, h, n); note_launch(); }
-        { k_px_inv_real<T, E, R0><<<b_half, thr, smem, s>>>(S, psi, n, logn, tw); note_launch(); }
+        { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
+        { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw); note_launch(); }
         (void)C2;
     }
 };
@@ -605,7 +619,7 @@ int plan_init_t(PoissonPlan& p, const Geom& g, cudaStream_t s) {
     if (cudaMalloc(&p.sigma, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (cudaMalloc(&p.dsym, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (setup_all<T>() != 0) return -2;
-    { k_fft_init<T><<<(p.n + 255) / 256, 256, 0, s>>>((cx_t<T>*)p.tw, (T*)p.sigma, (T*)p.dsym, p.n,
+    { launch_pdl(k_fft_init<T>, (p.n + 255) / 256, 256, 0, s, (cx_t<T>*)p.tw, (T*)p.sigma, (T*)p.dsym, p.n,
                                                        1.0 / (3.0 * g.h * g.h), 1.0 / (6.0 * g.h)); note_launch(); }
     const int E = p.logn < 4 ? 8 : 16;
     const int R0 = p.logn < 4 ? 1 : 1 << (p.logn % 4);

@@ -37,6 +37,7 @@ __device__ __forceinline__ T dy2(const T* F, int i, int k, const Geom& g, T c2) 
 template <typename T>
 __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __restrict__ meta, long long n,
                                   T* __restrict__ Ua, T* __restrict__ Va, Geom g, T c1, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -45,6 +46,7 @@ __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __r
         Ua[a] = dy1(psi, i, k, g, c1);
         Va[a] = -dx1(psi, i, k, g, c1);
     }
+    pdl_trigger();
 }
 
 // nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5); a = 2 nu_t S12, c = nu_t S11
@@ -52,6 +54,7 @@ __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __r
 template <typename T>
 __global__ void k_strain_nut(const T* __restrict__ S11, const T* __restrict__ S12, T* __restrict__ nut,
                              T* __restrict__ a, T* __restrict__ c, long long N, T csh2) {
+    pdl_wait();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         const T s11 = S11[p], s12 = S12[p];
@@ -60,12 +63,14 @@ __global__ void k_strain_nut(const T* __restrict__ S11, const T* __restrict__ S1
         if (a) a[p] = T(2) * nt * s12;
         if (c) c[p] = nt * s11;
     }
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restrict__ Vlat,
                                   const uint32_t* __restrict__ meta, long long n, T* __restrict__ Ua,
                                   T* __restrict__ Va, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -73,23 +78,27 @@ __global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restric
         Ua[a] = Ulat[p];
         Va[a] = Vlat[p];
     }
+    pdl_trigger();
 }
 
 // Pass 3: t0 = d(t3)/dy.
 template <typename T>
 __global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c1) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(p & g.mask), k = (int)(p >> g.L);
         t0[p] = dy1(t3, i, k, g, c1);
     }
+    pdl_trigger();
 }
 
 // Pass 4 at the active points: g = Dxx(t2) - Dyy(t2) - 4 Dx(t0).
 template <typename T>
 __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const uint32_t* __restrict__ meta,
                        long long n, T* __restrict__ ga, Geom g, T c1, T c2, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -97,6 +106,7 @@ __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const
         const int i = p & g.mask, k = p >> g.L;
         ga[a] = dx2(t2, i, k, g, c2) - dy2(t2, i, k, g, c2) - T(4) * dx1(t0, i, k, g, c1);
     }
+    pdl_trigger();
 }
 
 // Smagorinsky forcing restricted to where it is read (FP64 path).  g at an
@@ -107,6 +117,7 @@ __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const
 // the same order as a full lattice pass would use.
 __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ halo, Geom g,
                                 const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -118,6 +129,7 @@ __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, 
             for (int di = -2; di <= 2; ++di)
                 halo[((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask)] = 1;
     }
+    pdl_trigger();
 }
 
 // At halo points: S11 = D_x(D_y psi), S12 = (psi_yy - psi_xx)/2,
@@ -125,6 +137,7 @@ __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, 
 template <typename T>
 __global__ void k_sgs_halo_products(const T* __restrict__ psi, const uint8_t* __restrict__ halo,
                                     T* __restrict__ t2, T* __restrict__ t3, Geom g, T c1, T c2, T csh2) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -138,6 +151,7 @@ __global__ void k_sgs_halo_products(const T* __restrict__ psi, const uint8_t* __
         t2[p] = T(2) * nut * s12;
         t3[p] = nut * s11;
     }
+    pdl_trigger();
 }
 
 // At the active points: g = Dxx(t2) - Dyy(t2) - 4 D_x(D_y t3).
@@ -145,6 +159,7 @@ template <typename T>
 __global__ void k_sgs_halo_forcing(const T* __restrict__ t2, const T* __restrict__ t3,
                                    const uint32_t* __restrict__ meta, long long n, T* __restrict__ ga, Geom g, T c1,
                                    T c2, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -155,10 +170,12 @@ __global__ void k_sgs_halo_forcing(const T* __restrict__ t2, const T* __restrict
         const T dxdy = (T(8) * (vp1 - vm1) - (vp2 - vm2)) * c1;
         ga[a] = dx2(t2, i, k, g, c2) - dy2(t2, i, k, g, c2) - T(4) * dxdy;
     }
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void k_lattice_uv(const T* __restrict__ psi, T* __restrict__ U, T* __restrict__ V, Geom g, T c1) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -166,11 +183,13 @@ __global__ void k_lattice_uv(const T* __restrict__ psi, T* __restrict__ U, T* __
         U[p] = dy1(psi, i, k, g, c1);
         V[p] = -dx1(psi, i, k, g, c1);
     }
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void k_lattice_nut(const T* __restrict__ psi, const T* __restrict__ U, T* __restrict__ nut, Geom g,
                               T c1, T c2, T csh2) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -179,6 +198,7 @@ __global__ void k_lattice_nut(const T* __restrict__ psi, const T* __restrict__ U
         const T s12 = T(0.5) * (dy2(psi, i, k, g, c2) - dx2(psi, i, k, g, c2));
         nut[p] = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
     }
+    pdl_trigger();
 }
 
 // w = A_n q at the active points: -U Dx q - V Dy q + nu (Dxx + Dyy) q - r q (+ g),
@@ -190,6 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const T* __restrict__ F, co
                                                      const T* __restrict__ Va, const T* __restrict__ ga, T nu,
                                                      T r, T* __restrict__ w, Geom g, T c1J, T c2J,
                                                      const int* __restrict__ kstop, int jstep) {
+    pdl_wait();
     if (kstop && jstep >= *kstop) return;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -197,6 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const T* __restrict__ F, co
         if (ga) v += ga[a];
         w[a] = v;
     }
+    pdl_trigger();
 }
 
 // Lattice sums of R, R^2, U^2 + V^2 and |grad R|^2 (deterministic two-stage
@@ -205,6 +227,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_diag(const T* __restrict__ R, const T* __restrict__ psi,
                                                    double* __restrict__ partials, unsigned* __restrict__ counter,
                                                    double* __restrict__ out, Geom g, T c1) {
+    pdl_wait();
     __shared__ double s_red[kThreads / 32][4];
     __shared__ bool s_last;
     const long long N = (long long)g.NJ * g.NJ;
@@ -247,6 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const T* __restrict__ R, cons
         }
         if (threadIdx.x == 0) *counter = 0;
     }
+    pdl_trigger();
 }
 
 }  // namespace
@@ -254,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const T* __restrict__ R, cons
 template <typename T>
 void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* Ua, T* Va, const Geom& g,
                             cudaStream_t s, const int* dn) {
-    if (n > 0) { k_velocity_active<T><<<blocks_for(n), kThreads, 0, s>>>(psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h)), dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_velocity_active<T>, blocks_for(n), kThreads, 0, s, psi, meta, n, Ua, Va, g, T(1.0 / (12.0 * g.h)), dn); note_launch(); }
 }
 
 template <typename T>
@@ -264,9 +288,9 @@ void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs,
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
     cudaMemsetAsync(halo, 0, (size_t)N, s);
-    if (n > 0) { k_sgs_halo_mark<<<blocks_for(n), kThreads, 0, s>>>(meta, n, halo, g, dn); note_launch(); }
-    { k_sgs_halo_products<T><<<blocks_for(N), kThreads, 0, s>>>(psi, halo, t2, t3, g, c1, c2, csh2); note_launch(); }
-    if (n > 0) { k_sgs_halo_forcing<T><<<blocks_for(n), kThreads, 0, s>>>(t2, t3, meta, n, ga, g, c1, c2, dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_sgs_halo_mark, blocks_for(n), kThreads, 0, s, meta, n, halo, g, dn); note_launch(); }
+    { launch_pdl(k_sgs_halo_products<T>, blocks_for(N), kThreads, 0, s, psi, halo, t2, t3, g, c1, c2, csh2); note_launch(); }
+    if (n > 0) { launch_pdl(k_sgs_halo_forcing<T>, blocks_for(n), kThreads, 0, s, t2, t3, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
 template <typename T>
@@ -275,22 +299,22 @@ void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, lo
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
-    { k_strain_nut<T><<<blocks_for(N), kThreads, 0, s>>>(S11, S12, nullptr, ta, tc, N, csh2); note_launch(); }
-    { k_sgs3<T><<<blocks_for(N), kThreads, 0, s>>>(tc, tdyc, g, c1); note_launch(); }
-    if (n > 0) { k_sgs4<T><<<blocks_for(n), kThreads, 0, s>>>(ta, tdyc, meta, n, ga, g, c1, c2, dn); note_launch(); }
+    { launch_pdl(k_strain_nut<T>, blocks_for(N), kThreads, 0, s, S11, S12, nullptr, ta, tc, N, csh2); note_launch(); }
+    { launch_pdl(k_sgs3<T>, blocks_for(N), kThreads, 0, s, tc, tdyc, g, c1); note_launch(); }
+    if (n > 0) { launch_pdl(k_sgs4<T>, blocks_for(n), kThreads, 0, s, ta, tdyc, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
 template <typename T>
 void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s) {
     const long long N = (long long)g.NJ * g.NJ;
-    { k_strain_nut<T><<<blocks_for(N), kThreads, 0, s>>>(S11, S12, nut, nullptr, nullptr, N,
+    { launch_pdl(k_strain_nut<T>, blocks_for(N), kThreads, 0, s, S11, S12, nut, nullptr, nullptr, N,
                                                           T((cs * g.h) * (cs * g.h))); note_launch(); }
 }
 
 template <typename T>
 void launch_velocity_gather(const T* Ulat, const T* Vlat, const uint32_t* meta, long long n, T* Ua, T* Va,
                             cudaStream_t s, const int* dn) {
-    if (n > 0) { k_velocity_gather<T><<<blocks_for(n), kThreads, 0, s>>>(Ulat, Vlat, meta, n, Ua, Va, dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_velocity_gather<T>, blocks_for(n), kThreads, 0, s, Ulat, Vlat, meta, n, Ua, Va, dn); note_launch(); }
 }
 
 template <typename T>
@@ -299,16 +323,16 @@ void launch_lattice_uv_nut(const T* psi, T* U, T* V, T* nut, double cs, T* tmp, 
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     T* Uw = U ? U : tmp;
-    if (!uv_given) { k_lattice_uv<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, V ? V : tmp + N, g, c1); note_launch(); }
+    if (!uv_given) { launch_pdl(k_lattice_uv<T>, blocks_for(N), kThreads, 0, s, psi, Uw, V ? V : tmp + N, g, c1); note_launch(); }
     if (nut)
-        { k_lattice_nut<T><<<blocks_for(N), kThreads, 0, s>>>(psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h))); note_launch(); }
+        { launch_pdl(k_lattice_nut<T>, blocks_for(N), kThreads, 0, s, psi, Uw, nut, g, c1, c2, T((cs * g.h) * (cs * g.h))); note_launch(); }
 }
 
 template <typename T>
 void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va, const T* ga, double nu,
                    double r, T* w, const Geom& g, const int* kstop, int jstep, cudaStream_t s) {
     if (n > 0)
-        { k_matvec<T><<<blocks_for(n), kThreads, 0, s>>>(F, meta, n, Ua, Va, ga, T(nu), T(r), w, g,
+        { launch_pdl(k_matvec<T>, blocks_for(n), kThreads, 0, s, F, meta, n, Ua, Va, ga, T(nu), T(r), w, g,
                                                        T(1.0 / (12.0 * g.h)), T(1.0 / (12.0 * g.h * g.h)), kstop,
                                                        jstep); note_launch(); }
 }
@@ -316,19 +340,21 @@ void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, c
 template <typename T>
 void launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
                  cudaStream_t s) {
-    { k_diag<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(R, psi, partials, counter, out, g,
+    { launch_pdl(k_diag<T>, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, R, psi, partials, counter, out, g,
                                                                        T(1.0 / (12.0 * g.h))); note_launch(); }
 }
 
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, long long n) {
+    pdl_wait();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
         out[t] = (B)in[t];
+    pdl_trigger();
 }
 
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, long long n, cudaStream_t s) {
-    if (n > 0) { k_convert<A, B><<<blocks_for(n), kThreads, 0, s>>>(in, out, n); note_launch(); }
+    if (n > 0) { launch_pdl(k_convert<A, B>, blocks_for(n), kThreads, 0, s, in, out, n); note_launch(); }
 }
 template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);

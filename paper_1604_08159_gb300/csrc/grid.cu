@@ -12,6 +12,7 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 
 template <typename T>
 __global__ void k_init_vortices(T* __restrict__ L, const double* __restrict__ prm, int n, Geom g) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     const double twopi = 2.0 * kPi;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
@@ -28,15 +29,18 @@ __global__ void k_init_vortices(T* __restrict__ L, const double* __restrict__ pr
         }
         L[p] = (T)om;
     }
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict__ vals, long long n,
                           T* __restrict__ L, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x)
         L[meta_pos(meta[a])] = vals[a];
+    pdl_trigger();
 }
 
 // Coarse-to-fine inverse transform for one level: every non-active level-j
@@ -46,6 +50,7 @@ __global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict
 // and odd columns (n = NJ / 2^(J-j) points per row at this level).
 template <typename T>
 __global__ void k_recon_level_1d(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
+    pdl_wait();
     const int sh = g.J - j;
     const int lh = g.L - sh - 1;             // log2(n / 2)
     const int q = 1 << (2 * lh);             // n^2 / 4
@@ -57,6 +62,7 @@ __global__ void k_recon_level_1d(T* __restrict__ L, const uint8_t* __restrict__ 
         const long long p = ((long long)k << g.L) + i;
         if (!act[p]) L[p] = predict<T>(L, i, k, j, g);
     }
+    pdl_trigger();
 }
 
 // Pass 2: the points odd in both directions.  Their prediction is the y
@@ -68,6 +74,7 @@ __global__ void k_recon_level_1d(T* __restrict__ L, const uint8_t* __restrict__ 
 // prediction per point instead of five for most points.
 template <typename T>
 __global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
+    pdl_wait();
     const int sh = g.J - j;
     const int s = 1 << sh, m = g.mask;
     const int lh = g.L - sh - 1;
@@ -91,6 +98,7 @@ __global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ 
         }
         L[p] = dd4<T>(rv[0], rv[1], rv[2], rv[3]);
     }
+    pdl_trigger();
 }
 
 // Details d = u - Pred(u) at the active points (meta == nullptr: every lattice
@@ -102,6 +110,7 @@ template <typename T>
 __global__ void k_details_adj(const uint32_t* __restrict__ meta, long long n, const T* __restrict__ L,
                               double eps, T* __restrict__ det, uint8_t* __restrict__ sig,
                               uint8_t* __restrict__ nxt, Geom g, const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -130,6 +139,7 @@ __global__ void k_details_adj(const uint32_t* __restrict__ meta, long long n, co
             }
         }
     }
+    pdl_trigger();
 }
 
 // Visit the DD4 predictor points of level-j point (i, k).
@@ -156,6 +166,7 @@ __device__ __forceinline__ void for_predictor_points(int i, int k, int j, const 
 // Closure under prediction for one level (finest first): every marked level-j
 // point marks its predictor points, except where `excl` is set.
 __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __restrict__ excl, int j, Geom g) {
+    pdl_wait();
     const long long cnt = level_count(j, g);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
          t += (long long)gridDim.x * blockDim.x) {
@@ -167,6 +178,7 @@ __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __res
             if (!excl || !excl[q]) mask[q] = 1;
         });
     }
+    pdl_trigger();
 }
 
 // Stencil levels and ghost marks.  For an active point P of level l the
@@ -175,6 +187,7 @@ __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __res
 // the non-active ones among them are ghosts.  Same along y.
 __global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __restrict__ gho,
                                 uint8_t* __restrict__ JJ, Geom g) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -205,9 +218,11 @@ __global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __rest
             if (!act[qy]) gho[qy] = 1;
         }
     }
+    pdl_trigger();
 }
 
 __global__ void k_validate_grid(const uint8_t* __restrict__ act, int* __restrict__ flag, Geom g) {
+    pdl_wait();
     const long long N = (long long)g.NJ * g.NJ;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
@@ -224,6 +239,7 @@ __global__ void k_validate_grid(const uint8_t* __restrict__ act, int* __restrict
         });
         if (!ok) atomicOr(flag, 2);
     }
+    pdl_trigger();
 }
 
 // ---- stable multi-bucket compaction -----------------------------------------
@@ -257,6 +273,7 @@ __device__ __forceinline__ void keys16(const uint8_t* __restrict__ act, const ui
 __global__ void __launch_bounds__(kThreads) k_compact_count(const uint8_t* __restrict__ act,
                                                             const uint8_t* __restrict__ gho, Geom g, int nkeys,
                                                             int* __restrict__ blk_counts) {
+    pdl_wait();
     __shared__ int s_w[kThreads / 32][kMaxKeys];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long N = (long long)g.NJ * g.NJ;
@@ -279,6 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_count(const uint8_t* __res
         // key-major: the scan reads each key's counts contiguously
         blk_counts[(long long)threadIdx.x * gridDim.x + blockIdx.x] = c;
     }
+    pdl_trigger();
 }
 
 // Exclusive scan of v over a block of 1024 threads; *total receives the sum.
@@ -317,6 +335,7 @@ constexpr int kScanChunk = 4;
 
 __global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ blk_counts, int nblk, int nkeys,
                                                        int* __restrict__ blk_off, int* __restrict__ counts) {
+    pdl_wait();
     __shared__ int s_tot[kMaxKeys];
     const int chunk = (nblk + 1023) / 1024;
     const int b0 = threadIdx.x * chunk;
@@ -354,6 +373,7 @@ __global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ b
     }
     __syncthreads();
     if (threadIdx.x < nkeys) counts[threadIdx.x] = s_tot[threadIdx.x];
+    pdl_trigger();
 }
 
 // Stable scatter of one tile: thread t's entries of key k go after those of
@@ -363,6 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_scatter(const uint8_t* __r
                                                               const uint8_t* __restrict__ gho, Geom g, int nkeys,
                                                               const int* __restrict__ blk_off,
                                                               int* __restrict__ list) {
+    pdl_wait();
     __shared__ int s_base[kMaxKeys];
     __shared__ int s_w[kThreads / 32][kMaxKeys];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -397,12 +418,14 @@ __global__ void __launch_bounds__(kThreads) k_compact_scatter(const uint8_t* __r
         for (int u = 0; u < 16; ++u)
             if (key[u] == kk) list[off++] = (int)(p0 + u);
     }
+    pdl_trigger();
 }
 
 template <typename T>
 __global__ void k_finalize(const int* __restrict__ list, long long n, const uint8_t* __restrict__ JJ,
                            const T* __restrict__ L, uint32_t* __restrict__ meta, T* __restrict__ omega,
                            const int* __restrict__ dn) {
+    pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
@@ -411,21 +434,25 @@ __global__ void k_finalize(const int* __restrict__ list, long long n, const uint
         meta[a] = pack_meta(p, jj & 15, jj >> 4);
         omega[a] = L[p];
     }
+    pdl_trigger();
 }
 
 // Ghost values of one level from coarser active/ghost values (coarse to fine).
 template <typename T>
 __global__ void k_ghost_fill(T* __restrict__ F, const int* __restrict__ glist, long long n, int j, Geom g,
                              const int* __restrict__ kstop, int jstep) {
+    pdl_wait();
     if (kstop && jstep >= *kstop) return;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const int p = glist[a];
         F[p] = predict<T>(F, p & g.mask, p >> g.L, j, g);
     }
+    pdl_trigger();
 }
 
 __global__ void k_level_counts(const uint32_t* __restrict__ meta, long long n, unsigned long long* counts, Geom g) {
+    pdl_wait();
     __shared__ unsigned int sc[16];
     if (threadIdx.x < 16) sc[threadIdx.x] = 0;
     __syncthreads();
@@ -436,21 +463,27 @@ __global__ void k_level_counts(const uint32_t* __restrict__ meta, long long n, u
     }
     __syncthreads();
     if (threadIdx.x <= g.J && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)sc[threadIdx.x]);
+    pdl_trigger();
 }
 
 __global__ void k_meta_to_mask(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ mask) {
+    pdl_wait();
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x)
         mask[meta_pos(meta[a])] = 1;
+    pdl_trigger();
 }
 
 __global__ void k_list_to_mask(const int* __restrict__ list, long long n, uint8_t* __restrict__ mask) {
+    pdl_wait();
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x)
         mask[list[a]] = 1;
+    pdl_trigger();
 }
 
 __global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, int* idx, uint8_t* jx, uint8_t* jy) {
+    pdl_wait();
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         const uint32_t m = meta[a];
@@ -458,12 +491,14 @@ __global__ void k_meta_unpack(const uint32_t* __restrict__ meta, long long n, in
         if (jx) jx[a] = (uint8_t)meta_jx(m);
         if (jy) jy[a] = (uint8_t)meta_jy(m);
     }
+    pdl_trigger();
 }
 
 // Index of every grid point in the combined numbering: active points
 // 0..n_a-1, then the ghosts n_a.. in list order.
 __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __restrict__ lat2idx,
                           const int* __restrict__ dcounts, int nkeys) {
+    pdl_wait();
     if (dcounts) {
         n = 0;
         for (int q = 0; q < nkeys; ++q) n += dcounts[q];
@@ -471,6 +506,7 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
         lat2idx[list[t]] = (int)t;
+    pdl_trigger();
 }
 
 // Interpolation rows of the ghosts of one level: the value of a ghost is the
@@ -503,6 +539,7 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
                    const int* __restrict__ lat2idx, int* __restrict__ row_len, int* __restrict__ row_idx,
                    double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
                    const int* __restrict__ dcounts, int nkeys) {
+    pdl_wait();
     constexpr int kCap = 64;
     static_assert(kRowHash >= 2 * kCap && (kRowHash & (kRowHash - 1)) == 0 && kRowHash == 128, "row_hash gives 7 bits");
     __shared__ int s_idx[kRowWarps][kCap];
@@ -643,74 +680,75 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
         }
         __syncwarp();
     }
+    pdl_trigger();
 }
 
 }  // namespace
 
 template <typename T>
 void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s) {
-    { k_init_vortices<T><<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(L, params, n, g); note_launch(); }
+    { launch_pdl(k_init_vortices<T>, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, L, params, n, g); note_launch(); }
 }
 template <typename T>
 void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn) {
-    if (n > 0) { k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(meta, vals, n, L, dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_scatter<T>, blocks_for(n), kThreads, 0, s, meta, vals, n, L, dn); note_launch(); }
 }
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
     const long long q = level_count(j, g) / 3;   // n^2 / 4
-    { k_recon_level_1d<T><<<blocks_for(2 * q), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
-    { k_recon_level_2d<T><<<blocks_for(q), kThreads, 0, s>>>(L, act, j, g); note_launch(); }
+    { launch_pdl(k_recon_level_1d<T>, blocks_for(2 * q), kThreads, 0, s, L, act, j, g); note_launch(); }
+    { launch_pdl(k_recon_level_2d<T>, blocks_for(q), kThreads, 0, s, L, act, j, g); note_launch(); }
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
                         uint8_t* nxt, const Geom& g, cudaStream_t s, const int* dn) {
-    if (n > 0) { k_details_adj<T><<<blocks_for(n), kThreads, 0, s>>>(meta, n, L, eps, det, sig, nxt, g, dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_details_adj<T>, blocks_for(n), kThreads, 0, s, meta, n, L, eps, det, sig, nxt, g, dn); note_launch(); }
 }
 void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s) {
-    { k_closure_level<<<blocks_for(level_count(j, g)), kThreads, 0, s>>>(mask, excl, j, g); note_launch(); }
+    { launch_pdl(k_closure_level, blocks_for(level_count(j, g)), kThreads, 0, s, mask, excl, j, g); note_launch(); }
 }
 void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s) {
-    { k_stencil_ghost<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, gho, JJ, g); note_launch(); }
+    { launch_pdl(k_stencil_ghost, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, act, gho, JJ, g); note_launch(); }
 }
 void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s) {
-    { k_validate_grid<<<blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s>>>(act, flag, g); note_launch(); }
+    { launch_pdl(k_validate_grid, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, act, flag, g); note_launch(); }
 }
 void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int nkeys, int* blk_counts,
                     int* blk_off, int* counts, int* list, cudaStream_t s) {
     const long long N = (long long)g.NJ * g.NJ;
     const int nblk = (int)((N + kTile - 1) / kTile);
-    { k_compact_count<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_counts); note_launch(); }
-    { k_compact_scan<<<1, 1024, 0, s>>>(blk_counts, nblk, nkeys, blk_off, counts); note_launch(); }
-    { k_compact_scatter<<<nblk, kThreads, 0, s>>>(act, gho, g, nkeys, blk_off, list); note_launch(); }
+    { launch_pdl(k_compact_count, nblk, kThreads, 0, s, act, gho, g, nkeys, blk_counts); note_launch(); }
+    { launch_pdl(k_compact_scan, 1, 1024, 0, s, blk_counts, nblk, nkeys, blk_off, counts); note_launch(); }
+    { launch_pdl(k_compact_scatter, nblk, kThreads, 0, s, act, gho, g, nkeys, blk_off, list); note_launch(); }
 }
 template <typename T>
 void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
                      cudaStream_t s, const int* dn) {
-    if (n > 0) { k_finalize<T><<<blocks_for(n), kThreads, 0, s>>>(list, n, JJ, L, meta, omega, dn); note_launch(); }
+    if (n > 0) { launch_pdl(k_finalize<T>, blocks_for(n), kThreads, 0, s, list, n, JJ, L, meta, omega, dn); note_launch(); }
 }
 template <typename T>
 void launch_ghost_fill(T* F, const int* glist, long long n, int j, const Geom& g, const int* kstop, int jstep,
                        cudaStream_t s) {
-    if (n > 0) { k_ghost_fill<T><<<blocks_for(n), kThreads, 0, s>>>(F, glist, n, j, g, kstop, jstep); note_launch(); }
+    if (n > 0) { launch_pdl(k_ghost_fill<T>, blocks_for(n), kThreads, 0, s, F, glist, n, j, g, kstop, jstep); note_launch(); }
 }
 void launch_level_counts(const uint32_t* meta, long long n, unsigned long long* counts, const Geom& g,
                          cudaStream_t s) {
-    if (n > 0) { k_level_counts<<<blocks_for(n), kThreads, 0, s>>>(meta, n, counts, g); note_launch(); }
+    if (n > 0) { launch_pdl(k_level_counts, blocks_for(n), kThreads, 0, s, meta, n, counts, g); note_launch(); }
 }
 void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaStream_t s) {
-    if (n > 0) { k_meta_to_mask<<<blocks_for(n), kThreads, 0, s>>>(meta, n, mask); note_launch(); }
+    if (n > 0) { launch_pdl(k_meta_to_mask, blocks_for(n), kThreads, 0, s, meta, n, mask); note_launch(); }
 }
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s) {
-    if (n > 0) { k_list_to_mask<<<blocks_for(n), kThreads, 0, s>>>(list, n, mask); note_launch(); }
+    if (n > 0) { launch_pdl(k_list_to_mask, blocks_for(n), kThreads, 0, s, list, n, mask); note_launch(); }
 }
 void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
                        int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
                        int* overflow, cudaStream_t s, const int* dcounts, long long cap_a, long long cap_g) {
     if (dcounts) {
         // sizes on the device, grids over the capacities (capturable)
-        { k_lat2idx<<<blocks_for(cap_a + cap_g), kThreads, 0, s>>>(list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
+        { launch_pdl(k_lat2idx, blocks_for(cap_a + cap_g), kThreads, 0, s, list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
         for (int j = 1; j <= J; ++j) {
-            k_ghost_rows_level<<<blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s>>>(
+            launch_pdl(k_ghost_rows_level, blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s,
                 list, 0, 0, 0, 0, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, dcounts, J + 1);
             note_launch();
         }
@@ -718,17 +756,17 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
     }
     long long tot = n_act;
     for (int j = 1; j <= J; ++j) tot += gcnt[j];
-    if (tot > 0) { k_lat2idx<<<blocks_for(tot), kThreads, 0, s>>>(list, tot, lat2idx, nullptr, 0); note_launch(); }
+    if (tot > 0) { launch_pdl(k_lat2idx, blocks_for(tot), kThreads, 0, s, list, tot, lat2idx, nullptr, 0); note_launch(); }
     for (int j = 1; j <= J; ++j)
         if (gcnt[j] > 0) {
-            k_ghost_rows_level<<<blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s>>>(
+            launch_pdl(k_ghost_rows_level, blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s,
                 list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, nullptr,
                 0);
             note_launch();
         }
 }
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy, cudaStream_t s) {
-    if (n > 0) { k_meta_unpack<<<blocks_for(n), kThreads, 0, s>>>(meta, n, idx, jx, jy); note_launch(); }
+    if (n > 0) { launch_pdl(k_meta_unpack, blocks_for(n), kThreads, 0, s, meta, n, idx, jx, jy); note_launch(); }
 }
 
 #define WRC_INST(T)                                                                                       \
