@@ -55,6 +55,14 @@ What each function follows
 ``arnoldi_phi1``           Abstract / Sec. 2.1: projection of the discrete system
                            onto a Krylov subspace (exponential-Euler reading).
 ``step``                   One full time step followed by grid adaptation.
+``scalar_operator``, ``scalar_init``, ``step_with_scalar``
+                           Sec. "Transport of water vapor as a passive scalar":
+                           the vapour mixing ratio r_v carried by the flow,
+                           Eq. (vapour) with only a diffusion term on its
+                           right-hand side, advanced by the same Krylov
+                           projection on the same adaptive grid, which adapts
+                           to both fields (union of their significant sets; a
+                           reading: the paper does not spell the joint rule).
 
 Parity pins live in ``tests/test_oracle_*.py`` (closed forms, invariants,
 brute force on tiny lattices, the paper's Table 1 convergence rate).  Every
@@ -76,7 +84,8 @@ __all__ = [
     "smagorinsky_nut", "stress_vorticity_forcing", "sgs_forcing", "laplacian_symbol",
     "vortex_field", "Frozen", "freeze", "apply_operator", "arnoldi_phi1",
     "phi1_augmented", "adapt", "initial_state", "state_from_field", "step",
-    "diagnostics", "BREAKDOWN_TOL",
+    "diagnostics", "BREAKDOWN_TOL", "scalar_operator", "adapt_two", "scalar_init",
+    "step_with_scalar",
 ]
 
 # Happy-breakdown test of the Arnoldi process: stop when the new direction is
@@ -598,3 +607,70 @@ def diagnostics(cfg: Config, st: State) -> dict:
         "circulation": w * float(np.sum(R)),
         "n_active": int(st.active.sum()),
     }
+
+
+# --------------------------------------------------------------------------
+# Passive scalar: the vapour mixing ratio with diffusion only (the section on
+# the transport of water vapor; Eq. (vapour) with its right-hand side
+# replaced by a diffusion term)
+# --------------------------------------------------------------------------
+
+def scalar_operator(cfg: Config, fz: Frozen, kappa: float, q: np.ndarray) -> np.ndarray:
+    """A_r q = -U Dx q - V Dy q + kappa (Dxx + Dyy) q at the active points: the
+    material derivative with the frozen velocity and a diffusion term of
+    diffusivity kappa (no Rayleigh friction, no subgrid forcing), derivatives
+    as in ``apply_operator``."""
+    Q = np.zeros_like(fz.R)
+    Q[fz.A] = q
+    RQ = reconstruct(Q, fz.A, cfg.J)
+    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h)
+    a = fz.A
+    return -fz.U[a] * Dx[a] - fz.V[a] * Dy[a] + kappa * (Dxx[a] + Dyy[a])
+
+
+def adapt_two(cfg: Config, active: np.ndarray, omega: np.ndarray, rv: np.ndarray, rv_whole: bool = False):
+    """Grid adaptation driven by both fields: the significant sets of omega
+    and of r_v (each from its own details on the grid, or on every lattice
+    point for a freshly sampled r_v when ``rv_whole``) are joined, then the
+    adjacent zone and the closure; values at the new grid from the
+    reconstructions.  Returns (A', omega', r_v')."""
+    lev = levels(cfg.n0, cfg.J)
+    Rw = reconstruct(omega, active, cfg.J)
+    Sw = significant(details(Rw, active, cfg.J), active, lev, cfg.eps)
+    if rv_whole:
+        full = np.ones_like(active)
+        Rr = np.asarray(rv, dtype=np.float64)
+        Sr = significant(details(Rr, full, cfg.J), full, lev, cfg.eps)
+    else:
+        Rr = reconstruct(rv, active, cfg.J)
+        Sr = significant(details(Rr, active, cfg.J), active, lev, cfg.eps)
+    A2 = closure(adjacent_zone(Sw | Sr, lev, cfg.J), cfg.J)
+    return A2, np.where(A2, Rw, 0.0), np.where(A2, Rr, 0.0)
+
+
+def scalar_init(cfg: Config, st: State, rv_lattice: np.ndarray):
+    """Start the passive scalar from a field sampled on the full lattice: one
+    joint adaptation of the current omega grid and the sampled field.
+    Returns (state on the joint grid, r_v lattice array on it)."""
+    A2, om2, rv2 = adapt_two(cfg, st.active, st.omega, rv_lattice, rv_whole=True)
+    return State(A2, om2, st.t, st.nstep), rv2
+
+
+def step_with_scalar(cfg: Config, st: State, rv: np.ndarray, kappa: float):
+    """One step of omega (as ``step``) and of r_v with the same frozen
+    velocity: r_v^{n+1} = r_v^n + dt phi_1(dt A_r) A_r r_v^n, then the joint
+    adaptation.  Returns (new state, new r_v, StepInfo of omega, StepInfo of
+    r_v)."""
+    fz = freeze(cfg, st.active, st.omega)
+    om = st.omega[st.active]
+    b = apply_operator(cfg, fz, om) + fz.g[st.active]
+    inc, info = arnoldi_phi1(lambda q: apply_operator(cfg, fz, q), b, cfg.m, cfg.dt)
+    new = np.zeros_like(st.omega)
+    new[st.active] = om + inc
+    r = rv[st.active]
+    br = scalar_operator(cfg, fz, kappa, r)
+    inc_r, info_r = arnoldi_phi1(lambda q: scalar_operator(cfg, fz, kappa, q), br, cfg.m, cfg.dt)
+    newr = np.zeros_like(rv)
+    newr[st.active] = r + inc_r
+    A2, om2, rv2 = adapt_two(cfg, st.active, new, newr)
+    return State(A2, om2, st.t + cfg.dt, st.nstep + 1), rv2, info, info_r
