@@ -219,6 +219,33 @@ const char* wrc_last_error(const wrc_run* run);
 /* Release the run's device memory (synchronises its stream first). */
 void wrc_destroy(wrc_run* run);
 
+/* ---- Passive scalar ----------------------------------------------------------
+ * The vapour mixing ratio r_v of the paper's section on the transport of
+ * water vapor: Eq. (vapour) with only a diffusion term on its right-hand
+ * side, D r_v / Dt = kappa (Dxx + Dyy) r_v, carried by the run's flow.  Each
+ * wrc_step then advances r_v with the same Krylov projection and the same
+ * frozen velocity as omega, r_v^{n+1} = r_v^n + dt phi_1(dt A_r) A_r r_v^n with
+ * A_r = -U Dx - V Dy + kappa (Dxx + Dyy) (no Rayleigh friction, no subgrid
+ * forcing), and the adaptive grid adapts to both fields: the significant
+ * sets of omega and r_v (same eps) are joined before the adjacent zone and
+ * the closure.  Supported by wrc_step only (a batched ensemble or the server
+ * refuses such a run); a new initial condition (wrc_init_*, wrc_set_grid)
+ * drops the scalar. */
+
+/* Enable the passive scalar with diffusivity kappa >= 0 and its initial
+ * field: NJ*NJ doubles, row-major [k * NJ + i] (host or device memory per
+ * device_ptr; not kept).  The run must have an initial condition.  The grid
+ * is thresholded once more with omega's details on the current grid and the
+ * field's details on every lattice point; r_v at the new grid is the field
+ * there.  Synchronises.  WRC_ERR_ARG for a NULL field or kappa < 0;
+ * WRC_ERR_STATE without an initial condition; WRC_ERR_OOM, WRC_ERR_CUDA. */
+wrc_status wrc_scalar_init(wrc_run* run, double kappa, const double* field, int32_t device_ptr);
+
+/* The active lattice indices and r_v at them, in the order of
+ * wrc_query_active (cap >= the active count).  Synchronises.  WRC_ERR_STATE
+ * when the scalar is not enabled; WRC_ERR_ARG if cap is too small. */
+wrc_status wrc_query_scalar(wrc_run* run, int32_t* idx_out, double* r_out, int64_t cap, int32_t device_ptr);
+
 /* ---- Diagnostics without allocation ------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- code running while a stream is captured

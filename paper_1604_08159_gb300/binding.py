@@ -55,6 +55,8 @@ SIGNATURES = {
     "wrc_sync": (c_int32, [c_void_p]),
     "wrc_query_counts": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "wrc_query_active": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
+    "wrc_scalar_init": (c_int32, [c_void_p, c_double, c_void_p, c_int32]),
+    "wrc_query_scalar": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_query_masks": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
     "wrc_query_details": (c_int32, [c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_query_stencil_levels": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
@@ -204,6 +206,17 @@ def wrc_query_active(run, idx_out=None, omega_out=None, cap: int = 0):
     _check("wrc_query_active", load().wrc_query_active(run, pi, po, cap, _flag((pi, fi), (po, fo))), run)
 
 
+def wrc_scalar_init(run, kappa: float, field):
+    p, f = _ptr(field)
+    _check("wrc_scalar_init", load().wrc_scalar_init(run, float(kappa), p, f), run)
+
+
+def wrc_query_scalar(run, idx_out=None, r_out=None, cap: int = 0):
+    pi, fi = _ptr(idx_out)
+    pr, fr = _ptr(r_out)
+    _check("wrc_query_scalar", load().wrc_query_scalar(run, pi, pr, cap, _flag((pi, fi), (pr, fr))), run)
+
+
 def wrc_query_masks(run, active=None, ghost=None, significant=None):
     ps = [_ptr(x) for x in (active, ghost, significant)]
     _check("wrc_query_masks", load().wrc_query_masks(run, ps[0][0], ps[1][0], ps[2][0], _flag(*ps)), run)
@@ -345,6 +358,18 @@ class Run:
         om = np.zeros(na)
         wrc_query_active(self.h, idx, om, na)
         return idx, om
+
+    def scalar_init(self, kappa, field):
+        """Enable the passive scalar (vapour mixing ratio) from a lattice field."""
+        wrc_scalar_init(self.h, kappa, np.ascontiguousarray(field, dtype=np.float64) if isinstance(field, np.ndarray)
+                        else field)
+
+    def scalar(self):
+        na = self.counts()[0]
+        idx = np.zeros(na, dtype=np.int32)
+        r = np.zeros(na)
+        wrc_query_scalar(self.h, idx, r, na)
+        return idx, r
 
     def masks(self):
         n2 = self.NJ * self.NJ

@@ -163,6 +163,13 @@ struct wrc_run {
     double updates = 0.0;   // sum of the active count over the steps taken
     bool nonfinite = false; // a step met a non-finite Arnoldi coefficient (seen at its grid rebuild)
     bool init = false, frozen = false;
+
+    // passive scalar (the vapour mixing ratio with diffusion only), enabled by
+    // wrc_scalar_init: compact values on the grid, its reconstruction on the
+    // lattice, and the small arrays of its Krylov step (H, beta, y; kstop)
+    bool scalar = false;
+    double kappa = 0.0;
+    DevBuf rv[2], Lr, kr;
 };
 
 namespace {
@@ -221,6 +228,10 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     CK(R->meta[1 - R->cur].grow(sizeof(uint32_t) * c, 0, s));
     CK(R->omega[R->cur].grow(be, R->es * R->n_active, s));
     CK(R->omega[1 - R->cur].grow(be, 0, s));
+    if (R->scalar) {
+        CK(R->rv[R->cur].grow(be, R->es * R->n_active, s));
+        CK(R->rv[1 - R->cur].grow(be, 0, s));
+    }
     CK(R->det.grow(be, R->es * R->det_count, s));
     CK(R->Ua.grow(be, 0, s));
     CK(R->Va.grow(be, 0, s));
@@ -309,6 +320,9 @@ wrc_status rebuild_part2(wrc_run* R) {
     const int nc = 1 - R->cur;
     launch_finalize<T>(R->list, R->cap, R->JJ, (const T*)R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<T>(), s,
                        R->counts_dev);
+    if (R->scalar)   // r_v at the new grid from its reconstruction (meta is rewritten identically)
+        launch_finalize<T>(R->list, R->cap, R->JJ, R->Lr.as<T>(), R->meta[nc].as<uint32_t>(), R->rv[nc].as<T>(), s,
+                           R->counts_dev);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
     launch_ghost_rows(R->list, 0, nullptr, nullptr, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
                       R->row_w.as<double>(), kGhostRowMax, R->g, R->K.overflow, s, R->counts_dev, R->cap, R->cap_g);
@@ -380,6 +394,9 @@ wrc_status threshold_body(wrc_run* R, double eps, bool whole_lattice) {
     else
         launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, (const T*)R->L, eps, R->det.as<T>(), R->sig,
                               R->nxt, g, s, R->counts_dev);
+    if (R->scalar && !whole_lattice)   // the grid adapts to r_v as well: union of the significant sets
+        launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, R->Lr.as<T>(), eps, nullptr, R->sig, R->nxt, g,
+                              s, R->counts_dev);
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
     CKL("threshold");
     return rebuild_part1(R);
@@ -415,11 +432,23 @@ wrc_status reconstruct(wrc_run* R) {
     return WRC_OK;
 }
 
-// Linearisation at the current state: R(omega), psi, U, V and the SGS forcing.
+// Lr <- R(r_v), as reconstruct does for omega.
+template <typename T>
+wrc_status reconstruct_scalar(wrc_run* R) {
+    launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->rv[R->cur].as<T>(), R->cap, R->Lr.as<T>(), R->st,
+                      R->counts_dev);
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>(R->Lr.as<T>(), R->act, j, R->g, R->st);
+    CKL("reconstruct scalar");
+    return WRC_OK;
+}
+
+// Linearisation at the current state: R(omega), psi, U, V and the SGS forcing
+// (and R(r_v) when the passive scalar is on).
 template <typename T>
 wrc_status freeze(wrc_run* R) {
     TRY(reconstruct<T>(R));
     CKL("freeze/reconstruct");
+    if (R->scalar) TRY(reconstruct_scalar<T>(R));
     const cudaStream_t s = R->st;
     const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
     T* t0 = (T*)R->C1;
@@ -532,6 +561,27 @@ KrylovStepArgs krylov_args(wrc_run* R) {
     return A;
 }
 
+// Arguments of the Krylov step of the passive scalar: the same grid,
+// velocity and workspace, the operator -U Dx - V Dy + kappa (Dxx + Dyy) (no
+// Rayleigh friction, no subgrid forcing), its values and lattice, and its own
+// small arrays (the vorticity step's H, beta, y and k stay queryable).
+KrylovStepArgs krylov_args_scalar(wrc_run* R) {
+    KrylovStepArgs A = krylov_args(R);
+    const int m = R->cfg.krylov_m;
+    double* d = R->kr.as<double>();
+    A.ga = nullptr;
+    A.nu = R->kappa;
+    A.r = 0.0;
+    A.L = R->Lr.p;
+    A.omega = R->rv[R->cur].p;
+    A.H = d;
+    A.beta = d + (size_t)(m + 1) * m;
+    A.y = A.beta + 1;
+    A.kstop = (int*)(A.y + 32);
+    A.trace = nullptr;
+    return A;
+}
+
 // Clear the phase trace before a traced launch (on the run's stream).
 wrc_status trace_reset(wrc_run* R, int nb) {
     if (!R->tracing) return WRC_OK;
@@ -565,6 +615,7 @@ wrc_status krylov(wrc_run* R) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
         R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
     }
+    if (R->scalar) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s));
     return WRC_OK;
 }
 
@@ -581,6 +632,8 @@ wrc_status step_once(wrc_run* R) {
     TRY(run_phase(R, kPhaseAdapt1, [&] {
         // L holds omega^{n+1} at the grid points; reconstruct the rest, threshold
         for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
+        if (R->scalar)   // Lr holds r_v^{n+1} at the grid points
+            for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>(R->Lr.as<T>(), R->act, j, R->g, R->st);
         return threshold_body<T>(R, R->cfg.eps, false);
     }));
     R->det_count = R->n_active;
@@ -671,6 +724,7 @@ wrc_status set_grid_t(wrc_run* R, const uint8_t* active, const double* omega_lat
 template <typename T>
 wrc_status threshold_t(wrc_run* R, double eps) {
     TRY(reconstruct<T>(R));
+    if (R->scalar) TRY(reconstruct_scalar<T>(R));
     return threshold_current<T>(R, eps, false);
 }
 
@@ -742,12 +796,49 @@ wrc_status diagnostics_t(wrc_run* R) {
     return WRC_OK;
 }
 
+// Passive scalar from a lattice field: buffers, Lr <- the field, L <- R(omega)
+// on the current grid, one joint thresholding (omega's details on its grid,
+// the field's on every lattice point), and the rebuild, which samples r_v at
+// the new grid from the field.
+template <typename T>
+wrc_status scalar_init_t(wrc_run* R, double kappa, const double* field, int device_ptr) {
+    const cudaStream_t s = R->st;
+    const Geom& g = R->g;
+    const int m = R->cfg.krylov_m;
+    double* scr = R->fp32 ? lattice_scratch(R) : nullptr;
+    if (R->fp32 && !scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+    CK(R->Lr.grow(R->es * (size_t)R->N, 0, s));
+    CK(R->rv[0].grow(R->es * (size_t)R->cap, 0, s));
+    CK(R->rv[1].grow(R->es * (size_t)R->cap, 0, s));
+    CK(R->kr.grow(sizeof(double) * ((size_t)(m + 1) * m + 1 + 32) + sizeof(int) * 4, 0, s));
+    CK(cudaMemsetAsync(R->kr.p, 0, R->kr.bytes, s));
+    TRY(in_from_double<T>(R, R->Lr.as<T>(), field, R->N, device_ptr, scr));
+    TRY(reconstruct<T>(R));
+    CK(cudaMemsetAsync(R->sig, 0, R->N, s));
+    CK(cudaMemsetAsync(R->nxt, 0, R->N, s));
+    launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, (const T*)R->L, R->cfg.eps, R->det.as<T>(), R->sig,
+                          R->nxt, g, s, R->counts_dev);
+    launch_details_adj<T>(nullptr, R->N, R->Lr.as<T>(), R->cfg.eps, nullptr, R->sig, R->nxt, g, s);
+    for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
+    CKL("scalar threshold");
+    R->scalar = true;
+    R->kappa = kappa;
+    R->layout += 1;   // the captured phases change
+    R->det_count = R->n_active;
+    TRY(rebuild_part1(R));
+    TRY(rebuild_host(R));
+    TRY(rebuild_part2<T>(R));
+    rebuild_commit(R);
+    return WRC_OK;
+}
+
 void free_run(wrc_run* R) {
     if (!R) return;
     cudaStream_t s = R->st;
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
-                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace})
+                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace, &R->rv[0],
+                    &R->rv[1], &R->Lr, &R->kr})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->halo, R->list, R->lat2idx,
@@ -898,6 +989,8 @@ wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const doub
     CK(cudaStreamSynchronize(R->st));   // prm is a stack array
     CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
     R->n_active = 0;
+    if (R->scalar) R->layout += 1;
+    R->scalar = false;   // a new initial condition drops the passive scalar
     TRY(DISPATCH(R, threshold_current, R, R->cfg.eps, true));
     R->init = true;
     R->t = 0.0;
@@ -908,6 +1001,8 @@ wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const doub
 wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
     if (!omega_lattice) return fail(R, WRC_ERR_ARG, "omega_lattice is NULL");
+    if (R->scalar) R->layout += 1;
+    R->scalar = false;
     TRY(DISPATCH(R, init_field_t, R, omega_lattice, device_ptr));
     R->init = true;
     R->t = 0.0;
@@ -918,6 +1013,8 @@ wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t devic
 wrc_status wrc_set_grid(wrc_run* R, const uint8_t* active, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
     if (!active || !omega_lattice) return fail(R, WRC_ERR_ARG, "NULL input");
+    if (R->scalar) R->layout += 1;
+    R->scalar = false;
     TRY(DISPATCH(R, set_grid_t, R, active, omega_lattice, device_ptr));
     R->init = true;
     return WRC_OK;
@@ -977,6 +1074,36 @@ wrc_status wrc_query_active(wrc_run* R, int32_t* idx_out, double* omega_out, int
     }
     if (idx_out) {
         int* tmpi = R->tmp.as<int>();   // tmp holds >= n doubles, i.e. >= 2n ints
+        launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, tmpi, nullptr, nullptr, R->st);
+        CKL("unpack");
+        TRY(copy_out(R, idx_out, tmpi, sizeof(int) * n, device_ptr));
+    }
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
+wrc_status wrc_scalar_init(wrc_run* R, double kappa, const double* field, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!field) return fail(R, WRC_ERR_ARG, "field is NULL");
+    if (!(kappa >= 0) || !std::isfinite(kappa)) return fail(R, WRC_ERR_ARG, "kappa must be finite and >= 0");
+    const bool was = R->scalar;
+    const wrc_status st = DISPATCH(R, scalar_init_t, R, kappa, field, device_ptr);
+    if (st != WRC_OK && !was) R->scalar = false;
+    return st;
+}
+
+wrc_status wrc_query_scalar(wrc_run* R, int32_t* idx_out, double* r_out, int64_t cap, int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!R->scalar) return fail(R, WRC_ERR_STATE, "the passive scalar is not enabled (wrc_scalar_init)");
+    if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
+    const long long n = R->n_active;
+    if (r_out) {
+        if (R->fp32) TRY(out_as_double<float>(R, r_out, R->rv[R->cur].as<float>(), n, device_ptr, R->tmp.as<double>()));
+        else TRY(copy_out(R, r_out, R->rv[R->cur].p, sizeof(double) * n, device_ptr));
+        CK(cudaStreamSynchronize(R->st));
+    }
+    if (idx_out) {
+        int* tmpi = R->tmp.as<int>();
         launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, tmpi, nullptr, nullptr, R->st);
         CKL("unpack");
         TRY(copy_out(R, idx_out, tmpi, sizeof(int) * n, device_ptr));
@@ -1307,9 +1434,15 @@ wrc_status batch_step_t(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vec
         return st;
     };
     std::vector<long long> na0(M);
+    for (size_t i = 0; i < M; ++i)
+        if (runs[i]->scalar) {
+            runs[i]->err = "the passive scalar is advanced by wrc_step only";
+            mark(i, WRC_ERR_ARG);
+        }
     for (size_t i = 0; i < M; ++i) {
         wrc_run* R = runs[i];
         na0[i] = R->n_active;
+        if (rs[i] != WRC_OK) continue;
         const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); });
         if (st != WRC_OK) mark(i, st);
         else R->frozen = true;
