@@ -274,6 +274,48 @@ def measure_ensemble(args):
             "throughput_ratio": batched / solo if solo > 0 else None}
 
 
+def measure_scalar(args, wl):
+    """The passive scalar of the water-vapour section on the same workload:
+    r_v = 1 for y > 0, else 0 (the paper's initial condition), diffusivity
+    1/Re, advanced with omega by every step on the grid that adapts to both
+    fields.  Device time per step by CUDA events on the run's stream, after
+    warm-up steps; updates count the active points (each advancing both
+    fields)."""
+    import numpy as np
+    import torch
+
+    from paper_1604_08159_gb300 import binding as B
+
+    p = wl.params
+    NJ = p.NJ
+    y = -np.pi + (2.0 * np.pi / NJ) * np.arange(NJ)
+    field = np.repeat((y > 0).astype(np.float64)[:, None], NJ, axis=1)   # [k, i]
+    stream = torch.cuda.Stream()
+    with B.Run(p, stream=stream.cuda_stream) as run:
+        run.init_vortices(wl.vortices)
+        na_omega = run.stats()["n_active"]
+        run.scalar_init(1.0 / p.re, field)
+        run.step(3)
+        run.sync()
+        n = max(1, min(args.steps, 10))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        upd = 0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            upd += run.stats()["n_active"]
+            run.step(1)
+        e1.record(stream)
+        run.sync()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+    return {"initial_condition": "r_v = 1 for y > 0 else 0 (water-vapour section), kappa = 1/Re",
+            "steps": n, "ms_per_step": ms, "mean_active_points": upd / n,
+            "active_points_without_scalar": na_omega, "value": upd / (ms * 1e-3 * n),
+            "unit": UNIT + " (both fields advanced per update)"}
+
+
 KRYLOV_SOURCES = ("csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh", "csrc/kernels.h")
 
 
@@ -417,6 +459,9 @@ def run_ours(args):
     ensemble = None
     if not args.no_ensemble and rank == 0:
         ensemble = measure_ensemble(args)
+    scalar = None
+    if not args.no_scalar and rank == 0:
+        scalar = measure_scalar(args, wl)
 
     # max over ranks
     t_dev, upd = combine_ranks(dev_ms, upd, "cuda")
@@ -458,6 +503,7 @@ def run_ours(args):
             "clocks": sampler.summary(),
             "serving": serving,
             "ensemble": ensemble,
+            "scalar": scalar,
         }
         print(json.dumps(line), flush=True)
     run.close()
@@ -479,6 +525,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fujiwhara_1024")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-scalar", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=5)
     ap.add_argument("--ens-solo-sample", type=int, default=32)
