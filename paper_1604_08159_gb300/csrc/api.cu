@@ -481,8 +481,9 @@ wrc_status freeze(wrc_run* R) {
                                   R->counts_dev);
     }
     if (R->cfg.sgs == WRC_SGS_DYNAMIC)
-        launch_sgs_halo<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t2, t3, R->halo, R->g, s,
-                           R->counts_dev);
+        // t0, t1 (the first work array, free after the Poisson solve here) hold the halo list
+        launch_sgs_halo<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t2, t3, R->halo, (int*)t0, R->g,
+                           s, R->counts_dev);
     CKL("freeze");
     R->frozen = true;
     return WRC_OK;

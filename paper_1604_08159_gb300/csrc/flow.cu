@@ -1,6 +1,8 @@
 // Velocity from the streamfunction, the Smagorinsky forcing of Eq. 5, the
 // frozen linear operator A_n of the Krylov step (Sec. 2.5 collocation
 // derivatives at each point's stencil level), and lattice diagnostics.
+#include <algorithm>
+
 #include "kernels.h"
 #include "operator.cuh"
 
@@ -114,9 +116,12 @@ __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const
 // its x-neighbours at distance <= 2, i.e. nu_t S12 and nu_t S11 inside the
 // 5 x 5 box around it; those products are formed only at the lattice points
 // of the union of these boxes (the halo), from psi with the same stencils in
-// the same order as a full lattice pass would use.
-__global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ halo, Geom g,
-                                const int* __restrict__ dn) {
+// the same order as a full lattice pass would use.  The first visit of a
+// halo point (an atomic OR on the 32-bit word holding its mask byte) appends
+// it to the list hlist[1..], count in hlist[0], so the products run over the
+// halo only; the list order varies, the value at each point does not.
+__global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ halo,
+                                int* __restrict__ hlist, Geom g, const int* __restrict__ dn) {
     pdl_wait();
     n = eff_n(dn, n);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
@@ -126,8 +131,12 @@ __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, 
 #pragma unroll
         for (int dk = -2; dk <= 2; ++dk)
 #pragma unroll
-            for (int di = -2; di <= 2; ++di)
-                halo[((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask)] = 1;
+            for (int di = -2; di <= 2; ++di) {
+                const size_t q = ((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask);
+                const unsigned bit = 1u << (8 * (q & 3));
+                const unsigned old = atomicOr(reinterpret_cast<unsigned*>(halo + (q & ~(size_t)3)), bit);
+                if (!(old & bit)) hlist[1 + atomicAdd(hlist, 1)] = (int)q;
+            }
     }
     pdl_trigger();
 }
@@ -135,14 +144,13 @@ __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, 
 // At halo points: S11 = D_x(D_y psi), S12 = (psi_yy - psi_xx)/2,
 // nu_t = (C_s h)^2 2 sqrt(S11^2 + S12^2) (Eq. 5); t2 = 2 nu_t S12, t3 = nu_t S11.
 template <typename T>
-__global__ void k_sgs_halo_products(const T* __restrict__ psi, const uint8_t* __restrict__ halo,
+__global__ void k_sgs_halo_products(const T* __restrict__ psi, const int* __restrict__ hlist,
                                     T* __restrict__ t2, T* __restrict__ t3, Geom g, T c1, T c2, T csh2) {
     pdl_wait();
-    const long long N = (long long)g.NJ * g.NJ;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        if (!halo[p]) continue;
-        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+    const int nh = hlist[0];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nh; e += gridDim.x * blockDim.x) {
+        const int p = hlist[1 + e];
+        const int i = p & g.mask, k = p >> g.L;
         const T up1 = dy1(psi, i + 1, k, g, c1), um1 = dy1(psi, i - 1, k, g, c1);
         const T up2 = dy1(psi, i + 2, k, g, c1), um2 = dy1(psi, i - 2, k, g, c1);
         const T s11 = (T(8) * (up1 - um1) - (up2 - um2)) * c1;
@@ -283,13 +291,16 @@ void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* 
 
 template <typename T>
 void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t2, T* t3, uint8_t* halo,
-                     const Geom& g, cudaStream_t s, const int* dn) {
+                     int* hlist, const Geom& g, cudaStream_t s, const int* dn) {
     const long long N = (long long)g.NJ * g.NJ;
     const T c1 = T(1.0 / (12.0 * g.h)), c2 = T(1.0 / (12.0 * g.h * g.h));
     const T csh2 = T((cs * g.h) * (cs * g.h));
     cudaMemsetAsync(halo, 0, (size_t)N, s);
-    if (n > 0) { launch_pdl(k_sgs_halo_mark, blocks_for(n), kThreads, 0, s, meta, n, halo, g, dn); note_launch(); }
-    { launch_pdl(k_sgs_halo_products<T>, blocks_for(N), kThreads, 0, s, psi, halo, t2, t3, g, c1, c2, csh2); note_launch(); }
+    cudaMemsetAsync(hlist, 0, sizeof(int), s);
+    if (n > 0) { launch_pdl(k_sgs_halo_mark, blocks_for(n), kThreads, 0, s, meta, n, halo, hlist, g, dn); note_launch(); }
+    // grid-stride over the halo count on the device (capturable); 8 blocks per SM of 152
+    { launch_pdl(k_sgs_halo_products<T>, (int)std::min<long long>(blocks_for(N), 1216), kThreads, 0, s, psi,
+                 (const int*)hlist, t2, t3, g, c1, c2, csh2); note_launch(); }
     if (n > 0) { launch_pdl(k_sgs_halo_forcing<T>, blocks_for(n), kThreads, 0, s, t2, t3, meta, n, ga, g, c1, c2, dn); note_launch(); }
 }
 
@@ -363,7 +374,7 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
     template void launch_velocity_active<T>(const T*, const uint32_t*, long long, T*, T*, const Geom&,      \
                                             cudaStream_t, const int*);                                      \
     template void launch_sgs_halo<T>(const T*, const uint32_t*, long long, double, T*, T*, T*, uint8_t*,    \
-                                     const Geom&, cudaStream_t, const int*);                                \
+                                     int*, const Geom&, cudaStream_t, const int*);                          \
     template void launch_velocity_gather<T>(const T*, const T*, const uint32_t*, long long, T*, T*,         \
                                             cudaStream_t, const int*);                                      \
     template void launch_sgs_from_strain<T>(const T*, const T*, const uint32_t*, long long, double, T*, T*, \

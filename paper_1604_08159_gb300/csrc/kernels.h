@@ -71,10 +71,11 @@ void launch_velocity_active(const T* psi, const uint32_t* meta, long long n, T* 
                             const Geom& g, cudaStream_t s, const int* dn = nullptr);
 // Smagorinsky forcing at the active points from the lattice psi, with the
 // products nu_t S formed only in the 5 x 5 boxes around the active points
-// (halo: an NJ*NJ byte mask; t2, t3: lattice work arrays).
+// (halo: an NJ*NJ byte mask, 4-byte aligned; hlist: NJ*NJ + 1 ints of work
+// space for the halo list; t2, t3: lattice work arrays).
 template <typename T>
 void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs, T* ga, T* t2, T* t3,
-                     uint8_t* halo, const Geom& g, cudaStream_t s, const int* dn = nullptr);
+                     uint8_t* halo, int* hlist, const Geom& g, cudaStream_t s, const int* dn = nullptr);
 // Smagorinsky forcing from the lattice strain (S11, S12): nu_t, then
 // a = 2 nu_t S12 and c = nu_t S11 into ta, tc, D_y c into tdyc, g at the active points.
 template <typename T>
