@@ -46,8 +46,9 @@ __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 
-// Loads of data that other blocks of the same kernel may have written go
-// through L2 only (L1 is not coherent across SMs).
+// CG = true: an L2-only load (L1 is not coherent across SMs), for data that
+// other blocks of a running kernel may write without an acquire ordering it;
+// the Krylov kernel uses plain loads, ordered by its grid barrier's acquire.
 template <typename T, bool CG>
 __device__ __forceinline__ T ldv(const T* p) {
     if constexpr (CG) return __ldcg(p);
