@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -116,54 +117,86 @@ def time_oracle(wl, nsteps: int, warmup: int = 0):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons, each stamped with
+    the host time it arrived; the summary keeps the samples that fall inside
+    the marked region (the timed steps)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
+        self.lines = []            # (host time, csv line)
+        self.region = None
+        self._first = threading.Event()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
+            self._first.set()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        self._first.wait(timeout=5.0)      # sampling is running before the region starts
         return self
 
+    def mark(self, t0: float, t1: float):
+        self.region = (t0, t1)
+
     def __exit__(self, *exc):
-        self.out = ""
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                self.out, _ = self.proc.communicate()
+        if self.proc is None:
+            return
+        time.sleep(2e-3 * self.PERIOD_MS)  # one more period, so the region's end is covered
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.proc.wait()
+        self.reader.join(timeout=5)
 
     def summary(self):
-        sms, mx, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in (self.out or "").splitlines():
+        rows = []
+        for t, line in self.lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sms.append(float(f[1]))
-                mx = float(f[2])
+                rows.append((t, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for name, val in zip(names, f[5:9]):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        window = "timed region"
+        if self.region is not None:
+            t0, t1 = self.region
+            # a sample reports the period that ends when it arrives
+            sel = [r for r in rows if t0 < r[0] <= t1 + 1e-3 * self.PERIOD_MS]
+            if not sel:
+                sel = [min(rows, key=lambda r: abs(r[0] - t1))]
+                window = "nearest sample to the timed region's end"
+        else:
+            sel, window = rows, "whole run"
+        reasons = set()
+        for r in sel:
+            for name, val in zip(names, r[3]):
                 if val.lower() == "active":
                     reasons.add(name)
-        if not sms:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sms)}
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": sel[-1][2],
+                "reasons": sorted(reasons), "samples": len(sel), "period_ms": self.PERIOD_MS,
+                "window": window}
 
 
 def hbm_peak():
@@ -386,6 +419,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     run = B.Run(p, stream=stream.cuda_stream)
     run.init_vortices(wl.vortices)
+    sampler = ClockSampler(local)
+    sampler.__enter__()                  # sampling runs from the warm-up on
     run.step(args.warmup)
     run.sync()
 
@@ -397,8 +432,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    with sampler:
+    try:
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for q in range(args.steps):
@@ -408,7 +442,11 @@ def run_ours(args):
                 run.step(1)
                 ends[q].record(stream)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        wall = t1 - t0
+        sampler.mark(t0, t1)
+    finally:
+        sampler.__exit__(None, None, None)
     launches = run.stats()["launches"] - l0      # library kernels only (the flush is torch's)
     run.sync()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -516,7 +554,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-steps", type=int, default=2)
