@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -197,6 +198,55 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": sel[-1][2],
                 "reasons": sorted(reasons), "samples": len(sel), "period_ms": self.PERIOD_MS,
                 "window": window}
+
+
+# Algorithmic cost per step of the stages that have a simple model (bulk word
+# size es; N = NJ^2 lattice points, na active points):
+#   reconstruct  two inverse transforms per step, each writing every lattice
+#                value and reading it and the mask once: 2 (2 es + 1) N bytes
+#   poisson      two real 2-D FFTs of N points (forward, inverse) at the usual
+#                2.5 N log2 N flops each: 5 N log2 N FP64 flops
+#   velocity     meta, one psi word and U, V per active point: (4 + 3 es) na bytes
+#   krylov       the Krylov launch's own model (wrc_query_profile)
+#   adapt        the lattice masks read and written once each (significance,
+#                next grid, ghosts, stencil levels, compaction keys), the
+#                lattice-to-index map, and the new compact arrays:
+#                13 N + (4 + es) na bytes
+# The subgrid forcing and the host gap are reported by time only.
+STAGE_BOUND = {"reconstruct": "hbm", "poisson": "alu", "velocity": "hbm", "sgs": "alu (FP64 over the halo list)",
+               "krylov": "alu", "adapt": "hbm (small launches: latency)", "host": "host synchronisation"}
+
+
+def stage_report(sms, nsteps, p, na, hbm_gbs):
+    N = float(p.NJ) ** 2
+    es = 4.0 if p.prec == W.PREC_MIXED else 8.0
+    per = {k: v / max(1, nsteps) for k, v in sms.items()}
+    total = sum(per.values())
+    k = p.m
+    krylov_flops = na * (30.0 * (k + 1) + 3.0 * k + sum(8.0 * (j + 1) + 4.0 for j in range(k)))
+    model = {"reconstruct": ("bytes", 2.0 * (2.0 * es + 1.0) * N),
+             "poisson": ("flops", 5.0 * N * math.log2(N)) if es == 8.0 else None,
+             "velocity": ("bytes", (4.0 + 3.0 * es) * na),
+             "krylov": ("flops", krylov_flops) if es == 8.0 else None,
+             "adapt": ("bytes", 13.0 * N + (4.0 + es) * na)}
+    out = {"steps": nsteps, "mean_active_points": na, "launch": "direct (graphs off while stages are timed)",
+           "step_ms": total}
+    for name in sms:   # the library's stage order
+        ms = per.get(name, 0.0)
+        row = {"ms_per_step": ms, "share": ms / total if total > 0 else 0.0, "bound": STAGE_BOUND[name]}
+        m = model.get(name)
+        if m is not None and ms > 0:
+            kind, amount = m
+            if kind == "bytes":
+                a = amount / (ms * 1e-3) / 1e9
+                row.update({"algorithmic_bytes": amount, "achieved": a, "unit": "GB/s", "peak": hbm_gbs,
+                            "frac": a / hbm_gbs})
+            else:
+                a = amount / (ms * 1e-3) / 1e9
+                row.update({"algorithmic_flops": amount, "achieved": a, "unit": "GFLOP/s",
+                            "peak": FP64_PEAK_GFLOPS, "frac": a / FP64_PEAK_GFLOPS})
+        out[name] = row
+    return out
 
 
 def hbm_peak():
@@ -464,6 +514,19 @@ def run_ours(args):
     achieved_gbs = rec["bytes"] / sec / 1e9 if sec > 0 else 0.0
     achieved_gflops = rec["flops"] / sec / 1e9 if sec > 0 else 0.0
 
+    # every stage of the step, timed by the library's stage events in a
+    # window of direct-launched steps (graphs are off while stages are timed)
+    stages = None
+    if not args.no_stages:
+        run.profile(3)
+        sa = 0
+        for _ in range(prof_steps):
+            sa += run.stats()["n_active"]
+            run.step(1)
+        nst, sms = run.stages()
+        run.profile(False)
+        stages = stage_report(sms, nst, p, sa / max(1, nst), peak)
+
     # end to end through the C-ABI with host buffers (pinned), a fresh run
     e2e = None
     if not args.no_e2e:
@@ -542,6 +605,7 @@ def run_ours(args):
             "serving": serving,
             "ensemble": ensemble,
             "scalar": scalar,
+            "stages": stages,
         }
         print(json.dumps(line), flush=True)
     run.close()
@@ -564,6 +628,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
+    ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=5)
     ap.add_argument("--ens-solo-sample", type=int, default=32)

@@ -186,9 +186,44 @@ wrc_status wrc_query_stats(wrc_run* run, int64_t out[4]);
  * kernel, phi_1 and the update): when enabled, each step's Krylov launches
  * are bracketed by CUDA events on the run's stream; enabling or disabling
  * clears the record.  enable = 2 also traces the phases of the cooperative
- * kernel (wrc_query_phase_trace); 0 disables, 1 times only.  WRC_ERR_ARG for
- * other values. */
+ * kernel (wrc_query_phase_trace); 0 disables, 1 times only.  enable = 3
+ * times the stages of each step instead (wrc_query_stages): an event at each
+ * stage boundary, with the step's phases launched directly rather than
+ * replayed as CUDA graphs while it is on.  WRC_ERR_ARG for other values.
+ * Synchronises. */
 wrc_status wrc_profile(wrc_run* run, int32_t enable);
+
+/* Stages of a step timed by wrc_profile(run, 3), in the order a step runs
+ * them (the reconstruction twice: R(omega) before the Poisson solve, and the
+ * new omega's before thresholding; the adaptation in two parts around the
+ * host's read of the new grid's sizes):
+ *   RECONSTRUCT  inverse DD4 transform onto the finest lattice (Sec. 2.3)
+ *   POISSON      the FFT streamfunction solve (and, in the mixed mode, the
+ *                spectral velocity and strain)
+ *   VELOCITY     U, V at the active points
+ *   SGS          the Smagorinsky forcing (Eq. 5), empty without it
+ *   KRYLOV       the cooperative Arnoldi / phi_1 / update launch(es)
+ *   ADAPT        details, threshold, adjacent zone, closure, ghosts,
+ *                compaction, the new compact arrays and interpolation rows
+ *   HOST         from the end of the first adaptation part to the start of
+ *                the second: the host's wait for the new sizes and the
+ *                launch latency after it (no kernel of the step runs) */
+enum {
+    WRC_STAGE_RECONSTRUCT = 0,
+    WRC_STAGE_POISSON = 1,
+    WRC_STAGE_VELOCITY = 2,
+    WRC_STAGE_SGS = 3,
+    WRC_STAGE_KRYLOV = 4,
+    WRC_STAGE_ADAPT = 5,
+    WRC_STAGE_HOST = 6,
+    WRC_STAGE_COUNT = 7
+};
+
+/* Stage record since wrc_profile(run, 3): out[0] the steps timed, out[1 + s]
+ * the total device time of stage s over them in ms (CUDA events on the run's
+ * stream).  WRC_ERR_ARG if cap < 1 + WRC_STAGE_COUNT; WRC_ERR_STATE when
+ * stage timing is off.  Synchronises. */
+wrc_status wrc_query_stages(wrc_run* run, double* out, int32_t cap);
 
 /* Phase trace of the last cooperative Krylov launch of the run (profiling
  * mode 2): for each grid barrier p it passed, out[4p..4p+3] = the first and

@@ -22,6 +22,8 @@ STATUS = {0: "WRC_OK", -1: "WRC_ERR_ARG", -2: "WRC_ERR_OOM", -3: "WRC_ERR_CUDA",
           -4: "WRC_ERR_BREAKDOWN_NAN", -5: "WRC_ERR_TIMEOUT", -6: "WRC_ERR_BUSY", -7: "WRC_ERR_STATE"}
 FIELD_OMEGA, FIELD_PSI, FIELD_U, FIELD_V, FIELD_NUT = range(5)
 MAX_M = 31
+# stages of a step timed by wrc_profile(run, 3), in the order of the WRC_STAGE_* values
+STAGES = ("reconstruct", "poisson", "velocity", "sgs", "krylov", "adapt", "host")
 
 
 class WrcConfig(ctypes.Structure):
@@ -68,6 +70,7 @@ SIGNATURES = {
     "wrc_query_stats": (c_int32, [c_void_p, c_void_p]),
     "wrc_profile": (c_int32, [c_void_p, c_int32]),
     "wrc_query_profile": (c_int32, [c_void_p, c_void_p]),
+    "wrc_query_stages": (c_int32, [c_void_p, c_void_p, c_int32]),
     "wrc_query_phase_trace": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "wrc_last_error": (ctypes.c_char_p, [c_void_p]),
     "wrc_destroy": (None, [c_void_p]),
@@ -272,8 +275,16 @@ def wrc_query_stats(run):
 
 
 def wrc_profile(run, enable):
-    """enable: False/0 off, True/1 event timing, 2 timing and phase trace."""
+    """enable: False/0 off, True/1 event timing of the Krylov launches, 2 that
+    and the phase trace, 3 stage timing (wrc_query_stages)."""
     _check("wrc_profile", load().wrc_profile(run, int(enable)), run)
+
+
+def wrc_query_stages(run):
+    """Steps timed and the total ms of each stage since wrc_profile(run, 3)."""
+    out = np.zeros(1 + len(STAGES))
+    _check("wrc_query_stages", load().wrc_query_stages(run, out.ctypes.data, out.size), run)
+    return int(out[0]), dict(zip(STAGES, out[1:].tolist()))
 
 
 def wrc_query_profile(run):
@@ -418,6 +429,9 @@ class Run:
 
     def profile_record(self):
         return wrc_query_profile(self.h)
+
+    def stages(self):
+        return wrc_query_stages(self.h)
 
     def phase_trace(self):
         return wrc_query_phase_trace(self.h)

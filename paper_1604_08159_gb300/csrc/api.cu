@@ -152,6 +152,15 @@ struct wrc_run {
     bool use_graphs = false;
     struct ProfRec { int ev; double bytes, flops; };
     std::vector<ProfRec> ev_used;   // start-event index, algorithmic bytes and flops per launch
+    // stage timing (wrc_profile mode 3): an event at each stage boundary of a
+    // step, st_ids[i] the stage that starts at event i (kStageEnd closes the
+    // step); folded into st_ms at the end of a step once many are pending
+    bool stage_timing = false;
+    bool in_step = false;
+    std::vector<cudaEvent_t> st_pool;
+    std::vector<int> st_ids;
+    double st_ms[WRC_STAGE_COUNT] = {0};
+    long long st_steps = 0;
     long long host_syncs = 0;
 
     // state
@@ -343,7 +352,7 @@ void rebuild_commit(wrc_run* R) {
 // the launches directly.
 template <typename F>
 wrc_status run_phase(wrc_run* R, int phase, F&& body) {
-    if (!R->use_graphs) return body();
+    if (!R->use_graphs || R->stage_timing) return body();
     auto& G = R->graphs[phase][R->cur];
     if (!G.exec || G.layout != R->layout) {
         if (G.exec) {
@@ -377,6 +386,44 @@ wrc_status run_phase(wrc_run* R, int phase, F&& body) {
     }
     CK(cudaGraphLaunch(G.exec, R->st));
     g_launches.fetch_add(G.kernels, std::memory_order_relaxed);
+    return WRC_OK;
+}
+
+constexpr int kStageEnd = WRC_STAGE_COUNT;
+
+// Stage timing: record the start of stage `id` (kStageEnd: the step's end) on
+// the run's stream.  A no-op unless wrc_profile mode 3 is on and a step is
+// being taken (the step's phases then run as direct launches).
+wrc_status stage_mark(wrc_run* R, int id) {
+    if (!R->stage_timing || !R->in_step) return WRC_OK;
+    const size_t i = R->st_ids.size();
+    while (R->st_pool.size() <= i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        R->st_pool.push_back(e);
+    }
+    CK(cudaEventRecord(R->st_pool[i], R->st));
+    R->st_ids.push_back(id);
+    return WRC_OK;
+}
+
+// Add the recorded intervals to the per-stage totals (synchronises): the
+// interval from event i to event i + 1 belongs to stage st_ids[i], except
+// after a step's end.
+wrc_status stage_fold(wrc_run* R) {
+    if (R->st_ids.empty()) return WRC_OK;
+    CK(cudaStreamSynchronize(R->st));
+    for (size_t i = 0; i < R->st_ids.size(); ++i) {
+        if (R->st_ids[i] == kStageEnd) {
+            R->st_steps += 1;
+            continue;
+        }
+        if (i + 1 == R->st_ids.size()) break;
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, R->st_pool[i], R->st_pool[i + 1]));
+        R->st_ms[R->st_ids[i]] += t;
+    }
+    R->st_ids.clear();
     return WRC_OK;
 }
 
@@ -446,9 +493,11 @@ wrc_status reconstruct_scalar(wrc_run* R) {
 // (and R(r_v) when the passive scalar is on).
 template <typename T>
 wrc_status freeze(wrc_run* R) {
+    TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
     TRY(reconstruct<T>(R));
     CKL("freeze/reconstruct");
     if (R->scalar) TRY(reconstruct_scalar<T>(R));
+    TRY(stage_mark(R, WRC_STAGE_POISSON));
     const cudaStream_t s = R->st;
     const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
     T* t0 = (T*)R->C1;
@@ -467,8 +516,10 @@ wrc_status freeze(wrc_run* R) {
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, (T*)R->Lq, t0, scr,
                           dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr);
         CKL("freeze/poisson");
+        TRY(stage_mark(R, WRC_STAGE_VELOCITY));
         launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), s, R->counts_dev);
         CKL("freeze/velocity");
+        TRY(stage_mark(R, WRC_STAGE_SGS));
         if (dyn)
             launch_sgs_from_strain<T>(S11, S12, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s,
                                       R->counts_dev);
@@ -477,9 +528,11 @@ wrc_status freeze(wrc_run* R) {
         return WRC_OK;
     } else {
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s);
+        TRY(stage_mark(R, WRC_STAGE_VELOCITY));
         launch_velocity_active<T>((const T*)R->psi, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), R->g, s,
                                   R->counts_dev);
     }
+    TRY(stage_mark(R, WRC_STAGE_SGS));
     if (R->cfg.sgs == WRC_SGS_DYNAMIC)
         // t0, t1 (the first work array, free after the Poisson solve here) hold the halo list
         launch_sgs_halo<T>((const T*)R->psi, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t2, t3, R->halo, (int*)t0, R->g,
@@ -625,22 +678,42 @@ enum { kPhaseFreeze = 0, kPhaseAdapt1 = 1, kPhaseAdapt2 = 2 };
 // One time step: [freeze] -> Krylov launch -> [adapt part 1] -> host sync for
 // the new grid's sizes -> [adapt part 2]; bracketed phases run as CUDA graphs.
 template <typename T>
-wrc_status step_once(wrc_run* R) {
-    const long long na0 = R->n_active;
+wrc_status step_phases(wrc_run* R) {
     TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
     R->frozen = true;
+    TRY(stage_mark(R, WRC_STAGE_KRYLOV));
     TRY(krylov<T>(R));
     TRY(run_phase(R, kPhaseAdapt1, [&] {
         // L holds omega^{n+1} at the grid points; reconstruct the rest, threshold
+        TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
         for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
         if (R->scalar)   // Lr holds r_v^{n+1} at the grid points
             for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>(R->Lr.as<T>(), R->act, j, R->g, R->st);
+        TRY(stage_mark(R, WRC_STAGE_ADAPT));
         return threshold_body<T>(R, R->cfg.eps, false);
     }));
     R->det_count = R->n_active;
+    TRY(stage_mark(R, WRC_STAGE_HOST));
     TRY(rebuild_host(R));
+    TRY(stage_mark(R, WRC_STAGE_ADAPT));
     TRY(run_phase(R, kPhaseAdapt2, [&] { return rebuild_part2<T>(R); }));
+    TRY(stage_mark(R, kStageEnd));
     rebuild_commit(R);
+    return WRC_OK;
+}
+
+template <typename T>
+wrc_status step_once(wrc_run* R) {
+    const long long na0 = R->n_active;
+    const size_t m0 = R->st_ids.size();
+    R->in_step = true;
+    const wrc_status st = step_phases<T>(R);
+    R->in_step = false;
+    if (st != WRC_OK) {
+        R->st_ids.resize(m0);   // a step that failed leaves no stage intervals
+        return st;
+    }
+    if (R->st_ids.size() >= 1024) TRY(stage_fold(R));
     R->t += R->cfg.dt;
     R->nstep += 1;
     R->updates += (double)na0;
@@ -849,6 +922,7 @@ void free_run(wrc_run* R) {
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
     for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : R->st_pool) cudaEventDestroy(e);
     for (auto& ph : R->graphs)
         for (auto& G : ph)
             if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -1219,10 +1293,14 @@ wrc_status wrc_query_stats(wrc_run* R, int64_t out[4]) {
 
 wrc_status wrc_profile(wrc_run* R, int32_t enable) {
     if (!R) return WRC_ERR_ARG;
-    if (enable < 0 || enable > 2) return fail(R, WRC_ERR_ARG, "enable must be 0, 1 or 2");
+    if (enable < 0 || enable > 3) return fail(R, WRC_ERR_ARG, "enable must be 0, 1, 2 or 3");
     CK(cudaStreamSynchronize(R->st));
-    R->profiling = enable != 0;
+    R->profiling = enable == 1 || enable == 2;
     R->tracing = enable == 2;
+    R->stage_timing = enable == 3;
+    R->st_ids.clear();
+    std::fill(R->st_ms, R->st_ms + WRC_STAGE_COUNT, 0.0);
+    R->st_steps = 0;
     if (R->tracing) {
         const size_t words = 1 + (size_t)kTracePhases * (kMaxBlocks + 1);
         CK(R->trace.grow(sizeof(unsigned long long) * words, 0, R->st));
@@ -1260,6 +1338,16 @@ wrc_status wrc_query_phase_trace(wrc_run* R, double* out, int32_t cap, int32_t* 
         np = p + 1;
     }
     *nphases = np;
+    return WRC_OK;
+}
+
+wrc_status wrc_query_stages(wrc_run* R, double* out, int32_t cap) {
+    if (!R || !out) return WRC_ERR_ARG;
+    if (cap < 1 + WRC_STAGE_COUNT) return fail(R, WRC_ERR_ARG, "cap must be at least 1 + WRC_STAGE_COUNT");
+    if (!R->stage_timing) return fail(R, WRC_ERR_STATE, "stage timing is off (wrc_profile(run, 3))");
+    TRY(stage_fold(R));
+    out[0] = (double)R->st_steps;
+    for (int s = 0; s < WRC_STAGE_COUNT; ++s) out[1 + s] = R->st_ms[s];
     return WRC_OK;
 }
 
