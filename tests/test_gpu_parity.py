@@ -103,12 +103,15 @@ def test_init_vortices_matches_oracle_ic():
     with B.Run(p) as run:
         run.init_vortices(v)
         idx, om = run.active()
-        # both sides sample exp(); a detail within rounding of eps could flip a point
+        # both sides sample exp(), which may differ in the last bit; the
+        # inputs are chosen so that no detail lies within rounding of eps
+        # (otherwise a point could flip), and the test says so if they stop
+        # being so rather than passing without an assertion
         d = np.abs(O.details(O.vortex_field(cfg.NJ, v.xc, v.yc, v.gamma, v.s), np.ones_like(st.active), cfg.J))
         near = np.abs(d - cfg.eps) < 1e-12 * cfg.eps
-        if not near.any():
-            assert np.array_equal(idx, np.flatnonzero(st.active.ravel()))
-            assert rel_l2(om, st.omega[st.active]) <= 1e-14
+        assert not near.any(), "a detail of the initial field lies within rounding of eps"
+        assert np.array_equal(idx, np.flatnonzero(st.active.ravel()))
+        assert rel_l2(om, st.omega[st.active]) <= 1e-14
 
 
 def test_set_grid_validates_closure():
