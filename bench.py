@@ -265,11 +265,15 @@ def hbm_peak():
 
 
 def measure_serving(args):
-    """Replay a bounded sample of the serving trace (Poisson arrivals at
-    50/s of 2-3 vortex runs, finest 128^2-4096^2, mixed precision) through
-    the request server twice: continuous batching, and the plain per-run form
-    (FIFO, one run at a time, each run in FP64).  Time-to-result is measured
-    by the server from each request's arrival to its result on the host."""
+    """Replay a sample of the serving trace (Poisson arrivals at 50/s of 2-3
+    vortex runs, finest 128^2-4096^2) through the request server four times,
+    so that batching and precision are measured apart: continuous batching in
+    the mixed mode (the trace's precision) and in FP64, and the plain per-run
+    form (FIFO, one run at a time) in both precisions.  Time-to-result is
+    measured by the server from each request's arrival to its result on the
+    host.  The mixed results' error is stated per request against the same
+    request's FP64 per-run result (relative L2 of omega over the points
+    active in both, and the count of points active in only one)."""
     import dataclasses
 
     from paper_1604_08159_gb300 import binding as B
@@ -277,17 +281,18 @@ def measure_serving(args):
     trace = W.serving_trace()[:args.serve_requests]
     scale = args.serve_step_scale
 
-    def replay(policy, fp64):
+    def replay(policy, fp64, keep):
         with B.Server(policy=policy, max_slots=256, hbm_budget_bytes=150e9) as srv:
             t0 = srv.stats()["clock_s"] + 0.05
             ids = []
             for t, p, v, ns in trace:
-                if fp64:
-                    p = dataclasses.replace(p, prec=W.PREC_FP64)
+                p = dataclasses.replace(p, prec=W.PREC_FP64 if fp64 else W.PREC_MIXED)
                 ids.append(srv.submit(p, v, max(1, int(round(ns * scale))), t0 + t))
-            srv.wait(timeout_s=1800)
+            srv.wait(timeout_s=3600)
             infos = [srv.query(i) for i in ids]
             st = srv.stats()
+            results = [srv.result(i) if (keep and info.state == B.REQ_DONE) else None
+                       for i, info in zip(ids, infos)]
         done = [i for i in infos if i.state == B.REQ_DONE]
         lat = np.array([i.t_done - i.t_arrival for i in done]) if done else np.zeros(1)
         upd = sum(i.updates for i in done)
@@ -296,66 +301,143 @@ def measure_serving(args):
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "throughput": upd / span if span > 0 else 0.0, "unit": UNIT,
                 "requests_per_s": len(done) / span if span > 0 else 0.0, "makespan_s": span,
-                "peak_resident": int(st["peak_resident"]), "peak_hbm_gb": st["peak_charged_bytes"] / 1e9}
+                "peak_resident": int(st["peak_resident"]), "peak_hbm_gb": st["peak_charged_bytes"] / 1e9}, results
 
-    batched = replay(B.SERVE_BATCHED, fp64=False)
-    fifo = replay(B.SERVE_FIFO, fp64=True)
+    batched, res_bm = replay(B.SERVE_BATCHED, fp64=False, keep=True)
+    batched64, res_b64 = replay(B.SERVE_BATCHED, fp64=True, keep=True)
+    fifo_mixed, _ = replay(B.SERVE_FIFO, fp64=False, keep=False)
+    fifo, res_f64 = replay(B.SERVE_FIFO, fp64=True, keep=True)
+
+    def errors(res):
+        rel, flips = [], []
+        for a, b in zip(res, res_f64):
+            if a is None or b is None:
+                continue
+            r, f = compare_results(a[0], a[1], b[0], b[1])
+            rel.append(r)
+            flips.append(f / max(1, b[0].size))
+        if not rel:
+            return None
+        return {"requests": len(rel), "rel_l2_max": float(np.max(rel)), "rel_l2_median": float(np.median(rel)),
+                "grid_diff_frac_max": float(np.max(flips)), "per_request_rel_l2": [float(x) for x in rel]}
+
     sizes = sorted({p.NJ for _, p, _, _ in trace})
+    ratio = lambda a, b: a["throughput"] / b["throughput"] if b["throughput"] > 0 else None
     return {"sample": f"first {len(trace)} requests of the 50 req/s serving trace (seed 5), each run's step "
                       f"count scaled by {scale} (full trace: 200-2000 steps); lattices {sizes}",
-            "batched_mixed": batched, "fifo_fp64": fifo,
-            "throughput_ratio": batched["throughput"] / fifo["throughput"] if fifo["throughput"] > 0 else None,
-            "accuracy": "mixed results within 1e-6 relative L2 of FP64 (parity tests)"}
+            "batched_mixed": batched, "batched_fp64": batched64, "fifo_mixed": fifo_mixed, "fifo_fp64": fifo,
+            "throughput_ratio": ratio(batched, fifo),
+            "batching_gain_fp64": ratio(batched64, fifo), "batching_gain_mixed": ratio(batched, fifo_mixed),
+            "precision_gain_batched": ratio(batched, batched64),
+            "error_vs_fifo_fp64": {"batched_mixed": errors(res_bm), "batched_fp64": errors(res_b64),
+                                   "measure": "relative L2 of omega over points active in both results; "
+                                              "grid differences as a fraction of the FP64 active count"}}
 
 
 def measure_ensemble(args):
-    """The uneven ensemble (256 two-vortex members, finest 256^2-2048^2,
-    mixed precision) advanced together -- one cooperative Krylov launch per
-    step for all members, graph-replayed phases, autotuned block shape --
-    against the plain per-run form (each member alone, FP64, on a sample of
-    the members)."""
+    """The uneven ensemble (256 two-vortex members, finest 256^2-2048^2)
+    advanced together -- one cooperative Krylov launch per step for all
+    members, graph-replayed phases, autotuned block shape -- in the mixed
+    mode and in FP64, against the plain per-run form (each member alone) in
+    both precisions on a sample of the members, so that batching and
+    precision are measured apart.  The batched Krylov launches are timed
+    with events and set against the algorithmic bytes of the members' Krylov
+    steps (the HBM fraction of the batched launch, whose working set exceeds
+    L2).  Each mixed member's error is stated against its own FP64 batched
+    result after the same steps."""
+    import dataclasses
+
     import torch
 
     from paper_1604_08159_gb300 import binding as B
 
-    members = W.ensemble_members(n=args.ens_members)
-    stream = torch.cuda.Stream()
-    with B.Ensemble([p for p, _ in members], stream=stream.cuda_stream) as ens:
-        for m, (_, v) in zip(ens.members, members):
-            m.init_vortices(v)
-        ens.step(2)
-        shape = ens.tune(1)
-        ens.step(1)
-        torch.cuda.synchronize()
-        upd = 0
-        t0 = time.perf_counter()
-        for _ in range(args.ens_steps):
-            upd += ens.stats()["n_active"]
+    peak, peak_src = hbm_peak()
+    nsteps = args.ens_steps
+
+    # every arm ends at the same step count (the tuner advances the members
+    # by one step per shape it times: at most 9), so that the members' final
+    # states can be compared
+    final_steps = 2 + 9 + 1 + nsteps
+
+    def batched(prec):
+        members = W.ensemble_members(n=args.ens_members, prec=prec)
+        stream = torch.cuda.Stream()
+        with B.Ensemble([p for p, _ in members], stream=stream.cuda_stream) as ens:
+            for m, (_, v) in zip(ens.members, members):
+                m.init_vortices(v)
+            ens.step(2)
+            shape = ens.tune(1)
             ens.step(1)
-        ens.sync()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    batched = upd / wall
-    import dataclasses
-    sample = members[:args.ens_solo_sample]
-    s_upd, s_wall = 0, 0.0
-    for p, v in sample:
-        with B.Run(dataclasses.replace(p, prec=W.PREC_FP64), stream=stream.cuda_stream) as run:
-            run.init_vortices(v)
-            run.step(2)
-            run.sync()
-            t1 = time.perf_counter()
-            for _ in range(args.ens_steps):
-                s_upd += run.stats()["n_active"]
-                run.step(1)
-            run.sync()
-            s_wall += time.perf_counter() - t1
-    solo = s_upd / s_wall if s_wall > 0 else 0.0
-    return {"members": len(members), "steps": args.ens_steps, "block_shape": list(shape),
-            "batched_mixed": batched, "per_run_fp64": solo, "unit": UNIT,
-            "ms_per_ensemble_step": 1e3 * wall / args.ens_steps,
-            "per_run_sample": f"first {len(sample)} members, each alone in FP64, {args.ens_steps} steps",
-            "throughput_ratio": batched / solo if solo > 0 else None}
+            ens.sync()
+            torch.cuda.synchronize()
+            ens.profile(True)
+            ens.profile(True)                  # clears the record: only the timed steps count
+            upd = 0
+            t0 = time.perf_counter()
+            for _ in range(nsteps):
+                upd += ens.stats()["n_active"]
+                ens.step(1)
+            ens.sync()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            kms = ens.profile(False)
+            rest = final_steps - ens.stats()["steps"]
+            if rest > 0:
+                ens.step(rest)
+            ens.sync()
+            finals = [m.active() for m in ens.members]
+        es = 4.0 if prec == W.PREC_MIXED else 8.0
+        m = members[0][0].m
+        kbytes = krylov_bytes_per_update(m, es) * upd
+        kgbs = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+        return {"value": upd / wall, "unit": UNIT, "ms_per_ensemble_step": 1e3 * wall / nsteps,
+                "block_shape": list(shape), "mean_active_points_total": upd / nsteps,
+                "krylov_launch": {"bound": "hbm", "achieved": kgbs, "peak": peak, "unit": "GB/s",
+                                  "frac": kgbs / peak, "peak_source": peak_src,
+                                  "ms_per_step": kms / nsteps,
+                                  "algorithmic_bytes_per_update": krylov_bytes_per_update(m, es),
+                                  "working_set_bytes": (m + 1) * es * upd / nsteps}}, finals
+
+    def per_run(prec):
+        sample = W.ensemble_members(n=args.ens_members, prec=prec)[:args.ens_solo_sample]
+        stream = torch.cuda.Stream()
+        s_upd, s_wall = 0, 0.0
+        for p, v in sample:
+            with B.Run(p, stream=stream.cuda_stream) as run:
+                run.init_vortices(v)
+                run.step(2)
+                run.sync()
+                t1 = time.perf_counter()
+                for _ in range(nsteps):
+                    s_upd += run.stats()["n_active"]
+                    run.step(1)
+                run.sync()
+                s_wall += time.perf_counter() - t1
+        return s_upd / s_wall if s_wall > 0 else 0.0
+
+    bm, fin_m = batched(W.PREC_MIXED)
+    b64, fin_64 = batched(W.PREC_FP64)
+    rel, flips = [], []
+    for (ai, ao), (bi, bo) in zip(fin_m, fin_64):
+        r, f = compare_results(ai, ao, bi, bo)
+        rel.append(r)
+        flips.append(f / max(1, bi.size))
+    pm = per_run(W.PREC_MIXED)
+    p64 = per_run(W.PREC_FP64)
+    return {"members": args.ens_members, "steps": nsteps,
+            "batched_mixed": bm, "batched_fp64": b64,
+            "per_run_mixed": pm, "per_run_fp64": p64, "unit": UNIT,
+            "per_run_sample": f"first {args.ens_solo_sample} members, each alone, {nsteps} steps after 2",
+            "throughput_ratio": bm["value"] / p64 if p64 > 0 else None,
+            "batching_gain_fp64": b64["value"] / p64 if p64 > 0 else None,
+            "batching_gain_mixed": bm["value"] / pm if pm > 0 else None,
+            "precision_gain_batched": bm["value"] / b64["value"] if b64["value"] > 0 else None,
+            "mixed_error_vs_fp64": {"members": len(rel), "rel_l2_max": float(np.max(rel)),
+                                    "rel_l2_median": float(np.median(rel)),
+                                    "grid_diff_frac_max": float(np.max(flips)),
+                                    "per_member_rel_l2": [float(x) for x in rel],
+                                    "measure": f"each member after {final_steps} steps, mixed against FP64 "
+                                               "(both batched), over points active in both"}}
 
 
 def measure_scalar(args, wl):
@@ -401,26 +483,43 @@ def measure_scalar(args, wl):
 
 
 KRYLOV_SOURCES = ("csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh", "csrc/kernels.h")
+# DRAM bytes per launch of the Krylov kernel on the 1024^2 pair, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel sources whose SHA-256 is recorded with it; None until one is taken.
+KRYLOV_TRAFFIC = None   # {"sources_sha256": "...", "bytes_per_launch": N, "capture": "..."}
 
 
-def krylov_traffic(workload: str):
-    """DRAM bytes per launch of the Krylov kernel from the committed ncu
-    summary of this workload, or None if there is none or the kernel's
-    sources changed since the counters were taken."""
+def krylov_traffic():
+    """DRAM bytes per Krylov launch from the recorded ncu capture, or None if
+    there is none or the kernel's sources changed since it was taken."""
     import hashlib
-    import re
-    path = os.path.join(ROOT, "profiles", f"k_krylov_step_{workload}.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    m_b = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
-    m_h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
-    if not (m_b and m_h):
+    if not KRYLOV_TRAFFIC:
         return None
     h = hashlib.sha256()
     for f in KRYLOV_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1604_08159_gb300", f), "rb").read())
-    return int(m_b.group(1)) if h.hexdigest() == m_h.group(1) else None
+    return KRYLOV_TRAFFIC["bytes_per_launch"] if h.hexdigest() == KRYLOV_TRAFFIC["sources_sha256"] else None
+
+
+def krylov_bytes_per_update(m: int, es: float) -> float:
+    """Algorithmic bytes of the Krylov part per active-point update: m + 1
+    operator applications reading q, U, V and writing w (4 words each), at
+    Arnoldi step j a fused Gram-Schmidt pass reading j + 1 basis vectors and
+    w twice and writing w (2(j + 1) + 3 words), the combination reading m
+    vectors and omega and writing omega (m + 2 words): es (m^2 + 9m + 6)
+    bytes, with es the bulk word size (8 in FP64, 4 in the mixed mode)."""
+    return es * (m * m + 9.0 * m + 6.0)
+
+
+def compare_results(a_idx, a_om, b_idx, b_om):
+    """Relative L2 difference of omega over the lattice points active in
+    both results, and the number of points active in only one of them."""
+    common, ia, ib = np.intersect1d(a_idx, b_idx, assume_unique=True, return_indices=True)
+    x, y = a_om[ia], b_om[ib]
+    den = float(np.linalg.norm(y))
+    rel = float(np.linalg.norm(x - y) / den) if den > 0 else 0.0
+    flips = int(a_idx.size + b_idx.size - 2 * common.size)
+    return rel, flips
 
 
 def run_reference(args):
@@ -518,6 +617,7 @@ def run_ours(args):
     sec = rec["ms"] * 1e-3
     achieved_gbs = rec["bytes"] / sec / 1e9 if sec > 0 else 0.0
     achieved_gflops = rec["flops"] / sec / 1e9 if sec > 0 else 0.0
+    cluster = run.krylov_form()
 
     # every stage of the step, timed by the library's stage events in a
     # window of direct-launched steps (graphs are off while stages are timed)
@@ -531,6 +631,39 @@ def run_ours(args):
         nst, sms = run.stages()
         run.profile(False)
         stages = stage_report(sms, nst, p, sa / max(1, nst), peak)
+
+    # late window: the same run advanced further untimed (the vortices have
+    # merged further and the grid has grown), then timed as the main region
+    late = None
+    if args.late_steps > 0:
+        run.step(args.late_steps)
+        run.sync()
+        l_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        l_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        l_upd = 0
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for q in range(args.steps):
+                flush.zero_()
+                l_starts[q].record(stream)
+                l_upd += run.stats()["n_active"]
+                run.step(1)
+                l_ends[q].record(stream)
+        torch.cuda.synchronize()
+        l_ms = sum(a.elapsed_time(b) for a, b in zip(l_starts, l_ends))
+        run.profile(True)
+        run.step(prof_steps)
+        lrec = run.profile_record()
+        run.profile(False)
+        lsec = lrec["ms"] * 1e-3
+        lgbs = lrec["bytes"] / lsec / 1e9 if lsec > 0 else 0.0
+        na_late = l_upd / args.steps
+        late = {"after_steps": args.warmup + args.steps + 2 * prof_steps + args.late_steps,
+                "sim_time": run.diagnostics()["t"], "steps": args.steps, "value": l_upd / (l_ms * 1e-3),
+                "unit": UNIT, "ms_per_step": l_ms / args.steps, "mean_active_points": na_late,
+                "krylov_working_set_bytes": (p.m + 1) * 8.0 * na_late,
+                "roofline": {"bound": "hbm", "achieved": lgbs, "peak": peak, "unit": "GB/s", "frac": lgbs / peak,
+                             "avg_launch_us": 1e3 * lrec["ms"] / max(1, lrec["launches"])}}
 
     # end to end through the C-ABI with host buffers (pinned), a fresh run
     e2e = None
@@ -590,19 +723,21 @@ def run_ours(args):
                        "mean_active_points": upd / max(1, args.steps * ws),
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "wall_s": wall},
-            "roofline": {"bound": "alu", "kernel": "k_krylov_step (Arnoldi, phi_1 and the update: the Krylov part of a step)",
-                         "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                         "frac": achieved_gflops / FP64_PEAK_GFLOPS,
-                         "traffic": krylov_traffic("fujiwhara_1024" if args.workload == "fujiwhara_1024" else "-"),
-                         "traffic_unit": "DRAM bytes per launch (ncu; null once the kernel changed)",
-                         "traffic_source": "profiles/k_krylov_step_fujiwhara_1024.md: ncu capture of the "
-                                           "unclustered form (WRC_KRYLOV_CLUSTER=1), same sources and DRAM reads",
+            "roofline": {"bound": "hbm", "kernel": "k_krylov_step (Arnoldi, phi_1 and the update: the Krylov "
+                                                    "part of a step)",
+                         "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
+                         "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "traffic": krylov_traffic() if args.workload == "fujiwhara_1024" else None,
+                         "bytes_per_launch": rec["bytes"] / max(1, rec["launches"]),
+                         "bytes_model": "8 (m^2 + 9m + 6) bytes per active point (operator applications, fused "
+                                        "Gram-Schmidt passes, combination)",
                          "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(1, rec["launches"]),
-                         "flops_per_launch": rec["flops"] / max(1, rec["launches"]),
-                         "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                                 "frac": achieved_gbs / peak,
-                                 "bytes_per_launch": rec["bytes"] / max(1, rec["launches"])}},
+                         "cluster_size": cluster, "target_frac": 0.6,
+                         "fp64": {"achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                                  "frac": achieved_gflops / FP64_PEAK_GFLOPS,
+                                  "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; no measured FP64 peak)",
+                                  "flops_per_launch": rec["flops"] / max(1, rec["launches"])}},
+            "late": late,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -635,11 +770,16 @@ def main():
     ap.add_argument("--no-scalar", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
-    ap.add_argument("--ens-steps", type=int, default=5)
+    ap.add_argument("--ens-steps", type=int, default=50)
+    ap.add_argument("--late-steps", type=int, default=1000)
     ap.add_argument("--ens-solo-sample", type=int, default=32)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the whole serving trace (400 requests) at full step counts (takes many minutes)")
     args = ap.parse_args()
+    if args.serve_full:
+        args.serve_requests, args.serve_step_scale = 400, 1.0
     if args.warmup < 3 and args.impl == "ours":
         log("warm-up raised to 3 steps")
         args.warmup = 3

@@ -118,9 +118,32 @@ wrc_status wrc_threshold(wrc_run* run, double eps);
  * new grid's sizes. */
 wrc_status wrc_step(wrc_run* run, int32_t nsteps);
 
-/* Wait for the run's stream.  Returns WRC_ERR_BREAKDOWN_NAN if a step met a
+/* Wait for the run's stream: without a limit for timeout_ms < 0, else for at
+ * most timeout_ms milliseconds (0 polls once).  WRC_ERR_TIMEOUT if the
+ * queued work has not finished by then; it stays queued and a later call can
+ * wait for it again.  Returns WRC_ERR_BREAKDOWN_NAN if a step met a
  * non-finite Arnoldi coefficient since the last call. */
-wrc_status wrc_sync(wrc_run* run);
+wrc_status wrc_sync(wrc_run* run, int32_t timeout_ms);
+
+/* Bound of every device-side wait of the run's kernels (the grid barriers of
+ * the cooperative Krylov kernel), in seconds, 0 < seconds <= 60; default 2 s.
+ * A wait that runs out sets an error word and every block of the kernel
+ * returns; the step then fails with WRC_ERR_TIMEOUT and the run's state is
+ * undefined until a new initial condition (wrc_init_*, wrc_set_grid) or
+ * wrc_destroy.  WRC_ERR_ARG outside the range. */
+wrc_status wrc_set_wait_limit(wrc_run* run, double seconds);
+
+/* Thread-block cluster size (1, 2 or 4) of the run's next Krylov launch on
+ * its current grid.  Clusters of 2 or 4 blocks pre-add their dot sums in
+ * distributed shared memory; they are used when the device can hold the
+ * launch with them, the environment variable WRC_KRYLOV_CLUSTER (1 or 2,
+ * read at wrc_create) does not cap them, and the launch path forms them: a
+ * probe launch at the device's first wrc_create and the check of the
+ * device's first clustered launch (which, if its clusters were not formed,
+ * is issued again without them) switch them off for the device otherwise,
+ * e.g. under a profiler that replays cooperative launches without
+ * clusters. */
+wrc_status wrc_query_krylov_form(wrc_run* run, int32_t* cluster_size);
 
 /* Sizes of the current grid: active points, ghost points and active points
  * per level (per_level has J+1 entries; any pointer may be NULL). */
@@ -298,7 +321,8 @@ wrc_status wrc_query_scalar(wrc_run* run, int32_t* idx_out, double* r_out, int64
  * address, so make it before any stream capture.  All calls share the array:
  * calls that overlap on the GPU (different streams, or devices' views of one
  * call) race and give wrong sums; serialise them.  NJ must be a power of two,
- * 8 <= NJ <= WRC_MAX_NJ; otherwise WRC_ERR_ARG. */
+ * 8 <= NJ <= WRC_MAX_NJ, and cuda_stream must belong to the current device;
+ * otherwise WRC_ERR_ARG.  WRC_ERR_CUDA if a launch fails. */
 wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattice, const double* psi_lattice, int32_t NJ,
                                            double* out, void* cuda_stream);
 

@@ -54,7 +54,9 @@ SIGNATURES = {
     "wrc_set_grid": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
     "wrc_threshold": (c_int32, [c_void_p, c_double]),
     "wrc_step": (c_int32, [c_void_p, c_int32]),
-    "wrc_sync": (c_int32, [c_void_p]),
+    "wrc_sync": (c_int32, [c_void_p, c_int32]),
+    "wrc_set_wait_limit": (c_int32, [c_void_p, c_double]),
+    "wrc_query_krylov_form": (c_int32, [c_void_p, POINTER(c_int32)]),
     "wrc_query_counts": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "wrc_query_active": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_scalar_init": (c_int32, [c_void_p, c_double, c_void_p, c_int32]),
@@ -192,8 +194,19 @@ def wrc_step(run, nsteps: int = 1):
     _check("wrc_step", load().wrc_step(run, nsteps), run)
 
 
-def wrc_sync(run):
-    _check("wrc_sync", load().wrc_sync(run), run)
+def wrc_sync(run, timeout_ms=-1):
+    _check("wrc_sync", load().wrc_sync(run, int(timeout_ms)), run)
+
+
+def wrc_set_wait_limit(run, seconds):
+    _check("wrc_set_wait_limit", load().wrc_set_wait_limit(run, float(seconds)), run)
+
+
+def wrc_query_krylov_form(run):
+    """Thread-block cluster size (1, 2 or 4) of the run's next Krylov launch."""
+    cl = c_int32(0)
+    _check("wrc_query_krylov_form", load().wrc_query_krylov_form(run, byref(cl)), run)
+    return int(cl.value)
 
 
 def wrc_query_counts(run, J: int):
@@ -357,8 +370,14 @@ class Run:
     def step(self, n=1):
         wrc_step(self.h, n)
 
-    def sync(self):
-        wrc_sync(self.h)
+    def sync(self, timeout_ms=-1):
+        wrc_sync(self.h, timeout_ms)
+
+    def set_wait_limit(self, seconds):
+        wrc_set_wait_limit(self.h, seconds)
+
+    def krylov_form(self):
+        return wrc_query_krylov_form(self.h)
 
     def counts(self):
         return wrc_query_counts(self.h, self.J)

@@ -2,6 +2,8 @@
 // time step -- reconstruction, streamfunction, velocity and Smagorinsky
 // forcing, Krylov projection with the phi_1 update, grid adaptation.
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -172,6 +174,11 @@ struct wrc_run {
     double updates = 0.0;   // sum of the active count over the steps taken
     bool nonfinite = false; // a step met a non-finite Arnoldi coefficient (seen at its grid rebuild)
     bool init = false, frozen = false;
+    // bound of every device-side wait of the run's kernels (grid barriers of
+    // the Krylov kernel), wrc_set_wait_limit
+    unsigned long long wait_limit_ns = 2000000000ull;
+    int cluster_max = 4;   // largest thread-block cluster of the Krylov launch (WRC_KRYLOV_CLUSTER at creation)
+    cudaEvent_t sync_ev = nullptr;   // wrc_sync with a time limit
 
     // passive scalar (the vapour mixing ratio with diffusion only), enabled by
     // wrc_scalar_init: compact values on the grid, its reconstruction on the
@@ -304,7 +311,9 @@ wrc_status rebuild_host(wrc_run* R) {
             return fail(R, WRC_ERR_CUDA,
                         "the Krylov kernel was launched without its thread-block clusters (set WRC_KRYLOV_CLUSTER=1 "
                         "to use the unclustered kernel)");
-        return fail(R, WRC_ERR_TIMEOUT, "a grid barrier wait of the Krylov kernel ran out");
+        return fail(R, WRC_ERR_TIMEOUT,
+                    "a grid barrier wait of the Krylov kernel ran out; the run's state is undefined until it is "
+                    "re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
     }
     const long long na = R->counts_host[0];
     long long off = na, ng = 0;
@@ -610,7 +619,7 @@ KrylovStepArgs krylov_args(wrc_run* R) {
     A.m = m;
     A.dt = R->cfg.dt;
     A.tol = kBreakdownTol;
-    A.limit_ns = 2000000000ull;
+    A.limit_ns = R->wait_limit_ns;
     A.trace = R->tracing ? R->trace.as<unsigned long long>() : nullptr;
     return A;
 }
@@ -652,7 +661,7 @@ wrc_status krylov(wrc_run* R) {
     const long long n = R->n_active;
     const int m = R->cfg.krylov_m;
     const KrylovStepArgs A = krylov_args(R);
-    const int blocks = krylov_step_blocks(n, R->max_blocks, R->fp32);
+    const int blocks = krylov_step_blocks(n, R->max_blocks, R->fp32, R->device, R->cluster_max);
     TRY(trace_reset(R, blocks));
     int e0 = -1;
     if (R->profiling) {
@@ -664,12 +673,12 @@ wrc_status krylov(wrc_run* R) {
         e0 = (int)R->ev_used.size() * 2;
         CK(cudaEventRecord(R->ev_pool[e0], s));
     }
-    CK(launch_krylov_step<T>(A, blocks, s));
+    CK(launch_krylov_step<T>(A, blocks, s, R->device, R->cluster_max));
     if (R->profiling) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
         R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
     }
-    if (R->scalar) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s));
+    if (R->scalar) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s, R->device, R->cluster_max));
     return WRC_OK;
 }
 
@@ -865,7 +874,7 @@ template <typename T>
 wrc_status diagnostics_t(wrc_run* R) {
     TRY(reconstruct<T>(R));
     launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, R->st);
-    launch_diag<T>((const T*)R->L, (const T*)R->psi, R->K.part, R->K.counter, R->diag_dev, R->g, R->st);
+    CK(launch_diag<T>((const T*)R->L, (const T*)R->psi, R->K.part, R->K.counter, R->diag_dev, R->g, R->st));
     CKL("diagnostics");
     return WRC_OK;
 }
@@ -922,6 +931,7 @@ void free_run(wrc_run* R) {
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
     for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
+    if (R->sync_ev) cudaEventDestroy(R->sync_ev);
     for (cudaEvent_t e : R->st_pool) cudaEventDestroy(e);
     for (auto& ph : R->graphs)
         for (auto& G : ph)
@@ -998,7 +1008,8 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     if (e == cudaSuccess) e = alloc((void**)&R->vort_dev, sizeof(double) * 4 * WRC_MAX_VORTICES);
     if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
     // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
-    if (krylov_step_init(R->fp32, &R->max_blocks) != 0) {
+    R->cluster_max = krylov_cluster_max();
+    if (krylov_step_init(R->device, R->fp32, &R->max_blocks) != 0) {
         g_create_error = "cooperative Krylov kernel set-up failed";
         free_run(R);
         return WRC_ERR_CUDA;
@@ -1110,9 +1121,25 @@ wrc_status wrc_step(wrc_run* R, int32_t nsteps) {
     return WRC_OK;
 }
 
-wrc_status wrc_sync(wrc_run* R) {
+wrc_status wrc_sync(wrc_run* R, int32_t timeout_ms) {
     if (!R) return WRC_ERR_ARG;
-    CK(cudaStreamSynchronize(R->st));
+    if (timeout_ms < 0) {
+        CK(cudaStreamSynchronize(R->st));
+    } else {
+        // poll an event recorded behind the queued work; on expiry the work
+        // stays queued and a later wrc_sync can wait for it again
+        if (!R->sync_ev) CK(cudaEventCreateWithFlags(&R->sync_ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(R->sync_ev, R->st));
+        const auto t0 = std::chrono::steady_clock::now();
+        while (true) {
+            const cudaError_t q = cudaEventQuery(R->sync_ev);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) CK(q);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= (double)timeout_ms) return fail(R, WRC_ERR_TIMEOUT, "wrc_sync: the run's stream is still busy");
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
     int flags = 0;
     CK(cudaMemcpy(&flags, R->K.flags, sizeof(int), cudaMemcpyDeviceToHost));
     if (flags & 1) {
@@ -1306,6 +1333,20 @@ wrc_status wrc_profile(wrc_run* R, int32_t enable) {
         CK(R->trace.grow(sizeof(unsigned long long) * words, 0, R->st));
     }
     R->ev_used.clear();
+    return WRC_OK;
+}
+
+wrc_status wrc_query_krylov_form(wrc_run* R, int32_t* cluster_size) {
+    if (!R || !cluster_size) return WRC_ERR_ARG;
+    *cluster_size = krylov_step_cluster(R->n_active, R->max_blocks, R->fp32, R->device, R->cluster_max);
+    return WRC_OK;
+}
+
+wrc_status wrc_set_wait_limit(wrc_run* R, double seconds) {
+    if (!R) return WRC_ERR_ARG;
+    if (!(seconds > 0) || !(seconds <= 60.0)) return fail(R, WRC_ERR_ARG, "the wait limit must be in (0, 60] s");
+    double ns = std::ceil(seconds * 1e9);
+    R->wait_limit_ns = (unsigned long long)(ns < 1.0 ? 1.0 : ns);
     return WRC_OK;
 }
 

@@ -349,10 +349,12 @@ void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, c
 }
 
 template <typename T>
-void launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
-                 cudaStream_t s) {
-    { launch_pdl(k_diag<T>, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, R, psi, partials, counter, out, g,
-                                                                       T(1.0 / (12.0 * g.h))); note_launch(); }
+cudaError_t launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
+                        cudaStream_t s) {
+    const cudaError_t e = launch_pdl(k_diag<T>, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, R, psi, partials,
+                                     counter, out, g, T(1.0 / (12.0 * g.h)));
+    if (e == cudaSuccess) note_launch();
+    return e;
 }
 
 template <typename A, typename B>
@@ -384,7 +386,7 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
                                            bool);                                                           \
     template void launch_matvec<T>(const T*, const uint32_t*, long long, const T*, const T*, const T*,      \
                                    double, double, T*, const Geom&, const int*, int, cudaStream_t);        \
-    template void launch_diag<T>(const T*, const T*, double*, unsigned*, double*, const Geom&, cudaStream_t);
+    template cudaError_t launch_diag<T>(const T*, const T*, double*, unsigned*, double*, const Geom&, cudaStream_t);
 WRC_INST(double)
 WRC_INST(float)
 #undef WRC_INST

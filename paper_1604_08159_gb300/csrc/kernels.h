@@ -93,9 +93,10 @@ template <typename T>
 void launch_matvec(const T* F, const uint32_t* meta, long long n, const T* Ua, const T* Va,
                    const T* ga, double nu, double r, T* w, const Geom& g, const int* kstop, int jstep,
                    cudaStream_t s);
-// sums over the lattice of R, R^2, U^2 + V^2, |grad R|^2 -> out[0..3] (FP64 sums)
+// sums over the lattice of R, R^2, U^2 + V^2, |grad R|^2 -> out[0..3] (FP64 sums);
+// returns the launch status
 template <typename T>
-void launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
+cudaError_t launch_diag(const T* R, const T* psi, double* partials, unsigned* counter, double* out, const Geom& g,
                  cudaStream_t s);
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, long long n, cudaStream_t s);
@@ -136,6 +137,7 @@ struct KrylovStepArgs {
     int m;
     double dt, tol;
     unsigned long long limit_ns;
+    int refuse;             // test switch: a clustered launch behaves as if its clusters were not formed
     // phase trace (profiling; nullptr when off): trace[0] the start of block
     // 0, then per grid barrier p the arrival time of each block b at
     // trace[1 + p (nb + 1) + b] and block 0's release at trace[1 + p (nb + 1) + nb]
@@ -143,17 +145,27 @@ struct KrylovStepArgs {
     unsigned long long* trace;
 };
 constexpr int kTracePhases = 3 + 3 * 31;
-// Co-resident capacity of the single-run Krylov kernel (also for clusters of
-// 2 and 4 blocks, kept for krylov_step_blocks and the launch).
-int krylov_step_init(bool fp32, int* max_blocks);
+// Co-resident capacity of the single-run Krylov kernel on device dev (also
+// for clusters of 2 and 4 blocks, kept per device and precision for
+// krylov_step_blocks and the launch; a cluster size whose clusters a probe
+// launch does not see formed is not used).
+int krylov_step_init(int dev, bool fp32, int* max_blocks);
+// Largest cluster size a run created now may use: 4, or the cap set by the
+// environment variable WRC_KRYLOV_CLUSTER (1 or 2), read when called.
+int krylov_cluster_max();
 // Blocks for n active points: one thread per point, capped at max_blocks,
-// padded to a whole number of 4- or 2-block clusters where that fits.
-int krylov_step_blocks(long long n, int max_blocks, bool fp32);
-// Cooperative launch; clusters of 4 or 2 blocks when `blocks` is a multiple
-// within their capacity (their blocks pre-add the dot sums in distributed
-// shared memory).
+// padded to a whole number of 4- or 2-block clusters (at most cmax) where
+// that fits.
+int krylov_step_blocks(long long n, int max_blocks, bool fp32, int dev, int cmax);
+// Cluster size (1, 2 or 4) of the launch krylov_step_blocks plans for n points.
+int krylov_step_cluster(long long n, int max_blocks, bool fp32, int dev, int cmax);
+// Cooperative launch on device dev (current); clusters of 4 or 2 (<= cmax) blocks when
+// `blocks` is a multiple within their capacity (their blocks pre-add the dot
+// sums in distributed shared memory).  The first clustered launch per device
+// and precision synchronises `s` and, if the clusters were not formed,
+// switches them off for the device and launches again without them.
 template <typename T>
-cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s, int dev, int cmax);
 size_t krylov_partials_doubles(int max_blocks);
 // Batched Krylov step: `members` problems (device array of arguments) in one
 // cooperative launch of `blocks` blocks of pt (64, 128 or 256) threads; block

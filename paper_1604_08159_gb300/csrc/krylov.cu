@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdlib>
+#include <mutex>
 
 #include <type_traits>
 
@@ -731,13 +732,22 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
             dst[t] = sum;
         }
     } else {
+        // Two cluster barriers per call.  The first (arrive and wait) makes
+        // the blocks' sums visible to the cluster's block 0; the second is
+        // arrived at once block 0 has read its peers (the peers arrive at
+        // once) and waited for at the next call or at the kernel's end, so
+        // that no block rewrites its s_bp, or exits, while block 0 may still
+        // read it.  Every block of a cluster takes part in the same 2m
+        // barriers whatever path it takes (cluster_finish).
+        if (j > 1) __cluster_barrier_wait();
         for (int t = threadIdx.x; t < nout; t += PT) {
             double sum = 0.0;
             for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
             s_bp[t] = sum;
         }
         cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-        cl.sync();
+        __cluster_barrier_arrive();
+        __cluster_barrier_wait();
         if (cl.block_rank() == 0)
             for (int t = threadIdx.x; t < nout; t += PT) {
                 double sum = s_bp[t];
@@ -745,16 +755,33 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
                 for (int r = 1; r < CL; ++r) sum += cl.map_shared_rank(s_bp, r)[t];
                 dst[t] = sum;
             }
-        // a peer's s_bp is next written after the grid barrier that follows,
-        // which block 0 reaches only after these reads
+        __cluster_barrier_arrive();
+    }
+}
+
+// End of a clustered launch: wait for the second barrier of the last
+// step_dots call (if there was one), then take part in the cluster barriers
+// of the calls this block did not make (a breakdown, a failed grid barrier,
+// a refusal), so that every block of a cluster passes exactly 2m cluster
+// barriers and none exits while a peer may still read its shared memory.
+// Each of these waits ends: every block of the cluster reaches its own
+// remaining barriers, all its grid-barrier waits being bounded.
+__device__ __forceinline__ void cluster_finish(int calls, int m) {
+    if (calls > 0) __cluster_barrier_wait();
+    for (int c = calls; c < m; ++c) {
+        __cluster_barrier_arrive();
+        __cluster_barrier_wait();
+        __cluster_barrier_arrive();
+        __cluster_barrier_wait();
     }
 }
 
 // The Krylov step of one problem, run by its nb blocks (bid = this block's
 // index among them; with clusters of CL blocks, nb is a multiple of CL and
-// the cluster of block bid is bid / CL).
+// the cluster of block bid is bid / CL).  Returns the number of step_dots
+// calls made (Arnoldi steps j >= 1 entered), for cluster_finish.
 template <typename T, int PT, int CL>
-__device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int bid, const int nb) {
+__device__ __forceinline__ int krylov_body(const KrylovStepArgs& A, const int bid, const int nb) {
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
     const T* __restrict__ ga = (const T*)A.ga;
@@ -790,17 +817,10 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
     double acc[kNV + 1];
     int ph = 0;   // grid barriers passed (phase trace)
     if (lead && A.trace) A.trace[0] = gtimer();
+    int calls = 0;   // step_dots calls made
     if (*(volatile const int*)A.row_overflow) {
         if (lead) atomicOr(A.err, 4);
-        return;
-    }
-    if constexpr (CL > 1) {
-        // the cluster pre-sums read peers' shared memory: refuse to run (every
-        // block, before any barrier) unless the launch formed the clusters
-        if (cooperative_groups::this_cluster().num_blocks() != (unsigned)CL) {
-            if (lead) atomicOr(A.err, 8);
-            return;
-        }
+        return calls;
     }
     if (bid == 0)   // H is written by this block only
         for (int t = threadIdx.x; t < (m + 1) * m; t += blockDim.x) A.H[t] = 0.0;
@@ -828,7 +848,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         acc[kNV] += dbl(v) * dbl(v);
     }
     block_partials<PT, true>(acc, 0, P0 + (size_t)bid * kOutP, s_red);
-    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
     reduce_all<PT>(P0, 1, s_h, s_red, nb);
     // scalars of the step, once per block (FP64 division and square root
     // are long instruction sequences on this part)
@@ -861,7 +881,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             Gb[t] = g;
             Lq[A.glist[t]] = g;
         });
-        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
 
         // Arnoldi with CGS2 whose second pass is delayed by one step: step j
         // applies A to u, the vector of step j-1 after its first projection,
@@ -885,7 +905,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             acc[0] += dbl(basis[a]) * dbl(z);
         }
         block_partials<PT, false>(acc, 1, P0 + (size_t)bid * kOutP, s_red);
-        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
         reduce_all<PT>(P0, 1, s_h, s_red, nb);
         if (threadIdx.x == 0) {
             sH[0][0] = s_h[0];
@@ -902,14 +922,15 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
             Gu[t] = g;
             Lq[A.glist[t]] = g;
         });
-        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+        if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
 
         for (int j = 1; j <= m; ++j) {
             const bool last = j == m;   // only the second pass of u is left
             // z = A u and the dots of u and z with q_0 .. q_{j-1}: the values
             // [s, |u|^2, t, u.z] (the last step: [s, |u|^2])
             step_dots<T, PT, CL>(A, j, !last, bid, nb, P0 + (size_t)(bid / CL) * kOutP, s_dot, s_uz, s_bp);
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+            calls = j;
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
             reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb / CL);
             // scalars (every block the same; s_h holds s at 0..j-1, |u|^2 at j,
             // t at j+1..2j and u.z at 2j+1).  One warp's FP64 instruction
@@ -1034,7 +1055,7 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
                 }
             }
             ghost_step<T, PT>(A, zb, Gb, ldg, Gu, s_h, s_h + j + 1, qz, j, hinv, Lq, bid, nb, s_ws[wid], rc);
-            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+            if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
         }
         // H (every block holds it) to global memory, by block 0
         __syncthreads();
@@ -1053,10 +1074,10 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         if (bid == 0)
             for (int t = threadIdx.x; t < m; t += PT) A.y[t] = 0.0;
         if (lead) *A.kstop = 0;
-        return;
+        return calls;
     }
     if (bid == 0) phi1_block<PT>(A.H, k, m, A.dt, A.y, A.flags, s_red, s_h, s_int);
-    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return;
+    if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
     for (int t = threadIdx.x; t < k; t += PT) s_c[t] = A.dt * beta * A.y[t];
     __syncthreads();
     T* __restrict__ om = (T*)A.omega;
@@ -1069,11 +1090,29 @@ __device__ __forceinline__ void krylov_body(const KrylovStepArgs& A, const int b
         Lo[meta_pos(A.meta[a])] = x;
     }
     if (lead) *A.kstop = k;
+    return calls;
 }
 
 template <typename T, int PT, int CL>
 __global__ void __launch_bounds__(PT, 1) k_krylov_step(KrylovStepArgs A) {
-    krylov_body<T, PT, CL>(A, blockIdx.x, gridDim.x);
+    if constexpr (CL > 1) {
+        // the cluster pre-sums read peers' shared memory: refuse to run (every
+        // block, before any barrier) unless the launch formed the clusters
+        if (cooperative_groups::this_cluster().num_blocks() != (unsigned)CL || A.refuse) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, 8);
+            return;
+        }
+    }
+    const int calls = krylov_body<T, PT, CL>(A, blockIdx.x, gridDim.x);
+    if constexpr (CL > 1) cluster_finish(calls, A.m);
+    else (void)calls;
+}
+
+// Cluster formation check: launched with the attributes of the clustered
+// Krylov kernel (cooperative, clusters of CL blocks, grid of one cluster),
+// block 0 records how many blocks its cluster holds.  Reads no peer memory.
+__global__ void k_cluster_probe(int* out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out = (int)cooperative_groups::this_cluster().num_blocks();
 }
 
 // Batched form: several problems in one cooperative launch; block b works on
@@ -1084,16 +1123,29 @@ __global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __
                                                         const int* __restrict__ mem_b0) {
     const int q = blk2mem[blockIdx.x];
     const int b0 = mem_b0[q];
-    krylov_body<T, PT, 1>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
+    (void)krylov_body<T, PT, 1>(args[q], blockIdx.x - b0, mem_b0[q + 1] - b0);
 }
 
 }  // namespace
 
 namespace {
-// Co-resident blocks of the single-run kernel on this device for clusters of
-// 1, 2 and 4 blocks ([fp32][log2 CL]); 0 where a cluster size cannot be
-// launched cooperatively.
-int g_cap[2][3] = {{0, 0, 0}, {0, 0, 0}};
+// Per device and bulk precision: the co-resident blocks of the single-run
+// kernel for clusters of 1, 2 and 4 blocks (0 where a cluster size cannot
+// be launched cooperatively or was found not to form), and whether a
+// clustered launch has been checked for formed clusters on that device.
+constexpr int kMaxDevices = 64;
+struct ClusterCaps {
+    bool ready = false;
+    int cap[3] = {0, 0, 0};
+    bool checked = false;
+};
+ClusterCaps g_caps[kMaxDevices][2];
+std::mutex g_caps_mutex;
+// Test switch (environment variable WRC_KRYLOV_TEST_REFUSE=1, read once per
+// process): the first, checked clustered launch on a device behaves as if
+// its clusters were not formed, so that the fallback path can be tested on
+// a launch path that does form them.
+int g_test_refuse = -1;
 
 template <typename T, int CL>
 int cluster_capacity() {
@@ -1117,43 +1169,109 @@ int cluster_capacity() {
     return nc * CL;
 }
 
-// Cluster size for a launch of `blocks` blocks: the largest of 4 and 2 that
-// divides it within the co-resident capacity, else 1.
-int cluster_for(bool fp32, int blocks) {
-    if (blocks % 4 == 0 && blocks <= g_cap[fp32][2]) return 4;
-    if (blocks % 2 == 0 && blocks <= g_cap[fp32][1]) return 2;
+// Launch the probe as one cluster of CL blocks with the Krylov kernel's
+// attributes and report whether the cluster formed (1), did not (0), or the
+// launch failed (-1).  Synchronises the device's legacy stream only through
+// its own short-lived stream.
+int probe_cluster(int CL) {
+    int* d = nullptr;
+    cudaStream_t ps = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    int r = -1;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaMemsetAsync(d, 0, sizeof(int), ps) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeClusterDimension;
+        at[1].val.clusterDim.x = CL;
+        at[1].val.clusterDim.y = 1;
+        at[1].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(CL);
+        cfg.blockDim = dim3(32);
+        cfg.stream = ps;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        int h = 0;
+        if (cudaLaunchKernelEx(&cfg, k_cluster_probe, d) == cudaSuccess &&
+            cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, ps) == cudaSuccess &&
+            cudaStreamSynchronize(ps) == cudaSuccess) {
+            note_launch();
+            r = h == CL ? 1 : 0;
+        }
+    }
+    if (r < 0) cudaGetLastError();
+    if (ps) cudaStreamDestroy(ps);
+    cudaFree(d);
+    return r;
+}
+
+// Cluster size for a launch of `blocks` blocks: the largest of 4 and 2 (at
+// most cmax) that divides it within the co-resident capacity, else 1.
+int cluster_for(const ClusterCaps& c, int blocks, int cmax) {
+    if (cmax >= 4 && blocks % 4 == 0 && blocks <= c.cap[2]) return 4;
+    if (cmax >= 2 && blocks % 2 == 0 && blocks <= c.cap[1]) return 2;
     return 1;
+}
+
+ClusterCaps caps_of(int dev, bool fp32) {
+    std::lock_guard<std::mutex> lk(g_caps_mutex);
+    return (dev >= 0 && dev < kMaxDevices) ? g_caps[dev][fp32] : ClusterCaps{};
 }
 }  // namespace
 
-int krylov_step_init(bool fp32, int* max_blocks) {
-    // WRC_KRYLOV_CLUSTER = 1 or 2 caps the cluster size (default 4), e.g. for
-    // profilers that do not form the clusters of a cooperative launch
+int krylov_cluster_max() {
+    // WRC_KRYLOV_CLUSTER = 1 or 2 caps the cluster size (default 4)
     int cmax = 4;
     if (const char* ev = getenv("WRC_KRYLOV_CLUSTER")) cmax = atoi(ev) >= 4 ? 4 : (atoi(ev) >= 2 ? 2 : 1);
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+    return cmax;
+}
+
+int krylov_step_init(int dev, bool fp32, int* max_blocks) {
+    if (dev < 0 || dev >= kMaxDevices) return -1;
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<float, kPT, 1>, kPT, 0)
                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_krylov_step<double, kPT, 1>, kPT, 0);
     if (e != cudaSuccess || per < 1) return -2;
     *max_blocks = sms * per;
-    g_cap[fp32][0] = sms * per;
-    g_cap[fp32][1] = cmax < 2 ? 0 : (fp32 ? cluster_capacity<float, 2>() : cluster_capacity<double, 2>());
-    g_cap[fp32][2] = cmax < 4 ? 0 : (fp32 ? cluster_capacity<float, 4>() : cluster_capacity<double, 4>());
+    std::lock_guard<std::mutex> lk(g_caps_mutex);
+    if (g_test_refuse < 0) {
+        const char* ev = getenv("WRC_KRYLOV_TEST_REFUSE");
+        g_test_refuse = (ev && atoi(ev) == 1) ? 1 : 0;
+    }
+    ClusterCaps& c = g_caps[dev][fp32];
+    if (c.ready) return 0;
+    c.cap[0] = sms * per;
+    c.cap[1] = fp32 ? cluster_capacity<float, 2>() : cluster_capacity<double, 2>();
+    c.cap[2] = fp32 ? cluster_capacity<float, 4>() : cluster_capacity<double, 4>();
+    // a launch path that does not form clusters (some profilers replay a
+    // cooperative launch without them): use the unclustered kernel
+    for (int q = 2; q >= 1; --q)
+        if (c.cap[q] > 0 && probe_cluster(1 << q) != 1) c.cap[q] = 0;
+    c.ready = true;
     return 0;
 }
 
-int krylov_step_blocks(long long n, int max_blocks, bool fp32) {
+int krylov_step_blocks(long long n, int max_blocks, bool fp32, int dev, int cmax) {
+    const ClusterCaps c = caps_of(dev, fp32);
     long long b = (n + kPT - 1) / kPT;
     if (b < 1) b = 1;
     if (b > max_blocks) b = max_blocks;
     // padded to a whole number of clusters where that fits (the extra blocks
     // have no points and contribute zero partial sums)
     const long long b4 = (b + 3) / 4 * 4, b2 = (b + 1) / 2 * 2;
-    if (b4 <= g_cap[fp32][2] && b4 <= max_blocks) return (int)b4;
-    if (b2 <= g_cap[fp32][1] && b2 <= max_blocks) return (int)b2;
+    if (cmax >= 4 && b4 <= c.cap[2] && b4 <= max_blocks) return (int)b4;
+    if (cmax >= 2 && b2 <= c.cap[1] && b2 <= max_blocks) return (int)b2;
     return (int)b;
+}
+
+int krylov_step_cluster(long long n, int max_blocks, bool fp32, int dev, int cmax) {
+    return cluster_for(caps_of(dev, fp32), krylov_step_blocks(n, max_blocks, fp32, dev, cmax), cmax);
 }
 
 namespace {
@@ -1174,26 +1292,59 @@ cudaError_t launch_clustered(const KrylovStepArgs& args, int blocks, cudaStream_
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k_krylov_step<T, kPT, CL>, args);
 }
-}  // namespace
 
 template <typename T>
-cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
-    const int cl = cluster_for(sizeof(T) == 4, blocks);
+cudaError_t launch_unclustered(const KrylovStepArgs& args, int blocks, cudaStream_t s) {
+    KrylovStepArgs a = args;
+    void* params[] = {&a};
+    return cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT, 1>, dim3(blocks), dim3(kPT), params, 0, s);
+}
+}  // namespace
+
+// The first clustered launch on a device (per precision) is checked: the
+// stream is synchronised and, if the kernel refused to run because its
+// clusters were not formed (error bit 8, raised by every block before any
+// barrier or write), clusters are switched off for the device and the same
+// launch is issued again without them.  Later launches are not synchronised.
+template <typename T>
+cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s, int dev, int cmax) {
+    const bool fp32 = sizeof(T) == 4;
+    const ClusterCaps c = caps_of(dev, fp32);
+    const int cl = cluster_for(c, blocks, cmax);
+    KrylovStepArgs a = args;
+    a.refuse = (cl > 1 && !c.checked && g_test_refuse == 1) ? 1 : 0;
     cudaError_t e;
-    if (cl == 4) e = launch_clustered<T, 4>(args, blocks, s);
-    else if (cl == 2) e = launch_clustered<T, 2>(args, blocks, s);
-    else {
-        KrylovStepArgs a = args;
-        void* params[] = {&a};
-        e = cudaLaunchCooperativeKernel((const void*)k_krylov_step<T, kPT, 1>, dim3(blocks), dim3(kPT), params, 0, s);
+    if (cl == 4) e = launch_clustered<T, 4>(a, blocks, s);
+    else if (cl == 2) e = launch_clustered<T, 2>(a, blocks, s);
+    else e = launch_unclustered<T>(a, blocks, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || cl == 1 || c.checked) return e;
+    int err = 0;
+    e = cudaMemcpyAsync(&err, args.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_caps_mutex);
+        ClusterCaps& w = g_caps[dev][fp32];
+        w.checked = true;
+        if (err & 8) w.cap[1] = w.cap[2] = 0;
     }
+    if (!(err & 8)) return cudaSuccess;
+    e = cudaMemsetAsync(args.err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    // the same grid, unclustered (blocks past the active points carry no
+    // points and add zero partial sums)
+    a.refuse = 0;
+    e = launch_unclustered<T>(a, blocks, s);
     if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t launch_krylov_step<double>(const KrylovStepArgs&, int, cudaStream_t);
-template cudaError_t launch_krylov_step<float>(const KrylovStepArgs&, int, cudaStream_t);
+template cudaError_t launch_krylov_step<double>(const KrylovStepArgs&, int, cudaStream_t, int, int);
+template cudaError_t launch_krylov_step<float>(const KrylovStepArgs&, int, cudaStream_t, int, int);
 
 size_t krylov_partials_doubles(int max_blocks) { return (size_t)3 * max_blocks * kOutP; }
 

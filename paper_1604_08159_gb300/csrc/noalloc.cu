@@ -50,8 +50,13 @@ extern "C" wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattic
                                                       int32_t NJ, double* out, void* cuda_stream) {
     if (!omega_lattice || !psi_lattice || !out) return WRC_ERR_ARG;
     if (NJ < 8 || NJ > WRC_MAX_NJ || (NJ & (NJ - 1))) return WRC_ERR_ARG;   // beyond the stated maximum
-    int dev = 0;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the array is looked up for the device the stream belongs to, which
+    // must be the current one (a kernel is launched on the current device)
+    int dev = 0, sdev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return WRC_ERR_CUDA;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return WRC_ERR_ARG;
+    if (sdev != dev) return WRC_ERR_ARG;
     double* scratch = nullptr;
     {
         // set-up, once per device (with that device current): the device
@@ -64,7 +69,6 @@ extern "C" wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattic
         }
         scratch = g_noalloc_ptr[dev];
     }
-    const cudaStream_t s = (cudaStream_t)cuda_stream;
     unsigned* counter = (unsigned*)(scratch + kNoAllocPartials);
     // the counter must start at zero; the partial rows are overwritten
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return WRC_ERR_CUDA;
@@ -76,8 +80,11 @@ extern "C" wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattic
     g.J = 0;
     g.mask = NJ - 1;
     g.h = 2.0 * 3.141592653589793238462643383279502884 / NJ;
-    launch_diag<double>(omega_lattice, psi_lattice, scratch, counter, out, g, s);
-    k_noalloc_scale<<<1, 1, 0, s>>>(out, g.h * g.h);
+    if (launch_diag<double>(omega_lattice, psi_lattice, scratch, counter, out, g, s) != cudaSuccess) return WRC_ERR_CUDA;
+    double h2 = g.h * g.h;
+    void* args[] = {(void*)&out, (void*)&h2};
+    if (cudaLaunchKernel((const void*)k_noalloc_scale, dim3(1), dim3(1), args, 0, s) != cudaSuccess)
+        return WRC_ERR_CUDA;
     note_launch();
-    return cudaGetLastError() == cudaSuccess ? WRC_OK : WRC_ERR_CUDA;
+    return WRC_OK;
 }

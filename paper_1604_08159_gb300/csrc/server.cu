@@ -115,7 +115,7 @@ void retire(wrc_server* S, Request* q) {
     int64_t na = 0, ng = 0;
     std::vector<int32_t> idx;
     std::vector<double> om;
-    if (st == WRC_OK) st = wrc_sync(R);
+    if (st == WRC_OK) st = wrc_sync(R, -1);
     if (st == WRC_OK) st = wrc_diagnostics(R, d);
     if (st == WRC_OK) st = wrc_query_counts(R, &na, &ng, nullptr);
     if (st == WRC_OK) {

@@ -62,7 +62,9 @@ def test_create_rejects_oversized_lattice(lib):
 
 def test_null_run_handles(lib):
     assert lib.wrc_step(None, 1) == -1
-    assert lib.wrc_sync(None) == -1
+    assert lib.wrc_sync(None, -1) == -1
+    assert lib.wrc_set_wait_limit(None, 1.0) == -1
+    assert lib.wrc_query_krylov_form(None, None) == -1
     lib.wrc_destroy(None)
 
 
