@@ -25,8 +25,15 @@ column index.
 What each function follows
 --------------------------
 ``levels``                 Sec. 2.4: nested dyadic meshes G^0 c ... c G^J.
-``dd4_x/dd4_y``            Sec. 2.4: DD subdivision of order 2p = 4 (the 4-point
-                           Lagrange predictor from the coarser neighbours).
+``dd_predictor_weights``   Sec. 2.4: the 2p-point Lagrange predictor of DD order
+                           2p (Config.p; 2p = 4 is the default, 6, 8, 10 the
+                           higher orders of the Sec. 2.6.2 convergence study).
+``dd_scaling_derivative``  Sec. 2.5: phi'(n) at the integers from the
+                           refinement relation (eigenvector for 1/2).
+``first/second_derivative_integers``
+                           Sec. 2.5: the collocation stencils as integers over a
+                           common denominator (second derivative: a reading).
+``dd_x/dd_y``              Sec. 2.4: DD subdivision along one axis.
 ``predict_level``          Sec. 2.4: tensor-product DD prediction in 2-D.
 ``reconstruct``            Eq. 6: u^N evaluated on the finest lattice from the
                            retained coefficients (details of dropped points 0).
@@ -41,13 +48,17 @@ What each function follows
                            neighbours (reading).
 ``ghost_set``              Points outside the grid that the Sec. 2.5 stencils
                            read, with their values from Eq. 6 (reading).
-``d1/d2``                  Sec. 2.5: collocation derivatives; for 2p = 4 the DD
-                           first-derivative weights are those of the 5-point
-                           4th-order central difference; the second-derivative
-                           reading is the 5-point 4th-order stencil.
+``d1/d2``                  Sec. 2.5: collocation derivatives; the first
+                           derivative is the derivative of the DD interpolant at
+                           the collocation points (for 2p = 4 the 5-point
+                           4th-order central difference); the second-derivative
+                           reading is the central stencil of order 2p on 2p + 1
+                           points (phi'' is undefined at the integers for 2p = 4
+                           and only of order 2p - 2 beyond; Table 1's rates
+                           favour order 2p).
 ``streamfunction``         Poisson solve (the paper is silent): exact inverse of
-                           the 4th-order collocation Laplacian on the periodic
-                           finest lattice.
+                           the collocation Laplacian on the periodic finest
+                           lattice.
 ``velocity``               U = dpsi/dy, V = -dpsi/dx.
 ``strain``, ``smagorinsky_nut``, ``stress_vorticity_forcing``, ``sgs_forcing``
                            Eq. 5: Smagorinsky model, vorticity form of -div(tau).
@@ -72,12 +83,16 @@ function above is pinned; none is "parity unpinned".
 from __future__ import annotations
 
 from dataclasses import dataclass
+from fractions import Fraction
+from math import gcd
 
 import numpy as np
 import scipy.linalg
 
 __all__ = [
-    "Config", "State", "StepInfo", "levels", "dd4_x", "dd4_y", "predict_level",
+    "Config", "State", "StepInfo", "levels", "dd4_x", "dd4_y", "dd_x", "dd_y", "predict_level",
+    "dd_predictor_weights", "dd_predictor_integers", "dd_scaling_derivative",
+    "first_derivative_integers", "second_derivative_integers", "stencil_reach",
     "level_mask_sub", "reconstruct", "details", "significant", "adjacent_zone",
     "closure", "stencil_levels", "ghost_set", "at", "d1", "d2",
     "adaptive_derivatives", "streamfunction", "velocity", "strain",
@@ -109,6 +124,7 @@ class Config:
     cs: float = 0.0
     s_apriori: float = 0.0
     rayleigh_r: float = 0.0
+    p: int = 2           # DD order 2p (Sec. 2.4): 2p = 4, 6, 8 or 10
 
     @property
     def NJ(self) -> int:
@@ -161,22 +177,186 @@ def at(F: np.ndarray, di: int = 0, dk: int = 0) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# A2: DD4 prediction, reconstruction and details (Sec. 2.4, Eq. 6)
+# DD order 2p: predictor and collocation-derivative weights, derived here
+# (Sec. 2.4: the 2p-point Lagrange predictor; Sec. 2.5: derivatives of the
+# interpolant at the collocation points)
 # --------------------------------------------------------------------------
 
+def _frac_solve(A, b):
+    """Exact solution of the square system A x = b over the rationals
+    (Gaussian elimination on Fractions; A must be non-singular)."""
+    n = len(A)
+    M = [[Fraction(v) for v in row] + [Fraction(bv)] for row, bv in zip(A, b)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [a - f * bb for a, bb in zip(M[r], M[c])]
+    return [M[r][n] / M[r][r] for r in range(n)]
+
+
+def _common_denominator(fracs):
+    d = 1
+    for f in fracs:
+        d = d * f.denominator // gcd(d, f.denominator)
+    return d
+
+
+def dd_predictor_weights(p: int):
+    """Weights of the order-2p DD predictor (Sec. 2.4): the polynomial of
+    degree 2p - 1 through the coarser neighbours at odd offsets
+    +-1, +-3, ..., +-(2p - 1) evaluated at 0, as exact rationals; returns the
+    weight of the pair at +-(2k - 1), k = 1..p (symmetric)."""
+    xs = [2 * k - 1 for k in range(1, p + 1)]
+    nodes = [-x for x in reversed(xs)] + xs
+    w = []
+    for x in xs:
+        num, den = Fraction(1), Fraction(1)
+        for y in nodes:
+            if y != x:
+                num *= -y
+                den *= x - y
+        w.append(num / den)
+    return w
+
+
+def dd_predictor_integers(p: int):
+    """The predictor weights as integer numerators over a power of two:
+    (c_1..c_p, q) with weight_k = c_k 2^-q (every DD weight has a power-of-two
+    denominator)."""
+    w = dd_predictor_weights(p)
+    d = _common_denominator(w)
+    q = d.bit_length() - 1
+    assert d == 1 << q
+    return [int(x * d) for x in w], q
+
+
+def _frac_nullvector(A):
+    """A vector spanning the null space of A (exact, over the rationals) when
+    that null space has dimension one: reduced row echelon form, the free
+    column set to 1."""
+    rows, cols = len(A), len(A[0])
+    M = [[Fraction(v) for v in row] for row in A]
+    pivots, r = [], 0
+    for c in range(cols):
+        piv = next((q for q in range(r, rows) if M[q][c] != 0), None)
+        if piv is None:
+            continue
+        M[r], M[piv] = M[piv], M[r]
+        M[r] = [v / M[r][c] for v in M[r]]
+        for q in range(rows):
+            if q != r and M[q][c] != 0:
+                f = M[q][c]
+                M[q] = [a - f * b for a, b in zip(M[q], M[r])]
+        pivots.append(c)
+        r += 1
+    free = [c for c in range(cols) if c not in pivots]
+    assert len(free) == 1, "null space is not one-dimensional"
+    v = [Fraction(0)] * cols
+    v[free[0]] = Fraction(1)
+    for q, c in enumerate(pivots):
+        v[c] = -M[q][free[0]]
+    return v
+
+
+def dd_scaling_derivative(p: int):
+    """phi'(n) at the integers for the order-2p DD scaling function: the
+    refinement relation phi(x) = sum_k h_k phi(2x - k) (h_0 = 1, h_{+-(2k-1)}
+    the predictor weights) differentiated gives v = 2 M v with
+    M[n][m] = h_{2n-m}, i.e. the eigenvector of M for 1/2 (its null space of
+    2M - I is one-dimensional), normalised by sum_n n phi'(n) = -1 (the
+    derivative of sum_n n phi(x - n) = x).  Exact rationals for
+    n = 1 .. 2p - 2 (phi' is odd and vanishes at the integers beyond)."""
+    w = dd_predictor_weights(p)
+    h = {0: Fraction(1)}
+    for k, wk in enumerate(w, start=1):
+        h[2 * k - 1] = wk
+        h[-(2 * k - 1)] = wk
+    L = 2 * p - 2
+    ns = list(range(-L, L + 1))
+    A = []
+    for n in ns:
+        row = [2 * h.get(2 * n - m, Fraction(0)) for m in ns]
+        row[ns.index(n)] -= 1
+        A.append(row)
+    v = _frac_nullvector(A)
+    scale = Fraction(-1) / sum(n * x for n, x in zip(ns, v))
+    return [v[ns.index(n)] * scale for n in range(1, L + 1)]
+
+
+def first_derivative_integers(p: int):
+    """The first-derivative stencil of Sec. 2.5 as integers: D u_k =
+    (sum_j n_j (u_{k+j} - u_{k-j})) / (d h), j = 1 .. 2p - 2, with
+    n_j / d = -phi'(j) (the interpolant's derivative at the collocation point).
+    For 2p = 4 this is (8, -1) / 12, the 4th-order central difference."""
+    c = [-x for x in dd_scaling_derivative(p)]
+    d = _common_denominator(c)
+    return [int(x * d) for x in c], d
+
+
+def second_derivative_integers(p: int):
+    """The second-derivative stencil (reading: the central stencil of order
+    2p on the 2p + 1 points j = -p..p, exact for polynomials of degree
+    2p + 1) as integers: D2 u_k = (n_0 u_k + sum_j n_j (u_{k+j} + u_{k-j})) /
+    (d h^2).  For 2p = 4 this is (-30; 16, -1) / 12."""
+    pts = list(range(-p, p + 1))
+    A = [[Fraction(x) ** r for x in pts] for r in range(len(pts))]
+    b = [Fraction(0)] * len(pts)
+    b[2] = Fraction(2)
+    c = _frac_solve(A, b)
+    cs = [c[pts.index(j)] for j in range(0, p + 1)]
+    d = _common_denominator(cs)
+    return [int(x * d) for x in cs], d
+
+
+def stencil_reach(p: int) -> int:
+    """Largest offset (in units of the stencil spacing) read by the
+    derivative stencils of order 2p: 2p - 2 for the first derivative, p for
+    the second."""
+    return max(2 * p - 2, p)
+
+
+# --------------------------------------------------------------------------
+# A2: DD prediction, reconstruction and details (Sec. 2.4, Eq. 6)
+# --------------------------------------------------------------------------
+
+def dd_x(F: np.ndarray, p: int = 2) -> np.ndarray:
+    """DD order-2p prediction along x on a sublattice: the polynomial through
+    the neighbours at odd offsets +-1 .. +-(2p - 1) evaluated at 0, evaluated
+    with integer numerators as s = c_1 (a_1 + b_1), s = s + c_k (a_k + b_k)
+    for k = 2..p, then s 2^-q (a_k, b_k the neighbours at -+(2k - 1)).  For
+    2p = 4: (9 (a + b) - (c + d)) / 16."""
+    c, q = dd_predictor_integers(p)
+    acc = float(c[0]) * (at(F, -1) + at(F, 1))
+    for k in range(2, p + 1):
+        o = 2 * k - 1
+        acc = acc + float(c[k - 1]) * (at(F, -o) + at(F, o))
+    return acc * (2.0 ** -q)
+
+
+def dd_y(F: np.ndarray, p: int = 2) -> np.ndarray:
+    """As ``dd_x`` along y."""
+    c, q = dd_predictor_integers(p)
+    acc = float(c[0]) * (at(F, 0, -1) + at(F, 0, 1))
+    for k in range(2, p + 1):
+        o = 2 * k - 1
+        acc = acc + float(c[k - 1]) * (at(F, 0, -o) + at(F, 0, o))
+    return acc * (2.0 ** -q)
+
+
 def dd4_x(F: np.ndarray) -> np.ndarray:
-    """DD order-4 prediction along x on a sublattice: the cubic through the
-    neighbours at -3, -1, +1, +3 evaluated at 0, weights (-1, 9, 9, -1)/16,
-    evaluated as (9*(a+b) - (c+d)) * (1/16)."""
-    return (9.0 * (at(F, -1) + at(F, 1)) - (at(F, -3) + at(F, 3))) * 0.0625
+    """DD order-4 prediction along x: weights (-1, 9, 9, -1)/16."""
+    return dd_x(F, 2)
 
 
 def dd4_y(F: np.ndarray) -> np.ndarray:
     """As ``dd4_x`` along y."""
-    return (9.0 * (at(F, 0, -1) + at(F, 0, 1)) - (at(F, 0, -3) + at(F, 0, 3))) * 0.0625
+    return dd_y(F, 2)
 
 
-def predict_level(F: np.ndarray, J: int, j: int) -> np.ndarray:
+def predict_level(F: np.ndarray, J: int, j: int, p: int = 2) -> np.ndarray:
     """DD prediction of every level-j point from coarser points.  Returns an
     array on the stride-2^(J-j) sublattice: points odd in x only are predicted
     along x, points odd in y only along y, points odd in both by the tensor
@@ -187,33 +367,33 @@ def predict_level(F: np.ndarray, J: int, j: int) -> np.ndarray:
     n = sub.shape[0]
     odd = np.arange(n) % 2 == 1
     oi, ok = odd[None, :], odd[:, None]
-    px = dd4_x(sub)
-    py = dd4_y(sub)
-    pxy = dd4_y(px)
+    px = dd_x(sub, p)
+    py = dd_y(sub, p)
+    pxy = dd_y(px, p)
     return np.where(oi & ~ok, px, np.where(~oi & ok, py, pxy))
 
 
-def reconstruct(values: np.ndarray, active: np.ndarray, J: int) -> np.ndarray:
+def reconstruct(values: np.ndarray, active: np.ndarray, J: int, p: int = 2) -> np.ndarray:
     """R(u) of Eq. 6 on the full finest lattice: the values on the active set,
     and coarse-to-fine DD prediction (detail 0) at every other point."""
     R = np.where(active, values, 0.0)
     for j in range(1, J + 1):
         s = 1 << (J - j)
-        P = predict_level(R, J, j)
+        P = predict_level(R, J, j, p)
         sub = R[::s, ::s]
         fill = level_mask_sub(sub.shape[0]) & ~active[::s, ::s]
         sub[fill] = P[fill]
     return R
 
 
-def details(R: np.ndarray, active: np.ndarray, J: int) -> np.ndarray:
+def details(R: np.ndarray, active: np.ndarray, J: int, p: int = 2) -> np.ndarray:
     """Wavelet coefficients d = u - Pred(u) at active points of level >= 1
     (Eq. 6); 0 elsewhere.  ``R`` must hold the values on the active set and on
     the predictor points of every active point (true for a closed grid)."""
     d = np.zeros_like(R)
     for j in range(1, J + 1):
         s = 1 << (J - j)
-        P = predict_level(R, J, j)
+        P = predict_level(R, J, j, p)
         sub = R[::s, ::s]
         sel = level_mask_sub(sub.shape[0]) & active[::s, ::s]
         dv = d[::s, ::s]
@@ -249,10 +429,11 @@ def adjacent_zone(S: np.ndarray, lev: np.ndarray, J: int) -> np.ndarray:
     return A
 
 
-def _predictor_marks(src: np.ndarray) -> np.ndarray:
-    """Given a mask of level-j points on their sublattice, mark the DD4
-    predictor points of each one (offsets +-1, +-3 along x, along y, or the
-    4 x 4 tensor product, according to the point's type)."""
+def _predictor_marks(src: np.ndarray, p: int = 2) -> np.ndarray:
+    """Given a mask of level-j points on their sublattice, mark the DD
+    predictor points of each one (odd offsets +-1 .. +-(2p - 1) along x,
+    along y, or their 2p x 2p tensor product, according to the point's
+    type)."""
     n = src.shape[0]
     odd = np.arange(n) % 2 == 1
     oi, ok = odd[None, :], odd[:, None]
@@ -260,15 +441,16 @@ def _predictor_marks(src: np.ndarray) -> np.ndarray:
     Y = src & ~oi & ok
     XY = src & oi & ok
     M = np.zeros_like(src)
-    for a in (-3, -1, 1, 3):
+    offs = [o for k in range(1, p + 1) for o in (-(2 * k - 1), 2 * k - 1)]
+    for a in offs:
         M |= np.roll(X, a, axis=1)
         M |= np.roll(Y, a, axis=0)
-        for b in (-3, -1, 1, 3):
+        for b in offs:
             M |= np.roll(XY, (b, a), axis=(0, 1))
     return M
 
 
-def closure(A: np.ndarray, J: int) -> np.ndarray:
+def closure(A: np.ndarray, J: int, p: int = 2) -> np.ndarray:
     """Close the grid under DD prediction, finest level first: every point of
     level j in the grid adds its predictor points (all of coarser level), so
     that the grid's values are a valid multiresolution representation."""
@@ -277,7 +459,7 @@ def closure(A: np.ndarray, J: int) -> np.ndarray:
         s = 1 << (J - j)
         sub = A[::s, ::s]
         src = sub & level_mask_sub(sub.shape[0])
-        sub |= _predictor_marks(src)
+        sub |= _predictor_marks(src, p)
     return A
 
 
@@ -299,19 +481,22 @@ def stencil_levels(A: np.ndarray, lev: np.ndarray, J: int):
     return jx, jy
 
 
-def ghost_set(A: np.ndarray, jx: np.ndarray, jy: np.ndarray, J: int) -> np.ndarray:
-    """Ghost points: the points P +- h_{j*} e, P +- 2 h_{j*} e read by the
-    derivative stencil of an active point P that are not active, plus, finest
-    level first, the non-active predictor points of every ghost."""
+def ghost_set(A: np.ndarray, jx: np.ndarray, jy: np.ndarray, J: int, p: int = 2) -> np.ndarray:
+    """Ghost points: the points P +- r h_{j*} e (r = 1 .. stencil_reach(p))
+    read by the derivative stencils of an active point P that are not
+    active, plus, finest level first, the non-active predictor points of
+    every ghost."""
+    R = stencil_reach(p)
     G = np.zeros_like(A)
     for j in range(0, J + 1):
         s = 1 << (J - j)
         sx = (A & (jx == j))[::s, ::s]
         sy = (A & (jy == j))[::s, ::s]
         M = np.zeros_like(sx)
-        for a in (-2, -1, 1, 2):
-            M |= np.roll(sx, a, axis=1)
-            M |= np.roll(sy, a, axis=0)
+        for r in range(1, R + 1):
+            for a in (-r, r):
+                M |= np.roll(sx, a, axis=1)
+                M |= np.roll(sy, a, axis=0)
         gv = G[::s, ::s]
         gv |= M
     G &= ~A
@@ -319,7 +504,7 @@ def ghost_set(A: np.ndarray, jx: np.ndarray, jy: np.ndarray, J: int) -> np.ndarr
         s = 1 << (J - j)
         gv = G[::s, ::s]
         src = gv & level_mask_sub(gv.shape[0])
-        gv |= _predictor_marks(src) & ~A[::s, ::s]
+        gv |= _predictor_marks(src, p) & ~A[::s, ::s]
     return G
 
 
@@ -327,27 +512,37 @@ def ghost_set(A: np.ndarray, jx: np.ndarray, jy: np.ndarray, J: int) -> np.ndarr
 # Collocation derivatives (Sec. 2.5)
 # --------------------------------------------------------------------------
 
-def d1(F: np.ndarray, axis: int, h: float) -> np.ndarray:
-    """First derivative with unit (sub)lattice offsets and spacing h:
-    (8 (u_{+1} - u_{-1}) - (u_{+2} - u_{-2})) / (12 h)."""
-    if axis == 1:
-        p1, m1, p2, m2 = at(F, 1), at(F, -1), at(F, 2), at(F, -2)
-    else:
-        p1, m1, p2, m2 = at(F, 0, 1), at(F, 0, -1), at(F, 0, 2), at(F, 0, -2)
-    return (8.0 * (p1 - m1) - (p2 - m2)) / (12.0 * h)
+def _shift(F, axis, r):
+    return at(F, r) if axis == 1 else at(F, 0, r)
 
 
-def d2(F: np.ndarray, axis: int, h: float) -> np.ndarray:
-    """Second derivative: (-(u_{+2} + u_{-2}) + 16 (u_{+1} + u_{-1}) - 30 u) / (12 h^2)."""
-    if axis == 1:
-        p1, m1, p2, m2 = at(F, 1), at(F, -1), at(F, 2), at(F, -2)
-    else:
-        p1, m1, p2, m2 = at(F, 0, 1), at(F, 0, -1), at(F, 0, 2), at(F, 0, -2)
-    return (-(p2 + m2) + 16.0 * (p1 + m1) - 30.0 * F) / (12.0 * h * h)
+def d1(F: np.ndarray, axis: int, h: float, p: int = 2) -> np.ndarray:
+    """First derivative with unit (sub)lattice offsets and spacing h, the
+    stencil of ``first_derivative_integers``: acc = n_1 (u_{+1} - u_{-1}),
+    acc = acc + n_j (u_{+j} - u_{-j}) for j = 2 .., then acc / (d h).  For
+    2p = 4: (8 (u_{+1} - u_{-1}) - (u_{+2} - u_{-2})) / (12 h)."""
+    n, d = first_derivative_integers(p)
+    acc = float(n[0]) * (_shift(F, axis, 1) - _shift(F, axis, -1))
+    for j in range(2, len(n) + 1):
+        acc = acc + float(n[j - 1]) * (_shift(F, axis, j) - _shift(F, axis, -j))
+    return acc / (float(d) * h)
+
+
+def d2(F: np.ndarray, axis: int, h: float, p: int = 2) -> np.ndarray:
+    """Second derivative, the stencil of ``second_derivative_integers``:
+    acc = n_p (u_{+p} + u_{-p}), acc = acc + n_j (u_{+j} + u_{-j}) for
+    j = p - 1 .. 1, acc = acc + n_0 u, then acc / (d h^2).  For 2p = 4:
+    (-(u_{+2} + u_{-2}) + 16 (u_{+1} + u_{-1}) - 30 u) / (12 h^2)."""
+    n, d = second_derivative_integers(p)
+    acc = float(n[p]) * (_shift(F, axis, p) + _shift(F, axis, -p))
+    for j in range(p - 1, 0, -1):
+        acc = acc + float(n[j]) * (_shift(F, axis, j) + _shift(F, axis, -j))
+    acc = acc + float(n[0]) * F
+    return acc / (float(d) * h * h)
 
 
 def adaptive_derivatives(R: np.ndarray, A: np.ndarray, jx: np.ndarray, jy: np.ndarray,
-                         J: int, hJ: float):
+                         J: int, hJ: float, p: int = 2):
     """Dx, Dy, Dxx, Dyy of the reconstructed field R at active points, each
     along its axis with spacing h_{j*} = h_J 2^(J-j*) (lattice arrays, 0 off
     the grid)."""
@@ -362,11 +557,11 @@ def adaptive_derivatives(R: np.ndarray, A: np.ndarray, jx: np.ndarray, jy: np.nd
         sx = (A & (jx == j))[::s, ::s]
         sy = (A & (jy == j))[::s, ::s]
         if sx.any():
-            Dx[::s, ::s][sx] = d1(sub, 1, h)[sx]
-            Dxx[::s, ::s][sx] = d2(sub, 1, h)[sx]
+            Dx[::s, ::s][sx] = d1(sub, 1, h, p)[sx]
+            Dxx[::s, ::s][sx] = d2(sub, 1, h, p)[sx]
         if sy.any():
-            Dy[::s, ::s][sy] = d1(sub, 0, h)[sy]
-            Dyy[::s, ::s][sy] = d2(sub, 0, h)[sy]
+            Dy[::s, ::s][sy] = d1(sub, 0, h, p)[sy]
+            Dyy[::s, ::s][sy] = d2(sub, 0, h, p)[sy]
     return Dx, Dy, Dxx, Dyy
 
 
@@ -374,21 +569,30 @@ def adaptive_derivatives(R: np.ndarray, A: np.ndarray, jx: np.ndarray, jy: np.nd
 # A4/A5: streamfunction, velocity, Smagorinsky (Eq. 5)
 # --------------------------------------------------------------------------
 
-def laplacian_symbol(NJ: int, h: float) -> np.ndarray:
-    """sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta) / (12 h^2): minus the
-    Fourier symbol of the 4th-order second-derivative stencil at
-    theta = 2 pi n / NJ.  Evaluated through the exact identity
-    30 - 32 cos t + 2 cos 2t = 16 s^2 (3 + s^2), s = sin(t/2), which avoids the
-    cancellation of the direct form at small theta."""
-    s2 = np.sin(np.pi * np.arange(NJ) / NJ) ** 2
-    return 16.0 * s2 * (3.0 + s2) / (12.0 * h * h)
+def laplacian_symbol(NJ: int, h: float, p: int = 2) -> np.ndarray:
+    """sigma(theta): minus the Fourier symbol of the second-derivative stencil
+    at theta = 2 pi n / NJ.  With the stencil's integers (n_0; n_1..n_p) / d
+    and n_0 = -2 sum n_j, -(n_0 + 2 sum n_j cos j theta) = 4 sum n_j
+    sin^2(j theta / 2), so sigma = 4 sum_j n_j sin^2(j theta / 2) / (d h^2),
+    free of the cancellation of the cosine form at small theta.  For 2p = 4
+    it is evaluated through the identity 30 - 32 cos t + 2 cos 2t =
+    16 s^2 (3 + s^2), s = sin(t/2)."""
+    if p == 2:
+        s2 = np.sin(np.pi * np.arange(NJ) / NJ) ** 2
+        return 16.0 * s2 * (3.0 + s2) / (12.0 * h * h)
+    n, d = second_derivative_integers(p)
+    t = 2.0 * np.pi * np.arange(NJ) / NJ
+    acc = np.zeros(NJ)
+    for j in range(1, p + 1):
+        acc = acc + float(n[j]) * np.sin(0.5 * j * t) ** 2
+    return 4.0 * acc / (float(d) * h * h)
 
 
-def streamfunction(R: np.ndarray, h: float) -> np.ndarray:
-    """psi with L_h psi = -(R - mean R), L_h the 4th-order collocation
-    Laplacian on the periodic lattice, mean(psi) = 0."""
+def streamfunction(R: np.ndarray, h: float, p: int = 2) -> np.ndarray:
+    """psi with L_h psi = -(R - mean R), L_h the collocation Laplacian of
+    order 2p on the periodic lattice, mean(psi) = 0."""
     NJ = R.shape[0]
-    sig = laplacian_symbol(NJ, h)
+    sig = laplacian_symbol(NJ, h, p)
     den = sig[:, None] + sig[None, :]
     den[0, 0] = 1.0
     F = np.fft.fft2(R) / den
@@ -396,15 +600,15 @@ def streamfunction(R: np.ndarray, h: float) -> np.ndarray:
     return np.real(np.fft.ifft2(F))
 
 
-def velocity(psi: np.ndarray, h: float):
+def velocity(psi: np.ndarray, h: float, p: int = 2):
     """U = dpsi/dy, V = -dpsi/dx (finest-lattice stencils)."""
-    return d1(psi, 0, h), -d1(psi, 1, h)
+    return d1(psi, 0, h, p), -d1(psi, 1, h, p)
 
 
-def strain(psi: np.ndarray, U: np.ndarray, h: float):
+def strain(psi: np.ndarray, U: np.ndarray, h: float, p: int = 2):
     """Resolved strain of the velocity (U, V) = (psi_y, -psi_x):
     S11 = dU/dx = d2psi/dxdy (= -S22), S12 = (dU/dy + dV/dx)/2 = (psi_yy - psi_xx)/2."""
-    return d1(U, 1, h), 0.5 * (d2(psi, 0, h) - d2(psi, 1, h))
+    return d1(U, 1, h, p), 0.5 * (d2(psi, 0, h, p) - d2(psi, 1, h, p))
 
 
 def smagorinsky_nut(S11: np.ndarray, S12: np.ndarray, cs: float, h: float) -> np.ndarray:
@@ -413,20 +617,21 @@ def smagorinsky_nut(S11: np.ndarray, S12: np.ndarray, cs: float, h: float) -> np
     return (cs * h) ** 2 * (2.0 * np.sqrt(S11 * S11 + S12 * S12))
 
 
-def stress_vorticity_forcing(S11: np.ndarray, S12: np.ndarray, nut: np.ndarray, h: float) -> np.ndarray:
+def stress_vorticity_forcing(S11: np.ndarray, S12: np.ndarray, nut: np.ndarray, h: float,
+                             p: int = 2) -> np.ndarray:
     """Vorticity of the momentum forcing -d tau_ij/dx_j with tau_ij = -2 nu_t S_ij:
     g = (Dxx - Dyy)(2 nu_t S12) - 4 Dx Dy (nu_t S11)."""
     a = 2.0 * nut * S12
     c = nut * S11
-    return d2(a, 1, h) - d2(a, 0, h) - 4.0 * d1(d1(c, 0, h), 1, h)
+    return d2(a, 1, h, p) - d2(a, 0, h, p) - 4.0 * d1(d1(c, 0, h, p), 1, h, p)
 
 
-def sgs_forcing(psi: np.ndarray, U: np.ndarray, cs: float, h: float):
+def sgs_forcing(psi: np.ndarray, U: np.ndarray, cs: float, h: float, p: int = 2):
     """Smagorinsky forcing of the vorticity equation with pointwise |S| (Eq. 5).
     Returns (g, nu_t) on the lattice."""
-    S11, S12 = strain(psi, U, h)
+    S11, S12 = strain(psi, U, h, p)
     nut = smagorinsky_nut(S11, S12, cs, h)
-    return stress_vorticity_forcing(S11, S12, nut, h), nut
+    return stress_vorticity_forcing(S11, S12, nut, h, p), nut
 
 
 def vortex_field(NJ: int, xc, yc, gamma, s) -> np.ndarray:
@@ -469,11 +674,11 @@ def freeze(cfg: Config, A: np.ndarray, omega: np.ndarray) -> Frozen:
     """A4-A5: reconstruct omega, solve for psi, velocities and SGS forcing."""
     lev = levels(cfg.n0, cfg.J)
     jx, jy = stencil_levels(A, lev, cfg.J)
-    R = reconstruct(omega, A, cfg.J)
-    psi = streamfunction(R, cfg.h)
-    U, V = velocity(psi, cfg.h)
+    R = reconstruct(omega, A, cfg.J, cfg.p)
+    psi = streamfunction(R, cfg.h, cfg.p)
+    U, V = velocity(psi, cfg.h, cfg.p)
     if cfg.sgs == "dynamic":
-        g, _ = sgs_forcing(psi, U, cfg.cs, cfg.h)
+        g, _ = sgs_forcing(psi, U, cfg.cs, cfg.h, cfg.p)
     else:
         g = np.zeros_like(R)
     return Frozen(A, jx, jy, U, V, g, R, psi, cfg.nu_eff, cfg.rayleigh_r)
@@ -485,8 +690,8 @@ def apply_operator(cfg: Config, fz: Frozen, q: np.ndarray) -> np.ndarray:
     stencil level with ghost values from the DD reconstruction of q."""
     Q = np.zeros_like(fz.R)
     Q[fz.A] = q
-    RQ = reconstruct(Q, fz.A, cfg.J)
-    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h)
+    RQ = reconstruct(Q, fz.A, cfg.J, cfg.p)
+    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h, cfg.p)
     a = fz.A
     return -fz.U[a] * Dx[a] - fz.V[a] * Dy[a] + fz.nu_eff * (Dxx[a] + Dyy[a]) - fz.r * q
 
@@ -557,10 +762,10 @@ def adapt(cfg: Config, active: np.ndarray, omega: np.ndarray):
     adjacent zone, closure; values at newly added points from the
     reconstruction R(omega) on the current grid.  Returns (A', omega', d)."""
     lev = levels(cfg.n0, cfg.J)
-    R = reconstruct(omega, active, cfg.J)
-    d = details(R, active, cfg.J)
+    R = reconstruct(omega, active, cfg.J, cfg.p)
+    d = details(R, active, cfg.J, cfg.p)
     S = significant(d, active, lev, cfg.eps)
-    A2 = closure(adjacent_zone(S, lev, cfg.J), cfg.J)
+    A2 = closure(adjacent_zone(S, lev, cfg.J), cfg.J, cfg.p)
     return A2, np.where(A2, R, 0.0), d
 
 
@@ -595,10 +800,10 @@ def diagnostics(cfg: Config, st: State) -> dict:
     P = 1/2 int |grad omega|^2 and circulation int omega, by the rectangle rule
     on the reconstructed lattice fields."""
     h = cfg.h
-    R = reconstruct(st.omega, st.active, cfg.J)
-    psi = streamfunction(R, h)
-    U, V = velocity(psi, h)
-    gx, gy = d1(R, 1, h), d1(R, 0, h)
+    R = reconstruct(st.omega, st.active, cfg.J, cfg.p)
+    psi = streamfunction(R, h, cfg.p)
+    U, V = velocity(psi, h, cfg.p)
+    gx, gy = d1(R, 1, h, cfg.p), d1(R, 0, h, cfg.p)
     w = h * h
     return {
         "E": 0.5 * w * float(np.sum(U * U + V * V)),
@@ -622,8 +827,8 @@ def scalar_operator(cfg: Config, fz: Frozen, kappa: float, q: np.ndarray) -> np.
     as in ``apply_operator``."""
     Q = np.zeros_like(fz.R)
     Q[fz.A] = q
-    RQ = reconstruct(Q, fz.A, cfg.J)
-    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h)
+    RQ = reconstruct(Q, fz.A, cfg.J, cfg.p)
+    Dx, Dy, Dxx, Dyy = adaptive_derivatives(RQ, fz.A, fz.jx, fz.jy, cfg.J, cfg.h, cfg.p)
     a = fz.A
     return -fz.U[a] * Dx[a] - fz.V[a] * Dy[a] + kappa * (Dxx[a] + Dyy[a])
 
@@ -635,16 +840,16 @@ def adapt_two(cfg: Config, active: np.ndarray, omega: np.ndarray, rv: np.ndarray
     adjacent zone and the closure; values at the new grid from the
     reconstructions.  Returns (A', omega', r_v')."""
     lev = levels(cfg.n0, cfg.J)
-    Rw = reconstruct(omega, active, cfg.J)
-    Sw = significant(details(Rw, active, cfg.J), active, lev, cfg.eps)
+    Rw = reconstruct(omega, active, cfg.J, cfg.p)
+    Sw = significant(details(Rw, active, cfg.J, cfg.p), active, lev, cfg.eps)
     if rv_whole:
         full = np.ones_like(active)
         Rr = np.asarray(rv, dtype=np.float64)
-        Sr = significant(details(Rr, full, cfg.J), full, lev, cfg.eps)
+        Sr = significant(details(Rr, full, cfg.J, cfg.p), full, lev, cfg.eps)
     else:
-        Rr = reconstruct(rv, active, cfg.J)
-        Sr = significant(details(Rr, active, cfg.J), active, lev, cfg.eps)
-    A2 = closure(adjacent_zone(Sw | Sr, lev, cfg.J), cfg.J)
+        Rr = reconstruct(rv, active, cfg.J, cfg.p)
+        Sr = significant(details(Rr, active, cfg.J, cfg.p), active, lev, cfg.eps)
+    A2 = closure(adjacent_zone(Sw | Sr, lev, cfg.J), cfg.J, cfg.p)
     return A2, np.where(A2, Rw, 0.0), np.where(A2, Rr, 0.0)
 
 

@@ -22,12 +22,13 @@ def pdist(a, b, n):
     return min(d, n - d)
 
 
-def predictor_points(i, k, J, NJ):
-    """Coordinates of the DD4 predictor points of a level >= 1 point."""
+def predictor_points(i, k, J, NJ, p=2):
+    """Coordinates of the DD predictor points (order 2p) of a level >= 1
+    point: odd multiples of its level's spacing, up to (2p - 1)."""
     j = lev_of(i, k, J)
     s = 1 << (J - j)
     oi, ok = (i // s) % 2 == 1, (k // s) % 2 == 1
-    offs = (-3 * s, -s, s, 3 * s)
+    offs = [o * s for o in range(-(2 * p - 1), 2 * p, 2)]
     if oi and not ok:
         return [((i + o) % NJ, k) for o in offs]
     if ok and not oi:
@@ -51,13 +52,13 @@ def brute_adjacent(S, J, NJ):
     return out
 
 
-def brute_closure(A, J, NJ):
+def brute_closure(A, J, NJ, p=2):
     A = A.copy()
     for j in range(J, 0, -1):
         for k in range(NJ):
             for i in range(NJ):
                 if A[k, i] and lev_of(i, k, J) == j:
-                    for (pi, pk) in predictor_points(i, k, J, NJ):
+                    for (pi, pk) in predictor_points(i, k, J, NJ, p):
                         A[pk, pi] = True
     return A
 
@@ -84,14 +85,17 @@ def brute_stencil_levels(A, J, NJ):
     return jx, jy
 
 
-def brute_ghosts(A, jx, jy, J, NJ):
+def brute_ghosts(A, jx, jy, J, NJ, p=2):
+    # the first-derivative stencil of order 2p reads 2p - 2 points each side,
+    # the second-derivative one p
+    reach = max(2 * p - 2, p)
     G = np.zeros_like(A)
     for k in range(NJ):
         for i in range(NJ):
             if not A[k, i]:
                 continue
             sx, sy = 1 << (J - jx[k, i]), 1 << (J - jy[k, i])
-            for o in (-2, -1, 1, 2):
+            for o in [q for q in range(-reach, reach + 1) if q]:
                 for (qi, qk) in (((i + o * sx) % NJ, k), (i, (k + o * sy) % NJ)):
                     if not A[qk, qi]:
                         G[qk, qi] = True
@@ -99,7 +103,7 @@ def brute_ghosts(A, jx, jy, J, NJ):
         for k in range(NJ):
             for i in range(NJ):
                 if G[k, i] and lev_of(i, k, J) == j:
-                    for (pi, pk) in predictor_points(i, k, J, NJ):
+                    for (pi, pk) in predictor_points(i, k, J, NJ, p):
                         if not A[pk, pi]:
                             G[pk, pi] = True
     return G
@@ -113,26 +117,28 @@ def random_significance(n0, J, frac, seed):
     return S, lev
 
 
-@pytest.mark.parametrize("n0,J,frac,seed", [(4, 2, 0.05, 0), (4, 2, 0.2, 1), (4, 3, 0.02, 2), (8, 2, 0.03, 3)])
-def test_adjacent_and_closure_match_brute_force(n0, J, frac, seed):
+@pytest.mark.parametrize("n0,J,frac,seed,p", [(4, 2, 0.05, 0, 2), (4, 2, 0.2, 1, 2), (4, 3, 0.02, 2, 2),
+                                               (8, 2, 0.03, 3, 2), (8, 2, 0.02, 7, 3), (16, 2, 0.01, 8, 4)])
+def test_adjacent_and_closure_match_brute_force(n0, J, frac, seed, p):
     NJ = n0 << J
     S, lev = random_significance(n0, J, frac, seed)
     adj = O.adjacent_zone(S, lev, J)
     assert np.array_equal(adj, brute_adjacent(S, J, NJ))
-    A = O.closure(adj, J)
-    assert np.array_equal(A, brute_closure(adj, J, NJ))
+    A = O.closure(adj, J, p)
+    assert np.array_equal(A, brute_closure(adj, J, NJ, p))
 
 
-@pytest.mark.parametrize("n0,J,frac,seed", [(4, 2, 0.05, 4), (4, 3, 0.03, 5), (8, 2, 0.1, 6)])
-def test_stencil_levels_and_ghosts_match_brute_force(n0, J, frac, seed):
+@pytest.mark.parametrize("n0,J,frac,seed,p", [(4, 2, 0.05, 4, 2), (4, 3, 0.03, 5, 2), (8, 2, 0.1, 6, 2),
+                                               (8, 2, 0.02, 9, 3), (16, 2, 0.01, 10, 4)])
+def test_stencil_levels_and_ghosts_match_brute_force(n0, J, frac, seed, p):
     NJ = n0 << J
     S, lev = random_significance(n0, J, frac, seed)
-    A = O.closure(O.adjacent_zone(S, lev, J), J)
+    A = O.closure(O.adjacent_zone(S, lev, J), J, p)
     jx, jy = O.stencil_levels(A, lev, J)
     bx, by = brute_stencil_levels(A, J, NJ)
     assert np.array_equal(jx, bx) and np.array_equal(jy, by)
-    G = O.ghost_set(A, jx, jy, J)
-    assert np.array_equal(G, brute_ghosts(A, jx, jy, J, NJ))
+    G = O.ghost_set(A, jx, jy, J, p)
+    assert np.array_equal(G, brute_ghosts(A, jx, jy, J, NJ, p))
 
 
 def test_grid_invariants_on_vortex_pair():
