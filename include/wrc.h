@@ -13,7 +13,8 @@
  * or pointwise |S| as a vorticity forcing g_SGS), and Rayleigh friction r.
  * omega is held on an adaptive grid: the finest lattice is NJ x NJ with
  * NJ = n0 * 2^J, h_J = 2 pi / NJ; the grid is the epsilon-thresholded set of
- * DD4 wavelet coefficients (Eq. 6) plus its adjacent zone and closure.  One
+ * DD wavelet coefficients of order 2p (Eq. 6; wrc_config.p) plus its
+ * adjacent zone and closure.  One
  * time step is the exponential-Euler step
  *     omega^{n+1} = omega^n + dt phi_1(dt A_n) (A_n omega^n + g_n)
  * with A_n the frozen linear operator (Sec. 2.1: projection of the discrete
@@ -70,6 +71,10 @@ typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
  *  J         refinement levels, >= 1, with n0 * 2^J <= WRC_MAX_NJ
  *  krylov_m  Krylov dimension m, 1..WRC_MAX_M
  *  sgs       wrc_sgs; prec: wrc_precision
+ *  p         half the DD order 2p (Sec. 2.4, 2.6.2): 2 (2p = 4, also for 0),
+ *            3 or 4; the predictor interpolates 2p coarser neighbours, the
+ *            first derivative is the DD interpolant's (Sec. 2.5), the second
+ *            the central stencil of order 2p
  *  eps       threshold on |d| (absolute), >= 0 (Eq. 6)
  *  re        Reynolds number; nu = 1/re
  *  cs        Smagorinsky constant C_s (Eq. 5), filter width Delta = h_J
@@ -77,7 +82,7 @@ typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
  *  rayleigh_r linear damping coefficient r (Sec. 2.3), >= 0
  *  dt        time step, > 0                                            */
 typedef struct {
-    int32_t n0, J, krylov_m, sgs, prec, reserved;
+    int32_t n0, J, krylov_m, sgs, prec, p;
     double eps, re, cs, s_apriori, rayleigh_r, dt;
 } wrc_config;
 

@@ -28,7 +28,7 @@ STAGES = ("reconstruct", "poisson", "velocity", "sgs", "krylov", "adapt", "host"
 
 class WrcConfig(ctypes.Structure):
     _fields_ = [("n0", c_int32), ("J", c_int32), ("krylov_m", c_int32), ("sgs", c_int32),
-                ("prec", c_int32), ("reserved", c_int32), ("eps", c_double), ("re", c_double),
+                ("prec", c_int32), ("p", c_int32), ("eps", c_double), ("re", c_double),
                 ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double)]
 
 
@@ -158,8 +158,8 @@ def _flag(*ptrs):
 
 def make_config(params) -> WrcConfig:
     """WrcConfig from a ``workloads.RunParams``-like object."""
-    return WrcConfig(params.n0, params.J, params.m, params.sgs, params.prec, 0, params.eps, params.re,
-                     params.cs, params.s_apriori, params.rayleigh_r, params.dt)
+    return WrcConfig(params.n0, params.J, params.m, params.sgs, params.prec, getattr(params, "p", 2), params.eps,
+                     params.re, params.cs, params.s_apriori, params.rayleigh_r, params.dt)
 
 
 # ---- entry points -------------------------------------------------------------

@@ -178,6 +178,7 @@ struct wrc_run {
     // the Krylov kernel), wrc_set_wait_limit
     unsigned long long wait_limit_ns = 2000000000ull;
     int cluster_max = 4;   // largest thread-block cluster of the Krylov launch (WRC_KRYLOV_CLUSTER at creation)
+    int rmax = kGhostRowMax;   // longest ghost interpolation row (per DD order)
     cudaEvent_t sync_ev = nullptr;   // wrc_sync with a time limit
 
     // passive scalar (the vapour mixing ratio with diffusion only), enabled by
@@ -269,8 +270,8 @@ wrc_status ensure_ghost_capacity(wrc_run* R, long long ng) {
     const cudaStream_t s = R->st;
     const int m = R->cfg.krylov_m;
     CK(R->row_len.grow(sizeof(int) * c, 0, s));
-    CK(R->row_idx.grow(sizeof(int) * c * kGhostRowMax, 0, s));
-    CK(R->row_w.grow(sizeof(double) * c * kGhostRowMax, 0, s));
+    CK(R->row_idx.grow(sizeof(int) * c * R->rmax, 0, s));
+    CK(R->row_w.grow(sizeof(double) * c * R->rmax, 0, s));
     R->Gb.release(s);
     CK(R->Gb.grow(R->es * c * (m + 1), 0, s));
     R->cap_g = c;
@@ -306,7 +307,8 @@ wrc_status rebuild_host(wrc_run* R) {
     if (R->counts_host[kMaxKeys] != 0) {
         CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
         const int ev = R->counts_host[kMaxKeys];
-        if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded kGhostRowMax terms");
+        if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded its capacity of " +
+                                                      std::to_string(R->rmax) + " terms");
         if (ev & 8)
             return fail(R, WRC_ERR_CUDA,
                         "the Krylov kernel was launched without its thread-block clusters (set WRC_KRYLOV_CLUSTER=1 "
@@ -343,7 +345,7 @@ wrc_status rebuild_part2(wrc_run* R) {
                            R->counts_dev);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
     launch_ghost_rows(R->list, 0, nullptr, nullptr, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
-                      R->row_w.as<double>(), kGhostRowMax, R->g, R->K.overflow, s, R->counts_dev, R->cap, R->cap_g);
+                      R->row_w.as<double>(), R->rmax, R->g, R->K.overflow, s, R->counts_dev, R->cap, R->cap_g);
     CKL("finalize");
     return WRC_OK;
 }
@@ -438,9 +440,10 @@ wrc_status stage_fold(wrc_run* R) {
 
 // Thresholding with eps: details of the values in L on the current grid (or
 // on every lattice point for a freshly sampled field), significance and
-// adjacent zone into nxt, closure; then the rebuild.
+// adjacent zone into nxt, closure.  The details read only the grid's values
+// (its predictor points are in the closed grid).
 template <typename T>
-wrc_status threshold_body(wrc_run* R, double eps, bool whole_lattice) {
+wrc_status threshold_marks(wrc_run* R, double eps, bool whole_lattice) {
     const Geom& g = R->g;
     const cudaStream_t s = R->st;
     CK(cudaMemsetAsync(R->sig, 0, R->N, s));
@@ -455,6 +458,32 @@ wrc_status threshold_body(wrc_run* R, double eps, bool whole_lattice) {
                               s, R->counts_dev);
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
     CKL("threshold");
+    return WRC_OK;
+}
+
+// Thresholding and the first part of the rebuild (L holds the values on the
+// whole lattice, or at least at every point of the new grid).
+template <typename T>
+wrc_status threshold_body(wrc_run* R, double eps, bool whole_lattice) {
+    TRY(threshold_marks<T>(R, eps, whole_lattice));
+    return rebuild_part1(R);
+}
+
+// Adaptation after a step (Eq. 6), first part: L (and Lr with the passive
+// scalar) holds the new values at the current grid's points.  Details,
+// threshold, adjacent zone and closure give the new grid in nxt; the values
+// at its new points come from the reconstruction on the current grid,
+// evaluated only there (coarse to fine); then the rebuild's first part.
+template <typename T>
+wrc_status adapt_part1(wrc_run* R) {
+    TRY(stage_mark(R, WRC_STAGE_ADAPT));
+    TRY(threshold_marks<T>(R, R->cfg.eps, false));
+    TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
+    for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>((T*)R->L, R->act, R->nxt, j, R->g, R->st);
+    if (R->scalar)
+        for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>(R->Lr.as<T>(), R->act, R->nxt, j, R->g, R->st);
+    CKL("new values");
+    TRY(stage_mark(R, WRC_STAGE_ADAPT));
     return rebuild_part1(R);
 }
 
@@ -591,7 +620,7 @@ KrylovStepArgs krylov_args(wrc_run* R) {
     A.row_len = R->row_len.as<int>();
     A.row_idx = R->row_idx.as<int>();
     A.row_w = R->row_w.as<double>();
-    A.rmax = kGhostRowMax;
+    A.rmax = R->rmax;
     A.row_overflow = R->K.overflow;
     A.Gb = R->Gb.p;
     A.ldg = R->cap_g;
@@ -600,8 +629,8 @@ KrylovStepArgs krylov_args(wrc_run* R) {
     A.ga = R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.p : nullptr;
     A.nu = nu_eff(R);
     A.r = R->cfg.rayleigh_r;
-    A.c1J = 1.0 / (12.0 * R->g.h);
-    A.c2J = 1.0 / (12.0 * R->g.h * R->g.h);
+    A.c1J = 1.0 / (dd_d1den(R->g.P) * R->g.h);
+    A.c2J = 1.0 / (dd_d2den(R->g.P) * R->g.h * R->g.h);
     A.L = R->L;
     A.Lq = R->Lq;
     A.omega = R->omega[R->cur].p;
@@ -661,7 +690,7 @@ wrc_status krylov(wrc_run* R) {
     const long long n = R->n_active;
     const int m = R->cfg.krylov_m;
     const KrylovStepArgs A = krylov_args(R);
-    const int blocks = krylov_step_blocks(n, R->max_blocks, R->fp32, R->device, R->cluster_max);
+    const int blocks = krylov_step_blocks(n, R->max_blocks, R->fp32, R->g.P, R->device, R->cluster_max);
     TRY(trace_reset(R, blocks));
     int e0 = -1;
     if (R->profiling) {
@@ -692,15 +721,9 @@ wrc_status step_phases(wrc_run* R) {
     R->frozen = true;
     TRY(stage_mark(R, WRC_STAGE_KRYLOV));
     TRY(krylov<T>(R));
-    TRY(run_phase(R, kPhaseAdapt1, [&] {
-        // L holds omega^{n+1} at the grid points; reconstruct the rest, threshold
-        TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
-        for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
-        if (R->scalar)   // Lr holds r_v^{n+1} at the grid points
-            for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>(R->Lr.as<T>(), R->act, j, R->g, R->st);
-        TRY(stage_mark(R, WRC_STAGE_ADAPT));
-        return threshold_body<T>(R, R->cfg.eps, false);
-    }));
+    // L holds omega^{n+1} at the grid points (Lr r_v^{n+1}); threshold, then
+    // the values at the new grid's new points
+    TRY(run_phase(R, kPhaseAdapt1, [&] { return adapt_part1<T>(R); }));
     R->det_count = R->n_active;
     TRY(stage_mark(R, WRC_STAGE_HOST));
     TRY(rebuild_host(R));
@@ -948,6 +971,7 @@ bool valid_config(const wrc_config* c, std::string& why) {
     if (c->krylov_m < 1 || c->krylov_m > WRC_MAX_M) { why = "krylov_m must be in 1..WRC_MAX_M"; return false; }
     if (c->sgs < 0 || c->sgs > 2) { why = "unknown sgs mode"; return false; }
     if (c->prec != WRC_FP64 && c->prec != WRC_MIXED) { why = "unknown precision"; return false; }
+    if (c->p != 0 && (c->p < 2 || c->p > kMaxP)) { why = "p (half the DD order) must be 2, 3 or 4 (0: 2)"; return false; }
     if (!(c->eps >= 0) || !(c->re > 0) || !(c->dt > 0) || !(c->rayleigh_r >= 0) || !(c->cs >= 0) ||
         !(c->s_apriori >= 0)) {
         why = "eps, re, dt, rayleigh_r, cs, s_apriori out of range";
@@ -984,6 +1008,8 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     R->g.J = cfg->J;
     R->g.mask = NJ - 1;
     R->g.h = 2.0 * 3.141592653589793238462643383279502884 / NJ;
+    R->g.P = cfg->p == 0 ? 2 : cfg->p;
+    R->rmax = dd_row_max(R->g.P);
     R->N = (long long)NJ * NJ;
     const long long N = R->N;
     const int m = cfg->krylov_m;
@@ -1009,7 +1035,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
     // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
     R->cluster_max = krylov_cluster_max();
-    if (krylov_step_init(R->device, R->fp32, &R->max_blocks) != 0) {
+    if (krylov_step_init(R->device, R->fp32, R->g.P, &R->max_blocks) != 0) {
         g_create_error = "cooperative Krylov kernel set-up failed";
         free_run(R);
         return WRC_ERR_CUDA;
@@ -1338,7 +1364,7 @@ wrc_status wrc_profile(wrc_run* R, int32_t enable) {
 
 wrc_status wrc_query_krylov_form(wrc_run* R, int32_t* cluster_size) {
     if (!R || !cluster_size) return WRC_ERR_ARG;
-    *cluster_size = krylov_step_cluster(R->n_active, R->max_blocks, R->fp32, R->device, R->cluster_max);
+    *cluster_size = krylov_step_cluster(R->n_active, R->max_blocks, R->fp32, R->g.P, R->device, R->cluster_max);
     return WRC_OK;
 }
 
@@ -1502,7 +1528,7 @@ wrc_status batch_krylov(BatchCtx& C, const std::vector<wrc_run*>& live) {
         BCK(cudaEventRecord(C.ev_streams[q], C.streams[q]));
         BCK(cudaStreamWaitEvent(C.main, C.ev_streams[q], 0));
     }
-    const int maxb = krylov_batch_max_blocks(C.fp32, C.pt);
+    const int maxb = krylov_batch_max_blocks(C.fp32, C.P, C.pt);
     if (maxb <= 0) return cfail(C, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
     int total = 0;
     TRY(plan_batch(C, live, maxb, total));
@@ -1526,7 +1552,8 @@ wrc_status batch_krylov(BatchCtx& C, const std::vector<wrc_run*>& live) {
         BCK(cudaEventCreate(&pb));
         BCK(cudaEventRecord(pa, C.main));
     }
-    BCK(launch_krylov_batch<T>(C.d_args, C.d_blk, C.d_blk + total, (int)M, total, C.pt, max_n, C.main));
+    (void)max_n;
+    BCK(launch_krylov_batch<T>(C.d_args, C.d_blk, C.d_blk + total, (int)M, total, C.pt, C.P, C.main));
     if (C.profiling) {
         BCK(cudaEventRecord(pb, C.main));
         C.prof.push_back({pa, pb});
@@ -1590,10 +1617,7 @@ wrc_status batch_step_t(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vec
     }
     for (size_t i : live_i) {
         wrc_run* R = runs[i];
-        const wrc_status st = run_phase(R, kPhaseAdapt1, [&] {
-            for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
-            return threshold_body<T>(R, R->cfg.eps, false);
-        });
+        const wrc_status st = run_phase(R, kPhaseAdapt1, [&] { return adapt_part1<T>(R); });
         if (st != WRC_OK) mark(i, st);
         else R->det_count = R->n_active;
     }
@@ -1652,8 +1676,9 @@ long long grown_capacity(long long n) {
 
 }  // namespace
 
-wrc_status wrc::batch_init(BatchCtx& C, cudaStream_t main, int nstreams, bool fp32) {
+wrc_status wrc::batch_init(BatchCtx& C, cudaStream_t main, int nstreams, bool fp32, int P) {
     C.fp32 = fp32;
+    C.P = P;
     C.main = main;
     if (!C.main) {   // keep the batched launches off the legacy default stream
         BCK(cudaStreamCreateWithFlags(&C.main, cudaStreamNonBlocking));
@@ -1740,8 +1765,8 @@ double wrc::run_bytes_for(const wrc_config& cfg, long long na, long long ng) {
     const double c = (double)grown_capacity(na), cg = (double)grown_capacity(ng);
     // meta x2, omega x2, details, U, V, g, w, basis (m+1), doubles scratch
     b += c * (8.0 + 2.0 * es + 5.0 * es + es * m1 + 8.0);
-    // ghost rows: length, kGhostRowMax indices and weights; ghost basis values
-    b += cg * (4.0 + (4.0 + 8.0) * kGhostRowMax + es * m1);
+    // ghost rows: length, dd_row_max(p) indices and weights; ghost basis values
+    b += cg * (4.0 + (4.0 + 8.0) * dd_row_max(cfg.p == 0 ? 2 : cfg.p) + es * m1);
     return b;
 }
 
@@ -1803,8 +1828,8 @@ wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_str
         return WRC_ERR_ARG;
     }
     for (int i = 1; i < n; ++i)
-        if (cfgs[i].prec != cfgs[0].prec) {
-            g_ens_create_error = "all members of an ensemble share one precision";
+        if (cfgs[i].prec != cfgs[0].prec || (cfgs[i].p == 0 ? 2 : cfgs[i].p) != (cfgs[0].p == 0 ? 2 : cfgs[0].p)) {
+            g_ens_create_error = "all members of an ensemble share one precision and one DD order";
             return WRC_ERR_ARG;
         }
     wrc_ensemble* E = new wrc_ensemble();
@@ -1813,7 +1838,8 @@ wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_str
         wrc_ensemble_destroy(E);
         return st;
     };
-    if (batch_init(E->C, (cudaStream_t)cuda_stream, std::min(kBatchStreams, (int)n), cfgs[0].prec == WRC_MIXED) !=
+    if (batch_init(E->C, (cudaStream_t)cuda_stream, std::min(kBatchStreams, (int)n), cfgs[0].prec == WRC_MIXED,
+                   cfgs[0].p == 0 ? 2 : cfgs[0].p) !=
         WRC_OK)
         return cleanup(WRC_ERR_CUDA, E->C.err);
     const int S = (int)E->C.streams.size();
@@ -1880,7 +1906,7 @@ wrc_status wrc_ensemble_tune(wrc_ensemble* E, int32_t steps_per_candidate, int32
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             // a shape needs one co-resident block per member at least
-            if (krylov_batch_max_blocks(E->C.fp32, pts[a]) < (int)E->members.size()) continue;
+            if (krylov_batch_max_blocks(E->C.fp32, E->C.P, pts[a]) < (int)E->members.size()) continue;
             E->C.pt = pts[a];
             E->C.ept = epts[b];
             E->C.profiling = true;

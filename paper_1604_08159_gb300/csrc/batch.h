@@ -1,7 +1,7 @@
 // Stepping several runs together, shared by the batched ensemble and the
 // request server: each run's freeze and adaptation phases replay as its own
 // CUDA graphs on one of a few shared streams, and the Krylov part of all the
-// runs of one bulk precision goes into ONE cooperative launch whose blocks
+// runs of one bulk precision and DD order goes into ONE cooperative launch whose blocks
 // are shared out in proportion to their active counts.
 #pragma once
 
@@ -23,6 +23,7 @@ struct BatchCtx {
     std::vector<cudaEvent_t> ev_streams;
     cudaEvent_t ev_main = nullptr;
     bool fp32 = false;
+    int P = 2;                               // DD half-order of the runs (2p = 4, 6, 8)
     int pt = 128;                            // threads per block of the batched kernel
     int ept = 1;                             // target active points per thread
     KrylovStepArgs* h_args = nullptr;        // pinned
@@ -37,11 +38,12 @@ struct BatchCtx {
     std::string err;
 };
 
-// Streams (nstreams run streams, and `main`, created when NULL) and events.
-wrc_status batch_init(BatchCtx& C, cudaStream_t main, int nstreams, bool fp32);
+// Streams (nstreams run streams, and `main`, created when NULL) and events,
+// for runs of bulk precision fp32 and DD half-order P.
+wrc_status batch_init(BatchCtx& C, cudaStream_t main, int nstreams, bool fp32, int P);
 void batch_free(BatchCtx& C);
 
-// One step of every run in `runs` (all of C's bulk precision, each created on
+// One step of every run in `runs` (all of C's bulk precision and DD order, each created on
 // one of C.streams and initialised).  per_run (may be NULL) receives each
 // run's status: a run whose phase fails is left out of the later phases of
 // this step and the others carry on; a failure that is not one run's (the

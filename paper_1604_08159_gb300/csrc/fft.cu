@@ -515,22 +515,38 @@ __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int r
     pdl_trigger();
 }
 
-// Twiddles exp(-2 pi i t/n) (t < n) and the symbols
-// sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta)/(12 h^2) = 4 s^2 (3 + s^2)/(3 h^2),
-// s = sin(theta/2), theta = 2 pi t/n, of the 4th-order second difference, and
-// d(theta) = (8 sin theta - sin 2 theta)/(6 h) of the first difference (its
-// symbol is i d), all evaluated in FP64 and stored as T.
+// Twiddles exp(-2 pi i t/n) (t < n) and the symbols, theta = 2 pi t/n, of the
+// stencils of order 2P (all evaluated in FP64 and stored as T):
+//   2P = 4: sigma(theta) = (30 - 32 cos theta + 2 cos 2 theta)/(12 h^2)
+//           = 4 s^2 (3 + s^2)/(3 h^2), s = sin(theta/2), of the second
+//           difference, and d(theta) = (8 sin theta - sin 2 theta)/(6 h) of the
+//           first difference (its symbol is i d);
+//   2P > 4: with the second-derivative stencil (n_0; n_1..n_P)/(d2 h^2) and
+//           n_0 = -2 sum n_j, sigma = 4 sum_j n_j sin^2(j theta/2)/(d2 h^2)
+//           (no cancellation at small theta), and with the first-derivative
+//           stencil (n_1..n_R)/(d1 h), d = 2 sum_j n_j sin(j theta)/(d1 h).
 template <typename T>
-__global__ void k_fft_init(cx_t<T>* tw, T* sigma, T* dsym, int n, double inv3h2, double inv6h) {
+__global__ void k_fft_init(cx_t<T>* tw, T* sigma, T* dsym, int n, double h, int P) {
     pdl_wait();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         double sn, cs;
         sincospi(2.0 * t / n, &sn, &cs);
         tw[t] = mk<cx_t<T>>((T)cs, (T)(-sn));
-        const double s = sinpi((double)t / n);
-        const double s2 = s * s;
-        sigma[t] = (T)(4.0 * s2 * (3.0 + s2) * inv3h2);
-        dsym[t] = (T)((8.0 * sinpi(2.0 * t / n) - sinpi(4.0 * t / n)) * inv6h);
+        if (P == 3 || P == 4) {
+            double sg = 0.0, ds = 0.0;
+            for (int j = 1; j <= P; ++j) {
+                const double sj = sinpi((double)j * t / n);
+                sg += dd_d2(P, j) * sj * sj;
+            }
+            for (int j = 1; j <= dd_reach1(P); ++j) ds += dd_d1(P, j) * sinpi(2.0 * j * t / n);
+            sigma[t] = (T)(4.0 * sg / (dd_d2den(P) * h * h));
+            dsym[t] = (T)(2.0 * ds / (dd_d1den(P) * h));
+        } else {
+            const double s = sinpi((double)t / n);
+            const double s2 = s * s;
+            sigma[t] = (T)(4.0 * s2 * (3.0 + s2) * (1.0 / (3.0 * h * h)));
+            dsym[t] = (T)((8.0 * sinpi(2.0 * t / n) - sinpi(4.0 * t / n)) * (1.0 / (6.0 * h)));
+        }
     }
     pdl_trigger();
 }
@@ -620,7 +636,7 @@ int plan_init_t(PoissonPlan& p, const Geom& g, cudaStream_t s) {
     if (cudaMalloc(&p.dsym, sizeof(T) * p.n) != cudaSuccess) return -1;
     if (setup_all<T>() != 0) return -2;
     { launch_pdl(k_fft_init<T>, (p.n + 255) / 256, 256, 0, s, (cx_t<T>*)p.tw, (T*)p.sigma, (T*)p.dsym, p.n,
-                                                       1.0 / (3.0 * g.h * g.h), 1.0 / (6.0 * g.h)); note_launch(); }
+                                                       g.h, g.P); note_launch(); }
     const int E = p.logn < 4 ? 8 : 16;
     const int R0 = p.logn < 4 ? 1 : 1 << (p.logn % 4);
     { k_fft_pass_tables<cx_t<T>><<<(p.n + 255) / 256, 256, 0, s>>>((const cx_t<T>*)p.tw, (cx_t<T>*)p.ptw, p.n,

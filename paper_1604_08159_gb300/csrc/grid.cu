@@ -66,13 +66,13 @@ __global__ void k_recon_level_1d(T* __restrict__ L, const uint8_t* __restrict__ 
 }
 
 // Pass 2: the points odd in both directions.  Their prediction is the y
-// prediction over the x predictions of rows k -+ s, k -+ 3s at column i, and
-// those x predictions are exactly the values pass 1 stored at the points
-// (i, k -+ s), (i, k -+ 3s) unless these are active (same operands, same
-// rounded operations): only the rows of active neighbours are predicted
-// again.  Bit-identical to the tensor-product predictor, with one 1-D
+// prediction over the x predictions of rows k -+ s, k -+ 3s, .. (2P rows) at
+// column i, and those x predictions are exactly the values pass 1 stored at
+// the points (i, k -+ s), (i, k -+ 3s), .. unless these are active (same
+// operands, same rounded operations): only the rows of active neighbours are
+// predicted again.  Bit-identical to the tensor-product predictor, with one 1-D
 // prediction per point instead of five for most points.
-template <typename T>
+template <typename T, int P>
 __global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ act, int j, Geom g) {
     pdl_wait();
     const int sh = g.J - j;
@@ -84,19 +84,55 @@ __global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ 
         const int k = (2 * r + 1) << sh, i = (2 * c + 1) << sh;
         const long long p = ((long long)k << g.L) + i;
         if (act[p]) continue;
-        const int ks[4] = {(k - s) & m, (k + s) & m, (k - 3 * s) & m, (k + 3 * s) & m};
-        T rv[4];
+        if constexpr (P == 2) {
+            const int ks[4] = {(k - s) & m, (k + s) & m, (k - 3 * s) & m, (k + 3 * s) & m};
+            T rv[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const long long pe = ((long long)ks[e] << g.L) + i;
-            if (!act[pe]) {
-                rv[e] = L[pe];
-            } else {
-                const T* row = L + ((size_t)ks[e] << g.L);
-                rv[e] = dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+            for (int e = 0; e < 4; ++e) {
+                const long long pe = ((long long)ks[e] << g.L) + i;
+                if (!act[pe]) {
+                    rv[e] = L[pe];
+                } else {
+                    const T* row = L + ((size_t)ks[e] << g.L);
+                    rv[e] = dd4<T>(row[(i - s) & m], row[(i + s) & m], row[(i - 3 * s) & m], row[(i + 3 * s) & m]);
+                }
             }
+            L[p] = dd4<T>(rv[0], rv[1], rv[2], rv[3]);
+        } else {
+            // rows k -+ (2e + 1) s: the x prediction stored there by pass 1, or
+            // computed again where that point is active
+            T lo[P], hi[P];
+#pragma unroll
+            for (int e = 0; e < P; ++e) {
+                const int o = (2 * e + 1) * s;
+                const int kl = (k - o) & m, kh = (k + o) & m;
+                const long long pl = ((long long)kl << g.L) + i, ph = ((long long)kh << g.L) + i;
+                lo[e] = act[pl] ? predict_line<T, P, false>(L, i, kl, s, true, g) : L[pl];
+                hi[e] = act[ph] ? predict_line<T, P, false>(L, i, kh, s, true, g) : L[ph];
+            }
+            L[p] = ddp<T, P>(lo, hi);
         }
-        L[p] = dd4<T>(rv[0], rv[1], rv[2], rv[3]);
+    }
+    pdl_trigger();
+}
+
+// Values at the new points of a rebuilt grid (in `nxt`, not in `act`) for
+// one level: the DD prediction from the current grid's values (Eq. 6, detail
+// zero), tensor form for points odd in both directions.  Every predictor
+// point of a new point is in the closed new grid: a current point (value in
+// L) or a coarser new point (written by an earlier level's launch).  The
+// other non-current points are not written.
+template <typename T>
+__global__ void k_recon_new(T* __restrict__ L, const uint8_t* __restrict__ act, const uint8_t* __restrict__ nxt,
+                            int j, Geom g) {
+    pdl_wait();
+    const long long cnt = level_count(j, g);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, k;
+        level_point(t, j, g, i, k);
+        const long long p = ((long long)k << g.L) + i;
+        if (nxt[p] && !act[p]) L[p] = predict<T>(L, i, k, j, g);
     }
     pdl_trigger();
 }
@@ -142,24 +178,22 @@ __global__ void k_details_adj(const uint32_t* __restrict__ meta, long long n, co
     pdl_trigger();
 }
 
-// Visit the DD4 predictor points of level-j point (i, k).
+// Visit the DD predictor points (order 2 g.P) of level-j point (i, k): the
+// odd multiples of the level's spacing up to (2P - 1) along its odd
+// direction(s), or their 2P x 2P tensor product.
 template <typename F>
 __device__ __forceinline__ void for_predictor_points(int i, int k, int j, const Geom& g, F&& f) {
     const int sh = g.J - j;
     const int s = 1 << sh;
     const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
-    const int off[4] = {-3 * s, -s, s, 3 * s};
+    const int np = 2 * g.P;
     if (oi && !ok) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) f((i + off[q]) & g.mask, k);
+        for (int q = 0; q < np; ++q) f((i + (2 * q + 1 - np) * s) & g.mask, k);
     } else if (!oi && ok) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) f(i, (k + off[q]) & g.mask);
+        for (int q = 0; q < np; ++q) f(i, (k + (2 * q + 1 - np) * s) & g.mask);
     } else {
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) f((i + off[q]) & g.mask, (k + off[b]) & g.mask);
+        for (int b = 0; b < np; ++b)
+            for (int q = 0; q < np; ++q) f((i + (2 * q + 1 - np) * s) & g.mask, (k + (2 * b + 1 - np) * s) & g.mask);
     }
 }
 
@@ -183,8 +217,9 @@ __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __res
 
 // Stencil levels and ghost marks.  For an active point P of level l the
 // stencil level along x is the largest j in [l, J] with an active point at
-// P +- h_j e_x (l if none); the stencil reads P +- h_{j*}, P +- 2 h_{j*}, and
-// the non-active ones among them are ghosts.  Same along y.
+// P +- h_j e_x (l if none); the stencils read P +- r h_{j*}, r = 1 .. R
+// (R = 2 for 2P = 4, max(2P - 2, P) in general), and the non-active ones
+// among them are ghosts.  Same along y.
 __global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __restrict__ gho,
                                 uint8_t* __restrict__ JJ, Geom g) {
     pdl_wait();
@@ -209,8 +244,8 @@ __global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __rest
         }
         JJ[p] = (uint8_t)(jx | (jy << 4));
         const int sx = 1 << (g.J - jx), sy = 1 << (g.J - jy);
-#pragma unroll
-        for (int o = -2; o <= 2; ++o) {
+        const int R = dd_reach(g.P);
+        for (int o = -R; o <= R; ++o) {
             if (o == 0) continue;
             const long long qx = ((long long)k << g.L) + ((i + o * sx) & g.mask);
             if (!act[qx]) gho[qx] = 1;
@@ -683,6 +718,163 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
     pdl_trigger();
 }
 
+// Interpolation rows of the ghosts of one level for DD orders 2P > 4: as
+// k_ghost_rows_level (same merge in predictor order, same per-warp hash table),
+// with 2P or (2P)^2 predictors, their weights dd_pred(P, .) 2^-shift (products
+// of two for the tensor product), rows of up to dd_row_max(P) entries, and the
+// predictors' rows read from global memory (no staging).
+template <int P>
+__global__ void __launch_bounds__(32 * kRowWarps)
+k_ghost_rows_level_wide(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
+                        const int* __restrict__ lat2idx, int* __restrict__ row_len, int* __restrict__ row_idx,
+                        double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
+                        const int* __restrict__ dcounts, int nkeys) {
+    pdl_wait();
+    constexpr int kCapW = dd_row_max(P);
+    constexpr int kHashW = 2 * kCapW;
+    constexpr int kHashBits = P == 3 ? 8 : 9;
+    static_assert((1 << kHashBits) == kHashW, "hash table of 2 kCapW slots");
+    constexpr int NP1 = 2 * P;
+    __shared__ int s_idx[kRowWarps][kCapW];
+    __shared__ double s_wt[kRowWarps][kCapW];
+    __shared__ int s_hkey[kRowWarps][kHashW];   // -1: empty
+    __shared__ int s_hval[kRowWarps][kHashW];
+    __shared__ int s_hpos[kRowWarps][kCapW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* idx = s_idx[wid];
+    double* wt = s_wt[wid];
+    int* hkey = s_hkey[wid];
+    int* hval = s_hval[wid];
+    int* hpos = s_hpos[wid];
+    for (int h = lane; h < kHashW; h += 32) hkey[h] = -1;
+    __syncwarp();
+    if (dcounts) {
+        n_act = dcounts[0];
+        gbeg = 0;
+        n_tot = 0;
+        for (int q = 0; q < nkeys; ++q) {
+            if (q < j) gbeg += dcounts[q];
+            n_tot += dcounts[q];
+        }
+        cnt = dcounts[j];
+    }
+    const int cap = rmax < kCapW ? rmax : kCapW;
+    const int sh = g.J - j;
+    const int s = 1 << sh;
+    const double scale = 1.0 / (double)(1 << dd_shift(P));
+    auto w1 = [&](int a) {   // weight of the a-th predictor along one axis
+        const int o = 2 * a + 1 - NP1;
+        return dd_pred(P, ((o < 0 ? -o : o) - 1) >> 1) * scale;
+    };
+    auto hash = [](int key) { return (int)(((unsigned)key * 2654435761u) >> (32 - kHashBits)); };
+    for (long long t = (long long)blockIdx.x * kRowWarps + wid; t < cnt; t += (long long)gridDim.x * kRowWarps) {
+        const long long gi = gbeg - n_act + t;
+        const int p = list[gbeg + t];
+        const int i = p & g.mask, k = p >> g.L;
+        const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
+        const bool two_d = oi == ok;
+        const int np = two_d ? NP1 * NP1 : NP1;
+        int len = 0;
+        bool over = false;
+        for (int q0 = 0; q0 < np; q0 += 32) {
+            int my_id = -1, my_rl = 0;
+            const int qm = q0 + lane;
+            if (qm < np) {
+                const int a = two_d ? qm % NP1 : qm, b = two_d ? qm / NP1 : 0;
+                int qi = i, qk = k;
+                if (two_d) {
+                    qi = (i + (2 * a + 1 - NP1) * s) & g.mask;
+                    qk = (k + (2 * b + 1 - NP1) * s) & g.mask;
+                } else if (oi) {
+                    qi = (i + (2 * a + 1 - NP1) * s) & g.mask;
+                } else {
+                    qk = (k + (2 * a + 1 - NP1) * s) & g.mask;
+                }
+                my_id = lat2idx[((long long)qk << g.L) + qi];
+                my_rl = (my_id >= n_act && my_id < n_tot) ? row_len[my_id - n_act] : 1;
+            }
+            const int nq = np - q0 < 32 ? np - q0 : 32;
+            for (int qq = 0; qq < nq; ++qq) {
+                const int qg = q0 + qq;
+                const int id = __shfl_sync(0xffffffffu, my_id, qq);
+                const int rl0 = __shfl_sync(0xffffffffu, my_rl, qq);
+                const double w = two_d ? w1(qg % NP1) * w1(qg / NP1) : w1(qg);
+                if (id < 0 || id >= n_tot) {   // not a grid point: record, do not read
+                    over = true;
+                    continue;
+                }
+                const bool ghost = id >= n_act;
+                const int rl = ghost ? rl0 : 1;
+                const long long r = id - n_act;
+                for (int e0 = 0; e0 < rl; e0 += 32) {
+                    const int e = e0 + lane;
+                    const bool has = e < rl;
+                    int my = 0;
+                    double mw = 0.0;
+                    if (has) {
+                        if (!ghost) {
+                            my = id;
+                            mw = w;
+                        } else {
+                            my = row_idx[r * rmax + e];
+                            mw = w * row_w[r * rmax + e];
+                        }
+                    }
+                    int pos = -1;
+                    if (has)
+                        for (int h = hash(my);; h = (h + 1) & (kHashW - 1)) {
+                            const int key = hkey[h];
+                            if (key == my) {
+                                pos = hval[h];
+                                break;
+                            }
+                            if (key < 0) break;
+                        }
+                    if (pos >= 0) wt[pos] += mw;
+                    const unsigned fresh = __ballot_sync(0xffffffffu, has && pos < 0);
+                    if (has && pos < 0) {
+                        const int slot = len + __popc(fresh & ((1u << lane) - 1u));
+                        if (slot < cap) {
+                            idx[slot] = my;
+                            wt[slot] = mw;
+                            for (int h = hash(my);; h = (h + 1) & (kHashW - 1))
+                                if (atomicCAS(&hkey[h], -1, my) == -1) {
+                                    hval[h] = slot;
+                                    hpos[slot] = h;
+                                    break;
+                                }
+                        }
+                    }
+                    const int nf = __popc(fresh);
+                    if (len + nf > cap) over = true;
+                    len = len + nf < cap ? len + nf : cap;
+                    __syncwarp();
+                }
+            }
+        }
+        for (int e = lane; e < len; e += 32) {
+            row_idx[gi * rmax + e] = idx[e];
+            row_w[gi * rmax + e] = wt[e];
+            hkey[hpos[e]] = -1;
+        }
+        if (lane == 0) {
+            row_len[gi] = len;
+            if (over) atomicOr(overflow, 4);
+        }
+        __syncwarp();
+    }
+    pdl_trigger();
+}
+
+// The ghost-row kernel of the DD order of g.
+using RowsKernel = void (*)(const int*, long long, long long, long long, long long, const int*, int*, int*, double*,
+                            int, int, Geom, int*, const int*, int);
+RowsKernel rows_kernel(const Geom& g) {
+    if (g.P == 3) return k_ghost_rows_level_wide<3>;
+    if (g.P == 4) return k_ghost_rows_level_wide<4>;
+    return k_ghost_rows_level;
+}
+
 }  // namespace
 
 template <typename T>
@@ -697,7 +889,14 @@ template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
     const long long q = level_count(j, g) / 3;   // n^2 / 4
     { launch_pdl(k_recon_level_1d<T>, blocks_for(2 * q), kThreads, 0, s, L, act, j, g); note_launch(); }
-    { launch_pdl(k_recon_level_2d<T>, blocks_for(q), kThreads, 0, s, L, act, j, g); note_launch(); }
+    if (g.P == 3) launch_pdl(k_recon_level_2d<T, 3>, blocks_for(q), kThreads, 0, s, L, act, j, g);
+    else if (g.P == 4) launch_pdl(k_recon_level_2d<T, 4>, blocks_for(q), kThreads, 0, s, L, act, j, g);
+    else launch_pdl(k_recon_level_2d<T, 2>, blocks_for(q), kThreads, 0, s, L, act, j, g);
+    note_launch();
+}
+template <typename T>
+void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, int j, const Geom& g, cudaStream_t s) {
+    { launch_pdl(k_recon_new<T>, blocks_for(level_count(j, g)), kThreads, 0, s, L, act, nxt, j, g); note_launch(); }
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
@@ -748,7 +947,7 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
         // sizes on the device, grids over the capacities (capturable)
         { launch_pdl(k_lat2idx, blocks_for(cap_a + cap_g), kThreads, 0, s, list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
         for (int j = 1; j <= J; ++j) {
-            launch_pdl(k_ghost_rows_level, blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s,
+            launch_pdl(rows_kernel(g), blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s,
                 list, 0, 0, 0, 0, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, dcounts, J + 1);
             note_launch();
         }
@@ -759,7 +958,7 @@ void launch_ghost_rows(const int* list, long long n_act, const long long* goff, 
     if (tot > 0) { launch_pdl(k_lat2idx, blocks_for(tot), kThreads, 0, s, list, tot, lat2idx, nullptr, 0); note_launch(); }
     for (int j = 1; j <= J; ++j)
         if (gcnt[j] > 0) {
-            launch_pdl(k_ghost_rows_level, blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s,
+            launch_pdl(rows_kernel(g), blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s,
                 list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, nullptr,
                 0);
             note_launch();
@@ -773,6 +972,7 @@ void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx
     template void launch_init_vortices<T>(T*, const double*, int, const Geom&, cudaStream_t);             \
     template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t, const int*);  \
     template void launch_recon_level<T>(T*, const uint8_t*, int, const Geom&, cudaStream_t);              \
+    template void launch_recon_new<T>(T*, const uint8_t*, const uint8_t*, int, const Geom&, cudaStream_t);\
     template void launch_details_adj<T>(const uint32_t*, long long, const T*, double, T*, uint8_t*,       \
                                         uint8_t*, const Geom&, cudaStream_t, const int*);                 \
     template void launch_finalize<T>(const int*, long long, const uint8_t*, const T*, uint32_t*, T*,      \

@@ -14,6 +14,10 @@ template <typename T>
 void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn = nullptr);
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s);
+// Values at the level-j points of the new grid nxt that are not in act, by
+// DD prediction from the values of act (levels in increasing order).
+template <typename T>
+void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, int j, const Geom& g, cudaStream_t s);
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det,
                         uint8_t* sig, uint8_t* nxt, const Geom& g, cudaStream_t s, const int* dn = nullptr);
@@ -149,16 +153,16 @@ constexpr int kTracePhases = 3 + 3 * 31;
 // for clusters of 2 and 4 blocks, kept per device and precision for
 // krylov_step_blocks and the launch; a cluster size whose clusters a probe
 // launch does not see formed is not used).
-int krylov_step_init(int dev, bool fp32, int* max_blocks);
+int krylov_step_init(int dev, bool fp32, int P, int* max_blocks);
 // Largest cluster size a run created now may use: 4, or the cap set by the
 // environment variable WRC_KRYLOV_CLUSTER (1 or 2), read when called.
 int krylov_cluster_max();
 // Blocks for n active points: one thread per point, capped at max_blocks,
 // padded to a whole number of 4- or 2-block clusters (at most cmax) where
 // that fits.
-int krylov_step_blocks(long long n, int max_blocks, bool fp32, int dev, int cmax);
+int krylov_step_blocks(long long n, int max_blocks, bool fp32, int P, int dev, int cmax);
 // Cluster size (1, 2 or 4) of the launch krylov_step_blocks plans for n points.
-int krylov_step_cluster(long long n, int max_blocks, bool fp32, int dev, int cmax);
+int krylov_step_cluster(long long n, int max_blocks, bool fp32, int P, int dev, int cmax);
 // Cooperative launch on device dev (current); clusters of 4 or 2 (<= cmax) blocks when
 // `blocks` is a multiple within their capacity (their blocks pre-add the dot
 // sums in distributed shared memory).  The first clustered launch per device
@@ -170,9 +174,28 @@ size_t krylov_partials_doubles(int max_blocks);
 // Batched Krylov step: `members` problems (device array of arguments) in one
 // cooperative launch of `blocks` blocks of pt (64, 128 or 256) threads; block
 // b works on problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q+1]-1.
-int krylov_batch_max_blocks(bool fp32, int pt);
+int krylov_batch_max_blocks(bool fp32, int P, int pt);
 template <typename T>
 cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2mem, const int* d_mem_b0,
-                                int members, int blocks, int pt, int max_n, cudaStream_t s);
+                                int members, int blocks, int pt, int P, cudaStream_t s);
+
+// The kernels of one bulk type T and DD half-order P (2, 3, 4), compiled per
+// order in krylov_pP.cu: occupancy of the single-run kernel, co-resident
+// capacity for clusters of CL = 2 or 4 blocks, the single-run launch with
+// clusters of cl blocks (1: plain cooperative launch), and the batched
+// kernel for pt threads per block (64, 128, 256; nullptr otherwise).
+template <typename T, int P>
+struct KrylovKernels {
+    cudaError_t occupancy(int* per);
+    int cluster_capacity(int CL);
+    cudaError_t launch(const KrylovStepArgs& args, int blocks, int cl, cudaStream_t s);
+    const void* batch_kernel(int pt);
+};
+extern template struct KrylovKernels<double, 2>;
+extern template struct KrylovKernels<float, 2>;
+extern template struct KrylovKernels<double, 3>;
+extern template struct KrylovKernels<float, 3>;
+extern template struct KrylovKernels<double, 4>;
+extern template struct KrylovKernels<float, 4>;
 
 }  // namespace wrc

@@ -80,6 +80,7 @@ extern "C" wrc_status wrc_lattice_diagnostics_noalloc(const double* omega_lattic
     g.J = 0;
     g.mask = NJ - 1;
     g.h = 2.0 * 3.141592653589793238462643383279502884 / NJ;
+    g.P = 2;   // the order-4 stencils
     if (launch_diag<double>(omega_lattice, psi_lattice, scratch, counter, out, g, s) != cudaSuccess) return WRC_ERR_CUDA;
     double h2 = g.h * g.h;
     void* args[] = {(void*)&out, (void*)&h2};

@@ -9,8 +9,9 @@ namespace wrc {
 
 // -U Dx q - V Dy q + nu (Dxx + Dyy) q - r q at the active point described by
 // the packed word mw; q is read from the lattice array F (active and ghost
-// values), derivatives with offsets +-s, +-2s (s = 2^(J-j*)) and spacing
-// h_{j*} = s h_J, so 1/(12 h_j) = c1J 2^-sh and 1/(12 h_j^2) = c2J 4^-sh.
+// values), derivatives (order 2P = 4) with offsets +-s, +-2s (s = 2^(J-j*))
+// and spacing h_{j*} = s h_J, so 1/(12 h_j) = c1J 2^-sh and
+// 1/(12 h_j^2) = c2J 4^-sh; higher orders in apply_point_wide.
 // x 2^-k for a positive normal x whose scaled value stays normal (here
 // 1/(12 h_J) and 1/(12 h_J^2) scaled by at most 2^-2J): the exponent field
 // lowered by k, which is exact and equal to ldexp(x, -k), in integer
@@ -20,9 +21,50 @@ __device__ __forceinline__ double pow2_down(double x, int k) {
 }
 __device__ __forceinline__ float pow2_down(float x, int k) { return __int_as_float(__float_as_int(x) - (k << 23)); }
 
-template <typename T, bool CG>
+// Order 2P > 4: the stencils of common.cuh (first derivative with reach
+// 2P - 2, second derivative with reach P) at the point's stencil levels;
+// c1J = 1/(d1 h_J), c2J = 1/(d2 h_J^2) with the stencils' denominators.
+template <typename T, bool CG, int P>
+__device__ __forceinline__ T apply_point_wide(const T* __restrict__ F, uint32_t mw, T U, T V, T nu, T r,
+                                              const Geom& g, T c1J, T c2J) {
+    constexpr int R1 = dd_reach1(P);
+    const int p = meta_pos(mw);
+    const int i = p & g.mask, k = p >> g.L;
+    const int shx = g.J - meta_jx(mw), shy = g.J - meta_jy(mw);
+    const int sx = 1 << shx, sy = 1 << shy;
+    const T* row = F + ((size_t)k << g.L);
+    const T q0 = ldv<T, CG>(row + i);
+    T xp[R1], xm[R1], yp[R1], ym[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        xp[o] = ldv<T, CG>(row + ((i + (o + 1) * sx) & g.mask));
+        xm[o] = ldv<T, CG>(row + ((i - (o + 1) * sx) & g.mask));
+        yp[o] = ldv<T, CG>(F + ((size_t)((k + (o + 1) * sy) & g.mask) << g.L) + i);
+        ym[o] = ldv<T, CG>(F + ((size_t)((k - (o + 1) * sy) & g.mask) << g.L) + i);
+    }
+    const T c1x = pow2_down(c1J, shx), c1y = pow2_down(c1J, shy);
+    const T c2x = pow2_down(c2J, 2 * shx), c2y = pow2_down(c2J, 2 * shy);
+    T dx = T(dd_d1(P, 1)) * (xp[0] - xm[0]), dy = T(dd_d1(P, 1)) * (yp[0] - ym[0]);
+#pragma unroll
+    for (int o = 1; o < R1; ++o) {
+        dx += T(dd_d1(P, o + 1)) * (xp[o] - xm[o]);
+        dy += T(dd_d1(P, o + 1)) * (yp[o] - ym[o]);
+    }
+    T dxx = T(dd_d2(P, P)) * (xp[P - 1] + xm[P - 1]), dyy = T(dd_d2(P, P)) * (yp[P - 1] + ym[P - 1]);
+#pragma unroll
+    for (int o = P - 2; o >= 0; --o) {
+        dxx += T(dd_d2(P, o + 1)) * (xp[o] + xm[o]);
+        dyy += T(dd_d2(P, o + 1)) * (yp[o] + ym[o]);
+    }
+    dxx += T(dd_d2(P, 0)) * q0;
+    dyy += T(dd_d2(P, 0)) * q0;
+    return -U * (dx * c1x) - V * (dy * c1y) + nu * (dxx * c2x + dyy * c2y) - r * q0;
+}
+
+template <typename T, bool CG, int P = 2>
 __device__ __forceinline__ T apply_point(const T* __restrict__ F, uint32_t mw, T U, T V, T nu, T r, const Geom& g,
                                          T c1J, T c2J) {
+    if constexpr (P != 2) return apply_point_wide<T, CG, P>(F, mw, U, V, nu, r, g, c1J, c2J);
     const int p = meta_pos(mw);
     const int i = p & g.mask, k = p >> g.L;
     const int shx = g.J - meta_jx(mw), shy = g.J - meta_jy(mw);

@@ -172,15 +172,18 @@ void pick_shape(const wrc_server* S, BatchCtx& C, const std::vector<wrc_run*>& r
             ept = tept;
         }
     }
-    if ((int)runs.size() > krylov_batch_max_blocks(C.fp32, pt)) pt = 64;
+    if ((int)runs.size() > krylov_batch_max_blocks(C.fp32, C.P, pt)) pt = 64;
     C.pt = pt;
     C.ept = ept;
 }
 
 void serve(wrc_server* S) {
     cudaSetDevice(S->device);
-    BatchCtx ctx[2];
-    bool ctx_ok[2] = {false, false};
+    // one batch context per (precision, DD order): group g = 3 fp32 + (p - 2)
+    constexpr int kGroups = 6;
+    BatchCtx ctx[kGroups];
+    bool ctx_ok[kGroups] = {false, false, false, false, false, false};
+    auto group_of = [](const wrc_config& c) { return 3 * (c.prec == WRC_MIXED ? 1 : 0) + ((c.p == 0 ? 2 : c.p) - 2); };
     std::vector<Request*> res;   // resident runs, in admission order
     bool hold = false;           // device out of memory: admit nothing until a run leaves
     unsigned rr = 0;
@@ -221,11 +224,11 @@ void serve(wrc_server* S) {
         // create and initialise the admitted runs
         for (size_t a = 0; a < admit.size(); ++a) {
             Request* q = admit[a];
-            const int g = q->cfg.prec == WRC_MIXED ? 1 : 0;
+            const int g = group_of(q->cfg);
             wrc_status st = WRC_OK;
             std::string msg;
             if (!ctx_ok[g]) {
-                st = batch_init(ctx[g], nullptr, kServerStreams, g == 1);
+                st = batch_init(ctx[g], nullptr, kServerStreams, g >= 3, 2 + g % 3);
                 if (st == WRC_OK) ctx_ok[g] = true;
                 else msg = ctx[g].err;
             }
@@ -290,11 +293,11 @@ void serve(wrc_server* S) {
                 stepped = true;
             }
         } else {
-            for (int g = 0; g < 2; ++g) {
+            for (int g = 0; g < kGroups; ++g) {
                 std::vector<wrc_run*> runs;
                 std::vector<Request*> who;
                 for (Request* q : res)
-                    if ((q->cfg.prec == WRC_MIXED ? 1 : 0) == g && run_steps(q->run) < q->nsteps) {
+                    if (group_of(q->cfg) == g && run_steps(q->run) < q->nsteps) {
                         runs.push_back(q->run);
                         who.push_back(q);
                     }
@@ -370,7 +373,7 @@ void serve(wrc_server* S) {
         left.swap(S->queue);
     }
     for (Request* q : left) finish(S, q, false, WRC_ERR_STATE, "server stopped");
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < kGroups; ++g)
         if (ctx_ok[g]) batch_free(ctx[g]);
 }
 
@@ -406,8 +409,8 @@ wrc_status wrc_server_create(const wrc_server_config* cfg, wrc_server** out) {
     if (!(cfg->hbm_budget_bytes > 0) || !std::isfinite(cfg->hbm_budget_bytes)) return bad("hbm_budget_bytes must be > 0");
     if (cfg->policy == WRC_SERVE_BATCHED) {
         // every resident run needs one block of the batched launch at least
-        for (int f = 0; f < 2; ++f) {
-            const int lim = krylov_batch_max_blocks(f == 1, 64);
+        for (int f = 0; f < 2 * 3; ++f) {
+            const int lim = krylov_batch_max_blocks(f >= 3, 2 + f % 3, 64);
             if (lim <= 0) {
                 g_srv_create_error = "batched Krylov kernel occupancy query failed";
                 return WRC_ERR_CUDA;

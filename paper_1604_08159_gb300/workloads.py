@@ -33,6 +33,7 @@ class RunParams:
     s_apriori: float = 0.0
     rayleigh_r: float = 0.0
     prec: int = PREC_FP64
+    p: int = 2              # half the DD order 2p (2p = 4, 6, 8)
 
     @property
     def NJ(self) -> int:

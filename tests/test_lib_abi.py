@@ -54,6 +54,14 @@ def test_create_rejects_invalid_config_without_gpu(lib, field, value, msg):
     assert msg in lib.wrc_last_error(None).decode()
 
 
+@pytest.mark.parametrize("order", [1, 5, -1])
+def test_create_rejects_unsupported_dd_order(lib, order):
+    cfg = B.WrcConfig(16, 3, 20, 0, 0, order, 1e-3, 5000.0, 0.0, 0.0, 0.0, 1e-2)
+    h = ctypes.c_void_p()
+    assert lib.wrc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    assert b"DD order" in lib.wrc_last_error(None)
+
+
 def test_create_rejects_oversized_lattice(lib):
     cfg = B.WrcConfig(32, 8, 20, 0, 0, 0, 1e-3, 5000.0, 0.0, 0.0, 0.0, 1e-2)
     h = ctypes.c_void_p()
