@@ -528,9 +528,11 @@ def run_reference(args):
         return 0
     wl = workload_for(0, args.workload)
     warm = min(args.warmup, 1)
-    # one oracle step of the 1024^2 pair takes ~1.3 s on the host cores: the
-    # sample is capped at 60 steps so that the run ends within a few minutes
-    nsteps = max(1, min(args.steps, REFERENCE_MAX_STEPS))
+    # one oracle step of the 1024^2 pair takes ~1.3 s on the host cores (of
+    # the 4096^2 workload ~40-80 s): the sample is capped at 60 steps, and at
+    # 2 steps at 4096^2, so that the run ends within a few minutes
+    cap = REFERENCE_MAX_STEPS if wl.params.NJ < 4096 else 2
+    nsteps = max(1, min(args.steps, cap))
     val, wall, cores, upd = time_oracle(wl, nsteps, warmup=warm)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -615,7 +617,11 @@ def run_ours(args):
     run.profile(False)
     peak, peak_src = hbm_peak()
     sec = rec["ms"] * 1e-3
-    achieved_gbs = rec["bytes"] / sec / 1e9 if sec > 0 else 0.0
+    es = 4.0 if p.prec == W.PREC_MIXED else 8.0
+    # the library counts 8-byte words; the mixed mode's basis and stencil
+    # vectors are 4 bytes (the byte model's half)
+    kbytes = rec["bytes"] * es / 8.0
+    achieved_gbs = kbytes / sec / 1e9 if sec > 0 else 0.0
     achieved_gflops = rec["flops"] / sec / 1e9 if sec > 0 else 0.0
     cluster = run.krylov_form()
 
@@ -656,12 +662,12 @@ def run_ours(args):
         lrec = run.profile_record()
         run.profile(False)
         lsec = lrec["ms"] * 1e-3
-        lgbs = lrec["bytes"] / lsec / 1e9 if lsec > 0 else 0.0
+        lgbs = lrec["bytes"] * es / 8.0 / lsec / 1e9 if lsec > 0 else 0.0
         na_late = l_upd / args.steps
         late = {"after_steps": args.warmup + args.steps + 2 * prof_steps + args.late_steps,
                 "sim_time": run.diagnostics()["t"], "steps": args.steps, "value": l_upd / (l_ms * 1e-3),
                 "unit": UNIT, "ms_per_step": l_ms / args.steps, "mean_active_points": na_late,
-                "krylov_working_set_bytes": (p.m + 1) * 8.0 * na_late,
+                "krylov_working_set_bytes": (p.m + 1) * es * na_late,
                 "roofline": {"bound": "hbm", "achieved": lgbs, "peak": peak, "unit": "GB/s", "frac": lgbs / peak,
                              "avg_launch_us": 1e3 * lrec["ms"] / max(1, lrec["launches"])}}
 
@@ -692,6 +698,25 @@ def run_ours(args):
                "h2d_bytes_per_step": int(32 * v.n / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps)}
 
+    # the mixed mode's error against FP64: the same workload advanced the same
+    # steps from its initial condition in both precisions on the GPU (the
+    # FP64 path is held to 1e-10 of the oracle by the parity tests)
+    accuracy = None
+    if p.prec == W.PREC_MIXED and rank == 0:
+        import dataclasses
+        res = []
+        for prec in (W.PREC_MIXED, W.PREC_FP64):
+            with B.Run(dataclasses.replace(p, prec=prec), stream=stream.cuda_stream) as r2:
+                r2.init_vortices(wl.vortices)
+                r2.step(args.steps)
+                r2.sync()
+                res.append(r2.active())
+        rel, flips = compare_results(res[0][0], res[0][1], res[1][0], res[1][1])
+        accuracy = {"steps": args.steps, "rel_l2_vs_fp64": rel, "grid_differences": flips,
+                    "grid_diff_frac": flips / max(1, res[1][0].size),
+                    "measure": "omega after the same steps from the same initial condition, mixed against FP64 "
+                               "(both on the GPU), over the points active in both"}
+
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(args)
@@ -710,9 +735,10 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cval, cwall, cores, cupd = time_oracle(wl, args.cpu_steps)
+            csteps = args.cpu_steps if args.cpu_steps is not None else (1 if p.NJ >= 4096 else 2)
+            cval, cwall, cores, cupd = time_oracle(wl, csteps)
             cpu = {"value": cval, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{args.cpu_steps} oracle steps of {wl.name} from t=0 ({cupd} updates, {cwall:.1f} s)"}
+                   "sample": f"{csteps} oracle step(s) of {wl.name} from t=0 ({cupd} updates, {cwall:.1f} s)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev / args.steps, "higher_is_better": True,
@@ -728,9 +754,9 @@ def run_ours(args):
                          "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
                          "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "traffic": krylov_traffic() if args.workload == "fujiwhara_1024" else None,
-                         "bytes_per_launch": rec["bytes"] / max(1, rec["launches"]),
-                         "bytes_model": "8 (m^2 + 9m + 6) bytes per active point (operator applications, fused "
-                                        "Gram-Schmidt passes, combination)",
+                         "bytes_per_launch": kbytes / max(1, rec["launches"]),
+                         "bytes_model": f"{int(es)} (m^2 + 9m + 6) bytes per active point (operator applications, "
+                                        "fused Gram-Schmidt passes, combination)",
                          "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(1, rec["launches"]),
                          "cluster_size": cluster, "target_frac": 0.6,
                          "fp64": {"achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -738,6 +764,7 @@ def run_ours(args):
                                   "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; no measured FP64 peak)",
                                   "flops_per_launch": rec["flops"] / max(1, rec["launches"])}},
             "late": late,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -761,7 +788,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=None,
+                    help="oracle steps of the cpu_baseline sample (default 2, 1 at 4096^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fujiwhara_1024")

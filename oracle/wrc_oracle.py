@@ -66,6 +66,11 @@ What each function follows
 ``arnoldi_phi1``           Abstract / Sec. 2.1: projection of the discrete system
                            onto a Krylov subspace (exponential-Euler reading).
 ``step``                   One full time step followed by grid adaptation.
+``jacobian_operator``, ``step_rosenbrock``
+                           Sec. 1 / 2.1 (the Krylov projection with the full
+                           Jacobian, JFNK-style): the exponential
+                           Rosenbrock-Euler step, a Poisson solve per Krylov
+                           vector; the subgrid forcing held at t^n (reading).
 ``scalar_operator``, ``scalar_init``, ``step_with_scalar``
                            Sec. "Transport of water vapor as a passive scalar":
                            the vapour mixing ratio r_v carried by the flow,
@@ -100,7 +105,7 @@ __all__ = [
     "vortex_field", "Frozen", "freeze", "apply_operator", "arnoldi_phi1",
     "phi1_augmented", "adapt", "initial_state", "state_from_field", "step",
     "diagnostics", "BREAKDOWN_TOL", "scalar_operator", "adapt_two", "scalar_init",
-    "step_with_scalar",
+    "step_with_scalar", "vorticity_gradient", "jacobian_operator", "step_rosenbrock", "advance",
 ]
 
 # Happy-breakdown test of the Arnoldi process: stop when the new direction is
@@ -125,6 +130,7 @@ class Config:
     s_apriori: float = 0.0
     rayleigh_r: float = 0.0
     p: int = 2           # DD order 2p (Sec. 2.4): 2p = 4, 6, 8 or 10
+    scheme: str = "frozen"   # "frozen" (exponential Euler, A_n frozen) or "rosenbrock"
 
     @property
     def NJ(self) -> int:
@@ -793,6 +799,57 @@ def step(cfg: Config, st: State):
     new[st.active] = om + inc
     A2, om2, _ = adapt(cfg, st.active, new)
     return State(A2, om2, st.t + cfg.dt, st.nstep + 1), info
+
+
+def vorticity_gradient(cfg: Config, fz: Frozen, omega: np.ndarray):
+    """D_x omega, D_y omega at the active points: the collocation derivatives
+    of Sec. 2.5 at each point's stencil level, ghost values from R(omega)
+    (the gradient the advection term of A_n omega uses)."""
+    R = reconstruct(omega, fz.A, cfg.J, cfg.p)
+    Dx, Dy, _, _ = adaptive_derivatives(R, fz.A, fz.jx, fz.jy, cfg.J, cfg.h, cfg.p)
+    return Dx[fz.A], Dy[fz.A]
+
+
+def jacobian_operator(cfg: Config, fz: Frozen, dwx: np.ndarray, dwy: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """J_n q = A_n q - U[q] D_x omega_n - V[q] D_y omega_n at the active points:
+    the derivative of the right-hand side F(omega) = -U(omega) . grad omega
+    + nu_eff lap omega - r omega + g at omega_n in the direction q, with
+    U[q] = D_y psi[q], V[q] = -D_x psi[q] the velocity of q itself (its
+    reconstruction R(q) on the finest lattice, the streamfunction solve, the
+    finest-lattice stencils; a Poisson solve per application).  The subgrid
+    forcing g is held at t^n (a reading: its derivative is left out)."""
+    aq = apply_operator(cfg, fz, q)
+    Q = np.zeros_like(fz.R)
+    Q[fz.A] = q
+    RQ = reconstruct(Q, fz.A, cfg.J, cfg.p)
+    psi_q = streamfunction(RQ, cfg.h, cfg.p)
+    Uq, Vq = velocity(psi_q, cfg.h, cfg.p)
+    a = fz.A
+    return aq - Uq[a] * dwx - Vq[a] * dwy
+
+
+def step_rosenbrock(cfg: Config, st: State):
+    """One exponential Rosenbrock-Euler step (the full-Jacobian form of the
+    Krylov projection, Sec. 1 and 2.1):
+    omega^{n+1} = omega^n + dt phi_1(dt J_n) F(omega^n),
+    F(omega^n) = A_n omega^n + g_n (the same b as the frozen step), J_n the
+    Jacobian of ``jacobian_operator``; second order in time where g is
+    absent.  Followed by grid adaptation.  Returns (new state, StepInfo)."""
+    fz = freeze(cfg, st.active, st.omega)
+    om = st.omega[st.active]
+    b = apply_operator(cfg, fz, om) + fz.g[st.active]
+    dwx, dwy = vorticity_gradient(cfg, fz, st.omega)
+    inc, info = arnoldi_phi1(lambda q: jacobian_operator(cfg, fz, dwx, dwy, q), b, cfg.m, cfg.dt)
+    new = np.zeros_like(st.omega)
+    new[st.active] = om + inc
+    A2, om2, _ = adapt(cfg, st.active, new)
+    return State(A2, om2, st.t + cfg.dt, st.nstep + 1), info
+
+
+def advance(cfg: Config, st: State):
+    """One step of the scheme cfg.scheme: ``step`` (frozen linearisation) or
+    ``step_rosenbrock`` (full Jacobian)."""
+    return step_rosenbrock(cfg, st) if cfg.scheme == "rosenbrock" else step(cfg, st)
 
 
 def diagnostics(cfg: Config, st: State) -> dict:
