@@ -58,6 +58,19 @@ typedef enum {
 } wrc_status;
 
 typedef enum { WRC_FP64 = 0, WRC_MIXED = 1 } wrc_precision;
+/* Time integration (Sec. 1 and 2.1, the Krylov projection of the step):
+ *  WRC_SCHEME_FROZEN      exponential Euler with the linearisation frozen at
+ *                         t^n, omega^{n+1} = omega^n + dt phi_1(dt A_n)(A_n omega^n + g_n)
+ *                         (first order in time; one persistent kernel per step)
+ *  WRC_SCHEME_ROSENBROCK  exponential Rosenbrock-Euler with the Jacobian of the
+ *                         advection, omega^{n+1} = omega^n + dt phi_1(dt J_n) F(omega^n),
+ *                         J_n q = A_n q - U[q] . grad omega^n with U[q] the
+ *                         velocity of q's own streamfunction (a reconstruction
+ *                         and a Poisson solve per Krylov vector; second order in
+ *                         time without subgrid forcing, which is held at t^n);
+ *                         the Arnoldi process runs as host-driven launches.
+ *                         wrc_step only (an ensemble or the server refuses it). */
+typedef enum { WRC_SCHEME_FROZEN = 0, WRC_SCHEME_ROSENBROCK = 1 } wrc_scheme;
 typedef enum { WRC_SGS_OFF = 0, WRC_SGS_APRIORI = 1, WRC_SGS_DYNAMIC = 2 } wrc_sgs;
 typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
                WRC_FIELD_V = 3, WRC_FIELD_NUT = 4 } wrc_field;
@@ -80,10 +93,12 @@ typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
  *  cs        Smagorinsky constant C_s (Eq. 5), filter width Delta = h_J
  *  s_apriori the constant |S| used when sgs == WRC_SGS_APRIORI
  *  rayleigh_r linear damping coefficient r (Sec. 2.3), >= 0
- *  dt        time step, > 0                                            */
+ *  dt        time step, > 0
+ *  scheme    wrc_scheme (0: frozen linearisation)                       */
 typedef struct {
     int32_t n0, J, krylov_m, sgs, prec, p;
     double eps, re, cs, s_apriori, rayleigh_r, dt;
+    int32_t scheme, reserved;   /* wrc_scheme; reserved must be 0 */
 } wrc_config;
 
 /* Create a run on the current CUDA device, bound to `cuda_stream`

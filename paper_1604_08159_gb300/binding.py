@@ -29,7 +29,8 @@ STAGES = ("reconstruct", "poisson", "velocity", "sgs", "krylov", "adapt", "host"
 class WrcConfig(ctypes.Structure):
     _fields_ = [("n0", c_int32), ("J", c_int32), ("krylov_m", c_int32), ("sgs", c_int32),
                 ("prec", c_int32), ("p", c_int32), ("eps", c_double), ("re", c_double),
-                ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double)]
+                ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double),
+                ("scheme", c_int32), ("reserved", c_int32)]
 
 
 class WrcServerConfig(ctypes.Structure):
@@ -44,6 +45,7 @@ class WrcRequestInfo(ctypes.Structure):
 
 
 SERVE_BATCHED, SERVE_FIFO = 0, 1
+SCHEME_FROZEN, SCHEME_ROSENBROCK = 0, 1
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 # name -> (restype, argtypes); the list of entry points of include/wrc.h
@@ -159,7 +161,8 @@ def _flag(*ptrs):
 def make_config(params) -> WrcConfig:
     """WrcConfig from a ``workloads.RunParams``-like object."""
     return WrcConfig(params.n0, params.J, params.m, params.sgs, params.prec, getattr(params, "p", 2), params.eps,
-                     params.re, params.cs, params.s_apriori, params.rayleigh_r, params.dt)
+                     params.re, params.cs, params.s_apriori, params.rayleigh_r, params.dt,
+                     getattr(params, "scheme", 0), 0)
 
 
 # ---- entry points -------------------------------------------------------------

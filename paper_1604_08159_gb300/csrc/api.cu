@@ -187,6 +187,11 @@ struct wrc_run {
     bool scalar = false;
     double kappa = 0.0;
     DevBuf rv[2], Lr, kr;
+
+    // exponential Rosenbrock step (wrc_config.scheme): U[q], V[q], D_x omega,
+    // D_y omega at the active points (4 x cap, bulk type), the reductions'
+    // partial sums, and coefficients / scales
+    DevBuf jac, rbpart, rbsmall;
 };
 
 namespace {
@@ -255,6 +260,7 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     CK(R->ga.grow(be, 0, s));
     CK(R->w.grow(be, 0, s));
     CK(R->tmp.grow(sizeof(double) * (size_t)c, 0, s));   // doubles: conversions and queries
+    if (R->cfg.scheme == WRC_SCHEME_ROSENBROCK) CK(R->jac.grow(4 * be, 0, s));
     // the basis is rebuilt every step; its leading dimension changes with c
     R->basis.release(s);
     CK(R->basis.grow(be * (size_t)(m + 1), 0, s));
@@ -682,6 +688,9 @@ wrc_status trace_reset(wrc_run* R, int nb) {
     return WRC_OK;
 }
 
+template <typename T>
+wrc_status krylov_rosenbrock(wrc_run* R);
+
 // Arnoldi + phi_1 + update for the frozen linearisation (L holds R(omega)),
 // one cooperative launch.
 template <typename T>
@@ -702,12 +711,103 @@ wrc_status krylov(wrc_run* R) {
         e0 = (int)R->ev_used.size() * 2;
         CK(cudaEventRecord(R->ev_pool[e0], s));
     }
-    CK(launch_krylov_step<T>(A, blocks, s, R->device, R->cluster_max));
+    if (R->cfg.scheme == WRC_SCHEME_ROSENBROCK) TRY(krylov_rosenbrock<T>(R));
+    else CK(launch_krylov_step<T>(A, blocks, s, R->device, R->cluster_max));
     if (R->profiling) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
         R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
     }
     if (R->scalar) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s, R->device, R->cluster_max));
+    return WRC_OK;
+}
+
+// The exponential Rosenbrock-Euler step (WRC_SCHEME_ROSENBROCK; Sec. 1 and
+// 2.1 with the full Jacobian of the advection): after the freeze (L holds
+// R(omega), U, V and g at the active points), D omega at the active points,
+// b = A_n omega + g, then m Arnoldi steps, each applying J_n to q_j -- R(q_j)
+// on the lattice by the inverse transform, psi[q_j] by the Poisson solve,
+// U[q_j], V[q_j] at the active points -- followed by classical Gram-Schmidt
+// twice with FP64 inner products; phi_1 and the update.  Launches only (no
+// host synchronisation); a breakdown is decided on the device.
+template <typename T>
+wrc_status krylov_rosenbrock(wrc_run* R) {
+    const cudaStream_t s = R->st;
+    const long long n = R->n_active;
+    const int m = R->cfg.krylov_m;
+    const Geom& g = R->g;
+    const uint32_t* meta = R->meta[R->cur].as<uint32_t>();
+    CK(R->jac.grow(4 * R->es * (size_t)R->cap, 0, s));
+    CK(R->rbpart.grow(sizeof(double) * kRbPartBlocks * kRbPartWidth, 0, s));
+    CK(R->rbsmall.grow(sizeof(double) * 64, 0, s));
+    T* jb = R->jac.as<T>();
+    RbArgs a{};
+    a.g = g;
+    a.meta = meta;
+    a.n = (int)n;
+    a.L = R->L;
+    a.Lq = R->Lq;
+    a.Ua = R->Ua.p;
+    a.Va = R->Va.p;
+    a.Uq = jb;
+    a.Vq = jb + R->cap;
+    a.dwx = jb + 2 * R->cap;
+    a.dwy = jb + 3 * R->cap;
+    a.w = R->w.p;
+    a.basis = R->basis.p;
+    a.ld = R->cap;
+    a.omega = R->omega[R->cur].p;
+    a.part = R->rbpart.as<double>();
+    a.coef = R->rbsmall.as<double>();
+    a.sc = a.coef + 32;
+    a.H = R->K.H;
+    a.y = R->K.y;
+    a.beta = R->K.beta;
+    a.kstop = R->K.kstop;
+    a.flags = R->K.flags;
+    a.m = m;
+    a.dt = R->cfg.dt;
+    a.tol = kBreakdownTol;
+    a.nu = nu_eff(R);
+    a.r = R->cfg.rayleigh_r;
+    a.c1J = 1.0 / (dd_d1den(g.P) * g.h);
+    a.c2J = 1.0 / (dd_d2den(g.P) * g.h * g.h);
+    T* Lq = (T*)R->Lq;
+    T* Uq = (T*)a.Uq;
+    T* Vq = (T*)a.Vq;
+    double* scr = R->fp32 ? lattice_scratch(R) : nullptr;
+    if (R->fp32 && !scr) return fail(R, WRC_ERR_OOM, "lattice scratch");
+    CK(cudaMemsetAsync(R->K.H, 0, sizeof(double) * (m + 1) * m, s));
+    CK(rb_gradient<T>(a, s));
+    // b = A_n omega + g = F(omega^n), then beta and v_0
+    launch_matvec<T>((const T*)R->L, meta, n, R->Ua.as<T>(), R->Va.as<T>(),
+                     R->cfg.sgs == WRC_SGS_DYNAMIC ? R->ga.as<T>() : nullptr, a.nu, a.r, (T*)a.w, g, nullptr, 0, s);
+    CKL("rosenbrock b");
+    CK(rb_reduce<T>(a, 0, true, 3, -1, s));
+    CK(rb_scale<T>(a, -1, s));
+    for (int j = 0; j < m; ++j) {
+        // R(q_j) on the lattice (its ghost values included), psi[q_j], U[q_j], V[q_j]
+        launch_scatter<T>(meta, R->basis.as<T>() + (size_t)j * R->cap, n, Lq, s);
+        for (int l = 1; l <= g.J; ++l) launch_recon_level<T>(Lq, R->act, l, g, s);
+        if (R->fp32) {
+            // spectral U, V (as in the freeze): U into the second half of the
+            // scratch (the first holds the third FFT work array), V into C1
+            T* Ulat = (T*)(scr + R->N);
+            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s, Ulat, (T*)R->C1, scr);
+            launch_velocity_gather<T>(Ulat, (const T*)R->C1, meta, n, Uq, Vq, s);
+        } else {
+            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s);
+            launch_velocity_active<T>((const T*)R->psi, meta, n, Uq, Vq, g, s);
+        }
+        CKL("rosenbrock jacobian");
+        CK(rb_apply<T>(a, j, s));
+        CK(rb_reduce<T>(a, j + 1, true, 0, j, s));
+        CK(rb_axpy<T>(a, j + 1, j, s));
+        CK(rb_reduce<T>(a, j + 1, false, 1, j, s));
+        CK(rb_axpy<T>(a, j + 1, j, s));
+        CK(rb_reduce<T>(a, 0, true, 2, j, s));
+        CK(rb_scale<T>(a, j, s));
+    }
+    CK(rb_finish<T>(a, s));
     return WRC_OK;
 }
 
@@ -944,7 +1044,7 @@ void free_run(wrc_run* R) {
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
                     &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace, &R->rv[0],
-                    &R->rv[1], &R->Lr, &R->kr})
+                    &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->halo, R->list, R->lat2idx,
@@ -972,6 +1072,8 @@ bool valid_config(const wrc_config* c, std::string& why) {
     if (c->sgs < 0 || c->sgs > 2) { why = "unknown sgs mode"; return false; }
     if (c->prec != WRC_FP64 && c->prec != WRC_MIXED) { why = "unknown precision"; return false; }
     if (c->p != 0 && (c->p < 2 || c->p > kMaxP)) { why = "p (half the DD order) must be 2, 3 or 4 (0: 2)"; return false; }
+    if (c->scheme != WRC_SCHEME_FROZEN && c->scheme != WRC_SCHEME_ROSENBROCK) { why = "unknown scheme"; return false; }
+    if (c->reserved != 0) { why = "reserved must be 0"; return false; }
     if (!(c->eps >= 0) || !(c->re > 0) || !(c->dt > 0) || !(c->rayleigh_r >= 0) || !(c->cs >= 0) ||
         !(c->s_apriori >= 0)) {
         why = "eps, re, dt, rayleigh_r, cs, s_apriori out of range";
@@ -1594,6 +1696,9 @@ wrc_status batch_step_t(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vec
     for (size_t i = 0; i < M; ++i)
         if (runs[i]->scalar) {
             runs[i]->err = "the passive scalar is advanced by wrc_step only";
+            mark(i, WRC_ERR_ARG);
+        } else if (runs[i]->cfg.scheme == WRC_SCHEME_ROSENBROCK) {
+            runs[i]->err = "the exponential Rosenbrock scheme is advanced by wrc_step only";
             mark(i, WRC_ERR_ARG);
         }
     for (size_t i = 0; i < M; ++i) {

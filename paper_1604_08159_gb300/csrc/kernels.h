@@ -105,6 +105,45 @@ cudaError_t launch_diag(const T* R, const T* psi, double* partials, unsigned* co
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, long long n, cudaStream_t s);
 
+// ---- rosenbrock.cu: the exponential Rosenbrock-Euler step (full Jacobian) ---
+// Arguments of its launches (bulk type T behind the void pointers).
+struct RbArgs {
+    Geom g;
+    const uint32_t* meta;   // active points
+    int n;                  // active count
+    const void* L;          // R(omega) on the lattice (in); omega^{n+1} at the active points (out)
+    void* Lq;               // R(q) of the current Krylov vector on the lattice
+    const void *Ua, *Va;    // frozen velocity at the active points
+    void *Uq, *Vq;          // velocity of the current Krylov vector at the active points
+    void *dwx, *dwy;        // D_x omega^n, D_y omega^n at the active points
+    void* w;                // work vector
+    void* basis;            // (m + 1) x ld
+    long long ld;
+    void* omega;            // compact omega, updated in place
+    double* part;           // kRbPartBlocks x (kNV + 1) partial sums
+    double* coef;           // Gram-Schmidt coefficients of a pass
+    double* sc;             // [0] normalisation, [1] |A q_j|^2
+    double* H;              // (m + 1) x m row-major
+    double* y;
+    double* beta;
+    int* kstop;             // Krylov dimension used (set on the device)
+    int* flags;             // bit 0: non-finite value met
+    int m;
+    double dt, tol, nu, r, c1J, c2J;
+};
+constexpr int kRbPartBlocks = 1024;   // blocks of a reduction (partial-sum rows)
+constexpr int kRbPartWidth = 33;      // partial sums per block
+template <typename T> cudaError_t rb_gradient(const RbArgs& a, cudaStream_t s);
+template <typename T> cudaError_t rb_apply(const RbArgs& a, int j, cudaStream_t s);
+// Dot products of w with basis vectors 0..nv-1 (and |w|^2 with self), reduced,
+// then the bookkeeping of `mode` (0: first Gram-Schmidt pass of step j, 1:
+// second pass, 2: norm and breakdown test of step j, 3: beta).
+template <typename T> cudaError_t rb_reduce(const RbArgs& a, int nv, bool self, int mode, int j, cudaStream_t s);
+template <typename T> cudaError_t rb_axpy(const RbArgs& a, int nv, int j, cudaStream_t s);
+template <typename T> cudaError_t rb_scale(const RbArgs& a, int j, cudaStream_t s);
+// phi_1 of the projected matrix and the update of omega (and L).
+template <typename T> cudaError_t rb_finish(const RbArgs& a, cudaStream_t s);
+
 // ---- krylov.cu: the Krylov-projected step as one cooperative kernel ---------
 struct KrylovStepArgs {
     Geom g;

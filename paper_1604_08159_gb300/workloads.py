@@ -16,6 +16,7 @@ from dataclasses import dataclass, field, asdict
 import numpy as np
 
 SGS_OFF, SGS_APRIORI, SGS_DYNAMIC = 0, 1, 2
+SCHEME_FROZEN, SCHEME_ROSENBROCK = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -34,6 +35,7 @@ class RunParams:
     rayleigh_r: float = 0.0
     prec: int = PREC_FP64
     p: int = 2              # half the DD order 2p (2p = 4, 6, 8)
+    scheme: int = 0         # 0: frozen linearisation, 1: exponential Rosenbrock (full Jacobian)
 
     @property
     def NJ(self) -> int:
