@@ -311,17 +311,20 @@ wrc_status rebuild_host(wrc_run* R) {
     R->host_syncs += 1;
     if (R->counts_host[kMaxKeys + 1] & 1) R->nonfinite = true;
     if (R->counts_host[kMaxKeys] != 0) {
-        CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
         const int ev = R->counts_host[kMaxKeys];
+        // bit 4: a clustered launch ran unclustered (its clusters were not
+        // formed): plan the device's later launches without clusters
+        if (ev & 16) krylov_clusters_unformed(R->device);
+        if (ev == 16) {
+            CK(cudaMemsetAsync(R->K.err, 0, sizeof(int), s));
+        } else {
+        CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
         if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded its capacity of " +
                                                       std::to_string(R->rmax) + " terms");
-        if (ev & 8)
-            return fail(R, WRC_ERR_CUDA,
-                        "the Krylov kernel was launched without its thread-block clusters (set WRC_KRYLOV_CLUSTER=1 "
-                        "to use the unclustered kernel)");
         return fail(R, WRC_ERR_TIMEOUT,
                     "a grid barrier wait of the Krylov kernel ran out; the run's state is undefined until it is "
                     "re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
+        }
     }
     const long long na = R->counts_host[0];
     long long off = na, ng = 0;

@@ -176,11 +176,12 @@ struct KrylovStepArgs {
     int* flags;             // [1] bit 0: non-finite value met
     double* part;           // 3 x blocks x 33 partial sums
     unsigned* bar;          // grid barrier: {count, generation}
-    int* err;               // bit 1: a barrier wait ran out; bit 2 (4): row overflow; bit 3 (8): clusters not formed
+    int* err;               // bit 1: a barrier wait ran out; bit 2 (4): row overflow; bit 4 (16): a clustered
+                            // launch did not form its clusters and ran unclustered (not an error)
     int m;
     double dt, tol;
     unsigned long long limit_ns;
-    int refuse;             // test switch: a clustered launch behaves as if its clusters were not formed
+    int refuse;             // test switch: a clustered launch runs as if its clusters were not formed
     // phase trace (profiling; nullptr when off): trace[0] the start of block
     // 0, then per grid barrier p the arrival time of each block b at
     // trace[1 + p (nb + 1) + b] and block 0's release at trace[1 + p (nb + 1) + nb]
@@ -196,6 +197,9 @@ int krylov_step_init(int dev, bool fp32, int P, int* max_blocks);
 // Largest cluster size a run created now may use: 4, or the cap set by the
 // environment variable WRC_KRYLOV_CLUSTER (1 or 2), read when called.
 int krylov_cluster_max();
+// A clustered Krylov launch on device dev ran unclustered (its clusters were
+// not formed): later launches on the device are planned without clusters.
+void krylov_clusters_unformed(int dev);
 // Blocks for n active points: one thread per point, capped at max_blocks,
 // padded to a whole number of 4- or 2-block clusters (at most cmax) where
 // that fits.

@@ -175,11 +175,23 @@ int krylov_step_cluster(long long n, int max_blocks, bool fp32, int P, int dev, 
     return cluster_for(caps_of(dev, fp32, P), krylov_step_blocks(n, max_blocks, fp32, P, dev, cmax), cmax);
 }
 
+void krylov_clusters_unformed(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_caps_mutex);
+    DeviceClusters& D = g_dev[dev];
+    D.checked = true;
+    D.formed[1] = D.formed[2] = false;
+    for (auto& byp : D.caps)
+        for (auto& cc : byp) cc.cap[1] = cc.cap[2] = 0;
+}
+
 // The first clustered launch on a device is checked: the stream is
-// synchronised and, if the kernel refused to run because its clusters were
-// not formed (error bit 8, raised by every block before any barrier or
-// write), clusters are switched off for the device and the same launch is
-// issued again without them.  Later launches are not synchronised.
+// synchronised and, if the kernel found its clusters not formed (it then
+// runs as the unclustered kernel and raises bit 4 of the error word),
+// clusters are switched off for the device.  Later launches are not
+// synchronised; a later launch without its clusters (e.g. under a profiler)
+// runs unclustered all the same and is seen at the step's host
+// synchronisation.
 template <typename T>
 cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStream_t s, int dev, int cmax) {
     const bool fp32 = sizeof(T) == 4;
@@ -198,26 +210,14 @@ cudaError_t launch_krylov_step(const KrylovStepArgs& args, int blocks, cudaStrea
     e = cudaMemcpyAsync(&err, args.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    {
+    if (err & 16) {
+        krylov_clusters_unformed(dev);
+        if (err == 16) e = cudaMemsetAsync(args.err, 0, sizeof(int), s);   // informational only
+    } else {
         std::lock_guard<std::mutex> lk(g_caps_mutex);
-        DeviceClusters& D = g_dev[dev];
-        D.checked = true;
-        if (err & 8) {
-            D.formed[1] = D.formed[2] = false;
-            for (auto& byp : D.caps)
-                for (auto& cc : byp) cc.cap[1] = cc.cap[2] = 0;
-        }
+        g_dev[dev].checked = true;
     }
-    if (!(err & 8)) return cudaSuccess;
-    e = cudaMemsetAsync(args.err, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    // the same grid, unclustered (blocks past the active points carry no
-    // points and add zero partial sums)
-    a.refuse = 0;
-    e = by_order<T>(P, [&](auto K) { return K.launch(a, blocks, 1, s); });
-    if (e != cudaSuccess) return e;
-    note_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 template cudaError_t launch_krylov_step<double>(const KrylovStepArgs&, int, cudaStream_t, int, int);

@@ -129,12 +129,16 @@ __device__ __forceinline__ void group_sums(double (&v)[NV], double* ws) {
 // arrival is a release atomic and the wait polls with acquire loads (GPU
 // scope; the barrier's __syncthreads extend both to the whole block), so the
 // plain loads of the next phase see every block's writes; this measured
-// ~0.2 us faster per barrier than __threadfence around a relaxed atomic.  The wait of each block is bounded by limit_ns; a block that runs
-// out sets bit 1 of *err, and every waiter leaves as soon as *err is
-// non-zero, so the kernel always returns.
+// ~0.2 us faster per barrier than __threadfence around a relaxed atomic.
+// The wait of each block is bounded by limit_ns; a block that runs out sets
+// bit 1 of *err, and every waiter leaves as soon as one of the stopping bits
+// (kErrStop) of *err is set, so the kernel always returns.  Bit 4 (16) only
+// reports an unclustered run of a clustered launch and stops nothing.
 // The barrier spans the nb blocks of one problem (bid = block index within it).
 // With a trace buffer, the arrival of each block and the release of block 0
 // are stamped (phase index `ph`, counted by the caller).
+constexpr int kErrStop = 2 | 4;   // a barrier wait ran out; a ghost row exceeded its capacity
+
 __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, int bid, int nb,
                           unsigned long long* trace = nullptr, int ph = 0) {
     __syncthreads();
@@ -149,7 +153,7 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, 
             unsigned cur;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
             if ((old ^ cur) & 0x80000000u) break;
-            if (*verr) break;
+            if (*verr & kErrStop) break;
             if (gtimer() - t0 > limit_ns) {
                 atomicOr(err, 2);
                 break;
@@ -158,7 +162,7 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long limit_ns, 
         if (trace && ph < kTracePhases && bid == 0) trace[1 + (size_t)ph * (nb + 1) + nb] = gtimer();
     }
     __syncthreads();
-    return *(volatile int*)err == 0;
+    return (*(volatile int*)err & kErrStop) == 0;
 }
 
 // Per-block sums of acc[0..ndots) into dst[0..ndots) and, with NORM, of
@@ -658,10 +662,13 @@ __device__ __forceinline__ void ghost_step(const KrylovStepArgs& A, const T* __r
 // cluster leave their sums in shared memory (s_bp) and the cluster's block
 // 0 adds them in rank order through distributed shared memory and writes
 // the cluster's sums to dst: the grid-wide reduction then reads nb / CL
-// partial sums instead of nb.
+// partial sums instead of nb.  A clustered kernel whose launch did not form
+// its clusters (formed false) writes each block's sums, as the unclustered
+// kernel does.
 template <typename T, int PT, int CL, int P>
 __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool with_z, int bid, int nb, double* dst,
-                                          double (*s_dot)[2 * kNV], double (*s_uz)[2][33], double* s_bp) {
+                                          double (*s_dot)[2 * kNV], double (*s_uz)[2][33], double* s_bp,
+                                          bool formed) {
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
     const T* __restrict__ Lq = (const T*)A.Lq;
@@ -725,7 +732,7 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
     }
     __syncthreads();
     const int nout = with_z ? 2 * j + 2 : j + 1;
-    if constexpr (CL == 1) {
+    if (CL == 1 || !formed) {
         for (int t = threadIdx.x; t < nout; t += PT) {
             double sum = 0.0;
             for (int q = 0; q < PT / 32; ++q) sum += s_dot[q][t];
@@ -764,6 +771,7 @@ __device__ __forceinline__ void step_dots(const KrylovStepArgs& A, int j, bool w
 // of the calls this block did not make (a breakdown, a failed grid barrier,
 // a refusal), so that every block of a cluster passes exactly 2m cluster
 // barriers and none exits while a peer may still read its shared memory.
+// (Only for a launch that formed its clusters.)
 // Each of these waits ends: every block of the cluster reaches its own
 // remaining barriers, all its grid-barrier waits being bounded.
 __device__ __forceinline__ void cluster_finish(int calls, int m) {
@@ -777,11 +785,15 @@ __device__ __forceinline__ void cluster_finish(int calls, int m) {
 }
 
 // The Krylov step of one problem, run by its nb blocks (bid = this block's
-// index among them; with clusters of CL blocks, nb is a multiple of CL and
-// the cluster of block bid is bid / CL).  Returns the number of step_dots
-// calls made (Arnoldi steps j >= 1 entered), for cluster_finish.
+// index among them; with clusters of CL blocks that the launch formed, nb is
+// a multiple of CL and the cluster of block bid is bid / CL; a clustered
+// kernel whose launch did not form them -- formed false -- runs as the
+// unclustered one).  Returns the number of step_dots calls made (Arnoldi
+// steps j >= 1 entered), for cluster_finish.
 template <typename T, int PT, int CL, int P>
-__device__ __forceinline__ int krylov_body(const KrylovStepArgs& A, const int bid, const int nb) {
+__device__ __forceinline__ int krylov_body(const KrylovStepArgs& A, const int bid, const int nb,
+                                           const bool formed = CL > 1) {
+    const int pgroups = (CL > 1 && formed) ? CL : 1;   // blocks per partial-sum row
     const T* __restrict__ Ua = (const T*)A.Ua;
     const T* __restrict__ Va = (const T*)A.Va;
     const T* __restrict__ ga = (const T*)A.ga;
@@ -929,10 +941,11 @@ __device__ __forceinline__ int krylov_body(const KrylovStepArgs& A, const int bi
             const bool last = j == m;   // only the second pass of u is left
             // z = A u and the dots of u and z with q_0 .. q_{j-1}: the values
             // [s, |u|^2, t, u.z] (the last step: [s, |u|^2])
-            step_dots<T, PT, CL, P>(A, j, !last, bid, nb, P0 + (size_t)(bid / CL) * kOutP, s_dot, s_uz, s_bp);
+            step_dots<T, PT, CL, P>(A, j, !last, bid, nb, P0 + (size_t)(bid / pgroups) * kOutP, s_dot, s_uz, s_bp,
+                                    formed);
             calls = j;
             if (!grid_sync(A.bar, A.err, A.limit_ns, bid, nb, A.trace, ph++)) return calls;
-            reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb / CL);
+            reduce_all<PT>(P0, last ? j + 1 : 2 * j + 2, s_h, s_red, nb / pgroups);
             // scalars (every block the same; s_h holds s at 0..j-1, |u|^2 at j,
             // t at j+1..2j and u.z at 2j+1).  One warp's FP64 instruction
             // occupies its SM sub-partition for about 64 cycles on this part,
@@ -1096,17 +1109,21 @@ __device__ __forceinline__ int krylov_body(const KrylovStepArgs& A, const int bi
 
 template <typename T, int PT, int CL, int P>
 __global__ void __launch_bounds__(PT, 1) k_krylov_step(KrylovStepArgs A) {
+    bool formed = false;
     if constexpr (CL > 1) {
-        // the cluster pre-sums read peers' shared memory: refuse to run (every
-        // block, before any barrier) unless the launch formed the clusters
-        if (cooperative_groups::this_cluster().num_blocks() != (unsigned)CL || A.refuse) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, 8);
-            return;
-        }
+        // the cluster pre-sums read peers' shared memory: a launch that did
+        // not form the clusters (some profilers replay cooperative launches
+        // without them; the test switch A.refuse acts as one) runs as the
+        // unclustered kernel -- no peer access, no cluster barrier, one
+        // partial-sum row per block -- and says so in bit 4 (16) of *err
+        formed = cooperative_groups::this_cluster().num_blocks() == (unsigned)CL && !A.refuse;
+        if (!formed && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, 16);
     }
-    const int calls = krylov_body<T, PT, CL, P>(A, blockIdx.x, gridDim.x);
-    if constexpr (CL > 1) cluster_finish(calls, A.m);
-    else (void)calls;
+    const int calls = krylov_body<T, PT, CL, P>(A, blockIdx.x, gridDim.x, formed);
+    if constexpr (CL > 1) {
+        if (formed) cluster_finish(calls, A.m);
+    }
+    (void)calls;
 }
 
 // Batched form: several problems in one cooperative launch; block b works on

@@ -2,7 +2,7 @@
 that run out and report WRC_ERR_TIMEOUT, the time limit of wrc_sync, and
 the fallback of the Krylov launch to its unclustered form when a launch
 path does not form thread-block clusters (made to happen by a test switch
-that has the first clustered launch refuse, exactly as it does when its
+that has the first clustered launch behave exactly as it does when its
 clusters are missing)."""
 
 import json
@@ -136,9 +136,10 @@ print(json.dumps({{"before": before, "after": after, "idx": idx.tolist(), "om": 
 
 def test_unformed_clusters_fall_back_to_unclustered_launch():
     """In a fresh process with the test switch WRC_KRYLOV_TEST_REFUSE=1 the
-    first clustered Krylov launch refuses as it does when its clusters are
-    missing; the library re-issues it without clusters, keeps the device
-    unclustered, and the steps match the oracle and the clustered run."""
+    first clustered Krylov launch behaves as when its clusters are missing:
+    it runs as the unclustered kernel in the same launch and says so; the
+    library keeps the device unclustered from then on, and the steps match
+    the oracle and the clustered run."""
     import torch
     env = dict(os.environ, WRC_KRYLOV_TEST_REFUSE="1")
     env.pop("WRC_KRYLOV_CLUSTER", None)
