@@ -482,6 +482,44 @@ def measure_scalar(args, wl):
             "unit": UNIT + " (both fields advanced per update)"}
 
 
+def measure_exner(args):
+    """The compressible velocity-Exner form (Eqs. 1-2) on the 1024^2 pair
+    (``workloads.fujiwhara_exner_1024``): initial condition from the vortex
+    parameters (the library's Poisson solve for the velocity, pi = 1), 3
+    warm-up steps, then device time per step by CUDA events on the run's
+    stream; an update advances the three fields at one active point."""
+    import torch
+
+    from paper_1604_08159_gb300 import binding as B
+
+    wl = W.fujiwhara_exner_1024()
+    stream = torch.cuda.Stream()
+    with B.Run(wl.params, stream=stream.cuda_stream) as run:
+        run.exner_init_vortices(wl.vortices, wl.extra["pi0"])
+        run.step(3)
+        run.sync()
+        n = max(1, min(args.steps, 10))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        upd = 0
+        ks = []
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            upd += run.stats()["n_active"]
+            run.step(1)
+        e1.record(stream)
+        run.sync()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        kr = run.krylov()
+        _, u, v, p = run.exner()
+    return {"workload": wl.name, "scheme": "rosenbrock (exact Jacobian)", "cpt": wl.params.cpt,
+            "coriolis": wl.params.coriolis, "steps": n, "ms_per_step": ms, "mean_active_points": upd / n,
+            "krylov_k": kr["k"], "max_abs_pi_minus_1": float(abs(p - 1.0).max()),
+            "value": upd / (ms * 1e-3 * n), "unit": UNIT + " (u, v and pi advanced per update)"}
+
+
 KRYLOV_SOURCES = ("csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh", "csrc/kernels.h")
 # DRAM bytes per launch of the Krylov kernel on the 1024^2 pair, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
@@ -726,6 +764,9 @@ def run_ours(args):
     scalar = None
     if not args.no_scalar and rank == 0:
         scalar = measure_scalar(args, wl)
+    exner = None
+    if not args.no_exner and rank == 0:
+        exner = measure_exner(args)
 
     # max over ranks
     t_dev, upd = combine_ranks(dev_ms, upd, "cuda")
@@ -772,6 +813,7 @@ def run_ours(args):
             "serving": serving,
             "ensemble": ensemble,
             "scalar": scalar,
+            "exner": exner,
             "stages": stages,
         }
         print(json.dumps(line), flush=True)
@@ -796,6 +838,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
+    ap.add_argument("--no-exner", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=50)

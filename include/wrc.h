@@ -72,6 +72,11 @@ typedef enum { WRC_FP64 = 0, WRC_MIXED = 1 } wrc_precision;
  *                         wrc_step only (an ensemble or the server refuses it). */
 typedef enum { WRC_SCHEME_FROZEN = 0, WRC_SCHEME_ROSENBROCK = 1 } wrc_scheme;
 typedef enum { WRC_SGS_OFF = 0, WRC_SGS_APRIORI = 1, WRC_SGS_DYNAMIC = 2 } wrc_sgs;
+/* The equations a run solves:
+ *  WRC_MODEL_VORTICITY  the barotropic vorticity-streamfunction form above
+ *  WRC_MODEL_EXNER      the compressible velocity-Exner form of Eqs. 1-2
+ *                       (see "Compressible velocity-Exner form" below) */
+typedef enum { WRC_MODEL_VORTICITY = 0, WRC_MODEL_EXNER = 1 } wrc_model;
 typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
                WRC_FIELD_V = 3, WRC_FIELD_NUT = 4 } wrc_field;
 
@@ -94,11 +99,16 @@ typedef enum { WRC_FIELD_OMEGA = 0, WRC_FIELD_PSI = 1, WRC_FIELD_U = 2,
  *  s_apriori the constant |S| used when sgs == WRC_SGS_APRIORI
  *  rayleigh_r linear damping coefficient r (Sec. 2.3), >= 0
  *  dt        time step, > 0
- *  scheme    wrc_scheme (0: frozen linearisation)                       */
+ *  scheme    wrc_scheme (0: frozen linearisation)
+ *  model     wrc_model (0: vorticity form)
+ *  cpt, coriolis, gx, gy   (WRC_MODEL_EXNER only, else ignored) C = c_p theta_0
+ *            of Eq. 2 (>= 0), the Coriolis parameter f of the f-plane and the
+ *            mean geostrophic wind (G_x, G_y); finite                   */
 typedef struct {
     int32_t n0, J, krylov_m, sgs, prec, p;
     double eps, re, cs, s_apriori, rayleigh_r, dt;
-    int32_t scheme, reserved;   /* wrc_scheme; reserved must be 0 */
+    int32_t scheme, model;      /* wrc_scheme, wrc_model */
+    double cpt, coriolis, gx, gy;
 } wrc_config;
 
 /* Create a run on the current CUDA device, bound to `cuda_stream`
@@ -159,10 +169,10 @@ wrc_status wrc_set_wait_limit(wrc_run* run, double seconds);
  * launch with them, the environment variable WRC_KRYLOV_CLUSTER (1 or 2,
  * read at wrc_create) does not cap them, and the launch path forms them: a
  * probe launch at the device's first wrc_create and the check of the
- * device's first clustered launch (which, if its clusters were not formed,
- * is issued again without them) switch them off for the device otherwise,
+ * device's first clustered launch switch them off for the device otherwise,
  * e.g. under a profiler that replays cooperative launches without
- * clusters. */
+ * clusters; a launch whose clusters were not formed runs as the unclustered
+ * kernel and computes the same step. */
 wrc_status wrc_query_krylov_form(wrc_run* run, int32_t* cluster_size);
 
 /* Sizes of the current grid: active points, ghost points and active points
@@ -323,6 +333,52 @@ wrc_status wrc_scalar_init(wrc_run* run, double kappa, const double* field, int3
  * wrc_query_active (cap >= the active count).  Synchronises.  WRC_ERR_STATE
  * when the scalar is not enabled; WRC_ERR_ARG if cap is too small. */
 wrc_status wrc_query_scalar(wrc_run* run, int32_t* idx_out, double* r_out, int64_t cap, int32_t device_ptr);
+
+/* ---- Compressible velocity-Exner form ---------------------------------------
+ * A run created with model = WRC_MODEL_EXNER holds the velocity (u, v) and
+ * the Exner function pi on the adaptive grid and solves Eqs. 1-2 of the
+ * paper on the f-plane (Sec. 2.2), with Rayleigh friction standing for the
+ * balance of Eq. 4:
+ *     pi_t = -(u pi_x + v pi_y) - pi (u_x + v_y)
+ *     u_t  = -(u u_x + v u_y) - C pi_x + f (v - G_y) - r u + nu_eff lap u
+ *     v_t  = -(u v_x + v v_y) - C pi_y - f (u - G_x) - r v + nu_eff lap v
+ * (Eq. 1 as printed, coefficient one on pi div u; nu_eff = 1/re plus the
+ * constant eddy viscosity of the a-priori Smagorinsky model, Eq. 5; the
+ * dynamic model is not available here).  Linearised about rest it is an
+ * acoustic system with sound speed sqrt(C pi_0): the Krylov projection of the
+ * step (Sec. 2.1) takes its stiff part exactly.  One step is
+ *     U^{n+1} = U^n + dt phi_1(dt M) F(U^n),  U = [u; v; pi] at the active points,
+ * M the exact Jacobian of F (scheme WRC_SCHEME_ROSENBROCK, second order) or
+ * the operator with the coefficients u, v, pi frozen at t^n
+ * (WRC_SCHEME_FROZEN), unweighted l2 inner product over the stacked vector;
+ * no Poisson solve.  The grid adapts to all three fields: the union of their
+ * significant sets (same eps), the adjacent zone, the closure.  FP64 only
+ * (prec = WRC_FP64), wrc_step only (ensembles and the server refuse the
+ * model).  wrc_step, wrc_sync, wrc_query_counts, wrc_query_masks,
+ * wrc_query_stencil_levels, wrc_query_krylov, wrc_query_stats, wrc_profile
+ * (modes 0, 1 and 3), wrc_set_wait_limit and wrc_destroy apply to such a run;
+ * wrc_query_active returns its indices only (omega_out must be NULL); the
+ * other calls of the vorticity form return WRC_ERR_STATE. */
+
+/* Initial condition from sampled lattice fields u, v, pi (NJ*NJ doubles
+ * each, host or device per device_ptr; not kept): the full-lattice transform
+ * of each, their joint thresholding and the adaptation (Eq. 6).  WRC_ERR_ARG
+ * for a NULL field; WRC_ERR_STATE for a vorticity-form run. */
+wrc_status wrc_exner_init(wrc_run* run, const double* u, const double* v, const double* pi, int32_t device_ptr);
+
+/* Initial condition of n Gaussian vortices (as wrc_init_vortices) in the
+ * velocity form: the vorticity sampled on the full lattice, its
+ * streamfunction from the library's Poisson solve (the exact inverse of the
+ * collocation Laplacian), u = D_y psi, v = -D_x psi by the finest-lattice
+ * stencils, pi = pi0 everywhere (pi0 > 0); then as wrc_exner_init. */
+wrc_status wrc_exner_init_vortices(wrc_run* run, int32_t n, const double* xc, const double* yc,
+                                   const double* gamma, const double* s, double pi0);
+
+/* The active lattice indices and u, v, pi at them, in the order of
+ * wrc_query_active (cap >= the active count); any output may be NULL.
+ * Synchronises.  WRC_ERR_STATE for a vorticity-form run. */
+wrc_status wrc_query_exner(wrc_run* run, int32_t* idx_out, double* u_out, double* v_out, double* pi_out,
+                           int64_t cap, int32_t device_ptr);
 
 /* ---- Diagnostics without allocation ------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that

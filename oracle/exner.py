@@ -61,7 +61,7 @@ import numpy as np
 from . import wrc_oracle as W
 
 __all__ = ["ExnerConfig", "ExnerState", "Base", "freeze_exner", "exner_rhs", "exner_linear",
-           "exner_adapt", "exner_initial_state", "exner_step", "stack", "unstack"]
+           "exner_adapt", "exner_initial_state", "exner_vortex_state", "exner_step", "stack", "unstack"]
 
 
 @dataclass
@@ -190,6 +190,17 @@ def exner_initial_state(cfg: ExnerConfig, u, v, pi) -> ExnerState:
     thresholding of the full-lattice transforms)."""
     A, (u2, v2, p2) = exner_adapt(cfg, np.ones(np.shape(u), dtype=bool), [u, v, pi], whole=True)
     return ExnerState(A, u2, v2, p2)
+
+
+def exner_vortex_state(cfg: ExnerConfig, xc, yc, gamma, s, pi0: float) -> ExnerState:
+    """Initial state of Gaussian vortices in the velocity form: the vortex
+    field of Sec. 3.1 sampled on the lattice, its streamfunction (exact
+    inverse of the collocation Laplacian), u = D_y psi, v = -D_x psi on the
+    finest lattice, pi = pi0 everywhere; then the joint thresholding."""
+    om = W.vortex_field(cfg.NJ, xc, yc, gamma, s)
+    psi = W.streamfunction(om, cfg.h, cfg.p)
+    u, v = W.velocity(psi, cfg.h, cfg.p)
+    return exner_initial_state(cfg, u, v, np.full_like(u, float(pi0)))
 
 
 def exner_step(cfg: ExnerConfig, st: ExnerState):

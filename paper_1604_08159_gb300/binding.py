@@ -30,7 +30,8 @@ class WrcConfig(ctypes.Structure):
     _fields_ = [("n0", c_int32), ("J", c_int32), ("krylov_m", c_int32), ("sgs", c_int32),
                 ("prec", c_int32), ("p", c_int32), ("eps", c_double), ("re", c_double),
                 ("cs", c_double), ("s_apriori", c_double), ("rayleigh_r", c_double), ("dt", c_double),
-                ("scheme", c_int32), ("reserved", c_int32)]
+                ("scheme", c_int32), ("model", c_int32), ("cpt", c_double), ("coriolis", c_double),
+                ("gx", c_double), ("gy", c_double)]
 
 
 class WrcServerConfig(ctypes.Structure):
@@ -46,6 +47,7 @@ class WrcRequestInfo(ctypes.Structure):
 
 SERVE_BATCHED, SERVE_FIFO = 0, 1
 SCHEME_FROZEN, SCHEME_ROSENBROCK = 0, 1
+MODEL_VORTICITY, MODEL_EXNER = 0, 1
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 # name -> (restype, argtypes); the list of entry points of include/wrc.h
@@ -63,6 +65,9 @@ SIGNATURES = {
     "wrc_query_active": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_scalar_init": (c_int32, [c_void_p, c_double, c_void_p, c_int32]),
     "wrc_query_scalar": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
+    "wrc_exner_init": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
+    "wrc_exner_init_vortices": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_double]),
+    "wrc_query_exner": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_query_masks": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32]),
     "wrc_query_details": (c_int32, [c_void_p, c_void_p, c_int64, c_int32]),
     "wrc_query_stencil_levels": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
@@ -162,7 +167,8 @@ def make_config(params) -> WrcConfig:
     """WrcConfig from a ``workloads.RunParams``-like object."""
     return WrcConfig(params.n0, params.J, params.m, params.sgs, params.prec, getattr(params, "p", 2), params.eps,
                      params.re, params.cs, params.s_apriori, params.rayleigh_r, params.dt,
-                     getattr(params, "scheme", 0), 0)
+                     getattr(params, "scheme", 0), getattr(params, "model", 0), getattr(params, "cpt", 0.0),
+                     getattr(params, "coriolis", 0.0), getattr(params, "gx", 0.0), getattr(params, "gy", 0.0))
 
 
 # ---- entry points -------------------------------------------------------------
@@ -234,6 +240,22 @@ def wrc_query_scalar(run, idx_out=None, r_out=None, cap: int = 0):
     pi, fi = _ptr(idx_out)
     pr, fr = _ptr(r_out)
     _check("wrc_query_scalar", load().wrc_query_scalar(run, pi, pr, cap, _flag((pi, fi), (pr, fr))), run)
+
+
+def wrc_exner_init(run, u, v, pi):
+    ps = [_ptr(x) for x in (u, v, pi)]
+    _check("wrc_exner_init", load().wrc_exner_init(run, ps[0][0], ps[1][0], ps[2][0], _flag(*ps)), run)
+
+
+def wrc_exner_init_vortices(run, xc, yc, gamma, s, pi0: float):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xc, yc, gamma, s)]
+    _check("wrc_exner_init_vortices",
+           load().wrc_exner_init_vortices(run, arrs[0].size, *[a.ctypes.data for a in arrs], float(pi0)), run)
+
+
+def wrc_query_exner(run, idx_out=None, u_out=None, v_out=None, pi_out=None, cap: int = 0):
+    ps = [_ptr(x) for x in (idx_out, u_out, v_out, pi_out)]
+    _check("wrc_query_exner", load().wrc_query_exner(run, *[p for p, _ in ps], cap, _flag(*ps)), run)
 
 
 def wrc_query_masks(run, active=None, ghost=None, significant=None):
@@ -403,6 +425,22 @@ class Run:
         r = np.zeros(na)
         wrc_query_scalar(self.h, idx, r, na)
         return idx, r
+
+    def exner_init(self, u, v, pi):
+        """Velocity-Exner initial condition from lattice fields u, v, pi."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a for a in (u, v, pi)]
+        wrc_exner_init(self.h, *arrs)
+
+    def exner_init_vortices(self, vortices, pi0=1.0):
+        wrc_exner_init_vortices(self.h, vortices.xc, vortices.yc, vortices.gamma, vortices.s, pi0)
+
+    def exner(self):
+        """(idx, u, v, pi) at the active points of a velocity-Exner run."""
+        na = self.counts()[0]
+        idx = np.zeros(na, dtype=np.int32)
+        u, v, p = np.zeros(na), np.zeros(na), np.zeros(na)
+        wrc_query_exner(self.h, idx, u, v, p, na)
+        return idx, u, v, p
 
     def masks(self):
         n2 = self.NJ * self.NJ

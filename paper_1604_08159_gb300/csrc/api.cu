@@ -192,6 +192,15 @@ struct wrc_run {
     // D_y omega at the active points (4 x cap, bulk type), the reductions'
     // partial sums, and coefficients / scales
     DevBuf jac, rbpart, rbsmall;
+
+    // compressible velocity-Exner form (wrc_config.model = WRC_MODEL_EXNER):
+    // u lives in the first field's slots (omega, L), v in the second's (rv,
+    // Lr, as the passive scalar), pi in pe and Lp; the Krylov vectors stack
+    // the three fields (xbasis (m + 1) x 3 cap, xw 3 cap); Lqx holds the
+    // lattices of a Krylov vector's v and pi parts (Lq its u part), xd the
+    // state's derivatives at the active points (8 x cap)
+    bool exner = false;
+    DevBuf pe[2], Lp, Lqx, xd, xbasis, xw;
 };
 
 namespace {
@@ -250,9 +259,17 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
     CK(R->meta[1 - R->cur].grow(sizeof(uint32_t) * c, 0, s));
     CK(R->omega[R->cur].grow(be, R->es * R->n_active, s));
     CK(R->omega[1 - R->cur].grow(be, 0, s));
-    if (R->scalar) {
+    if (R->scalar || R->exner) {
         CK(R->rv[R->cur].grow(be, R->es * R->n_active, s));
         CK(R->rv[1 - R->cur].grow(be, 0, s));
+    }
+    if (R->exner) {
+        CK(R->pe[R->cur].grow(be, R->es * R->n_active, s));
+        CK(R->pe[1 - R->cur].grow(be, 0, s));
+        CK(R->xd.grow(8 * be, 0, s));
+        CK(R->xw.grow(3 * be, 0, s));
+        R->xbasis.release(s);
+        CK(R->xbasis.grow(3 * be * (size_t)(m + 1), 0, s));
     }
     CK(R->det.grow(be, R->es * R->det_count, s));
     CK(R->Ua.grow(be, 0, s));
@@ -349,8 +366,11 @@ wrc_status rebuild_part2(wrc_run* R) {
     const int nc = 1 - R->cur;
     launch_finalize<T>(R->list, R->cap, R->JJ, (const T*)R->L, R->meta[nc].as<uint32_t>(), R->omega[nc].as<T>(), s,
                        R->counts_dev);
-    if (R->scalar)   // r_v at the new grid from its reconstruction (meta is rewritten identically)
+    if (R->scalar || R->exner)   // r_v (v) at the new grid from its lattice (meta is rewritten identically)
         launch_finalize<T>(R->list, R->cap, R->JJ, R->Lr.as<T>(), R->meta[nc].as<uint32_t>(), R->rv[nc].as<T>(), s,
+                           R->counts_dev);
+    if (R->exner)
+        launch_finalize<T>(R->list, R->cap, R->JJ, R->Lp.as<T>(), R->meta[nc].as<uint32_t>(), R->pe[nc].as<T>(), s,
                            R->counts_dev);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
     launch_ghost_rows(R->list, 0, nullptr, nullptr, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
@@ -465,6 +485,14 @@ wrc_status threshold_marks(wrc_run* R, double eps, bool whole_lattice) {
     if (R->scalar && !whole_lattice)   // the grid adapts to r_v as well: union of the significant sets
         launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, R->Lr.as<T>(), eps, nullptr, R->sig, R->nxt, g,
                               s, R->counts_dev);
+    if (R->exner) {   // the grid adapts to u (L), v (Lr) and pi (Lp): union of the significant sets
+        for (T* F : {R->Lr.as<T>(), R->Lp.as<T>()}) {
+            if (whole_lattice) launch_details_adj<T>(nullptr, R->N, F, eps, nullptr, R->sig, R->nxt, g, s);
+            else
+                launch_details_adj<T>(R->meta[R->cur].as<uint32_t>(), R->cap, F, eps, nullptr, R->sig, R->nxt, g, s,
+                                      R->counts_dev);
+        }
+    }
     for (int j = g.J; j >= 1; --j) launch_closure_level(R->nxt, nullptr, j, g, s);
     CKL("threshold");
     return WRC_OK;
@@ -489,8 +517,10 @@ wrc_status adapt_part1(wrc_run* R) {
     TRY(threshold_marks<T>(R, R->cfg.eps, false));
     TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
     for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>((T*)R->L, R->act, R->nxt, j, R->g, R->st);
-    if (R->scalar)
+    if (R->scalar || R->exner)
         for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>(R->Lr.as<T>(), R->act, R->nxt, j, R->g, R->st);
+    if (R->exner)
+        for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>(R->Lp.as<T>(), R->act, R->nxt, j, R->g, R->st);
     CKL("new values");
     TRY(stage_mark(R, WRC_STAGE_ADAPT));
     return rebuild_part1(R);
@@ -814,16 +844,113 @@ wrc_status krylov_rosenbrock(wrc_run* R) {
     return WRC_OK;
 }
 
+// Arguments of the velocity-Exner launches on the run's current grid.
+ExArgs exner_args(wrc_run* R) {
+    ExArgs a{};
+    a.g = R->g;
+    a.meta = R->meta[R->cur].as<uint32_t>();
+    a.n = (int)R->n_active;
+    a.glist = R->list + R->n_active;
+    a.ng = (int)R->n_ghost;
+    a.row_len = R->row_len.as<int>();
+    a.row_idx = R->row_idx.as<int>();
+    a.row_w = R->row_w.as<double>();
+    a.rmax = R->rmax;
+    a.Lb[0] = (double*)R->L;
+    a.Lb[1] = R->Lr.as<double>();
+    a.Lb[2] = R->Lp.as<double>();
+    a.Lq[0] = (double*)R->Lq;
+    a.Lq[1] = R->Lqx.as<double>();
+    a.Lq[2] = R->Lqx.as<double>() + R->N;
+    a.f[0] = a.f_out[0] = R->omega[R->cur].as<double>();
+    a.f[1] = a.f_out[1] = R->rv[R->cur].as<double>();
+    a.f[2] = a.f_out[2] = R->pe[R->cur].as<double>();
+    a.d = R->xd.as<double>();
+    a.ld = R->cap;
+    a.C = R->cfg.cpt;
+    a.fc = R->cfg.coriolis;
+    a.gx = R->cfg.gx;
+    a.gy = R->cfg.gy;
+    a.r = R->cfg.rayleigh_r;
+    a.nu = nu_eff(R);
+    a.c1J = 1.0 / (dd_d1den(R->g.P) * R->g.h);
+    a.c2J = 1.0 / (dd_d2den(R->g.P) * R->g.h * R->g.h);
+    a.full = R->cfg.scheme == WRC_SCHEME_ROSENBROCK;
+    return a;
+}
+
+// The Krylov part of a velocity-Exner step (Eqs. 1-2): the state's lattices
+// (active and ghost values) and derivatives, b = F(U^n), then the Arnoldi
+// process on the stacked vectors [u; v; pi] (classical Gram-Schmidt twice,
+// FP64 partial sums added in a fixed order, breakdown on the device), one
+// lattice launch and one operator launch per Krylov vector, phi_1 and the
+// update.  FP64 only.
+wrc_status exner_krylov(wrc_run* R) {
+    const cudaStream_t s = R->st;
+    const long long n = R->n_active;
+    const int m = R->cfg.krylov_m;
+    CK(R->rbpart.grow(sizeof(double) * kRbPartBlocks * kRbPartWidth, 0, s));
+    CK(R->rbsmall.grow(sizeof(double) * 64, 0, s));
+    const ExArgs a = exner_args(R);
+    const long long ld3 = 3 * R->cap;
+    RbArgs rb{};
+    rb.n = (int)(3 * n);
+    rb.w = R->xw.p;
+    rb.basis = R->xbasis.p;
+    rb.ld = ld3;
+    rb.part = R->rbpart.as<double>();
+    rb.coef = R->rbsmall.as<double>();
+    rb.sc = rb.coef + 32;
+    rb.H = R->K.H;
+    rb.y = R->K.y;
+    rb.beta = R->K.beta;
+    rb.kstop = R->K.kstop;
+    rb.flags = R->K.flags;
+    rb.m = m;
+    rb.dt = R->cfg.dt;
+    rb.tol = kBreakdownTol;
+    double* const Lb[3] = {a.Lb[0], a.Lb[1], a.Lb[2]};
+    const double* const fs[3] = {a.f[0], a.f[1], a.f[2]};
+    double* const Lq[3] = {a.Lq[0], a.Lq[1], a.Lq[2]};
+    double* const w = R->xw.as<double>();
+    double* const basis = R->xbasis.as<double>();
+    CK(cudaMemsetAsync(R->K.H, 0, sizeof(double) * (m + 1) * m, s));
+    CK(ex_scatter_fields(a, fs, Lb, nullptr, 0, s));
+    CK(ex_base(a, w, s));
+    CK(rb_reduce<double>(rb, 0, true, 3, -1, s));
+    CK(rb_scale<double>(rb, -1, s));
+    for (int j = 0; j < m; ++j) {
+        const double* qj = basis + (size_t)j * ld3;
+        const double* const qp[3] = {qj, qj + n, qj + 2 * n};
+        CK(ex_scatter_fields(a, qp, Lq, R->K.kstop, j, s));
+        CK(ex_apply(a, qj, w, R->K.kstop, j, s));
+        CK(rb_reduce<double>(rb, j + 1, true, 0, j, s));
+        CK(rb_axpy<double>(rb, j + 1, j, s));
+        CK(rb_reduce<double>(rb, j + 1, false, 1, j, s));
+        CK(rb_axpy<double>(rb, j + 1, j, s));
+        CK(rb_reduce<double>(rb, 0, true, 2, j, s));
+        CK(rb_scale<double>(rb, j, s));
+    }
+    CK(rb_phi1(rb, s));
+    CK(ex_combine(a, basis, ld3, R->K.y, R->K.beta, R->cfg.dt, R->K.kstop, s));
+    return WRC_OK;
+}
+
 enum { kPhaseFreeze = 0, kPhaseAdapt1 = 1, kPhaseAdapt2 = 2 };
 
 // One time step: [freeze] -> Krylov launch -> [adapt part 1] -> host sync for
 // the new grid's sizes -> [adapt part 2]; bracketed phases run as CUDA graphs.
 template <typename T>
 wrc_status step_phases(wrc_run* R) {
-    TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
-    R->frozen = true;
-    TRY(stage_mark(R, WRC_STAGE_KRYLOV));
-    TRY(krylov<T>(R));
+    if (R->exner) {
+        TRY(stage_mark(R, WRC_STAGE_KRYLOV));
+        TRY(exner_krylov(R));
+    } else {
+        TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
+        R->frozen = true;
+        TRY(stage_mark(R, WRC_STAGE_KRYLOV));
+        TRY(krylov<T>(R));
+    }
     // L holds omega^{n+1} at the grid points (Lr r_v^{n+1}); threshold, then
     // the values at the new grid's new points
     TRY(run_phase(R, kPhaseAdapt1, [&] { return adapt_part1<T>(R); }));
@@ -858,6 +985,12 @@ wrc_status step_once(wrc_run* R) {
 wrc_status check_ready(wrc_run* R) {
     if (!R) return WRC_ERR_ARG;
     if (!R->init) return fail(R, WRC_ERR_STATE, "run has no initial condition");
+    return WRC_OK;
+}
+
+// Calls of the vorticity form only.
+wrc_status vorticity_only(wrc_run* R, const char* fn) {
+    if (R && R->exner) return fail(R, WRC_ERR_STATE, std::string(fn) + " does not apply to a velocity-Exner run");
     return WRC_OK;
 }
 
@@ -909,6 +1042,14 @@ wrc_status init_field_t(wrc_run* R, const double* omega_lattice, int device_ptr)
     CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
     R->n_active = 0;
     return threshold_current<T>(R, R->cfg.eps, true);
+}
+
+// Velocity-Exner initial condition: u, v, pi on the whole lattice in L, Lr,
+// Lp; the joint thresholding of their full-lattice transforms.
+wrc_status exner_threshold_whole(wrc_run* R) {
+    CK(cudaMemsetAsync(R->act, 1, R->N, R->st));
+    R->n_active = 0;
+    return threshold_current<double>(R, R->cfg.eps, true);
 }
 
 template <typename T>
@@ -1047,7 +1188,8 @@ void free_run(wrc_run* R) {
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
                     &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace, &R->rv[0],
-                    &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall})
+                    &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall, &R->pe[0], &R->pe[1], &R->Lp, &R->Lqx,
+                    &R->xd, &R->xbasis, &R->xw})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->halo, R->list, R->lat2idx,
@@ -1076,7 +1218,16 @@ bool valid_config(const wrc_config* c, std::string& why) {
     if (c->prec != WRC_FP64 && c->prec != WRC_MIXED) { why = "unknown precision"; return false; }
     if (c->p != 0 && (c->p < 2 || c->p > kMaxP)) { why = "p (half the DD order) must be 2, 3 or 4 (0: 2)"; return false; }
     if (c->scheme != WRC_SCHEME_FROZEN && c->scheme != WRC_SCHEME_ROSENBROCK) { why = "unknown scheme"; return false; }
-    if (c->reserved != 0) { why = "reserved must be 0"; return false; }
+    if (c->model != WRC_MODEL_VORTICITY && c->model != WRC_MODEL_EXNER) { why = "unknown model"; return false; }
+    if (c->model == WRC_MODEL_EXNER) {
+        if (c->prec != WRC_FP64) { why = "the velocity-Exner form runs in FP64 only"; return false; }
+        if (c->sgs == WRC_SGS_DYNAMIC) { why = "the velocity-Exner form takes the a-priori subgrid model only"; return false; }
+        if (!(c->cpt >= 0) || !std::isfinite(c->cpt) || !std::isfinite(c->coriolis) || !std::isfinite(c->gx) ||
+            !std::isfinite(c->gy)) {
+            why = "cpt must be finite and >= 0; coriolis, gx, gy finite";
+            return false;
+        }
+    }
     if (!(c->eps >= 0) || !(c->re > 0) || !(c->dt > 0) || !(c->rayleigh_r >= 0) || !(c->cs >= 0) ||
         !(c->s_apriori >= 0)) {
         why = "eps, re, dt, rayleigh_r, cs, s_apriori out of range";
@@ -1116,6 +1267,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     R->g.P = cfg->p == 0 ? 2 : cfg->p;
     R->rmax = dd_row_max(R->g.P);
     R->N = (long long)NJ * NJ;
+    R->exner = cfg->model == WRC_MODEL_EXNER;
     const long long N = R->N;
     const int m = cfg->krylov_m;
     const int nblk = (int)((N + kTile - 1) / kTile);
@@ -1171,6 +1323,16 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
         free_run(R);
         return WRC_ERR_OOM;
     }
+    if (R->exner) {   // lattices of v and pi, and of a Krylov vector's v and pi parts
+        cudaError_t ex = R->Lr.grow(sizeof(double) * N, 0, R->st);
+        if (ex == cudaSuccess) ex = R->Lp.grow(sizeof(double) * N, 0, R->st);
+        if (ex == cudaSuccess) ex = R->Lqx.grow(2 * sizeof(double) * N, 0, R->st);
+        if (ex != cudaSuccess) {
+            g_create_error = std::string("allocation failed: ") + cudaGetErrorString(ex);
+            free_run(R);
+            return ex == cudaErrorMemoryAllocation ? WRC_ERR_OOM : WRC_ERR_CUDA;
+        }
+    }
     if (poisson_plan_init(R->plan, R->g, R->fp32, R->st) != 0) {
         g_create_error = "FFT/expm kernel set-up failed";
         free_run(R);
@@ -1188,6 +1350,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
 wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const double* yc, const double* gamma,
                              const double* s) {
     if (!R) return WRC_ERR_ARG;
+    TRY(vorticity_only(R, "wrc_init_vortices"));
     if (n < 1 || n > WRC_MAX_VORTICES || !xc || !yc || !gamma || !s)
         return fail(R, WRC_ERR_ARG, "need 1..WRC_MAX_VORTICES vortices and four host arrays");
     double prm[4 * WRC_MAX_VORTICES];
@@ -1217,6 +1380,7 @@ wrc_status wrc_init_vortices(wrc_run* R, int32_t n, const double* xc, const doub
 
 wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
+    TRY(vorticity_only(R, "wrc_init_field"));
     if (!omega_lattice) return fail(R, WRC_ERR_ARG, "omega_lattice is NULL");
     if (R->scalar) R->layout += 1;
     R->scalar = false;
@@ -1229,6 +1393,7 @@ wrc_status wrc_init_field(wrc_run* R, const double* omega_lattice, int32_t devic
 
 wrc_status wrc_set_grid(wrc_run* R, const uint8_t* active, const double* omega_lattice, int32_t device_ptr) {
     if (!R) return WRC_ERR_ARG;
+    TRY(vorticity_only(R, "wrc_set_grid"));
     if (!active || !omega_lattice) return fail(R, WRC_ERR_ARG, "NULL input");
     if (R->scalar) R->layout += 1;
     R->scalar = false;
@@ -1239,6 +1404,7 @@ wrc_status wrc_set_grid(wrc_run* R, const uint8_t* active, const double* omega_l
 
 wrc_status wrc_threshold(wrc_run* R, double eps) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_threshold"));
     if (!(eps >= 0)) return fail(R, WRC_ERR_ARG, "eps must be >= 0");
     R->cfg.eps = eps;
     R->layout += 1;   // eps is baked into the captured thresholding phase
@@ -1299,6 +1465,7 @@ wrc_status wrc_query_counts(wrc_run* R, int64_t* n_active, int64_t* n_ghost, int
 wrc_status wrc_query_active(wrc_run* R, int32_t* idx_out, double* omega_out, int64_t cap, int32_t device_ptr) {
     TRY(check_ready(R));
     if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
+    if (omega_out) TRY(vorticity_only(R, "wrc_query_active with omega_out"));
     const long long n = R->n_active;
     if (omega_out) {
         if (R->fp32) TRY(out_as_double<float>(R, omega_out, R->omega[R->cur].as<float>(), n, device_ptr, R->tmp.as<double>()));
@@ -1317,6 +1484,7 @@ wrc_status wrc_query_active(wrc_run* R, int32_t* idx_out, double* omega_out, int
 
 wrc_status wrc_scalar_init(wrc_run* R, double kappa, const double* field, int32_t device_ptr) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_scalar_init"));
     if (!field) return fail(R, WRC_ERR_ARG, "field is NULL");
     if (!(kappa >= 0) || !std::isfinite(kappa)) return fail(R, WRC_ERR_ARG, "kappa must be finite and >= 0");
     const bool was = R->scalar;
@@ -1345,6 +1513,74 @@ wrc_status wrc_query_scalar(wrc_run* R, int32_t* idx_out, double* r_out, int64_t
     return WRC_OK;
 }
 
+wrc_status wrc_exner_init(wrc_run* R, const double* u, const double* v, const double* pi, int32_t device_ptr) {
+    if (!R) return WRC_ERR_ARG;
+    if (!R->exner) return fail(R, WRC_ERR_STATE, "wrc_exner_init needs a run of model WRC_MODEL_EXNER");
+    if (!u || !v || !pi) return fail(R, WRC_ERR_ARG, "NULL field");
+    R->init = false;
+    TRY(copy_in(R, R->L, u, sizeof(double) * R->N, device_ptr));
+    TRY(copy_in(R, R->Lr.p, v, sizeof(double) * R->N, device_ptr));
+    TRY(copy_in(R, R->Lp.p, pi, sizeof(double) * R->N, device_ptr));
+    TRY(exner_threshold_whole(R));
+    R->init = true;
+    R->t = 0.0;
+    R->nstep = 0;
+    return WRC_OK;
+}
+
+wrc_status wrc_exner_init_vortices(wrc_run* R, int32_t n, const double* xc, const double* yc, const double* gamma,
+                                   const double* s, double pi0) {
+    if (!R) return WRC_ERR_ARG;
+    if (!R->exner) return fail(R, WRC_ERR_STATE, "wrc_exner_init_vortices needs a run of model WRC_MODEL_EXNER");
+    if (n < 1 || n > WRC_MAX_VORTICES || !xc || !yc || !gamma || !s)
+        return fail(R, WRC_ERR_ARG, "need 1..WRC_MAX_VORTICES vortices and four host arrays");
+    if (!(pi0 > 0) || !std::isfinite(pi0)) return fail(R, WRC_ERR_ARG, "pi0 must be finite and > 0");
+    double prm[4 * WRC_MAX_VORTICES];
+    for (int q = 0; q < n; ++q) {
+        if (!(s[q] > 0) || !std::isfinite(xc[q]) || !std::isfinite(yc[q]) || !std::isfinite(gamma[q]))
+            return fail(R, WRC_ERR_ARG, "vortex parameters must be finite with s > 0");
+        prm[q] = xc[q];
+        prm[n + q] = yc[q];
+        prm[2 * n + q] = gamma[q];
+        prm[3 * n + q] = s[q];
+    }
+    R->init = false;
+    const cudaStream_t st = R->st;
+    CK(cudaMemcpyAsync(R->vort_dev, prm, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+    // omega on the lattice (in Lq), psi, then u = D_y psi into L and v = -D_x psi into Lr
+    launch_init_vortices<double>((double*)R->Lq, R->vort_dev, n, R->g, st);
+    launch_poisson<double>(R->plan, (const double*)R->Lq, (double*)R->psi, R->C1, R->C2, R->g, st);
+    launch_lattice_uv_nut<double>((const double*)R->psi, (double*)R->L, R->Lr.as<double>(), nullptr, 0.0,
+                                  (double*)R->C1, R->g, st);
+    CKL("exner vortices");
+    CK(ex_fill(R->Lp.as<double>(), R->N, pi0, st));
+    CK(cudaStreamSynchronize(st));   // prm is a stack array
+    TRY(exner_threshold_whole(R));
+    R->init = true;
+    R->t = 0.0;
+    R->nstep = 0;
+    return WRC_OK;
+}
+
+wrc_status wrc_query_exner(wrc_run* R, int32_t* idx_out, double* u_out, double* v_out, double* pi_out, int64_t cap,
+                           int32_t device_ptr) {
+    TRY(check_ready(R));
+    if (!R->exner) return fail(R, WRC_ERR_STATE, "wrc_query_exner needs a run of model WRC_MODEL_EXNER");
+    if (cap < R->n_active) return fail(R, WRC_ERR_ARG, "cap smaller than the active count");
+    const long long n = R->n_active;
+    if (u_out) TRY(copy_out(R, u_out, R->omega[R->cur].p, sizeof(double) * n, device_ptr));
+    if (v_out) TRY(copy_out(R, v_out, R->rv[R->cur].p, sizeof(double) * n, device_ptr));
+    if (pi_out) TRY(copy_out(R, pi_out, R->pe[R->cur].p, sizeof(double) * n, device_ptr));
+    if (idx_out) {
+        int* tmpi = R->tmp.as<int>();
+        launch_meta_unpack(R->meta[R->cur].as<uint32_t>(), n, tmpi, nullptr, nullptr, R->st);
+        CKL("unpack");
+        TRY(copy_out(R, idx_out, tmpi, sizeof(int) * n, device_ptr));
+    }
+    CK(cudaStreamSynchronize(R->st));
+    return WRC_OK;
+}
+
 wrc_status wrc_query_masks(wrc_run* R, uint8_t* active, uint8_t* ghost, uint8_t* significant, int32_t device_ptr) {
     TRY(check_ready(R));
     if (active) TRY(copy_out(R, active, R->act, R->N, device_ptr));
@@ -1355,6 +1591,7 @@ wrc_status wrc_query_masks(wrc_run* R, uint8_t* active, uint8_t* ghost, uint8_t*
 }
 
 wrc_status wrc_query_details(wrc_run* R, double* d_out, int64_t cap, int32_t device_ptr) {
+    TRY(vorticity_only(R, "wrc_query_details"));
     TRY(check_ready(R));
     if (!d_out) return fail(R, WRC_ERR_ARG, "NULL output");
     if (cap < R->det_count) return fail(R, WRC_ERR_ARG, "cap smaller than the detail count");
@@ -1380,6 +1617,7 @@ wrc_status wrc_query_stencil_levels(wrc_run* R, uint8_t* jx_out, uint8_t* jy_out
 
 wrc_status wrc_query_field(wrc_run* R, int32_t which, double* out, int32_t device_ptr) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_query_field"));
     if (!out || which < 0 || which > 4) return fail(R, WRC_ERR_ARG, "bad field or NULL output");
     TRY(DISPATCH(R, query_field_t, R, which, out, device_ptr));
     CK(cudaStreamSynchronize(R->st));
@@ -1388,6 +1626,7 @@ wrc_status wrc_query_field(wrc_run* R, int32_t which, double* out, int32_t devic
 
 wrc_status wrc_freeze(wrc_run* R) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_freeze"));
     TRY(DISPATCH(R, freeze, R));
     CK(cudaStreamSynchronize(R->st));
     return WRC_OK;
@@ -1395,6 +1634,7 @@ wrc_status wrc_freeze(wrc_run* R) {
 
 wrc_status wrc_apply_operator(wrc_run* R, const double* q, double* w, double* g_out, int32_t device_ptr) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_apply_operator"));
     if (!R->frozen) return fail(R, WRC_ERR_STATE, "call wrc_freeze after the last grid change");
     if (!q || !w) return fail(R, WRC_ERR_ARG, "NULL input or output");
     TRY(DISPATCH(R, apply_operator_t, R, q, w, g_out, device_ptr));
@@ -1423,6 +1663,7 @@ wrc_status wrc_query_krylov(wrc_run* R, double* beta, int32_t* k, double* h_last
 
 wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
     TRY(check_ready(R));
+    TRY(vorticity_only(R, "wrc_diagnostics"));
     if (!out) return fail(R, WRC_ERR_ARG, "NULL output");
     TRY(DISPATCH(R, diagnostics_t, R));
     double s[4];
@@ -1452,6 +1693,7 @@ wrc_status wrc_query_stats(wrc_run* R, int64_t out[4]) {
 wrc_status wrc_profile(wrc_run* R, int32_t enable) {
     if (!R) return WRC_ERR_ARG;
     if (enable < 0 || enable > 3) return fail(R, WRC_ERR_ARG, "enable must be 0, 1, 2 or 3");
+    if (enable == 2) TRY(vorticity_only(R, "the phase trace of wrc_profile"));
     CK(cudaStreamSynchronize(R->st));
     R->profiling = enable == 1 || enable == 2;
     R->tracing = enable == 2;
@@ -1935,6 +2177,11 @@ wrc_status wrc_ensemble_create(int32_t n, const wrc_config* cfgs, void* cuda_str
         g_ens_create_error = "need at least one member configuration";
         return WRC_ERR_ARG;
     }
+    for (int i = 0; i < n; ++i)
+        if (cfgs[i].model != WRC_MODEL_VORTICITY) {
+            g_ens_create_error = "the batched ensemble runs the vorticity form only";
+            return WRC_ERR_ARG;
+        }
     for (int i = 1; i < n; ++i)
         if (cfgs[i].prec != cfgs[0].prec || (cfgs[i].p == 0 ? 2 : cfgs[i].p) != (cfgs[0].p == 0 ? 2 : cfgs[0].p)) {
             g_ens_create_error = "all members of an ensemble share one precision and one DD order";

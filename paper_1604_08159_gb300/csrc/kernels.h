@@ -143,6 +143,47 @@ template <typename T> cudaError_t rb_axpy(const RbArgs& a, int nv, int j, cudaSt
 template <typename T> cudaError_t rb_scale(const RbArgs& a, int j, cudaStream_t s);
 // phi_1 of the projected matrix and the update of omega (and L).
 template <typename T> cudaError_t rb_finish(const RbArgs& a, cudaStream_t s);
+// phi_1 of the projected matrix alone: y = phi_1(dt H_k) e_1, k = *kstop.
+cudaError_t rb_phi1(const RbArgs& a, cudaStream_t s);
+
+// ---- exner.cu: the compressible velocity-Exner form (Eqs. 1-2) -------------
+// Arguments of its launches (FP64).  Vectors of the Krylov process stack the
+// three fields of the active points: [u (n) | v (n) | pi (n)].
+struct ExArgs {
+    Geom g;
+    const uint32_t* meta;   // active points
+    int n;                  // active count
+    const int* glist;       // lattice positions of the ghosts
+    int ng;
+    const int* row_len;     // ghost interpolation rows over the active points
+    const int* row_idx;
+    const double* row_w;
+    int rmax;
+    double* Lb[3];          // lattices of u, v, pi at t^n (active and ghost values)
+    double* Lq[3];          // lattices of the current Krylov vector's three parts
+    const double* f[3];     // compact u, v, pi at t^n
+    double* f_out[3];       // compact u, v, pi updated in place
+    double* d;              // 8 x ld: u_x, u_y, v_x, v_y, pi_x, pi_y, lap u, lap v
+    long long ld;           // leading dimension of d (>= n)
+    double C, fc, gx, gy, r, nu, c1J, c2J;
+    int full;               // 1: the exact Jacobian; 0: the frozen-coefficient operator
+};
+// Lattices of the three fields from their compact values (active points and,
+// through the interpolation rows, the ghosts).
+cudaError_t ex_scatter_fields(const ExArgs& a, const double* const src[3], double* const dst[3], const int* kstop,
+                              int j, cudaStream_t s);
+// First derivatives and Laplacians of the state at the active points (into
+// a.d) and the right-hand side F(U^n) stacked into w (3 n).
+cudaError_t ex_base(const ExArgs& a, double* w, cudaStream_t s);
+// w = M q (M the Jacobian or the frozen operator) for the stacked vector q
+// whose lattices a.Lq hold its values; skipped after a breakdown (j >= *kstop).
+cudaError_t ex_apply(const ExArgs& a, const double* q, double* w, const int* kstop, int j, cudaStream_t s);
+// U^{n+1} = U^n + dt beta V_k y at the active points, into the compact arrays
+// and the state lattices a.Lb.
+cudaError_t ex_combine(const ExArgs& a, const double* basis, long long ld3, const double* y, const double* beta,
+                       double dt, const int* kstop, cudaStream_t s);
+// Fill a lattice with a constant.
+cudaError_t ex_fill(double* F, long long n, double value, cudaStream_t s);
 
 // ---- krylov.cu: the Krylov-projected step as one cooperative kernel ---------
 struct KrylovStepArgs {

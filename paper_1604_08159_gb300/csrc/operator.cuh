@@ -86,4 +86,54 @@ __device__ __forceinline__ T apply_point(const T* __restrict__ F, uint32_t mw, T
     return -U * Dx - V * Dy + nu * (Dxx + Dyy) - r * q0;
 }
 
+// The collocation derivatives of a lattice field F at the active point mw
+// (Sec. 2.5, each axis at its own stencil level j*, ghost values in F):
+// Dx, Dy and the Laplacian Dxx + Dyy, for the operators of the
+// velocity-Exner form.
+template <typename T, int P>
+__device__ __forceinline__ void point_derivs(const T* __restrict__ F, uint32_t mw, const Geom& g, T c1J, T c2J,
+                                             T& Dx, T& Dy, T& Lap) {
+    constexpr int R1 = P == 2 ? 2 : dd_reach1(P);
+    const int p = meta_pos(mw);
+    const int i = p & g.mask, k = p >> g.L;
+    const int shx = g.J - meta_jx(mw), shy = g.J - meta_jy(mw);
+    const int sx = 1 << shx, sy = 1 << shy;
+    const T* row = F + ((size_t)k << g.L);
+    const T q0 = row[i];
+    T xp[R1], xm[R1], yp[R1], ym[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        xp[o] = row[(i + (o + 1) * sx) & g.mask];
+        xm[o] = row[(i - (o + 1) * sx) & g.mask];
+        yp[o] = F[((size_t)((k + (o + 1) * sy) & g.mask) << g.L) + i];
+        ym[o] = F[((size_t)((k - (o + 1) * sy) & g.mask) << g.L) + i];
+    }
+    const T c1x = pow2_down(c1J, shx), c1y = pow2_down(c1J, shy);
+    const T c2x = pow2_down(c2J, 2 * shx), c2y = pow2_down(c2J, 2 * shy);
+    if constexpr (P == 2) {
+        Dx = (T(8) * (xp[0] - xm[0]) - (xp[1] - xm[1])) * c1x;
+        Dy = (T(8) * (yp[0] - ym[0]) - (yp[1] - ym[1])) * c1y;
+        Lap = (-(xp[1] + xm[1]) + T(16) * (xp[0] + xm[0]) - T(30) * q0) * c2x +
+              (-(yp[1] + ym[1]) + T(16) * (yp[0] + ym[0]) - T(30) * q0) * c2y;
+    } else {
+        T dx = T(dd_d1(P, 1)) * (xp[0] - xm[0]), dy = T(dd_d1(P, 1)) * (yp[0] - ym[0]);
+#pragma unroll
+        for (int o = 1; o < R1; ++o) {
+            dx += T(dd_d1(P, o + 1)) * (xp[o] - xm[o]);
+            dy += T(dd_d1(P, o + 1)) * (yp[o] - ym[o]);
+        }
+        T dxx = T(dd_d2(P, P)) * (xp[P - 1] + xm[P - 1]), dyy = T(dd_d2(P, P)) * (yp[P - 1] + ym[P - 1]);
+#pragma unroll
+        for (int o = P - 2; o >= 0; --o) {
+            dxx += T(dd_d2(P, o + 1)) * (xp[o] + xm[o]);
+            dyy += T(dd_d2(P, o + 1)) * (yp[o] + ym[o]);
+        }
+        dxx += T(dd_d2(P, 0)) * q0;
+        dyy += T(dd_d2(P, 0)) * q0;
+        Dx = dx * c1x;
+        Dy = dy * c1y;
+        Lap = dxx * c2x + dyy * c2y;
+    }
+}
+
 }  // namespace wrc

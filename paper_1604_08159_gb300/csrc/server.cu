@@ -437,9 +437,9 @@ wrc_status wrc_server_submit(wrc_server* S, const wrc_config* cfg, int32_t nv, c
                              const double* gamma, const double* s, int64_t nsteps, double arrival_s, int64_t* id) {
     if (!S || !id) return WRC_ERR_ARG;
     std::string why;
-    if (!valid_run_config(cfg, why)) {
+    if (!valid_run_config(cfg, why) || cfg->model != WRC_MODEL_VORTICITY) {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->err = "submit: " + why;
+        S->err = "submit: " + (why.empty() ? std::string("the server runs the vorticity form only") : why);
         return WRC_ERR_ARG;
     }
     if (nv < 1 || nv > WRC_MAX_VORTICES || !xc || !yc || !gamma || !s || nsteps < 0 || !std::isfinite(arrival_s)) {

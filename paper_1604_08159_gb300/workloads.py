@@ -17,6 +17,7 @@ import numpy as np
 
 SGS_OFF, SGS_APRIORI, SGS_DYNAMIC = 0, 1, 2
 SCHEME_FROZEN, SCHEME_ROSENBROCK = 0, 1
+MODEL_VORTICITY, MODEL_EXNER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -36,6 +37,11 @@ class RunParams:
     prec: int = PREC_FP64
     p: int = 2              # half the DD order 2p (2p = 4, 6, 8)
     scheme: int = 0         # 0: frozen linearisation, 1: exponential Rosenbrock (full Jacobian)
+    model: int = MODEL_VORTICITY   # 1: the compressible velocity-Exner form (Eqs. 1-2)
+    cpt: float = 0.0        # velocity-Exner form: C = c_p theta_0, Coriolis f, geostrophic wind G
+    coriolis: float = 0.0
+    gx: float = 0.0
+    gy: float = 0.0
 
     @property
     def NJ(self) -> int:
@@ -95,6 +101,19 @@ def fujiwhara_1024(seed: int = 2) -> Workload:
     p = RunParams(n0=32, J=5, eps=1e-4, re=5000.0, dt=1e-2, m=30,
                   sgs=SGS_DYNAMIC, cs=0.17)
     return Workload("fujiwhara_pair_1024_sgs_fp64", p, _pair(1.2, 1.0, 1.0, 0.3, jit), 2000)
+
+
+def fujiwhara_exner_1024(seed: int = 2) -> Workload:
+    """The 1024^2 pair of ``fujiwhara_1024`` in the compressible velocity-Exner
+    form (Eqs. 1-2): the vortices' velocity, pi = 1, C = c_p theta_0 = 25 (sound
+    speed 5, about 15 times the vortices' peak speed, so dt = 1e-2 is some 8
+    acoustic CFL numbers), f = 0.5, no subgrid model, the exact-Jacobian
+    (Rosenbrock) step, m = 30, eps = 1e-4."""
+    rng = np.random.default_rng(seed)
+    jit = rng.uniform(-0.01, 0.01, size=(2, 2))
+    p = RunParams(n0=32, J=5, eps=1e-4, re=5000.0, dt=1e-2, m=30, scheme=SCHEME_ROSENBROCK,
+                  model=MODEL_EXNER, cpt=25.0, coriolis=0.5)
+    return Workload("fujiwhara_pair_1024_exner_fp64", p, _pair(1.2, 1.0, 1.0, 0.3, jit), 200, {"pi0": 1.0})
 
 
 def three_vortex_4096(seed: int = 3) -> Workload:

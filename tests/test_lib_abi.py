@@ -137,3 +137,26 @@ def test_server_null_handles(lib):
     assert lib.wrc_server_query(None, 0, None) == -1
     assert lib.wrc_server_stats(None, None) == -1
     lib.wrc_server_destroy(None)
+
+
+@pytest.mark.parametrize("changes,msg", [
+    (dict(model=2), "unknown model"),
+    (dict(model=1, prec=1), "FP64 only"),
+    (dict(model=1, sgs=2), "a-priori"),
+    (dict(model=1, cpt=-1.0), "cpt"),
+    (dict(model=1, coriolis=float("nan")), "cpt"),
+])
+def test_create_rejects_invalid_exner_config_without_gpu(lib, changes, msg):
+    cfg = B.WrcConfig(16, 3, 20, 0, 0, 0, 1e-3, 5000.0, 0.0, 0.0, 0.0, 1e-2)
+    for k, v in changes.items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p()
+    st = lib.wrc_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == -1 and h.value is None
+    assert msg in lib.wrc_last_error(None).decode()
+
+
+def test_config_struct_layout_matches_the_header():
+    # six int32, six doubles, two int32, four doubles: 112 bytes, doubles 8-aligned
+    assert ctypes.sizeof(B.WrcConfig) == 112
+    assert B.WrcConfig.model.offset == 76 and B.WrcConfig.cpt.offset == 80
