@@ -520,11 +520,14 @@ def measure_exner(args):
             "value": upd / (ms * 1e-3 * n), "unit": UNIT + " (u, v and pi advanced per update)"}
 
 
-KRYLOV_SOURCES = ("csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh", "csrc/kernels.h")
+KRYLOV_SOURCES = ("csrc/krylov_impl.cuh", "csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh",
+                  "csrc/kernels.h")
 # DRAM bytes per launch of the Krylov kernel on the 1024^2 pair, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
-# kernel sources whose SHA-256 is recorded with it; None until one is taken.
-KRYLOV_TRAFFIC = None   # {"sources_sha256": "...", "bytes_per_launch": N, "capture": "..."}
+# kernel sources whose SHA-256 is recorded with it.
+KRYLOV_TRAFFIC = {"sources_sha256": "5d37c6deb0d4207243bb69533bf7ec284d46a29edb94e6d64c6b0fa5e77d1e2f",
+                  "bytes_per_launch": 2682624,
+                  "capture": "ncu --set full, unclustered form, 1024^2 pair, third launch"}
 
 
 def krylov_traffic():
