@@ -187,6 +187,13 @@ struct wrc_run {
     bool scalar = false;
     double kappa = 0.0;
     DevBuf rv[2], Lr, kr;
+    // the scalar's Krylov problem runs beside omega's in one cooperative
+    // launch: its own basis, work vector, ghost values, lattice vector,
+    // partial sums and barrier words, and the launch's argument array and
+    // block map (device, with a pinned host copy)
+    DevBuf sbasis, sw, sGb, sLq, spart, sbar, sdev;
+    void* shost = nullptr;
+    size_t shost_bytes = 0;
 
     // exponential Rosenbrock step (wrc_config.scheme): U[q], V[q], D_x omega,
     // D_y omega at the active points (4 x cap, bulk type), the reductions'
@@ -713,6 +720,63 @@ KrylovStepArgs krylov_args_scalar(wrc_run* R) {
     return A;
 }
 
+// The Krylov steps of omega and of the passive scalar as two problems of one
+// cooperative launch of the batched kernel (each with half of the co-resident
+// blocks, its own grid barrier and workspace), so that the latency-bound
+// phases of one overlap the FP64 work of the other.  The scalar's workspace
+// grows with the grid here.
+template <typename T>
+wrc_status krylov_pair(wrc_run* R, const KrylovStepArgs& A) {
+    const cudaStream_t s = R->st;
+    const int m = R->cfg.krylov_m;
+    constexpr int kPairPT = 128;   // threads per block of the batched kernel
+    const int maxb = krylov_batch_max_blocks(R->fp32, R->g.P, kPairPT);
+    if (maxb < 2) return fail(R, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
+    CK(R->sbasis.grow(R->es * (size_t)R->cap * (m + 1), 0, s));
+    CK(R->sw.grow(R->es * (size_t)R->cap, 0, s));
+    CK(R->sGb.grow(R->es * (size_t)(R->cap_g > 0 ? R->cap_g : 1) * (m + 1), 0, s));
+    CK(R->sLq.grow(R->es * (size_t)R->N, 0, s));
+    CK(R->spart.grow(sizeof(double) * krylov_partials_doubles(maxb), 0, s));
+    if (!R->sbar.p) {
+        CK(R->sbar.grow(sizeof(unsigned) * 4, 0, s));
+        CK(cudaMemsetAsync(R->sbar.p, 0, R->sbar.bytes, s));
+    }
+    KrylovStepArgs B = krylov_args_scalar(R);
+    B.basis = R->sbasis.p;
+    B.w = R->sw.p;
+    B.Gb = R->sGb.p;
+    B.Lq = R->sLq.p;
+    B.part = R->spart.as<double>();
+    B.bar = R->sbar.as<unsigned>();
+    const long long need = (R->n_active + kPairPT - 1) / kPairPT;
+    const int each = (int)std::max(1LL, std::min(need, (long long)(maxb / 2)));
+    const int total = 2 * each;
+    const size_t bytes = 2 * sizeof(KrylovStepArgs) + sizeof(int) * (total + 3);
+    CK(R->sdev.grow(bytes, 0, s));
+    if (R->shost_bytes < bytes) {
+        CK(cudaStreamSynchronize(s));   // the last copy from the old staging buffer
+        if (R->shost) cudaFreeHost(R->shost);
+        R->shost = nullptr;
+        R->shost_bytes = 0;
+        CK(cudaMallocHost(&R->shost, bytes));
+        R->shost_bytes = bytes;
+    }
+    KrylovStepArgs* ha = (KrylovStepArgs*)R->shost;
+    ha[0] = A;
+    ha[1] = B;
+    int* blk = (int*)(ha + 2);
+    for (int b = 0; b < total; ++b) blk[b] = b < each ? 0 : 1;
+    blk[total] = 0;
+    blk[total + 1] = each;
+    blk[total + 2] = total;
+    if (R->tracing) R->trace_nb = each;
+    CK(cudaMemcpyAsync(R->sdev.p, R->shost, bytes, cudaMemcpyHostToDevice, s));
+    const KrylovStepArgs* da = (const KrylovStepArgs*)R->sdev.p;
+    const int* dblk = (const int*)(da + 2);
+    CK(launch_krylov_batch<T>(da, dblk, dblk + total, 2, total, kPairPT, R->g.P, s));
+    return WRC_OK;
+}
+
 // Clear the phase trace before a traced launch (on the run's stream).
 wrc_status trace_reset(wrc_run* R, int nb) {
     if (!R->tracing) return WRC_OK;
@@ -744,13 +808,16 @@ wrc_status krylov(wrc_run* R) {
         e0 = (int)R->ev_used.size() * 2;
         CK(cudaEventRecord(R->ev_pool[e0], s));
     }
+    const bool pair = R->scalar && R->cfg.scheme != WRC_SCHEME_ROSENBROCK;
     if (R->cfg.scheme == WRC_SCHEME_ROSENBROCK) TRY(krylov_rosenbrock<T>(R));
+    else if (pair) TRY(krylov_pair<T>(R, A));
     else CK(launch_krylov_step<T>(A, blocks, s, R->device, R->cluster_max));
     if (R->profiling) {
         CK(cudaEventRecord(R->ev_pool[e0 + 1], s));
-        R->ev_used.push_back({e0, krylov_algorithmic_bytes(n, m), krylov_algorithmic_flops(n, m)});
+        const double f = pair ? 2.0 : 1.0;
+        R->ev_used.push_back({e0, f * krylov_algorithmic_bytes(n, m), f * krylov_algorithmic_flops(n, m)});
     }
-    if (R->scalar) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s, R->device, R->cluster_max));
+    if (R->scalar && !pair) CK(launch_krylov_step<T>(krylov_args_scalar(R), blocks, s, R->device, R->cluster_max));
     return WRC_OK;
 }
 
@@ -880,59 +947,41 @@ ExArgs exner_args(wrc_run* R) {
 }
 
 // The Krylov part of a velocity-Exner step (Eqs. 1-2): the state's lattices
-// (active and ghost values) and derivatives, b = F(U^n), then the Arnoldi
+// (active and ghost values) and derivatives and b = F(U^n), then the Arnoldi
 // process on the stacked vectors [u; v; pi] (classical Gram-Schmidt twice,
-// FP64 partial sums added in a fixed order, breakdown on the device), one
-// lattice launch and one operator launch per Krylov vector, phi_1 and the
-// update.  FP64 only.
+// FP64 partial sums added in a fixed order, breakdown on the device), phi_1
+// and the update in one persistent cooperative launch.  FP64 only.
 wrc_status exner_krylov(wrc_run* R) {
     const cudaStream_t s = R->st;
     const long long n = R->n_active;
     const int m = R->cfg.krylov_m;
-    CK(R->rbpart.grow(sizeof(double) * kRbPartBlocks * kRbPartWidth, 0, s));
-    CK(R->rbsmall.grow(sizeof(double) * 64, 0, s));
+    const int maxb = ex_krylov_max_blocks(R->g.P);
+    if (maxb < 1) return fail(R, WRC_ERR_CUDA, "velocity-Exner Krylov kernel occupancy query failed");
+    const int blocks = (int)std::max(1LL, std::min((long long)maxb, (n + kExKrylovThreads - 1) / kExKrylovThreads));
+    CK(R->rbpart.grow(sizeof(double) * (size_t)maxb * kExPartWidth, 0, s));
     const ExArgs a = exner_args(R);
-    const long long ld3 = 3 * R->cap;
-    RbArgs rb{};
-    rb.n = (int)(3 * n);
-    rb.w = R->xw.p;
-    rb.basis = R->xbasis.p;
-    rb.ld = ld3;
-    rb.part = R->rbpart.as<double>();
-    rb.coef = R->rbsmall.as<double>();
-    rb.sc = rb.coef + 32;
-    rb.H = R->K.H;
-    rb.y = R->K.y;
-    rb.beta = R->K.beta;
-    rb.kstop = R->K.kstop;
-    rb.flags = R->K.flags;
-    rb.m = m;
-    rb.dt = R->cfg.dt;
-    rb.tol = kBreakdownTol;
+    ExKrylov K{};
+    K.basis = R->xbasis.as<double>();
+    K.ld3 = 3 * R->cap;
+    K.w = R->xw.as<double>();
+    K.part = R->rbpart.as<double>();
+    K.H = R->K.H;
+    K.y = R->K.y;
+    K.beta = R->K.beta;
+    K.kstop = R->K.kstop;
+    K.flags = R->K.flags;
+    K.bar = R->K.bar;
+    K.err = R->K.err;
+    K.limit_ns = R->wait_limit_ns;
+    K.m = m;
+    K.dt = R->cfg.dt;
+    K.tol = kBreakdownTol;
     double* const Lb[3] = {a.Lb[0], a.Lb[1], a.Lb[2]};
     const double* const fs[3] = {a.f[0], a.f[1], a.f[2]};
-    double* const Lq[3] = {a.Lq[0], a.Lq[1], a.Lq[2]};
-    double* const w = R->xw.as<double>();
-    double* const basis = R->xbasis.as<double>();
     CK(cudaMemsetAsync(R->K.H, 0, sizeof(double) * (m + 1) * m, s));
     CK(ex_scatter_fields(a, fs, Lb, nullptr, 0, s));
-    CK(ex_base(a, w, s));
-    CK(rb_reduce<double>(rb, 0, true, 3, -1, s));
-    CK(rb_scale<double>(rb, -1, s));
-    for (int j = 0; j < m; ++j) {
-        const double* qj = basis + (size_t)j * ld3;
-        const double* const qp[3] = {qj, qj + n, qj + 2 * n};
-        CK(ex_scatter_fields(a, qp, Lq, R->K.kstop, j, s));
-        CK(ex_apply(a, qj, w, R->K.kstop, j, s));
-        CK(rb_reduce<double>(rb, j + 1, true, 0, j, s));
-        CK(rb_axpy<double>(rb, j + 1, j, s));
-        CK(rb_reduce<double>(rb, j + 1, false, 1, j, s));
-        CK(rb_axpy<double>(rb, j + 1, j, s));
-        CK(rb_reduce<double>(rb, 0, true, 2, j, s));
-        CK(rb_scale<double>(rb, j, s));
-    }
-    CK(rb_phi1(rb, s));
-    CK(ex_combine(a, basis, ld3, R->K.y, R->K.beta, R->cfg.dt, R->K.kstop, s));
+    CK(ex_base(a, K.w, s));
+    CK(ex_krylov(a, K, blocks, s));
     return WRC_OK;
 }
 
@@ -1189,7 +1238,7 @@ void free_run(wrc_run* R) {
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
                     &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace, &R->rv[0],
                     &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall, &R->pe[0], &R->pe[1], &R->Lp, &R->Lqx,
-                    &R->xd, &R->xbasis, &R->xw})
+                    &R->xd, &R->xbasis, &R->xw, &R->sbasis, &R->sw, &R->sGb, &R->sLq, &R->spart, &R->sbar, &R->sdev})
         b->release(s);
     cudaStreamSynchronize(s);
     void* ptrs[] = {R->L, R->Lq, R->psi, R->C1, R->C2, R->act, R->nxt, R->gho, R->sig, R->JJ, R->halo, R->list, R->lat2idx,
@@ -1198,6 +1247,7 @@ void free_run(wrc_run* R) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (R->counts_host) cudaFreeHost(R->counts_host);
+    if (R->shost) cudaFreeHost(R->shost);
     for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
     if (R->sync_ev) cudaEventDestroy(R->sync_ev);
     for (cudaEvent_t e : R->st_pool) cudaEventDestroy(e);

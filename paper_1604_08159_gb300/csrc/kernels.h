@@ -143,8 +143,6 @@ template <typename T> cudaError_t rb_axpy(const RbArgs& a, int nv, int j, cudaSt
 template <typename T> cudaError_t rb_scale(const RbArgs& a, int j, cudaStream_t s);
 // phi_1 of the projected matrix and the update of omega (and L).
 template <typename T> cudaError_t rb_finish(const RbArgs& a, cudaStream_t s);
-// phi_1 of the projected matrix alone: y = phi_1(dt H_k) e_1, k = *kstop.
-cudaError_t rb_phi1(const RbArgs& a, cudaStream_t s);
 
 // ---- exner.cu: the compressible velocity-Exner form (Eqs. 1-2) -------------
 // Arguments of its launches (FP64).  Vectors of the Krylov process stack the
@@ -175,15 +173,32 @@ cudaError_t ex_scatter_fields(const ExArgs& a, const double* const src[3], doubl
 // First derivatives and Laplacians of the state at the active points (into
 // a.d) and the right-hand side F(U^n) stacked into w (3 n).
 cudaError_t ex_base(const ExArgs& a, double* w, cudaStream_t s);
-// w = M q (M the Jacobian or the frozen operator) for the stacked vector q
-// whose lattices a.Lq hold its values; skipped after a breakdown (j >= *kstop).
-cudaError_t ex_apply(const ExArgs& a, const double* q, double* w, const int* kstop, int j, cudaStream_t s);
-// U^{n+1} = U^n + dt beta V_k y at the active points, into the compact arrays
-// and the state lattices a.Lb.
-cudaError_t ex_combine(const ExArgs& a, const double* basis, long long ld3, const double* y, const double* beta,
-                       double dt, const int* kstop, cudaStream_t s);
 // Fill a lattice with a constant.
 cudaError_t ex_fill(double* F, long long n, double value, cudaStream_t s);
+// The whole Krylov projection of a velocity-Exner step in one persistent
+// cooperative launch (b = F(U^n) in w on entry): classical Gram-Schmidt
+// twice on the stacked vectors, four grid barriers per Arnoldi step (bounded
+// waits: bit 1 of *err on expiry), phi_1 by block 0, the update.
+struct ExKrylov {
+    double* basis;          // (m + 1) x ld3
+    long long ld3;
+    double* w;              // 3 n: b on entry, the work vector
+    double* part;           // blocks x kExPartWidth partial sums
+    double* H;              // (m + 1) x m, zero on entry
+    double* y;
+    double* beta;
+    int* kstop;
+    int* flags;             // bit 0: non-finite value met
+    unsigned* bar;          // grid barrier words
+    int* err;
+    unsigned long long limit_ns;
+    int m;
+    double dt, tol;
+};
+int ex_krylov_max_blocks(int P);
+cudaError_t ex_krylov(const ExArgs& a, const ExKrylov& K, int blocks, cudaStream_t s);
+constexpr int kExKrylovThreads = 128;
+constexpr int kExPartWidth = 66;
 
 // ---- krylov.cu: the Krylov-projected step as one cooperative kernel ---------
 struct KrylovStepArgs {

@@ -268,12 +268,6 @@ cudaError_t rb_finish(const RbArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t rb_phi1(const RbArgs& a, cudaStream_t s) {
-    k_rb_phi1<<<1, kPT, 0, s>>>(a.H, a.kstop, a.m, a.dt, a.y, a.flags);
-    note_launch();
-    return cudaGetLastError();
-}
-
 #define WRC_INST(T)                                                                   \
     template cudaError_t rb_gradient<T>(const RbArgs&, cudaStream_t);                 \
     template cudaError_t rb_apply<T>(const RbArgs&, int, cudaStream_t);               \
