@@ -783,6 +783,18 @@ def run_ours(args):
             cval, cwall, cores, cupd = time_oracle(wl, csteps)
             cpu = {"value": cval, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{csteps} oracle step(s) of {wl.name} from t=0 ({cupd} updates, {cwall:.1f} s)"}
+        # the whole step against HBM: b (m^2 + 9m + 12) bytes per active-point
+        # update (Krylov part and adaptation) plus ~30 b per lattice point
+        # (reconstruction, FFT solve, velocity, SGS) per step, b the bulk bytes
+        na_step = upd / max(1, args.steps * ws)
+        step_bytes = es * ((p.m * p.m + 9 * p.m + 12) * na_step + 30.0 * p.NJ * p.NJ)
+        step_gbs = step_bytes / (t_dev / args.steps * 1e-3) / 1e9
+        step_hbm = {"achieved": step_gbs, "peak": peak, "unit": "GB/s", "frac": step_gbs / peak,
+                    "bytes_per_step": step_bytes,
+                    "bytes_model": f"{int(es)} (m^2 + 9m + 12) bytes per active point + {int(30 * es)} bytes per "
+                                   "lattice point, per step",
+                    "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "target_frac": 0.6}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev / args.steps, "higher_is_better": True,
@@ -807,6 +819,7 @@ def run_ours(args):
                                   "frac": achieved_gflops / FP64_PEAK_GFLOPS,
                                   "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; no measured FP64 peak)",
                                   "flops_per_launch": rec["flops"] / max(1, rec["launches"])}},
+            "step_hbm": step_hbm,
             "late": late,
             "accuracy": accuracy,
             "cpu_baseline": cpu,

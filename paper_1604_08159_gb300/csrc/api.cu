@@ -957,7 +957,8 @@ wrc_status exner_krylov(wrc_run* R) {
     const int m = R->cfg.krylov_m;
     const int maxb = ex_krylov_max_blocks(R->g.P);
     if (maxb < 1) return fail(R, WRC_ERR_CUDA, "velocity-Exner Krylov kernel occupancy query failed");
-    const int blocks = (int)std::max(1LL, std::min((long long)maxb, (n + kExKrylovThreads - 1) / kExKrylovThreads));
+    const int blocks =
+        (int)std::max(1LL, std::min((long long)maxb, (3 * n + kExKrylovThreads - 1) / kExKrylovThreads));
     CK(R->rbpart.grow(sizeof(double) * (size_t)maxb * kExPartWidth, 0, s));
     const ExArgs a = exner_args(R);
     ExKrylov K{};

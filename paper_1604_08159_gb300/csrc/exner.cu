@@ -56,12 +56,21 @@ __global__ void k_ex_fields(const uint32_t* __restrict__ meta, int n, const int*
             const int* ri = row_idx + e * rmax;
             const double* rw = row_w + e * rmax;
             double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int i = 0; i < rl; ++i) {
-                const int q = ri[i];
-                const double wt = rw[i];
-                a0 += wt * s0[q];
-                a1 += wt * s1[q];
-                a2 += wt * s2[q];
+            for (int r0 = 0; r0 < rl; r0 += kGatherLane) {
+                int id[kGatherLane];
+                double wt[kGatherLane];
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u) {
+                    id[u] = r0 + u < rl ? ri[r0 + u] : -1;
+                    wt[u] = r0 + u < rl ? rw[r0 + u] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u)
+                    if (id[u] >= 0) {
+                        a0 += wt[u] * s0[id[u]];
+                        a1 += wt[u] * s1[id[u]];
+                        a2 += wt[u] * s2[id[u]];
+                    }
             }
             const int p = glist[e];
             d0[p] = a0;
@@ -101,117 +110,187 @@ __global__ void k_ex_base(ExArgs a, double* __restrict__ w) {
 // the state's velocity, pressure gradient, pi times the divergence,
 // Coriolis, friction, viscosity) plus, for the exact Jacobian, the terms of
 // the state's gradients.
+// Entry e of M q (e = f n + i: field f at active point i; M the exact
+// Jacobian with full, else the frozen-coefficient operator): the own field's
+// collocation derivatives at the point's stencil levels and the cross terms
+// of the other fields (the lattices a.Lq hold q with its ghost values).
 template <int P>
-__device__ __forceinline__ void ex_point(const ExArgs& a, const double* __restrict__ q, int i, double (&J)[3]) {
+__device__ __forceinline__ double ex_entry(const ExArgs& a, const double* __restrict__ q, int f, int i) {
     const int n = a.n;
     const long long ld = a.ld;
     const uint32_t mw = a.meta[i];
-    double dux, duy, dlu, dvx, dvy, dlv, dpx, dpy, dlp;
-    point_derivs<double, P>(a.Lq[0], mw, a.g, a.c1J, a.c2J, dux, duy, dlu);
-    point_derivs<double, P>(a.Lq[1], mw, a.g, a.c1J, a.c2J, dvx, dvy, dlv);
-    point_derivs<double, P>(a.Lq[2], mw, a.g, a.c1J, a.c2J, dpx, dpy, dlp);
-    const double du = q[i], dv = q[n + i], dp = q[2 * n + i];
-    const double u = a.f[0][i], v = a.f[1][i], p = a.f[2][i];
-    double Ju = -(u * dux + v * duy) - a.C * dpx + a.fc * dv - a.r * du + a.nu * dlu;
-    double Jv = -(u * dvx + v * dvy) - a.C * dpy - a.fc * du - a.r * dv + a.nu * dlv;
-    double Jp = -(u * dpx + v * dpy) - p * (dux + dvy);
-    if (a.full) {
-        const double* d = a.d;
-        const double ux = d[i], uy = d[ld + i], vx = d[2 * ld + i], vy = d[3 * ld + i];
-        const double px = d[4 * ld + i], py = d[5 * ld + i];
-        Ju -= du * ux + dv * uy;
-        Jv -= du * vx + dv * vy;
-        Jp -= (du * px + dv * py) + dp * (ux + vy);
+    const double* d = a.d;
+    const double u = a.f[0][i], v = a.f[1][i];
+    const double du = q[i], dv = q[n + i];
+    if (f == 0) {
+        double dx, dy, lap;
+        point_derivs<double, P>(a.Lq[0], mw, a.g, a.c1J, a.c2J, dx, dy, lap);
+        const double dpx = point_d1<double, P>(a.Lq[2], mw, a.g, a.c1J, 0);
+        double J = -(u * dx + v * dy) - a.C * dpx + a.fc * dv - a.r * du + a.nu * lap;
+        if (a.full) J -= du * d[i] + dv * d[ld + i];
+        return J;
     }
-    J[0] = Ju;
-    J[1] = Jv;
-    J[2] = Jp;
+    if (f == 1) {
+        double dx, dy, lap;
+        point_derivs<double, P>(a.Lq[1], mw, a.g, a.c1J, a.c2J, dx, dy, lap);
+        const double dpy = point_d1<double, P>(a.Lq[2], mw, a.g, a.c1J, 1);
+        double J = -(u * dx + v * dy) - a.C * dpy - a.fc * du - a.r * dv + a.nu * lap;
+        if (a.full) J -= du * d[2 * ld + i] + dv * d[3 * ld + i];
+        return J;
+    }
+    const double dpx = point_d1<double, P>(a.Lq[2], mw, a.g, a.c1J, 0);
+    const double dpy = point_d1<double, P>(a.Lq[2], mw, a.g, a.c1J, 1);
+    const double dux = point_d1<double, P>(a.Lq[0], mw, a.g, a.c1J, 0);
+    const double dvy = point_d1<double, P>(a.Lq[1], mw, a.g, a.c1J, 1);
+    double J = -(u * dpx + v * dpy) - a.f[2][i] * (dux + dvy);
+    if (a.full) J -= (du * d[4 * ld + i] + dv * d[5 * ld + i]) + q[2 * n + i] * (d[i] + d[3 * ld + i]);
+    return J;
 }
 
-// Basis vector q_c = w * scale at the block's own points (stacked entries),
-// its lattices at the own active points, and at the block's share of the
-// ghosts (ghost bid + nb * t ...) from the interpolation rows over w (whose
-// entries are final for every point when this runs).
-__device__ __forceinline__ void ex_new_vector(const ExArgs& a, const ExKrylov& K, int c, double scale, int bid,
-                                              int nb) {
+// Field and point of a stacked entry.
+__device__ __forceinline__ void ex_split(long long e, int n, int& f, int& i) {
+    f = e >= 2LL * n ? 2 : (e >= n ? 1 : 0);
+    i = (int)(e - (long long)f * n);
+}
+
+// Basis vector q_c = w * scale at the block's own stacked entries, their
+// lattices at the active points, and the block's share of the ghost values
+// (items f ng + g: field f at ghost g) from the interpolation rows over w
+// (whose entries are final for every point when this runs).
+__device__ __forceinline__ void ex_new_vector(const ExArgs& a, const ExKrylov& K, int c, double scale, long long e0,
+                                              long long stride, double* ws) {
     const int n = a.n;
+    const long long N3 = 3LL * n;
     double* q = K.basis + (size_t)c * K.ld3;
     const double* w = K.w;
-    for (int i = bid * kExKrylovThreads + threadIdx.x; i < n; i += nb * kExKrylovThreads) {
-        const int p = meta_pos(a.meta[i]);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const double x = w[(size_t)f * n + i] * scale;
-            q[(size_t)f * n + i] = x;
-            a.Lq[f][p] = x;
-        }
+    for (long long e = e0; e < N3; e += stride) {
+        int f, i;
+        ex_split(e, n, f, i);
+        const double x = w[e] * scale;
+        q[e] = x;
+        a.Lq[f][meta_pos(a.meta[i])] = x;
     }
-    for (int t = bid * kExKrylovThreads + threadIdx.x; t < a.ng; t += nb * kExKrylovThreads) {
-        const int rl = a.row_len[t];
-        const int* ri = a.row_idx + (size_t)t * a.rmax;
-        const double* rw = a.row_w + (size_t)t * a.rmax;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int e = 0; e < rl; ++e) {
-            const int q0 = ri[e];
-            const double wt = rw[e];
-            s0 += wt * w[q0];
-            s1 += wt * w[n + q0];
-            s2 += wt * w[2 * n + q0];
+    // ghosts: eight lanes per ghost, each gathering up to kGatherLane row
+    // terms of the three fields with all its loads in flight, then the
+    // group's sums in a fixed order (group_sums); the loop is uniform over
+    // the warp
+    const int lane = threadIdx.x & 31, gl = lane & (kGhostLanes - 1);
+    const long long gstride = stride / kGhostLanes;
+    for (long long base = (e0 - lane) / kGhostLanes; base < a.ng; base += gstride) {
+        const long long t = base + lane / kGhostLanes;
+        const bool valid = t < a.ng;
+        const int gi = valid ? (int)t : 0;
+        const int rl = valid ? a.row_len[gi] : 0;
+        const int* ri = a.row_idx + (size_t)gi * a.rmax;
+        const double* rw = a.row_w + (size_t)gi * a.rmax;
+        double pv[3] = {0.0, 0.0, 0.0};
+        for (int r0 = 0; r0 < rl; r0 += kGhostLanes * kGatherLane) {
+            int id[kGatherLane];
+            double wt[kGatherLane];
+#pragma unroll
+            for (int u = 0; u < kGatherLane; ++u) {
+                const int r = r0 + gl + kGhostLanes * u;
+                id[u] = r < rl ? ri[r] : -1;
+                wt[u] = r < rl ? rw[r] : 0.0;
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                double xv[kGatherLane];
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u) xv[u] = id[u] >= 0 ? w[(size_t)f * n + id[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kGatherLane; ++u) pv[f] += wt[u] * xv[u];
+            }
         }
-        const int p = a.glist[t];
-        a.Lq[0][p] = s0 * scale;
-        a.Lq[1][p] = s1 * scale;
-        a.Lq[2][p] = s2 * scale;
+        group_sums<3>(pv, ws);
+        if (valid && gl == 0) {
+            const int p = a.glist[gi];
+            a.Lq[0][p] = pv[0] * scale;
+            a.Lq[1][p] = pv[1] * scale;
+            a.Lq[2][p] = pv[2] * scale;
+        }
     }
 }
 
-// Block partial sums of q_t . x for t < nv (x stacked, the block's own
-// points) into prow[0..nv): each warp stages its 32 points' three entries in
-// shared memory and lane l forms whole dot products over them (row l mod nv
-// and field l / nv when 3 nv <= 32, else row l over all three fields), so
-// that no per-thread accumulator array is needed; the warps' sums are added
-// in warp order.  1 <= nv <= 31.
-__device__ __forceinline__ void ex_dots(const ExKrylov& K, int n, int nv, const double* __restrict__ x,
-                                        double* prow, double (*s_x)[96], double (*s_dot)[40], int bid, int nb) {
+// Lanes per basis row in the warp dots: 32 / L rows fit, L a power of two.
+__device__ __forceinline__ int ex_lanes_per_row(int nv) {
+    int L = 32;
+    while (L > 1 && L * nv > 32) L >>= 1;
+    return L;
+}
+
+// After a warp has staged the values x of its 32 consecutive stacked
+// entries wb .. wb + 31 in s_x, lane l adds its share of q_t . x for row
+// t = l / L (t < nv), entries l mod L, l mod L + L, ... (one FP64 operation
+// per entry and lane instead of nv per entry and thread).
+__device__ __forceinline__ double ex_warp_dots(const ExKrylov& K, long long N3, int nv, int L, long long wb,
+                                               const double* s_x, double acc) {
+    const int lane = threadIdx.x & 31;
+    const int t = lane / L, sub = lane - t * L;
+    if (t < nv) {
+        const double* qt = K.basis + (size_t)t * K.ld3 + wb;
+        const int np = (int)min(32LL, N3 - wb);
+        for (int p = sub; p < np; p += L) acc += qt[p] * s_x[p];
+    }
+    return acc;
+}
+
+// The block's partial sums of the rows (the lanes' shares, the warps in
+// order) into prow[0..nv).
+__device__ __forceinline__ void ex_dots_finish(double acc, int nv, int L, double* prow, double (*s_dot)[96]) {
     constexpr int PT = kExKrylovThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const bool split = 3 * nv <= 32;
-    const int t = split ? lane % nv : lane;
-    const int f0 = split ? lane / nv : 0, f1 = split ? f0 + 1 : 3;
-    const bool act = split ? lane < 3 * nv : lane < nv;
-    const double* qt = K.basis + (size_t)(act ? t : 0) * K.ld3;
-    double acc = 0.0;
-    for (int wb = bid * PT + wid * 32; wb < n; wb += nb * PT) {
-        const int i = wb + lane;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) s_x[wid][f * 32 + lane] = i < n ? x[(size_t)f * n + i] : 0.0;
-        __syncwarp();
-        if (act) {
-            const int np = min(32, n - wb);
-            for (int f = f0; f < f1; ++f) {
-                const double* qf = qt + (size_t)f * n + wb;
-                const double* xf = s_x[wid] + f * 32;
-                for (int q = 0; q < np; ++q) acc += qf[q] * xf[q];
-            }
-        }
-        __syncwarp();
-    }
-    s_dot[wid][lane] = act ? acc : 0.0;
+    s_dot[wid][lane] = acc;
     __syncthreads();
     for (int r = threadIdx.x; r < nv; r += PT) {
         double sum = 0.0;
-        for (int w = 0; w < PT / 32; ++w) {
-            if (split) sum += (s_dot[w][r] + s_dot[w][nv + r]) + s_dot[w][2 * nv + r];
-            else sum += s_dot[w][r];
-        }
+        for (int w = 0; w < PT / 32; ++w)
+            for (int s2 = 0; s2 < L; ++s2) sum += s_dot[w][r * L + s2];
         prow[r] = sum;
+    }
+    __syncthreads();
+}
+
+// Sum over the nb blocks' rows part[b * kOutP + t], t < nout <= 32, into
+// s_out, in the same order in every block: lane l of warp w adds output
+// l mod ns (ns = nout rounded up to a power of two) of blocks w + kW (g + L u),
+// g = l / ns, L = 32 / ns, sixteen loads ahead of their additions; then the
+// groups and the warps in order.
+__device__ __forceinline__ void ex_reduce(const double* part, int nout, double* s_out, double (*s_red)[kNV + 1],
+                                          int nb) {
+    constexpr int PT = kExKrylovThreads, kW = PT / 32, kB = 16;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int ns = 1;
+    while (ns < nout) ns <<= 1;
+    const int L = 32 / ns, t = lane & (ns - 1), g = lane / ns, bstep = kW * L;
+    double v = 0.0;
+    if (t < nout) {
+        const double* p = part + t;
+        int b = wid + kW * g;
+        // batches of kB loads in flight; the last one padded with zeros,
+        // which leave the ordered sum unchanged
+        for (; b < nb; b += kB * bstep) {
+            double x[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) x[u] = b + u * bstep < nb ? p[(size_t)(b + u * bstep) * kOutP] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) v += x[u];
+        }
+    }
+    s_red[wid][lane] = v;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nout; q += PT) {
+        double sum = 0.0;
+        for (int w = 0; w < kW; ++w)
+            for (int gg = 0; gg < L; ++gg) sum += s_red[w][gg * ns + q];
+        s_out[q] = sum;
     }
     __syncthreads();
 }
 
 // Block partial sum of v over the block's threads into *dst (warp sums
 // through shared memory, then the warps in order).
-__device__ __forceinline__ void ex_block_sum(double v, double* dst, double (*s_dot)[40]) {
+__device__ __forceinline__ void ex_block_sum(double v, double* dst, double (*s_dot)[96]) {
     constexpr int PT = kExKrylovThreads;
     const int wid = threadIdx.x >> 5;
     const double ws = warp_sum(v, s_dot[wid]);
@@ -227,36 +306,34 @@ __device__ __forceinline__ void ex_block_sum(double v, double* dst, double (*s_d
 }
 
 // The Krylov projection of one velocity-Exner step by every block of a
-// cooperative launch; block bid owns points bid * PT + t, stride nb * PT, and
-// their three stacked entries.  Per Arnoldi step j: w = M q_j, the first
-// Gram-Schmidt dots and |w|^2 | w -= Q c and the second dots | w -= Q c' and
-// |w|^2 | h, breakdown test, q_{j+1} and its lattices; each | a grid
-// barrier.  Every block reduces the partial sums itself, in the same order,
-// so all take the same decisions; block 0 writes H and evaluates phi_1.
+// cooperative launch over the 3 n stacked entries (block bid owns entries
+// bid * PT + t, stride nb * PT).  Per Arnoldi step j: w = M q_j entry by
+// entry, the first Gram-Schmidt dots (warp-transposed) and |w|^2 | w -= Q c
+// and the second dots | w -= Q c' and |w|^2 | h, breakdown test, q_{j+1}
+// and its lattices; each | a grid barrier.  Every block reduces the partial
+// sums itself, in the same order, so all take the same decisions; block 0
+// writes H and evaluates phi_1.
 template <int P>
 __global__ void __launch_bounds__(kExKrylovThreads, 1) k_ex_krylov(ExArgs a, ExKrylov K) {
     constexpr int PT = kExKrylovThreads;
     __shared__ double s_red[PT / 32][kNV + 1];
     __shared__ double s_h[kOutP];
     __shared__ double s_c[kNV + 1];
-    __shared__ double s_x[PT / 32][96];
-    __shared__ double s_dot[PT / 32][40];
+    __shared__ double s_x[PT / 32][32];
+    __shared__ double s_dot[PT / 32][96];
     __shared__ int s_int[3];
-    const int bid = blockIdx.x, nb = gridDim.x, n = a.n, m = K.m;
-    const int a0 = bid * PT + threadIdx.x, stride = nb * PT;
+    const int bid = blockIdx.x, nb = gridDim.x, n = a.n, m = K.m, wid = threadIdx.x >> 5;
+    const long long N3 = 3LL * n;
+    const long long e0 = (long long)bid * PT + threadIdx.x, stride = (long long)nb * PT;
+    const long long wb0 = (long long)bid * PT + wid * 32;
     const bool lead = bid == 0 && threadIdx.x == 0;
     double* __restrict__ w = K.w;
     double* prow = K.part + (size_t)bid * kOutP;
     double nrm = 0.0;
-    for (int i = a0; i < n; i += stride)
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const double x = w[(size_t)f * n + i];
-            nrm += x * x;
-        }
+    for (long long e = e0; e < N3; e += stride) nrm += w[e] * w[e];
     ex_block_sum(nrm, prow, s_dot);
     if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
-    reduce_all<PT>(K.part, 1, s_h, s_red, nb);
+    ex_reduce(K.part, 1, s_h, s_red, nb);
     const double beta = sqrt(s_h[0]);
     int k = m;
     if (!(beta > 0.0) || !isfinite(beta)) {
@@ -265,70 +342,73 @@ __global__ void __launch_bounds__(kExKrylovThreads, 1) k_ex_krylov(ExArgs a, ExK
     }
     if (lead) *K.beta = beta;
     if (k > 0) {
-        ex_new_vector(a, K, 0, 1.0 / beta, bid, nb);
+        ex_new_vector(a, K, 0, 1.0 / beta, e0, stride, s_dot[wid]);
         if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
         for (int j = 0; j < m; ++j) {
             const double* qj = K.basis + (size_t)j * K.ld3;
+            const int nv = j + 1, L = ex_lanes_per_row(nv);
             // w = M q_j; c = Q^T w and |w|^2
             nrm = 0.0;
-            for (int i = a0; i < n; i += stride) {
-                double J[3];
-                ex_point<P>(a, qj, i, J);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) w[(size_t)f * n + i] = J[f];
-                nrm += (J[0] * J[0] + J[1] * J[1]) + J[2] * J[2];
+            double acc = 0.0;
+            for (long long wb = wb0; wb < N3; wb += stride) {
+                const long long e = wb + (threadIdx.x & 31);
+                double x = 0.0;
+                if (e < N3) {
+                    int f, i;
+                    ex_split(e, n, f, i);
+                    x = ex_entry<P>(a, qj, f, i);
+                    w[e] = x;
+                    nrm += x * x;
+                }
+                s_x[wid][threadIdx.x & 31] = x;
+                __syncwarp();
+                acc = ex_warp_dots(K, N3, nv, L, wb, s_x[wid], acc);
+                __syncwarp();
             }
-            __syncthreads();
-            ex_dots(K, n, j + 1, w, prow, s_x, s_dot, bid, nb);
-            ex_block_sum(nrm, prow + j + 1, s_dot);
+            ex_dots_finish(acc, nv, L, prow, s_dot);
+            ex_block_sum(nrm, prow + nv, s_dot);
             if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
-            reduce_all<PT>(K.part, j + 2, s_h, s_red, nb);
-            const double wn2 = s_h[j + 1];
-            for (int t = threadIdx.x; t <= j; t += PT) {
+            ex_reduce(K.part, nv + 1, s_h, s_red, nb);
+            const double wn2 = s_h[nv];
+            for (int t = threadIdx.x; t < nv; t += PT) {
                 s_c[t] = s_h[t];
                 if (bid == 0) K.H[(size_t)t * m + j] = s_h[t];
             }
             __syncthreads();
             // w -= Q c; c' = Q^T w
-            for (int i = a0; i < n; i += stride) {
-                double x[3] = {w[i], w[n + i], w[2 * n + i]};
-                for (int t = 0; t <= j; ++t) {
-                    const double* qt = K.basis + (size_t)t * K.ld3;
-                    const double ct = s_c[t];
-                    x[0] -= ct * qt[i];
-                    x[1] -= ct * qt[n + i];
-                    x[2] -= ct * qt[2 * n + i];
+            acc = 0.0;
+            for (long long wb = wb0; wb < N3; wb += stride) {
+                const long long e = wb + (threadIdx.x & 31);
+                double x = 0.0;
+                if (e < N3) {
+                    x = w[e];
+                    for (int t = 0; t < nv; ++t) x -= s_c[t] * K.basis[(size_t)t * K.ld3 + e];
+                    w[e] = x;
                 }
-#pragma unroll
-                for (int f = 0; f < 3; ++f) w[(size_t)f * n + i] = x[f];
+                s_x[wid][threadIdx.x & 31] = x;
+                __syncwarp();
+                acc = ex_warp_dots(K, N3, nv, L, wb, s_x[wid], acc);
+                __syncwarp();
             }
-            __syncthreads();
-            ex_dots(K, n, j + 1, w, prow, s_x, s_dot, bid, nb);
+            ex_dots_finish(acc, nv, L, prow, s_dot);
             if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
-            reduce_all<PT>(K.part, j + 1, s_h, s_red, nb);
-            for (int t = threadIdx.x; t <= j; t += PT) {
+            ex_reduce(K.part, nv, s_h, s_red, nb);
+            for (int t = threadIdx.x; t < nv; t += PT) {
                 s_c[t] = s_h[t];
                 if (bid == 0) K.H[(size_t)t * m + j] += s_h[t];
             }
             __syncthreads();
             // w -= Q c'; |w|^2
             nrm = 0.0;
-            for (int i = a0; i < n; i += stride) {
-                double x[3] = {w[i], w[n + i], w[2 * n + i]};
-                for (int t = 0; t <= j; ++t) {
-                    const double* qt = K.basis + (size_t)t * K.ld3;
-                    const double ct = s_c[t];
-                    x[0] -= ct * qt[i];
-                    x[1] -= ct * qt[n + i];
-                    x[2] -= ct * qt[2 * n + i];
-                }
-#pragma unroll
-                for (int f = 0; f < 3; ++f) w[(size_t)f * n + i] = x[f];
-                nrm += (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+            for (long long e = e0; e < N3; e += stride) {
+                double x = w[e];
+                for (int t = 0; t < nv; ++t) x -= s_c[t] * K.basis[(size_t)t * K.ld3 + e];
+                w[e] = x;
+                nrm += x * x;
             }
             ex_block_sum(nrm, prow, s_dot);
             if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
-            reduce_all<PT>(K.part, 1, s_h, s_red, nb);
+            ex_reduce(K.part, 1, s_h, s_red, nb);
             const double h = sqrt(s_h[0]);
             if (lead) K.H[(size_t)(j + 1) * m + j] = h;
             const bool bad = !isfinite(h) || !isfinite(wn2);
@@ -338,7 +418,7 @@ __global__ void __launch_bounds__(kExKrylovThreads, 1) k_ex_krylov(ExArgs a, ExK
                 break;
             }
             if (j + 1 == m) break;
-            ex_new_vector(a, K, j + 1, 1.0 / h, bid, nb);
+            ex_new_vector(a, K, j + 1, 1.0 / h, e0, stride, s_dot[wid]);
             if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
         }
     }
@@ -354,16 +434,14 @@ __global__ void __launch_bounds__(kExKrylovThreads, 1) k_ex_krylov(ExArgs a, ExK
     if (!grid_sync(K.bar, K.err, K.limit_ns, bid, nb)) return;
     for (int t = threadIdx.x; t < k; t += PT) s_c[t] = K.dt * beta * K.y[t];
     __syncthreads();
-    for (int i = a0; i < n; i += stride) {
-        const int p = meta_pos(a.meta[i]);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            double inc = 0.0;
-            for (int t = 0; t < k; ++t) inc += s_c[t] * K.basis[(size_t)t * K.ld3 + (size_t)f * n + i];
-            const double x = a.f_out[f][i] + inc;
-            a.f_out[f][i] = x;
-            a.Lb[f][p] = x;
-        }
+    for (long long e = e0; e < N3; e += stride) {
+        int f, i;
+        ex_split(e, n, f, i);
+        double inc = 0.0;
+        for (int t = 0; t < k; ++t) inc += s_c[t] * K.basis[(size_t)t * K.ld3 + e];
+        const double x = a.f_out[f][i] + inc;
+        a.f_out[f][i] = x;
+        a.Lb[f][meta_pos(a.meta[i])] = x;
     }
 }
 

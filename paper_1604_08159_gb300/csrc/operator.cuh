@@ -136,4 +136,35 @@ __device__ __forceinline__ void point_derivs(const T* __restrict__ F, uint32_t m
     }
 }
 
+// One collocation first derivative of a lattice field F at the active point
+// mw along x (axis 0) or y (axis 1), at that axis's stencil level (Sec. 2.5).
+template <typename T, int P>
+__device__ __forceinline__ T point_d1(const T* __restrict__ F, uint32_t mw, const Geom& g, T c1J, int axis) {
+    constexpr int R1 = dd_reach1(P);
+    const int p = meta_pos(mw);
+    const int i = p & g.mask, k = p >> g.L;
+    const int sh = g.J - (axis == 0 ? meta_jx(mw) : meta_jy(mw));
+    const int st = 1 << sh;
+    T fp[R1], fm[R1];
+#pragma unroll
+    for (int o = 0; o < R1; ++o) {
+        if (axis == 0) {
+            fp[o] = F[((size_t)k << g.L) + ((i + (o + 1) * st) & g.mask)];
+            fm[o] = F[((size_t)k << g.L) + ((i - (o + 1) * st) & g.mask)];
+        } else {
+            fp[o] = F[((size_t)((k + (o + 1) * st) & g.mask) << g.L) + i];
+            fm[o] = F[((size_t)((k - (o + 1) * st) & g.mask) << g.L) + i];
+        }
+    }
+    const T c1 = pow2_down(c1J, sh);
+    if constexpr (P == 2) {
+        return (T(8) * (fp[0] - fm[0]) - (fp[1] - fm[1])) * c1;
+    } else {
+        T d = T(dd_d1(P, 1)) * (fp[0] - fm[0]);
+#pragma unroll
+        for (int o = 1; o < R1; ++o) d += T(dd_d1(P, o + 1)) * (fp[o] - fm[o]);
+        return d * c1;
+    }
+}
+
 }  // namespace wrc

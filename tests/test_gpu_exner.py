@@ -127,3 +127,26 @@ def test_vorticity_calls_and_batched_forms_refuse_the_exner_model():
         with pytest.raises(B.WrcError) as e:
             run.exner_init_vortices(W.fujiwhara_small().vortices, 1.0)
         assert e.value.status == -7
+
+
+def test_exner_barrier_wait_limit_runs_out():
+    """A wait limit of 100 ns: a grid barrier of the velocity-Exner Krylov
+    kernel runs out, every block returns, the step reports WRC_ERR_TIMEOUT,
+    and the run steps correctly after a new initial condition."""
+    prm = exner_params()
+    cfg = oracle_config(prm)
+    st = E.exner_vortex_state(cfg, VORT["xc"], VORT["yc"], VORT["gamma"], VORT["s"], 1.0)
+    st1, _ = E.exner_step(cfg, st)
+    vort = W.Vortices(*(np.array(VORT[k]) for k in ("xc", "yc", "gamma", "s")))
+    with B.Run(prm) as run:
+        run.exner_init_vortices(vort, 1.0)
+        run.set_wait_limit(1e-7)
+        with pytest.raises(B.WrcError) as e:
+            run.step(1)
+        assert e.value.status == -5, e.value
+        run.sync()
+        run.set_wait_limit(2.0)
+        run.exner_init_vortices(vort, 1.0)
+        run.step(1)
+        run.sync()
+        _check(run, st1)
