@@ -520,6 +520,47 @@ def measure_exner(args):
             "value": upd / (ms * 1e-3 * n), "unit": UNIT + " (u, v and pi advanced per update)"}
 
 
+def measure_variants(args):
+    """The next rows of the 1024^2 pair's step, each timed alone: the
+    exponential Rosenbrock-Euler step with the full Jacobian (a
+    reconstruction and a Poisson solve per Krylov vector) and the DD orders
+    2p = 6 and 8.  Same workload and initial condition; 3 warm-up steps, then
+    device time per step by CUDA events on the run's stream."""
+    import dataclasses
+
+    import torch
+
+    from paper_1604_08159_gb300 import binding as B
+
+    wl = W.fujiwhara_1024()
+    out = {}
+    for name, change in (("rosenbrock", {"scheme": W.SCHEME_ROSENBROCK}), ("dd_order_6", {"p": 3}),
+                         ("dd_order_8", {"p": 4})):
+        prm = dataclasses.replace(wl.params, **change)
+        stream = torch.cuda.Stream()
+        with B.Run(prm, stream=stream.cuda_stream) as run:
+            run.init_vortices(wl.vortices)
+            run.step(3)
+            run.sync()
+            n = max(1, min(args.steps, 10))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            upd = 0
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(n):
+                upd += run.stats()["n_active"]
+                run.step(1)
+            e1.record(stream)
+            run.sync()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / n
+            kr = run.krylov()
+        out[name] = {"change": change, "steps": n, "ms_per_step": ms, "mean_active_points": upd / n,
+                     "krylov_k": kr["k"], "value": upd / (ms * 1e-3 * n), "unit": UNIT}
+    return out
+
+
 KRYLOV_SOURCES = ("csrc/krylov_impl.cuh", "csrc/krylov.cu", "csrc/operator.cuh", "csrc/common.cuh",
                   "csrc/kernels.h")
 # DRAM bytes per launch of the Krylov kernel on the 1024^2 pair, from one ncu
@@ -770,6 +811,9 @@ def run_ours(args):
     exner = None
     if not args.no_exner and rank == 0:
         exner = measure_exner(args)
+    variants = None
+    if not args.no_variants and rank == 0 and args.workload == "fujiwhara_1024":
+        variants = measure_variants(args)
 
     # max over ranks
     t_dev, upd = combine_ranks(dev_ms, upd, "cuda")
@@ -830,6 +874,7 @@ def run_ours(args):
             "ensemble": ensemble,
             "scalar": scalar,
             "exner": exner,
+            "variants": variants,
             "stages": stages,
         }
         print(json.dumps(line), flush=True)
@@ -855,6 +900,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
     ap.add_argument("--no-exner", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--ens-members", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=50)
