@@ -53,6 +53,7 @@ CASES = [
     dict(scheme=W.SCHEME_FROZEN, gx=0.2, gy=-0.1, rayleigh_r=0.05),
     dict(sgs=W.SGS_APRIORI, cs=0.17, s_apriori=2.0, cpt=25.0, dt=0.05, m=24),
     dict(p=3, J=2, coriolis=-0.8),
+    dict(p=4, J=2, scheme=W.SCHEME_FROZEN, m=16),
 ]
 
 
@@ -150,3 +151,21 @@ def test_exner_barrier_wait_limit_runs_out():
         run.step(1)
         run.sync()
         _check(run, st1)
+
+
+def test_exner_uniform_geostrophic_wind_has_no_krylov_space():
+    """u = G, pi uniform: F(U) = 0 exactly, so beta = 0, the Krylov dimension
+    is 0 and the state does not change (the breakdown path at k = 0)."""
+    prm = exner_params(n0=16, J=2, eps=1e-3, gx=0.3, gy=-0.2, re=float("inf"))
+    NJ = prm.NJ
+    one = np.ones((NJ, NJ))
+    with B.Run(prm) as run:
+        run.exner_init(prm.gx * one, prm.gy * one, 1.2 * one)
+        idx0, u0, v0, p0 = run.exner()
+        run.step(2)
+        run.sync()
+        kr = run.krylov()
+        assert kr["k"] == 0 and kr["beta"] == 0.0
+        idx, u, v, p = run.exner()
+        assert np.array_equal(idx, idx0)
+        assert np.array_equal(u, u0) and np.array_equal(v, v0) and np.array_equal(p, p0)
