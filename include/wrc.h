@@ -224,11 +224,16 @@ wrc_status wrc_apply_operator(wrc_run* run, const double* q, double* w, double* 
 wrc_status wrc_query_krylov(wrc_run* run, double* beta, int32_t* k, double* h_last, double* H,
                             double* y);
 
-/* Diagnostics of the current state, out[0..7] = energy E = 1/2 int |U|^2,
+/* Diagnostics of the current state, out[0..8] = energy E = 1/2 int |U|^2,
  * enstrophy Z = 1/2 int omega^2, palinstrophy P = 1/2 int |grad omega|^2,
  * circulation int omega (rectangle rule on the reconstructed lattice
- * fields), time t, step count, active count, ghost count. */
-wrc_status wrc_diagnostics(wrc_run* run, double out[8]);
+ * fields), time t, step count, active count, ghost count, and the Krylov
+ * error estimate of the last step, dt beta h_{k+1,k} |y_k| with
+ * y = phi_1(dt H_k) e_1 (the residual-based estimate of the projection's
+ * error in the increment; 0 after a breakdown at k = 0 or before any step;
+ * the paper gives no estimate -- this is the standard one for Krylov
+ * approximations of phi_1). */
+wrc_status wrc_diagnostics(wrc_run* run, double out[9]);
 
 /* Counters: out[0] kernel launches made by the library in this process,
  * out[1] steps taken by this run, out[2] host synchronisations made by its

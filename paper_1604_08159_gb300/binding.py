@@ -300,9 +300,9 @@ def wrc_query_krylov(run, m: int):
 
 
 def wrc_diagnostics(run):
-    out = np.zeros(8)
+    out = np.zeros(9)
     _check("wrc_diagnostics", load().wrc_diagnostics(run, out.ctypes.data), run)
-    keys = ("E", "Z", "P", "circulation", "t", "nstep", "n_active", "n_ghost")
+    keys = ("E", "Z", "P", "circulation", "t", "nstep", "n_active", "n_ghost", "krylov_err")
     return dict(zip(keys, out.tolist()))
 
 

@@ -1712,7 +1712,7 @@ wrc_status wrc_query_krylov(wrc_run* R, double* beta, int32_t* k, double* h_last
     return WRC_OK;
 }
 
-wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
+wrc_status wrc_diagnostics(wrc_run* R, double out[9]) {
     TRY(check_ready(R));
     TRY(vorticity_only(R, "wrc_diagnostics"));
     if (!out) return fail(R, WRC_ERR_ARG, "NULL output");
@@ -1729,6 +1729,13 @@ wrc_status wrc_diagnostics(wrc_run* R, double out[8]) {
     out[5] = (double)R->nstep;
     out[6] = (double)R->n_active;
     out[7] = (double)R->n_ghost;
+    out[8] = 0.0;
+    if (R->nstep > 0) {
+        double beta = 0.0, hl = 0.0, y[WRC_MAX_M];
+        int32_t k = 0;
+        TRY(wrc_query_krylov(R, &beta, &k, &hl, nullptr, y));
+        if (k > 0) out[8] = R->cfg.dt * beta * hl * std::fabs(y[k - 1]);
+    }
     return WRC_OK;
 }
 

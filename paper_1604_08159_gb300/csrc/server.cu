@@ -111,7 +111,7 @@ void retire(wrc_server* S, Request* q) {
     wrc_run* R = q->run;
     wrc_status st = q->failed ? q->fail_status : WRC_OK;
     std::string msg = q->fail_msg;
-    double d[8] = {0};
+    double d[9] = {0};
     int64_t na = 0, ng = 0;
     std::vector<int32_t> idx;
     std::vector<double> om;

@@ -188,6 +188,11 @@ def _run_steps_compare(p, vort, nsteps):
         for key in ("E", "Z", "P", "circulation"):
             assert abs(d[key] - od[key]) <= 1e-10 * abs(od[key]), key
         assert d["nstep"] == nsteps
+        # the Krylov error estimate of the last step from the oracle's H and y
+        # (an estimate far below the increment's rounding level, dt beta 1e-12,
+        # is compared only against that level)
+        est = cfg.dt * info.beta * info.h_last * abs(info.y[info.k - 1]) if info.k > 0 else 0.0
+        assert abs(d["krylov_err"] - est) <= 1e-4 * est + 1e-12 * cfg.dt * info.beta
 
 
 def test_steps_pair_128_matches_oracle():
