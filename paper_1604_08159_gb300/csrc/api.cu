@@ -730,7 +730,7 @@ wrc_status krylov_pair(wrc_run* R, const KrylovStepArgs& A) {
     const cudaStream_t s = R->st;
     const int m = R->cfg.krylov_m;
     constexpr int kPairPT = 128;   // threads per block of the batched kernel
-    const int maxb = krylov_batch_max_blocks(R->fp32, R->g.P, kPairPT);
+    const int maxb = krylov_batch_max_blocks(R->fp32, R->g.P, kPairPT, true);
     if (maxb < 2) return fail(R, WRC_ERR_CUDA, "batched Krylov kernel occupancy query failed");
     CK(R->sbasis.grow(R->es * (size_t)R->cap * (m + 1), 0, s));
     CK(R->sw.grow(R->es * (size_t)R->cap, 0, s));
@@ -773,7 +773,7 @@ wrc_status krylov_pair(wrc_run* R, const KrylovStepArgs& A) {
     CK(cudaMemcpyAsync(R->sdev.p, R->shost, bytes, cudaMemcpyHostToDevice, s));
     const KrylovStepArgs* da = (const KrylovStepArgs*)R->sdev.p;
     const int* dblk = (const int*)(da + 2);
-    CK(launch_krylov_batch<T>(da, dblk, dblk + total, 2, total, kPairPT, R->g.P, s));
+    CK(launch_krylov_batch<T>(da, dblk, dblk + total, 2, total, kPairPT, R->g.P, s, true));
     return WRC_OK;
 }
 

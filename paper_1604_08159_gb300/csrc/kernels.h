@@ -273,22 +273,24 @@ size_t krylov_partials_doubles(int max_blocks);
 // Batched Krylov step: `members` problems (device array of arguments) in one
 // cooperative launch of `blocks` blocks of pt (64, 128 or 256) threads; block
 // b works on problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q+1]-1.
-int krylov_batch_max_blocks(bool fp32, int P, int pt);
+// pair: the spill-free form for the two problems of one run (pt = 128).
+int krylov_batch_max_blocks(bool fp32, int P, int pt, bool pair = false);
 template <typename T>
 cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2mem, const int* d_mem_b0,
-                                int members, int blocks, int pt, int P, cudaStream_t s);
+                                int members, int blocks, int pt, int P, cudaStream_t s, bool pair = false);
 
 // The kernels of one bulk type T and DD half-order P (2, 3, 4), compiled per
 // order in krylov_pP.cu: occupancy of the single-run kernel, co-resident
 // capacity for clusters of CL = 2 or 4 blocks, the single-run launch with
 // clusters of cl blocks (1: plain cooperative launch), and the batched
-// kernel for pt threads per block (64, 128, 256; nullptr otherwise).
+// kernel for pt threads per block (64, 128, 256; nullptr otherwise; with
+// pair, its spill-free form, pt = 128 only).
 template <typename T, int P>
 struct KrylovKernels {
     cudaError_t occupancy(int* per);
     int cluster_capacity(int CL);
     cudaError_t launch(const KrylovStepArgs& args, int blocks, int cl, cudaStream_t s);
-    const void* batch_kernel(int pt);
+    const void* batch_kernel(int pt, bool pair = false);
 };
 extern template struct KrylovKernels<double, 2>;
 extern template struct KrylovKernels<float, 2>;

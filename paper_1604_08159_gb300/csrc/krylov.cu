@@ -225,12 +225,12 @@ template cudaError_t launch_krylov_step<float>(const KrylovStepArgs&, int, cudaS
 
 size_t krylov_partials_doubles(int max_blocks) { return (size_t)3 * max_blocks * kOutP; }
 
-int krylov_batch_max_blocks(bool fp32, int P, int pt) {
+int krylov_batch_max_blocks(bool fp32, int P, int pt, bool pair) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void* k = fp32 ? by_order<float>(P, [&](auto K) { return K.batch_kernel(pt); })
-                         : by_order<double>(P, [&](auto K) { return K.batch_kernel(pt); });
+    const void* k = fp32 ? by_order<float>(P, [&](auto K) { return K.batch_kernel(pt, pair); })
+                         : by_order<double>(P, [&](auto K) { return K.batch_kernel(pt, pair); });
     if (!k) return -1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, pt, 0) != cudaSuccess || per < 1) return -2;
     return sms * per;
@@ -238,9 +238,9 @@ int krylov_batch_max_blocks(bool fp32, int P, int pt) {
 
 template <typename T>
 cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2mem, const int* d_mem_b0,
-                                int members, int blocks, int pt, int P, cudaStream_t s) {
+                                int members, int blocks, int pt, int P, cudaStream_t s, bool pair) {
     void* params[] = {(void*)&d_args, (void*)&d_blk2mem, (void*)&d_mem_b0};
-    const void* k = by_order<T>(P, [&](auto K) { return K.batch_kernel(pt); });
+    const void* k = by_order<T>(P, [&](auto K) { return K.batch_kernel(pt, pair); });
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(pt), params, 0, s);
     if (e != cudaSuccess) return e;
@@ -250,8 +250,8 @@ cudaError_t launch_krylov_batch(const KrylovStepArgs* d_args, const int* d_blk2m
 }
 
 template cudaError_t launch_krylov_batch<double>(const KrylovStepArgs*, const int*, const int*, int, int, int, int,
-                                                 cudaStream_t);
+                                                 cudaStream_t, bool);
 template cudaError_t launch_krylov_batch<float>(const KrylovStepArgs*, const int*, const int*, int, int, int, int,
-                                                cudaStream_t);
+                                                cudaStream_t, bool);
 
 }  // namespace wrc

@@ -1127,9 +1127,16 @@ __global__ void __launch_bounds__(PT, 1) k_krylov_step(KrylovStepArgs A) {
 }
 
 // Batched form: several problems in one cooperative launch; block b works on
-// problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q + 1] - 1.
-template <typename T, int PT, int P>
-__global__ void __launch_bounds__(PT, 1) k_krylov_batch(const KrylovStepArgs* __restrict__ args,
+// problem blk2mem[b], whose blocks are mem_b0[q] .. mem_b0[q + 1] - 1.  The
+// ensemble's members have few blocks each, which walk many points, so that
+// form is bound by the latency of those walks and is compiled for MB =
+// batch_min_blocks(PT) resident blocks per SM at the price of register
+// spills (measured faster than one or two spill-free blocks per SM); the two
+// problems of one run (omega and the passive scalar) spread over all SMs
+// and use the spill-free form (MB = 1).
+__host__ __device__ constexpr int batch_min_blocks(int pt) { return pt == 64 ? 8 : (pt == 128 ? 4 : 4); }
+template <typename T, int PT, int P, int MB>
+__global__ void __launch_bounds__(PT, MB) k_krylov_batch(const KrylovStepArgs* __restrict__ args,
                                                         const int* __restrict__ blk2mem,
                                                         const int* __restrict__ mem_b0) {
     const int q = blk2mem[blockIdx.x];
@@ -1196,11 +1203,12 @@ cudaError_t KrylovKernels<T, P>::launch(const KrylovStepArgs& args, int blocks, 
 }
 
 template <typename T, int P>
-const void* KrylovKernels<T, P>::batch_kernel(int pt) {
+const void* KrylovKernels<T, P>::batch_kernel(int pt, bool pair) {
+    if (pair) return pt == 128 ? (const void*)k_krylov_batch<T, 128, P, 1> : nullptr;
     switch (pt) {
-        case 64: return (const void*)k_krylov_batch<T, 64, P>;
-        case 128: return (const void*)k_krylov_batch<T, 128, P>;
-        case 256: return (const void*)k_krylov_batch<T, 256, P>;
+        case 64: return (const void*)k_krylov_batch<T, 64, P, batch_min_blocks(64)>;
+        case 128: return (const void*)k_krylov_batch<T, 128, P, batch_min_blocks(128)>;
+        case 256: return (const void*)k_krylov_batch<T, 256, P, batch_min_blocks(256)>;
         default: return nullptr;
     }
 }

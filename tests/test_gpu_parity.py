@@ -312,3 +312,24 @@ def test_unclustered_krylov_kernel_matches_oracle(cluster, monkeypatch):
     monkeypatch.setenv("WRC_KRYLOV_CLUSTER", cluster)
     wl = W.fujiwhara_small()
     _run_steps_compare(wl.params, wl.vortices, nsteps=3)
+
+
+def test_fujiwhara_128_whole_run_of_50_steps():
+    """The whole 128^2 pair workload (50 steps of dt = 1e-2) against the
+    oracle: the grid identical after every step, omega within the FP64 bound
+    after every tenth, the Krylov dimension equal throughout."""
+    wl = W.fujiwhara_small()
+    cfg = oracle_config(wl.params)
+    v = wl.vortices
+    st = O.initial_state(cfg, v.xc, v.yc, v.gamma, v.s)
+    with B.Run(wl.params) as run:
+        run.init_vortices(v)
+        for n in range(wl.nsteps):
+            st, info = O.step(cfg, st)
+            run.step(1)
+            run.sync()
+            assert run.krylov()["k"] == info.k
+            act, _, _ = run.masks()
+            assert np.array_equal(act, st.active), f"grid differs after step {n + 1}"
+            if (n + 1) % 10 == 0:
+                _state_equal(run, st)
