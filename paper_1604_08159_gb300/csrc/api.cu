@@ -342,12 +342,13 @@ wrc_status rebuild_host(wrc_run* R) {
         if (ev == 16) {
             CK(cudaMemsetAsync(R->K.err, 0, sizeof(int), s));
         } else {
-        CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
-        if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded its capacity of " +
-                                                      std::to_string(R->rmax) + " terms");
-        return fail(R, WRC_ERR_TIMEOUT,
-                    "a grid barrier wait of the Krylov kernel ran out; the run's state is undefined until it is "
-                    "re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
+            CK(cudaMemsetAsync(R->K.err, 0, sizeof(int) * 4, s));   // err and the barrier words
+            if (R->sbar.p) CK(cudaMemsetAsync(R->sbar.p, 0, R->sbar.bytes, s));   // the scalar problem's barrier
+            if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded its capacity of " +
+                                                          std::to_string(R->rmax) + " terms");
+            return fail(R, WRC_ERR_TIMEOUT,
+                        "a grid barrier wait of the Krylov kernel ran out; the run's state is undefined until it "
+                        "is re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
         }
     }
     const long long na = R->counts_host[0];

@@ -84,6 +84,46 @@ def test_grid_barrier_wait_limit_runs_out(cluster_cap, monkeypatch):
         _check_against(fresh, st2)
 
 
+def test_scalar_pair_wait_limit_runs_out():
+    """The passive scalar's step runs omega and r_v as two problems of one
+    cooperative launch, each with its own grid barrier.  With a wait limit
+    of 100 ns a barrier runs out and the step reports WRC_ERR_TIMEOUT; after
+    re-initialising, both problems' barriers start clean and the next steps
+    match the oracle's omega and r_v."""
+    import torch
+    from helpers import small_params
+    p = small_params(n0=16, J=3, eps=1e-3, re=2000.0, m=16)
+    cfg = oracle_config(p)
+    v = W.fujiwhara_small().vortices
+    kappa = 2e-3
+    x = -np.pi + cfg.h * np.arange(cfg.NJ)
+    X, Y = np.meshgrid(x, x)
+    front = 0.5 * (1.0 + np.tanh((Y - 0.3 * np.sin(X)) / 0.2))
+    st = O.initial_state(cfg, v.xc, v.yc, v.gamma, v.s)
+    st, rv = O.scalar_init(cfg, st, front)
+    stream = torch.cuda.Stream()
+    with B.Run(p, stream=stream.cuda_stream) as run:
+        st0 = O.initial_state(cfg, v.xc, v.yc, v.gamma, v.s)
+        run.set_grid(st0.active, st0.omega)
+        run.scalar_init(kappa, front)
+        run.set_wait_limit(1e-7)
+        with pytest.raises(B.WrcError) as e:
+            run.step(1)
+        assert e.value.status == -5, e.value
+        run.sync()
+        run.set_wait_limit(2.0)
+        run.set_grid(st0.active, st0.omega)
+        run.scalar_init(kappa, front)
+        for _ in range(2):
+            st, rv, _, _ = O.step_with_scalar(cfg, st, rv, kappa)
+        run.step(2)
+        run.sync()
+        _check_against(run, st)
+        idx, r = run.scalar()
+        assert np.array_equal(idx, np.flatnonzero(st.active.ravel()))
+        assert rel_l2(r, rv[st.active]) <= 1e-10
+
+
 def test_wait_limit_rejects_out_of_range():
     wl = W.fujiwhara_small()
     with B.Run(wl.params) as run:
