@@ -524,11 +524,9 @@ wrc_status adapt_part1(wrc_run* R) {
     TRY(stage_mark(R, WRC_STAGE_ADAPT));
     TRY(threshold_marks<T>(R, R->cfg.eps, false));
     TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>((T*)R->L, R->act, R->nxt, j, R->g, R->st);
-    if (R->scalar || R->exner)
-        for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>(R->Lr.as<T>(), R->act, R->nxt, j, R->g, R->st);
-    if (R->exner)
-        for (int j = 1; j <= R->g.J; ++j) launch_recon_new<T>(R->Lp.as<T>(), R->act, R->nxt, j, R->g, R->st);
+    launch_recon_new<T>((T*)R->L, R->act, R->nxt, R->g, R->st);
+    if (R->scalar || R->exner) launch_recon_new<T>(R->Lr.as<T>(), R->act, R->nxt, R->g, R->st);
+    if (R->exner) launch_recon_new<T>(R->Lp.as<T>(), R->act, R->nxt, R->g, R->st);
     CKL("new values");
     TRY(stage_mark(R, WRC_STAGE_ADAPT));
     return rebuild_part1(R);
@@ -559,7 +557,7 @@ wrc_status reconstruct(wrc_run* R) {
     launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->cap, (T*)R->L, R->st,
                       R->counts_dev);
     CKL("reconstruct/scatter");
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>((T*)R->L, R->act, j, R->g, R->st);
+    launch_reconstruct<T>((T*)R->L, R->act, R->g, R->st);
     CKL("reconstruct");
     return WRC_OK;
 }
@@ -569,7 +567,7 @@ template <typename T>
 wrc_status reconstruct_scalar(wrc_run* R) {
     launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->rv[R->cur].as<T>(), R->cap, R->Lr.as<T>(), R->st,
                       R->counts_dev);
-    for (int j = 1; j <= R->g.J; ++j) launch_recon_level<T>(R->Lr.as<T>(), R->act, j, R->g, R->st);
+    launch_reconstruct<T>(R->Lr.as<T>(), R->act, R->g, R->st);
     CKL("reconstruct scalar");
     return WRC_OK;
 }
@@ -888,7 +886,7 @@ wrc_status krylov_rosenbrock(wrc_run* R) {
     for (int j = 0; j < m; ++j) {
         // R(q_j) on the lattice (its ghost values included), psi[q_j], U[q_j], V[q_j]
         launch_scatter<T>(meta, R->basis.as<T>() + (size_t)j * R->cap, n, Lq, s);
-        for (int l = 1; l <= g.J; ++l) launch_recon_level<T>(Lq, R->act, l, g, s);
+        launch_reconstruct<T>(Lq, R->act, g, s);
         if (R->fp32) {
             // spectral U, V (as in the freeze): U into the second half of the
             // scratch (the first holds the third FFT work array), V into C1

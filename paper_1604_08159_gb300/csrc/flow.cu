@@ -163,25 +163,57 @@ __global__ void k_sgs4(const T* __restrict__ t2, const T* __restrict__ t0, const
 // the same order as a full lattice pass would use.  The first visit of a
 // halo point (an atomic OR on the 32-bit word holding its mask byte) appends
 // it to the list hlist[1..], count in hlist[0], so the products run over the
-// halo only; the list order varies, the value at each point does not.
+// halo only; the list order varies, the value at each point does not.  The
+// appends of a warp share one atomic addition on the count: each lane keeps
+// the points it visited first as bits, the warp scans their counts, lane 0
+// reserves the warp's total.  The loop runs warp-uniformly (a lane past n
+// takes part with no points), so the warp's shuffles see all 32 lanes.
 template <int P>
 __global__ void k_sgs_halo_mark(const uint32_t* __restrict__ meta, long long n, uint8_t* __restrict__ halo,
                                 int* __restrict__ hlist, Geom g, const int* __restrict__ dn) {
     pdl_wait();
     constexpr int R = dd_reach(P);
+    constexpr int W = 2 * R + 1, NB = W * W, NW = (NB + 31) / 32;
     n = eff_n(dn, n);
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
-         a += (long long)gridDim.x * blockDim.x) {
-        const int p = meta_pos(meta[a]);
-        const int i = p & g.mask, k = p >> g.L;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); a0 < n; a0 += stride) {
+        const long long a = a0 + lane;
+        unsigned fresh[NW];
 #pragma unroll
-        for (int dk = -R; dk <= R; ++dk)
+        for (int w = 0; w < NW; ++w) fresh[w] = 0u;
+        int i = 0, k = 0;
+        if (a < n) {
+            const int p = meta_pos(meta[a]);
+            i = p & g.mask;
+            k = p >> g.L;
 #pragma unroll
-            for (int di = -R; di <= R; ++di) {
+            for (int b = 0; b < NB; ++b) {
+                const int dk = b / W - R, di = b % W - R;
                 const size_t q = ((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask);
                 const unsigned bit = 1u << (8 * (q & 3));
                 const unsigned old = atomicOr(reinterpret_cast<unsigned*>(halo + (q & ~(size_t)3)), bit);
-                if (!(old & bit)) hlist[1 + atomicAdd(hlist, 1)] = (int)q;
+                if (!(old & bit)) fresh[b >> 5] |= 1u << (b & 31);
+            }
+        }
+        int c = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) c += __popc(fresh[w]);
+        int x = c;   // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        int base = 0;
+        if (lane == 0 && total > 0) base = atomicAdd(hlist, total);
+        int off = __shfl_sync(0xffffffffu, base, 0) + x - c;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if ((fresh[b >> 5] >> (b & 31)) & 1u) {
+                const int dk = b / W - R, di = b % W - R;
+                hlist[1 + off++] = (int)(((size_t)((k + dk) & g.mask) << g.L) + ((i + di) & g.mask));
             }
     }
     pdl_trigger();

@@ -2,6 +2,8 @@
 // Eq. 6), thresholding with the adjacent zone, closure under prediction,
 // stencil levels and ghost points (Sec. 2.5), and the stable multi-bucket
 // compaction that turns the masks into index lists.
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace wrc {
@@ -112,6 +114,282 @@ __global__ void k_recon_level_2d(T* __restrict__ L, const uint8_t* __restrict__ 
             }
             L[p] = ddp<T, P>(lo, hi);
         }
+    }
+    pdl_trigger();
+}
+
+// Regions of a tile's reconstruction along one axis: level J is the tile
+// [t0, t0 + ts); level j - 1 covers level j widened by the predictor's reach
+// (2P - 1) 2^(J-j) on each side, rounded outward to the level-(j-1) lattice.
+// lo[j]: first coordinate (fine units; may lie outside [0, NJ): periodic);
+// n[j]: number of level-j lattice points.  The sizes depend on t0 only
+// modulo the coarsest spacing 2^J.
+constexpr int kReconLevels = 11;   // J <= 10
+struct TileAxis {
+    int lo[kReconLevels];
+    int n[kReconLevels];
+};
+struct ReconTiles {
+    int ts, tiles_x, bytes, pmax;
+    int off[kReconLevels];     // level j's values in shared memory (elements of T)
+    int aoff[kReconLevels];    // level j's grid flags (bytes from the start)
+    int pitch[kReconLevels];   // row length of both; value rows: pitch + 2 (2P - 1)
+};
+constexpr int kReconPitchMax = 64;   // a level's region holds at most 64^2 points
+
+__host__ __device__ inline void tile_axis(int t0, int ts, int J, int P, TileAxis& a) {
+    int lo = t0, hi = t0 + ts - 1;
+    a.lo[J] = lo;
+    a.n[J] = ts;
+    for (int j = J; j >= 1; --j) {
+        const int r = (2 * P - 1) << (J - j);
+        const int sh = J - j + 1;   // log2 of the level-(j-1) spacing
+        lo = ((lo - r) >> sh) << sh;
+        hi = ((hi + r + (1 << sh) - 1) >> sh) << sh;
+        a.lo[j - 1] = lo;
+        a.n[j - 1] = ((hi - lo) >> sh) + 1;
+    }
+}
+
+// Tile size and shared-memory layout for the tiled reconstruction (the
+// largest tile of at most 64^2 whose arrays fit kReconSmemMax); false when
+// none does (the level-by-level kernels are used then).
+constexpr int kReconSmemMax = 160 * 1024;
+bool recon_tiles_layout(const Geom& g, size_t es, ReconTiles& lay) {
+    if (g.J >= kReconLevels) return false;
+    const int E = 2 * g.P - 1;
+    int cap = 64;   // tile edge (1024^2, J = 5 on GB300: 64 before 32, 16)
+    if (const char* v = std::getenv("WRC_RECON_TILE")) cap = std::atoi(v);
+    if (cap < 8) return false;   // 0: the level-by-level kernels
+    for (int ts = g.NJ < cap ? g.NJ : cap; ts >= 8 && ts <= g.NJ; ts /= 2) {
+        int nmax[kReconLevels] = {0};
+        const int per = 1 << g.J;
+        for (int t0 = 0; t0 < (per > ts ? per : ts); t0 += ts) {
+            TileAxis a;
+            tile_axis(t0, ts, g.J, g.P, a);
+            for (int j = 0; j <= g.J; ++j) nmax[j] = a.n[j] > nmax[j] ? a.n[j] : nmax[j];
+        }
+        long long off = 0;
+        int pmax = 0;
+        for (int j = 0; j <= g.J; ++j) {
+            lay.off[j] = (int)off;
+            lay.pitch[j] = nmax[j];
+            off += (long long)(nmax[j] + 2 * E) * nmax[j];
+            pmax = nmax[j] > pmax ? nmax[j] : pmax;
+        }
+        long long b = off * (long long)es;
+        for (int j = 0; j <= g.J; ++j) {
+            lay.aoff[j] = (int)b;
+            b += (long long)nmax[j] * nmax[j];
+        }
+        if (pmax <= kReconPitchMax && b <= kReconSmemMax) {
+            lay.pmax = pmax;
+            lay.ts = ts;
+            lay.tiles_x = g.NJ / ts;
+            lay.bytes = (int)b;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Entry t = u + v n of a loop over rows n wide, t advancing by kThreads,
+// without a division per step.
+struct RowWalk {
+    int u, v, du, dv, n;
+    __device__ __forceinline__ RowWalk(int t, int n_) : n(n_) {
+        u = t % n;
+        v = t / n;
+        du = kThreads % n;
+        dv = kThreads / n;
+    }
+    __device__ __forceinline__ void next() {
+        u += du;
+        v += dv;
+        if (u >= n) {
+            u -= n;
+            ++v;
+        }
+    }
+};
+
+// The whole coarse-to-fine inverse transform in one launch, one tile of the
+// finest lattice per block.  A block reconstructs the values of every level
+// over its tile widened, level by level, by the predictor's reach (points
+// of the level-j lattice within (2P - 1) 2^(J-j) fine cells of the region
+// of level j + 1), in shared memory: levels are not synchronised across
+// blocks; each block recomputes the coarse values its tile depends on.
+// At level j, phase 1 copies the points of level j - 1 and makes the 1-D
+// predictions: of the points odd in x only (also in 2P - 1 extra rows above
+// and below the region, for phase 2) and of those odd in y only; phase 2
+// predicts the points odd in both directions from the x predictions of
+// phase 1 (the tensor product, y over x, as predict does); phase 3 puts the
+// values of grid points in place of their predictions and stores the
+// non-grid points of the tile.  The operations and their order are those of
+// the level-by-level kernels, so L is bit-identical.  Only non-grid points
+// are written, each by the block whose tile holds it; grid points are only
+// read.
+// FP64 issue is a bound (a warp instruction costs the same whatever the
+// number of active lanes), so each loop enumerates only its own kind of
+// point: every lane of a warp makes a prediction of the same form, from
+// operands at base - q d and base + (1 + q) d (d = 1 along x, the row pitch
+// along y).  Loads are issued ahead of their use: each level's grid values
+// into registers before its predictions (used in phase 3), the next level's
+// grid flags during this level's predictions.
+template <typename T, int P, int PMAX>
+__global__ void __launch_bounds__(kThreads) k_recon_tiles(T* __restrict__ L, const uint8_t* __restrict__ act, Geom g,
+                                                          ReconTiles lay) {
+    extern __shared__ __align__(16) unsigned char recon_smem[];
+    T* sm = reinterpret_cast<T*>(recon_smem);
+    constexpr int E = 2 * P - 1;   // extra rows of x predictions on each side
+    constexpr int kPre = (PMAX * PMAX + kThreads - 1) / kThreads;   // entries of a region per thread
+    const int ts = lay.ts, m = g.mask;
+    const int x0 = (int)(blockIdx.x % lay.tiles_x) * ts, y0 = (int)(blockIdx.x / lay.tiles_x) * ts;
+    TileAxis ax, ay;
+    tile_axis(x0, ts, g.J, P, ax);
+    tile_axis(y0, ts, g.J, P, ay);
+    // grid flags of the level-j points of level j's region (entries
+    // threadIdx.x + t kThreads): loaded into fv, then stored to shared memory
+    uint8_t fv[kPre];
+    auto load_flags = [&](int j) {
+        const int sh = g.J - j, nx = ax.n[j], ny = ay.n[j];
+        RowWalk w(threadIdx.x, nx);
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            fv[t] = 0;
+            if (w.v >= ny) break;
+            const int i = ax.lo[j] + (w.u << sh), k = ay.lo[j] + (w.v << sh);
+            if (((i >> sh) | (k >> sh)) & 1) fv[t] = act[((size_t)(k & m) << g.L) + (i & m)];
+            w.next();
+        }
+    };
+    auto store_flags = [&](int j) {
+        const int nx = ax.n[j], ny = ay.n[j], pitch = lay.pitch[j];
+        uint8_t* F = recon_smem + lay.aoff[j];
+        RowWalk w(threadIdx.x, nx);
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            if (w.v >= ny) break;
+            F[w.v * pitch + w.u] = fv[t];
+            w.next();
+        }
+    };
+    pdl_wait();
+    load_flags(1);
+    {
+        // level 0: every point is a grid point (and is never written)
+        T* A = sm + lay.off[0];
+        const int pitch = lay.pitch[0], nx = ax.n[0], ny = ay.n[0], sh = g.J;
+        for (int e = threadIdx.x; e < nx * ny; e += kThreads) {
+            const int c = e % nx, r = e / nx;
+            const int i = (ax.lo[0] + (c << sh)) & m, k = (ay.lo[0] + (r << sh)) & m;
+            A[(r + E) * pitch + c] = L[((size_t)k << g.L) + i];
+        }
+    }
+    store_flags(1);
+    __syncthreads();
+    for (int j = 1; j <= g.J; ++j) {
+        const int sh = g.J - j;
+        const T* C = sm + lay.off[j - 1];
+        const int cp = lay.pitch[j - 1], cx0 = ax.lo[j - 1], cy0 = ay.lo[j - 1];
+        T* A = sm + lay.off[j];
+        const uint8_t* F = recon_smem + lay.aoff[j];
+        const int pitch = lay.pitch[j], nx = ax.n[j], ny = ay.n[j], lx = ax.lo[j], ly = ay.lo[j];
+        // this thread's grid values of phase 3 (entries threadIdx.x + t kThreads)
+        T pv[kPre];
+        {
+            RowWalk w(threadIdx.x, nx);
+#pragma unroll
+            for (int t = 0; t < kPre; ++t) {
+                pv[t] = T(0);
+                if (w.v >= ny) break;
+                if (F[w.v * pitch + w.u])
+                    pv[t] = L[((size_t)((ly + (w.v << sh)) & m) << g.L) + ((lx + (w.u << sh)) & m)];
+                w.next();
+            }
+        }
+        if (j < g.J) load_flags(j + 1);
+        // first odd and even columns, even rows (all), odd rows (the region's)
+        const int co0 = ((lx >> sh) & 1) ? 0 : 1, ce0 = 1 - co0;
+        const int nxo = (nx - co0 + 1) >> 1, nxe = (nx - ce0 + 1) >> 1;
+        const int re0 = ((ly >> sh) - E) & 1, nre = (ny + 2 * E - re0 + 1) >> 1;
+        const int ro0 = E + (((ly >> sh) & 1) ? 0 : 1), nro = (ny - (ro0 - E) + 1) >> 1;
+        // row rr of A holds fine row ly + (rr - E) s; its level-(j-1) row in C
+        // is (rr - E + (ly - cy0) / s) / 2 + E, its column c is (c + (lx - cx0) / s) / 2
+        const int dr = (ly - cy0) >> sh, dc = (lx - cx0) >> sh;
+        if (nxo > 0) {   // odd in x only: along the row, from level j - 1
+            RowWalk w(threadIdx.x, nxo);
+#pragma unroll 4
+            for (int t = threadIdx.x; t < nxo * nre; t += kThreads) {
+                const int c = co0 + 2 * w.u, rr = re0 + 2 * w.v;
+                const int b = (((rr - E + dr) >> 1) + E) * cp + ((c - 1 + dc) >> 1);
+                T lo[P], hi[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    lo[q] = C[b - q];
+                    hi[q] = C[b + 1 + q];
+                }
+                A[rr * pitch + c] = ddp<T, P>(lo, hi);
+                w.next();
+            }
+        }
+        if (nxe > 0) {   // odd in y only: along the column
+            RowWalk w(threadIdx.x, nxe);
+#pragma unroll 4
+            for (int t = threadIdx.x; t < nxe * nro; t += kThreads) {
+                const int c = ce0 + 2 * w.u, rr = ro0 + 2 * w.v;
+                const int b = (((rr - 1 - E + dr) >> 1) + E) * cp + ((c + dc) >> 1);
+                T lo[P], hi[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    lo[q] = C[b - q * cp];
+                    hi[q] = C[b + (1 + q) * cp];
+                }
+                A[rr * pitch + c] = ddp<T, P>(lo, hi);
+                w.next();
+            }
+            RowWalk wc(threadIdx.x, nxe);
+#pragma unroll 4
+            for (int t = threadIdx.x; t < nxe * nre; t += kThreads) {   // points of level j - 1
+                const int c = ce0 + 2 * wc.u, rr = re0 + 2 * wc.v;
+                A[rr * pitch + c] = C[(((rr - E + dr) >> 1) + E) * cp + ((c + dc) >> 1)];
+                wc.next();
+            }
+        }
+        __syncthreads();
+        if (nxo > 0) {   // odd in both: y over the x predictions
+            RowWalk w(threadIdx.x, nxo);
+#pragma unroll 4
+            for (int t = threadIdx.x; t < nxo * nro; t += kThreads) {
+                const int c = co0 + 2 * w.u, r = ro0 + 2 * w.v;
+                T lo[P], hi[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    lo[q] = A[(r - (2 * q + 1)) * pitch + c];
+                    hi[q] = A[(r + (2 * q + 1)) * pitch + c];
+                }
+                A[r * pitch + c] = ddp<T, P>(lo, hi);
+                w.next();
+            }
+        }
+        __syncthreads();
+        {
+            RowWalk w(threadIdx.x, nx);
+#pragma unroll
+            for (int t = 0; t < kPre; ++t) {
+                if (w.v >= ny) break;
+                const int i = lx + (w.u << sh), k = ly + (w.v << sh);
+                if (((i >> sh) | (k >> sh)) & 1) {
+                    T* a = A + (w.v + E) * pitch + w.u;
+                    if (F[w.v * pitch + w.u]) *a = pv[t];
+                    else if (i >= x0 && i < x0 + ts && k >= y0 && k < y0 + ts)
+                        L[((size_t)(k & m) << g.L) + (i & m)] = *a;
+                }
+                w.next();
+            }
+        }
+        if (j < g.J) store_flags(j + 1);
+        __syncthreads();
     }
     pdl_trigger();
 }
@@ -895,8 +1173,25 @@ void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStre
     note_launch();
 }
 template <typename T>
-void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, int j, const Geom& g, cudaStream_t s) {
-    { launch_pdl(k_recon_new<T>, blocks_for(level_count(j, g)), kThreads, 0, s, L, act, nxt, j, g); note_launch(); }
+void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, const Geom& g, cudaStream_t s) {
+    for (int j = 1; j <= g.J; ++j) {
+        launch_pdl(k_recon_new<T>, blocks_for(level_count(j, g)), kThreads, 0, s, L, act, nxt, j, g);
+        note_launch();
+    }
+}
+template <typename T>
+void launch_reconstruct(T* L, const uint8_t* act, const Geom& g, cudaStream_t s) {
+    ReconTiles lay;
+    if (recon_tiles_layout(g, sizeof(T), lay)) {
+        auto k = lay.pmax <= 32
+                     ? (g.P == 3 ? k_recon_tiles<T, 3, 32> : (g.P == 4 ? k_recon_tiles<T, 4, 32> : k_recon_tiles<T, 2, 32>))
+                     : (g.P == 3 ? k_recon_tiles<T, 3, 64> : (g.P == 4 ? k_recon_tiles<T, 4, 64> : k_recon_tiles<T, 2, 64>));
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.bytes);
+        launch_pdl(k, lay.tiles_x * lay.tiles_x, kThreads, lay.bytes, s, L, act, g, lay);
+        note_launch();
+        return;
+    }
+    for (int j = 1; j <= g.J; ++j) launch_recon_level<T>(L, act, j, g, s);
 }
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det, uint8_t* sig,
@@ -971,8 +1266,8 @@ void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx
 #define WRC_INST(T)                                                                                       \
     template void launch_init_vortices<T>(T*, const double*, int, const Geom&, cudaStream_t);             \
     template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t, const int*);  \
-    template void launch_recon_level<T>(T*, const uint8_t*, int, const Geom&, cudaStream_t);              \
-    template void launch_recon_new<T>(T*, const uint8_t*, const uint8_t*, int, const Geom&, cudaStream_t);\
+    template void launch_reconstruct<T>(T*, const uint8_t*, const Geom&, cudaStream_t);                   \
+    template void launch_recon_new<T>(T*, const uint8_t*, const uint8_t*, const Geom&, cudaStream_t);     \
     template void launch_details_adj<T>(const uint32_t*, long long, const T*, double, T*, uint8_t*,       \
                                         uint8_t*, const Geom&, cudaStream_t, const int*);                 \
     template void launch_finalize<T>(const int*, long long, const uint8_t*, const T*, uint32_t*, T*,      \

@@ -12,12 +12,16 @@ void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cuda
 // given (n is then the capacity the grid covers; capturable in a CUDA graph).
 template <typename T>
 void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn = nullptr);
+// L <- R(u): the values at the grid points of act stay, every other lattice
+// point gets its coarse-to-fine DD prediction (Eq. 6, detail zero).  One
+// tiled launch (or, where its shared-memory arrays do not fit, two launches
+// per level).
 template <typename T>
-void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s);
-// Values at the level-j points of the new grid nxt that are not in act, by
-// DD prediction from the values of act (levels in increasing order).
+void launch_reconstruct(T* L, const uint8_t* act, const Geom& g, cudaStream_t s);
+// Values at the points of the new grid nxt that are not in act, by DD
+// prediction from the values of act (one launch per level, coarse to fine).
 template <typename T>
-void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, int j, const Geom& g, cudaStream_t s);
+void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, const Geom& g, cudaStream_t s);
 template <typename T>
 void launch_details_adj(const uint32_t* meta, long long n, const T* L, double eps, T* det,
                         uint8_t* sig, uint8_t* nxt, const Geom& g, cudaStream_t s, const int* dn = nullptr);
