@@ -156,11 +156,13 @@ wrc_status wrc_step(wrc_run* run, int32_t nsteps);
 wrc_status wrc_sync(wrc_run* run, int32_t timeout_ms);
 
 /* Bound of every device-side wait of the run's kernels (the grid barriers of
- * the cooperative Krylov kernel), in seconds, 0 < seconds <= 60; default 2 s.
- * A wait that runs out sets an error word and every block of the kernel
- * returns; the step then fails with WRC_ERR_TIMEOUT and the run's state is
- * undefined until a new initial condition (wrc_init_*, wrc_set_grid) or
- * wrc_destroy.  WRC_ERR_ARG outside the range. */
+ * the cooperative Krylov kernel; in the grid rebuild, a ghost's wait for the
+ * interpolation rows of its coarser ghost predictors), in seconds,
+ * 0 < seconds <= 60; default 2 s.  A wait that runs out sets an error word
+ * and the kernel returns; the step (for a rebuild's wait: the next step)
+ * then fails with WRC_ERR_TIMEOUT and the run's state is undefined until a
+ * new initial condition (wrc_init_*, wrc_set_grid) or wrc_destroy.
+ * WRC_ERR_ARG outside the range. */
 wrc_status wrc_set_wait_limit(wrc_run* run, double seconds);
 
 /* Thread-block cluster size (1, 2 or 4) of the run's next Krylov launch on

@@ -120,6 +120,7 @@ struct wrc_run {
     long long cap = 0;
     // ghost interpolation rows and the ghost values of the basis vectors
     DevBuf row_len, row_idx, row_w, Gb;
+    DevBuf row_ready;   // cap_g + 1 ints: ready flags of the rows, the ghost counter
     long long cap_g = 0;
 
     // Krylov small arrays and cooperative-kernel scratch
@@ -294,12 +295,13 @@ wrc_status ensure_capacity(wrc_run* R, long long n) {
 }
 
 wrc_status ensure_ghost_capacity(wrc_run* R, long long ng) {
-    if (ng <= R->cap_g) return WRC_OK;
+    if (ng <= R->cap_g && R->row_ready.p) return WRC_OK;   // the ready flags exist even for a grid without ghosts
     long long c = ng + ng / 4 + 1024;
     c = (c + 255) / 256 * 256;
     const cudaStream_t s = R->st;
     const int m = R->cfg.krylov_m;
     CK(R->row_len.grow(sizeof(int) * c, 0, s));
+    CK(R->row_ready.grow(sizeof(int) * (c + 1), 0, s));
     CK(R->row_idx.grow(sizeof(int) * c * R->rmax, 0, s));
     CK(R->row_w.grow(sizeof(double) * c * R->rmax, 0, s));
     R->Gb.release(s);
@@ -347,8 +349,9 @@ wrc_status rebuild_host(wrc_run* R) {
             if (ev & 4) return fail(R, WRC_ERR_STATE, "a ghost interpolation row exceeded its capacity of " +
                                                           std::to_string(R->rmax) + " terms");
             return fail(R, WRC_ERR_TIMEOUT,
-                        "a grid barrier wait of the Krylov kernel ran out; the run's state is undefined until it "
-                        "is re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
+                        "a bounded wait ran out (a grid barrier of the Krylov kernel, or a ghost's wait for a "
+                        "coarser ghost's interpolation row); the run's state is undefined until it is "
+                        "re-initialised (wrc_init_vortices, wrc_init_field, wrc_set_grid)");
         }
     }
     const long long na = R->counts_host[0];
@@ -381,8 +384,9 @@ wrc_status rebuild_part2(wrc_run* R) {
         launch_finalize<T>(R->list, R->cap, R->JJ, R->Lp.as<T>(), R->meta[nc].as<uint32_t>(), R->pe[nc].as<T>(), s,
                            R->counts_dev);
     CK(cudaMemsetAsync(R->K.overflow, 0, sizeof(int), s));
-    launch_ghost_rows(R->list, 0, nullptr, nullptr, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(),
-                      R->row_w.as<double>(), R->rmax, R->g, R->K.overflow, s, R->counts_dev, R->cap, R->cap_g);
+    launch_ghost_rows(R->list, R->g.J, R->lat2idx, R->row_len.as<int>(), R->row_idx.as<int>(), R->row_w.as<double>(),
+                      R->rmax, R->g, R->K.overflow, R->row_ready.as<int>(), R->K.err, R->wait_limit_ns, s,
+                      R->counts_dev, R->cap, R->cap_g);
     CKL("finalize");
     return WRC_OK;
 }
@@ -1236,7 +1240,8 @@ void free_run(wrc_run* R) {
     cudaStream_t s = R->st;
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
-                    &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb, &R->lat64, &R->trace, &R->rv[0],
+                    &R->basis, &R->tmp, &R->row_len, &R->row_ready, &R->row_idx, &R->row_w, &R->Gb, &R->lat64,
+                    &R->trace, &R->rv[0],
                     &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall, &R->pe[0], &R->pe[1], &R->Lp, &R->Lqx,
                     &R->xd, &R->xbasis, &R->xw, &R->sbasis, &R->sw, &R->sGb, &R->sLq, &R->spart, &R->sbar, &R->sdev})
         b->release(s);
@@ -1777,6 +1782,7 @@ wrc_status wrc_set_wait_limit(wrc_run* R, double seconds) {
     if (!(seconds > 0) || !(seconds <= 60.0)) return fail(R, WRC_ERR_ARG, "the wait limit must be in (0, 60] s");
     double ns = std::ceil(seconds * 1e9);
     R->wait_limit_ns = (unsigned long long)(ns < 1.0 ? 1.0 : ns);
+    R->layout += 1;   // the captured rebuild phase holds the limit in its ghost-row launch
     return WRC_OK;
 }
 
@@ -2172,8 +2178,8 @@ double wrc::run_bytes_for(const wrc_config& cfg, long long na, long long ng) {
     const double c = (double)grown_capacity(na), cg = (double)grown_capacity(ng);
     // meta x2, omega x2, details, U, V, g, w, basis (m+1), doubles scratch
     b += c * (8.0 + 2.0 * es + 5.0 * es + es * m1 + 8.0);
-    // ghost rows: length, dd_row_max(p) indices and weights; ghost basis values
-    b += cg * (4.0 + (4.0 + 8.0) * dd_row_max(cfg.p == 0 ? 2 : cfg.p) + es * m1);
+    // ghost rows: length, ready flag, dd_row_max(p) indices and weights; ghost basis values
+    b += cg * (8.0 + (4.0 + 8.0) * dd_row_max(cfg.p == 0 ? 2 : cfg.p) + es * m1) + 4.0;
     return b;
 }
 
@@ -2188,7 +2194,8 @@ double wrc::run_device_bytes(const wrc_run* R) {
     b += 8.0 * (m1 * cfg.krylov_m + 33) +
          8.0 * (double)std::max(krylov_partials_doubles(R->max_blocks), (size_t)kMaxBlocks * 4);
     const DevBuf* bufs[] = {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga,
-                            &R->det, &R->w, &R->basis, &R->tmp, &R->row_len, &R->row_idx, &R->row_w, &R->Gb};
+                            &R->det, &R->w, &R->basis, &R->tmp, &R->row_len, &R->row_ready, &R->row_idx, &R->row_w,
+                            &R->Gb};
     for (const DevBuf* d : bufs) b += (double)d->bytes;
     return b;
 }

@@ -822,13 +822,62 @@ __global__ void k_lat2idx(const int* __restrict__ list, long long n, int* __rest
     pdl_trigger();
 }
 
-// Interpolation rows of the ghosts of one level: the value of a ghost is the
-// DD prediction from its predictor points, which are active points or ghosts
-// of coarser levels (whose rows exist already); substituting gives the ghost
+// ---- interpolation rows of all ghosts in one launch ----------------------
+// The ghosts are numbered in list order, coarser levels first, and a ghost's
+// row depends only on rows of coarser ghosts.  Each warp takes the next
+// ghost number from a counter (in increasing order), waits until the rows of
+// its ghost predictors are published, builds its row and publishes it (a
+// release store of its ready flag after the row's writes).  The smallest
+// unfinished number depends only on smaller numbers, which were all taken
+// by running warps and are finished, so the waits always end, whatever the
+// number of resident warps.  Each wait is also bounded by limit_ns (bit 1 of
+// *err when it runs out; the next Krylov step then stops and reports it).
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The warp's next ghost number (lane 0 takes it from the counter *next).
+__device__ __forceinline__ long long next_ghost(int* next, long long ng, int lane) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(next, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < ng ? (long long)t : ng;
+}
+
+__device__ __forceinline__ void wait_ready(const int* flag, int* err, unsigned long long limit_ns) {
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v) return;
+        if (*(volatile int*)err & 2) return;   // another wait ran out
+        if (it == 0) {
+            t0 = globaltimer_ns();
+        } else if (globaltimer_ns() - t0 > limit_ns) {
+            atomicOr(err, 2);
+            return;
+        }
+    }
+}
+
+// The row of ghost gi is complete (every lane's writes ordered before lane
+// 0's release store of the flag).
+__device__ __forceinline__ void publish_ready(int* flag, int lane) {
+    __syncwarp();
+    if (lane == 0) asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flag), "r"(1) : "memory");
+    __syncwarp();
+}
+
+// Interpolation rows of the ghosts: the value of a ghost is the DD
+// prediction from its predictor points, which are active points or ghosts
+// of coarser levels (whose rows are published first); substituting gives the ghost
 // as a weighted sum of active values.  The weights are products of the DD4
 // weights (-1, 9, 9, -1)/16, exact binary fractions, and repeated points are
 // merged, so the rows are exact.  A row longer than rmax sets *overflow.
-// One warp per ghost.  Lane q < 16 takes predictor q (order: a fastest, then
+// One warp per ghost at a time.  Lane q < 16 takes predictor q (order: a fastest, then
 // b; 4 predictors for a 1-D prediction, 16 for the tensor product), looks up
 // its grid index and, for a ghost, its row length; the rows (up to
 // kRowStage entries each) are then staged in shared memory with all loads in
@@ -848,10 +897,10 @@ __constant__ double c_dd4w[4] = {-0.0625, 0.5625, 0.5625, -0.0625};
 __device__ __forceinline__ int row_hash(int key) { return (int)(((unsigned)key * 2654435761u) >> 25); }
 
 __global__ void __launch_bounds__(32 * kRowWarps)
-k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
-                   const int* __restrict__ lat2idx, int* __restrict__ row_len, int* __restrict__ row_idx,
-                   double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
-                   const int* __restrict__ dcounts, int nkeys) {
+k_ghost_rows(const int* __restrict__ list, const int* __restrict__ lat2idx, int* __restrict__ row_len,
+             int* __restrict__ row_idx, double* __restrict__ row_w, int rmax, Geom g, int* __restrict__ overflow,
+             const int* __restrict__ dcounts, int nkeys, int* __restrict__ ready, int* __restrict__ err,
+             unsigned long long limit_ns, int stall) {
     pdl_wait();
     constexpr int kCap = 64;
     static_assert(kRowHash >= 2 * kCap && (kRowHash & (kRowHash - 1)) == 0 && kRowHash == 128, "row_hash gives 7 bits");
@@ -870,23 +919,19 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
     int* hpos = s_hpos[wid];
     for (int h = lane; h < kRowHash; h += 32) hkey[h] = -1;
     __syncwarp();
-    if (dcounts) {   // key 0: active points, key l: ghosts of level l
-        n_act = dcounts[0];
-        gbeg = 0;
-        n_tot = 0;
-        for (int q = 0; q < nkeys; ++q) {
-            if (q < j) gbeg += dcounts[q];
-            n_tot += dcounts[q];
-        }
-        cnt = dcounts[j];
-    }
+    long long n_act = dcounts[0], n_tot = 0;   // key 0: active points, key l: ghosts of level l
+    for (int q = 0; q < nkeys; ++q) n_tot += dcounts[q];
+    const long long ng = n_tot - n_act;
     const int cap = rmax < kCap ? rmax : kCap;
-    const int sh = g.J - j;
-    const int s = 1 << sh;
-    for (long long t = (long long)blockIdx.x * kRowWarps + wid; t < cnt; t += (long long)gridDim.x * kRowWarps) {
-        const long long gi = gbeg - n_act + t;          // ghost number
-        const int p = list[gbeg + t];
+    for (;;) {
+        if (ng <= 0) break;   // no ghosts: the counter is not touched
+        const long long gi = next_ghost(ready + ng, ng, lane);   // ghost number, in list order
+        if (gi >= ng) break;
+        if (stall && gi == 0 && lane == 0) wait_ready(ready + gi, err, limit_ns);   // test switch: runs out
+        const int p = list[n_act + gi];
         const int i = p & g.mask, k = p >> g.L;
+        const int sh = g.J - level_of(i, k, g.J);
+        const int s = 1 << sh;
         const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
         const bool two_d = oi == ok;                    // odd-odd: tensor product of two 1-D predictions
         const int np = two_d ? 16 : 4;
@@ -905,9 +950,14 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
                 qk = (k + off_a) & g.mask;
             }
             my_id = lat2idx[((long long)qk << g.L) + qi];
-            if (my_id >= n_act && my_id < n_tot) my_rl = row_len[my_id - n_act];
-            else my_rl = 1;
+            if (my_id >= n_act && my_id < n_tot) {   // a coarser ghost: its row once published
+                wait_ready(ready + (my_id - n_act), err, limit_ns);
+                my_rl = row_len[my_id - n_act];
+            } else {
+                my_rl = 1;
+            }
         }
+        __syncwarp();
         // stage the predictor rows (their loads all in flight)
         for (int q = 0; q < np; ++q) {
             const int id = __shfl_sync(0xffffffffu, my_id, q);
@@ -991,22 +1041,22 @@ k_ghost_rows_level(const int* __restrict__ list, long long gbeg, long long cnt, 
             row_len[gi] = len;
             if (over) atomicOr(overflow, 4);
         }
-        __syncwarp();
+        publish_ready(ready + gi, lane);
     }
     pdl_trigger();
 }
 
-// Interpolation rows of the ghosts of one level for DD orders 2P > 4: as
-// k_ghost_rows_level (same merge in predictor order, same per-warp hash table),
+// Interpolation rows of the ghosts for DD orders 2P > 4: as k_ghost_rows
+// (same order of work, waits and publication; same merge in predictor order, same per-warp hash table),
 // with 2P or (2P)^2 predictors, their weights dd_pred(P, .) 2^-shift (products
 // of two for the tensor product), rows of up to dd_row_max(P) entries, and the
 // predictors' rows read from global memory (no staging).
 template <int P>
 __global__ void __launch_bounds__(32 * kRowWarps)
-k_ghost_rows_level_wide(const int* __restrict__ list, long long gbeg, long long cnt, long long n_act, long long n_tot,
-                        const int* __restrict__ lat2idx, int* __restrict__ row_len, int* __restrict__ row_idx,
-                        double* __restrict__ row_w, int rmax, int j, Geom g, int* __restrict__ overflow,
-                        const int* __restrict__ dcounts, int nkeys) {
+k_ghost_rows_wide(const int* __restrict__ list, const int* __restrict__ lat2idx, int* __restrict__ row_len,
+                  int* __restrict__ row_idx, double* __restrict__ row_w, int rmax, Geom g, int* __restrict__ overflow,
+                  const int* __restrict__ dcounts, int nkeys, int* __restrict__ ready, int* __restrict__ err,
+                  unsigned long long limit_ns, int stall) {
     pdl_wait();
     constexpr int kCapW = dd_row_max(P);
     constexpr int kHashW = 2 * kCapW;
@@ -1026,29 +1076,28 @@ k_ghost_rows_level_wide(const int* __restrict__ list, long long gbeg, long long 
     int* hpos = s_hpos[wid];
     for (int h = lane; h < kHashW; h += 32) hkey[h] = -1;
     __syncwarp();
-    if (dcounts) {
-        n_act = dcounts[0];
-        gbeg = 0;
-        n_tot = 0;
-        for (int q = 0; q < nkeys; ++q) {
-            if (q < j) gbeg += dcounts[q];
-            n_tot += dcounts[q];
-        }
-        cnt = dcounts[j];
-    }
+    long long n_act = dcounts[0], n_tot = 0;
+    for (int q = 0; q < nkeys; ++q) n_tot += dcounts[q];
+    const long long ng = n_tot - n_act;
     const int cap = rmax < kCapW ? rmax : kCapW;
-    const int sh = g.J - j;
-    const int s = 1 << sh;
+    if (ng <= 0) {   // no ghosts: the counter is not touched
+        pdl_trigger();
+        return;
+    }
     const double scale = 1.0 / (double)(1 << dd_shift(P));
     auto w1 = [&](int a) {   // weight of the a-th predictor along one axis
         const int o = 2 * a + 1 - NP1;
         return dd_pred(P, ((o < 0 ? -o : o) - 1) >> 1) * scale;
     };
     auto hash = [](int key) { return (int)(((unsigned)key * 2654435761u) >> (32 - kHashBits)); };
-    for (long long t = (long long)blockIdx.x * kRowWarps + wid; t < cnt; t += (long long)gridDim.x * kRowWarps) {
-        const long long gi = gbeg - n_act + t;
-        const int p = list[gbeg + t];
+    for (;;) {
+        const long long gi = next_ghost(ready + ng, ng, lane);
+        if (gi >= ng) break;
+        if (stall && gi == 0 && lane == 0) wait_ready(ready + gi, err, limit_ns);   // test switch: runs out
+        const int p = list[n_act + gi];
         const int i = p & g.mask, k = p >> g.L;
+        const int sh = g.J - level_of(i, k, g.J);
+        const int s = 1 << sh;
         const bool oi = (i >> sh) & 1, ok = (k >> sh) & 1;
         const bool two_d = oi == ok;
         const int np = two_d ? NP1 * NP1 : NP1;
@@ -1069,8 +1118,14 @@ k_ghost_rows_level_wide(const int* __restrict__ list, long long gbeg, long long 
                     qk = (k + (2 * a + 1 - NP1) * s) & g.mask;
                 }
                 my_id = lat2idx[((long long)qk << g.L) + qi];
-                my_rl = (my_id >= n_act && my_id < n_tot) ? row_len[my_id - n_act] : 1;
+                if (my_id >= n_act && my_id < n_tot) {   // a coarser ghost: its row once published
+                    wait_ready(ready + (my_id - n_act), err, limit_ns);
+                    my_rl = row_len[my_id - n_act];
+                } else {
+                    my_rl = 1;
+                }
             }
+            __syncwarp();
             const int nq = np - q0 < 32 ? np - q0 : 32;
             for (int qq = 0; qq < nq; ++qq) {
                 const int qg = q0 + qq;
@@ -1139,18 +1194,18 @@ k_ghost_rows_level_wide(const int* __restrict__ list, long long gbeg, long long 
             row_len[gi] = len;
             if (over) atomicOr(overflow, 4);
         }
-        __syncwarp();
+        publish_ready(ready + gi, lane);
     }
     pdl_trigger();
 }
 
 // The ghost-row kernel of the DD order of g.
-using RowsKernel = void (*)(const int*, long long, long long, long long, long long, const int*, int*, int*, double*,
-                            int, int, Geom, int*, const int*, int);
+using RowsKernel = void (*)(const int*, const int*, int*, int*, double*, int, Geom, int*, const int*, int, int*, int*,
+                            unsigned long long, int);
 RowsKernel rows_kernel(const Geom& g) {
-    if (g.P == 3) return k_ghost_rows_level_wide<3>;
-    if (g.P == 4) return k_ghost_rows_level_wide<4>;
-    return k_ghost_rows_level;
+    if (g.P == 3) return k_ghost_rows_wide<3>;
+    if (g.P == 4) return k_ghost_rows_wide<4>;
+    return k_ghost_rows;
 }
 
 }  // namespace
@@ -1235,29 +1290,19 @@ void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaS
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s) {
     if (n > 0) { launch_pdl(k_list_to_mask, blocks_for(n), kThreads, 0, s, list, n, mask); note_launch(); }
 }
-void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
-                       int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
-                       int* overflow, cudaStream_t s, const int* dcounts, long long cap_a, long long cap_g) {
-    if (dcounts) {
-        // sizes on the device, grids over the capacities (capturable)
-        { launch_pdl(k_lat2idx, blocks_for(cap_a + cap_g), kThreads, 0, s, list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
-        for (int j = 1; j <= J; ++j) {
-            launch_pdl(rows_kernel(g), blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s,
-                list, 0, 0, 0, 0, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, dcounts, J + 1);
-            note_launch();
-        }
-        return;
-    }
-    long long tot = n_act;
-    for (int j = 1; j <= J; ++j) tot += gcnt[j];
-    if (tot > 0) { launch_pdl(k_lat2idx, blocks_for(tot), kThreads, 0, s, list, tot, lat2idx, nullptr, 0); note_launch(); }
-    for (int j = 1; j <= J; ++j)
-        if (gcnt[j] > 0) {
-            launch_pdl(rows_kernel(g), blocks_for(gcnt[j], kRowWarps), 32 * kRowWarps, 0, s,
-                list, goff[j], gcnt[j], n_act, tot, lat2idx, row_len, row_idx, row_w, rmax, j, g, overflow, nullptr,
-                0);
-            note_launch();
-        }
+void launch_ghost_rows(const int* list, int J, int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax,
+                       const Geom& g, int* overflow, int* ready, int* err, unsigned long long limit_ns,
+                       cudaStream_t s, const int* dcounts, long long cap_a, long long cap_g) {
+    // sizes on the device, grids over the capacities (capturable)
+    { launch_pdl(k_lat2idx, blocks_for(cap_a + cap_g), kThreads, 0, s, list, cap_a + cap_g, lat2idx, dcounts, J + 1); note_launch(); }
+    if (!ready || cap_g <= 0) return;   // no ghost capacity: no rows
+    cudaMemsetAsync(ready, 0, sizeof(int) * (size_t)(cap_g + 1), s);   // flags and the ghost counter
+    // test switch: the first ghost's warp waits for a flag nothing sets
+    const char* sv = std::getenv("WRC_TEST_GHOST_STALL");
+    const int stall = sv && std::atoi(sv) != 0;
+    launch_pdl(rows_kernel(g), blocks_for(cap_g, kRowWarps), 32 * kRowWarps, 0, s, list, (const int*)lat2idx, row_len,
+               row_idx, row_w, rmax, g, overflow, dcounts, J + 1, ready, err, limit_ns, stall);
+    note_launch();
 }
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy, cudaStream_t s) {
     if (n > 0) { launch_pdl(k_meta_unpack, blocks_for(n), kThreads, 0, s, meta, n, idx, jx, jy); note_launch(); }

@@ -42,15 +42,17 @@ void launch_meta_to_mask(const uint32_t* meta, long long n, uint8_t* mask, cudaS
 void launch_list_to_mask(const int* list, long long n, uint8_t* mask, cudaStream_t s);
 void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx, uint8_t* jy,
                         cudaStream_t s);
-// Interpolation rows of all ghosts (levels 1..J; ghosts of level j at
-// list[goff[j] ..]) over the active points, and the combined index map.
+// Interpolation rows of all ghosts (the list holds the active points, then
+// the ghosts of levels 1..J) over the active points, and the combined index
+// map.  dcounts: the compaction's per-key counts on the device (all sizes
+// are read there; the grids cover cap_a + cap_g items).  One launch for all
+// levels: ready (cap_g + 1 ints, cleared here) holds the ghosts' ready flags
+// and the counter that hands out ghosts in list order; a wait for a coarser
+// ghost's row longer than limit_ns sets bit 1 of *err.
 constexpr int kGhostRowMax = 64;
-// With dcounts (the compaction's per-key counts on the device), all sizes are
-// read on the device and the grids cover cap_a + cap_g items.
-void launch_ghost_rows(const int* list, long long n_act, const long long* goff, const long long* gcnt, int J,
-                       int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax, const Geom& g,
-                       int* overflow, cudaStream_t s, const int* dcounts = nullptr, long long cap_a = 0,
-                       long long cap_g = 0);
+void launch_ghost_rows(const int* list, int J, int* lat2idx, int* row_len, int* row_idx, double* row_w, int rmax,
+                       const Geom& g, int* overflow, int* ready, int* err, unsigned long long limit_ns,
+                       cudaStream_t s, const int* dcounts, long long cap_a, long long cap_g);
 
 // ---- fft.cu: streamfunction -------------------------------------------------
 struct PoissonPlan {

@@ -1,5 +1,6 @@
 """Failure detection on the GPU without a fault: bounded device-side waits
-that run out and report WRC_ERR_TIMEOUT, the time limit of wrc_sync, and
+(grid barriers of the Krylov kernel, the ghost-row ready flags) that run
+out and report WRC_ERR_TIMEOUT, the time limit of wrc_sync, and
 the fallback of the Krylov launch to its unclustered form when a launch
 path does not form thread-block clusters (made to happen by a test switch
 that has the first clustered launch behave exactly as it does when its
@@ -122,6 +123,36 @@ def test_scalar_pair_wait_limit_runs_out():
         idx, r = run.scalar()
         assert np.array_equal(idx, np.flatnonzero(st.active.ravel()))
         assert rel_l2(r, rv[st.active]) <= 1e-10
+
+
+def test_ghost_row_wait_limit_runs_out(monkeypatch):
+    """The interpolation rows of all ghosts are built in one launch in which
+    a ghost waits (bounded by the wait limit) for the rows of its coarser
+    ghost predictors.  With the test switch WRC_TEST_GHOST_STALL=1 the first
+    ghost's warp waits for a flag nothing sets: the wait runs out after the
+    limit, the next step reports WRC_ERR_TIMEOUT, and after re-initialising
+    without the switch the run steps like the oracle."""
+    import torch
+    wl = W.fujiwhara_small()
+    p = W.RunParams(**{**wl.params.as_dict(), "sgs": W.SGS_DYNAMIC, "cs": 0.17})
+    v = wl.vortices
+    st2 = _oracle_steps(p, v, 2)
+    stream = torch.cuda.Stream()
+    with B.Run(p, stream=stream.cuda_stream) as run:
+        run.set_wait_limit(0.01)
+        monkeypatch.setenv("WRC_TEST_GHOST_STALL", "1")
+        run.init_vortices(v)                        # the rebuild's ghost rows: one wait runs out
+        monkeypatch.delenv("WRC_TEST_GHOST_STALL")
+        assert run.counts()[1] > 0
+        with pytest.raises(B.WrcError) as e:
+            run.step(1)
+        assert e.value.status == -5, e.value
+        run.sync()
+        run.set_wait_limit(2.0)
+        run.init_vortices(v)
+        run.step(2)
+        run.sync()
+        _check_against(run, st2)
 
 
 def test_wait_limit_rejects_out_of_range():
