@@ -33,6 +33,8 @@ CASES = [
     dict(n0=8, J=4, eps=1e-3, p=3),     # 128^2, 2p = 6
     dict(n0=4, J=5, eps=1e-3, p=4),     # 128^2, 2p = 8, coarse regions wider than the lattice
     dict(n0=4, J=1, eps=1e-2, p=2),     # 8^2: a single tile smaller than 64
+    dict(n0=4, J=8, eps=1e-3, p=2),     # 1024^2, nine levels: coarse regions far wider than a tile
+    dict(n0=4, J=8, eps=1e-3, p=4),     # the same with 2p = 8 (the largest shared-memory layout here)
 ]
 
 
