@@ -121,6 +121,8 @@ struct wrc_run {
     // ghost interpolation rows and the ghost values of the basis vectors
     DevBuf row_len, row_idx, row_w, Gb;
     DevBuf row_ready;   // cap_g + 1 ints: ready flags of the rows, the ghost counter
+    DevBuf rows;        // NJ + 1 ints: flags of the row pairs of psi a step reads, their count and list
+    bool rows_psi = false;   // psi of the last freeze holds only those rows
     long long cap_g = 0;
 
     // Krylov small arrays and cooperative-kernel scratch
@@ -556,10 +558,15 @@ wrc_status threshold_current(wrc_run* R, double eps, bool whole_lattice) {
 }
 
 // L <- R(omega): the grid values, then coarse-to-fine prediction elsewhere.
+// With rows, the flags R->rows of the row pairs within 2 dd_reach(P) rows of
+// a grid point are set as well: the rows of psi a step reads (the velocity
+// stencils at the grid points, and the SGS halo, dd_reach(P) around them,
+// with its own stencils).
 template <typename T>
-wrc_status reconstruct(wrc_run* R) {
+wrc_status reconstruct(wrc_run* R, bool rows = false) {
+    if (rows) CK(cudaMemsetAsync(R->rows.p, 0, R->rows.bytes, R->st));
     launch_scatter<T>(R->meta[R->cur].as<uint32_t>(), R->omega[R->cur].as<T>(), R->cap, (T*)R->L, R->st,
-                      R->counts_dev);
+                      R->counts_dev, rows ? R->rows.as<int>() : nullptr, 2 * dd_reach(R->g.P), &R->g);
     CKL("reconstruct/scatter");
     launch_reconstruct<T>((T*)R->L, R->act, R->g, R->st);
     CKL("reconstruct");
@@ -577,11 +584,14 @@ wrc_status reconstruct_scalar(wrc_run* R) {
 }
 
 // Linearisation at the current state: R(omega), psi, U, V and the SGS forcing
-// (and R(r_v) when the passive scalar is on).
+// (and R(r_v) when the passive scalar is on).  In a step (FP64 bulk) psi is
+// computed only on the rows the step reads (rows_psi); the field queries
+// want all of it.
 template <typename T>
-wrc_status freeze(wrc_run* R) {
+wrc_status freeze(wrc_run* R, bool in_step = false) {
     TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
-    TRY(reconstruct<T>(R));
+    R->rows_psi = in_step && !R->fp32;
+    TRY(reconstruct<T>(R, R->rows_psi));
     CKL("freeze/reconstruct");
     if (R->scalar) TRY(reconstruct_scalar<T>(R));
     TRY(stage_mark(R, WRC_STAGE_POISSON));
@@ -614,7 +624,8 @@ wrc_status freeze(wrc_run* R) {
         R->frozen = true;
         return WRC_OK;
     } else {
-        launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s);
+        launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, nullptr, nullptr, nullptr,
+                          nullptr, nullptr, nullptr, R->rows_psi ? R->rows.as<int>() : nullptr);
         TRY(stage_mark(R, WRC_STAGE_VELOCITY));
         launch_velocity_active<T>((const T*)R->psi, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), R->g, s,
                                   R->counts_dev);
@@ -898,7 +909,9 @@ wrc_status krylov_rosenbrock(wrc_run* R) {
             launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s, Ulat, (T*)R->C1, scr);
             launch_velocity_gather<T>(Ulat, (const T*)R->C1, meta, n, Uq, Vq, s);
         } else {
-            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s);
+            // psi[q_j] at the rows the velocity stencils read (flagged by the freeze)
+            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, R->rows_psi ? R->rows.as<int>() : nullptr);
             launch_velocity_active<T>((const T*)R->psi, meta, n, Uq, Vq, g, s);
         }
         CKL("rosenbrock jacobian");
@@ -999,7 +1012,7 @@ wrc_status step_phases(wrc_run* R) {
         TRY(stage_mark(R, WRC_STAGE_KRYLOV));
         TRY(exner_krylov(R));
     } else {
-        TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); }));
+        TRY(run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R, true); }));
         R->frozen = true;
         TRY(stage_mark(R, WRC_STAGE_KRYLOV));
         TRY(krylov<T>(R));
@@ -1241,7 +1254,7 @@ void free_run(wrc_run* R) {
     cudaStreamSynchronize(s);
     for (auto* b : {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga, &R->det, &R->w,
                     &R->basis, &R->tmp, &R->row_len, &R->row_ready, &R->row_idx, &R->row_w, &R->Gb, &R->lat64,
-                    &R->trace, &R->rv[0],
+                    &R->trace, &R->rows, &R->rv[0],
                     &R->rv[1], &R->Lr, &R->kr, &R->jac, &R->rbpart, &R->rbsmall, &R->pe[0], &R->pe[1], &R->Lp, &R->Lqx,
                     &R->xd, &R->xbasis, &R->xw, &R->sbasis, &R->sw, &R->sGb, &R->sLq, &R->spart, &R->sbar, &R->sdev})
         b->release(s);
@@ -1345,6 +1358,7 @@ wrc_status wrc_create(const wrc_config* cfg, void* cuda_stream, wrc_run** out) {
     if (e == cudaSuccess) e = alloc((void**)&R->lvl_dev, sizeof(unsigned long long) * 16);
     if (e == cudaSuccess) e = alloc((void**)&R->vort_dev, sizeof(double) * 4 * WRC_MAX_VORTICES);
     if (e == cudaSuccess) e = alloc((void**)&R->diag_dev, sizeof(double) * 8);
+    if (e == cudaSuccess) e = R->rows.grow(sizeof(int) * ((size_t)NJ + 1), 0, R->st);
     // Krylov small arrays: H, then o1/o2/o3/beta/y in one block, partials, ints
     R->cluster_max = krylov_cluster_max();
     if (krylov_step_init(R->device, R->fp32, R->g.P, &R->max_blocks) != 0) {
@@ -2013,7 +2027,7 @@ wrc_status batch_step_t(BatchCtx& C, const std::vector<wrc_run*>& runs, std::vec
         wrc_run* R = runs[i];
         na0[i] = R->n_active;
         if (rs[i] != WRC_OK) continue;
-        const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R); });
+        const wrc_status st = run_phase(R, kPhaseFreeze, [&] { return freeze<T>(R, true); });
         if (st != WRC_OK) mark(i, st);
         else R->frozen = true;
     }
@@ -2195,7 +2209,7 @@ double wrc::run_device_bytes(const wrc_run* R) {
          8.0 * (double)std::max(krylov_partials_doubles(R->max_blocks), (size_t)kMaxBlocks * 4);
     const DevBuf* bufs[] = {&R->meta[0], &R->meta[1], &R->omega[0], &R->omega[1], &R->Ua, &R->Va, &R->ga,
                             &R->det, &R->w, &R->basis, &R->tmp, &R->row_len, &R->row_ready, &R->row_idx, &R->row_w,
-                            &R->Gb};
+                            &R->Gb, &R->rows};
     for (const DevBuf* d : bufs) b += (double)d->bytes;
     return b;
 }

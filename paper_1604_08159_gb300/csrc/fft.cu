@@ -422,17 +422,30 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
 
 // Step 5 for psi: rows 2q, 2q+1 from their half spectra (Hermitian extension
 // X[n-k] = conj X[k]; X[0], X[n/2] from the packed bin): Z = X_a + i X_b,
-// inverse FFT, real part to row 2q, imaginary part to row 2q+1.
+// inverse FFT, real part to row 2q, imaginary part to row 2q+1.  With rows
+// (the list of the pairs wanted: count at rows[h], pairs from rows[h + 1]),
+// block b transforms the listed pairs b F .. b F + F - 1 and the blocks past
+// the list return at once; a pair is transformed independently of the
+// others, so the rows computed are the same.
 template <typename T, int E, int R0>
 __global__ void __launch_bounds__(256) k_px_inv_real(const cx_t<T>* __restrict__ S, T* __restrict__ out, int n,
-                                                     int logn, const cx_t<T>* __restrict__ tw) {
+                                                     int logn, const cx_t<T>* __restrict__ tw,
+                                                     const int* __restrict__ rows) {
     pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
     const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
     const int h = n / 2;
-    const int q = blockIdx.x * F + f;
+    int q = blockIdx.x * F + f;
+    if (rows) {
+        const int cnt = rows[h];
+        if ((int)blockIdx.x * F >= cnt) {
+            pdl_trigger();
+            return;
+        }
+        q = q < cnt ? rows[h + 1 + q] : h;   // h: no pair
+    }
     const bool on = q < h;
     C* sm = (C*)smraw + (size_t)f * smlen_of(n);
     const C* sa = S + (size_t)(2 * (on ? q : 0)) * h;
@@ -574,7 +587,7 @@ struct Shape {
     }
 
     static void run(const PoissonPlan& p, const T* Rf, T* psi, cx_t<T>* C1, cx_t<T>* C2, cudaStream_t s, T* U, T* V,
-                    cx_t<T>* C3, T* S11, T* S12, cx_t<T>* C4) {
+                    cx_t<T>* C3, T* S11, T* S12, cx_t<T>* C4, const int* rows) {
         using C = cx_t<T>;
         const int n = p.n, logn = p.logn, h = n / 2;
         const int nt = n / E, F = nt >= 128 ? 1 : 128 / nt;
@@ -601,7 +614,8 @@ struct Shape {
                                                                         (const T*)p.sigma, (const T*)p.dsym,
                                                                         scale); note_launch(); }
                 { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
-                { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw); note_launch(); }
+                { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw,
+                             (const int*)nullptr); note_launch(); }
                 // U + i V: QT (C2) -> a buffer that V (the caller's, possibly in C1) does not overlap
                 C* Q = st ? C4 : C3;
                 { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, QT, Q, n, n); note_launch(); }
@@ -617,7 +631,7 @@ struct Shape {
                                                                  (const T*)p.sigma, (const T*)p.dsym,
                                                                  scale); note_launch(); }
         { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
-        { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw); note_launch(); }
+        { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw, rows); note_launch(); }
         (void)C2;
     }
 };
@@ -667,24 +681,24 @@ void poisson_plan_free(PoissonPlan& p) {
 
 template <typename T>
 void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1v, void* C2v, const Geom& g, cudaStream_t s,
-                    T* U, T* V, void* C3v, T* S11, T* S12, void* C4v) {
+                    T* U, T* V, void* C3v, T* S11, T* S12, void* C4v, const int* rows) {
     using C = cx_t<T>;
     C* C1 = (C*)C1v;
     C* C2 = (C*)C2v;
     C* C3 = (C*)C3v;
     C* C4 = (C*)C4v;
     const int logn = p.logn;
-    if (logn < 4) Shape<T, 8, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
-    else if (logn % 4 == 0) Shape<T, 16, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
-    else if (logn % 4 == 1) Shape<T, 16, 2>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
-    else if (logn % 4 == 2) Shape<T, 16, 4>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
-    else Shape<T, 16, 8>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4);
+    if (logn < 4) Shape<T, 8, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4, rows);
+    else if (logn % 4 == 0) Shape<T, 16, 1>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4, rows);
+    else if (logn % 4 == 1) Shape<T, 16, 2>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4, rows);
+    else if (logn % 4 == 2) Shape<T, 16, 4>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4, rows);
+    else Shape<T, 16, 8>::run(p, R, psi, C1, C2, s, U, V, C3, S11, S12, C4, rows);
     (void)g;
 }
 
 template void launch_poisson<double>(const PoissonPlan&, const double*, double*, void*, void*, const Geom&,
-                                     cudaStream_t, double*, double*, void*, double*, double*, void*);
+                                     cudaStream_t, double*, double*, void*, double*, double*, void*, const int*);
 template void launch_poisson<float>(const PoissonPlan&, const float*, float*, void*, void*, const Geom&, cudaStream_t,
-                                    float*, float*, void*, float*, float*, void*);
+                                    float*, float*, void*, float*, float*, void*, const int*);
 
 }  // namespace wrc

@@ -34,14 +34,35 @@ __global__ void k_init_vortices(T* __restrict__ L, const double* __restrict__ pr
     pdl_trigger();
 }
 
+// With rows (see launch_scatter): the pair q of rows 2q, 2q+1 within margin
+// rows of a grid point is flagged (rows[q]) and, by the thread that flags it
+// first, appended to the list rows[h + 1 ..] (count at rows[h]; any order).
+__device__ __forceinline__ void flag_pair(int* rows, int h, int q) {
+    if (*(volatile int*)(rows + q)) return;
+    if (atomicExch(rows + q, 1) == 0) rows[h + 1 + atomicAdd(rows + h, 1)] = q;
+}
+
 template <typename T>
 __global__ void k_scatter(const uint32_t* __restrict__ meta, const T* __restrict__ vals, long long n,
-                          T* __restrict__ L, const int* __restrict__ dn) {
+                          T* __restrict__ L, const int* __restrict__ dn, int* __restrict__ rows, int margin,
+                          int lg, int mask) {
     pdl_wait();
     n = eff_n(dn, n);
+    const int h = (mask + 1) >> 1;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
-         a += (long long)gridDim.x * blockDim.x)
-        L[meta_pos(meta[a])] = vals[a];
+         a += (long long)gridDim.x * blockDim.x) {
+        const uint32_t p = meta_pos(meta[a]);
+        L[p] = vals[a];
+        if (rows) {
+            // one lane per distinct row among the warp's points flags its pairs
+            const int k = (int)(p >> lg);
+            const unsigned same = __match_any_sync(__activemask(), k);
+            if ((int)(threadIdx.x & 31) == __ffs(same) - 1) {
+                for (int d = -margin; d <= margin; d += 2) flag_pair(rows, h, ((k + d) & mask) >> 1);
+                flag_pair(rows, h, ((k + margin) & mask) >> 1);
+            }
+        }
+    }
     pdl_trigger();
 }
 
@@ -1215,8 +1236,11 @@ void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cuda
     { launch_pdl(k_init_vortices<T>, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, L, params, n, g); note_launch(); }
 }
 template <typename T>
-void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn) {
-    if (n > 0) { launch_pdl(k_scatter<T>, blocks_for(n), kThreads, 0, s, meta, vals, n, L, dn); note_launch(); }
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn,
+                    int* rows, int margin, const Geom* g) {
+    const int lg = g ? g->L : 0, mask = g ? g->mask : 0;
+    if (!g) rows = nullptr;
+    if (n > 0) { launch_pdl(k_scatter<T>, blocks_for(n), kThreads, 0, s, meta, vals, n, L, dn, rows, margin, lg, mask); note_launch(); }
 }
 template <typename T>
 void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStream_t s) {
@@ -1310,7 +1334,8 @@ void launch_meta_unpack(const uint32_t* meta, long long n, int* idx, uint8_t* jx
 
 #define WRC_INST(T)                                                                                       \
     template void launch_init_vortices<T>(T*, const double*, int, const Geom&, cudaStream_t);             \
-    template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t, const int*);  \
+    template void launch_scatter<T>(const uint32_t*, const T*, long long, T*, cudaStream_t, const int*,     \
+                                    int*, int, const Geom*);                                              \
     template void launch_reconstruct<T>(T*, const uint8_t*, const Geom&, cudaStream_t);                   \
     template void launch_recon_new<T>(T*, const uint8_t*, const uint8_t*, const Geom&, cudaStream_t);     \
     template void launch_details_adj<T>(const uint32_t*, long long, const T*, double, T*, uint8_t*,       \

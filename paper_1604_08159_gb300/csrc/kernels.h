@@ -10,8 +10,12 @@ template <typename T>
 void launch_init_vortices(T* L, const double* params, int n, const Geom& g, cudaStream_t s);
 // Launchers taking `dn` read the item count from device memory when it is
 // given (n is then the capacity the grid covers; capturable in a CUDA graph).
+// With rows (NJ + 1 ints, zero before: h = NJ/2 flags, one per pair of
+// rows 2q, 2q+1, then a count and a list), also flags the pairs holding a
+// row within `margin` rows of a grid point and lists them (in any order).
 template <typename T>
-void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn = nullptr);
+void launch_scatter(const uint32_t* meta, const T* vals, long long n, T* L, cudaStream_t s, const int* dn = nullptr,
+                    int* rows = nullptr, int margin = 0, const Geom* g = nullptr);
 // L <- R(u): the values at the grid points of act stay, every other lattice
 // point gets its coarse-to-fine DD prediction (Eq. 6, detail zero).  One
 // tiled launch (or, where its shared-memory arrays do not fit, two launches
@@ -70,10 +74,14 @@ void poisson_plan_free(PoissonPlan& p);
 // V = -D_x psi on the lattice, evaluated in the Fourier domain (no cancellation);
 // with S11, S12 and a fourth work array C4, also the strain S11 = D_x D_y psi and
 // S12 = (D_yy - D_xx) psi / 2.  S11 and S12 may not alias C1, C2 or C3.
+// With rows (the flags and list launch_scatter makes; psi alone, without U
+// and V), psi is written only on the rows of the listed pairs: the inverse
+// row pass takes them from the list, a few per block, so that the blocks
+// with work are the first ones and spread over the SMs.
 template <typename T>
 void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1, void* C2, const Geom& g, cudaStream_t s,
                     T* U = nullptr, T* V = nullptr, void* C3 = nullptr, T* S11 = nullptr, T* S12 = nullptr,
-                    void* C4 = nullptr);
+                    void* C4 = nullptr, const int* rows = nullptr);
 
 // ---- flow.cu: velocity, Smagorinsky forcing, operator, diagnostics ----------
 template <typename T>
