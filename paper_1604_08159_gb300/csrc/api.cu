@@ -584,13 +584,14 @@ wrc_status reconstruct_scalar(wrc_run* R) {
 }
 
 // Linearisation at the current state: R(omega), psi, U, V and the SGS forcing
-// (and R(r_v) when the passive scalar is on).  In a step (FP64 bulk) psi is
-// computed only on the rows the step reads (rows_psi); the field queries
-// want all of it.
+// (and R(r_v) when the passive scalar is on).  In a step the inverse row
+// passes of the Poisson solve run only on the rows the step reads
+// (rows_psi): psi there (FP64), or U, V and the strain (FP32 bulk); the
+// field queries want all of it.
 template <typename T>
 wrc_status freeze(wrc_run* R, bool in_step = false) {
     TRY(stage_mark(R, WRC_STAGE_RECONSTRUCT));
-    R->rows_psi = in_step && !R->fp32;
+    R->rows_psi = in_step;
     TRY(reconstruct<T>(R, R->rows_psi));
     CKL("freeze/reconstruct");
     if (R->scalar) TRY(reconstruct_scalar<T>(R));
@@ -611,7 +612,8 @@ wrc_status freeze(wrc_run* R, bool in_step = false) {
         T* S11 = t2;
         T* S12 = t3;
         launch_poisson<T>(R->plan, (const T*)R->L, (T*)R->psi, R->C1, R->C2, R->g, s, (T*)R->Lq, t0, scr,
-                          dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr);
+                          dyn ? S11 : nullptr, dyn ? S12 : nullptr, dyn ? (void*)(scr + R->N) : nullptr,
+                          R->rows_psi ? R->rows.as<int>() : nullptr);
         CKL("freeze/poisson");
         TRY(stage_mark(R, WRC_STAGE_VELOCITY));
         launch_velocity_gather<T>((const T*)R->Lq, t0, meta, R->cap, R->Ua.as<T>(), R->Va.as<T>(), s, R->counts_dev);
@@ -906,7 +908,8 @@ wrc_status krylov_rosenbrock(wrc_run* R) {
             // spectral U, V (as in the freeze): U into the second half of the
             // scratch (the first holds the third FFT work array), V into C1
             T* Ulat = (T*)(scr + R->N);
-            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s, Ulat, (T*)R->C1, scr);
+            launch_poisson<T>(R->plan, Lq, (T*)R->psi, R->C1, R->C2, g, s, Ulat, (T*)R->C1, scr, nullptr, nullptr,
+                              nullptr, R->rows_psi ? R->rows.as<int>() : nullptr);
             launch_velocity_gather<T>(Ulat, (const T*)R->C1, meta, n, Uq, Vq, s);
         } else {
             // psi[q_j] at the rows the velocity stencils read (flagged by the freeze)

@@ -483,17 +483,27 @@ __global__ void __launch_bounds__(256) k_px_inv_real(const cx_t<T>* __restrict__
 }
 
 // Step 5 for a full complex spectrum (U + i V, S11 + i S12): row y, inverse
-// FFT, real part to A, imaginary part to B.
+// FFT, real part to A, imaginary part to B.  With rows (the list of row
+// pairs wanted, as for k_px_inv_real), block b transforms the rows of the
+// listed pairs b F / 2 ..., and the blocks past them return at once.
 template <typename T, int E, int R0>
 __global__ void __launch_bounds__(256) k_px_inv_pair(const cx_t<T>* __restrict__ Q, T* __restrict__ A,
                                                      T* __restrict__ B, int n, int logn,
-                                                     const cx_t<T>* __restrict__ tw) {
+                                                     const cx_t<T>* __restrict__ tw, const int* __restrict__ rows) {
     pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nt = n / E, F = blockDim.x / nt;
     const int f = threadIdx.x / nt, i = threadIdx.x - f * nt;
-    const int y = blockIdx.x * F + f;
+    int y = blockIdx.x * F + f;
+    if (rows) {
+        const int h = n / 2, cnt = 2 * rows[h];   // rows of the listed pairs
+        if ((int)blockIdx.x * F >= cnt) {
+            pdl_trigger();
+            return;
+        }
+        y = y < cnt ? 2 * rows[h + 1 + y / 2] + (y & 1) : n;   // n: no row
+    }
     const bool on = y < n;
     C* sm = (C*)smraw + (size_t)f * smlen_of(n);
     const C* row = Q + (size_t)(on ? y : 0) * n;
@@ -614,15 +624,16 @@ struct Shape {
                                                                         (const T*)p.sigma, (const T*)p.dsym,
                                                                         scale); note_launch(); }
                 { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
-                { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw,
-                             (const int*)nullptr); note_launch(); }
+                // psi: a step (rows given) reads U and V, not psi
+                if (!rows) { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw,
+                                        (const int*)nullptr); note_launch(); }
                 // U + i V: QT (C2) -> a buffer that V (the caller's, possibly in C1) does not overlap
                 C* Q = st ? C4 : C3;
                 { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, QT, Q, n, n); note_launch(); }
-                { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, Q, U, V, n, logn, tw); note_launch(); }
+                { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, Q, U, V, n, logn, tw, rows); note_launch(); }
                 if (st) {
                     { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, WT, C4, n, n); note_launch(); }
-                    { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, C4, S11, S12, n, logn, tw); note_launch(); }
+                    { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, C4, S11, S12, n, logn, tw, rows); note_launch(); }
                 }
                 return;
             }

@@ -74,10 +74,11 @@ void poisson_plan_free(PoissonPlan& p);
 // V = -D_x psi on the lattice, evaluated in the Fourier domain (no cancellation);
 // with S11, S12 and a fourth work array C4, also the strain S11 = D_x D_y psi and
 // S12 = (D_yy - D_xx) psi / 2.  S11 and S12 may not alias C1, C2 or C3.
-// With rows (the flags and list launch_scatter makes; psi alone, without U
-// and V), psi is written only on the rows of the listed pairs: the inverse
-// row pass takes them from the list, a few per block, so that the blocks
-// with work are the first ones and spread over the SMs.
+// With rows (the flags and list launch_scatter makes), the inverse row
+// passes take the listed row pairs only, a few per block, so that the blocks
+// with work are the first ones and spread over the SMs: psi alone is written
+// only on those rows; with U and V (a step's FP32 form), U, V and the strain
+// are written only there and psi, which such a step does not read, not at all.
 template <typename T>
 void launch_poisson(const PoissonPlan& p, const T* R, T* psi, void* C1, void* C2, const Geom& g, cudaStream_t s,
                     T* U = nullptr, T* V = nullptr, void* C3 = nullptr, T* S11 = nullptr, T* S12 = nullptr,
