@@ -179,7 +179,11 @@ constexpr int kReconSmemMax = 160 * 1024;
 bool recon_tiles_layout(const Geom& g, size_t es, ReconTiles& lay) {
     if (g.J >= kReconLevels) return false;
     const int E = 2 * g.P - 1;
-    int cap = 64;   // tile edge (1024^2, J = 5 on GB300: 64 before 32, 16)
+    // tile edge: 64 up to 1024^2 (on GB300 at 1024^2, J = 5: 64 before 32, 16
+    // and the level-by-level kernels); beyond, the level-by-level kernels,
+    // whose passes then have parallelism enough (4096^2, J = 7: 0.22 ms
+    // against 0.33 ms tiled); WRC_RECON_TILE sets the edge (0: level by level)
+    int cap = g.NJ <= 1024 ? 64 : 0;
     if (const char* v = std::getenv("WRC_RECON_TILE")) cap = std::atoi(v);
     if (cap < 8) return false;   // 0: the level-by-level kernels
     for (int ts = g.NJ < cap ? g.NJ : cap; ts >= 8 && ts <= g.NJ; ts /= 2) {
