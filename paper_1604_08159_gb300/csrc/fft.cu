@@ -623,10 +623,12 @@ struct Shape {
                 { launch_pdl(k_py_solve<T, E, R0, true>, b_half, thr, 2 * smem, s, ST, QT, WT, n, logn, tw,
                                                                         (const T*)p.sigma, (const T*)p.dsym,
                                                                         scale); note_launch(); }
-                { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
                 // psi: a step (rows given) reads U and V, not psi
-                if (!rows) { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw,
-                                        (const int*)nullptr); note_launch(); }
+                if (!rows) {
+                    { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
+                    { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw,
+                                 (const int*)nullptr); note_launch(); }
+                }
                 // U + i V: QT (C2) -> a buffer that V (the caller's, possibly in C1) does not overlap
                 C* Q = st ? C4 : C3;
                 { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, QT, Q, n, n); note_launch(); }
