@@ -314,7 +314,7 @@ template <typename T, int E, int R0, bool QW>
 __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t<T>* __restrict__ QT,
                                                   cx_t<T>* __restrict__ WT, int n, int logn,
                                                   const cx_t<T>* __restrict__ tw, const T* __restrict__ sigma,
-                                                  const T* __restrict__ dsym, T scale) {
+                                                  const T* __restrict__ dsym, T scale, int want_psi) {
     pdl_wait();
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -355,18 +355,21 @@ __global__ void __launch_bounds__(256) k_py_solve(cx_t<T>* __restrict__ ST, cx_t
             b = cscale(fm, fc);
         }
     };
-    // psi: X1 (kx > 0) or X1 + i X2 (packed kx = 0, n/2)
+    // psi: X1 (kx > 0) or X1 + i X2 (packed kx = 0, n/2); a step of the FP32
+    // form (want_psi 0, uniform over the grid) reads U and V, not psi
+    if (!QW || want_psi) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        C a, b;
-        x12(i + e * nt, a, b);
-        v[e] = kxs == 0 ? mk<C>(a.x - b.y, a.y + b.x) : a;
+        for (int e = 0; e < E; ++e) {
+            C a, b;
+            x12(i + e * nt, a, b);
+            v[e] = kxs == 0 ? mk<C>(a.x - b.y, a.y + b.x) : a;
+        }
+        if constexpr (!QW) __syncthreads();   // fb is the exchange buffer
+        fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
+        if (on)
+#pragma unroll
+            for (int e = 0; e < E; ++e) row[i + e * nt] = v[e];
     }
-    if constexpr (!QW) __syncthreads();   // fb is the exchange buffer
-    fft_reg<E, R0, true>(v, sm, i, n, logn, tw);
-    if (on)
-#pragma unroll
-        for (int e = 0; e < E; ++e) row[i + e * nt] = v[e];
     if constexpr (QW) {
         const int c2 = kxs == 0 ? h : n - kxs;
         const T dx = dsym[kxs], sc2 = sigma[c2];
@@ -622,7 +625,7 @@ struct Shape {
                 C* WT = st ? C3 : nullptr;     // n x n
                 { launch_pdl(k_py_solve<T, E, R0, true>, b_half, thr, 2 * smem, s, ST, QT, WT, n, logn, tw,
                                                                         (const T*)p.sigma, (const T*)p.dsym,
-                                                                        scale); note_launch(); }
+                                                                        scale, rows ? 0 : 1); note_launch(); }
                 // psi: a step (rows given) reads U and V, not psi
                 if (!rows) {
                     { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
@@ -642,7 +645,7 @@ struct Shape {
         }
         { launch_pdl(k_py_solve<T, E, R0, false>, b_half, thr, smem, s, ST, nullptr, nullptr, n, logn, tw,
                                                                  (const T*)p.sigma, (const T*)p.dsym,
-                                                                 scale); note_launch(); }
+                                                                 scale, 1); note_launch(); }
         { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
         { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw, rows); note_launch(); }
         (void)C2;
