@@ -621,7 +621,7 @@ wrc_status freeze(wrc_run* R, bool in_step = false) {
         TRY(stage_mark(R, WRC_STAGE_SGS));
         if (dyn)
             launch_sgs_from_strain<T>(S11, S12, meta, R->cap, R->cfg.cs, R->ga.as<T>(), t1, t0, (T*)scr, R->g, s,
-                                      R->counts_dev);
+                                      R->counts_dev, R->rows_psi ? R->rows.as<int>() : nullptr);
         CKL("freeze");
         R->frozen = true;
         return WRC_OK;

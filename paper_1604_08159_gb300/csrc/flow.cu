@@ -97,12 +97,28 @@ __global__ void k_velocity_active(const T* __restrict__ psi, const uint32_t* __r
 
 // nu_t = (C_s h)^2 * 2 sqrt(S11^2 + S12^2) (Eq. 5); a = 2 nu_t S12, c = nu_t S11
 // (nut and c may be null).
+// Lattice passes over the rows of listed row pairs only (rows: the flags,
+// count and list of launch_scatter; NJ = 2^lg): the number of points, and
+// the lattice index of the e-th (nullptr: every point, in order).
+__device__ __forceinline__ long long listed_points(const int* rows, long long N, int lg) {
+    return rows ? (2LL * rows[1 << (lg - 1)]) << lg : N;
+}
+__device__ __forceinline__ long long listed_point(const int* rows, long long e, int lg) {
+    if (!rows) return e;
+    const long long slot = e >> lg;   // row slot: pair slot / 2, row of the pair slot & 1
+    const int row = 2 * rows[(1 << (lg - 1)) + 1 + (int)(slot >> 1)] + (int)(slot & 1);
+    return ((long long)row << lg) + (e & ((1LL << lg) - 1));
+}
+
 template <typename T>
 __global__ void k_strain_nut(const T* __restrict__ S11, const T* __restrict__ S12, T* __restrict__ nut,
-                             T* __restrict__ a, T* __restrict__ c, long long N, T csh2) {
+                             T* __restrict__ a, T* __restrict__ c, long long N, T csh2, const int* __restrict__ rows,
+                             int lg) {
     pdl_wait();
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
+    const long long tot = listed_points(rows, N, lg);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long p = listed_point(rows, e, lg);
         const T s11 = S11[p], s12 = S12[p];
         const T nt = csh2 * (T(2) * sqrt(s11 * s11 + s12 * s12));
         if (nut) nut[p] = nt;
@@ -129,11 +145,12 @@ __global__ void k_velocity_gather(const T* __restrict__ Ulat, const T* __restric
 
 // Pass 3: t0 = d(t3)/dy.
 template <typename T, int P>
-__global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c1) {
+__global__ void k_sgs3(const T* __restrict__ t3, T* __restrict__ t0, Geom g, T c1, const int* __restrict__ rows) {
     pdl_wait();
-    const long long N = (long long)g.NJ * g.NJ;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
+    const long long tot = listed_points(rows, (long long)g.NJ * g.NJ, g.L);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long p = listed_point(rows, e, g.L);
         const int i = (int)(p & g.mask), k = (int)(p >> g.L);
         t0[p] = dy1<T, P>(t3, i, k, g, c1);
     }
@@ -411,14 +428,14 @@ void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs,
 
 template <typename T>
 void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
-                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn) {
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn, const int* rows) {
     const long long N = (long long)g.NJ * g.NJ;
     const T csh2 = T((cs * g.h) * (cs * g.h));
-    { launch_pdl(k_strain_nut<T>, blocks_for(N), kThreads, 0, s, S11, S12, nullptr, ta, tc, N, csh2); note_launch(); }
+    { launch_pdl(k_strain_nut<T>, blocks_for(N), kThreads, 0, s, S11, S12, nullptr, ta, tc, N, csh2, rows, g.L); note_launch(); }
     by_order(g, [&](auto PC) {
         constexpr int P = decltype(PC)::value;
         const T c1 = c1_of<T, P>(g.h), c2 = c2_of<T, P>(g.h);
-        { launch_pdl(k_sgs3<T, P>, blocks_for(N), kThreads, 0, s, tc, tdyc, g, c1); note_launch(); }
+        { launch_pdl(k_sgs3<T, P>, blocks_for(N), kThreads, 0, s, tc, tdyc, g, c1, rows); note_launch(); }
         if (n > 0) { launch_pdl(k_sgs4<T, P>, blocks_for(n), kThreads, 0, s, ta, tdyc, meta, n, ga, g, c1, c2, dn); note_launch(); }
     });
 }
@@ -427,7 +444,7 @@ template <typename T>
 void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s) {
     const long long N = (long long)g.NJ * g.NJ;
     { launch_pdl(k_strain_nut<T>, blocks_for(N), kThreads, 0, s, S11, S12, nut, nullptr, nullptr, N,
-                                                          T((cs * g.h) * (cs * g.h))); note_launch(); }
+                                                          T((cs * g.h) * (cs * g.h)), (const int*)nullptr, g.L); note_launch(); }
 }
 
 template <typename T>
@@ -498,7 +515,7 @@ template void launch_convert<float, double>(const float*, double*, long long, cu
     template void launch_velocity_gather<T>(const T*, const T*, const uint32_t*, long long, T*, T*,         \
                                             cudaStream_t, const int*);                                      \
     template void launch_sgs_from_strain<T>(const T*, const T*, const uint32_t*, long long, double, T*, T*, \
-                                            T*, T*, const Geom&, cudaStream_t, const int*);                 \
+                                            T*, T*, const Geom&, cudaStream_t, const int*, const int*);     \
     template void launch_nut_from_strain<T>(const T*, const T*, T*, double, const Geom&, cudaStream_t);     \
     template void launch_lattice_uv_nut<T>(const T*, T*, T*, T*, double, T*, const Geom&, cudaStream_t,     \
                                            bool);                                                           \

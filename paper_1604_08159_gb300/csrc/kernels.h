@@ -97,9 +97,12 @@ void launch_sgs_halo(const T* psi, const uint32_t* meta, long long n, double cs,
                      uint8_t* halo, int* hlist, const Geom& g, cudaStream_t s, const int* dn = nullptr);
 // Smagorinsky forcing from the lattice strain (S11, S12): nu_t, then
 // a = 2 nu_t S12 and c = nu_t S11 into ta, tc, D_y c into tdyc, g at the active points.
+// With rows (the row-pair list of launch_scatter, margin 2 dd_reach(P)), the
+// lattice passes run on the listed rows only, which hold what g reads.
 template <typename T>
 void launch_sgs_from_strain(const T* S11, const T* S12, const uint32_t* meta, long long n, double cs, T* ga, T* ta,
-                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn = nullptr);
+                            T* tc, T* tdyc, const Geom& g, cudaStream_t s, const int* dn = nullptr,
+                            const int* rows = nullptr);
 template <typename T>
 void launch_nut_from_strain(const T* S11, const T* S12, T* nut, double cs, const Geom& g, cudaStream_t s);
 template <typename T>
