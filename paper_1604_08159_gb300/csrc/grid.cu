@@ -440,6 +440,29 @@ __global__ void k_recon_new(T* __restrict__ L, const uint8_t* __restrict__ act, 
     pdl_trigger();
 }
 
+// k_recon_new for the finest level J, 16 consecutive lattice points per
+// thread: the new-grid and grid flags read as 16-byte vectors (neither is
+// written here), the chunks without a new point skipped.
+template <typename T>
+__global__ void k_recon_new_fine(T* __restrict__ L, const uint8_t* __restrict__ act,
+                                 const uint8_t* __restrict__ nxt, Geom g) {
+    pdl_wait();
+    const long long N16 = (long long)g.NJ * g.NJ / 16;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N16;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint4 a = reinterpret_cast<const uint4*>(act)[c], x = reinterpret_cast<const uint4*>(nxt)[c];
+        const uint32_t nw[4] = {x.x & ~a.x, x.y & ~a.y, x.z & ~a.z, x.w & ~a.w};   // flags are 0 or 1
+        if (!(nw[0] | nw[1] | nw[2] | nw[3])) continue;
+        for (int u = 0; u < 16; ++u) {
+            if (!((nw[u >> 2] >> (8 * (u & 3))) & 0xffu)) continue;
+            const long long p = 16 * c + u;
+            const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+            if ((i | k) & 1) L[p] = predict<T>(L, i, k, g.J, g);
+        }
+    }
+    pdl_trigger();
+}
+
 // Details d = u - Pred(u) at the active points (meta == nullptr: every lattice
 // point), significance |d| >= eps (level 0 always significant), and the
 // adjacent zone of every significant point of level j >= 1: the points of
@@ -518,7 +541,38 @@ __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __res
     pdl_trigger();
 }
 
-// Stencil levels and ghost marks.  For an active point P of level l the
+// The closure pass of the finest level J, 16 consecutive lattice points per
+// thread: their level-J marks (odd row or odd column) are read as separate
+// bytes, all in flight, and never the coarser points' bytes, which the pass
+// writes.
+__global__ void k_closure_fine(uint8_t* __restrict__ mask, const uint8_t* __restrict__ excl, Geom g) {
+    pdl_wait();
+    const long long N16 = (long long)g.NJ * g.NJ / 16;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N16;
+         c += (long long)gridDim.x * blockDim.x) {
+        uint8_t b[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const long long p = 16 * c + u;
+            const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+            b[u] = ((i | k) & 1) ? mask[p] : 0;
+        }
+        for (int u = 0; u < 16; ++u) {
+            if (!b[u]) continue;
+            const long long p = 16 * c + u;
+            const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+            for_predictor_points(i, k, g.J, g, [&](int qi, int qk) {
+                const long long q = ((long long)qk << g.L) + qi;
+                if (!excl || !excl[q]) mask[q] = 1;
+            });
+        }
+    }
+    pdl_trigger();
+}
+
+// Stencil levels and ghost marks (each thread reads the flags of 16
+// consecutive lattice points at once, NJ^2 being a multiple of 64, and
+// skips them when none is a grid point).  For an active point P of level l the
 // stencil level along x is the largest j in [l, J] with an active point at
 // P +- h_j e_x (l if none); the stencils read P +- r h_{j*}, r = 1 .. R
 // (R = 2 for 2P = 4, max(2P - 2, P) in general), and the non-active ones
@@ -526,34 +580,44 @@ __global__ void k_closure_level(uint8_t* __restrict__ mask, const uint8_t* __res
 __global__ void k_stencil_ghost(const uint8_t* __restrict__ act, uint8_t* __restrict__ gho,
                                 uint8_t* __restrict__ JJ, Geom g) {
     pdl_wait();
-    const long long N = (long long)g.NJ * g.NJ;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        if (!act[p]) continue;
-        const int i = (int)(p & g.mask), k = (int)(p >> g.L);
-        const int lev = level_of(i, k, g.J);
-        const uint8_t* row = act + ((long long)k << g.L);
-        int jx = lev, jy = lev;
-        for (int j = g.J; j > lev; --j) {
-            const int s = 1 << (g.J - j);
-            if (row[(i + s) & g.mask] || row[(i - s) & g.mask]) { jx = j; break; }
-        }
-        for (int j = g.J; j > lev; --j) {
-            const int s = 1 << (g.J - j);
-            if (act[((long long)((k + s) & g.mask) << g.L) + i] || act[((long long)((k - s) & g.mask) << g.L) + i]) {
-                jy = j;
-                break;
+    const long long N16 = (long long)g.NJ * g.NJ / 16;
+    const int R = dd_reach(g.P);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N16;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4*>(act)[c];
+        if (!(v.x | v.y | v.z | v.w)) continue;
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+        for (int u = 0; u < 16; ++u) {
+            if (!((wv[u >> 2] >> (8 * (u & 3))) & 0xffu)) continue;
+            const long long p = 16 * c + u;
+            const int i = (int)(p & g.mask), k = (int)(p >> g.L);
+            const int lev = level_of(i, k, g.J);
+            const uint8_t* row = act + ((long long)k << g.L);
+            int jx = lev, jy = lev;
+            for (int j = g.J; j > lev; --j) {
+                const int s = 1 << (g.J - j);
+                if (row[(i + s) & g.mask] || row[(i - s) & g.mask]) {
+                    jx = j;
+                    break;
+                }
             }
-        }
-        JJ[p] = (uint8_t)(jx | (jy << 4));
-        const int sx = 1 << (g.J - jx), sy = 1 << (g.J - jy);
-        const int R = dd_reach(g.P);
-        for (int o = -R; o <= R; ++o) {
-            if (o == 0) continue;
-            const long long qx = ((long long)k << g.L) + ((i + o * sx) & g.mask);
-            if (!act[qx]) gho[qx] = 1;
-            const long long qy = ((long long)((k + o * sy) & g.mask) << g.L) + i;
-            if (!act[qy]) gho[qy] = 1;
+            for (int j = g.J; j > lev; --j) {
+                const int s = 1 << (g.J - j);
+                if (act[((long long)((k + s) & g.mask) << g.L) + i] ||
+                    act[((long long)((k - s) & g.mask) << g.L) + i]) {
+                    jy = j;
+                    break;
+                }
+            }
+            JJ[p] = (uint8_t)(jx | (jy << 4));
+            const int sx = 1 << (g.J - jx), sy = 1 << (g.J - jy);
+            for (int o = -R; o <= R; ++o) {
+                if (o == 0) continue;
+                const long long qx = ((long long)k << g.L) + ((i + o * sx) & g.mask);
+                if (!act[qx]) gho[qx] = 1;
+                const long long qy = ((long long)((k + o * sy) & g.mask) << g.L) + i;
+                if (!act[qy]) gho[qy] = 1;
+            }
         }
     }
     pdl_trigger();
@@ -1257,10 +1321,12 @@ void launch_recon_level(T* L, const uint8_t* act, int j, const Geom& g, cudaStre
 }
 template <typename T>
 void launch_recon_new(T* L, const uint8_t* act, const uint8_t* nxt, const Geom& g, cudaStream_t s) {
-    for (int j = 1; j <= g.J; ++j) {
+    for (int j = 1; j < g.J; ++j) {
         launch_pdl(k_recon_new<T>, blocks_for(level_count(j, g)), kThreads, 0, s, L, act, nxt, j, g);
         note_launch();
     }
+    launch_pdl(k_recon_new_fine<T>, blocks_for((long long)g.NJ * g.NJ / 16), kThreads, 0, s, L, act, nxt, g);
+    note_launch();
 }
 template <typename T>
 void launch_reconstruct(T* L, const uint8_t* act, const Geom& g, cudaStream_t s) {
@@ -1282,10 +1348,14 @@ void launch_details_adj(const uint32_t* meta, long long n, const T* L, double ep
     if (n > 0) { launch_pdl(k_details_adj<T>, blocks_for(n), kThreads, 0, s, meta, n, L, eps, det, sig, nxt, g, dn); note_launch(); }
 }
 void launch_closure_level(uint8_t* mask, const uint8_t* excl, int j, const Geom& g, cudaStream_t s) {
-    { launch_pdl(k_closure_level, blocks_for(level_count(j, g)), kThreads, 0, s, mask, excl, j, g); note_launch(); }
+    if (j == g.J)
+        launch_pdl(k_closure_fine, blocks_for((long long)g.NJ * g.NJ / 16), kThreads, 0, s, mask, excl, g);
+    else
+        launch_pdl(k_closure_level, blocks_for(level_count(j, g)), kThreads, 0, s, mask, excl, j, g);
+    note_launch();
 }
 void launch_stencil_ghost(const uint8_t* act, uint8_t* gho, uint8_t* JJ, const Geom& g, cudaStream_t s) {
-    { launch_pdl(k_stencil_ghost, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, act, gho, JJ, g); note_launch(); }
+    { launch_pdl(k_stencil_ghost, blocks_for((long long)g.NJ * g.NJ / 16), kThreads, 0, s, act, gho, JJ, g); note_launch(); }
 }
 void launch_validate_grid(const uint8_t* act, int* flag, const Geom& g, cudaStream_t s) {
     { launch_pdl(k_validate_grid, blocks_for((long long)g.NJ * g.NJ), kThreads, 0, s, act, flag, g); note_launch(); }
