@@ -781,14 +781,22 @@ __global__ void __launch_bounds__(1024) k_compact_scan(const int* __restrict__ b
 // Stable scatter of one tile: thread t's entries of key k go after those of
 // the threads before it (an exclusive scan over the block per key) and the
 // block's base offset, in lattice order.
+// A tile without an entry (its counts from k_compact_count all zero, as in
+// most tiles of a large lattice) returns at once.
 __global__ void __launch_bounds__(kThreads) k_compact_scatter(const uint8_t* __restrict__ act,
                                                               const uint8_t* __restrict__ gho, Geom g, int nkeys,
                                                               const int* __restrict__ blk_off,
+                                                              const int* __restrict__ blk_counts,
                                                               int* __restrict__ list) {
     pdl_wait();
     __shared__ int s_base[kMaxKeys];
     __shared__ int s_w[kThreads / 32][kMaxKeys];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int mine = threadIdx.x < nkeys ? blk_counts[(long long)threadIdx.x * gridDim.x + blockIdx.x] : 0;
+    if (!__syncthreads_or(mine)) {
+        pdl_trigger();
+        return;
+    }
     if (threadIdx.x < nkeys) s_base[threadIdx.x] = blk_off[(long long)threadIdx.x * gridDim.x + blockIdx.x];
     const long long N = (long long)g.NJ * g.NJ;
     const long long p0 = (long long)blockIdx.x * kTile + 16LL * threadIdx.x;
@@ -1366,7 +1374,8 @@ void launch_compact(const uint8_t* act, const uint8_t* gho, const Geom& g, int n
     const int nblk = (int)((N + kTile - 1) / kTile);
     { launch_pdl(k_compact_count, nblk, kThreads, 0, s, act, gho, g, nkeys, blk_counts); note_launch(); }
     { launch_pdl(k_compact_scan, 1, 1024, 0, s, blk_counts, nblk, nkeys, blk_off, counts); note_launch(); }
-    { launch_pdl(k_compact_scatter, nblk, kThreads, 0, s, act, gho, g, nkeys, blk_off, list); note_launch(); }
+    { launch_pdl(k_compact_scatter, nblk, kThreads, 0, s, act, gho, g, nkeys, (const int*)blk_off,
+                 (const int*)blk_counts, list); note_launch(); }
 }
 template <typename T>
 void launch_finalize(const int* list, long long n, const uint8_t* JJ, const T* L, uint32_t* meta, T* omega,
