@@ -17,6 +17,8 @@
 // for n = 4096); no bit reversal.
 #include <type_traits>
 
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace wrc {
@@ -523,6 +525,22 @@ __global__ void __launch_bounds__(256) k_px_inv_pair(const cx_t<T>* __restrict__
     pdl_trigger();
 }
 
+// Test switch WRC_TEST_POISON_ROWS: the rows of the pairs not listed (flag
+// rows[q] clear) of up to two lattices set to NaN after the inverse passes,
+// so that a step that read one would show it.
+template <typename T>
+__global__ void k_poison_rows(T* __restrict__ a, T* __restrict__ b, const int* __restrict__ rows, int n) {
+    pdl_wait();
+    const long long N = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (rows[(int)(e / n) >> 1]) continue;
+        a[e] = T(NAN);
+        if (b) b[e] = T(NAN);
+    }
+    pdl_trigger();
+}
+
 // out[c][r] = in[r][c] for a rows x cols complex matrix, 32 x 32 tiles.
 template <typename C>
 __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int rows, int cols) {
@@ -582,6 +600,11 @@ constexpr int kMaxSmem = (int)sizeof(double2) * smlen_of(kMaxLattice);
 
 // The kernels of one (E, R0) shape; dynamic shared memory limits are
 // process-wide per kernel, so they are set once for the largest lattice.
+bool poison_rows() {
+    const char* v = std::getenv("WRC_TEST_POISON_ROWS");
+    return v && std::atoi(v) != 0;
+}
+
 template <typename T, int E, int R0>
 struct Shape {
     static int setup() {
@@ -636,9 +659,11 @@ struct Shape {
                 C* Q = st ? C4 : C3;
                 { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, QT, Q, n, n); note_launch(); }
                 { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, Q, U, V, n, logn, tw, rows); note_launch(); }
+                if (rows && poison_rows()) { launch_pdl(k_poison_rows<T>, 1216, 256, 0, s, U, V, rows, n); note_launch(); }
                 if (st) {
                     { launch_pdl(k_transpose<C>, g_nn, tb, 0, s, WT, C4, n, n); note_launch(); }
                     { launch_pdl(k_px_inv_pair<T, E, R0>, b_full, thr, smem, s, C4, S11, S12, n, logn, tw, rows); note_launch(); }
+                    if (rows && poison_rows()) { launch_pdl(k_poison_rows<T>, 1216, 256, 0, s, S11, S12, rows, n); note_launch(); }
                 }
                 return;
             }
@@ -648,6 +673,7 @@ struct Shape {
                                                                  scale, 1); note_launch(); }
         { launch_pdl(k_transpose<C>, g_hn, tb, 0, s, ST, S, h, n); note_launch(); }
         { launch_pdl(k_px_inv_real<T, E, R0>, b_half, thr, smem, s, S, psi, n, logn, tw, rows); note_launch(); }
+        if (rows && poison_rows()) { launch_pdl(k_poison_rows<T>, 1216, 256, 0, s, psi, (T*)nullptr, rows, n); note_launch(); }
         (void)C2;
     }
 };
